@@ -1,0 +1,153 @@
+/*
+ * tuckersinr.h -- C ABI of the GB300 (sm_103a) library for SINR evaluation
+ * from the groupwise Tucker form of MIMO channel submatrices
+ * (Zhang, Zhu, Zhang: "Compressing MIMO Channel Submatrices with Tucker
+ * Decomposition", arXiv 2401.09792).
+ *
+ * System (Section 2.2): J cells, one BS and one UE per cell (the paper's
+ * experiments keep one interfering UE per cell, Section 4).  Link (i, k) is
+ * the channel from BS k to the UE of cell i; it is stored as ch = i * J + k.
+ * Every BS sends L streams to its own UE and interferes with all other UEs.
+ *
+ * Groupwise Tucker form (eq. 14): X_ik ~ G_ik x_1 A_i x_2 B_k x_3 C_ik with
+ * orthonormal A_i (M x m), B_k (N x n), C_ik (P x p) and core G_ik
+ * (m x n x p).  For subcarrier kappa with path coefficients c_ik(kappa) in
+ * C^P the compressed channel is (eq. 15)
+ *     H~_ik(kappa) = G_ik x_3 (c_ik(kappa)* C_ik)   (m x n),
+ * and the SINR is evaluated on H~ alone because A and B cancel (Section 3.3).
+ *
+ * Conventions
+ *   - complex numbers are interleaved (re, im) float32 pairs (ts_c64);
+ *   - every array is row-major and dense, with the layouts given per call;
+ *   - every data pointer is DEVICE memory owned by the caller unless a call
+ *     says otherwise; the library allocates nothing and frees nothing;
+ *   - calls are asynchronous on the given CUDA stream (a cudaStream_t passed
+ *     as void*; NULL = the legacy default stream) and never synchronise;
+ *   - return value: TS_OK, or a TS_ERR_* code.  Argument errors are detected
+ *     before any launch and leave the outputs untouched.  TS_ERR_CUDA reports
+ *     a launch failure (the CUDA error is kept for ts_last_cuda_error()).
+ *     Numerical trouble inside a kernel does not fail the call: it sets bits
+ *     in the per-result flags array (when given) and the affected SINR values
+ *     become NaN.
+ *   - the gradient of a real loss l with respect to a complex parameter
+ *     z = x + iy is reported as dl/dx + i dl/dy.
+ */
+#ifndef TUCKERSINR_H
+#define TUCKERSINR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  float re, im;
+} ts_c64;
+
+/* Sizes of one multi-cell system (notation of the paper, Section 2.1). */
+typedef struct {
+  int32_t J;          /* cells = base stations = groups                        */
+  int32_t M, N, P;    /* UE antennas, BS antennas, submatrices per link         */
+  int32_t m, n, p;    /* Tucker ranks: 1 <= m <= min(M, 16), n <= min(N, 512),
+                         p <= min(P, 32), P <= 1024, P * p <= 8192            */
+  int32_t K;          /* OFDM subcarriers, kappa = 0 .. K-1                      */
+  int32_t L;          /* streams per UE, 1 <= L <= min(m, n)                     */
+  float delta_f_hz;   /* subcarrier spacing (path-form coefficients only)      */
+} ts_dims;
+
+/* Path coefficients c_ik(kappa) of eq. (2) / eq. (9). */
+enum { TS_COEF_DENSE = 0, TS_COEF_PATHS = 1 };
+typedef struct {
+  int32_t mode;        /* TS_COEF_DENSE or TS_COEF_PATHS                         */
+  const ts_c64* c;     /* DENSE: c[ch][kappa][P]                                 */
+  const ts_c64* alpha; /* PATHS: alpha[ch][P]: c_p(kappa) = conj(alpha_p        */
+  const float* tau_s;  /* PATHS: tau[ch][P] (s)   * exp(-j 2 pi kappa df tau_p)) */
+} ts_coef;
+
+/* Status codes. */
+enum {
+  TS_OK = 0,
+  TS_ERR_DIMS = 1,      /* sizes out of range or inconsistent                 */
+  TS_ERR_NULL = 2,      /* a required pointer is NULL                         */
+  TS_ERR_ALIGN = 3,     /* a pointer is not 8-byte aligned                    */
+  TS_ERR_WORKSPACE = 4, /* workspace too small (see ts_workspace_bytes)       */
+  TS_ERR_CUDA = 5,      /* a CUDA launch failed                               */
+  TS_ERR_MODE = 6       /* unknown coefficient mode or operation              */
+};
+
+/* Per-result flag bits (flags[i][kappa], uint8). */
+enum {
+  TS_FLAG_NOT_PD = 1,         /* a Cholesky pivot was not positive            */
+  TS_FLAG_NONFINITE = 2,      /* a non-finite value reached the solve         */
+  TS_FLAG_RANK_DEFICIENT = 4, /* a serving link had a zero singular value
+                                 among the top L (SVD precoding)              */
+  TS_FLAG_EIG_UNCONVERGED = 8 /* the Jacobi eigensolver hit its sweep cap     */
+};
+
+/* Operations, for ts_workspace_bytes. */
+enum {
+  TS_OP_SINR_SVD = 0,
+  TS_OP_SINR_MMSE = 1
+};
+
+/* Human-readable name of a status code (static storage). */
+const char* ts_status_string(int status);
+
+/* The CUDA error (cudaError_t as int) behind the last TS_ERR_CUDA on this
+ * host thread, or 0. */
+int ts_last_cuda_error(void);
+
+/* Version of this ABI (incremented on any incompatible change). */
+int ts_abi_version(void);
+
+/* Device workspace, in bytes, that operation `op` needs for sizes `d`.
+ * Returns 0 for invalid sizes.  The caller allocates it (256-byte aligned)
+ * and passes it to the call; its contents need no initialisation. */
+size_t ts_workspace_bytes(const ts_dims* d, int op);
+
+/* a0 -- path coefficients on the subcarrier grid (eq. 2, eq. 9):
+ *   c[ch][kappa][p] = conj(alpha[ch][p]) * exp(+j 2 pi kappa df tau[ch][p]).
+ * The phase kappa * df * tau is reduced modulo one turn in 64-bit fixed point
+ * before the float32 sine/cosine, so its error does not grow with kappa.
+ * alpha: [J*J][P]; tau_s: [J*J][P]; c (out): [J*J][K][P]. */
+int ts_coefficients(const ts_dims* d, const ts_c64* alpha, const float* tau_s,
+                    ts_c64* c, void* stream);
+
+/* Wideband precoder carried into the compressed domain (Section 3.3, with the
+ * matrix form A G B^T of the mode products of Section 2.3):
+ *   Pt[k] = B_k^T P_k   (n x L).
+ * B: [J][N][n]; Pfull: [J][N][L]; Pt (out): [J][n][L]. */
+int ts_project_precoder(const ts_dims* d, const ts_c64* B, const ts_c64* Pfull,
+                        ts_c64* Pt, void* stream);
+
+/* MMSE SINR with caller-given wideband precoders (eq. 3-6 evaluated on the
+ * compressed form, eq. 15 and eq. 24-28):
+ *   E_ik(kappa) = H~_ik(kappa) Pt_k,  Q~_i = sum_k E_ik E_ik* + sigma2_i I_m,
+ *   SINR_i,r(kappa) = s~_r / (w~_r* Q~_i w~_r - s~_r),  W~ = Q~_i^{-1} E_ii.
+ * G: [J*J][p][m][n] (core, mode-3 slabs G_ik[:, :, q], n fastest);
+ * C: [J*J][P][p]; coef: see ts_coef; Pt: [J][n][L] (ts_project_precoder);
+ * sigma2: [J] noise power per UE; sinr (out): [J][K][L] float;
+ * flags (out, may be NULL): [J][K] uint8 TS_FLAG_* bits;
+ * ws: workspace of ts_workspace_bytes(d, TS_OP_SINR_MMSE) bytes. */
+int ts_sinr_mmse(const ts_dims* d, const ts_coef* coef, const ts_c64* G,
+                 const ts_c64* C, const ts_c64* Pt, const float* sigma2,
+                 float* sinr, uint8_t* flags, void* ws, size_t ws_bytes,
+                 void* stream);
+
+/* SVD-precoded SINR (eq. 7 and eq. 23-28): every BS k precodes with the top-L
+ * right singular vectors V~_k(kappa) of its compressed serving channel
+ * H~_kk(kappa), found from a Jacobi eigensolve of H~_kk H~_kk* (m x m); then
+ * the same MMSE SINR as ts_sinr_mmse with E_ik = H~_ik V~_k.  Streams are
+ * ordered by decreasing singular value.  Arguments as ts_sinr_mmse; ws holds
+ * ts_workspace_bytes(d, TS_OP_SINR_SVD) bytes. */
+int ts_sinr_svd(const ts_dims* d, const ts_coef* coef, const ts_c64* G,
+                const ts_c64* C, const float* sigma2, float* sinr,
+                uint8_t* flags, void* ws, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TUCKERSINR_H */

@@ -1,0 +1,203 @@
+// C ABI of the tuckersinr library: argument checks, workspace carving and
+// kernel dispatch.  No allocation, no synchronisation, no exceptions.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "kernels.h"
+#include "tuckersinr.h"
+
+namespace {
+
+thread_local int g_last_cuda = 0;
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return TS_OK;
+  g_last_cuda = (int)e;
+  return TS_ERR_CUDA;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+bool aligned8(const void* p) { return ((uintptr_t)p & 7u) == 0; }
+
+// Sizes the SINR kernels accept.
+int check_dims(const ts_dims* d) {
+  if (d == nullptr) return TS_ERR_NULL;
+  if (d->J < 1 || d->M < 1 || d->N < 1 || d->P < 1 || d->K < 1) return TS_ERR_DIMS;
+  if (d->m < 1 || d->n < 1 || d->p < 1 || d->L < 1) return TS_ERR_DIMS;
+  if (d->m > d->M || d->n > d->N || d->p > d->P) return TS_ERR_DIMS;
+  if (d->m > ts::kMaxRankM) return TS_ERR_DIMS;
+  if (d->L > d->m || d->L > d->n) return TS_ERR_DIMS;
+  // staging limits of the kernels: C_ik (P x p) and one H~ (m x n) per
+  // subcarrier live in shared memory
+  if (d->P > 1024 || d->p > 32 || (int64_t)d->P * d->p > 8192 || d->n > 512) return TS_ERR_DIMS;
+  if ((int64_t)d->J * d->J > 65535 || d->J > 65535) return TS_ERR_DIMS;
+  return TS_OK;
+}
+
+// Workspace layout (byte offsets from the base, each 256-byte aligned).
+struct Workspace {
+  size_t turns = 0, V = 0, pflag = 0, F = 0, total = 0;
+};
+
+Workspace carve(const ts_dims* d, int op) {
+  Workspace w;
+  size_t o = 0;
+  const size_t nch = (size_t)d->J * d->J;
+  w.turns = o;
+  o = align_up(o + nch * d->P * sizeof(unsigned long long), 256);
+  if (op == TS_OP_SINR_SVD) {
+    w.V = o;
+    o = align_up(o + (size_t)d->J * d->K * d->n * d->L * sizeof(float2), 256);
+    w.pflag = o;
+    o = align_up(o + (size_t)d->J * d->K, 256);
+  } else {
+    w.F = o;
+    o = align_up(o + nch * d->p * d->m * d->L * sizeof(float2), 256);
+  }
+  w.total = o;
+  return w;
+}
+
+int check_coef(const ts_coef* c) {
+  if (c == nullptr) return TS_ERR_NULL;
+  if (c->mode == TS_COEF_DENSE) {
+    if (c->c == nullptr) return TS_ERR_NULL;
+    if (!aligned8(c->c)) return TS_ERR_ALIGN;
+  } else if (c->mode == TS_COEF_PATHS) {
+    if (c->alpha == nullptr || c->tau_s == nullptr) return TS_ERR_NULL;
+    if (!aligned8(c->alpha) || ((uintptr_t)c->tau_s & 3u)) return TS_ERR_ALIGN;
+  } else {
+    return TS_ERR_MODE;
+  }
+  return TS_OK;
+}
+
+ts::SinrArgs base_args(const ts_dims* d, const ts_coef* coef, const ts_c64* G, const ts_c64* C,
+                       const float* sigma2, float* sinr, uint8_t* flags, char* ws,
+                       const Workspace& w) {
+  ts::SinrArgs a{};
+  a.J = d->J; a.m = d->m; a.n = d->n; a.p = d->p; a.P = d->P; a.K = d->K; a.L = d->L;
+  a.coef_mode = coef->mode;
+  a.G = reinterpret_cast<const float2*>(G);
+  a.C = reinterpret_cast<const float2*>(C);
+  a.coef = reinterpret_cast<const float2*>(coef->mode == TS_COEF_DENSE ? coef->c : coef->alpha);
+  a.turns = reinterpret_cast<const unsigned long long*>(ws + w.turns);
+  a.sigma2 = sigma2;
+  a.sinr = sinr;
+  a.flags = flags;
+  return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ts_status_string(int status) {
+  switch (status) {
+    case TS_OK: return "ok";
+    case TS_ERR_DIMS: return "sizes out of range or inconsistent";
+    case TS_ERR_NULL: return "a required pointer is NULL";
+    case TS_ERR_ALIGN: return "a pointer is not suitably aligned";
+    case TS_ERR_WORKSPACE: return "workspace too small";
+    case TS_ERR_CUDA: return "CUDA launch failed";
+    case TS_ERR_MODE: return "unknown coefficient mode or operation";
+    default: return "unknown status";
+  }
+}
+
+int ts_last_cuda_error(void) { return g_last_cuda; }
+
+int ts_abi_version(void) { return 1; }
+
+size_t ts_workspace_bytes(const ts_dims* d, int op) {
+  if (check_dims(d) != TS_OK) return 0;
+  if (op != TS_OP_SINR_SVD && op != TS_OP_SINR_MMSE) return 0;
+  return carve(d, op).total;
+}
+
+int ts_coefficients(const ts_dims* d, const ts_c64* alpha, const float* tau_s, ts_c64* c,
+                    void* stream) {
+  if (d == nullptr || alpha == nullptr || tau_s == nullptr || c == nullptr) return TS_ERR_NULL;
+  if (d->J < 1 || d->K < 1 || d->P < 1) return TS_ERR_DIMS;
+  if (!aligned8(alpha) || !aligned8(c) || ((uintptr_t)tau_s & 3u)) return TS_ERR_ALIGN;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int nch = d->J * d->J;
+  return cuda_status(ts::launch_coefficients(reinterpret_cast<const float2*>(alpha), tau_s,
+                                             d->delta_f_hz, nch, d->K, d->P,
+                                             reinterpret_cast<float2*>(c), s));
+}
+
+int ts_project_precoder(const ts_dims* d, const ts_c64* B, const ts_c64* Pfull, ts_c64* Pt,
+                        void* stream) {
+  int st = check_dims(d);
+  if (st != TS_OK) return st;
+  if (B == nullptr || Pfull == nullptr || Pt == nullptr) return TS_ERR_NULL;
+  if (!aligned8(B) || !aligned8(Pfull) || !aligned8(Pt)) return TS_ERR_ALIGN;
+  return cuda_status(ts::launch_project_precoder(
+      reinterpret_cast<const float2*>(B), reinterpret_cast<const float2*>(Pfull), d->J, d->N, d->n,
+      d->L, reinterpret_cast<float2*>(Pt), static_cast<cudaStream_t>(stream)));
+}
+
+static int sinr_common_checks(const ts_dims* d, const ts_coef* coef, const ts_c64* G,
+                              const ts_c64* C, const float* sigma2, float* sinr, void* ws,
+                              size_t ws_bytes, int op) {
+  int st = check_dims(d);
+  if (st != TS_OK) return st;
+  st = check_coef(coef);
+  if (st != TS_OK) return st;
+  if (G == nullptr || C == nullptr || sigma2 == nullptr || sinr == nullptr) return TS_ERR_NULL;
+  if (!aligned8(G) || !aligned8(C) || ((uintptr_t)sigma2 & 3u) || ((uintptr_t)sinr & 3u))
+    return TS_ERR_ALIGN;
+  const size_t need = carve(d, op).total;
+  if (ws == nullptr || ws_bytes < need) return TS_ERR_WORKSPACE;
+  if (((uintptr_t)ws & 255u) != 0) return TS_ERR_ALIGN;
+  return TS_OK;
+}
+
+int ts_sinr_mmse(const ts_dims* d, const ts_coef* coef, const ts_c64* G, const ts_c64* C,
+                 const ts_c64* Pt, const float* sigma2, float* sinr, uint8_t* flags, void* ws,
+                 size_t ws_bytes, void* stream) {
+  int st = sinr_common_checks(d, coef, G, C, sigma2, sinr, ws, ws_bytes, TS_OP_SINR_MMSE);
+  if (st != TS_OK) return st;
+  if (Pt == nullptr) return TS_ERR_NULL;
+  if (!aligned8(Pt)) return TS_ERR_ALIGN;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Workspace w = carve(d, TS_OP_SINR_MMSE);
+  char* base = static_cast<char*>(ws);
+  ts::SinrArgs a = base_args(d, coef, G, C, sigma2, sinr, flags, base, w);
+  float2* F = reinterpret_cast<float2*>(base + w.F);
+  a.F = F;
+  cudaError_t e = cudaSuccess;
+  if (coef->mode == TS_COEF_PATHS)
+    e = ts::launch_turns(coef->tau_s, d->delta_f_hz, d->J * d->J * d->P,
+                         reinterpret_cast<unsigned long long*>(base + w.turns), s);
+  if (e == cudaSuccess)
+    e = ts::launch_mmse_fold(a.G, reinterpret_cast<const float2*>(Pt), d->J, d->m, d->n, d->p,
+                             d->L, F, s);
+  if (e == cudaSuccess) e = ts::launch_sinr_accumulate(a, false, s);
+  return cuda_status(e);
+}
+
+int ts_sinr_svd(const ts_dims* d, const ts_coef* coef, const ts_c64* G, const ts_c64* C,
+                const float* sigma2, float* sinr, uint8_t* flags, void* ws, size_t ws_bytes,
+                void* stream) {
+  int st = sinr_common_checks(d, coef, G, C, sigma2, sinr, ws, ws_bytes, TS_OP_SINR_SVD);
+  if (st != TS_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Workspace w = carve(d, TS_OP_SINR_SVD);
+  char* base = static_cast<char*>(ws);
+  ts::SinrArgs a = base_args(d, coef, G, C, sigma2, sinr, flags, base, w);
+  a.V = reinterpret_cast<float2*>(base + w.V);
+  a.pflag = reinterpret_cast<uint8_t*>(base + w.pflag);
+  cudaError_t e = cudaSuccess;
+  if (coef->mode == TS_COEF_PATHS)
+    e = ts::launch_turns(coef->tau_s, d->delta_f_hz, d->J * d->J * d->P,
+                         reinterpret_cast<unsigned long long*>(base + w.turns), s);
+  if (e == cudaSuccess) e = ts::launch_svd_precoder(a, s);
+  if (e == cudaSuccess) e = ts::launch_sinr_accumulate(a, true, s);
+  return cuda_status(e);
+}
+
+}  // extern "C"

@@ -1,0 +1,13 @@
+// Template instances of the SINR kernels for groups of 16 lanes (m <= 16).
+#include "sinr_impl.cuh"
+
+namespace ts {
+namespace detail {
+template cudaError_t run_precoder<16, 4>(const SinrArgs&, cudaStream_t);
+template cudaError_t run_accumulate<16, 4>(const SinrArgs&, bool, cudaStream_t);
+template cudaError_t run_precoder<16, 8>(const SinrArgs&, cudaStream_t);
+template cudaError_t run_accumulate<16, 8>(const SinrArgs&, bool, cudaStream_t);
+template cudaError_t run_precoder<16, 16>(const SinrArgs&, cudaStream_t);
+template cudaError_t run_accumulate<16, 16>(const SinrArgs&, bool, cudaStream_t);
+}  // namespace detail
+}  // namespace ts

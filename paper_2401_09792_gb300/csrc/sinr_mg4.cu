@@ -1,0 +1,11 @@
+// Template instances of the SINR kernels for groups of 4 lanes (m <= 4).
+#include "sinr_impl.cuh"
+
+namespace ts {
+namespace detail {
+template cudaError_t run_precoder<4, 2>(const SinrArgs&, cudaStream_t);
+template cudaError_t run_accumulate<4, 2>(const SinrArgs&, bool, cudaStream_t);
+template cudaError_t run_precoder<4, 4>(const SinrArgs&, cudaStream_t);
+template cudaError_t run_accumulate<4, 4>(const SinrArgs&, bool, cudaStream_t);
+}  // namespace detail
+}  // namespace ts

@@ -1,0 +1,13 @@
+// Template instances of the SINR kernels for groups of 8 lanes (m <= 8).
+#include "sinr_impl.cuh"
+
+namespace ts {
+namespace detail {
+template cudaError_t run_precoder<8, 2>(const SinrArgs&, cudaStream_t);
+template cudaError_t run_accumulate<8, 2>(const SinrArgs&, bool, cudaStream_t);
+template cudaError_t run_precoder<8, 4>(const SinrArgs&, cudaStream_t);
+template cudaError_t run_accumulate<8, 4>(const SinrArgs&, bool, cudaStream_t);
+template cudaError_t run_precoder<8, 8>(const SinrArgs&, cudaStream_t);
+template cudaError_t run_accumulate<8, 8>(const SinrArgs&, bool, cudaStream_t);
+}  // namespace detail
+}  // namespace ts

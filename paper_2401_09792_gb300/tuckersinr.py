@@ -1,0 +1,190 @@
+"""Python binding of ``libtuckersinr.so`` (C ABI in ``include/tuckersinr.h``).
+
+Argument marshalling only: every step of the SINR path runs in the CUDA
+library.  Tensors are PyTorch CUDA tensors used as device memory; complex
+arrays are ``torch.complex64`` (interleaved re/im, the ABI's ``ts_c64``).
+Functions carry the C names (``ts_sinr_svd`` ...) and raise ``TsError`` on a
+non-zero status.  There is no CPU fallback: if the library or a GPU is
+missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libtuckersinr.so")
+
+TS_COEF_DENSE, TS_COEF_PATHS = 0, 1
+TS_OP_SINR_SVD, TS_OP_SINR_MMSE = 0, 1
+TS_FLAG_NOT_PD, TS_FLAG_NONFINITE, TS_FLAG_RANK_DEFICIENT, TS_FLAG_EIG_UNCONVERGED = 1, 2, 4, 8
+
+
+class TsError(RuntimeError):
+    """A tuckersinr call returned a non-zero status."""
+
+    def __init__(self, fn: str, status: int, lib=None):
+        msg = lib.ts_status_string(status).decode() if lib is not None else str(status)
+        extra = ""
+        if lib is not None and status == 5:
+            extra = f" (cudaError {lib.ts_last_cuda_error()})"
+        super().__init__(f"{fn}: status {status}: {msg}{extra}")
+        self.status = status
+
+
+class ts_dims(ctypes.Structure):
+    _fields_ = [("J", ctypes.c_int32), ("M", ctypes.c_int32), ("N", ctypes.c_int32),
+                ("P", ctypes.c_int32), ("m", ctypes.c_int32), ("n", ctypes.c_int32),
+                ("p", ctypes.c_int32), ("K", ctypes.c_int32), ("L", ctypes.c_int32),
+                ("delta_f_hz", ctypes.c_float)]
+
+
+class ts_coef(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("c", ctypes.c_void_p), ("alpha", ctypes.c_void_p),
+                ("tau_s", ctypes.c_void_p)]
+
+
+_P = ctypes.c_void_p
+_SIG = {
+    "ts_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "ts_last_cuda_error": (ctypes.c_int, []),
+    "ts_abi_version": (ctypes.c_int, []),
+    "ts_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(ts_dims), ctypes.c_int]),
+    "ts_coefficients": (ctypes.c_int, [ctypes.POINTER(ts_dims), _P, _P, _P, _P]),
+    "ts_project_precoder": (ctypes.c_int, [ctypes.POINTER(ts_dims), _P, _P, _P, _P]),
+    "ts_sinr_mmse": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.POINTER(ts_coef), _P, _P, _P,
+                                    _P, _P, _P, _P, ctypes.c_size_t, _P]),
+    "ts_sinr_svd": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.POINTER(ts_coef), _P, _P, _P,
+                                   _P, _P, _P, ctypes.c_size_t, _P]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the shared library (once) and declare every exported signature."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it first (__graft_entry__.build())")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIG.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+@dataclass(frozen=True)
+class Dims:
+    """Sizes of one system (see ts_dims)."""
+
+    J: int
+    M: int
+    N: int
+    P: int
+    m: int
+    n: int
+    p: int
+    K: int
+    L: int
+    delta_f_hz: float = 15e3
+
+    def c(self) -> ts_dims:
+        return ts_dims(self.J, self.M, self.N, self.P, self.m, self.n, self.p, self.K, self.L,
+                       self.delta_f_hz)
+
+    @staticmethod
+    def of(w) -> "Dims":
+        return Dims(w.J, w.M, w.N, w.P, w.m, w.n, w.p, w.K, w.L, w.delta_f_hz)
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("tensor must be on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream or None
+
+
+def _check(fn: str, st: int):
+    if st != 0:
+        raise TsError(fn, st, _lib)
+
+
+def ts_workspace_bytes(d: Dims, op: int) -> int:
+    return load().ts_workspace_bytes(ctypes.byref(d.c()), op)
+
+
+def workspace(d: Dims, op: int, device="cuda") -> torch.Tensor:
+    """A device workspace buffer for `op` (PyTorch allocations are 256-byte aligned)."""
+    nb = ts_workspace_bytes(d, op)
+    if nb == 0:
+        raise TsError("ts_workspace_bytes", 1, load())
+    return torch.empty(nb, dtype=torch.uint8, device=device)
+
+
+def make_coef(c=None, alpha=None, tau=None) -> tuple[ts_coef, tuple]:
+    """Dense (c) or path-form (alpha, tau) coefficients; returns the struct and the
+    tensors it points into (keep them alive for the call)."""
+    if c is not None:
+        return ts_coef(TS_COEF_DENSE, _ptr(c), None, None), (c,)
+    return ts_coef(TS_COEF_PATHS, None, _ptr(alpha), _ptr(tau)), (alpha, tau)
+
+
+def ts_coefficients(d: Dims, alpha, tau, c, stream=None):
+    lib = load()
+    _check("ts_coefficients", lib.ts_coefficients(ctypes.byref(d.c()), _ptr(alpha), _ptr(tau),
+                                                  _ptr(c), _stream(stream)))
+
+
+def ts_project_precoder(d: Dims, B, Pfull, Pt, stream=None):
+    lib = load()
+    _check("ts_project_precoder", lib.ts_project_precoder(ctypes.byref(d.c()), _ptr(B), _ptr(Pfull),
+                                                          _ptr(Pt), _stream(stream)))
+
+
+def ts_sinr_mmse(d: Dims, coef: ts_coef, G, C, Pt, sigma2, sinr, flags, ws, stream=None):
+    lib = load()
+    _check("ts_sinr_mmse", lib.ts_sinr_mmse(ctypes.byref(d.c()), ctypes.byref(coef), _ptr(G), _ptr(C),
+                                            _ptr(Pt), _ptr(sigma2), _ptr(sinr), _ptr(flags),
+                                            _ptr(ws), ws.numel(), _stream(stream)))
+
+
+def ts_sinr_svd(d: Dims, coef: ts_coef, G, C, sigma2, sinr, flags, ws, stream=None):
+    lib = load()
+    _check("ts_sinr_svd", lib.ts_sinr_svd(ctypes.byref(d.c()), ctypes.byref(coef), _ptr(G), _ptr(C),
+                                          _ptr(sigma2), _ptr(sinr), _ptr(flags), _ptr(ws),
+                                          ws.numel(), _stream(stream)))
+
+
+# ----------------------------------------------------------- layout marshalling
+def core_to_device(G, device="cuda") -> torch.Tensor:
+    """(J, J, m, n, p) complex -> device [J*J][p][m][n] complex64."""
+    import numpy as np
+    J, _, m, n, p = G.shape
+    a = np.ascontiguousarray(np.transpose(G, (0, 1, 4, 2, 3)).reshape(J * J, p, m, n))
+    return torch.from_numpy(a.astype(np.complex64)).to(device)
+
+
+def factor_to_device(X, device="cuda") -> torch.Tensor:
+    """Any complex array -> contiguous complex64 device tensor, leading link axes merged
+    when the first two axes are (J, J)."""
+    import numpy as np
+    return torch.from_numpy(np.ascontiguousarray(X).astype(np.complex64)).to(device)
+
+
+def real_to_device(x, device="cuda") -> torch.Tensor:
+    import numpy as np
+    return torch.from_numpy(np.ascontiguousarray(x).astype(np.float32)).to(device)

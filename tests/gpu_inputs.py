@@ -1,0 +1,82 @@
+"""Shared set-up for the GPU parity tests: seeded inputs through the oracle
+(expected values) and through the C ABI (device results)."""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+import torch
+
+from oracle import sinr as S
+from paper_2401_09792_gb300 import synth
+from paper_2401_09792_gb300 import tuckersinr as ts
+
+
+def workload(base: synth.Workload, **kw) -> synth.Workload:
+    return dataclasses.replace(base, **kw)
+
+
+class Case:
+    """One synthetic system: host (float64) arrays and device (complex64) copies."""
+
+    def __init__(self, w: synth.Workload, dev="cuda"):
+        self.w = w
+        self.tk = synth.direct_tucker(w)
+        self.alpha, self.tau = synth.path_gains_delays(w)
+        self.s2 = synth.noise_powers(w)
+        self.Pw = synth.wideband_precoders(w)
+        self.coef = S.coefficients(self.alpha, self.tau, w.K, w.delta_f_hz)
+        self.Ptn = np.stack([S.project_precoder(self.tk["B"][k], self.Pw[k]) for k in range(w.J)])
+        J, P = w.J, w.P
+        self.d = ts.Dims.of(w)
+        self.dev = dev
+        self.G = ts.core_to_device(self.tk["G"], dev)
+        self.C = ts.factor_to_device(self.tk["C"].reshape(J * J, P, w.p), dev)
+        self.c = ts.factor_to_device(self.coef.reshape(J * J, w.K, P), dev)
+        self.al = ts.factor_to_device(self.alpha.reshape(J * J, P), dev)
+        self.ta = ts.real_to_device(self.tau.reshape(J * J, P), dev)
+        self.sig = ts.real_to_device(self.s2, dev)
+        self.B = ts.factor_to_device(self.tk["B"], dev)
+        self.Pf = ts.factor_to_device(self.Pw, dev)
+
+    def coef_struct(self, mode: str):
+        if mode == "dense":
+            return ts.make_coef(c=self.c)
+        return ts.make_coef(alpha=self.al, tau=self.ta)
+
+    def gpu_sinr(self, precoder: str, mode: str = "paths"):
+        w = self.w
+        cs, keep = self.coef_struct(mode)
+        sinr = torch.full((w.J, w.K, w.L), float("nan"), device=self.dev)
+        flags = torch.full((w.J, w.K), 255, dtype=torch.uint8, device=self.dev)
+        if precoder == "svd":
+            ws = ts.workspace(self.d, ts.TS_OP_SINR_SVD, self.dev)
+            ts.ts_sinr_svd(self.d, cs, self.G, self.C, self.sig, sinr, flags, ws)
+        else:
+            Pt = torch.empty(w.J, w.n, w.L, dtype=torch.complex64, device=self.dev)
+            ts.ts_project_precoder(self.d, self.B, self.Pf, Pt)
+            ws = ts.workspace(self.d, ts.TS_OP_SINR_MMSE, self.dev)
+            ts.ts_sinr_mmse(self.d, cs, self.G, self.C, Pt, self.sig, sinr, flags, ws)
+        torch.cuda.synchronize()
+        del keep
+        return sinr.cpu().numpy().astype(np.float64), flags.cpu().numpy()
+
+    def oracle_sinr(self, precoder: str):
+        Pt = self.Ptn if precoder == "mmse" else None
+        return S.tucker_sinr(self.tk["G"], self.tk["C"], self.coef, self.s2, self.w.L, precoder, Pt)
+
+
+def svd_gap(case: Case) -> np.ndarray:
+    """Smallest relative gap between the squared singular values that the SVD
+    precoder must separate (within the top L, and between L and L+1), over all
+    serving links, per subcarrier: (K,)."""
+    w = case.w
+    gaps = np.full(w.K, np.inf)
+    Hs = S.compressed_channels(case.tk["G"], case.tk["C"], case.coef)
+    for k in range(w.J):
+        sv = np.linalg.svd(Hs[k, k], compute_uv=False) ** 2          # (K, min(m, n))
+        top = sv[:, :min(w.L + 1, sv.shape[1])]
+        d = -np.diff(top, axis=1) / sv[:, :1]
+        if d.shape[1]:
+            gaps = np.minimum(gaps, d.min(axis=1))
+    return gaps

@@ -1,0 +1,91 @@
+"""The C ABI library loads and exports what include/tuckersinr.h declares;
+host-side argument checks (no GPU needed: nothing here launches a kernel)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2401_09792_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "tuckersinr.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    path = B.build()
+    from paper_2401_09792_gb300 import tuckersinr as ts
+    return ts.load(path)
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ts_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("ts_sinr_svd", "ts_sinr_mmse", "ts_workspace_bytes", "ts_status_string",
+                     "ts_coefficients", "ts_project_precoder"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_names_match_the_header():
+    from paper_2401_09792_gb300 import tuckersinr as ts
+    for name in declared_functions():
+        assert name in ts._SIG, f"binding lacks {name}"
+
+
+def test_status_strings(lib):
+    assert lib.ts_status_string(0) == b"ok"
+    assert b"workspace" in lib.ts_status_string(4)
+    assert lib.ts_abi_version() >= 1
+
+
+def _dims(**kw):
+    from paper_2401_09792_gb300 import tuckersinr as ts
+    base = dict(J=2, M=4, N=32, P=8, m=4, n=8, p=4, K=64, L=2, delta_f_hz=15e3)
+    base.update(kw)
+    return ts.ts_dims(**base)
+
+
+def test_workspace_sizes(lib):
+    d = _dims()
+    nch, P, K, n, L, p, m = 4, 8, 64, 8, 2, 4, 4
+    svd = lib.ts_workspace_bytes(ctypes.byref(d), 0)
+    mmse = lib.ts_workspace_bytes(ctypes.byref(d), 1)
+    assert svd >= nch * P * 8 + 2 * K * n * L * 8 + 2 * K
+    assert mmse >= nch * P * 8 + nch * p * m * L * 8
+    assert svd % 256 == 0 and mmse % 256 == 0
+    assert lib.ts_workspace_bytes(ctypes.byref(d), 7) == 0
+
+
+@pytest.mark.parametrize("bad", [dict(m=5), dict(L=5), dict(L=0), dict(m=17, M=17),
+                                 dict(n=33), dict(p=9), dict(p=33, P=40), dict(K=0), dict(J=0)])
+def test_invalid_dims_rejected_before_launch(lib, bad):
+    d = _dims(**bad)
+    assert lib.ts_workspace_bytes(ctypes.byref(d), 0) == 0
+    from paper_2401_09792_gb300 import tuckersinr as ts
+    coef = ts.ts_coef(0, 8, None, None)
+    st = lib.ts_sinr_svd(ctypes.byref(d), ctypes.byref(coef), 8, 8, 8, 8, None, 256, 1 << 30, None)
+    assert st == 1
+
+
+def test_null_and_alignment_checks(lib):
+    from paper_2401_09792_gb300 import tuckersinr as ts
+    d = _dims()
+    coef = ts.ts_coef(0, None, None, None)
+    assert lib.ts_sinr_svd(ctypes.byref(d), ctypes.byref(coef), 8, 8, 8, 8, None, 256, 1 << 30, None) == 2
+    coef = ts.ts_coef(0, 8, None, None)
+    assert lib.ts_sinr_svd(ctypes.byref(d), ctypes.byref(coef), 12, 8, 8, 8, None, 256, 1 << 30, None) == 3
+    assert lib.ts_sinr_svd(ctypes.byref(d), ctypes.byref(coef), 8, 8, 8, 8, None, 256, 16, None) == 4
+    assert lib.ts_sinr_svd(ctypes.byref(d), ctypes.byref(coef), 8, 8, 8, 8, None, 264, 1 << 30, None) == 3
+    coef = ts.ts_coef(3, 8, None, None)
+    assert lib.ts_sinr_svd(ctypes.byref(d), ctypes.byref(coef), 8, 8, 8, 8, None, 256, 1 << 30, None) == 6

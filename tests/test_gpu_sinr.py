@@ -1,0 +1,106 @@
+"""Parity of the CUDA SINR path (through the C ABI) with the FP64 oracle.
+
+Tolerances (FP32 arithmetic on the GPU, complex128 in the oracle):
+  * MMSE SINR with a wideband precoder: relative error <= 1e-5 per SINR.
+  * SVD-precoded SINR: relative error <= 1e-5 per SINR where the serving
+    links' squared singular values are separated by a relative gap of at
+    least 1e-2; elsewhere the precoder itself is ill-conditioned (its
+    columns move by ~u/gap under any rounding, u = 2^-24) and the bound is
+    1e-5 + 64 u / gap.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import sinr as S  # noqa: E402
+from paper_2401_09792_gb300 import synth  # noqa: E402
+from paper_2401_09792_gb300 import tuckersinr as ts  # noqa: E402
+from tests.gpu_inputs import Case, svd_gap, workload  # noqa: E402
+
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    assert torch.cuda.is_available()
+
+
+def _check(case: Case, precoder: str, mode: str):
+    got, flags = case.gpu_sinr(precoder, mode)
+    ref = case.oracle_sinr(precoder)
+    assert np.all(np.isfinite(got)), "non-finite SINR"
+    assert np.all(flags == 0), np.unique(flags)
+    rel = np.abs(got - ref) / np.abs(ref)
+    if precoder == "mmse":
+        tol = np.full(rel.shape, 1e-5)
+    else:
+        gap = svd_gap(case)
+        tol_k = np.where(gap >= 1e-2, 1e-5, 1e-5 + 64 * U32 / np.maximum(gap, 1e-30))
+        tol = np.broadcast_to(tol_k[None, :, None], rel.shape)
+    bad = rel > tol
+    assert not bad.any(), (f"{bad.sum()} of {rel.size} SINRs out of tolerance; "
+                           f"max rel {rel.max():.3e}, at {np.unravel_index(np.argmax(rel / tol), rel.shape)}")
+    return rel
+
+
+@pytest.mark.parametrize("precoder", ["svd", "mmse"])
+@pytest.mark.parametrize("mode", ["dense", "paths"])
+def test_small_workload(precoder, mode):
+    _check(Case(synth.SMALL), precoder, mode)
+
+
+@pytest.mark.parametrize("precoder", ["svd", "mmse"])
+def test_mid_workload_full_size(precoder):
+    # J=8, M=8, N=256, P=32, K=1024, ranks (8,32,16), L=8: the benchmark's sizes
+    rel = _check(Case(synth.MID), precoder, "paths")
+    assert rel.shape == (8, 1024, 8)
+
+
+EDGE = {
+    "single_cell": dict(J=1, K=5),
+    "ragged_K": dict(K=70),
+    "one_subcarrier": dict(K=1),
+    "odd_m_n_p1": dict(M=3, m=3, n=13, N=20, p=1, L=2),
+    "one_stream": dict(L=1),
+    "m1": dict(M=1, m=1, L=1),
+    "m2_full": dict(M=2, m=2, L=2, n=2, N=8),
+    "max_m16": dict(J=2, M=16, m=16, L=16, N=24, n=16, P=6, p=3, K=40),
+    "m16_L8_n24": dict(J=3, M=16, m=12, L=8, N=40, n=24, P=10, p=5, K=33),
+}
+
+
+@pytest.mark.parametrize("name", sorted(EDGE))
+@pytest.mark.parametrize("precoder", ["svd", "mmse"])
+def test_edge_cases(name, precoder):
+    w = workload(synth.SMALL, **EDGE[name])
+    _check(Case(w), precoder, "paths")
+
+
+def test_coefficients_kernel():
+    w = workload(synth.MID, K=3300)       # the largest subcarrier count of the workloads
+    alpha, tau = synth.path_gains_delays(w)
+    ref = S.coefficients(alpha, tau, w.K, w.delta_f_hz).reshape(w.J * w.J, w.K, w.P)
+    d = ts.Dims.of(w)
+    al = ts.factor_to_device(alpha.reshape(w.J * w.J, w.P))
+    ta = ts.real_to_device(tau.reshape(w.J * w.J, w.P))
+    c = torch.empty(w.J * w.J, w.K, w.P, dtype=torch.complex64, device="cuda")
+    ts.ts_coefficients(d, al, ta, c)
+    got = c.cpu().numpy()
+    amp = np.abs(alpha.reshape(w.J * w.J, 1, w.P))
+    assert np.all(np.abs(got - ref) <= 1e-6 * amp + 1e-30)
+
+
+def test_nonfinite_input_flags_and_nan():
+    case = Case(synth.SMALL)
+    G = case.G.clone()
+    G.view(-1)[0] = complex(float("nan"), 0.0)      # core of link (0, 0)
+    case.G = G
+    got, flags = case.gpu_sinr("mmse", "dense")
+    assert np.isnan(got[0]).all()
+    assert np.all(flags[0] != 0)
