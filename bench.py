@@ -1,0 +1,438 @@
+#!/usr/bin/env python
+"""Throughput of Tucker-form SINR evaluation on GB300 (subcarrier-SINRs/s).
+
+One step = one SVD-precoded MMSE SINR evaluation of the whole mid-size system
+(J=8 cells, M=8, N=256, P=32, K=1024 subcarriers, ranks (8,32,16), L=8):
+path coefficients (a0), projection c*C (a1), core contraction (a2), SVD
+precoders through the Jacobi eigensolve (a3), effective channels (a4),
+covariance (a5), Cholesky solves and SINR (a6), all in the CUDA library,
+called through its C ABI.  Inputs are resident in HBM; L2 is flushed before
+every timed step.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank evaluates its own independent system (weak
+scaling, no collective on the data path); the value is all ranks' SINRs
+divided by the slowest rank's time.  `--impl reference` times the FP64 CPU
+oracle on the same workload instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2401_09792_gb300 import synth  # noqa: E402
+
+WORKLOAD = synth.MID
+METRIC = "subcarrier-SINRs/s"
+FLUSH_BYTES = 256 << 20          # > 129 MB of L2
+
+
+def workload_config(w, precoder="svd"):
+    return {
+        "workload": (f"mid: J={w.J} cells, M={w.M}, N={w.N}, P={w.P}, K={w.K} subcarriers, "
+                     f"ranks (m,n,p)=({w.m},{w.n},{w.p}), L={w.L} streams; {precoder}-precoded "
+                     f"MMSE SINR; path-form coefficients; Tucker form drawn directly"),
+        "precoder": precoder,
+        "l2": "flushed before every timed step (256 MiB write)",
+        "units_per_step": w.J * w.K,
+    }
+
+
+# --------------------------------------------------------------- flop counts
+def accumulate_flops(w, precoder="svd") -> int:
+    """Algorithmic real flops of one launch of the SINR accumulation kernel.
+
+    Per (UE, subcarrier) unit, in complex multiply-adds (8 flops each):
+      J * P p            projection c* C for every link (eq. 15)
+      J * m n p          core contraction (eq. 15)            [svd only]
+      J * m n L          E = H~ V~ (eq. 24)                   [svd only]
+      J * p m L          E = sum_q w_q F[q]                   [wideband precoder]
+      J * m^2 L          covariance rows (eq. 25), Q~ and R
+      2 m^3/6 + 2 m^2 L/2 + m L^2/2 + 2 L^3/6   Cholesky factors and solves
+    """
+    J, m, n, p, P, L = w.J, w.m, w.n, w.p, w.P, w.L
+    per_link = P * p + (m * n * p + m * n * L if precoder == "svd" else p * m * L) + m * m * L
+    small = 2 * m ** 3 / 6 + 2 * m * m * L / 2 + m * L * L / 2 + 2 * L ** 3 / 6
+    return int(8 * w.K * J * (J * per_link + small))
+
+
+def precoder_flops(w) -> int:
+    """Algorithmic flops of the SVD precoder phase: H~_kk (Pp + mnp), Gram m^2 n,
+    V~ = H~* U / sigma (m n L) per (BS, subcarrier); the Jacobi sweeps are not counted."""
+    J, m, n, p, P, L = w.J, w.m, w.n, w.p, w.P, w.L
+    return int(8 * w.K * J * (P * p + m * n * p + m * m * n + m * n * L))
+
+
+# ----------------------------------------------------------------- helpers
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2401_09792_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    mh = re.search(r"kernel_source_hash:\s*(\w+)", text)
+    mb = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not mh or not mb or mh.group(1) != kernel_source_hash():
+        return None
+    return float(mb.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9 and parts[0] == str(self.index):
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2401_09792_gb300 import tuckersinr as ts
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    barrier()
+    ts.load()
+
+    w = synth.Workload(**{**WORKLOAD.__dict__, "seed": WORKLOAD.seed + rank})
+    J, K, L, P = w.J, w.K, w.L, w.P
+    tk = synth.direct_tucker(w)
+    alpha, tau = synth.path_gains_delays(w)
+    s2 = synth.noise_powers(w)
+    d = ts.Dims.of(w)
+    host = {
+        "G": torch.from_numpy(np.ascontiguousarray(np.transpose(tk["G"], (0, 1, 4, 2, 3))
+                                                   .reshape(J * J, w.p, w.m, w.n)).astype(np.complex64)),
+        "C": torch.from_numpy(tk["C"].reshape(J * J, P, w.p).astype(np.complex64)),
+        "alpha": torch.from_numpy(alpha.reshape(J * J, P).astype(np.complex64)),
+        "tau": torch.from_numpy(tau.reshape(J * J, P).astype(np.float32)),
+        "sigma2": torch.from_numpy(s2.astype(np.float32)),
+    }
+    dv = {k: v.to(dev) for k, v in host.items()}
+    coef, keep = ts.make_coef(alpha=dv["alpha"], tau=dv["tau"])
+    sinr = torch.empty(J, K, L, device=dev)
+    flags = torch.empty(J, K, dtype=torch.uint8, device=dev)
+    ws = ts.workspace(d, ts.TS_OP_SINR_SVD, dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def step(e0=None, e1=None, e2=None):
+        if e0 is not None:
+            e0.record(stream)
+        ts.ts_svd_precoders(d, coef, dv["G"], dv["C"], ws, stream)
+        if e1 is not None:
+            e1.record(stream)
+        ts.ts_sinr_svd_from_precoders(d, coef, dv["G"], dv["C"], dv["sigma2"], sinr, flags, ws, stream)
+        if e2 is not None:
+            e2.record(stream)
+
+    launches_per_step = 3            # phase steps of the paths, precoders, SINR accumulation
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local) if rank == 0 else None
+    evs = [(ev(), ev(), ev()) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for e0, e1, e2 in evs:
+        flush.zero_()
+        step(e0, e1, e2)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop() if sampler else None
+    step_ms = [e0.elapsed_time(e2) for e0, _, e2 in evs]
+    acc_ms = [e1.elapsed_time(e2) for _, e1, e2 in evs]
+    pre_ms = [e0.elapsed_time(e1) for e0, e1, _ in evs]
+    total_ms = float(np.sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    units = J * K
+    value = world * units * args.steps / (total_ms * 1e-3)
+    assert int(flags.max().item()) == 0, "numerical flags raised in the timed steps"
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies timed
+    pinned = {k: v.pin_memory() for k, v in host.items()}
+    out_host = torch.empty(J, K, L).pin_memory()
+    h2d = sum(v.numel() * v.element_size() for v in pinned.values())
+    d2h = out_host.numel() * out_host.element_size()
+
+    def e2e_step():
+        for k in pinned:
+            dv[k].copy_(pinned[k], non_blocking=True)
+        ts.ts_sinr_svd(d, coef, dv["G"], dv["C"], dv["sigma2"], sinr, flags, ws, stream)
+        out_host.copy_(sinr, non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = ev(), ev()
+        a.record(stream)
+        e2e_step()
+        b.record(stream)
+        b.synchronize()
+        e2e_ms += a.elapsed_time(b)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * units * args.steps / (e2e_ms * 1e-3)
+
+    # ---- the MMSE variant (wideband precoders), same timing discipline
+    Pw = synth.wideband_precoders(w)
+    B = torch.from_numpy(tk["B"].astype(np.complex64)).to(dev)
+    Pf = torch.from_numpy(Pw.astype(np.complex64)).to(dev)
+    Pt = torch.empty(J, w.n, L, dtype=torch.complex64, device=dev)
+    ts.ts_project_precoder(d, B, Pf, Pt, stream)
+    ws_m = ts.workspace(d, ts.TS_OP_SINR_MMSE, dev)
+    for _ in range(args.warmup):
+        ts.ts_sinr_mmse(d, coef, dv["G"], dv["C"], Pt, dv["sigma2"], sinr, flags, ws_m, stream)
+    mm_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = ev(), ev()
+        a.record(stream)
+        ts.ts_sinr_mmse(d, coef, dv["G"], dv["C"], Pt, dv["sigma2"], sinr, flags, ws_m, stream)
+        b.record(stream)
+        b.synchronize()
+        mm_ms += a.elapsed_time(b)
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    pk = peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    fp32_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12       # TFLOP/s, FFMA on every lane
+    acc_mean = float(np.mean(acc_ms))
+    achieved = accumulate_flops(w, "svd") / (acc_mean * 1e-3) / 1e12
+    traffic = recorded_traffic("k_sinr_accumulate", "mid")
+    roofline = {"kernel": "k_sinr_accumulate (svd)", "bound": "alu", "achieved": round(achieved, 3),
+                "peak": round(fp32_peak, 2), "unit": "TFLOP/s", "frac": round(achieved / fp32_peak, 4),
+                "traffic": traffic,
+                "peak_basis": f"FP32 FFMA: {sms} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz "
+                              "(unit counts and maximum SM clock)",
+                "flops_per_launch": accumulate_flops(w, "svd"),
+                "kernel_ms": round(acc_mean, 5),
+                "share_of_step": round(float(np.sum(acc_ms)) / float(np.sum(step_ms)), 3)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {**workload_config(w), "parallelism": f"independent systems x{world}"},
+        "roofline": roofline,
+        "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "phases_ms": {"precoders": round(float(np.mean(pre_ms)), 5),
+                      "sinr_accumulate": round(acc_mean, 5)},
+        "variants": {"mmse_wideband_precoder": {"value": units * args.steps / (mm_ms * 1e-3),
+                                                "ms_per_step": mm_ms / args.steps}},
+        "wall_s_timed_region": round(wall, 4),
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        gpu_out = _gpu_svd_sinr(ts, d, coef, dv, ws, stream)
+        line["cpu_baseline"], line["sinr_err"] = cpu_baseline(w, tk, alpha, tau, s2, gpu_out)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    del keep
+
+
+def _gpu_svd_sinr(ts, d, coef, dv, ws, stream):
+    import torch
+    J, K, L = d.J, d.K, d.L
+    out = torch.empty(J, K, L, device=dv["G"].device)
+    ts.ts_sinr_svd(d, coef, dv["G"], dv["C"], dv["sigma2"], out, None, ws, stream)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().astype(np.float64)
+
+
+def cpu_baseline(w, tk, alpha, tau, s2, gpu_sinr=None, budget_s=12.0, kslice=128):
+    """The FP64 oracle, as it stands, on subcarrier slices of the same system,
+    for about `budget_s` seconds; also the GPU result's error on those slices."""
+    from oracle import sinr as S
+    J = w.J
+    coef = S.coefficients(alpha, tau, w.K, w.delta_f_hz)
+    t0 = time.perf_counter()
+    c0 = time.process_time()
+    done, errs, start = 0, [], 0
+    while time.perf_counter() - t0 < budget_s and start < w.K:
+        sl = slice(start, min(start + kslice, w.K))
+        ref = S.tucker_sinr(tk["G"], tk["C"], coef[:, :, sl], s2, w.L, "svd")
+        if gpu_sinr is not None:
+            errs.append(np.abs(gpu_sinr[:, sl] - ref) / np.abs(ref))
+        done += J * (sl.stop - sl.start)
+        start = sl.stop
+    wall = time.perf_counter() - t0
+    cpu = time.process_time() - c0
+    base = {"value": done / wall, "unit": METRIC, "cores": max(1, round(cpu / wall)),
+            "kind": "oracle",
+            "sample": f"FP64 NumPy oracle, svd SINR of the same system on subcarriers "
+                      f"0..{start - 1} ({done} subcarrier-SINRs, {wall:.1f} s wall, "
+                      f"{os.cpu_count()} host cores visible)"}
+    err = None
+    if errs:
+        e = np.concatenate([x.ravel() for x in errs])
+        err = {"max_rel": float(e.max()), "p99_rel": float(np.percentile(e, 99)),
+               "median_rel": float(np.median(e)), "n": int(e.size),
+               "vs": "FP64 oracle on the cpu_baseline subcarriers"}
+    return base, err
+
+
+# ------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import sinr as S
+    w = WORKLOAD
+    tk = synth.direct_tucker(w)
+    alpha, tau = synth.path_gains_delays(w)
+    s2 = synth.noise_powers(w)
+    coef = S.coefficients(alpha, tau, w.K, w.delta_f_hz)
+    kslice = 128
+
+    def one(start):
+        sl = slice(start % w.K, start % w.K + kslice)
+        S.tucker_sinr(tk["G"], tk["C"], coef[:, :, sl], s2, w.L, "svd")
+
+    for s in range(args.warmup):
+        one(s * kslice)
+    c0 = time.process_time()
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        one(s * kslice)
+    wall = time.perf_counter() - t0
+    cpu = time.process_time() - c0
+    units = w.J * kslice * args.steps
+    value = units / wall
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {**workload_config(w), "parallelism": "none (host CPU)"},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": max(1, round(cpu / wall)),
+                         "kind": "oracle",
+                         "sample": f"each step: FP64 NumPy oracle on {kslice} of the {w.K} "
+                                   f"subcarriers ({w.J * kslice} subcarrier-SINRs); "
+                                   f"{os.cpu_count()} host cores visible"},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

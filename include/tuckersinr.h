@@ -146,6 +146,20 @@ int ts_sinr_svd(const ts_dims* d, const ts_coef* coef, const ts_c64* G,
                 const ts_c64* C, const float* sigma2, float* sinr,
                 uint8_t* flags, void* ws, size_t ws_bytes, void* stream);
 
+/* The two phases of ts_sinr_svd, for callers that time or reuse them.
+ * ts_svd_precoders writes the precoders V~_k(kappa) (eq. 7, eq. 23; and, for
+ * path-form coefficients, the per-path phase steps) into ws.
+ * ts_sinr_svd_from_precoders then evaluates eq. (24)-(28) from them.  Both
+ * calls must receive the same d, coef, G, C and ws, in this order on one
+ * stream; ts_sinr_svd issues exactly these two calls. */
+int ts_svd_precoders(const ts_dims* d, const ts_coef* coef, const ts_c64* G,
+                     const ts_c64* C, void* ws, size_t ws_bytes, void* stream);
+int ts_sinr_svd_from_precoders(const ts_dims* d, const ts_coef* coef,
+                               const ts_c64* G, const ts_c64* C,
+                               const float* sigma2, float* sinr,
+                               uint8_t* flags, void* ws, size_t ws_bytes,
+                               void* stream);
+
 #ifdef __cplusplus
 }
 #endif

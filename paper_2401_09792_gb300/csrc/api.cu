@@ -180,9 +180,29 @@ int ts_sinr_mmse(const ts_dims* d, const ts_coef* coef, const ts_c64* G, const t
   return cuda_status(e);
 }
 
-int ts_sinr_svd(const ts_dims* d, const ts_coef* coef, const ts_c64* G, const ts_c64* C,
-                const float* sigma2, float* sinr, uint8_t* flags, void* ws, size_t ws_bytes,
-                void* stream) {
+int ts_svd_precoders(const ts_dims* d, const ts_coef* coef, const ts_c64* G, const ts_c64* C,
+                     void* ws, size_t ws_bytes, void* stream) {
+  static const float kOne = 1.f;
+  static float dummy_out;
+  int st = sinr_common_checks(d, coef, G, C, &kOne, &dummy_out, ws, ws_bytes, TS_OP_SINR_SVD);
+  if (st != TS_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Workspace w = carve(d, TS_OP_SINR_SVD);
+  char* base = static_cast<char*>(ws);
+  ts::SinrArgs a = base_args(d, coef, G, C, nullptr, nullptr, nullptr, base, w);
+  a.V = reinterpret_cast<float2*>(base + w.V);
+  a.pflag = reinterpret_cast<uint8_t*>(base + w.pflag);
+  cudaError_t e = cudaSuccess;
+  if (coef->mode == TS_COEF_PATHS)
+    e = ts::launch_turns(coef->tau_s, d->delta_f_hz, d->J * d->J * d->P,
+                         reinterpret_cast<unsigned long long*>(base + w.turns), s);
+  if (e == cudaSuccess) e = ts::launch_svd_precoder(a, s);
+  return cuda_status(e);
+}
+
+int ts_sinr_svd_from_precoders(const ts_dims* d, const ts_coef* coef, const ts_c64* G,
+                               const ts_c64* C, const float* sigma2, float* sinr, uint8_t* flags,
+                               void* ws, size_t ws_bytes, void* stream) {
   int st = sinr_common_checks(d, coef, G, C, sigma2, sinr, ws, ws_bytes, TS_OP_SINR_SVD);
   if (st != TS_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -191,13 +211,15 @@ int ts_sinr_svd(const ts_dims* d, const ts_coef* coef, const ts_c64* G, const ts
   ts::SinrArgs a = base_args(d, coef, G, C, sigma2, sinr, flags, base, w);
   a.V = reinterpret_cast<float2*>(base + w.V);
   a.pflag = reinterpret_cast<uint8_t*>(base + w.pflag);
-  cudaError_t e = cudaSuccess;
-  if (coef->mode == TS_COEF_PATHS)
-    e = ts::launch_turns(coef->tau_s, d->delta_f_hz, d->J * d->J * d->P,
-                         reinterpret_cast<unsigned long long*>(base + w.turns), s);
-  if (e == cudaSuccess) e = ts::launch_svd_precoder(a, s);
-  if (e == cudaSuccess) e = ts::launch_sinr_accumulate(a, true, s);
-  return cuda_status(e);
+  return cuda_status(ts::launch_sinr_accumulate(a, true, s));
+}
+
+int ts_sinr_svd(const ts_dims* d, const ts_coef* coef, const ts_c64* G, const ts_c64* C,
+                const float* sigma2, float* sinr, uint8_t* flags, void* ws, size_t ws_bytes,
+                void* stream) {
+  int st = ts_svd_precoders(d, coef, G, C, ws, ws_bytes, stream);
+  if (st != TS_OK) return st;
+  return ts_sinr_svd_from_precoders(d, coef, G, C, sigma2, sinr, flags, ws, ws_bytes, stream);
 }
 
 }  // extern "C"

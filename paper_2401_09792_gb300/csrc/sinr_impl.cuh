@@ -213,7 +213,8 @@ __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, con
     }
     off = gsum<MG>(off);
     dia = gsum<MG>(dia);
-    converged = off <= 1e-14f * dia;
+    // FP32 stopping rule: off-diagonal energy below (8 u)^2 of the total, u = 2^-24
+    converged = off <= 2.3e-13f * dia;
     // the decision is taken warp-wide: every group keeps sweeping until all
     // groups of the warp have converged (extra sweeps leave S unchanged)
     if (__all_sync(FULL, converged) || sweep == max_sweeps) break;

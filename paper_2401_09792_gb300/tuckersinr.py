@@ -59,6 +59,10 @@ _SIG = {
                                     _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "ts_sinr_svd": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.POINTER(ts_coef), _P, _P, _P,
                                    _P, _P, _P, ctypes.c_size_t, _P]),
+    "ts_svd_precoders": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.POINTER(ts_coef), _P, _P,
+                                        _P, ctypes.c_size_t, _P]),
+    "ts_sinr_svd_from_precoders": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.POINTER(ts_coef),
+                                                  _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
 }
 
 _lib = None
@@ -165,6 +169,20 @@ def ts_sinr_mmse(d: Dims, coef: ts_coef, G, C, Pt, sigma2, sinr, flags, ws, stre
 def ts_sinr_svd(d: Dims, coef: ts_coef, G, C, sigma2, sinr, flags, ws, stream=None):
     lib = load()
     _check("ts_sinr_svd", lib.ts_sinr_svd(ctypes.byref(d.c()), ctypes.byref(coef), _ptr(G), _ptr(C),
+                                          _ptr(sigma2), _ptr(sinr), _ptr(flags), _ptr(ws),
+                                          ws.numel(), _stream(stream)))
+
+
+def ts_svd_precoders(d: Dims, coef: ts_coef, G, C, ws, stream=None):
+    lib = load()
+    _check("ts_svd_precoders", lib.ts_svd_precoders(ctypes.byref(d.c()), ctypes.byref(coef), _ptr(G),
+                                                    _ptr(C), _ptr(ws), ws.numel(), _stream(stream)))
+
+
+def ts_sinr_svd_from_precoders(d: Dims, coef: ts_coef, G, C, sigma2, sinr, flags, ws, stream=None):
+    lib = load()
+    _check("ts_sinr_svd_from_precoders",
+           lib.ts_sinr_svd_from_precoders(ctypes.byref(d.c()), ctypes.byref(coef), _ptr(G), _ptr(C),
                                           _ptr(sigma2), _ptr(sinr), _ptr(flags), _ptr(ws),
                                           ws.numel(), _stream(stream)))
 

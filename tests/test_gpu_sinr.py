@@ -6,7 +6,7 @@ Tolerances (FP32 arithmetic on the GPU, complex128 in the oracle):
     links' squared singular values are separated by a relative gap of at
     least 1e-2; elsewhere the precoder itself is ill-conditioned (its
     columns move by ~u/gap under any rounding, u = 2^-24) and the bound is
-    1e-5 + 64 u / gap.
+    1e-5 + 8 u / gap.
 """
 import dataclasses
 
@@ -41,7 +41,7 @@ def _check(case: Case, precoder: str, mode: str):
         tol = np.full(rel.shape, 1e-5)
     else:
         gap = svd_gap(case)
-        tol_k = np.where(gap >= 1e-2, 1e-5, 1e-5 + 64 * U32 / np.maximum(gap, 1e-30))
+        tol_k = np.where(gap >= 1e-2, 1e-5, 1e-5 + 8 * U32 / np.maximum(gap, 1e-30))
         tol = np.broadcast_to(tol_k[None, :, None], rel.shape)
     bad = rel > tol
     assert not bad.any(), (f"{bad.sum()} of {rel.size} SINRs out of tolerance; "
