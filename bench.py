@@ -52,21 +52,23 @@ def workload_config(w, precoder="svd"):
 
 
 # --------------------------------------------------------------- flop counts
-def accumulate_flops(w, precoder="svd") -> int:
-    """Algorithmic real flops of one launch of the SINR accumulation kernel.
+def link_flops(w, precoder="svd") -> int:
+    """Algorithmic real flops of one launch of the per-link kernel k_sinr_link.
 
-    Per (UE, subcarrier) unit, in complex multiply-adds (8 flops each):
-      J * P p            projection c* C for every link (eq. 15)
-      J * m n p          core contraction (eq. 15)            [svd only]
-      J * m n L          E = H~ V~ (eq. 24)                   [svd only]
-      J * p m L          E = sum_q w_q F[q]                   [wideband precoder]
-      J * m^2 L          covariance rows (eq. 25), Q~ and R
-      2 m^3/6 + 2 m^2 L/2 + m L^2/2 + 2 L^3/6   Cholesky factors and solves
+    One CTA column per (UE i, link k, subcarrier); per unit, in complex
+    multiply-adds (8 flops each):
+      P p                projection c* C (eq. 15)
+      m n p              core contraction H~ = G x_3 (c* C) (eq. 15)   [svd]
+      m n L              effective channel E = H~ V~ (eq. 24)          [svd]
+      p m L              E = sum_q w_q F[q] (wideband precoder)
+      m^2 L              covariance rows E E* (eq. 25)
+    over J (J - 1) interfering links (svd: the serving link comes from the
+    precoder phase) or J^2 links (wideband precoder) and K subcarriers.
     """
     J, m, n, p, P, L = w.J, w.m, w.n, w.p, w.P, w.L
-    per_link = P * p + (m * n * p + m * n * L if precoder == "svd" else p * m * L) + m * m * L
-    small = 2 * m ** 3 / 6 + 2 * m * m * L / 2 + m * L * L / 2 + 2 * L ** 3 / 6
-    return int(8 * w.K * J * (J * per_link + small))
+    if precoder == "svd":
+        return int(8 * w.K * J * (J - 1) * (P * p + m * n * p + m * n * L + m * m * L))
+    return int(8 * w.K * J * (J * (P * p + p * m * L) + (J - 1) * m * m * L))
 
 
 def precoder_flops(w) -> int:
@@ -198,37 +200,45 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
-    def step(e0=None, e1=None, e2=None):
+    def step(e0=None, e1=None, e2=None, k0=None, k1=None):
         if e0 is not None:
             e0.record(stream)
         ts.ts_svd_precoders(d, coef, dv["G"], dv["C"], ws, stream)
         if e1 is not None:
             e1.record(stream)
+        ts.ts_set_timing_events(k0, k1)
         ts.ts_sinr_svd_from_precoders(d, coef, dv["G"], dv["C"], dv["sigma2"], sinr, flags, ws, stream)
+        ts.ts_set_timing_events(None, None)
         if e2 is not None:
             e2.record(stream)
 
-    launches_per_step = 3            # phase steps of the paths, precoders, SINR accumulation
+    launches_per_step = 5            # path phase steps, serving links, precoders, links, finalize
     for _ in range(args.warmup):
         flush.zero_()
         step()
     torch.cuda.synchronize()
 
+    evs = [tuple(ev() for _ in range(5)) for _ in range(args.steps)]
+    for e in evs:
+        for x in e:
+            x.record(stream)          # create the events before their handles are used
+    torch.cuda.synchronize()
     sampler = ClockSampler(local) if rank == 0 else None
-    evs = [(ev(), ev(), ev()) for _ in range(args.steps)]
+    time.sleep(0.5 if sampler else 0.0)
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for e0, e1, e2 in evs:
+    for e0, e1, e2, k0, k1 in evs:
         flush.zero_()
-        step(e0, e1, e2)
+        step(e0, e1, e2, k0, k1)
     torch.cuda.synchronize()
     barrier()
     wall = time.perf_counter() - t0
     clocks = sampler.stop() if sampler else None
-    step_ms = [e0.elapsed_time(e2) for e0, _, e2 in evs]
-    acc_ms = [e1.elapsed_time(e2) for _, e1, e2 in evs]
-    pre_ms = [e0.elapsed_time(e1) for e0, e1, _ in evs]
+    step_ms = [e[0].elapsed_time(e[2]) for e in evs]
+    link_ms = [e[3].elapsed_time(e[4]) for e in evs]
+    pre_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    fin_ms = [e[1].elapsed_time(e[2]) for e in evs]
     total_ms = float(np.sum(step_ms))
     if world > 1:
         t = torch.tensor([total_ms], device=dev)
@@ -238,6 +248,30 @@ def run_ours(args):
     value = world * units * args.steps / (total_ms * 1e-3)
     assert int(flags.max().item()) == 0, "numerical flags raised in the timed steps"
 
+    if args.step_only:
+        e2e_value = h2d = d2h = mm_ms = dense_value = dense_ms = dense_steps = None
+    else:
+        e2e_value, h2d, d2h, mm_ms, dense_value, dense_ms, dense_steps = _extras(
+            args, ts, torch, dist, world, dev, w, tk, host, dv, coef, d, ws, sinr, flags, flush,
+            stream, ev, units)
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    _report(args, ts, torch, world, dev, w, tk, alpha, tau, s2, d, coef, dv, ws, stream, units,
+            value, total_ms, step_ms, link_ms, pre_ms, fin_ms, wall, clocks, launches_per_step,
+            e2e_value, h2d, d2h, mm_ms, dense_value, dense_ms, dense_steps)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    del keep
+
+
+def _extras(args, ts, torch, dist, world, dev, w, tk, host, dv, coef, d, ws, sinr, flags, flush,
+            stream, ev, units):
+    """End-to-end, wideband-precoder and dense-comparator timings."""
+    J, K, L, P = w.J, w.K, w.L, w.P
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
     pinned = {k: v.pin_memory() for k, v in host.items()}
     out_host = torch.empty(J, K, L).pin_memory()
@@ -287,27 +321,48 @@ def run_ours(args):
         b.synchronize()
         mm_ms += a.elapsed_time(b)
 
-    if rank != 0:
-        if world > 1:
-            dist.barrier()
-            dist.destroy_process_group()
-        return
+    # ---- dense-channel comparator on the same system: full M x N channels per
+    # subcarrier (eq. 9), precoders and solves at (M, N); same kernels, C = I
+    X = synth.channel_submatrices(w)
+    Xd = torch.from_numpy(np.ascontiguousarray(np.transpose(X, (0, 1, 4, 2, 3))
+                                               .reshape(J * J, P, w.M, w.N)).astype(np.complex64)).to(dev)
+    del X
+    ws_d = ts.workspace(d, ts.TS_OP_DENSE_SVD, dev)
+    for _ in range(args.warmup):
+        ts.ts_dense_sinr_svd(d, coef, Xd, dv["sigma2"], sinr, flags, ws_d, stream)
+    dense_ms = 0.0
+    dense_steps = max(3, args.steps // 10)
+    for _ in range(dense_steps):
+        flush.zero_()
+        a, b = ev(), ev()
+        a.record(stream)
+        ts.ts_dense_sinr_svd(d, coef, Xd, dv["sigma2"], sinr, flags, ws_d, stream)
+        b.record(stream)
+        b.synchronize()
+        dense_ms += a.elapsed_time(b)
+    dense_value = units * dense_steps / (dense_ms * 1e-3)
+    del Xd, ws_d
+    return e2e_value, h2d, d2h, mm_ms, dense_value, dense_ms, dense_steps
 
+
+def _report(args, ts, torch, world, dev, w, tk, alpha, tau, s2, d, coef, dv, ws, stream, units,
+            value, total_ms, step_ms, link_ms, pre_ms, fin_ms, wall, clocks, launches_per_step,
+            e2e_value, h2d, d2h, mm_ms, dense_value, dense_ms, dense_steps):
     pk = peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
     fp32_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12       # TFLOP/s, FFMA on every lane
-    acc_mean = float(np.mean(acc_ms))
-    achieved = accumulate_flops(w, "svd") / (acc_mean * 1e-3) / 1e12
-    traffic = recorded_traffic("k_sinr_accumulate", "mid")
-    roofline = {"kernel": "k_sinr_accumulate (svd)", "bound": "alu", "achieved": round(achieved, 3),
+    link_mean = float(np.mean(link_ms))
+    achieved = link_flops(w, "svd") / (link_mean * 1e-3) / 1e12
+    traffic = recorded_traffic("k_sinr_link", "mid")
+    roofline = {"kernel": "k_sinr_link (svd)", "bound": "alu", "achieved": round(achieved, 3),
                 "peak": round(fp32_peak, 2), "unit": "TFLOP/s", "frac": round(achieved / fp32_peak, 4),
                 "traffic": traffic,
                 "peak_basis": f"FP32 FFMA: {sms} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz "
                               "(unit counts and maximum SM clock)",
-                "flops_per_launch": accumulate_flops(w, "svd"),
-                "kernel_ms": round(acc_mean, 5),
-                "share_of_step": round(float(np.sum(acc_ms)) / float(np.sum(step_ms)), 3)}
+                "flops_per_launch": link_flops(w, "svd"),
+                "kernel_ms": round(link_mean, 5),
+                "share_of_step": round(float(np.sum(link_ms)) / float(np.sum(step_ms)), 3)}
 
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
@@ -320,19 +375,25 @@ def run_ours(args):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
         "phases_ms": {"precoders": round(float(np.mean(pre_ms)), 5),
-                      "sinr_accumulate": round(acc_mean, 5)},
-        "variants": {"mmse_wideband_precoder": {"value": units * args.steps / (mm_ms * 1e-3),
-                                                "ms_per_step": mm_ms / args.steps}},
+                      "links_and_finalize": round(float(np.mean(fin_ms)), 5),
+                      "links": round(link_mean, 5)},
+        "variants": None if mm_ms is None else {
+            "mmse_wideband_precoder": {"value": units * args.steps / (mm_ms * 1e-3),
+                                       "ms_per_step": mm_ms / args.steps}},
+        "dense_comparator": None if dense_ms is None else {
+            "value": dense_value, "unit": METRIC, "ms_per_step": dense_ms / dense_steps,
+            "what": "same SVD-precoded SINR from the uncompressed channels "
+                    f"(M={w.M}, N={w.N}, P={w.P}) on the same GPU kernels",
+            "tucker_over_dense": value / world / dense_value},
         "wall_s_timed_region": round(wall, 4),
     }
+    if args.step_only:
+        for key in ("e2e", "variants", "dense_comparator"):
+            line.pop(key)
     if world == 1 and not args.no_cpu_baseline:
         gpu_out = _gpu_svd_sinr(ts, d, coef, dv, ws, stream)
         line["cpu_baseline"], line["sinr_err"] = cpu_baseline(w, tk, alpha, tau, s2, gpu_out)
     print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.barrier()
-        dist.destroy_process_group()
-    del keep
 
 
 def _gpu_svd_sinr(ts, d, coef, dv, ws, stream):
@@ -352,21 +413,23 @@ def cpu_baseline(w, tk, alpha, tau, s2, gpu_sinr=None, budget_s=12.0, kslice=128
     coef = S.coefficients(alpha, tau, w.K, w.delta_f_hz)
     t0 = time.perf_counter()
     c0 = time.process_time()
-    done, errs, start = 0, [], 0
-    while time.perf_counter() - t0 < budget_s and start < w.K:
+    done, errs, start, passes = 0, [], 0, 0
+    while time.perf_counter() - t0 < budget_s:
         sl = slice(start, min(start + kslice, w.K))
         ref = S.tucker_sinr(tk["G"], tk["C"], coef[:, :, sl], s2, w.L, "svd")
-        if gpu_sinr is not None:
+        if gpu_sinr is not None and passes == 0:
             errs.append(np.abs(gpu_sinr[:, sl] - ref) / np.abs(ref))
         done += J * (sl.stop - sl.start)
         start = sl.stop
+        if start >= w.K:
+            start, passes = 0, passes + 1
     wall = time.perf_counter() - t0
     cpu = time.process_time() - c0
     base = {"value": done / wall, "unit": METRIC, "cores": max(1, round(cpu / wall)),
             "kind": "oracle",
-            "sample": f"FP64 NumPy oracle, svd SINR of the same system on subcarriers "
-                      f"0..{start - 1} ({done} subcarrier-SINRs, {wall:.1f} s wall, "
-                      f"{os.cpu_count()} host cores visible)"}
+            "sample": f"FP64 NumPy oracle, svd SINR of the same system in slices of "
+                      f"{kslice} subcarriers, repeated for {wall:.1f} s wall ({done} "
+                      f"subcarrier-SINRs; {os.cpu_count()} host cores visible)"}
     err = None
     if errs:
         e = np.concatenate([x.ravel() for x in errs])
@@ -421,10 +484,12 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--step-only", action="store_true",
+                    help="time only the SVD step (no end-to-end, variant or comparator runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -89,7 +89,9 @@ enum {
 /* Operations, for ts_workspace_bytes. */
 enum {
   TS_OP_SINR_SVD = 0,
-  TS_OP_SINR_MMSE = 1
+  TS_OP_SINR_MMSE = 1,
+  TS_OP_DENSE_SVD = 2,
+  TS_OP_DENSE_MMSE = 3
 };
 
 /* Human-readable name of a status code (static storage). */
@@ -101,6 +103,12 @@ int ts_last_cuda_error(void);
 
 /* Version of this ABI (incremented on any incompatible change). */
 int ts_abi_version(void);
+
+/* Profiling hook: caller-created CUDA events (cudaEvent_t as void*) that the
+ * following SINR calls on this host thread record on their stream right
+ * before and right after their dominant kernel (the per-link rebuild and
+ * covariance kernel).  NULL, NULL turns it off.  Not used otherwise. */
+void ts_set_timing_events(void* start, void* stop);
 
 /* Device workspace, in bytes, that operation `op` needs for sizes `d`.
  * Returns 0 for invalid sizes.  The caller allocates it (256-byte aligned)
@@ -159,6 +167,21 @@ int ts_sinr_svd_from_precoders(const ts_dims* d, const ts_coef* coef,
                                const float* sigma2, float* sinr,
                                uint8_t* flags, void* ws, size_t ws_bytes,
                                void* stream);
+
+/* Dense-channel comparator: the same SINR computed from the uncompressed
+ * channel tensors, rebuilding the full M x N channel of every link and
+ * subcarrier, H_ik(kappa) = X_ik x_3 c_ik(kappa)* (eq. 9), and running the
+ * precoder, covariance and solves at size (M, N) (eq. 3-7) -- the "original
+ * data" side of the paper's speedup R_t (Section 4).
+ * X: [J*J][P][M][N] (the submatrices of eq. 2 stacked on mode 3, N fastest).
+ * Pfull (mmse): [J][N][L].  d->m, d->n, d->p are ignored; limits M <= 16,
+ * N <= 512, P <= 32.  ws: ts_workspace_bytes(d, TS_OP_DENSE_SVD / _MMSE). */
+int ts_dense_sinr_svd(const ts_dims* d, const ts_coef* coef, const ts_c64* X,
+                      const float* sigma2, float* sinr, uint8_t* flags, void* ws,
+                      size_t ws_bytes, void* stream);
+int ts_dense_sinr_mmse(const ts_dims* d, const ts_coef* coef, const ts_c64* X,
+                       const ts_c64* Pfull, const float* sigma2, float* sinr,
+                       uint8_t* flags, void* ws, size_t ws_bytes, void* stream);
 
 #ifdef __cplusplus
 }

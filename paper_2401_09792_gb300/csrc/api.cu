@@ -10,6 +10,21 @@
 namespace {
 
 thread_local int g_last_cuda = 0;
+// optional caller-owned events recorded around the dominant kernel of the
+// next SINR calls on this host thread (ts_set_timing_events)
+thread_local cudaEvent_t g_ev_start = nullptr;
+thread_local cudaEvent_t g_ev_stop = nullptr;
+
+// The per-link kernel (the dominant one) bracketed by the timing events,
+// then the finalisation.
+cudaError_t links_then_finalize(const ts::SinrArgs& a, bool svd, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (g_ev_start != nullptr) e = cudaEventRecord(g_ev_start, s);
+  if (e == cudaSuccess) e = ts::launch_sinr_links(a, svd, s);
+  if (e == cudaSuccess && g_ev_stop != nullptr) e = cudaEventRecord(g_ev_stop, s);
+  if (e == cudaSuccess) e = ts::launch_sinr_finalize(a, svd, s);
+  return e;
+}
 
 int cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return TS_OK;
@@ -19,6 +34,7 @@ int cuda_status(cudaError_t e) {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// NULL counts as aligned (optional pointers are checked separately)
 bool aligned8(const void* p) { return ((uintptr_t)p & 7u) == 0; }
 
 // Sizes the SINR kernels accept.
@@ -38,7 +54,7 @@ int check_dims(const ts_dims* d) {
 
 // Workspace layout (byte offsets from the base, each 256-byte aligned).
 struct Workspace {
-  size_t turns = 0, V = 0, pflag = 0, F = 0, total = 0;
+  size_t turns = 0, V = 0, Hserv = 0, Eserv = 0, Rpart = 0, pflag = 0, F = 0, total = 0;
 };
 
 Workspace carve(const ts_dims* d, int op) {
@@ -47,9 +63,15 @@ Workspace carve(const ts_dims* d, int op) {
   const size_t nch = (size_t)d->J * d->J;
   w.turns = o;
   o = align_up(o + nch * d->P * sizeof(unsigned long long), 256);
+  w.Eserv = o;
+  o = align_up(o + (size_t)d->J * d->K * d->m * d->L * sizeof(float2), 256);
+  w.Rpart = o;
+  o = align_up(o + (size_t)d->J * (d->J - 1) * d->K * d->m * d->m * sizeof(float2), 256);
   if (op == TS_OP_SINR_SVD) {
     w.V = o;
     o = align_up(o + (size_t)d->J * d->K * d->n * d->L * sizeof(float2), 256);
+    w.Hserv = o;
+    o = align_up(o + (size_t)d->J * d->K * d->m * d->n * sizeof(float2), 256);
     w.pflag = o;
     o = align_up(o + (size_t)d->J * d->K, 256);
   } else {
@@ -74,6 +96,8 @@ int check_coef(const ts_coef* c) {
   return TS_OK;
 }
 
+ts_dims dense_dims(const ts_dims* d);
+
 ts::SinrArgs base_args(const ts_dims* d, const ts_coef* coef, const ts_c64* G, const ts_c64* C,
                        const float* sigma2, float* sinr, uint8_t* flags, char* ws,
                        const Workspace& w) {
@@ -84,6 +108,9 @@ ts::SinrArgs base_args(const ts_dims* d, const ts_coef* coef, const ts_c64* G, c
   a.C = reinterpret_cast<const float2*>(C);
   a.coef = reinterpret_cast<const float2*>(coef->mode == TS_COEF_DENSE ? coef->c : coef->alpha);
   a.turns = reinterpret_cast<const unsigned long long*>(ws + w.turns);
+  a.Eserv = reinterpret_cast<float2*>(ws + w.Eserv);
+  a.Rpart = reinterpret_cast<float2*>(ws + w.Rpart);
+  a.Hserv = reinterpret_cast<float2*>(ws + w.Hserv);
   a.sigma2 = sigma2;
   a.sinr = sinr;
   a.flags = flags;
@@ -111,7 +138,18 @@ int ts_last_cuda_error(void) { return g_last_cuda; }
 
 int ts_abi_version(void) { return 1; }
 
+void ts_set_timing_events(void* start, void* stop) {
+  g_ev_start = static_cast<cudaEvent_t>(start);
+  g_ev_stop = static_cast<cudaEvent_t>(stop);
+}
+
 size_t ts_workspace_bytes(const ts_dims* d, int op) {
+  if (d == nullptr) return 0;
+  if (op == TS_OP_DENSE_SVD || op == TS_OP_DENSE_MMSE) {
+    const ts_dims e = dense_dims(d);
+    if (check_dims(&e) != TS_OK) return 0;
+    return carve(&e, op == TS_OP_DENSE_SVD ? TS_OP_SINR_SVD : TS_OP_SINR_MMSE).total;
+  }
   if (check_dims(d) != TS_OK) return 0;
   if (op != TS_OP_SINR_SVD && op != TS_OP_SINR_MMSE) return 0;
   return carve(d, op).total;
@@ -140,14 +178,29 @@ int ts_project_precoder(const ts_dims* d, const ts_c64* B, const ts_c64* Pfull, 
       d->L, reinterpret_cast<float2*>(Pt), static_cast<cudaStream_t>(stream)));
 }
 
-static int sinr_common_checks(const ts_dims* d, const ts_coef* coef, const ts_c64* G,
-                              const ts_c64* C, const float* sigma2, float* sinr, void* ws,
-                              size_t ws_bytes, int op) {
+}  // extern "C"
+
+namespace {
+
+// The dense-channel comparator runs the compressed path on the trivial
+// factorisation G = X, C = I: (m, n, p) = (M, N, P).
+ts_dims dense_dims(const ts_dims* d) {
+  ts_dims e = *d;
+  e.m = d->M;
+  e.n = d->N;
+  e.p = d->P;
+  return e;
+}
+
+int sinr_common_checks(const ts_dims* d, const ts_coef* coef, const ts_c64* G, const ts_c64* C,
+                       bool identity, const float* sigma2, float* sinr, void* ws, size_t ws_bytes,
+                       int op) {
   int st = check_dims(d);
   if (st != TS_OK) return st;
   st = check_coef(coef);
   if (st != TS_OK) return st;
-  if (G == nullptr || C == nullptr || sigma2 == nullptr || sinr == nullptr) return TS_ERR_NULL;
+  if (G == nullptr || (!identity && C == nullptr) || sigma2 == nullptr || sinr == nullptr)
+    return TS_ERR_NULL;
   if (!aligned8(G) || !aligned8(C) || ((uintptr_t)sigma2 & 3u) || ((uintptr_t)sinr & 3u))
     return TS_ERR_ALIGN;
   const size_t need = carve(d, op).total;
@@ -156,10 +209,10 @@ static int sinr_common_checks(const ts_dims* d, const ts_coef* coef, const ts_c6
   return TS_OK;
 }
 
-int ts_sinr_mmse(const ts_dims* d, const ts_coef* coef, const ts_c64* G, const ts_c64* C,
-                 const ts_c64* Pt, const float* sigma2, float* sinr, uint8_t* flags, void* ws,
-                 size_t ws_bytes, void* stream) {
-  int st = sinr_common_checks(d, coef, G, C, sigma2, sinr, ws, ws_bytes, TS_OP_SINR_MMSE);
+int sinr_mmse_impl(const ts_dims* d, const ts_coef* coef, const ts_c64* G, const ts_c64* C,
+                   bool identity, const ts_c64* Pt, const float* sigma2, float* sinr,
+                   uint8_t* flags, void* ws, size_t ws_bytes, void* stream) {
+  int st = sinr_common_checks(d, coef, G, C, identity, sigma2, sinr, ws, ws_bytes, TS_OP_SINR_MMSE);
   if (st != TS_OK) return st;
   if (Pt == nullptr) return TS_ERR_NULL;
   if (!aligned8(Pt)) return TS_ERR_ALIGN;
@@ -167,6 +220,7 @@ int ts_sinr_mmse(const ts_dims* d, const ts_coef* coef, const ts_c64* G, const t
   const Workspace w = carve(d, TS_OP_SINR_MMSE);
   char* base = static_cast<char*>(ws);
   ts::SinrArgs a = base_args(d, coef, G, C, sigma2, sinr, flags, base, w);
+  a.identity_C = identity;
   float2* F = reinterpret_cast<float2*>(base + w.F);
   a.F = F;
   cudaError_t e = cudaSuccess;
@@ -176,50 +230,94 @@ int ts_sinr_mmse(const ts_dims* d, const ts_coef* coef, const ts_c64* G, const t
   if (e == cudaSuccess)
     e = ts::launch_mmse_fold(a.G, reinterpret_cast<const float2*>(Pt), d->J, d->m, d->n, d->p,
                              d->L, F, s);
-  if (e == cudaSuccess) e = ts::launch_sinr_accumulate(a, false, s);
+  if (e == cudaSuccess) e = links_then_finalize(a, false, s);
   return cuda_status(e);
 }
 
-int ts_svd_precoders(const ts_dims* d, const ts_coef* coef, const ts_c64* G, const ts_c64* C,
-                     void* ws, size_t ws_bytes, void* stream) {
+int svd_precoders_impl(const ts_dims* d, const ts_coef* coef, const ts_c64* G, const ts_c64* C,
+                       bool identity, void* ws, size_t ws_bytes, void* stream) {
   static const float kOne = 1.f;
   static float dummy_out;
-  int st = sinr_common_checks(d, coef, G, C, &kOne, &dummy_out, ws, ws_bytes, TS_OP_SINR_SVD);
+  int st = sinr_common_checks(d, coef, G, C, identity, &kOne, &dummy_out, ws, ws_bytes,
+                              TS_OP_SINR_SVD);
   if (st != TS_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const Workspace w = carve(d, TS_OP_SINR_SVD);
   char* base = static_cast<char*>(ws);
   ts::SinrArgs a = base_args(d, coef, G, C, nullptr, nullptr, nullptr, base, w);
+  a.identity_C = identity;
   a.V = reinterpret_cast<float2*>(base + w.V);
   a.pflag = reinterpret_cast<uint8_t*>(base + w.pflag);
   cudaError_t e = cudaSuccess;
   if (coef->mode == TS_COEF_PATHS)
     e = ts::launch_turns(coef->tau_s, d->delta_f_hz, d->J * d->J * d->P,
                          reinterpret_cast<unsigned long long*>(base + w.turns), s);
+  if (e == cudaSuccess) e = ts::launch_sinr_serving(a, s);
   if (e == cudaSuccess) e = ts::launch_svd_precoder(a, s);
   return cuda_status(e);
 }
 
-int ts_sinr_svd_from_precoders(const ts_dims* d, const ts_coef* coef, const ts_c64* G,
-                               const ts_c64* C, const float* sigma2, float* sinr, uint8_t* flags,
-                               void* ws, size_t ws_bytes, void* stream) {
-  int st = sinr_common_checks(d, coef, G, C, sigma2, sinr, ws, ws_bytes, TS_OP_SINR_SVD);
+int svd_from_precoders_impl(const ts_dims* d, const ts_coef* coef, const ts_c64* G,
+                            const ts_c64* C, bool identity, const float* sigma2, float* sinr,
+                            uint8_t* flags, void* ws, size_t ws_bytes, void* stream) {
+  int st = sinr_common_checks(d, coef, G, C, identity, sigma2, sinr, ws, ws_bytes, TS_OP_SINR_SVD);
   if (st != TS_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const Workspace w = carve(d, TS_OP_SINR_SVD);
   char* base = static_cast<char*>(ws);
   ts::SinrArgs a = base_args(d, coef, G, C, sigma2, sinr, flags, base, w);
+  a.identity_C = identity;
   a.V = reinterpret_cast<float2*>(base + w.V);
   a.pflag = reinterpret_cast<uint8_t*>(base + w.pflag);
-  return cuda_status(ts::launch_sinr_accumulate(a, true, s));
+  return cuda_status(links_then_finalize(a, true, s));
+}
+
+}  // namespace
+
+extern "C" {
+
+int ts_sinr_mmse(const ts_dims* d, const ts_coef* coef, const ts_c64* G, const ts_c64* C,
+                 const ts_c64* Pt, const float* sigma2, float* sinr, uint8_t* flags, void* ws,
+                 size_t ws_bytes, void* stream) {
+  return sinr_mmse_impl(d, coef, G, C, false, Pt, sigma2, sinr, flags, ws, ws_bytes, stream);
+}
+
+int ts_svd_precoders(const ts_dims* d, const ts_coef* coef, const ts_c64* G, const ts_c64* C,
+                     void* ws, size_t ws_bytes, void* stream) {
+  return svd_precoders_impl(d, coef, G, C, false, ws, ws_bytes, stream);
+}
+
+int ts_sinr_svd_from_precoders(const ts_dims* d, const ts_coef* coef, const ts_c64* G,
+                               const ts_c64* C, const float* sigma2, float* sinr, uint8_t* flags,
+                               void* ws, size_t ws_bytes, void* stream) {
+  return svd_from_precoders_impl(d, coef, G, C, false, sigma2, sinr, flags, ws, ws_bytes, stream);
 }
 
 int ts_sinr_svd(const ts_dims* d, const ts_coef* coef, const ts_c64* G, const ts_c64* C,
                 const float* sigma2, float* sinr, uint8_t* flags, void* ws, size_t ws_bytes,
                 void* stream) {
-  int st = ts_svd_precoders(d, coef, G, C, ws, ws_bytes, stream);
+  int st = svd_precoders_impl(d, coef, G, C, false, ws, ws_bytes, stream);
   if (st != TS_OK) return st;
-  return ts_sinr_svd_from_precoders(d, coef, G, C, sigma2, sinr, flags, ws, ws_bytes, stream);
+  return svd_from_precoders_impl(d, coef, G, C, false, sigma2, sinr, flags, ws, ws_bytes, stream);
+}
+
+int ts_dense_sinr_svd(const ts_dims* d, const ts_coef* coef, const ts_c64* X, const float* sigma2,
+                      float* sinr, uint8_t* flags, void* ws, size_t ws_bytes, void* stream) {
+  if (d == nullptr) return TS_ERR_NULL;
+  const ts_dims e = dense_dims(d);
+  int st = svd_precoders_impl(&e, coef, X, nullptr, true, ws, ws_bytes, stream);
+  if (st != TS_OK) return st;
+  return svd_from_precoders_impl(&e, coef, X, nullptr, true, sigma2, sinr, flags, ws, ws_bytes,
+                                 stream);
+}
+
+int ts_dense_sinr_mmse(const ts_dims* d, const ts_coef* coef, const ts_c64* X, const ts_c64* Pfull,
+                       const float* sigma2, float* sinr, uint8_t* flags, void* ws, size_t ws_bytes,
+                       void* stream) {
+  if (d == nullptr) return TS_ERR_NULL;
+  const ts_dims e = dense_dims(d);
+  return sinr_mmse_impl(&e, coef, X, nullptr, true, Pfull, sigma2, sinr, flags, ws, ws_bytes,
+                        stream);
 }
 
 }  // extern "C"

@@ -6,23 +6,41 @@
 namespace ts {
 namespace detail {
 extern template cudaError_t run_precoder<2, 2>(const SinrArgs&, cudaStream_t);
-extern template cudaError_t run_accumulate<2, 2>(const SinrArgs&, bool, cudaStream_t);
+extern template cudaError_t run_serving<2, 2>(const SinrArgs&, cudaStream_t);
+extern template cudaError_t run_links<2, 2>(const SinrArgs&, bool, cudaStream_t);
+extern template cudaError_t run_finalize<2, 2>(const SinrArgs&, bool, cudaStream_t);
 extern template cudaError_t run_precoder<4, 2>(const SinrArgs&, cudaStream_t);
-extern template cudaError_t run_accumulate<4, 2>(const SinrArgs&, bool, cudaStream_t);
+extern template cudaError_t run_serving<4, 2>(const SinrArgs&, cudaStream_t);
+extern template cudaError_t run_links<4, 2>(const SinrArgs&, bool, cudaStream_t);
+extern template cudaError_t run_finalize<4, 2>(const SinrArgs&, bool, cudaStream_t);
 extern template cudaError_t run_precoder<4, 4>(const SinrArgs&, cudaStream_t);
-extern template cudaError_t run_accumulate<4, 4>(const SinrArgs&, bool, cudaStream_t);
+extern template cudaError_t run_serving<4, 4>(const SinrArgs&, cudaStream_t);
+extern template cudaError_t run_links<4, 4>(const SinrArgs&, bool, cudaStream_t);
+extern template cudaError_t run_finalize<4, 4>(const SinrArgs&, bool, cudaStream_t);
 extern template cudaError_t run_precoder<8, 2>(const SinrArgs&, cudaStream_t);
-extern template cudaError_t run_accumulate<8, 2>(const SinrArgs&, bool, cudaStream_t);
+extern template cudaError_t run_serving<8, 2>(const SinrArgs&, cudaStream_t);
+extern template cudaError_t run_links<8, 2>(const SinrArgs&, bool, cudaStream_t);
+extern template cudaError_t run_finalize<8, 2>(const SinrArgs&, bool, cudaStream_t);
 extern template cudaError_t run_precoder<8, 4>(const SinrArgs&, cudaStream_t);
-extern template cudaError_t run_accumulate<8, 4>(const SinrArgs&, bool, cudaStream_t);
+extern template cudaError_t run_serving<8, 4>(const SinrArgs&, cudaStream_t);
+extern template cudaError_t run_links<8, 4>(const SinrArgs&, bool, cudaStream_t);
+extern template cudaError_t run_finalize<8, 4>(const SinrArgs&, bool, cudaStream_t);
 extern template cudaError_t run_precoder<8, 8>(const SinrArgs&, cudaStream_t);
-extern template cudaError_t run_accumulate<8, 8>(const SinrArgs&, bool, cudaStream_t);
+extern template cudaError_t run_serving<8, 8>(const SinrArgs&, cudaStream_t);
+extern template cudaError_t run_links<8, 8>(const SinrArgs&, bool, cudaStream_t);
+extern template cudaError_t run_finalize<8, 8>(const SinrArgs&, bool, cudaStream_t);
 extern template cudaError_t run_precoder<16, 4>(const SinrArgs&, cudaStream_t);
-extern template cudaError_t run_accumulate<16, 4>(const SinrArgs&, bool, cudaStream_t);
+extern template cudaError_t run_serving<16, 4>(const SinrArgs&, cudaStream_t);
+extern template cudaError_t run_links<16, 4>(const SinrArgs&, bool, cudaStream_t);
+extern template cudaError_t run_finalize<16, 4>(const SinrArgs&, bool, cudaStream_t);
 extern template cudaError_t run_precoder<16, 8>(const SinrArgs&, cudaStream_t);
-extern template cudaError_t run_accumulate<16, 8>(const SinrArgs&, bool, cudaStream_t);
+extern template cudaError_t run_serving<16, 8>(const SinrArgs&, cudaStream_t);
+extern template cudaError_t run_links<16, 8>(const SinrArgs&, bool, cudaStream_t);
+extern template cudaError_t run_finalize<16, 8>(const SinrArgs&, bool, cudaStream_t);
 extern template cudaError_t run_precoder<16, 16>(const SinrArgs&, cudaStream_t);
-extern template cudaError_t run_accumulate<16, 16>(const SinrArgs&, bool, cudaStream_t);
+extern template cudaError_t run_serving<16, 16>(const SinrArgs&, cudaStream_t);
+extern template cudaError_t run_links<16, 16>(const SinrArgs&, bool, cudaStream_t);
+extern template cudaError_t run_finalize<16, 16>(const SinrArgs&, bool, cudaStream_t);
 
 namespace {
 // ------------------------------------------------------------ small kernels
@@ -91,7 +109,9 @@ int ltile(int L) { return L <= 2 ? 2 : L <= 4 ? 4 : L <= 8 ? 8 : 16; }
 using detail::group_size;
 using detail::ltile;
 using detail::run_precoder;
-using detail::run_accumulate;
+using detail::run_links;
+using detail::run_serving;
+using detail::run_finalize;
 
 #define TS_DISPATCH(FN, ...)                                                        \
   do {                                                                              \
@@ -107,8 +127,14 @@ using detail::run_accumulate;
 
 cudaError_t launch_svd_precoder(const SinrArgs& a, cudaStream_t s) { TS_DISPATCH(run_precoder, a, s); }
 
-cudaError_t launch_sinr_accumulate(const SinrArgs& a, bool svd, cudaStream_t s) {
-  TS_DISPATCH(run_accumulate, a, svd, s);
+cudaError_t launch_sinr_serving(const SinrArgs& a, cudaStream_t s) { TS_DISPATCH(run_serving, a, s); }
+
+cudaError_t launch_sinr_links(const SinrArgs& a, bool svd, cudaStream_t s) {
+  TS_DISPATCH(run_links, a, svd, s);
+}
+
+cudaError_t launch_sinr_finalize(const SinrArgs& a, bool svd, cudaStream_t s) {
+  TS_DISPATCH(run_finalize, a, svd, s);
 }
 
 cudaError_t launch_turns(const float* tau, float df, int count, unsigned long long* turns,

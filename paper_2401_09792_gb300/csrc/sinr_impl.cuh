@@ -3,19 +3,23 @@
 // Work decomposition.  A unit is one (UE i, subcarrier kappa).  A group of MG
 // consecutive lanes (MG = next power of two >= m) evaluates one unit, lane a
 // owning row a of every m-row matrix: the compressed channel H~_ik(kappa)
-// (eq. 15), the effective channel E_ik = H~_ik V_k (eq. 24), the covariance
-// Q~_i (eq. 25) and its Cholesky factor.  A CTA holds T = 256 / MG (at most
-// 64) consecutive subcarriers of one UE, so that every core G_ik and factor
-// C_ik staged in shared memory serves T subcarriers.
+// (eq. 15), the effective channel E_ik = H~_ik V~_k (eq. 24), the covariance
+// Q~_i (eq. 25) and its Cholesky factor.  A CTA of 128 threads holds
+// T = 128 / MG consecutive subcarriers of one UE (or BS).
 //
 //   k_svd_precoder       (BS k, subcarrier tile): H~_kk, Gram H~_kk H~_kk*,
 //                        Jacobi eigensolve, V~_k = H~_kk* U_L Sigma_L^{-1}
-//                        (eq. 7, eq. 23) -> workspace V[k][kappa][n][L]
-//   k_sinr_accumulate    (UE i, subcarrier tile): for every BS k,
-//                        w = c* C (eq. 15), E_ik = H~_ik V~_k (svd) or
-//                        sum_q w_q F_ik[q] (wideband precoder), accumulate
-//                        R_i = sum_{k != i} E E* + sigma^2 I; then the SINR
-//                        of eq. (5) in a cancellation-free form (below).
+//                        (eq. 7, eq. 23) and the serving effective channel
+//                        E_kk = H~_kk V~_k = U_L Sigma_L -> workspace
+//   k_sinr_link          (subcarrier tile, UE i, link k): w = c* C (eq. 15),
+//                        E_ik = H~_ik V~_k (svd) or sum_q w_q F_ik[q]
+//                        (wideband precoder) and the partial covariance
+//                        E_ik E_ik* -> workspace.  The core and precoder
+//                        column chunks are staged through a double-buffered
+//                        cp.async pipeline, one chunk ahead of the arithmetic.
+//   k_sinr_finalize      (UE i, subcarrier): R_i = sum_{k != i} E E* +
+//                        sigma^2 I, Q~_i = R_i + E_ii E_ii* (eq. 25), then the
+//                        SINR of eq. (5) in a cancellation-free form (below).
 //
 // SINR form.  With e_r the columns of E_ii and Q~ = R + E_ii E_ii*,
 // eq. (5) equals a_r / x_r where a_r = e_r* Q~^{-1} e_r = |L_Q^{-1} e_r|^2 and
@@ -30,7 +34,7 @@
 namespace ts {
 namespace detail {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 128;
 // dynamic shared memory a SINR launch may use (the per-CTA limit is 227 KB)
 constexpr size_t kSmemBudget = 200 * 1024;
 
@@ -44,62 +48,28 @@ __device__ __forceinline__ float2 path_coef(float2 alpha, unsigned long long tur
   return make_float2(fmaf(alpha.x, c, alpha.y * s), fmaf(alpha.x, s, -alpha.y * c));
 }
 
-// Stage the coefficient tile c[ch][kap0 .. kap0+T)[0 .. P) into cs[T][P]
-// (zero beyond K) and project it: ws[t][q] = sum_P conj(c[t][P]) C[P][q]
-// (the row vector c* C of eq. 15).  Ends with the block synchronised.
-__device__ __forceinline__ void stage_projection(const SinrArgs& A, int ch, int kap0, int T,
-                                                 float2* cs, float2* Cs, float2* ws, int wstride) {
-  const int P = A.P, p = A.p, K = A.K;
-  const int nth = blockDim.x, tid = threadIdx.x;
-  for (int idx = tid; idx < T * P; idx += nth) {
-    const int t = idx / P, pp = idx - t * P;
-    const int kap = kap0 + t;
-    float2 v = cz();
-    if (kap < K) {
-      if (A.coef_mode == 0)
-        v = A.coef[((size_t)ch * K + kap) * P + pp];
-      else
-        v = path_coef(A.coef[(size_t)ch * P + pp], A.turns[(size_t)ch * P + pp], kap);
-    }
-    cs[idx] = v;
-  }
-  for (int idx = tid; idx < P * p; idx += nth) Cs[idx] = A.C[(size_t)ch * P * p + idx];
-  __syncthreads();
-  for (int idx = tid; idx < T * p; idx += nth) {
-    const int t = idx / p, q = idx - t * p;
-    float2 acc = cz();
-    const float2* crow = cs + t * P;
-    for (int pp = 0; pp < P; ++pp) cmacc(acc, Cs[pp * p + q], crow[pp]);
-    ws[t * wstride + q] = acc;
-  }
-  __syncthreads();
+// 8-byte asynchronous global->shared copy; `valid == false` writes zeros and
+// reads nothing (the source operand then only needs to be a global address).
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool valid) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  const int nbytes = valid ? 8 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(nbytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Stage G_ch[:, 0..m, c0 .. c0+NC) as Gs[q][a][cc] (row stride SG), zero
-// padded for a >= m and columns >= n.
-template <int MG, int NC>
-__device__ __forceinline__ void stage_core_chunk(const SinrArgs& A, int ch, int c0, float2* Gs,
-                                                 int SG) {
-  const int p = A.p, m = A.m, n = A.n;
-  const int nth = blockDim.x, tid = threadIdx.x;
-  const float2* Gch = A.G + (size_t)ch * p * m * n;
-  for (int idx = tid; idx < p * MG * NC; idx += nth) {
-    const int cc = idx % NC;
-    const int a = (idx / NC) % MG;
-    const int q = idx / (NC * MG);
-    const int c = c0 + cc;
-    float2 v = cz();
-    if (a < m && c < n) v = Gch[((size_t)q * m + a) * n + c];
-    Gs[(q * MG + a) * SG + cc] = v;
-  }
-}
-
-// H~ chunk of row a for one subcarrier: h[cc] = sum_q w_q G[q][a][c0 + cc].
+// H~ chunk of row a for one subcarrier: h[cc] = sum_q w_q G[q][a][cc] from a
+// shared-memory chunk with row stride SG (float2 units, even).
 template <int NC>
 __device__ __forceinline__ void core_chunk(const float2* wrow, const float2* Gs, int SG, int MG,
                                            int a, int p, float2 (&h)[NC]) {
 #pragma unroll
   for (int cc = 0; cc < NC; ++cc) h[cc] = cz();
+#pragma unroll 4
   for (int q = 0; q < p; ++q) {
     const float2 w = wrow[q];
     const float4* g4 = reinterpret_cast<const float4*>(Gs + (q * MG + a) * SG);
@@ -113,26 +83,23 @@ __device__ __forceinline__ void core_chunk(const float2* wrow, const float2* Gs,
 }
 
 // ------------------------------------------------------------------ phase 1
-// Shared memory plan of k_svd_precoder (float2 units).
+// k_svd_precoder: one group of MG lanes per (BS k, subcarrier).  Reads the
+// serving link's compressed channel H~_kk (written by k_sinr_link in serve
+// mode), forms the Gram S = H~ H~*, diagonalises it by cyclic Jacobi, rotates
+// the rows W = U* H~, refines them by one sweep of one-sided Jacobi and
+// writes the top-L right singular vectors V~ (normalised rows of W, in order
+// of decreasing row norm = singular value).
 struct PrecoderPlan {
-  int T, NC, SG, SH, SS, wstride;
-  int off_cs, off_Cs, off_ws, off_Gs, off_Hs, off_Ss, off_Us, off_rot, off_sel, total;
+  int T, SH, SS;
+  int off_Hs, off_Ss, off_Us, off_rot, off_sel, total;
 };
 
-__host__ __device__ inline PrecoderPlan precoder_plan(int MG, int T, int NC, int P, int p, int n) {
+__host__ __device__ inline PrecoderPlan precoder_plan(int MG, int T, int n) {
   PrecoderPlan pl;
   pl.T = T;
-  pl.NC = NC;
-  pl.SG = NC + 2;
   pl.SH = n + 1;
   pl.SS = MG + 1;
-  pl.wstride = p + 1;
   int o = 0;
-  pl.off_cs = o; o += T * P;
-  pl.off_Cs = o; o += P * p;
-  pl.off_ws = o; o += T * pl.wstride;
-  pl.off_Gs = o; o += p * MG * pl.SG;
-  o = (o + 1) & ~1;
   pl.off_Hs = o; o += T * MG * pl.SH;
   pl.off_Ss = o; o += T * MG * pl.SS;
   pl.off_Us = o; o += T * MG * pl.SS;
@@ -143,40 +110,31 @@ __host__ __device__ inline PrecoderPlan precoder_plan(int MG, int T, int NC, int
   return pl;
 }
 
-template <int MG, int LT, int NC>
+template <int MG, int LT>
 __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, const PrecoderPlan pl) {
   extern __shared__ __align__(16) float2 sm[];
   const int T = pl.T;
   const int tid = threadIdx.x, g = tid / MG, a = tid % MG;
+  const int nth = blockDim.x;
   const int k = blockIdx.y;
-  const int ch = k * A.J + k;
   const int kap0 = blockIdx.x * T;
   const int kap = kap0 + g;
-  const int m = A.m, n = A.n, p = A.p, L = A.L, K = A.K;
-  float2* cs = sm + pl.off_cs;
-  float2* Cs = sm + pl.off_Cs;
-  float2* ws = sm + pl.off_ws;
-  float2* Gs = sm + pl.off_Gs;
+  const int m = A.m, n = A.n, L = A.L, K = A.K;
   float2* Hs = sm + pl.off_Hs + g * MG * pl.SH;
   float2* Ss = sm + pl.off_Ss + g * MG * pl.SS;
   float2* Us = sm + pl.off_Us + g * MG * pl.SS;
   float4* rot = reinterpret_cast<float4*>(sm + pl.off_rot) + g * (MG / 2);
   int* sel = reinterpret_cast<int*>(sm + pl.off_sel) + g * MG;
 
-  stage_projection(A, ch, kap0, T, cs, Cs, ws, pl.wstride);
-
-  // compressed serving channel H~_kk(kappa), eq. (15), one row per lane
-  for (int c0 = 0; c0 < n; c0 += NC) {
-    if (c0 > 0) __syncthreads();
-    stage_core_chunk<MG, NC>(A, ch, c0, Gs, pl.SG);
-    __syncthreads();
-    float2 h[NC];
-    core_chunk<NC>(ws + g * pl.wstride, Gs, pl.SG, MG, a, p, h);
-#pragma unroll
-    for (int cc = 0; cc < NC; ++cc)
-      if (c0 + cc < n) Hs[a * pl.SH + c0 + cc] = h[cc];
+  // H~_kk rows of the T subcarriers (zero rows for a >= m and beyond K)
+  for (int idx = tid; idx < T * MG * n; idx += nth) {
+    const int c = idx % n, aa = (idx / n) % MG, t = idx / (n * MG);
+    const int kk = kap0 + t;
+    float2 v = cz();
+    if (aa < m && kk < K) v = A.Hserv[(((size_t)k * K + kk) * m + aa) * n + c];
+    sm[pl.off_Hs + (t * MG + aa) * pl.SH + c] = v;
   }
-  __syncwarp();
+  __syncthreads();
 
   // Gram S = H~ H~* (m x m, padded to MG with zero rows), U = I
   {
@@ -202,7 +160,7 @@ __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, con
   // S_pq = |b| e^{i phi} is J = [[c, s e^{i phi}], [-s e^{-i phi}, c]] (the
   // real symmetric Jacobi rotation of [[S_pp, |b|], [|b|, S_qq]] conjugated
   // by diag(1, e^{-i phi})); S <- J* S J, U <- U J.
-  const int max_sweeps = MG <= 8 ? 12 : 16;
+  const int max_sweeps = MG <= 8 ? 8 : 10;
   bool converged = false;
   for (int sweep = 0;; ++sweep) {
     float off = 0.f, dia = 0.f;
@@ -213,8 +171,9 @@ __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, con
     }
     off = gsum<MG>(off);
     dia = gsum<MG>(dia);
-    // FP32 stopping rule: off-diagonal energy below (8 u)^2 of the total, u = 2^-24
-    converged = off <= 2.3e-13f * dia;
+    // the eigenvectors only precondition the one-sided sweeps below, so the
+    // two-sided stage stops at a relative off-diagonal norm of 1e-3
+    converged = off <= 1e-6f * dia;
     // the decision is taken warp-wide: every group keeps sweeping until all
     // groups of the warp have converged (extra sweeps leave S unchanged)
     if (__all_sync(FULL, converged) || sweep == max_sweeps) break;
@@ -282,62 +241,162 @@ __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, con
     }
   }
 
-  // order eigenvalues (descending; padded rows last), pick the top L
-  const float lam_a = (a < m) ? Ss[a * pl.SS + a].x : -INFINITY;
+  // W = U* H~ in place of H~ (rows ~ sigma_r v_r*), column block by block
+  {
+    constexpr int CW = 32 / MG;
+    for (int c0 = 0; c0 < n; c0 += CW) {
+      float2 hb[MG][CW];
+#pragma unroll
+      for (int b = 0; b < MG; ++b)
+#pragma unroll
+        for (int cc = 0; cc < CW; ++cc) hb[b][cc] = (c0 + cc < n) ? Hs[b * pl.SH + c0 + cc] : cz();
+      __syncwarp();
+#pragma unroll
+      for (int cc = 0; cc < CW; ++cc) {
+        float2 acc = cz();
+#pragma unroll
+        for (int b = 0; b < MG; ++b) cmacc(acc, hb[b][cc], Us[b * pl.SS + a]);
+        if (c0 + cc < n) Hs[a * pl.SH + c0 + cc] = acc;
+      }
+      __syncwarp();
+    }
+  }
+  // One-sided (Hestenes) Jacobi sweeps on the rows of W: the rotation of rows
+  // (p, q) is the two-sided rotation of their 2 x 2 Gram block, now formed
+  // from W itself, so small singular values keep their relative accuracy
+  // (the Gram of H~ squares the condition number).  The same rotations are
+  // applied to the columns of U, so that H~ = U W holds throughout.  Two
+  // lanes per pair, each on half of the columns of W and half of the rows of
+  // U.  Sweeps repeat (at most 3) until every pair is orthogonal to 1e-6
+  // relative, decided warp-wide.
+  bool refined = false;
+  {
+    const int j = a >> 1, half = a & 1;
+    const int nh = (n + 1) >> 1;
+    const int c_lo = half * nh, c_hi = min(n, c_lo + nh);
+    const int r_lo = half * (MG / 2), r_hi = r_lo + MG / 2;
+    for (int sweep = 0; sweep < 3; ++sweep) {
+      float worst = 0.f;
+#pragma unroll 1
+      for (int step = 0; step < MG - 1; ++step) {
+        int pp, qq;
+        if (j == 0) { pp = step; qq = MG - 1; }
+        else { pp = (step + j) % (MG - 1); qq = (step - j + MG - 1) % (MG - 1); }
+        float al = 0.f, be = 0.f;
+        float2 ga = cz();
+        for (int c = c_lo; c < c_hi; ++c) {
+          const float2 x = Hs[pp * pl.SH + c], y = Hs[qq * pl.SH + c];
+          al += cabs2(x);
+          be += cabs2(y);
+          cmacc(ga, x, y);
+        }
+        al += __shfl_xor_sync(FULL, al, 1, MG);
+        be += __shfl_xor_sync(FULL, be, 1, MG);
+        ga.x += __shfl_xor_sync(FULL, ga.x, 1, MG);
+        ga.y += __shfl_xor_sync(FULL, ga.y, 1, MG);
+        const float g2 = cabs2(ga);
+        if (al > 0.f && be > 0.f) worst = fmaxf(worst, g2 / (al * be));
+        const float ab = sqrtf(g2);
+        if (ab > 1e-30f && ab > 1e-9f * sqrtf(al * be)) {
+          const float tau = (be - al) / (2.f * ab);
+          const float t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
+          const float cr = 1.f / sqrtf(fmaf(t, t, 1.f));
+          const float sr = t * cr;
+          const float2 e = cscale(ga, 1.f / ab);
+          const float2 se = cscale(e, sr), sec = cscale(cconj(e), sr);
+          for (int c = c_lo; c < c_hi; ++c) {        // W <- J* W (rows p, q)
+            const float2 x = Hs[pp * pl.SH + c], y = Hs[qq * pl.SH + c];
+            float2 nx = cscale(x, cr), ny = cscale(y, cr);
+            cms(nx, se, y);                          // c x - s e y
+            cmac(ny, sec, x);                        // s conj(e) x + c y
+            Hs[pp * pl.SH + c] = nx;
+            Hs[qq * pl.SH + c] = ny;
+          }
+          for (int r = r_lo; r < r_hi; ++r) {        // U <- U J (columns p, q)
+            const float2 x = Us[r * pl.SS + pp], y = Us[r * pl.SS + qq];
+            float2 nx = cscale(x, cr), ny = cscale(y, cr);
+            cms(nx, sec, y);                         // c x - s conj(e) y
+            cmac(ny, se, x);                         // s e x + c y
+            Us[r * pl.SS + pp] = nx;
+            Us[r * pl.SS + qq] = ny;
+          }
+        }
+        __syncwarp();
+      }
+      worst = fmaxf(worst, __shfl_xor_sync(FULL, worst, 1, MG));
+#pragma unroll
+      for (int o = 2; o < MG; o <<= 1) worst = fmaxf(worst, __shfl_xor_sync(FULL, worst, o, MG));
+      refined = worst <= 1e-12f;
+      if (__all_sync(FULL, refined)) break;
+    }
+  }
+
+  // singular values = row norms of W; order them (descending; padding last)
+  float nrm2 = 0.f;
+  for (int c = 0; c < n; ++c) nrm2 += cabs2(Hs[a * pl.SH + c]);
+  Ss[a * pl.SS + a].x = (a < m) ? nrm2 : -INFINITY;
+  __syncwarp();
   int rank = 0;
-  float lam_max = 0.f;
 #pragma unroll
   for (int b = 0; b < MG; ++b) {
-    const float lb = (b < m) ? Ss[b * pl.SS + b].x : -INFINITY;
-    lam_max = fmaxf(lam_max, lb);
-    rank += (lb > lam_a) || (lb == lam_a && b < a);
+    const float lb = Ss[b * pl.SS + b].x;
+    const float la = Ss[a * pl.SS + a].x;
+    rank += (lb > la) || (lb == la && b < a);
   }
   __syncwarp();
   if (rank < MG) sel[rank] = a;
   __syncwarp();
   int idx[LT];
-  float inv_sigma[LT];
+  float inv[LT];
   bool deficient = false;
 #pragma unroll
   for (int r = 0; r < LT; ++r) {
     idx[r] = sel[r < MG ? r : 0];
-    const float lam = Ss[idx[r] * pl.SS + idx[r]].x;
-    const bool bad = (r < L) && !(lam > 0.f);
-    deficient |= bad;
-    inv_sigma[r] = (lam > 0.f) ? 1.f / sqrtf(lam) : 0.f;
+    const float s2 = Ss[idx[r] * pl.SS + idx[r]].x;
+    deficient |= (r < L) && !(s2 > 0.f);
+    inv[r] = (s2 > 0.f) ? 1.f / sqrtf(s2) : 0.f;
   }
 
-  // V~[:, r] = H~* u_r / sigma_r; lanes stride over the n columns
+  // V~[:, r] = conj(row idx_r of W) / sigma_r; lanes stride over the columns
   if (kap < K) {
     float2* Vout = A.V + ((size_t)k * K + kap) * n * L;
     for (int c = a; c < n; c += MG) {
-      float2 v[LT];
-#pragma unroll
-      for (int r = 0; r < LT; ++r) v[r] = cz();
-      for (int b = 0; b < m; ++b) {
-        const float2 hb = cconj(Hs[b * pl.SH + c]);
-#pragma unroll
-        for (int r = 0; r < LT; ++r) cmac(v[r], hb, Us[b * pl.SS + idx[r]]);
-      }
 #pragma unroll
       for (int r = 0; r < LT; ++r)
-        if (r < L) Vout[(size_t)c * L + r] = cscale(v[r], inv_sigma[r]);
+        if (r < L) Vout[(size_t)c * L + r] = cscale(cconj(Hs[idx[r] * pl.SH + c]), inv[r]);
+    }
+    // serving effective channel E_kk = H~_kk V~_k = U W W* / sigma = U_L Sigma_L
+    if (a < m) {
+      float2* Eout = A.Eserv + (((size_t)k * K + kap) * m + a) * L;
+#pragma unroll
+      for (int r = 0; r < LT; ++r)
+        if (r < L) {
+          const float sg = Ss[idx[r] * pl.SS + idx[r]].x;
+          Eout[r] = cscale(Us[a * pl.SS + idx[r]], sg > 0.f ? sqrtf(sg) : 0.f);
+        }
     }
     if (a == 0)
-      A.pflag[(size_t)k * K + kap] =
-          (deficient ? TS_FLAG_RANK_DEFICIENT : 0) | (converged ? 0 : TS_FLAG_EIG_UNCONVERGED);
+      A.pflag[(size_t)k * K + kap] = (deficient ? TS_FLAG_RANK_DEFICIENT : 0) |
+                                     ((converged || refined) ? 0 : TS_FLAG_EIG_UNCONVERGED);
   }
 }
 
 // ------------------------------------------------------------------ phase 2
-struct AccumPlan {
+// k_sinr_link: one CTA per (subcarrier tile, UE i, link).  It rebuilds
+// H~_ik on the T subcarriers of its tile chunk by chunk, forms E_ik and
+// writes the partial covariance rows E_ik E_ik* (interfering links) or E_ii
+// itself (the serving link of the wideband-precoder variant) to workspace.
+// Shared memory plan (float2 units): C_ik, the coefficient tile or path
+// form, two stage buffers (core chunk or wideband fold, precoder chunk), the
+// projection ws; the per-group scratch Es reuses the stage buffers.
+struct LinkPlan {
   int T, NC, SG, SV, SF, ES, wstride;
-  int off_cs, off_Cs, off_ws, off_Gs, off_Vs, off_Fs, off_Es, total;
+  int off_Cs, off_cs, off_pa, off_pt, off_ws, off_stage, stage, off_Gs, off_Vs, off_Es, total;
 };
 
-__host__ __device__ inline AccumPlan accum_plan(int MG, int LT, int T, int NC, int P, int p,
-                                                bool svd) {
-  AccumPlan pl;
+__host__ __device__ inline LinkPlan link_plan(int MG, int LT, int T, int NC, int P, int p, int mode) {
+  const bool svd = mode != 1;            // chunked modes (svd, serve)
+  LinkPlan pl;
   pl.T = T;
   pl.NC = NC;
   pl.SG = NC + 2;
@@ -346,110 +405,242 @@ __host__ __device__ inline AccumPlan accum_plan(int MG, int LT, int T, int NC, i
   pl.ES = MG * LT + 2;
   pl.wstride = p + 1;
   int o = 0;
-  pl.off_cs = o; o += T * P;
   pl.off_Cs = o; o += P * p;
+  pl.off_cs = o; o += T * P;
+  pl.off_pa = o; o += P;
+  pl.off_pt = o; o += P;
   pl.off_ws = o; o += T * pl.wstride;
   o = (o + 1) & ~1;
-  pl.off_Gs = pl.off_Vs = pl.off_Fs = o;
-  if (svd) {
-    o += p * MG * pl.SG;
-    o = (o + 1) & ~1;
-    pl.off_Vs = o; o += T * pl.SV;
-  } else {
-    o += p * MG * pl.SF;
-  }
-  o = (o + 1) & ~1;
-  pl.off_Es = o; o += T * pl.ES;
+  pl.off_stage = o;
+  int so = 0;
+  pl.off_Gs = so; so += svd ? p * MG * pl.SG : p * MG * pl.SF;
+  so = (so + 1) & ~1;
+  pl.off_Vs = so; if (mode == 0) so += T * pl.SV;
+  so = (so + 1) & ~1;
+  pl.stage = so;
+  const int nbuf = svd ? 2 : 1;
+  const int es = T * pl.ES;
+  o += (nbuf * so > es ? nbuf * so : es);
+  pl.off_Es = pl.off_stage;
   pl.total = o;
   return pl;
 }
 
-template <int MG, int LT, int NC, bool SVD>
-__global__ void __launch_bounds__(kThreads) k_sinr_accumulate(const SinrArgs A, const AccumPlan pl) {
+// Modes of k_sinr_link.
+constexpr int kModeSvd = 0;     // interfering link, E = H~ V~ (SVD precoders)
+constexpr int kModeFold = 1;    // any link, E = sum_q w_q F[q] (wideband precoder)
+constexpr int kModeServe = 2;   // serving link of the SVD variant: write H~_kk rows
+
+template <int MG, int LT, int NC, int MODE>
+__global__ void __launch_bounds__(kThreads) k_sinr_link(const SinrArgs A, const LinkPlan pl) {
+  constexpr bool CHUNKED = MODE != kModeFold;
   extern __shared__ __align__(16) float2 sm[];
   const int T = pl.T;
   const int tid = threadIdx.x, g = tid / MG, a = tid % MG;
+  const int nth = blockDim.x;
   const int i = blockIdx.y;
+  const int z = blockIdx.z;
   const int kap0 = blockIdx.x * T;
   const int kap = kap0 + g;
-  const int J = A.J, m = A.m, n = A.n, p = A.p, L = A.L, K = A.K;
-  float2* cs = sm + pl.off_cs;
+  const int J = A.J, m = A.m, n = A.n, p = A.p, L = A.L, K = A.K, P = A.P;
+  // svd: z enumerates the interfering links; fold: z is the BS index;
+  // serve: the serving link
+  const int k = MODE == kModeSvd ? (z < i ? z : z + 1) : MODE == kModeFold ? z : i;
+  const int ch = i * J + k;
+  const int nchunk = CHUNKED ? (n + NC - 1) / NC : 1;
   float2* Cs = sm + pl.off_Cs;
+  float2* cs = sm + pl.off_cs;
   float2* ws = sm + pl.off_ws;
-  float2* Gs = sm + pl.off_Gs;
-  float2* Vs = sm + pl.off_Vs;
-  float2* Fs = sm + pl.off_Fs;
-  float2* Es = sm + pl.off_Es + g * pl.ES;
+  float2* stage0 = sm + pl.off_stage;
   const float2* wrow = ws + g * pl.wstride;
 
-  float2 R[MG];      // row a of R_i = sum_{k != i} E_ik E_ik* (+ sigma^2 I later)
-  float2 Eself[LT];  // row a of E_ii
-#pragma unroll
-  for (int b = 0; b < MG; ++b) R[b] = cz();
-#pragma unroll
-  for (int l = 0; l < LT; ++l) Eself[l] = cz();
-
-  for (int k = 0; k < J; ++k) {
-    const int ch = i * J + k;
-    __syncthreads();
-    if (!SVD) {
-      // F_ik[q][a][l] = (G_ik x_2 Pt_k^T)[a][l][q], folded once per call
-      const float2* Fch = A.F + (size_t)ch * p * m * L;
-      for (int idx = tid; idx < p * MG * LT; idx += blockDim.x) {
-        const int l = idx % LT, aa = (idx / LT) % MG, q = idx / (LT * MG);
-        Fs[(q * MG + aa) * pl.SF + l] =
-            (aa < m && l < L) ? Fch[((size_t)q * m + aa) * L + l] : cz();
+  auto issue_chunk = [&](int cidx) {
+    float2* buf = stage0 + (cidx & 1) * pl.stage;
+    const int c0 = cidx * NC;
+    const float2* Gch = A.G + (size_t)ch * p * m * n;
+    for (int idx = tid; idx < p * MG * NC; idx += nth) {
+      const int cc = idx % NC, aa = (idx / NC) % MG, q = idx / (NC * MG);
+      const int c = c0 + cc;
+      const bool ok = aa < m && c < n;
+      cp_async8(buf + pl.off_Gs + (q * MG + aa) * pl.SG + cc,
+                ok ? Gch + ((size_t)q * m + aa) * n + c : A.G, ok);
+    }
+    if (MODE == kModeSvd) {
+      for (int idx = tid; idx < T * NC * LT; idx += nth) {
+        const int l = idx % LT, cc = (idx / LT) % NC, t = idx / (LT * NC);
+        const int kk2 = kap0 + t, c = c0 + cc;
+        const bool ok = kk2 < K && c < n && l < L;
+        cp_async8(buf + pl.off_Vs + t * pl.SV + cc * LT + l,
+                  ok ? A.V + (((size_t)k * K + kk2) * n + c) * L + l : A.V, ok);
       }
     }
-    stage_projection(A, ch, kap0, T, cs, Cs, ws, pl.wstride);
+  };
 
-    float2 E[LT];
+  // group 0: C_ik, the coefficients of the tile and chunk 0 (or the fold)
+  if (!A.identity_C)
+    for (int idx = tid; idx < P * p; idx += nth)
+      cp_async8(Cs + idx, A.C + (size_t)ch * P * p + idx, true);
+  if (A.coef_mode == 0) {
+    for (int idx = tid; idx < T * P; idx += nth) {
+      const int t = idx / P, pp = idx - t * P;
+      const bool ok = kap0 + t < K;
+      cp_async8(cs + idx, ok ? A.coef + ((size_t)ch * K + kap0 + t) * P + pp : A.coef, ok);
+    }
+  } else {
+    for (int idx = tid; idx < P; idx += nth) {
+      cp_async8(sm + pl.off_pa + idx, A.coef + (size_t)ch * P + idx, true);
+      cp_async8(sm + pl.off_pt + idx, A.turns + (size_t)ch * P + idx, true);
+    }
+  }
+  if (CHUNKED) {
+    issue_chunk(0);
+  } else {
+    const float2* Fch = A.F + (size_t)ch * p * m * L;
+    for (int idx = tid; idx < p * MG * LT; idx += nth) {
+      const int l = idx % LT, aa = (idx / LT) % MG, q = idx / (LT * MG);
+      const bool ok = aa < m && l < L;
+      cp_async8(stage0 + pl.off_Gs + (q * MG + aa) * pl.SF + l,
+                ok ? Fch + ((size_t)q * m + aa) * L + l : A.F, ok);
+    }
+  }
+  cp_async_commit();
+  if (CHUNKED && nchunk > 1) issue_chunk(1);
+  cp_async_commit();
+  cp_async_wait<1>();
+  __syncthreads();
+
+  // projection w = c* C for the T subcarriers (eq. 15)
+  if (A.coef_mode != 0) {
+    const float2* pa = sm + pl.off_pa;
+    const unsigned long long* pt = reinterpret_cast<const unsigned long long*>(sm + pl.off_pt);
+    for (int idx = tid; idx < T * P; idx += nth) {
+      const int t = idx / P, pp = idx - t * P;
+      cs[idx] = (kap0 + t < K) ? path_coef(pa[pp], pt[pp], kap0 + t) : cz();
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < T * p; idx += nth) {
+    const int t = idx / p, q = idx - t * p;
+    float2 acc = cz();
+    const float2* crow = cs + t * P;
+    if (A.identity_C)
+      acc = cconj(crow[q]);            // dense channel: C = I, p = P
+    else
+      for (int pp = 0; pp < P; ++pp) cmacc(acc, Cs[pp * p + q], crow[pp]);
+    ws[t * pl.wstride + q] = acc;
+  }
+  __syncthreads();
+
+  float2 E[LT];   // row a of E_ik
 #pragma unroll
-    for (int l = 0; l < LT; ++l) E[l] = cz();
-    if (SVD) {
-      for (int c0 = 0; c0 < n; c0 += NC) {
-        if (c0 > 0) __syncthreads();
-        stage_core_chunk<MG, NC>(A, ch, c0, Gs, pl.SG);
-        for (int idx = tid; idx < T * NC * LT; idx += blockDim.x) {
-          const int l = idx % LT, cc = (idx / LT) % NC, t = idx / (LT * NC);
-          const int kk = kap0 + t, c = c0 + cc;
-          float2 v = cz();
-          if (kk < K && c < n && l < L) v = A.V[(((size_t)k * K + kk) * n + c) * L + l];
-          Vs[t * pl.SV + cc * LT + l] = v;
-        }
+  for (int l = 0; l < LT; ++l) E[l] = cz();
+  float2* Hrow = nullptr;
+  if (MODE == kModeServe)
+    Hrow = A.Hserv + (((size_t)i * K + (kap < K ? kap : 0)) * m + (a < m ? a : 0)) * n;
+  const bool hvalid = kap < K && a < m;
+  if (CHUNKED) {
+    for (int cidx = 0; cidx < nchunk; ++cidx) {
+      if (cidx > 0) {
+        if (cidx + 1 < nchunk) issue_chunk(cidx + 1);
+        cp_async_commit();
+        cp_async_wait<1>();
         __syncthreads();
-        float2 h[NC];
-        core_chunk<NC>(wrow, Gs, pl.SG, MG, a, p, h);
-        const float2* vrow = Vs + g * pl.SV;
+      }
+      const float2* buf = stage0 + (cidx & 1) * pl.stage;
+      float2 h[NC];
+      core_chunk<NC>(wrow, buf + pl.off_Gs, pl.SG, MG, a, p, h);
+      if (MODE == kModeServe) {
+        const int c0 = cidx * NC;
+        if (hvalid) {
+#pragma unroll
+          for (int cc = 0; cc < NC; ++cc)
+            if (c0 + cc < n) Hrow[c0 + cc] = h[cc];
+        }
+      } else {
+        const float2* vrow = buf + pl.off_Vs + g * pl.SV;
 #pragma unroll
         for (int cc = 0; cc < NC; ++cc) {
 #pragma unroll
-          for (int l = 0; l < LT; ++l) cmac(E[l], h[cc], vrow[cc * LT + l]);
+          for (int l2 = 0; l2 < LT / 2; ++l2) {
+            const float4 v = reinterpret_cast<const float4*>(vrow + cc * LT)[l2];
+            cmac(E[2 * l2], h[cc], make_float2(v.x, v.y));
+            cmac(E[2 * l2 + 1], h[cc], make_float2(v.z, v.w));
+          }
         }
       }
-    } else {
-      for (int q = 0; q < p; ++q) {
-        const float2 w = wrow[q];
-        const float2* frow = Fs + (q * MG + a) * pl.SF;
+      __syncthreads();   // this buffer is refilled two chunks later
+    }
+  } else {
+    const float2* Fs = stage0 + pl.off_Gs;
+#pragma unroll 4
+    for (int q = 0; q < p; ++q) {
+      const float2 w = wrow[q];
+      const float4* f4 = reinterpret_cast<const float4*>(Fs + (q * MG + a) * pl.SF);
 #pragma unroll
-        for (int l = 0; l < LT; ++l) cmac(E[l], w, frow[l]);
+      for (int l2 = 0; l2 < LT / 2; ++l2) {
+        const float4 f = f4[l2];
+        cmac(E[2 * l2], w, make_float2(f.x, f.y));
+        cmac(E[2 * l2 + 1], w, make_float2(f.z, f.w));
       }
     }
+    __syncthreads();     // Es below reuses the stage buffer
+  }
+  cp_async_wait<0>();
 
-    if (k == i) {
+  if (MODE == kModeServe || !hvalid) return;    // no shuffles or block barriers below
+  if (MODE == kModeFold && k == i) {
+    // serving effective channel of the wideband-precoder variant
+    float2* Eout = A.Eserv + (((size_t)i * K + kap) * m + a) * L;
 #pragma unroll
-      for (int l = 0; l < LT; ++l) Eself[l] = E[l];
-    } else {
+    for (int l = 0; l < LT; ++l)
+      if (l < L) Eout[l] = E[l];
+    return;
+  }
+  // partial covariance rows (E E*)[a][b], b < m (eq. 25)
+  float2* Es = sm + pl.off_Es + g * pl.ES;
 #pragma unroll
-      for (int l = 0; l < LT; ++l) Es[a * LT + l] = E[l];
-      __syncwarp();
+  for (int l = 0; l < LT; ++l) Es[a * LT + l] = E[l];
+  __syncwarp(__activemask());
+  const int slot = MODE == kModeSvd ? z : (z < i ? z : z - 1);
+  float2* Rout = A.Rpart + ((((size_t)i * (J - 1) + slot) * K + kap) * m + a) * m;
+  for (int b = 0; b < m; ++b) {
+    float2 r = cz();
 #pragma unroll
-      for (int b = 0; b < MG; ++b) {
+    for (int l = 0; l < LT; ++l) cmacc(r, E[l], Es[b * LT + l]);
+    Rout[b] = r;
+  }
+}
+
+// k_sinr_finalize: one group of MG lanes per (UE i, subcarrier): sums the
+// partial covariances, adds the noise (eq. 25) and evaluates the SINR.
+template <int MG, int LT, bool SVD>
+__global__ void __launch_bounds__(kThreads) k_sinr_finalize(const SinrArgs A, int T) {
+  __shared__ __align__(16) float2 sm_es[kThreads * LT + (kThreads / 2) * 2];
+  const int tid = threadIdx.x, g = tid / MG, a = tid % MG;
+  const int i = blockIdx.y;
+  const int kap = blockIdx.x * T + g;
+  const int J = A.J, m = A.m, L = A.L, K = A.K;
+  const int kc = kap < K ? kap : K - 1;     // tail groups recompute the last subcarrier
+  float2* Es = sm_es + g * (MG * LT + 2);
+
+  float2 R[MG], Eself[LT];
 #pragma unroll
-        for (int l = 0; l < LT; ++l) cmacc(R[b], E[l], Es[b * LT + l]);
-      }
-      __syncwarp();
+  for (int b = 0; b < MG; ++b) R[b] = cz();
+  if (a < m) {
+    for (int s = 0; s < J - 1; ++s) {
+      const float2* Rin = A.Rpart + ((((size_t)i * (J - 1) + s) * K + kc) * m + a) * m;
+#pragma unroll
+      for (int b = 0; b < MG; ++b)
+        if (b < m) R[b] = cadd(R[b], Rin[b]);
     }
+    // serving effective channel E_ii (eq. 24), from the precoder phase (svd)
+    // or from the serving-link pass of k_sinr_link (wideband precoder)
+    const float2* Ein = A.Eserv + (((size_t)i * K + kc) * m + a) * L;
+#pragma unroll
+    for (int l = 0; l < LT; ++l) Eself[l] = (l < L) ? Ein[l] : cz();
+  } else {
+#pragma unroll
+    for (int l = 0; l < LT; ++l) Eself[l] = cz();
   }
 
   // noise on the m x m block, identity on the padding rows (eq. 25)
@@ -520,18 +711,18 @@ __global__ void __launch_bounds__(kThreads) k_sinr_accumulate(const SinrArgs A, 
 
 template <int MG, int LT>
 cudaError_t run_precoder(const SinrArgs& A, cudaStream_t s) {
-  constexpr int NC = MG >= 16 ? 8 : 16;
-  // groups per CTA: as many as fit 96 KB of shared memory, at most 256 / MG
+  // groups per CTA: 128 / MG, halved while the CTA needs more than 28 KB of
+  // shared memory (eight CTAs per SM), keeping whole warps for the group
+  // shuffles and votes
   int T = kThreads / MG;
-  PrecoderPlan pl = precoder_plan(MG, T, NC, A.P, A.p, A.n);
-  // keep whole warps: the group shuffles and votes use the full lane mask
-  while (T * MG > 32 && (size_t)pl.total * sizeof(float2) > 96 * 1024) {
+  PrecoderPlan pl = precoder_plan(MG, T, A.n);
+  while (T * MG > 32 && (size_t)pl.total * sizeof(float2) > 28 * 1024) {
     T /= 2;
-    pl = precoder_plan(MG, T, NC, A.P, A.p, A.n);
+    pl = precoder_plan(MG, T, A.n);
   }
   const size_t smem = (size_t)pl.total * sizeof(float2);
   if (smem > kSmemBudget) return cudaErrorInvalidValue;
-  auto kern = k_svd_precoder<MG, LT, NC>;
+  auto kern = k_svd_precoder<MG, LT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((A.K + T - 1) / T, A.J);
@@ -539,29 +730,47 @@ cudaError_t run_precoder(const SinrArgs& A, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int MG, int LT>
-cudaError_t run_accumulate(const SinrArgs& A, bool svd, cudaStream_t s) {
-  constexpr int NC = MG >= 16 ? 8 : 16;
-  int T = (kThreads / MG) > 64 ? 64 : kThreads / MG;
-  AccumPlan pl = accum_plan(MG, LT, T, NC, A.P, A.p, svd);
+template <int MG, int LT, int MODE>
+cudaError_t launch_link_mode(const SinrArgs& A, int nz, cudaStream_t s) {
+  constexpr int NC = 8;
+  if (nz == 0) return cudaSuccess;
+  int T = kThreads / MG;
+  LinkPlan pl = link_plan(MG, LT, T, NC, A.P, A.p, MODE);
   while (T * MG > 32 && (size_t)pl.total * sizeof(float2) > kSmemBudget) {
     T /= 2;
-    pl = accum_plan(MG, LT, T, NC, A.P, A.p, svd);
+    pl = link_plan(MG, LT, T, NC, A.P, A.p, MODE);
   }
   const size_t smem = (size_t)pl.total * sizeof(float2);
   if (smem > kSmemBudget) return cudaErrorInvalidValue;
+  dim3 grid((A.K + T - 1) / T, A.J, nz);
+  auto kern = k_sinr_link<MG, LT, NC, MODE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, T * MG, smem, s>>>(A, pl);
+  return cudaGetLastError();
+}
+
+// svd: interfering links; wideband precoder: every link
+template <int MG, int LT>
+cudaError_t run_links(const SinrArgs& A, bool svd, cudaStream_t s) {
+  return svd ? launch_link_mode<MG, LT, kModeSvd>(A, A.J - 1, s)
+             : launch_link_mode<MG, LT, kModeFold>(A, A.J, s);
+}
+
+// svd: rebuild the serving links' compressed channels H~_kk into workspace
+template <int MG, int LT>
+cudaError_t run_serving(const SinrArgs& A, cudaStream_t s) {
+  return launch_link_mode<MG, LT, kModeServe>(A, 1, s);
+}
+
+template <int MG, int LT>
+cudaError_t run_finalize(const SinrArgs& A, bool svd, cudaStream_t s) {
+  const int T = kThreads / MG;
   dim3 grid((A.K + T - 1) / T, A.J);
-  if (svd) {
-    auto kern = k_sinr_accumulate<MG, LT, NC, true>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kern<<<grid, T * MG, smem, s>>>(A, pl);
-  } else {
-    auto kern = k_sinr_accumulate<MG, LT, NC, false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kern<<<grid, T * MG, smem, s>>>(A, pl);
-  }
+  if (svd)
+    k_sinr_finalize<MG, LT, true><<<grid, kThreads, 0, s>>>(A, T);
+  else
+    k_sinr_finalize<MG, LT, false><<<grid, kThreads, 0, s>>>(A, T);
   return cudaGetLastError();
 }
 

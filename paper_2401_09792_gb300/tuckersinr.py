@@ -19,7 +19,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libtuckersinr.so")
 
 TS_COEF_DENSE, TS_COEF_PATHS = 0, 1
-TS_OP_SINR_SVD, TS_OP_SINR_MMSE = 0, 1
+TS_OP_SINR_SVD, TS_OP_SINR_MMSE, TS_OP_DENSE_SVD, TS_OP_DENSE_MMSE = 0, 1, 2, 3
 TS_FLAG_NOT_PD, TS_FLAG_NONFINITE, TS_FLAG_RANK_DEFICIENT, TS_FLAG_EIG_UNCONVERGED = 1, 2, 4, 8
 
 
@@ -52,6 +52,7 @@ _SIG = {
     "ts_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "ts_last_cuda_error": (ctypes.c_int, []),
     "ts_abi_version": (ctypes.c_int, []),
+    "ts_set_timing_events": (None, [_P, _P]),
     "ts_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(ts_dims), ctypes.c_int]),
     "ts_coefficients": (ctypes.c_int, [ctypes.POINTER(ts_dims), _P, _P, _P, _P]),
     "ts_project_precoder": (ctypes.c_int, [ctypes.POINTER(ts_dims), _P, _P, _P, _P]),
@@ -59,6 +60,10 @@ _SIG = {
                                     _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "ts_sinr_svd": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.POINTER(ts_coef), _P, _P, _P,
                                    _P, _P, _P, ctypes.c_size_t, _P]),
+    "ts_dense_sinr_svd": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.POINTER(ts_coef), _P, _P,
+                                         _P, _P, _P, ctypes.c_size_t, _P]),
+    "ts_dense_sinr_mmse": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.POINTER(ts_coef), _P, _P,
+                                          _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "ts_svd_precoders": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.POINTER(ts_coef), _P, _P,
                                         _P, ctypes.c_size_t, _P]),
     "ts_sinr_svd_from_precoders": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.POINTER(ts_coef),
@@ -127,6 +132,13 @@ def _check(fn: str, st: int):
         raise TsError(fn, st, _lib)
 
 
+def ts_set_timing_events(start=None, stop=None):
+    """Record two torch.cuda.Event objects around the dominant kernel of the
+    following SINR calls on this thread (None, None: off)."""
+    h = lambda e: None if e is None else e.cuda_event  # noqa: E731
+    load().ts_set_timing_events(h(start), h(stop))
+
+
 def ts_workspace_bytes(d: Dims, op: int) -> int:
     return load().ts_workspace_bytes(ctypes.byref(d.c()), op)
 
@@ -185,6 +197,29 @@ def ts_sinr_svd_from_precoders(d: Dims, coef: ts_coef, G, C, sigma2, sinr, flags
            lib.ts_sinr_svd_from_precoders(ctypes.byref(d.c()), ctypes.byref(coef), _ptr(G), _ptr(C),
                                           _ptr(sigma2), _ptr(sinr), _ptr(flags), _ptr(ws),
                                           ws.numel(), _stream(stream)))
+
+
+def ts_dense_sinr_svd(d: Dims, coef: ts_coef, X, sigma2, sinr, flags, ws, stream=None):
+    lib = load()
+    _check("ts_dense_sinr_svd", lib.ts_dense_sinr_svd(ctypes.byref(d.c()), ctypes.byref(coef), _ptr(X),
+                                                      _ptr(sigma2), _ptr(sinr), _ptr(flags), _ptr(ws),
+                                                      ws.numel(), _stream(stream)))
+
+
+def ts_dense_sinr_mmse(d: Dims, coef: ts_coef, X, Pfull, sigma2, sinr, flags, ws, stream=None):
+    lib = load()
+    _check("ts_dense_sinr_mmse", lib.ts_dense_sinr_mmse(ctypes.byref(d.c()), ctypes.byref(coef),
+                                                        _ptr(X), _ptr(Pfull), _ptr(sigma2), _ptr(sinr),
+                                                        _ptr(flags), _ptr(ws), ws.numel(),
+                                                        _stream(stream)))
+
+
+def channels_to_device(X, device="cuda") -> torch.Tensor:
+    """(J, J, M, N, P) complex -> device [J*J][P][M][N] complex64."""
+    import numpy as np
+    J, _, M, N, P = X.shape
+    a = np.ascontiguousarray(np.transpose(X, (0, 1, 4, 2, 3)).reshape(J * J, P, M, N))
+    return torch.from_numpy(a.astype(np.complex64)).to(device)
 
 
 # ----------------------------------------------------------- layout marshalling

@@ -61,18 +61,47 @@ class Case:
         del keep
         return sinr.cpu().numpy().astype(np.float64), flags.cpu().numpy()
 
+    def with_channels(self, X=None):
+        """Attach dense channels (default: drawn by the channel model) for the
+        dense-comparator path."""
+        self.X = synth.channel_submatrices(self.w) if X is None else X
+        self.Xd = ts.channels_to_device(self.X, self.dev)
+        return self
+
+    def gpu_dense_sinr(self, precoder: str, mode: str = "paths"):
+        w = self.w
+        cs, keep = self.coef_struct(mode)
+        sinr = torch.full((w.J, w.K, w.L), float("nan"), device=self.dev)
+        flags = torch.full((w.J, w.K), 255, dtype=torch.uint8, device=self.dev)
+        if precoder == "svd":
+            ws = ts.workspace(self.d, ts.TS_OP_DENSE_SVD, self.dev)
+            ts.ts_dense_sinr_svd(self.d, cs, self.Xd, self.sig, sinr, flags, ws)
+        else:
+            ws = ts.workspace(self.d, ts.TS_OP_DENSE_MMSE, self.dev)
+            ts.ts_dense_sinr_mmse(self.d, cs, self.Xd, self.Pf, self.sig, sinr, flags, ws)
+        torch.cuda.synchronize()
+        del keep
+        return sinr.cpu().numpy().astype(np.float64), flags.cpu().numpy()
+
+    def oracle_dense_sinr(self, precoder: str):
+        Pw = self.Pw if precoder == "mmse" else None
+        return S.dense_sinr(self.X, self.coef, self.s2, self.w.L, precoder, Pw)
+
     def oracle_sinr(self, precoder: str):
         Pt = self.Ptn if precoder == "mmse" else None
         return S.tucker_sinr(self.tk["G"], self.tk["C"], self.coef, self.s2, self.w.L, precoder, Pt)
 
 
-def svd_gap(case: Case) -> np.ndarray:
+def svd_gap(case: Case, dense: bool = False) -> np.ndarray:
     """Smallest relative gap between the squared singular values that the SVD
     precoder must separate (within the top L, and between L and L+1), over all
     serving links, per subcarrier: (K,)."""
     w = case.w
     gaps = np.full(w.K, np.inf)
-    Hs = S.compressed_channels(case.tk["G"], case.tk["C"], case.coef)
+    if dense:
+        Hs = S.dense_channels(case.X, case.coef)
+    else:
+        Hs = S.compressed_channels(case.tk["G"], case.tk["C"], case.coef)
     for k in range(w.J):
         sv = np.linalg.svd(Hs[k, k], compute_uv=False) ** 2          # (K, min(m, n))
         top = sv[:, :min(w.L + 1, sv.shape[1])]
@@ -80,3 +109,25 @@ def svd_gap(case: Case) -> np.ndarray:
         if d.shape[1]:
             gaps = np.minimum(gaps, d.min(axis=1))
     return gaps
+
+
+def interference_condition(case: Case, precoder: str, dense: bool = False) -> np.ndarray:
+    """2-norm condition number of each UE's interference-plus-noise covariance
+    R_i(kappa) = sum_{k != i} E_ik E_ik* + sigma_i^2 I (eq. 4 / eq. 25 without the
+    serving term), from the oracle: (J, K).  FP32 rounding of the effective
+    channels perturbs the SINR by up to ~u cond(R) relative."""
+    w = case.w
+    if dense:
+        Hs = S.dense_channels(case.X, case.coef)
+        Pw = case.Pw
+    else:
+        Hs = S.compressed_channels(case.tk["G"], case.tk["C"], case.coef)
+        Pw = case.Ptn
+    V = S._precoders(Hs, w.L, precoder, Pw if precoder == "mmse" else None)
+    E = S.effective_channels(Hs, V)
+    Q = S.covariance(E, case.s2)
+    out = np.empty((w.J, w.K))
+    for i in range(w.J):
+        R = Q[i] - E[i, i] @ np.conj(np.swapaxes(E[i, i], 1, 2))
+        out[i] = np.linalg.cond(R)
+    return out
