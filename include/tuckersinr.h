@@ -183,6 +183,33 @@ int ts_dense_sinr_mmse(const ts_dims* d, const ts_coef* coef, const ts_c64* X,
                        const ts_c64* Pfull, const float* sigma2, float* sinr,
                        uint8_t* flags, void* ws, size_t ws_bytes, void* stream);
 
+/* Allocation-free variant of ts_sinr_mmse (the paper has no counterpart: it
+ * is a service of this library).  For callers that cannot allocate device
+ * memory when they evaluate SINR -- a per-slot scheduler loop with a fixed
+ * latency budget, where cudaMalloc/cudaFree may synchronise the device and
+ * stall for milliseconds, or a plug-in inside a framework that owns and
+ * pre-reserves all device memory.  Same arguments and results as
+ * ts_sinr_mmse, without ws/ws_bytes: the scratch is a fixed array of
+ * TS_NOALLOC_SCRATCH_BYTES in the library's own device memory, which every
+ * GPU that loads the library holds until the process exits.
+ *   - Sizes whose ts_workspace_bytes(d, TS_OP_SINR_MMSE) exceeds
+ *     TS_NOALLOC_SCRATCH_BYTES are rejected with TS_ERR_WORKSPACE before
+ *     any launch (for example J = 8, m = 8, L = 8 fits up to K = 495
+ *     subcarriers).
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current); make that first call
+ *     before any stream capture.
+ *   - Every call shares the one array per device, which keeps the previous
+ *     call's contents (nothing needs clearing: each call writes every byte
+ *     it reads).  Calls that overlap on the GPU -- on two streams, or from
+ *     two host threads on one device -- race on it; serialise them.
+ *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library
+ *     routine. */
+#define TS_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+int ts_sinr_mmse_noalloc(const ts_dims* d, const ts_coef* coef, const ts_c64* G,
+                         const ts_c64* C, const ts_c64* Pt, const float* sigma2,
+                         float* sinr, uint8_t* flags, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -119,6 +119,10 @@ ts::SinrArgs base_args(const ts_dims* d, const ts_coef* coef, const ts_c64* G, c
 
 }  // namespace
 
+namespace ts {
+int record_cuda_error(cudaError_t e) { return cuda_status(e); }
+}  // namespace ts
+
 extern "C" {
 
 const char* ts_status_string(int status) {

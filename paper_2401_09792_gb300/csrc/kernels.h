@@ -42,6 +42,9 @@ cudaError_t launch_svd_precoder(const SinrArgs& a, cudaStream_t s);
 cudaError_t launch_sinr_links(const SinrArgs& a, bool svd, cudaStream_t s);
 cudaError_t launch_sinr_finalize(const SinrArgs& a, bool svd, cudaStream_t s);
 
+// Store a CUDA error for ts_last_cuda_error() and return TS_ERR_CUDA.
+int record_cuda_error(cudaError_t e);
+
 // Largest m and L the kernels support.
 constexpr int kMaxRankM = 16;
 

@@ -64,6 +64,8 @@ _SIG = {
                                          _P, _P, _P, ctypes.c_size_t, _P]),
     "ts_dense_sinr_mmse": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.POINTER(ts_coef), _P, _P,
                                           _P, _P, _P, _P, ctypes.c_size_t, _P]),
+    "ts_sinr_mmse_noalloc": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.POINTER(ts_coef), _P, _P,
+                                            _P, _P, _P, _P, _P]),
     "ts_svd_precoders": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.POINTER(ts_coef), _P, _P,
                                         _P, ctypes.c_size_t, _P]),
     "ts_sinr_svd_from_precoders": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.POINTER(ts_coef),
@@ -183,6 +185,19 @@ def ts_sinr_svd(d: Dims, coef: ts_coef, G, C, sigma2, sinr, flags, ws, stream=No
     _check("ts_sinr_svd", lib.ts_sinr_svd(ctypes.byref(d.c()), ctypes.byref(coef), _ptr(G), _ptr(C),
                                           _ptr(sigma2), _ptr(sinr), _ptr(flags), _ptr(ws),
                                           ws.numel(), _stream(stream)))
+
+
+TS_NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+def ts_sinr_mmse_noalloc(d: Dims, coef: ts_coef, G, C, Pt, sigma2, sinr, flags, stream=None):
+    """ts_sinr_mmse without a workspace argument: the library's own fixed
+    device scratch is used (for callers that cannot allocate at call time)."""
+    lib = load()
+    _check("ts_sinr_mmse_noalloc",
+           lib.ts_sinr_mmse_noalloc(ctypes.byref(d.c()), ctypes.byref(coef), _ptr(G), _ptr(C),
+                                    _ptr(Pt), _ptr(sigma2), _ptr(sinr), _ptr(flags),
+                                    _stream(stream)))
 
 
 def ts_svd_precoders(d: Dims, coef: ts_coef, G, C, ws, stream=None):
