@@ -82,6 +82,82 @@ __device__ __forceinline__ void core_chunk(const float2* wrow, const float2* Gs,
   }
 }
 
+// One step of cyclic two-sided Jacobi on the Hermitian MG x MG matrix S
+// (row a of S and of the accumulated rotation U in lane a of the group), with
+// the round-robin ordering: in step t (0 <= t < MG-1) lane MG-1 pairs with
+// lane t, and lanes t+j, t-j (mod MG-1) pair for 1 <= j < MG/2.  For a pair
+// (p, q) with S_pq = |b| e^{i phi} the rotation is
+// J = [[c, s e^{i phi}], [-s e^{-i phi}, c]] -- the real symmetric Jacobi
+// rotation of [[S_pp, |b|], [|b|, S_qq]] conjugated by diag(1, e^{-i phi}) --
+// and S <- J* S J, U <- U J.  Both lanes of a pair compute the rotation from
+// the same three numbers (lane p's S_pq and the two diagonals), so they agree
+// bit for bit; rows are exchanged by shuffles, columns rotate in registers.
+template <int MG>
+__device__ __forceinline__ void jacobi_step(const int t, float2 (&S)[MG], float2 (&U)[MG], int a) {
+  int b;
+  bool is_p;
+  if (a == MG - 1) { b = t; is_p = false; }
+  else if (a == t) { b = MG - 1; is_p = true; }
+  else {
+    const int d = (a - t + (MG - 1)) % (MG - 1);
+    is_p = d < MG / 2;
+    b = (2 * t - a + 2 * (MG - 1)) % (MG - 1);
+  }
+  const float d_self = pick(S, a).x;
+  const float d_other = __shfl_sync(FULL, d_self, b, MG);
+  const float2 mine = pick(S, b);
+  const float2 theirs = gshfl<MG>(mine, b);
+  const float app = is_p ? d_self : d_other, aqq = is_p ? d_other : d_self;
+  const float2 bpq = is_p ? mine : theirs;
+  const float ab = sqrtf(cabs2(bpq));
+  float c = 1.f, s = 0.f;
+  float2 e = make_float2(1.f, 0.f);
+  if (ab > 1e-30f && ab > 1e-9f * sqrtf(fabsf(app * aqq))) {
+    const float tau = (aqq - app) / (2.f * ab);
+    const float tt = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
+    c = 1.f / sqrtf(fmaf(tt, tt, 1.f));
+    s = tt * c;
+    e = cscale(bpq, 1.f / ab);
+  }
+  // rows: S <- J* S (row p' = c p - s e q, row q' = s conj(e) p + c q)
+  {
+    const float2 se = cscale(e, s), sec = cscale(cconj(e), s);
+#pragma unroll
+    for (int k = 0; k < MG; ++k) {
+      const float2 other = gshfl<MG>(S[k], b);
+      float2 v = cscale(S[k], c);
+      if (is_p) cms(v, se, other); else cmac(v, sec, other);
+      S[k] = v;
+    }
+  }
+  // columns: S <- S J and U <- U J, every pair of this step
+#pragma unroll
+  for (int j = 0; j < MG / 2; ++j) {
+    const int pj = j == 0 ? t : (t + j) % (MG - 1);
+    const int qj = j == 0 ? MG - 1 : (t - j + MG - 1) % (MG - 1);
+    const float cj = __shfl_sync(FULL, c, pj, MG);
+    const float sj = __shfl_sync(FULL, s, pj, MG);
+    const float2 ej = gshfl<MG>(e, pj);
+    const float2 se = cscale(ej, sj), sec = cscale(cconj(ej), sj);
+    {
+      const float2 x = S[pj], y = S[qj];
+      float2 nx = cscale(x, cj), ny = cscale(y, cj);
+      cms(nx, sec, y);     // c x - s conj(e) y
+      cmac(ny, se, x);     // s e x + c y
+      S[pj] = nx;
+      S[qj] = ny;
+    }
+    {
+      const float2 x = U[pj], y = U[qj];
+      float2 nx = cscale(x, cj), ny = cscale(y, cj);
+      cms(nx, sec, y);
+      cmac(ny, se, x);
+      U[pj] = nx;
+      U[qj] = ny;
+    }
+  }
+}
+
 // ------------------------------------------------------------------ phase 1
 // k_svd_precoder: one group of MG lanes per (BS k, subcarrier).  Reads the
 // serving link's compressed channel H~_kk (written by k_sinr_link in serve
@@ -91,7 +167,7 @@ __device__ __forceinline__ void core_chunk(const float2* wrow, const float2* Gs,
 // of decreasing row norm = singular value).
 struct PrecoderPlan {
   int T, SH, SS;
-  int off_Hs, off_Ss, off_Us, off_rot, off_sel, total;
+  int off_Hs, off_Ss, off_Us, off_sel, total;
 };
 
 __host__ __device__ inline PrecoderPlan precoder_plan(int MG, int T, int n) {
@@ -103,8 +179,6 @@ __host__ __device__ inline PrecoderPlan precoder_plan(int MG, int T, int n) {
   pl.off_Hs = o; o += T * MG * pl.SH;
   pl.off_Ss = o; o += T * MG * pl.SS;
   pl.off_Us = o; o += T * MG * pl.SS;
-  o = (o + 1) & ~1;
-  pl.off_rot = o; o += T * MG;           // MG/2 float4 per group
   pl.off_sel = o; o += T * MG / 2 + 1;   // MG int per group
   pl.total = o;
   return pl;
@@ -123,7 +197,6 @@ __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, con
   float2* Hs = sm + pl.off_Hs + g * MG * pl.SH;
   float2* Ss = sm + pl.off_Ss + g * MG * pl.SS;
   float2* Us = sm + pl.off_Us + g * MG * pl.SS;
-  float4* rot = reinterpret_cast<float4*>(sm + pl.off_rot) + g * (MG / 2);
   int* sel = reinterpret_cast<int*>(sm + pl.off_sel) + g * MG;
 
   // H~_kk rows of the T subcarriers (zero rows for a >= m and beyond K)
@@ -136,110 +209,45 @@ __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, con
   }
   __syncthreads();
 
-  // Gram S = H~ H~* (m x m, padded to MG with zero rows), U = I
-  {
-    float2 srow[MG];
+  // Gram S = H~ H~* (m x m, padded to MG with zero rows), row a in lane a
+  float2 S[MG], U[MG];
 #pragma unroll
-    for (int b = 0; b < MG; ++b) srow[b] = cz();
+  for (int b = 0; b < MG; ++b) {
+    S[b] = cz();
+    U[b] = make_float2(b == a ? 1.f : 0.f, 0.f);
+  }
+  {
     const float2* ha = Hs + a * pl.SH;
     for (int c = 0; c < n; ++c) {
       const float2 x = ha[c];
 #pragma unroll
-      for (int b = 0; b < MG; ++b) cmacc(srow[b], x, Hs[b * pl.SH + c]);
-    }
-#pragma unroll
-    for (int b = 0; b < MG; ++b) {
-      Ss[a * pl.SS + b] = srow[b];
-      Us[a * pl.SS + b] = make_float2(b == a ? 1.f : 0.f, 0.f);
+      for (int b = 0; b < MG; ++b) cmacc(S[b], x, Hs[b * pl.SH + c]);
     }
   }
-  __syncwarp();
 
-  // cyclic Jacobi with a round-robin ordering: MG/2 disjoint rotations per
-  // step, MG-1 steps per sweep.  The rotation for pair (p, q) with
-  // S_pq = |b| e^{i phi} is J = [[c, s e^{i phi}], [-s e^{-i phi}, c]] (the
-  // real symmetric Jacobi rotation of [[S_pp, |b|], [|b|, S_qq]] conjugated
-  // by diag(1, e^{-i phi})); S <- J* S J, U <- U J.
+  // Cyclic Jacobi on S held in registers (see jacobi_step): the eigenvectors
+  // only precondition the one-sided sweeps below, so the two-sided stage stops
+  // at a relative off-diagonal norm of 1e-3.  The stopping decision is taken
+  // warp-wide (extra sweeps leave a converged S unchanged).
   const int max_sweeps = MG <= 8 ? 8 : 10;
   bool converged = false;
   for (int sweep = 0;; ++sweep) {
     float off = 0.f, dia = 0.f;
 #pragma unroll
     for (int b = 0; b < MG; ++b) {
-      const float v = cabs2(Ss[a * pl.SS + b]);
+      const float v = cabs2(S[b]);
       if (b == a) dia += v; else off += v;
     }
     off = gsum<MG>(off);
     dia = gsum<MG>(dia);
-    // the eigenvectors only precondition the one-sided sweeps below, so the
-    // two-sided stage stops at a relative off-diagonal norm of 1e-3
     converged = off <= 1e-6f * dia;
-    // the decision is taken warp-wide: every group keeps sweeping until all
-    // groups of the warp have converged (extra sweeps leave S unchanged)
     if (__all_sync(FULL, converged) || sweep == max_sweeps) break;
-#pragma unroll 1
-    for (int step = 0; step < MG - 1; ++step) {
-      if (a < MG / 2) {
-        int pp, qq;
-        if (a == 0) { pp = step; qq = MG - 1; }
-        else { pp = (step + a) % (MG - 1); qq = (step - a + MG - 1) % (MG - 1); }
-        const float app = Ss[pp * pl.SS + pp].x, aqq = Ss[qq * pl.SS + qq].x;
-        const float2 b = Ss[pp * pl.SS + qq];
-        const float ab = sqrtf(cabs2(b));
-        float c = 1.f, s = 0.f;
-        float2 e = make_float2(1.f, 0.f);
-        if (ab > 1e-30f && ab > 1e-9f * sqrtf(fabsf(app * aqq))) {
-          const float tau = (aqq - app) / (2.f * ab);
-          const float t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
-          c = 1.f / sqrtf(fmaf(t, t, 1.f));
-          s = t * c;
-          e = cscale(b, 1.f / ab);
-        }
-        rot[a] = make_float4(c, s, e.x, e.y);
-        sel[2 * a] = pp;
-        sel[2 * a + 1] = qq;
-      }
-      __syncwarp();
-      // rows: S <- J* S ; lane = column
 #pragma unroll
-      for (int j = 0; j < MG / 2; ++j) {
-        const float4 r = rot[j];
-        const int pp = sel[2 * j], qq = sel[2 * j + 1];
-        const float2 e = make_float2(r.z, r.w);
-        const float2 x = Ss[pp * pl.SS + a], y = Ss[qq * pl.SS + a];
-        float2 nx = cscale(x, r.x), ny = cscale(y, r.x);
-        cms(nx, cscale(e, r.y), y);            // c x - s e y
-        cmac(ny, cscale(cconj(e), r.y), x);    // s conj(e) x + c y
-        Ss[pp * pl.SS + a] = nx;
-        Ss[qq * pl.SS + a] = ny;
-      }
-      __syncwarp();
-      // columns: S <- S J and U <- U J ; lane = row
-#pragma unroll
-      for (int j = 0; j < MG / 2; ++j) {
-        const float4 r = rot[j];
-        const int pp = sel[2 * j], qq = sel[2 * j + 1];
-        const float2 e = make_float2(r.z, r.w);
-        {
-          const float2 x = Ss[a * pl.SS + pp], y = Ss[a * pl.SS + qq];
-          float2 nx = cscale(x, r.x), ny = cscale(y, r.x);
-          cms(nx, cscale(cconj(e), r.y), y);   // c x - s conj(e) y
-          cmac(ny, cscale(e, r.y), x);         // s e x + c y
-          Ss[a * pl.SS + pp] = nx;
-          Ss[a * pl.SS + qq] = ny;
-        }
-        {
-          const float2 x = Us[a * pl.SS + pp], y = Us[a * pl.SS + qq];
-          float2 nx = cscale(x, r.x), ny = cscale(y, r.x);
-          cms(nx, cscale(cconj(e), r.y), y);
-          cmac(ny, cscale(e, r.y), x);
-          Us[a * pl.SS + pp] = nx;
-          Us[a * pl.SS + qq] = ny;
-        }
-      }
-      __syncwarp();
-    }
+    for (int t = 0; t < MG - 1; ++t) jacobi_step<MG>(t, S, U, a);
   }
+#pragma unroll
+  for (int b = 0; b < MG; ++b) Us[a * pl.SS + b] = U[b];
+  __syncwarp();
 
   // W = U* H~ in place of H~ (rows ~ sigma_r v_r*), column block by block
   {
