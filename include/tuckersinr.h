@@ -91,7 +91,9 @@ enum {
   TS_OP_SINR_SVD = 0,
   TS_OP_SINR_MMSE = 1,
   TS_OP_DENSE_SVD = 2,
-  TS_OP_DENSE_MMSE = 3
+  TS_OP_DENSE_MMSE = 3,
+  TS_OP_SINR_SVD_ADJOINT = 4,
+  TS_OP_SINR_MMSE_ADJOINT = 5
 };
 
 /* Human-readable name of a status code (static storage). */
@@ -182,6 +184,34 @@ int ts_dense_sinr_svd(const ts_dims* d, const ts_coef* coef, const ts_c64* X,
 int ts_dense_sinr_mmse(const ts_dims* d, const ts_coef* coef, const ts_c64* X,
                        const ts_c64* Pfull, const float* sigma2, float* sinr,
                        uint8_t* flags, void* ws, size_t ws_bytes, void* stream);
+
+/* Adjoints (vector-Jacobian products) of the compressed SINR.  The paper has
+ * no adjoint; these differentiate its compressed SINR (eq. 15, 23-28) for a
+ * real loss l whose gradient dl/dSINR is `dsinr` ([J][K][L] float):
+ *   ts_sinr_svd_adjoint:  dG = dl/dG ([J*J][p][m][n]), dC = dl/dC ([J*J][P][p])
+ *                         through the SVD precoders of eq. (7) as well;
+ *   ts_sinr_mmse_adjoint: also dPt = dl/dPt ([J][n][L]) for the wideband
+ *                         precoders (ts_project_precoder_adjoint carries it to
+ *                         dl/dB).
+ * Gradients of complex parameters are dl/dRe + i dl/dIm; outputs are
+ * overwritten.  dl/dA is zero: A cancels (eq. 28).  The forward quantities
+ * are recomputed from (G, C, coefficients), nothing is kept from a forward
+ * call; `sinr` (may be NULL) receives the recomputed forward SINR.
+ * Near-degenerate singular values of a serving channel make the SVD adjoint
+ * ill-conditioned (1 / (s_r^2 - s_s^2) terms), as they make the SINR itself.
+ * ws: ts_workspace_bytes(d, TS_OP_SINR_SVD_ADJOINT / _MMSE_ADJOINT) bytes. */
+int ts_sinr_svd_adjoint(const ts_dims* d, const ts_coef* coef, const ts_c64* G,
+                        const ts_c64* C, const float* sigma2, const float* dsinr,
+                        ts_c64* dG, ts_c64* dC, float* sinr, void* ws,
+                        size_t ws_bytes, void* stream);
+int ts_sinr_mmse_adjoint(const ts_dims* d, const ts_coef* coef, const ts_c64* G,
+                         const ts_c64* C, const ts_c64* Pt, const float* sigma2,
+                         const float* dsinr, ts_c64* dG, ts_c64* dC, ts_c64* dPt,
+                         float* sinr, void* ws, size_t ws_bytes, void* stream);
+/* dB[k] = conj(Pfull[k]) dPt[k]^T, the adjoint of Pt = B^T Pfull.
+ * Pfull: [J][N][L]; dPt: [J][n][L]; dB (out): [J][N][n]. */
+int ts_project_precoder_adjoint(const ts_dims* d, const ts_c64* Pfull,
+                                const ts_c64* dPt, ts_c64* dB, void* stream);
 
 /* Allocation-free variant of ts_sinr_mmse (the paper has no counterpart: it
  * is a service of this library).  For callers that cannot allocate device

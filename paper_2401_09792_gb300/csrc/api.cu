@@ -82,6 +82,37 @@ Workspace carve(const ts_dims* d, int op) {
   return w;
 }
 
+// Adjoint workspace (byte offsets, each 256-byte aligned).
+struct AdjWorkspace {
+  size_t turns = 0, Hall = 0, V = 0, Eserv = 0, pflag = 0, U = 0, S = 0, Vm = 0, W = 0, E = 0,
+         gE = 0, gH = 0, gV = 0, gw = 0, total = 0;
+};
+
+AdjWorkspace carve_adjoint(const ts_dims* d, bool svd) {
+  AdjWorkspace w;
+  size_t o = 0;
+  const size_t nch = (size_t)d->J * d->J, K = d->K, m = d->m, n = d->n, L = d->L, p = d->p;
+  auto take = [&](size_t bytes) { const size_t at = o; o = align_up(o + bytes, 256); return at; };
+  w.turns = take(nch * d->P * sizeof(unsigned long long));
+  w.Hall = take(nch * K * m * n * sizeof(float2));
+  if (svd) {
+    w.V = take((size_t)d->J * K * n * L * sizeof(float2));
+    w.Eserv = take((size_t)d->J * K * m * L * sizeof(float2));
+    w.pflag = take((size_t)d->J * K);
+    w.U = take((size_t)d->J * K * m * m * sizeof(float2));
+    w.S = take((size_t)d->J * K * m * sizeof(float));
+    w.Vm = take((size_t)d->J * K * n * m * sizeof(float2));
+  }
+  w.W = take(nch * K * p * sizeof(float2));
+  w.E = take(nch * K * m * L * sizeof(float2));
+  w.gE = take(nch * K * m * L * sizeof(float2));
+  w.gH = take(nch * K * m * n * sizeof(float2));
+  w.gV = take((size_t)d->J * K * n * L * sizeof(float2));
+  w.gw = take(nch * K * p * sizeof(float2));
+  w.total = o;
+  return w;
+}
+
 int check_coef(const ts_coef* c) {
   if (c == nullptr) return TS_ERR_NULL;
   if (c->mode == TS_COEF_DENSE) {
@@ -111,6 +142,7 @@ ts::SinrArgs base_args(const ts_dims* d, const ts_coef* coef, const ts_c64* G, c
   a.Eserv = reinterpret_cast<float2*>(ws + w.Eserv);
   a.Rpart = reinterpret_cast<float2*>(ws + w.Rpart);
   a.Hserv = reinterpret_cast<float2*>(ws + w.Hserv);
+  a.serv_stride = 1;
   a.sigma2 = sigma2;
   a.sinr = sinr;
   a.flags = flags;
@@ -155,6 +187,8 @@ size_t ts_workspace_bytes(const ts_dims* d, int op) {
     return carve(&e, op == TS_OP_DENSE_SVD ? TS_OP_SINR_SVD : TS_OP_SINR_MMSE).total;
   }
   if (check_dims(d) != TS_OK) return 0;
+  if (op == TS_OP_SINR_SVD_ADJOINT || op == TS_OP_SINR_MMSE_ADJOINT)
+    return carve_adjoint(d, op == TS_OP_SINR_SVD_ADJOINT).total;
   if (op != TS_OP_SINR_SVD && op != TS_OP_SINR_MMSE) return 0;
   return carve(d, op).total;
 }
@@ -180,6 +214,98 @@ int ts_project_precoder(const ts_dims* d, const ts_c64* B, const ts_c64* Pfull, 
   return cuda_status(ts::launch_project_precoder(
       reinterpret_cast<const float2*>(B), reinterpret_cast<const float2*>(Pfull), d->J, d->N, d->n,
       d->L, reinterpret_cast<float2*>(Pt), static_cast<cudaStream_t>(stream)));
+}
+
+}  // extern "C"
+
+namespace {
+
+int adjoint_impl(const ts_dims* d, const ts_coef* coef, const ts_c64* G, const ts_c64* C,
+                 const ts_c64* Pt, const float* sigma2, const float* dsinr, ts_c64* dG, ts_c64* dC,
+                 ts_c64* dPt, float* sinr, void* ws, size_t ws_bytes, void* stream) {
+  const bool svd = Pt == nullptr;
+  int st = check_dims(d);
+  if (st != TS_OK) return st;
+  st = check_coef(coef);
+  if (st != TS_OK) return st;
+  if (G == nullptr || C == nullptr || sigma2 == nullptr || dsinr == nullptr || dG == nullptr ||
+      dC == nullptr || (!svd && dPt == nullptr))
+    return TS_ERR_NULL;
+  if (!aligned8(G) || !aligned8(C) || !aligned8(Pt) || !aligned8(dG) || !aligned8(dC) ||
+      !aligned8(dPt) || ((uintptr_t)sigma2 & 3u) || ((uintptr_t)dsinr & 3u) ||
+      ((uintptr_t)sinr & 3u))
+    return TS_ERR_ALIGN;
+  const AdjWorkspace w = carve_adjoint(d, svd);
+  if (ws == nullptr || ws_bytes < w.total) return TS_ERR_WORKSPACE;
+  if (((uintptr_t)ws & 255u) != 0) return TS_ERR_ALIGN;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  char* base = static_cast<char*>(ws);
+  Workspace fw;
+  fw.turns = w.turns;
+  ts::SinrArgs a = base_args(d, coef, G, C, sigma2, sinr, nullptr, base, fw);
+  a.Hserv = reinterpret_cast<float2*>(base + w.Hall);
+  a.serv_stride = d->J + 1;          // serving link (k, k) inside the all-link layout
+  cudaError_t e = cudaSuccess;
+  if (coef->mode == TS_COEF_PATHS)
+    e = ts::launch_turns(coef->tau_s, d->delta_f_hz, d->J * d->J * d->P,
+                         reinterpret_cast<unsigned long long*>(base + w.turns), s);
+  if (e == cudaSuccess) e = ts::launch_sinr_rebuild(a, s);
+  if (svd && e == cudaSuccess) {
+    a.V = reinterpret_cast<float2*>(base + w.V);
+    a.Eserv = reinterpret_cast<float2*>(base + w.Eserv);
+    a.pflag = reinterpret_cast<uint8_t*>(base + w.pflag);
+    a.Uout = reinterpret_cast<float2*>(base + w.U);
+    a.Sout = reinterpret_cast<float*>(base + w.S);
+    a.Vmout = reinterpret_cast<float2*>(base + w.Vm);
+    e = ts::launch_svd_precoder(a, s);
+  }
+  if (e == cudaSuccess) {
+    ts::AdjointWork aw{};
+    aw.Pt = reinterpret_cast<const float2*>(Pt);
+    aw.dsinr = dsinr;
+    aw.sinr = sinr;
+    aw.W = reinterpret_cast<float2*>(base + w.W);
+    aw.E = reinterpret_cast<float2*>(base + w.E);
+    aw.gE = reinterpret_cast<float2*>(base + w.gE);
+    aw.gH = reinterpret_cast<float2*>(base + w.gH);
+    aw.gV = reinterpret_cast<float2*>(base + w.gV);
+    aw.gw = reinterpret_cast<float2*>(base + w.gw);
+    aw.dG = reinterpret_cast<float2*>(dG);
+    aw.dC = reinterpret_cast<float2*>(dC);
+    aw.dPt = reinterpret_cast<float2*>(dPt);
+    e = ts::launch_adjoint(a, aw, s);
+  }
+  return cuda_status(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+int ts_sinr_svd_adjoint(const ts_dims* d, const ts_coef* coef, const ts_c64* G, const ts_c64* C,
+                        const float* sigma2, const float* dsinr, ts_c64* dG, ts_c64* dC,
+                        float* sinr, void* ws, size_t ws_bytes, void* stream) {
+  return adjoint_impl(d, coef, G, C, nullptr, sigma2, dsinr, dG, dC, nullptr, sinr, ws, ws_bytes,
+                      stream);
+}
+
+int ts_sinr_mmse_adjoint(const ts_dims* d, const ts_coef* coef, const ts_c64* G, const ts_c64* C,
+                         const ts_c64* Pt, const float* sigma2, const float* dsinr, ts_c64* dG,
+                         ts_c64* dC, ts_c64* dPt, float* sinr, void* ws, size_t ws_bytes,
+                         void* stream) {
+  if (Pt == nullptr) return TS_ERR_NULL;
+  return adjoint_impl(d, coef, G, C, Pt, sigma2, dsinr, dG, dC, dPt, sinr, ws, ws_bytes, stream);
+}
+
+int ts_project_precoder_adjoint(const ts_dims* d, const ts_c64* Pfull, const ts_c64* dPt,
+                                ts_c64* dB, void* stream) {
+  int st = check_dims(d);
+  if (st != TS_OK) return st;
+  if (Pfull == nullptr || dPt == nullptr || dB == nullptr) return TS_ERR_NULL;
+  if (!aligned8(Pfull) || !aligned8(dPt) || !aligned8(dB)) return TS_ERR_ALIGN;
+  return cuda_status(ts::launch_project_precoder_adjoint(
+      reinterpret_cast<const float2*>(Pfull), reinterpret_cast<const float2*>(dPt), d->J, d->N,
+      d->n, d->L, reinterpret_cast<float2*>(dB), static_cast<cudaStream_t>(stream)));
 }
 
 }  // extern "C"

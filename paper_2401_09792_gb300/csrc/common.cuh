@@ -128,4 +128,30 @@ __device__ __forceinline__ void trsv_rows(const float2 (&Lr)[NN], float2 (&Y)[NR
   }
 }
 
+// Back substitution L* X = Y for the NN x NN lower-triangular L held one row
+// per lane (from chol_rows); Y (NN x NR, one row per lane) is overwritten by
+// X.  Row j of L is broadcast entry by entry, so lane a < j gets L[j][a].
+template <int MG, int NN, int NR>
+__device__ __forceinline__ void trsv_rows_conjT(const float2 (&Lr)[NN], float2 (&Y)[NR], int a) {
+#pragma unroll
+  for (int j = NN - 1; j >= 0; --j) {
+    if (a == j) {
+      const float inv = 1.0f / Lr[j].x;
+#pragma unroll
+      for (int r = 0; r < NR; ++r) Y[r] = cscale(Y[r], inv);
+    }
+    float2 lja = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int c = 0; c < j; ++c) {
+      const float2 v = gshfl<MG>(Lr[c], j);
+      if (c == a) lja = v;
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const float2 xj = gshfl<MG>(Y[r], j);
+      if (a < j) cmsc(Y[r], xj, lja);     // Y[a] -= conj(L[j][a]) X[j]
+    }
+  }
+}
+
 }  // namespace ts

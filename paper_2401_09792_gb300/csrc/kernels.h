@@ -19,7 +19,12 @@ struct SinrArgs {
   float2* V;                        // svd: precoders [J][K][n][L] (workspace)
   uint8_t* pflag;                   // svd: precoder flags [J][K] (workspace)
   float2* Eserv;                    // wideband: serving effective channels [J][K][m][L] (workspace)
-  float2* Hserv;                    // svd: serving compressed channels [J][K][m][n] (workspace)
+  float2* Hserv;                    // svd: serving compressed channels [J][K][m][n] (workspace),
+                                    // or all links [J*J][K][m][n] (adjoint)
+  int serv_stride;                  // serving link k at Hserv[(k * serv_stride) * K + kappa]
+  float2* Uout;                     // adjoint: left singular vectors [J][K][m][m] (or nullptr)
+  float* Sout;                      // adjoint: singular values [J][K][m]
+  float2* Vmout;                    // adjoint: right singular vectors [J][K][n][m]
   float2* Rpart;                    // partial covariances [J][J-1][K][m][m] (workspace)
   const float2* F;                  // mmse: G_ik x_2 Pt_k^T, [J*J][p][m][L] (workspace)
   const float* sigma2;              // [J]
@@ -41,6 +46,27 @@ cudaError_t launch_sinr_serving(const SinrArgs& a, cudaStream_t s);
 cudaError_t launch_svd_precoder(const SinrArgs& a, cudaStream_t s);
 cudaError_t launch_sinr_links(const SinrArgs& a, bool svd, cudaStream_t s);
 cudaError_t launch_sinr_finalize(const SinrArgs& a, bool svd, cudaStream_t s);
+
+// Buffers of the adjoint pipeline (adjoint.cu); Pt == nullptr selects SVD
+// precoders (read from SinrArgs::Vmout/Uout/Sout).
+struct AdjointWork {
+  const float2* Pt;        // wideband: projected precoders [J][n][L]
+  const float* dsinr;      // [J][K][L]
+  float* sinr;             // forward SINR [J][K][L] (optional)
+  float2* W;               // w = c* C   [J*J][K][p]
+  float2* E;               // E_ik       [J*J][K][m][L]
+  float2* gE;              // dl/dE_ik   [J*J][K][m][L]
+  float2* gH;              // dl/dH~_ik  [J*J][K][m][n]
+  float2* gV;              // dl/dV_k    [J][K][n][L]
+  float2* gw;              // dl/dw      [J*J][K][p]
+  float2* dG;              // [J*J][p][m][n]
+  float2* dC;              // [J*J][P][p]
+  float2* dPt;             // [J][n][L] (wideband)
+};
+cudaError_t launch_sinr_rebuild(const SinrArgs& a, cudaStream_t s);
+cudaError_t launch_adjoint(const SinrArgs& a, const AdjointWork& w, cudaStream_t s);
+cudaError_t launch_project_precoder_adjoint(const float2* Pfull, const float2* dPt, int J, int N,
+                                            int n, int L, float2* dB, cudaStream_t s);
 
 // Store a CUDA error for ts_last_cuda_error() and return TS_ERR_CUDA.
 int record_cuda_error(cudaError_t e);

@@ -7,38 +7,47 @@ namespace ts {
 namespace detail {
 extern template cudaError_t run_precoder<2, 2>(const SinrArgs&, cudaStream_t);
 extern template cudaError_t run_serving<2, 2>(const SinrArgs&, cudaStream_t);
+extern template cudaError_t run_rebuild<2, 2>(const SinrArgs&, cudaStream_t);
 extern template cudaError_t run_links<2, 2>(const SinrArgs&, bool, cudaStream_t);
 extern template cudaError_t run_finalize<2, 2>(const SinrArgs&, bool, cudaStream_t);
 extern template cudaError_t run_precoder<4, 2>(const SinrArgs&, cudaStream_t);
 extern template cudaError_t run_serving<4, 2>(const SinrArgs&, cudaStream_t);
+extern template cudaError_t run_rebuild<4, 2>(const SinrArgs&, cudaStream_t);
 extern template cudaError_t run_links<4, 2>(const SinrArgs&, bool, cudaStream_t);
 extern template cudaError_t run_finalize<4, 2>(const SinrArgs&, bool, cudaStream_t);
 extern template cudaError_t run_precoder<4, 4>(const SinrArgs&, cudaStream_t);
 extern template cudaError_t run_serving<4, 4>(const SinrArgs&, cudaStream_t);
+extern template cudaError_t run_rebuild<4, 4>(const SinrArgs&, cudaStream_t);
 extern template cudaError_t run_links<4, 4>(const SinrArgs&, bool, cudaStream_t);
 extern template cudaError_t run_finalize<4, 4>(const SinrArgs&, bool, cudaStream_t);
 extern template cudaError_t run_precoder<8, 2>(const SinrArgs&, cudaStream_t);
 extern template cudaError_t run_serving<8, 2>(const SinrArgs&, cudaStream_t);
+extern template cudaError_t run_rebuild<8, 2>(const SinrArgs&, cudaStream_t);
 extern template cudaError_t run_links<8, 2>(const SinrArgs&, bool, cudaStream_t);
 extern template cudaError_t run_finalize<8, 2>(const SinrArgs&, bool, cudaStream_t);
 extern template cudaError_t run_precoder<8, 4>(const SinrArgs&, cudaStream_t);
 extern template cudaError_t run_serving<8, 4>(const SinrArgs&, cudaStream_t);
+extern template cudaError_t run_rebuild<8, 4>(const SinrArgs&, cudaStream_t);
 extern template cudaError_t run_links<8, 4>(const SinrArgs&, bool, cudaStream_t);
 extern template cudaError_t run_finalize<8, 4>(const SinrArgs&, bool, cudaStream_t);
 extern template cudaError_t run_precoder<8, 8>(const SinrArgs&, cudaStream_t);
 extern template cudaError_t run_serving<8, 8>(const SinrArgs&, cudaStream_t);
+extern template cudaError_t run_rebuild<8, 8>(const SinrArgs&, cudaStream_t);
 extern template cudaError_t run_links<8, 8>(const SinrArgs&, bool, cudaStream_t);
 extern template cudaError_t run_finalize<8, 8>(const SinrArgs&, bool, cudaStream_t);
 extern template cudaError_t run_precoder<16, 4>(const SinrArgs&, cudaStream_t);
 extern template cudaError_t run_serving<16, 4>(const SinrArgs&, cudaStream_t);
+extern template cudaError_t run_rebuild<16, 4>(const SinrArgs&, cudaStream_t);
 extern template cudaError_t run_links<16, 4>(const SinrArgs&, bool, cudaStream_t);
 extern template cudaError_t run_finalize<16, 4>(const SinrArgs&, bool, cudaStream_t);
 extern template cudaError_t run_precoder<16, 8>(const SinrArgs&, cudaStream_t);
 extern template cudaError_t run_serving<16, 8>(const SinrArgs&, cudaStream_t);
+extern template cudaError_t run_rebuild<16, 8>(const SinrArgs&, cudaStream_t);
 extern template cudaError_t run_links<16, 8>(const SinrArgs&, bool, cudaStream_t);
 extern template cudaError_t run_finalize<16, 8>(const SinrArgs&, bool, cudaStream_t);
 extern template cudaError_t run_precoder<16, 16>(const SinrArgs&, cudaStream_t);
 extern template cudaError_t run_serving<16, 16>(const SinrArgs&, cudaStream_t);
+extern template cudaError_t run_rebuild<16, 16>(const SinrArgs&, cudaStream_t);
 extern template cudaError_t run_links<16, 16>(const SinrArgs&, bool, cudaStream_t);
 extern template cudaError_t run_finalize<16, 16>(const SinrArgs&, bool, cudaStream_t);
 
@@ -111,6 +120,7 @@ using detail::ltile;
 using detail::run_precoder;
 using detail::run_links;
 using detail::run_serving;
+using detail::run_rebuild;
 using detail::run_finalize;
 
 #define TS_DISPATCH(FN, ...)                                                        \
@@ -128,6 +138,8 @@ using detail::run_finalize;
 cudaError_t launch_svd_precoder(const SinrArgs& a, cudaStream_t s) { TS_DISPATCH(run_precoder, a, s); }
 
 cudaError_t launch_sinr_serving(const SinrArgs& a, cudaStream_t s) { TS_DISPATCH(run_serving, a, s); }
+
+cudaError_t launch_sinr_rebuild(const SinrArgs& a, cudaStream_t s) { TS_DISPATCH(run_rebuild, a, s); }
 
 cudaError_t launch_sinr_links(const SinrArgs& a, bool svd, cudaStream_t s) {
   TS_DISPATCH(run_links, a, svd, s);

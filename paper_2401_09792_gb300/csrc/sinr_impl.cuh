@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, con
     const int c = idx % n, aa = (idx / n) % MG, t = idx / (n * MG);
     const int kk = kap0 + t;
     float2 v = cz();
-    if (aa < m && kk < K) v = A.Hserv[(((size_t)k * K + kk) * m + aa) * n + c];
+    if (aa < m && kk < K) v = A.Hserv[(((size_t)k * A.serv_stride * K + kk) * m + aa) * n + c];
     sm[pl.off_Hs + (t * MG + aa) * pl.SH + c] = v;
   }
   __syncthreads();
@@ -386,6 +386,17 @@ __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, con
     if (a == 0)
       A.pflag[(size_t)k * K + kap] = (deficient ? TS_FLAG_RANK_DEFICIENT : 0) |
                                      ((converged || refined) ? 0 : TS_FLAG_EIG_UNCONVERGED);
+    if (A.Uout != nullptr && a < m) {
+      // the full SVD of H~_kk for the adjoint: lane a writes singular triplet a
+      const int ia = sel[a];
+      const float s2 = Ss[ia * pl.SS + ia].x;
+      const float sg = s2 > 0.f ? sqrtf(s2) : 0.f, isg = s2 > 0.f ? 1.f / sg : 0.f;
+      const size_t base = (size_t)k * K + kap;
+      A.Sout[base * m + a] = sg;
+      for (int b = 0; b < m; ++b) A.Uout[(base * m + b) * m + a] = Us[b * pl.SS + ia];
+      for (int c = 0; c < n; ++c)
+        A.Vmout[(base * n + c) * m + a] = cscale(cconj(Hs[ia * pl.SH + c]), isg);
+    }
   }
 }
 
@@ -438,6 +449,7 @@ __host__ __device__ inline LinkPlan link_plan(int MG, int LT, int T, int NC, int
 constexpr int kModeSvd = 0;     // interfering link, E = H~ V~ (SVD precoders)
 constexpr int kModeFold = 1;    // any link, E = sum_q w_q F[q] (wideband precoder)
 constexpr int kModeServe = 2;   // serving link of the SVD variant: write H~_kk rows
+constexpr int kModeRebuild = 3; // every link (adjoint): write H~_ik rows
 
 template <int MG, int LT, int NC, int MODE>
 __global__ void __launch_bounds__(kThreads) k_sinr_link(const SinrArgs A, const LinkPlan pl) {
@@ -453,7 +465,7 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link(const SinrArgs A, const 
   const int J = A.J, m = A.m, n = A.n, p = A.p, L = A.L, K = A.K, P = A.P;
   // svd: z enumerates the interfering links; fold: z is the BS index;
   // serve: the serving link
-  const int k = MODE == kModeSvd ? (z < i ? z : z + 1) : MODE == kModeFold ? z : i;
+  const int k = MODE == kModeSvd ? (z < i ? z : z + 1) : MODE == kModeServe ? i : z;
   const int ch = i * J + k;
   const int nchunk = CHUNKED ? (n + NC - 1) / NC : 1;
   float2* Cs = sm + pl.off_Cs;
@@ -545,6 +557,8 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link(const SinrArgs A, const 
   float2* Hrow = nullptr;
   if (MODE == kModeServe)
     Hrow = A.Hserv + (((size_t)i * K + (kap < K ? kap : 0)) * m + (a < m ? a : 0)) * n;
+  if (MODE == kModeRebuild)
+    Hrow = A.Hserv + (((size_t)ch * K + (kap < K ? kap : 0)) * m + (a < m ? a : 0)) * n;
   const bool hvalid = kap < K && a < m;
   if (CHUNKED) {
     for (int cidx = 0; cidx < nchunk; ++cidx) {
@@ -557,7 +571,7 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link(const SinrArgs A, const 
       const float2* buf = stage0 + (cidx & 1) * pl.stage;
       float2 h[NC];
       core_chunk<NC>(wrow, buf + pl.off_Gs, pl.SG, MG, a, p, h);
-      if (MODE == kModeServe) {
+      if (MODE == kModeServe || MODE == kModeRebuild) {
         const int c0 = cidx * NC;
         if (hvalid) {
 #pragma unroll
@@ -595,7 +609,7 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link(const SinrArgs A, const 
   }
   cp_async_wait<0>();
 
-  if (MODE == kModeServe || !hvalid) return;    // no shuffles or block barriers below
+  if (MODE == kModeServe || MODE == kModeRebuild || !hvalid) return;   // nothing below for them
   if (MODE == kModeFold && k == i) {
     // serving effective channel of the wideband-precoder variant
     float2* Eout = A.Eserv + (((size_t)i * K + kap) * m + a) * L;
@@ -617,6 +631,66 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link(const SinrArgs A, const 
     for (int l = 0; l < LT; ++l) cmacc(r, E[l], Es[b * LT + l]);
     Rout[b] = r;
   }
+}
+
+// SINR of one unit from row a of R = interference + noise (padding rows set
+// to the identity) and row a of E_ii, with the same arithmetic everywhere it
+// is needed (forward and adjoint).  With Q~ = R + E_ii E_ii* (eq. 25):
+//   a_r = e_r* Q~^{-1} e_r = |L_Q^{-1} e_r|^2   (as[r], every lane)
+//   x_r = [(I + Z*Z)^{-1}]_rr, Z = L_R^{-1} E_ii   (xs[r], every lane)
+// and SINR_r = a_r / x_r (eq. 5).  Returns Lq = chol(Q~) row a and
+// Zq = L_Q^{-1} E_ii row a; false if a factorisation failed.  R is destroyed
+// (it holds chol(R) on return); Es is the group's MG x LT shared scratch.
+template <int MG, int LT>
+__device__ __forceinline__ bool sinr_core(float2 (&R)[MG], const float2 (&Eself)[LT], float2* Es,
+                                          int a, float2 (&Lq)[MG], float2 (&Zq)[LT],
+                                          float (&as)[LT], float (&xs)[LT]) {
+  // Q~ = R + E_ii E_ii*
+#pragma unroll
+  for (int l = 0; l < LT; ++l) Es[a * LT + l] = Eself[l];
+  __syncwarp();
+#pragma unroll
+  for (int b = 0; b < MG; ++b) {
+    Lq[b] = R[b];
+#pragma unroll
+    for (int l = 0; l < LT; ++l) cmacc(Lq[b], Eself[l], Es[b * LT + l]);
+  }
+  __syncwarp();
+
+  bool ok = chol_rows<MG, MG>(R, a);
+  ok = chol_rows<MG, MG>(Lq, a) && ok;
+  float2 Z[LT];
+#pragma unroll
+  for (int l = 0; l < LT; ++l) Z[l] = Zq[l] = Eself[l];
+  trsv_rows<MG, MG, LT>(R, Z, a);
+  trsv_rows<MG, MG, LT>(Lq, Zq, a);
+
+#pragma unroll
+  for (int l = 0; l < LT; ++l) as[l] = gsum<MG>(cabs2(Zq[l]));
+
+  // F = I + Z*Z (LT x LT), one row per lane a < LT
+#pragma unroll
+  for (int l = 0; l < LT; ++l) Es[a * LT + l] = Z[l];
+  __syncwarp();
+  float2 F[LT];
+#pragma unroll
+  for (int s = 0; s < LT; ++s) F[s] = make_float2(s == a ? 1.f : 0.f, 0.f);
+  if (a < LT) {
+    for (int b = 0; b < MG; ++b) {
+      const float2 zba = cconj(Es[b * LT + a]);
+#pragma unroll
+      for (int s = 0; s < LT; ++s) cmac(F[s], zba, Es[b * LT + s]);
+    }
+  }
+  __syncwarp();
+  ok = chol_rows<MG, LT>(F, a) && ok;
+  float2 X[LT];
+#pragma unroll
+  for (int s = 0; s < LT; ++s) X[s] = make_float2(s == a ? 1.f : 0.f, 0.f);
+  trsv_rows<MG, LT, LT>(F, X, a);
+#pragma unroll
+  for (int s = 0; s < LT; ++s) xs[s] = gsum<MG>(a < LT ? cabs2(X[s]) : 0.f);
+  return ok;
 }
 
 // k_sinr_finalize: one group of MG lanes per (UE i, subcarrier): sums the
@@ -653,55 +727,9 @@ __global__ void __launch_bounds__(kThreads) k_sinr_finalize(const SinrArgs A, in
 
   // noise on the m x m block, identity on the padding rows (eq. 25)
   add_diag(R, a, a < m ? A.sigma2[i] : 1.f);
-  // Q~ = R + E_ii E_ii*
-  float2 Q[MG];
-#pragma unroll
-  for (int l = 0; l < LT; ++l) Es[a * LT + l] = Eself[l];
-  __syncwarp();
-#pragma unroll
-  for (int b = 0; b < MG; ++b) {
-    Q[b] = R[b];
-#pragma unroll
-    for (int l = 0; l < LT; ++l) cmacc(Q[b], Eself[l], Es[b * LT + l]);
-  }
-  __syncwarp();
-
-  bool ok = chol_rows<MG, MG>(R, a);
-  ok = chol_rows<MG, MG>(Q, a) && ok;
-  float2 Z[LT], Y[LT];
-#pragma unroll
-  for (int l = 0; l < LT; ++l) Z[l] = Y[l] = Eself[l];
-  trsv_rows<MG, MG, LT>(R, Z, a);
-  trsv_rows<MG, MG, LT>(Q, Y, a);
-
-  // a_r = |L_Q^{-1} e_r|^2
-  float as[LT];
-#pragma unroll
-  for (int l = 0; l < LT; ++l) as[l] = gsum<MG>(cabs2(Y[l]));
-
-  // F = I + Z*Z (LT x LT), one row per lane a < LT
-#pragma unroll
-  for (int l = 0; l < LT; ++l) Es[a * LT + l] = Z[l];
-  __syncwarp();
-  float2 F[LT];
-#pragma unroll
-  for (int s = 0; s < LT; ++s) F[s] = make_float2(s == a ? 1.f : 0.f, 0.f);
-  if (a < LT) {
-    for (int b = 0; b < MG; ++b) {
-      const float2 zba = cconj(Es[b * LT + a]);
-#pragma unroll
-      for (int s = 0; s < LT; ++s) cmac(F[s], zba, Es[b * LT + s]);
-    }
-  }
-  __syncwarp();
-  ok = chol_rows<MG, LT>(F, a) && ok;
-  float2 X[LT];
-#pragma unroll
-  for (int s = 0; s < LT; ++s) X[s] = make_float2(s == a ? 1.f : 0.f, 0.f);
-  trsv_rows<MG, LT, LT>(F, X, a);
-  float xs[LT];
-#pragma unroll
-  for (int s = 0; s < LT; ++s) xs[s] = gsum<MG>(a < LT ? cabs2(X[s]) : 0.f);
+  float2 Lq[MG], Zq[LT];
+  float as[LT], xs[LT];
+  const bool ok = sinr_core<MG, LT>(R, Eself, Es, a, Lq, Zq, as, xs);
 
   if (kap < K) {
     const float num = pickf(as, a), den = pickf(xs, a);
@@ -769,6 +797,12 @@ cudaError_t run_links(const SinrArgs& A, bool svd, cudaStream_t s) {
 template <int MG, int LT>
 cudaError_t run_serving(const SinrArgs& A, cudaStream_t s) {
   return launch_link_mode<MG, LT, kModeServe>(A, 1, s);
+}
+
+// adjoint: rebuild every link's compressed channel H~_ik into workspace
+template <int MG, int LT>
+cudaError_t run_rebuild(const SinrArgs& A, cudaStream_t s) {
+  return launch_link_mode<MG, LT, kModeRebuild>(A, A.J, s);
 }
 
 template <int MG, int LT>

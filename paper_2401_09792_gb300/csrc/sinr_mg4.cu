@@ -5,10 +5,12 @@ namespace ts {
 namespace detail {
 template cudaError_t run_precoder<4, 2>(const SinrArgs&, cudaStream_t);
 template cudaError_t run_serving<4, 2>(const SinrArgs&, cudaStream_t);
+template cudaError_t run_rebuild<4, 2>(const SinrArgs&, cudaStream_t);
 template cudaError_t run_links<4, 2>(const SinrArgs&, bool, cudaStream_t);
 template cudaError_t run_finalize<4, 2>(const SinrArgs&, bool, cudaStream_t);
 template cudaError_t run_precoder<4, 4>(const SinrArgs&, cudaStream_t);
 template cudaError_t run_serving<4, 4>(const SinrArgs&, cudaStream_t);
+template cudaError_t run_rebuild<4, 4>(const SinrArgs&, cudaStream_t);
 template cudaError_t run_links<4, 4>(const SinrArgs&, bool, cudaStream_t);
 template cudaError_t run_finalize<4, 4>(const SinrArgs&, bool, cudaStream_t);
 }  // namespace detail
