@@ -93,7 +93,8 @@ enum {
   TS_OP_DENSE_SVD = 2,
   TS_OP_DENSE_MMSE = 3,
   TS_OP_SINR_SVD_ADJOINT = 4,
-  TS_OP_SINR_MMSE_ADJOINT = 5
+  TS_OP_SINR_MMSE_ADJOINT = 5,
+  TS_OP_TUCKER_FIT = 6
 };
 
 /* Human-readable name of a status code (static storage). */
@@ -184,6 +185,23 @@ int ts_dense_sinr_svd(const ts_dims* d, const ts_coef* coef, const ts_c64* X,
 int ts_dense_sinr_mmse(const ts_dims* d, const ts_coef* coef, const ts_c64* X,
                        const ts_c64* Pfull, const float* sigma2, float* sinr,
                        uint8_t* flags, void* ws, size_t ws_bytes, void* stream);
+
+/* Groupwise Tucker compression (Section 3.2, eq. 16-22, Algorithm 2), FP64
+ * inside: initialisation from the mode Grams of X (eq. 20-22 with the other
+ * factors set to the identity; init = 0) or from the factors given in A, B,
+ * C (init = 1, e.g. to resume), then S Gauss-Seidel sweeps -- all A_i
+ * (eq. 20), then all B_k (eq. 21), then all C_ik (eq. 22), each the leading
+ * eigenvectors of a summed mode Gram -- and the core (eq. 17) once at the
+ * end.  Eigensolvers: cyclic Jacobi for Gram dimensions <= 72, block subspace
+ * iteration with a Rayleigh-Ritz step above that.
+ * X: [J*J][P][M][N] (link i*J+k, submatrices of eq. 2 stacked on mode 3);
+ * A (out, or in for init = 1): [J][M][m]; B: [J][N][n]; C: [J*J][P][p];
+ * G (out): [J*J][p][m][n]; g_hist (device, may be NULL): 3 S + 1 doubles,
+ * the objective g of eq. (19) after the initialisation and after every block
+ * update.  Ranks up to 64.  ws: ts_workspace_bytes(d, TS_OP_TUCKER_FIT). */
+int ts_tucker_fit(const ts_dims* d, const ts_c64* X, int S, int init, ts_c64* A,
+                  ts_c64* B, ts_c64* C, ts_c64* G, double* g_hist, void* ws,
+                  size_t ws_bytes, void* stream);
 
 /* Adjoints (vector-Jacobian products) of the compressed SINR.  The paper has
  * no adjoint; these differentiate its compressed SINR (eq. 15, 23-28) for a

@@ -113,6 +113,20 @@ AdjWorkspace carve_adjoint(const ts_dims* d, bool svd) {
   return w;
 }
 
+ts::FitDims fit_dims(const ts_dims* d) {
+  return ts::FitDims{d->J, d->M, d->N, d->P, d->m, d->n, d->p};
+}
+
+// Sizes the fit accepts: ranks up to 64 (eigensolver block limit).
+int fit_checks(const ts_dims* d) {
+  if (d == nullptr) return TS_ERR_NULL;
+  if (d->J < 1 || d->M < 1 || d->N < 1 || d->P < 1) return TS_ERR_DIMS;
+  if (d->m < 1 || d->n < 1 || d->p < 1 || d->m > d->M || d->n > d->N || d->p > d->P) return TS_ERR_DIMS;
+  if (d->m > 64 || d->n > 64 || d->p > 64) return TS_ERR_DIMS;
+  if (d->M > 4096 || d->N > 4096 || d->P > 4096 || d->J > 256) return TS_ERR_DIMS;
+  return TS_OK;
+}
+
 int check_coef(const ts_coef* c) {
   if (c == nullptr) return TS_ERR_NULL;
   if (c->mode == TS_COEF_DENSE) {
@@ -187,6 +201,7 @@ size_t ts_workspace_bytes(const ts_dims* d, int op) {
     return carve(&e, op == TS_OP_DENSE_SVD ? TS_OP_SINR_SVD : TS_OP_SINR_MMSE).total;
   }
   if (check_dims(d) != TS_OK) return 0;
+  if (op == TS_OP_TUCKER_FIT) return fit_checks(d) == TS_OK ? ts::fit_workspace_bytes(fit_dims(d)) : 0;
   if (op == TS_OP_SINR_SVD_ADJOINT || op == TS_OP_SINR_MMSE_ADJOINT)
     return carve_adjoint(d, op == TS_OP_SINR_SVD_ADJOINT).total;
   if (op != TS_OP_SINR_SVD && op != TS_OP_SINR_MMSE) return 0;
@@ -295,6 +310,23 @@ int ts_sinr_mmse_adjoint(const ts_dims* d, const ts_coef* coef, const ts_c64* G,
                          void* stream) {
   if (Pt == nullptr) return TS_ERR_NULL;
   return adjoint_impl(d, coef, G, C, Pt, sigma2, dsinr, dG, dC, dPt, sinr, ws, ws_bytes, stream);
+}
+
+int ts_tucker_fit(const ts_dims* d, const ts_c64* X, int S, int init, ts_c64* A, ts_c64* B,
+                  ts_c64* C, ts_c64* G, double* g_hist, void* ws, size_t ws_bytes, void* stream) {
+  int st = fit_checks(d);
+  if (st != TS_OK) return st;
+  if (S < 0 || (init != 0 && init != 1)) return TS_ERR_MODE;
+  if (X == nullptr || A == nullptr || B == nullptr || C == nullptr || G == nullptr) return TS_ERR_NULL;
+  if (!aligned8(X) || !aligned8(A) || !aligned8(B) || !aligned8(C) || !aligned8(G) || !aligned8(g_hist))
+    return TS_ERR_ALIGN;
+  const ts::FitDims f = fit_dims(d);
+  if (ws == nullptr || ws_bytes < ts::fit_workspace_bytes(f)) return TS_ERR_WORKSPACE;
+  if (((uintptr_t)ws & 255u) != 0) return TS_ERR_ALIGN;
+  return cuda_status(ts::launch_fit(f, reinterpret_cast<const float2*>(X), S, init,
+                                    reinterpret_cast<float2*>(A), reinterpret_cast<float2*>(B),
+                                    reinterpret_cast<float2*>(C), reinterpret_cast<float2*>(G),
+                                    g_hist, ws, static_cast<cudaStream_t>(stream)));
 }
 
 int ts_project_precoder_adjoint(const ts_dims* d, const ts_c64* Pfull, const ts_c64* dPt,

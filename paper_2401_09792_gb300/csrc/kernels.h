@@ -68,6 +68,14 @@ cudaError_t launch_adjoint(const SinrArgs& a, const AdjointWork& w, cudaStream_t
 cudaError_t launch_project_precoder_adjoint(const float2* Pfull, const float2* dPt, int J, int N,
                                             int n, int L, float2* dB, cudaStream_t s);
 
+// Groupwise Tucker fit (fit.cu).
+struct FitDims {
+  int J, M, N, P, m, n, p;
+};
+size_t fit_workspace_bytes(const FitDims& f);
+cudaError_t launch_fit(const FitDims& f, const float2* X, int S, int init, float2* A, float2* B,
+                       float2* C, float2* G, double* g_hist, void* ws, cudaStream_t s);
+
 // Store a CUDA error for ts_last_cuda_error() and return TS_ERR_CUDA.
 int record_cuda_error(cudaError_t e);
 

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_PKG, "libtuckersinr.so")
 
 TS_COEF_DENSE, TS_COEF_PATHS = 0, 1
 TS_OP_SINR_SVD, TS_OP_SINR_MMSE, TS_OP_DENSE_SVD, TS_OP_DENSE_MMSE = 0, 1, 2, 3
-TS_OP_SINR_SVD_ADJOINT, TS_OP_SINR_MMSE_ADJOINT = 4, 5
+TS_OP_SINR_SVD_ADJOINT, TS_OP_SINR_MMSE_ADJOINT, TS_OP_TUCKER_FIT = 4, 5, 6
 TS_FLAG_NOT_PD, TS_FLAG_NONFINITE, TS_FLAG_RANK_DEFICIENT, TS_FLAG_EIG_UNCONVERGED = 1, 2, 4, 8
 
 
@@ -65,6 +65,8 @@ _SIG = {
                                          _P, _P, _P, ctypes.c_size_t, _P]),
     "ts_dense_sinr_mmse": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.POINTER(ts_coef), _P, _P,
                                           _P, _P, _P, _P, ctypes.c_size_t, _P]),
+    "ts_tucker_fit": (ctypes.c_int, [ctypes.POINTER(ts_dims), _P, ctypes.c_int, ctypes.c_int, _P, _P,
+                                     _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "ts_sinr_svd_adjoint": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.POINTER(ts_coef), _P, _P,
                                            _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "ts_sinr_mmse_adjoint": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.POINTER(ts_coef), _P, _P,
@@ -191,6 +193,13 @@ def ts_sinr_svd(d: Dims, coef: ts_coef, G, C, sigma2, sinr, flags, ws, stream=No
     _check("ts_sinr_svd", lib.ts_sinr_svd(ctypes.byref(d.c()), ctypes.byref(coef), _ptr(G), _ptr(C),
                                           _ptr(sigma2), _ptr(sinr), _ptr(flags), _ptr(ws),
                                           ws.numel(), _stream(stream)))
+
+
+def ts_tucker_fit(d: Dims, X, S, init, A, B, C, G, g_hist, ws, stream=None):
+    lib = load()
+    _check("ts_tucker_fit", lib.ts_tucker_fit(ctypes.byref(d.c()), _ptr(X), S, init, _ptr(A), _ptr(B),
+                                              _ptr(C), _ptr(G), _ptr(g_hist), _ptr(ws), ws.numel(),
+                                              _stream(stream)))
 
 
 def ts_sinr_svd_adjoint(d: Dims, coef: ts_coef, G, C, sigma2, dsinr, dG, dC, sinr, ws, stream=None):

@@ -1,0 +1,82 @@
+"""Parity of the CUDA groupwise Tucker fit (Algorithm 2, through the C ABI)
+with the FP64 oracle's fit on the same (complex64-rounded) channels.
+
+Compared: the objective g of eq. (19) after the initialisation and after every
+block update (relative 1e-8 where every Gram is solved by Jacobi, 1e-6 where
+the N x N Gram goes through subspace iteration), the factor subspaces
+(projectors A A*, B B*, C C*), orthonormality, and the reconstruction
+identity f = ||X||^2 - ||G||^2 (eq. 18) of the returned core.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import tucker as T  # noqa: E402
+from paper_2401_09792_gb300 import synth  # noqa: E402
+from paper_2401_09792_gb300 import tuckersinr as ts  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    assert torch.cuda.is_available()
+
+
+def _gpu_fit(X, ranks, S):
+    J, _, M, N, P = X.shape
+    m, n, p = ranks
+    d = ts.Dims(J, M, N, P, m, n, p, 1, 1)
+    Xd = ts.channels_to_device(X)
+    A = torch.empty(J, M, m, dtype=torch.complex64, device="cuda")
+    B = torch.empty(J, N, n, dtype=torch.complex64, device="cuda")
+    C = torch.empty(J * J, P, p, dtype=torch.complex64, device="cuda")
+    G = torch.empty(J * J, p, m, n, dtype=torch.complex64, device="cuda")
+    g = torch.empty(3 * S + 1, dtype=torch.float64, device="cuda")
+    ws = ts.workspace(d, ts.TS_OP_TUCKER_FIT)
+    ts.ts_tucker_fit(d, Xd, S, 0, A, B, C, G, g, ws)
+    torch.cuda.synchronize()
+    c = lambda t: t.cpu().numpy().astype(np.complex128)  # noqa: E731
+    Gh = np.transpose(c(G).reshape(J, J, p, m, n), (0, 1, 3, 4, 2))
+    return c(A), c(B), c(C).reshape(J, J, P, p), Gh, g.cpu().numpy()
+
+
+def _check(w, S, gtol):
+    X = synth.channel_submatrices(w).astype(np.complex64).astype(np.complex128)
+    ranks = (w.m, w.n, w.p)
+    ref = T.fit_groupwise(X, ranks, S=S, history=True)
+    A, B, C, G, g = _gpu_fit(X, ranks, S)
+    np.testing.assert_allclose(g, ref["g"], rtol=gtol)
+    J = w.J
+    proj = lambda F: F @ np.conj(np.swapaxes(F, -1, -2))  # noqa: E731
+    for got, want, r in ((A, ref["A"], w.m), (B, ref["B"], w.n), (C, ref["C"], w.p)):
+        assert np.max(np.abs(proj(got) - proj(want))) < 1e-4
+        eye = np.conj(np.swapaxes(got, -1, -2)) @ got
+        assert np.max(np.abs(eye - np.eye(r))) < 1e-5
+    f = T.objective_f(X, A, B, C, G)
+    gG = sum(T.fro2(G[i, k]) for i in range(J) for k in range(J))
+    assert abs(f - (T.fro2(X) - gG)) < 1e-5 * T.fro2(X)
+    assert abs(gG - ref["g"][-1]) < 1e-5 * ref["g"][-1]
+
+
+def test_fit_small_workload():
+    # every Gram <= 72 x 72: Jacobi throughout
+    _check(synth.SMALL, S=3, gtol=1e-8)
+
+
+def test_fit_large_transmit_dimension():
+    # N = 256: the B Grams go through block subspace iteration
+    w = dataclasses.replace(synth.MID, J=2, P=16, m=8, n=16, p=8)
+    _check(w, S=2, gtol=1e-6)
+
+
+def test_fit_full_rank_reconstructs():
+    w = dataclasses.replace(synth.SMALL, J=2, M=3, N=5, P=4, m=3, n=5, p=4)
+    X = synth.channel_submatrices(w).astype(np.complex64).astype(np.complex128)
+    A, B, C, G, g = _gpu_fit(X, (3, 5, 4), 1)
+    f = T.objective_f(X, A, B, C, G)
+    assert f < 1e-9 * T.fro2(X)
