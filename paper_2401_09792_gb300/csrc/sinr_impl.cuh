@@ -56,6 +56,14 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool val
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(nbytes)
                : "memory");
 }
+// 16-byte asynchronous copy (both addresses 16-byte aligned); `valid ==
+// false` writes zeros and reads nothing.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  const int nbytes = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(nbytes)
+               : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
@@ -409,7 +417,7 @@ __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, con
 // form, two stage buffers (core chunk or wideband fold, precoder chunk), the
 // projection ws; the per-group scratch Es reuses the stage buffers.
 struct LinkPlan {
-  int T, NC, SG, SV, SF, ES, wstride;
+  int T, NC, SG, SV, SF, ES, wstride, wide;
   int off_Cs, off_cs, off_pa, off_pt, off_ws, off_stage, stage, off_Gs, off_Vs, off_Es, total;
 };
 
@@ -423,6 +431,7 @@ __host__ __device__ inline LinkPlan link_plan(int MG, int LT, int T, int NC, int
   pl.SF = LT + 2;
   pl.ES = MG * LT + 2;
   pl.wstride = p + 1;
+  pl.wide = 0;
   int o = 0;
   pl.off_Cs = o; o += P * p;
   pl.off_cs = o; o += T * P;
@@ -474,10 +483,38 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link(const SinrArgs A, const 
   float2* stage0 = sm + pl.off_stage;
   const float2* wrow = ws + g * pl.wstride;
 
+  // Staging of one column chunk: G_ik[:, 0..m, c0 .. c0+NC) and (svd) the
+  // precoder rows V_k(kappa)[c0 .. c0+NC][0..L) of the tile.  With even n and
+  // L (and 16-byte aligned arrays) the copies move complex pairs; each thread
+  // walks fixed positions with constant strides.
+  const bool wide = pl.wide != 0;
   auto issue_chunk = [&](int cidx) {
     float2* buf = stage0 + (cidx & 1) * pl.stage;
     const int c0 = cidx * NC;
     const float2* Gch = A.G + (size_t)ch * p * m * n;
+    if (wide) {
+      constexpr int GU = MG * NC / 2;                 // 16-byte units per q slab
+      const int cc = 2 * (tid % (NC / 2)), aa = (tid / (NC / 2)) % MG;
+      const bool rowok = aa < m && c0 + cc < n;
+      const float2* src = Gch + ((size_t)(tid / GU) * m + aa) * n + c0 + cc;
+      float2* dst = buf + pl.off_Gs + ((tid / GU) * MG + aa) * pl.SG + cc;
+      const size_t sstep = (size_t)(kThreads / GU) * m * n;
+      const int dstep = (kThreads / GU) * MG * pl.SG;
+      for (int q = tid / GU; q < p; q += kThreads / GU, src += sstep, dst += dstep)
+        cp_async16(dst, rowok ? src : A.G, rowok);
+      if (MODE == kModeSvd) {
+        constexpr int VU = NC * LT / 2;               // 16-byte units per subcarrier
+        const int l = 2 * (tid % (LT / 2)), vc = (tid / (LT / 2)) % NC;
+        const int t0 = tid / VU;
+        const bool colok = c0 + vc < n && l < L;
+        for (int t = t0; t < T; t += kThreads / VU) {
+          const bool ok = colok && kap0 + t < K;
+          cp_async16(buf + pl.off_Vs + t * pl.SV + vc * LT + l,
+                     ok ? A.V + (((size_t)k * K + kap0 + t) * n + c0 + vc) * L + l : A.V, ok);
+        }
+      }
+      return;
+    }
     for (int idx = tid; idx < p * MG * NC; idx += nth) {
       const int cc = idx % NC, aa = (idx / NC) % MG, q = idx / (NC * MG);
       const int c = c0 + cc;
@@ -778,6 +815,10 @@ cudaError_t launch_link_mode(const SinrArgs& A, int nz, cudaStream_t s) {
   }
   const size_t smem = (size_t)pl.total * sizeof(float2);
   if (smem > kSmemBudget) return cudaErrorInvalidValue;
+  // pairwise (16-byte) staging needs even n and L, 16-byte aligned G and V and
+  // a full 128-thread CTA
+  pl.wide = (A.n % 2 == 0) && (A.L % 2 == 0) && LT >= 2 && (T * MG == kThreads) &&
+            (((uintptr_t)A.G & 15u) == 0) && (((uintptr_t)A.V & 15u) == 0);
   dim3 grid((A.K + T - 1) / T, A.J, nz);
   auto kern = k_sinr_link<MG, LT, NC, MODE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
