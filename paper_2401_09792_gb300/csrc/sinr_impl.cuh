@@ -233,11 +233,10 @@ __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, con
     }
   }
 
-  // Cyclic Jacobi on S held in registers (see jacobi_step): the eigenvectors
-  // only precondition the one-sided sweeps below, so the two-sided stage stops
-  // at a relative off-diagonal norm of 1e-3.  The stopping decision is taken
-  // warp-wide (extra sweeps leave a converged S unchanged).
-  const int max_sweeps = MG <= 8 ? 8 : 10;
+  // Cyclic Jacobi on S held in registers (see jacobi_step), to FP32
+  // convergence (relative off-diagonal norm ~5e-7).  The stopping decision is
+  // taken warp-wide (extra sweeps leave a converged S unchanged).
+  const int max_sweeps = MG <= 8 ? 10 : 12;
   bool converged = false;
   for (int sweep = 0;; ++sweep) {
     float off = 0.f, dia = 0.f;
@@ -248,10 +247,29 @@ __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, con
     }
     off = gsum<MG>(off);
     dia = gsum<MG>(dia);
-    converged = off <= 1e-6f * dia;
+    converged = off <= 2.3e-13f * dia;
     if (__all_sync(FULL, converged) || sweep == max_sweeps) break;
 #pragma unroll
     for (int t = 0; t < MG - 1; ++t) jacobi_step<MG>(t, S, U, a);
+  }
+  // The eigenvectors of the Gram are accurate unless a kept singular value is
+  // small: refine with one-sided sweeps (below) when lambda_L < 1e-4 lambda_1
+  // in any group of the warp.
+  bool need_refine;
+  {
+    const float lam = (a < m) ? pick(S, a).x : -INFINITY;
+    float lmax = lam;
+#pragma unroll
+    for (int o = 1; o < MG; o <<= 1) lmax = fmaxf(lmax, __shfl_xor_sync(FULL, lmax, o, MG));
+    // rank of this lane's eigenvalue; the L-th largest decides
+    int rank = 0;
+#pragma unroll
+    for (int b = 0; b < MG; ++b) {
+      const float lb = __shfl_sync(FULL, lam, b, MG);
+      rank += (lb > lam) || (lb == lam && b < a);
+    }
+    const bool small_kept = (a < m) && (rank < L) && !(lam >= 1e-4f * lmax);
+    need_refine = __any_sync(FULL, small_kept);
   }
 #pragma unroll
   for (int b = 0; b < MG; ++b) Us[a * pl.SS + b] = U[b];
@@ -285,13 +303,13 @@ __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, con
   // lanes per pair, each on half of the columns of W and half of the rows of
   // U.  Sweeps repeat (at most 3) until every pair is orthogonal to 1e-6
   // relative, decided warp-wide.
-  bool refined = false;
+  bool refined = !need_refine;
   {
     const int j = a >> 1, half = a & 1;
     const int nh = (n + 1) >> 1;
     const int c_lo = half * nh, c_hi = min(n, c_lo + nh);
     const int r_lo = half * (MG / 2), r_hi = r_lo + MG / 2;
-    for (int sweep = 0; sweep < 3; ++sweep) {
+    for (int sweep = 0; sweep < (need_refine ? 3 : 0); ++sweep) {
       float worst = 0.f;
 #pragma unroll 1
       for (int step = 0; step < MG - 1; ++step) {
