@@ -748,6 +748,229 @@ __device__ __forceinline__ bool sinr_core(float2 (&R)[MG], const float2 (&Eself)
   return ok;
 }
 
+// Blocked variant of the interfering-link SVD pass (k_sinr_link, svd mode),
+// for MG >= 4.  A group of GL = MG/2 lanes evaluates two subcarriers and lane
+// j owns rows j and j + GL of both, so every core element read from shared
+// memory feeds two subcarriers and every precoder element two rows (a 128-bit
+// shared load costs four wavefronts per warp whether or not lanes share
+// addresses, so reuse has to happen in registers).  128 threads, T = 512/MG
+// subcarriers per CTA, column chunks of NC = 4.  Path-form coefficients are
+// evaluated inside the projection, so only dense coefficients are staged.
+template <int MG, int LT>
+__global__ void __launch_bounds__(kThreads) k_sinr_link_blk(const SinrArgs A, const LinkPlan pl) {
+  constexpr int NC = 4;
+  constexpr int GL = MG / 2;
+  constexpr int T = 2 * kThreads / GL;
+  constexpr int QS = kThreads / T;          // threads per subcarrier in the projection
+  constexpr int QA = 32 / QS;               // projection accumulators per thread (p <= 32)
+  extern __shared__ __align__(16) float2 sm[];
+  const int tid = threadIdx.x;
+  const int gp = tid / GL, j = tid % GL;
+  const int i = blockIdx.y, z = blockIdx.z;
+  const int kap0 = blockIdx.x * T;
+  const int J = A.J, m = A.m, n = A.n, p = A.p, L = A.L, K = A.K, P = A.P;
+  const int k = z < i ? z : z + 1;
+  const int ch = i * J + k;
+  const int nchunk = (n + NC - 1) / NC;
+  float2* Cs = sm + pl.off_Cs;
+  float2* cs = sm + pl.off_cs;
+  float2* ws = sm + pl.off_ws;
+  float2* stage0 = sm + pl.off_stage;
+  const bool wide = pl.wide != 0;
+
+  auto issue_chunk = [&](int cidx) {
+    float2* buf = stage0 + (cidx & 1) * pl.stage;
+    const int c0 = cidx * NC;
+    const float2* Gch = A.G + (size_t)ch * p * m * n;
+    if (wide) {
+      constexpr int GU = MG * NC / 2;
+      const int cc = 2 * (tid % (NC / 2)), aa = (tid / (NC / 2)) % MG;
+      const bool rowok = aa < m && c0 + cc < n;
+      const float2* src = Gch + ((size_t)(tid / GU) * m + aa) * n + c0 + cc;
+      float2* dst = buf + pl.off_Gs + ((tid / GU) * MG + aa) * pl.SG + cc;
+      const size_t sstep = (size_t)(kThreads / GU) * m * n;
+      const int dstep = (kThreads / GU) * MG * pl.SG;
+      for (int q = tid / GU; q < p; q += kThreads / GU, src += sstep, dst += dstep)
+        cp_async16(dst, rowok ? src : A.G, rowok);
+      constexpr int VU = NC * LT / 2;
+      const int l = 2 * (tid % (LT / 2)), vc = (tid / (LT / 2)) % NC;
+      const bool colok = c0 + vc < n && l < L;
+      for (int t = tid / VU; t < T; t += kThreads / VU) {
+        const bool ok = colok && kap0 + t < K;
+        cp_async16(buf + pl.off_Vs + t * pl.SV + vc * LT + l,
+                   ok ? A.V + (((size_t)k * K + kap0 + t) * n + c0 + vc) * L + l : A.V, ok);
+      }
+      return;
+    }
+    for (int idx = tid; idx < p * MG * NC; idx += kThreads) {
+      const int cc = idx % NC, aa = (idx / NC) % MG, q = idx / (NC * MG);
+      const int c = c0 + cc;
+      const bool ok = aa < m && c < n;
+      cp_async8(buf + pl.off_Gs + (q * MG + aa) * pl.SG + cc,
+                ok ? Gch + ((size_t)q * m + aa) * n + c : A.G, ok);
+    }
+    for (int idx = tid; idx < T * NC * LT; idx += kThreads) {
+      const int l = idx % LT, cc = (idx / LT) % NC, t = idx / (LT * NC);
+      const int kk2 = kap0 + t, c = c0 + cc;
+      const bool ok = kk2 < K && c < n && l < L;
+      cp_async8(buf + pl.off_Vs + t * pl.SV + cc * LT + l,
+                ok ? A.V + (((size_t)k * K + kk2) * n + c) * L + l : A.V, ok);
+    }
+  };
+
+  // group 0: C_ik, the coefficients (dense tile, or the path form) and chunk 0
+  if (!A.identity_C)
+    for (int idx = tid; idx < P * p; idx += kThreads)
+      cp_async8(Cs + idx, A.C + (size_t)ch * P * p + idx, true);
+  if (A.coef_mode == 0) {
+    for (int idx = tid; idx < T * P; idx += kThreads) {
+      const int t = idx / P, pp = idx - t * P;
+      const bool ok = kap0 + t < K;
+      cp_async8(cs + idx, ok ? A.coef + ((size_t)ch * K + kap0 + t) * P + pp : A.coef, ok);
+    }
+  } else {
+    for (int idx = tid; idx < P; idx += kThreads) {
+      cp_async8(sm + pl.off_pa + idx, A.coef + (size_t)ch * P + idx, true);
+      cp_async8(sm + pl.off_pt + idx, A.turns + (size_t)ch * P + idx, true);
+    }
+  }
+  issue_chunk(0);
+  cp_async_commit();
+  if (nchunk > 1) issue_chunk(1);
+  cp_async_commit();
+  cp_async_wait<1>();
+  __syncthreads();
+
+  // projection w[t][q] = sum_P C[P][q] conj(c_P(kappa_t)) (eq. 15): QS threads
+  // per subcarrier, thread qs handles q = qs, qs + QS, ...
+  {
+    const int t = tid / QS, qs = tid % QS;
+    const int kap_t = kap0 + t;
+    float2 acc[QA];
+#pragma unroll
+    for (int u = 0; u < QA; ++u) acc[u] = cz();
+    const float2* pa = sm + pl.off_pa;
+    const unsigned long long* pt = reinterpret_cast<const unsigned long long*>(sm + pl.off_pt);
+    for (int pp = 0; pp < P; ++pp) {
+      float2 c = cz();
+      if (kap_t < K)
+        c = A.coef_mode == 0 ? cs[t * P + pp] : path_coef(pa[pp], pt[pp], kap_t);
+      if (A.identity_C) {
+#pragma unroll
+        for (int u = 0; u < QA; ++u)
+          if (qs + u * QS == pp) acc[u] = cconj(c);
+      } else {
+        const float2* crow = Cs + pp * p;
+#pragma unroll
+        for (int u = 0; u < QA; ++u)
+          if (qs + u * QS < p) cmacc(acc[u], crow[qs + u * QS], c);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < QA; ++u)
+      if (qs + u * QS < p) ws[t * pl.wstride + qs + u * QS] = acc[u];
+  }
+  __syncthreads();
+
+  float2 E[2][2][LT];   // [subcarrier of the pair][row j, j + GL][stream]
+#pragma unroll
+  for (int x = 0; x < 2; ++x)
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int l = 0; l < LT; ++l) E[x][r][l] = cz();
+  const float2* w0 = ws + (2 * gp) * pl.wstride;
+  const float2* w1 = w0 + pl.wstride;
+  for (int cidx = 0; cidx < nchunk; ++cidx) {
+    if (cidx > 0) {
+      if (cidx + 1 < nchunk) issue_chunk(cidx + 1);
+      cp_async_commit();
+      cp_async_wait<1>();
+      __syncthreads();
+    }
+    const float2* buf = stage0 + (cidx & 1) * pl.stage;
+    float2 h[2][2][NC];
+#pragma unroll
+    for (int x = 0; x < 2; ++x)
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int cc = 0; cc < NC; ++cc) h[x][r][cc] = cz();
+    const float2* g0 = buf + pl.off_Gs + j * pl.SG;
+    const float2* g1 = g0 + GL * pl.SG;
+#pragma unroll 4
+    for (int q = 0; q < p; ++q) {
+      const float2 wa = w0[q], wb = w1[q];
+      const float4* ga = reinterpret_cast<const float4*>(g0 + q * MG * pl.SG);
+      const float4* gb = reinterpret_cast<const float4*>(g1 + q * MG * pl.SG);
+#pragma unroll
+      for (int c2 = 0; c2 < NC / 2; ++c2) {
+        const float4 u = ga[c2], v = gb[c2];
+        const float2 u0 = make_float2(u.x, u.y), u1 = make_float2(u.z, u.w);
+        const float2 v0 = make_float2(v.x, v.y), v1 = make_float2(v.z, v.w);
+        cmac(h[0][0][2 * c2], wa, u0);
+        cmac(h[0][0][2 * c2 + 1], wa, u1);
+        cmac(h[1][0][2 * c2], wb, u0);
+        cmac(h[1][0][2 * c2 + 1], wb, u1);
+        cmac(h[0][1][2 * c2], wa, v0);
+        cmac(h[0][1][2 * c2 + 1], wa, v1);
+        cmac(h[1][1][2 * c2], wb, v0);
+        cmac(h[1][1][2 * c2 + 1], wb, v1);
+      }
+    }
+    const float2* va = buf + pl.off_Vs + (2 * gp) * pl.SV;
+    const float2* vb = va + pl.SV;
+#pragma unroll
+    for (int cc = 0; cc < NC; ++cc) {
+#pragma unroll
+      for (int l2 = 0; l2 < LT / 2; ++l2) {
+        const float4 x = reinterpret_cast<const float4*>(va + cc * LT)[l2];
+        const float4 y = reinterpret_cast<const float4*>(vb + cc * LT)[l2];
+        const float2 x0 = make_float2(x.x, x.y), x1 = make_float2(x.z, x.w);
+        const float2 y0 = make_float2(y.x, y.y), y1 = make_float2(y.z, y.w);
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          cmac(E[0][r][2 * l2], h[0][r][cc], x0);
+          cmac(E[0][r][2 * l2 + 1], h[0][r][cc], x1);
+          cmac(E[1][r][2 * l2], h[1][r][cc], y0);
+          cmac(E[1][r][2 * l2 + 1], h[1][r][cc], y1);
+        }
+      }
+    }
+    __syncthreads();   // this buffer is refilled two chunks later
+  }
+  cp_async_wait<0>();
+
+  // partial covariance rows (E E*)[a][b], b < m (eq. 25), for both subcarriers;
+  // the group's scratch reuses the stage buffers
+  float2* Es = stage0 + gp * (2 * MG * LT + 2);
+#pragma unroll
+  for (int x = 0; x < 2; ++x)
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int l = 0; l < LT; ++l) Es[(x * MG + j + r * GL) * LT + l] = E[x][r][l];
+  __syncwarp();
+#pragma unroll
+  for (int x = 0; x < 2; ++x) {
+    const int kap = kap0 + 2 * gp + x;
+    if (kap >= K) continue;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int a = j + r * GL;
+      if (a >= m) continue;
+      float2* Rout = A.Rpart + ((((size_t)i * (J - 1) + z) * K + kap) * m + a) * m;
+      for (int b = 0; b < m; ++b) {
+        float2 acc = cz();
+        const float2* eb = Es + (x * MG + b) * LT;
+#pragma unroll
+        for (int l = 0; l < LT; ++l) cmacc(acc, E[x][r][l], eb[l]);
+        Rout[b] = acc;
+      }
+    }
+  }
+}
+
 // k_sinr_finalize: one group of MG lanes per (UE i, subcarrier): sums the
 // partial covariances, adds the noise (eq. 25) and evaluates the SINR.
 template <int MG, int LT, bool SVD>
@@ -845,11 +1068,44 @@ cudaError_t launch_link_mode(const SinrArgs& A, int nz, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// svd: interfering links; wideband precoder: every link
+template <int MG, int LT>
+cudaError_t launch_link_blocked(const SinrArgs& A, cudaStream_t s) {
+  constexpr int NC = 4;
+  constexpr int T = 2 * kThreads / (MG / 2);
+  if (A.J < 2) return cudaSuccess;
+  LinkPlan pl = link_plan(MG, LT, T, NC, A.P, A.p, kModeSvd);
+  // the coefficient tile is only staged for dense coefficients
+  if (A.coef_mode != 0) {
+    const int shrink = T * A.P;
+    pl.off_pa -= shrink; pl.off_pt -= shrink; pl.off_ws -= shrink; pl.off_stage -= shrink;
+    pl.off_Es -= shrink; pl.total -= shrink;
+  }
+  // scratch of the epilogue (2 MG LT + 2 per pair of subcarriers) must fit
+  // in the stage buffers
+  const int es = (kThreads / (MG / 2)) * (2 * MG * LT + 2);
+  if (es > 2 * pl.stage) pl.total += es - 2 * pl.stage;
+  const size_t smem = (size_t)pl.total * sizeof(float2);
+  // large dense coefficient tiles: the unblocked kernel shrinks its tile
+  if (smem > kSmemBudget) return launch_link_mode<MG, LT, kModeSvd>(A, A.J - 1, s);
+  pl.wide = (A.n % 2 == 0) && (A.L % 2 == 0) && LT >= 2 && (((uintptr_t)A.G & 15u) == 0) &&
+            (((uintptr_t)A.V & 15u) == 0);
+  dim3 grid((A.K + T - 1) / T, A.J, A.J - 1);
+  auto kern = k_sinr_link_blk<MG, LT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, kThreads, smem, s>>>(A, pl);
+  return cudaGetLastError();
+}
+
+// svd: interfering links (the blocked kernel for m > 2); wideband precoder:
+// every link
 template <int MG, int LT>
 cudaError_t run_links(const SinrArgs& A, bool svd, cudaStream_t s) {
-  return svd ? launch_link_mode<MG, LT, kModeSvd>(A, A.J - 1, s)
-             : launch_link_mode<MG, LT, kModeFold>(A, A.J, s);
+  if (svd) {
+    if (MG >= 4 && A.p <= 32) return launch_link_blocked<(MG >= 4 ? MG : 4), LT>(A, s);
+    return launch_link_mode<MG, LT, kModeSvd>(A, A.J - 1, s);
+  }
+  return launch_link_mode<MG, LT, kModeFold>(A, A.J, s);
 }
 
 // svd: rebuild the serving links' compressed channels H~_kk into workspace
