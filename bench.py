@@ -212,7 +212,7 @@ def run_ours(args):
         if e2 is not None:
             e2.record(stream)
 
-    launches_per_step = 5            # path phase steps, serving links, precoders, links, finalize
+    launches_per_step = 4            # path phase steps, precoders (with the serving links), links, finalize
     for _ in range(args.warmup):
         flush.zero_()
         step()

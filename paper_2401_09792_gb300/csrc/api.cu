@@ -70,8 +70,10 @@ Workspace carve(const ts_dims* d, int op) {
   if (op == TS_OP_SINR_SVD) {
     w.V = o;
     o = align_up(o + (size_t)d->J * d->K * d->n * d->L * sizeof(float2), 256);
-    w.Hserv = o;
-    o = align_up(o + (size_t)d->J * d->K * d->m * d->n * sizeof(float2), 256);
+    if (!ts::precoder_fuses_serve(d->m, d->n, d->p)) {
+      w.Hserv = o;
+      o = align_up(o + (size_t)d->J * d->K * d->m * d->n * sizeof(float2), 256);
+    }
     w.pflag = o;
     o = align_up(o + (size_t)d->J * d->K, 256);
   } else {
@@ -155,8 +157,6 @@ ts::SinrArgs base_args(const ts_dims* d, const ts_coef* coef, const ts_c64* G, c
   a.turns = reinterpret_cast<const unsigned long long*>(ws + w.turns);
   a.Eserv = reinterpret_cast<float2*>(ws + w.Eserv);
   a.Rpart = reinterpret_cast<float2*>(ws + w.Rpart);
-  a.Hserv = reinterpret_cast<float2*>(ws + w.Hserv);
-  a.serv_stride = 1;
   a.sigma2 = sigma2;
   a.sinr = sinr;
   a.flags = flags;
@@ -414,7 +414,12 @@ int svd_precoders_impl(const ts_dims* d, const ts_coef* coef, const ts_c64* G, c
   if (coef->mode == TS_COEF_PATHS)
     e = ts::launch_turns(coef->tau_s, d->delta_f_hz, d->J * d->J * d->P,
                          reinterpret_cast<unsigned long long*>(base + w.turns), s);
-  if (e == cudaSuccess) e = ts::launch_sinr_serving(a, s);
+  a.fuse_serve = ts::precoder_fuses_serve(d->m, d->n, d->p) ? 1 : 0;
+  if (!a.fuse_serve) {
+    a.Hserv = reinterpret_cast<float2*>(base + w.Hserv);
+    a.serv_stride = 1;
+    if (e == cudaSuccess) e = ts::launch_sinr_serving(a, s);
+  }
   if (e == cudaSuccess) e = ts::launch_svd_precoder(a, s);
   return cuda_status(e);
 }

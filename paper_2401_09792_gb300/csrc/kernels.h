@@ -19,9 +19,11 @@ struct SinrArgs {
   float2* V;                        // svd: precoders [J][K][n][L] (workspace)
   uint8_t* pflag;                   // svd: precoder flags [J][K] (workspace)
   float2* Eserv;                    // wideband: serving effective channels [J][K][m][L] (workspace)
-  float2* Hserv;                    // svd: serving compressed channels [J][K][m][n] (workspace),
-                                    // or all links [J*J][K][m][n] (adjoint)
+  float2* Hserv;                    // svd with large cores: serving compressed channels
+                                    // [J][K][m][n] (workspace), or all links
+                                    // [J*J][K][m][n] (adjoint)
   int serv_stride;                  // serving link k at Hserv[(k * serv_stride) * K + kappa]
+  int fuse_serve;                   // svd precoder forms H~_kk itself (Hserv unused)
   float2* Uout;                     // adjoint: left singular vectors [J][K][m][m] (or nullptr)
   float* Sout;                      // adjoint: singular values [J][K][m]
   float2* Vmout;                    // adjoint: right singular vectors [J][K][n][m]
@@ -42,7 +44,6 @@ cudaError_t launch_project_precoder(const float2* B, const float2* Pfull, int J,
                                     int L, float2* Pt, cudaStream_t s);
 cudaError_t launch_mmse_fold(const float2* G, const float2* Pt, int J, int m, int n, int p,
                              int L, float2* F, cudaStream_t s);
-cudaError_t launch_sinr_serving(const SinrArgs& a, cudaStream_t s);
 cudaError_t launch_svd_precoder(const SinrArgs& a, cudaStream_t s);
 cudaError_t launch_sinr_links(const SinrArgs& a, bool svd, cudaStream_t s);
 cudaError_t launch_sinr_finalize(const SinrArgs& a, bool svd, cudaStream_t s);
@@ -64,6 +65,11 @@ struct AdjointWork {
   float2* dPt;             // [J][n][L] (wideband)
 };
 cudaError_t launch_sinr_rebuild(const SinrArgs& a, cudaStream_t s);
+cudaError_t launch_sinr_serving(const SinrArgs& a, cudaStream_t s);
+// The SVD precoder forms H~_kk itself (re-reading the core G_kk once per
+// subcarrier tile from L2) when the core is at most 64 KB; larger cores (the
+// dense-channel comparator) go through a separate serving-link pass.
+inline bool precoder_fuses_serve(int m, int n, int p) { return (long long)m * n * p <= 8192; }
 cudaError_t launch_adjoint(const SinrArgs& a, const AdjointWork& w, cudaStream_t s);
 cudaError_t launch_project_precoder_adjoint(const float2* Pfull, const float2* dPt, int J, int N,
                                             int n, int L, float2* dB, cudaStream_t s);

@@ -119,8 +119,8 @@ using detail::group_size;
 using detail::ltile;
 using detail::run_precoder;
 using detail::run_links;
-using detail::run_serving;
 using detail::run_rebuild;
+using detail::run_serving;
 using detail::run_finalize;
 
 #define TS_DISPATCH(FN, ...)                                                        \
@@ -137,9 +137,9 @@ using detail::run_finalize;
 
 cudaError_t launch_svd_precoder(const SinrArgs& a, cudaStream_t s) { TS_DISPATCH(run_precoder, a, s); }
 
-cudaError_t launch_sinr_serving(const SinrArgs& a, cudaStream_t s) { TS_DISPATCH(run_serving, a, s); }
 
 cudaError_t launch_sinr_rebuild(const SinrArgs& a, cudaStream_t s) { TS_DISPATCH(run_rebuild, a, s); }
+cudaError_t launch_sinr_serving(const SinrArgs& a, cudaStream_t s) { TS_DISPATCH(run_serving, a, s); }
 
 cudaError_t launch_sinr_links(const SinrArgs& a, bool svd, cudaStream_t s) {
   TS_DISPATCH(run_links, a, svd, s);

@@ -11,12 +11,19 @@
 //                        Jacobi eigensolve, V~_k = H~_kk* U_L Sigma_L^{-1}
 //                        (eq. 7, eq. 23) and the serving effective channel
 //                        E_kk = H~_kk V~_k = U_L Sigma_L -> workspace
-//   k_sinr_link          (subcarrier tile, UE i, link k): w = c* C (eq. 15),
-//                        E_ik = H~_ik V~_k (svd) or sum_q w_q F_ik[q]
-//                        (wideband precoder) and the partial covariance
-//                        E_ik E_ik* -> workspace.  The core and precoder
-//                        column chunks are staged through a double-buffered
-//                        cp.async pipeline, one chunk ahead of the arithmetic.
+//   k_sinr_link_blk      (subcarrier tile, UE i, interfering link k), SVD
+//                        precoders: w = c* C (eq. 15), E_ik = H~_ik V~_k and
+//                        the partial covariance E_ik E_ik* -> workspace, two
+//                        subcarriers and two rows per lane.  The core and
+//                        precoder column chunks are staged through a
+//                        double-buffered cp.async pipeline, one chunk ahead
+//                        of the arithmetic.
+//   k_sinr_link          the same, one row per lane (m <= 2, large dense
+//                        coefficient tiles), the wideband-precoder fold
+//                        E_ik = sum_q w_q F_ik[q], the serving links H~_kk
+//                        when the cores are too large to re-read per
+//                        precoder tile, and the rebuild of every H~_ik for
+//                        the adjoint.
 //   k_sinr_finalize      (UE i, subcarrier): R_i = sum_{k != i} E E* +
 //                        sigma^2 I, Q~_i = R_i + E_ii E_ii* (eq. 25), then the
 //                        SINR of eq. (5) in a cancellation-free form (below).
@@ -41,8 +48,10 @@ constexpr size_t kSmemBudget = 200 * 1024;
 __device__ __forceinline__ float2 path_coef(float2 alpha, unsigned long long turn, int kappa) {
   // c_p(kappa) = conj(alpha_p) exp(+j 2 pi kappa df tau_p); the phase is kept
   // modulo one turn in 64-bit fixed point, then mapped to half-turns in [-1, 1)
+  // from its upper 32 bits (a 2^-31 half-turn step, far below FP32 sincos
+  // accuracy; a 64-bit integer conversion would run on the FP64 pipe)
   const unsigned long long ph = turn * (unsigned long long)kappa;
-  const float x = (float)(long long)ph * 0x1p-63f;
+  const float x = (float)(int)(unsigned)(ph >> 32) * 0x1p-31f;
   float s, c;
   sincospif(x, &s, &c);
   return make_float2(fmaf(alpha.x, c, alpha.y * s), fmaf(alpha.x, s, -alpha.y * c));
@@ -100,8 +109,14 @@ __device__ __forceinline__ void core_chunk(const float2* wrow, const float2* Gs,
 // and S <- J* S J, U <- U J.  Both lanes of a pair compute the rotation from
 // the same three numbers (lane p's S_pq and the two diagonals), so they agree
 // bit for bit; rows are exchanged by shuffles, columns rotate in registers.
+// The diagonal entry of the lane's row is tracked in `dg` (S_pp - t|b|,
+// S_qq + t|b|), which spares a register select per step.  The rotation uses
+// hardware reciprocal square roots: any (c, s) with c^2 + s^2 = 1 to a few
+// ulps is a valid Jacobi rotation, and the iteration still drives the
+// off-diagonal to zero.  S is expected to be scaled to unit trace.
 template <int MG>
-__device__ __forceinline__ void jacobi_step(const int t, float2 (&S)[MG], float2 (&U)[MG], int a) {
+__device__ __forceinline__ void jacobi_step(const int t, float2 (&S)[MG], float2 (&U)[MG],
+                                            float& dg, int a) {
   int b;
   bool is_p;
   if (a == MG - 1) { b = t; is_p = false; }
@@ -111,30 +126,35 @@ __device__ __forceinline__ void jacobi_step(const int t, float2 (&S)[MG], float2
     is_p = d < MG / 2;
     b = (2 * t - a + 2 * (MG - 1)) % (MG - 1);
   }
-  const float d_self = pick(S, a).x;
-  const float d_other = __shfl_sync(FULL, d_self, b, MG);
+  const float d_other = __shfl_sync(FULL, dg, b, MG);
   const float2 mine = pick(S, b);
   const float2 theirs = gshfl<MG>(mine, b);
-  const float app = is_p ? d_self : d_other, aqq = is_p ? d_other : d_self;
+  const float app = is_p ? dg : d_other, aqq = is_p ? d_other : dg;
   const float2 bpq = is_p ? mine : theirs;
-  const float ab = sqrtf(cabs2(bpq));
-  float c = 1.f, s = 0.f;
-  float2 e = make_float2(1.f, 0.f);
-  if (ab > 1e-30f && ab > 1e-9f * sqrtf(fabsf(app * aqq))) {
-    const float tau = (aqq - app) / (2.f * ab);
-    const float tt = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
-    c = 1.f / sqrtf(fmaf(tt, tt, 1.f));
-    s = tt * c;
-    e = cscale(bpq, 1.f / ab);
+  const float ab2 = cabs2(bpq);
+  float c = 1.f;
+  float2 se = cz();                        // s e^{i phi}
+  if (ab2 > 1e-36f && ab2 > 1e-18f * fabsf(app * aqq)) {
+    const float r = rsqrtf(ab2);           // 1 / |b|
+    const float tau = 0.5f * (aqq - app) * r;
+    const float at = fabsf(tau);
+    const float h = fmaf(tau, tau, 1.f);
+    // t = sign(tau) / (|tau| + sqrt(1 + tau^2)), the smaller root
+    const float tm = at > 1e15f ? __fdividef(0.5f, at) : __fdividef(1.f, at + h * rsqrtf(h));
+    const float tt = copysignf(tm, tau);
+    c = rsqrtf(fmaf(tt, tt, 1.f));
+    se = cscale(bpq, tt * c * r);
+    const float tb = tt * (ab2 * r);
+    dg = is_p ? app - tb : aqq + tb;
   }
   // rows: S <- J* S (row p' = c p - s e q, row q' = s conj(e) p + c q)
   {
-    const float2 se = cscale(e, s), sec = cscale(cconj(e), s);
+    const float2 f = is_p ? make_float2(-se.x, -se.y) : cconj(se);
 #pragma unroll
     for (int k = 0; k < MG; ++k) {
       const float2 other = gshfl<MG>(S[k], b);
       float2 v = cscale(S[k], c);
-      if (is_p) cms(v, se, other); else cmac(v, sec, other);
+      cmac(v, f, other);
       S[k] = v;
     }
   }
@@ -144,22 +164,20 @@ __device__ __forceinline__ void jacobi_step(const int t, float2 (&S)[MG], float2
     const int pj = j == 0 ? t : (t + j) % (MG - 1);
     const int qj = j == 0 ? MG - 1 : (t - j + MG - 1) % (MG - 1);
     const float cj = __shfl_sync(FULL, c, pj, MG);
-    const float sj = __shfl_sync(FULL, s, pj, MG);
-    const float2 ej = gshfl<MG>(e, pj);
-    const float2 se = cscale(ej, sj), sec = cscale(cconj(ej), sj);
+    const float2 se_j = gshfl<MG>(se, pj), sec_j = cconj(se_j);
     {
       const float2 x = S[pj], y = S[qj];
       float2 nx = cscale(x, cj), ny = cscale(y, cj);
-      cms(nx, sec, y);     // c x - s conj(e) y
-      cmac(ny, se, x);     // s e x + c y
+      cms(nx, sec_j, y);     // c x - s conj(e) y
+      cmac(ny, se_j, x);     // s e x + c y
       S[pj] = nx;
       S[qj] = ny;
     }
     {
       const float2 x = U[pj], y = U[qj];
       float2 nx = cscale(x, cj), ny = cscale(y, cj);
-      cms(nx, sec, y);
-      cmac(ny, se, x);
+      cms(nx, sec_j, y);
+      cmac(ny, se_j, x);
       U[pj] = nx;
       U[qj] = ny;
     }
@@ -167,29 +185,114 @@ __device__ __forceinline__ void jacobi_step(const int t, float2 (&S)[MG], float2
 }
 
 // ------------------------------------------------------------------ phase 1
-// k_svd_precoder: one group of MG lanes per (BS k, subcarrier).  Reads the
-// serving link's compressed channel H~_kk (written by k_sinr_link in serve
-// mode), forms the Gram S = H~ H~*, diagonalises it by cyclic Jacobi, rotates
-// the rows W = U* H~, refines them by one sweep of one-sided Jacobi and
-// writes the top-L right singular vectors V~ (normalised rows of W, in order
-// of decreasing row norm = singular value).
+// k_svd_precoder: one group of MG lanes per (BS k, subcarrier).  Forms the
+// serving link's compressed channel H~_kk (or reads it from workspace: large
+// cores, and the all-link rebuild of the adjoint), the Gram S = H~ H~*, diagonalises it by cyclic
+// Jacobi, rotates the rows W = U* H~, refines them by one-sided Jacobi when a
+// kept singular value is small, and writes the top-L right singular vectors
+// V~ (normalised rows of W, in order of decreasing row norm = singular value).
 struct PrecoderPlan {
   int T, SH, SS;
-  int off_Hs, off_Ss, off_Us, off_sel, total;
+  int off_Hs, off_Ss, off_Us, off_cs, off_w, off_sel, total;
 };
 
-__host__ __device__ inline PrecoderPlan precoder_plan(int MG, int T, int n) {
+// coefficient chunk of the fused H~_kk evaluation
+constexpr int kServePC = 32;
+
+__host__ __device__ inline PrecoderPlan precoder_plan(int MG, int T, int n, int p, bool fused) {
   PrecoderPlan pl;
   pl.T = T;
   pl.SH = n + 1;
   pl.SS = MG + 1;
   int o = 0;
   pl.off_Hs = o; o += T * MG * pl.SH;
-  pl.off_Ss = o; o += T * MG * pl.SS;
-  pl.off_Us = o; o += T * MG * pl.SS;
+  // S and U scratch; before the Gram it holds the coefficient chunk and the
+  // projections w of the fused H~_kk evaluation
+  int r = 2 * T * MG * pl.SS;
+  if (fused && T * (kServePC + p) > r) r = T * (kServePC + p);
+  pl.off_Ss = o;
+  pl.off_Us = o + T * MG * pl.SS;
+  pl.off_cs = o;
+  pl.off_w = o + T * kServePC;
+  o += r;
   pl.off_sel = o; o += T * MG / 2 + 1;   // MG int per group
   pl.total = o;
   return pl;
+}
+
+// H~_kk(kappa) = sum_q w_q G_kk[:, :, q] with w = C_kk^T conj(c(kappa))
+// (eq. 15, link (k, k)) for the T subcarriers of a precoder CTA, written to
+// the rows of Hs (zero rows for a >= m and for kappa >= K).
+template <int MG>
+__device__ __forceinline__ void serve_channels(const SinrArgs& A, const PrecoderPlan& pl, int k,
+                                               int kap0, float2* sm) {
+  const int T = pl.T, nth = blockDim.x, tid = threadIdx.x;
+  const int J = A.J, m = A.m, n = A.n, p = A.p, P = A.P, K = A.K;
+  const int ch = k * J + k;
+  float2* cs = sm + pl.off_cs;
+  float2* w = sm + pl.off_w;
+  const float2* Cch = A.C + (size_t)ch * P * p;
+  const unsigned long long* turns = A.turns + (size_t)ch * P;
+  auto coef_at = [&](int t, int pp) -> float2 {
+    const int kk = kap0 + t;
+    if (kk >= K) return cz();
+    return A.coef_mode == 0 ? A.coef[((size_t)ch * K + kk) * P + pp]
+                            : path_coef(A.coef[(size_t)ch * P + pp], turns[pp], kk);
+  };
+  if (A.identity_C) {                      // dense channel: C = I, p = P
+    for (int idx = tid; idx < T * p; idx += nth) w[idx] = cconj(coef_at(idx / p, idx % p));
+  } else {
+    for (int idx = tid; idx < T * p; idx += nth) w[idx] = cz();
+    for (int P0 = 0; P0 < P; P0 += kServePC) {
+      const int pc = min(kServePC, P - P0);
+      __syncthreads();                     // previous chunk consumed
+      for (int idx = tid; idx < T * kServePC; idx += nth) {
+        const int t = idx / kServePC, pp = idx % kServePC;
+        cs[idx] = pp < pc ? coef_at(t, P0 + pp) : cz();
+      }
+      __syncthreads();
+      for (int idx = tid; idx < T * p; idx += nth) {
+        const int t = idx / p, q = idx - t * p;
+        float2 acc = w[idx];
+        const float2* crow = cs + t * kServePC;
+        for (int pp = 0; pp < pc; ++pp) cmacc(acc, Cch[(size_t)(P0 + pp) * p + q], crow[pp]);
+        w[idx] = acc;
+      }
+    }
+  }
+  __syncthreads();
+  // rows: thread per (row a, column c), eight subcarriers at a time
+  constexpr int TB = 8;
+  const float2* Gch = A.G + (size_t)ch * p * m * n;
+  for (int idx = tid; idx < MG * n; idx += nth) {
+    const int aa = idx / n, c = idx - aa * n;
+    for (int t0 = 0; t0 < T; t0 += TB) {
+      float2 acc[TB];
+#pragma unroll
+      for (int u = 0; u < TB; ++u) acc[u] = cz();
+      if (aa < m) {
+        // eight independent core loads in flight per step
+        const float2* g = Gch + (size_t)aa * n + c;
+        const size_t qs = (size_t)m * n;
+        for (int q0 = 0; q0 < p; q0 += 8) {
+          float2 gv[8];
+#pragma unroll
+          for (int v = 0; v < 8; ++v) gv[v] = q0 + v < p ? __ldg(g + (q0 + v) * qs) : cz();
+#pragma unroll
+          for (int v = 0; v < 8; ++v) {
+            if (q0 + v < p) {
+#pragma unroll
+              for (int u = 0; u < TB; ++u)
+                if (t0 + u < T) cmac(acc[u], w[(t0 + u) * p + q0 + v], gv[v]);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < TB; ++u)
+        if (t0 + u < T) sm[pl.off_Hs + ((t0 + u) * MG + aa) * pl.SH + c] = acc[u];
+    }
+  }
 }
 
 template <int MG, int LT>
@@ -207,13 +310,18 @@ __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, con
   float2* Us = sm + pl.off_Us + g * MG * pl.SS;
   int* sel = reinterpret_cast<int*>(sm + pl.off_sel) + g * MG;
 
-  // H~_kk rows of the T subcarriers (zero rows for a >= m and beyond K)
-  for (int idx = tid; idx < T * MG * n; idx += nth) {
-    const int c = idx % n, aa = (idx / n) % MG, t = idx / (n * MG);
-    const int kk = kap0 + t;
-    float2 v = cz();
-    if (aa < m && kk < K) v = A.Hserv[(((size_t)k * A.serv_stride * K + kk) * m + aa) * n + c];
-    sm[pl.off_Hs + (t * MG + aa) * pl.SH + c] = v;
+  // H~_kk rows of the T subcarriers (zero rows for a >= m and beyond K),
+  // formed here or read from the all-link rebuild of the adjoint
+  if (A.fuse_serve) {
+    serve_channels<MG>(A, pl, k, kap0, sm);
+  } else {
+    for (int idx = tid; idx < T * MG * n; idx += nth) {
+      const int c = idx % n, aa = (idx / n) % MG, t = idx / (n * MG);
+      const int kk = kap0 + t;
+      float2 v = cz();
+      if (aa < m && kk < K) v = A.Hserv[(((size_t)k * A.serv_stride * K + kk) * m + aa) * n + c];
+      sm[pl.off_Hs + (t * MG + aa) * pl.SH + c] = v;
+    }
   }
   __syncthreads();
 
@@ -233,6 +341,14 @@ __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, con
     }
   }
 
+  // scale S to unit trace (eigenvectors and eigenvalue ratios are unchanged;
+  // the singular values are taken from W below)
+  {
+    const float tr = gsum<MG>(pick(S, a).x);
+    const float sc = tr > 0.f ? 1.f / tr : 1.f;
+#pragma unroll
+    for (int b = 0; b < MG; ++b) S[b] = cscale(S[b], sc);
+  }
   // Cyclic Jacobi on S held in registers (see jacobi_step), to FP32
   // convergence (relative off-diagonal norm ~5e-7).  The stopping decision is
   // taken warp-wide (extra sweeps leave a converged S unchanged).
@@ -249,8 +365,9 @@ __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, con
     dia = gsum<MG>(dia);
     converged = off <= 2.3e-13f * dia;
     if (__all_sync(FULL, converged) || sweep == max_sweeps) break;
+    float dg = pick(S, a).x;
 #pragma unroll
-    for (int t = 0; t < MG - 1; ++t) jacobi_step<MG>(t, S, U, a);
+    for (int t = 0; t < MG - 1; ++t) jacobi_step<MG>(t, S, U, dg, a);
   }
   // The eigenvectors of the Gram are accurate unless a kept singular value is
   // small: refine with one-sided sweeps (below) when lambda_L < 1e-4 lambda_1
@@ -440,7 +557,7 @@ struct LinkPlan {
 };
 
 __host__ __device__ inline LinkPlan link_plan(int MG, int LT, int T, int NC, int P, int p, int mode) {
-  const bool svd = mode != 1;            // chunked modes (svd, serve)
+  const bool svd = mode != 1;            // chunked modes (svd, serve, rebuild)
   LinkPlan pl;
   pl.T = T;
   pl.NC = NC;
@@ -475,7 +592,7 @@ __host__ __device__ inline LinkPlan link_plan(int MG, int LT, int T, int NC, int
 // Modes of k_sinr_link.
 constexpr int kModeSvd = 0;     // interfering link, E = H~ V~ (SVD precoders)
 constexpr int kModeFold = 1;    // any link, E = sum_q w_q F[q] (wideband precoder)
-constexpr int kModeServe = 2;   // serving link of the SVD variant: write H~_kk rows
+constexpr int kModeServe = 2;   // serving links (large cores): write H~_kk rows
 constexpr int kModeRebuild = 3; // every link (adjoint): write H~_ik rows
 
 template <int MG, int LT, int NC, int MODE>
@@ -490,8 +607,8 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link(const SinrArgs A, const 
   const int kap0 = blockIdx.x * T;
   const int kap = kap0 + g;
   const int J = A.J, m = A.m, n = A.n, p = A.p, L = A.L, K = A.K, P = A.P;
-  // svd: z enumerates the interfering links; fold: z is the BS index;
-  // serve: the serving link
+  // svd: z enumerates the interfering links; fold and rebuild: z is the BS
+  // index; serve: the serving link
   const int k = MODE == kModeSvd ? (z < i ? z : z + 1) : MODE == kModeServe ? i : z;
   const int ch = i * J + k;
   const int nchunk = CHUNKED ? (n + NC - 1) / NC : 1;
@@ -1029,10 +1146,11 @@ cudaError_t run_precoder(const SinrArgs& A, cudaStream_t s) {
   // shared memory (eight CTAs per SM), keeping whole warps for the group
   // shuffles and votes
   int T = kThreads / MG;
-  PrecoderPlan pl = precoder_plan(MG, T, A.n);
+  const bool fused = A.fuse_serve != 0;
+  PrecoderPlan pl = precoder_plan(MG, T, A.n, A.p, fused);
   while (T * MG > 32 && (size_t)pl.total * sizeof(float2) > 28 * 1024) {
     T /= 2;
-    pl = precoder_plan(MG, T, A.n);
+    pl = precoder_plan(MG, T, A.n, A.p, fused);
   }
   const size_t smem = (size_t)pl.total * sizeof(float2);
   if (smem > kSmemBudget) return cudaErrorInvalidValue;
@@ -1108,7 +1226,8 @@ cudaError_t run_links(const SinrArgs& A, bool svd, cudaStream_t s) {
   return launch_link_mode<MG, LT, kModeFold>(A, A.J, s);
 }
 
-// svd: rebuild the serving links' compressed channels H~_kk into workspace
+// svd with large cores: the serving links' compressed channels H~_kk into
+// workspace, for the precoder to read
 template <int MG, int LT>
 cudaError_t run_serving(const SinrArgs& A, cudaStream_t s) {
   return launch_link_mode<MG, LT, kModeServe>(A, 1, s);
