@@ -152,6 +152,30 @@ class ClockSampler:
                 "samples": len(rows), "reasons": reasons}
 
 
+# ------------------------------------------------------- multi-rank host logic
+def rank_workload(rank: int):
+    """Each rank evaluates its own independent system: the mid workload with
+    the seed offset by the rank (weak scaling, no data-path collective)."""
+    return synth.Workload(**{**WORKLOAD.__dict__, "seed": WORKLOAD.seed + rank})
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The slowest rank's time (all ranks get it); `x` unchanged at world 1."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world: int, units_per_rank: int, steps: int, max_ms: float) -> float:
+    """Subcarrier-SINRs per second of the whole job: every rank's units over
+    the slowest rank's time."""
+    return world * units_per_rank * steps / (max_ms * 1e-3)
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args):
     import torch
@@ -177,7 +201,7 @@ def run_ours(args):
     barrier()
     ts.load()
 
-    w = synth.Workload(**{**WORKLOAD.__dict__, "seed": WORKLOAD.seed + rank})
+    w = rank_workload(rank)
     J, K, L, P = w.J, w.K, w.L, w.P
     tk = synth.direct_tucker(w)
     alpha, tau = synth.path_gains_delays(w)
@@ -239,13 +263,9 @@ def run_ours(args):
     link_ms = [e[3].elapsed_time(e[4]) for e in evs]
     pre_ms = [e[0].elapsed_time(e[1]) for e in evs]
     fin_ms = [e[1].elapsed_time(e[2]) for e in evs]
-    total_ms = float(np.sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(np.sum(step_ms)), world, dev)
     units = J * K
-    value = world * units * args.steps / (total_ms * 1e-3)
+    value = whole_job_value(world, units, args.steps, total_ms)
     assert int(flags.max().item()) == 0, "numerical flags raised in the timed steps"
 
     if args.step_only:
@@ -296,11 +316,8 @@ def _extras(args, ts, torch, dist, world, dev, w, tk, host, dv, coef, d, ws, sin
         b.record(stream)
         b.synchronize()
         e2e_ms += a.elapsed_time(b)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * units * args.steps / (e2e_ms * 1e-3)
+    e2e_ms = max_over_ranks(e2e_ms, world, dev)
+    e2e_value = whole_job_value(world, units, args.steps, e2e_ms)
 
     # ---- the MMSE variant (wideband precoders), same timing discipline
     Pw = synth.wideband_precoders(w)
