@@ -53,7 +53,8 @@ def workload_config(w, precoder="svd"):
 
 # --------------------------------------------------------------- flop counts
 def link_flops(w, precoder="svd") -> int:
-    """Algorithmic real flops of one launch of the per-link kernel k_sinr_link.
+    """Algorithmic real flops of one launch of the interfering-link kernel
+    (k_sinr_link_blk; k_sinr_link fold mode for the wideband precoder).
 
     One CTA column per (UE i, link k, subcarrier); per unit, in complex
     multiply-adds (8 flops each):
@@ -371,8 +372,8 @@ def _report(args, ts, torch, world, dev, w, tk, alpha, tau, s2, d, coef, dv, ws,
     fp32_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12       # TFLOP/s, FFMA on every lane
     link_mean = float(np.mean(link_ms))
     achieved = link_flops(w, "svd") / (link_mean * 1e-3) / 1e12
-    traffic = recorded_traffic("k_sinr_link", "mid")
-    roofline = {"kernel": "k_sinr_link (svd)", "bound": "alu", "achieved": round(achieved, 3),
+    traffic = recorded_traffic("k_sinr_link_blk", "mid")
+    roofline = {"kernel": "k_sinr_link_blk (svd)", "bound": "alu", "achieved": round(achieved, 3),
                 "peak": round(fp32_peak, 2), "unit": "TFLOP/s", "frac": round(achieved / fp32_peak, 4),
                 "traffic": traffic,
                 "peak_basis": f"FP32 FFMA: {sms} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz "
