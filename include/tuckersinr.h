@@ -83,7 +83,9 @@ enum {
   TS_FLAG_NONFINITE = 2,      /* a non-finite value reached the solve         */
   TS_FLAG_RANK_DEFICIENT = 4, /* a serving link had a zero singular value
                                  among the top L (SVD precoding)              */
-  TS_FLAG_EIG_UNCONVERGED = 8 /* the Jacobi eigensolver hit its sweep cap     */
+  TS_FLAG_EIG_UNCONVERGED = 8, /* the Jacobi eigensolver hit its sweep cap    */
+  TS_FLAG_TIMEOUT = 16        /* a bounded device wait of the tensor-core pass
+                                 gave up; the unit's SINR is NaN             */
 };
 
 /* Operations, for ts_workspace_bytes. */
@@ -94,7 +96,22 @@ enum {
   TS_OP_DENSE_MMSE = 3,
   TS_OP_SINR_SVD_ADJOINT = 4,
   TS_OP_SINR_MMSE_ADJOINT = 5,
-  TS_OP_TUCKER_FIT = 6
+  TS_OP_TUCKER_FIT = 6,
+  TS_OP_SINR_SVD_TF32 = 7,    /* ts_sinr_svd_prec with TS_PREC_TF32   */
+  TS_OP_SINR_SVD_BF16X2 = 8   /* ts_sinr_svd_prec with TS_PREC_BF16X2 */
+};
+
+/* Arithmetic of the core contraction H~ = G x_3 (c* C) (eq. 15) in
+ * ts_sinr_svd_prec.  FP32: FMA pipe, the default of every other call.
+ * TF32: tensor cores, w = c* C and G rounded to TF32 (10-bit mantissa), FP32
+ * accumulation.  BF16X2: tensor cores, w and G split into BF16 high and low
+ * parts, products w_hi G_hi + w_lo G_hi + w_hi G_lo, FP32 accumulation
+ * (about 16 significant bits).  The projection, the precoders, the
+ * effective channels, the covariance and the solves stay FP32. */
+enum {
+  TS_PREC_FP32 = 0,
+  TS_PREC_TF32 = 1,
+  TS_PREC_BF16X2 = 2
 };
 
 /* Human-readable name of a status code (static storage). */
@@ -170,6 +187,24 @@ int ts_sinr_svd_from_precoders(const ts_dims* d, const ts_coef* coef,
                                const float* sigma2, float* sinr,
                                uint8_t* flags, void* ws, size_t ws_bytes,
                                void* stream);
+
+/* ts_sinr_svd with the interfering links' core contraction (eq. 15) in the
+ * arithmetic `precision` (TS_PREC_*; TS_PREC_FP32 is ts_sinr_svd).  The
+ * serving links and the precoders stay FP32.  Tensor-core modes need
+ * L <= 8, p <= 32 and m <= 16 (else TS_ERR_MODE); ws holds
+ * ts_workspace_bytes(d, TS_OP_SINR_SVD_TF32 / _BF16X2) bytes (the core
+ * rewritten as a tensor-core operand, then the ts_sinr_svd workspace).
+ * ts_sinr_svd_from_precoders_prec is its second phase (after
+ * ts_svd_precoders on the same ws). */
+int ts_sinr_svd_prec(const ts_dims* d, const ts_coef* coef, const ts_c64* G,
+                     const ts_c64* C, const float* sigma2, int precision,
+                     float* sinr, uint8_t* flags, void* ws, size_t ws_bytes,
+                     void* stream);
+int ts_sinr_svd_from_precoders_prec(const ts_dims* d, const ts_coef* coef,
+                                    const ts_c64* G, const ts_c64* C,
+                                    const float* sigma2, int precision,
+                                    float* sinr, uint8_t* flags, void* ws,
+                                    size_t ws_bytes, void* stream);
 
 /* Dense-channel comparator: the same SINR computed from the uncompressed
  * channel tensors, rebuilding the full M x N channel of every link and

@@ -84,6 +84,12 @@ Workspace carve(const ts_dims* d, int op) {
   return w;
 }
 
+// Reduced-precision workspace: the ts_sinr_svd workspace, then the core
+// rewritten as a tensor-core operand.
+size_t prec_workspace_bytes(const ts_dims* d, int prec) {
+  return carve(d, TS_OP_SINR_SVD).total + ts::tc_prep_bytes(d->J, d->m, d->L, d->n, d->p, prec);
+}
+
 // Adjoint workspace (byte offsets, each 256-byte aligned).
 struct AdjWorkspace {
   size_t turns = 0, Hall = 0, V = 0, Eserv = 0, pflag = 0, U = 0, S = 0, Vm = 0, W = 0, E = 0,
@@ -204,6 +210,10 @@ size_t ts_workspace_bytes(const ts_dims* d, int op) {
   if (op == TS_OP_TUCKER_FIT) return fit_checks(d) == TS_OK ? ts::fit_workspace_bytes(fit_dims(d)) : 0;
   if (op == TS_OP_SINR_SVD_ADJOINT || op == TS_OP_SINR_MMSE_ADJOINT)
     return carve_adjoint(d, op == TS_OP_SINR_SVD_ADJOINT).total;
+  if (op == TS_OP_SINR_SVD_TF32 || op == TS_OP_SINR_SVD_BF16X2)
+    return ts::tc_supported(d->m, d->L, d->p)
+               ? prec_workspace_bytes(d, op == TS_OP_SINR_SVD_TF32 ? TS_PREC_TF32 : TS_PREC_BF16X2)
+               : 0;
   if (op != TS_OP_SINR_SVD && op != TS_OP_SINR_MMSE) return 0;
   return carve(d, op).total;
 }
@@ -424,6 +434,34 @@ int svd_precoders_impl(const ts_dims* d, const ts_coef* coef, const ts_c64* G, c
   return cuda_status(e);
 }
 
+int svd_from_precoders_prec_impl(const ts_dims* d, const ts_coef* coef, const ts_c64* G,
+                                 const ts_c64* C, const float* sigma2, int prec, float* sinr,
+                                 uint8_t* flags, void* ws, size_t ws_bytes, void* stream) {
+  int st = sinr_common_checks(d, coef, G, C, false, sigma2, sinr, ws, ws_bytes, TS_OP_SINR_SVD);
+  if (st != TS_OK) return st;
+  if (ws_bytes < prec_workspace_bytes(d, prec)) return TS_ERR_WORKSPACE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Workspace w = carve(d, TS_OP_SINR_SVD);
+  char* base = static_cast<char*>(ws);
+  ts::SinrArgs a = base_args(d, coef, G, C, sigma2, sinr, flags, base, w);
+  a.V = reinterpret_cast<float2*>(base + w.V);
+  a.pflag = reinterpret_cast<uint8_t*>(base + w.pflag);
+  void* prep = base + w.total;
+  cudaError_t e = ts::launch_core_prep(a, prec, prep, s);
+  if (e == cudaSuccess && g_ev_start != nullptr) e = cudaEventRecord(g_ev_start, s);
+  if (e == cudaSuccess) e = ts::launch_sinr_links_tc(a, prec, prep, s);
+  if (e == cudaSuccess && g_ev_stop != nullptr) e = cudaEventRecord(g_ev_stop, s);
+  if (e == cudaSuccess) e = ts::launch_sinr_finalize(a, true, s);
+  return cuda_status(e);
+}
+
+int check_prec(const ts_dims* d, int precision) {
+  if (precision != TS_PREC_TF32 && precision != TS_PREC_BF16X2) return TS_ERR_MODE;
+  int st = check_dims(d);
+  if (st != TS_OK) return st;
+  return ts::tc_supported(d->m, d->L, d->p) ? TS_OK : TS_ERR_MODE;
+}
+
 int svd_from_precoders_impl(const ts_dims* d, const ts_coef* coef, const ts_c64* G,
                             const ts_c64* C, bool identity, const float* sigma2, float* sinr,
                             uint8_t* flags, void* ws, size_t ws_bytes, void* stream) {
@@ -466,6 +504,32 @@ int ts_sinr_svd(const ts_dims* d, const ts_coef* coef, const ts_c64* G, const ts
   int st = svd_precoders_impl(d, coef, G, C, false, ws, ws_bytes, stream);
   if (st != TS_OK) return st;
   return svd_from_precoders_impl(d, coef, G, C, false, sigma2, sinr, flags, ws, ws_bytes, stream);
+}
+
+int ts_sinr_svd_prec(const ts_dims* d, const ts_coef* coef, const ts_c64* G, const ts_c64* C,
+                     const float* sigma2, int precision, float* sinr, uint8_t* flags, void* ws,
+                     size_t ws_bytes, void* stream) {
+  if (precision == TS_PREC_FP32)
+    return ts_sinr_svd(d, coef, G, C, sigma2, sinr, flags, ws, ws_bytes, stream);
+  int st = check_prec(d, precision);
+  if (st != TS_OK) return st;
+  if (ws != nullptr && ws_bytes < prec_workspace_bytes(d, precision)) return TS_ERR_WORKSPACE;
+  st = svd_precoders_impl(d, coef, G, C, false, ws, ws_bytes, stream);
+  if (st != TS_OK) return st;
+  return svd_from_precoders_prec_impl(d, coef, G, C, sigma2, precision, sinr, flags, ws, ws_bytes,
+                                      stream);
+}
+
+int ts_sinr_svd_from_precoders_prec(const ts_dims* d, const ts_coef* coef, const ts_c64* G,
+                                    const ts_c64* C, const float* sigma2, int precision,
+                                    float* sinr, uint8_t* flags, void* ws, size_t ws_bytes,
+                                    void* stream) {
+  if (precision == TS_PREC_FP32)
+    return ts_sinr_svd_from_precoders(d, coef, G, C, sigma2, sinr, flags, ws, ws_bytes, stream);
+  int st = check_prec(d, precision);
+  if (st != TS_OK) return st;
+  return svd_from_precoders_prec_impl(d, coef, G, C, sigma2, precision, sinr, flags, ws, ws_bytes,
+                                      stream);
 }
 
 int ts_dense_sinr_svd(const ts_dims* d, const ts_coef* coef, const ts_c64* X, const float* sigma2,

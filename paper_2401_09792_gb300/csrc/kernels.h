@@ -66,6 +66,13 @@ struct AdjointWork {
 };
 cudaError_t launch_sinr_rebuild(const SinrArgs& a, cudaStream_t s);
 cudaError_t launch_sinr_serving(const SinrArgs& a, cudaStream_t s);
+// Tensor-core interfering-link pass (reduced-precision modes, sinr_tc.cu):
+// shape support, bytes of the rewritten core, the core rewrite into `prep`
+// (once per call), and the link kernel.
+bool tc_supported(int m, int L, int p);
+size_t tc_prep_bytes(int J, int m, int L, int n, int p, int prec);
+cudaError_t launch_core_prep(const SinrArgs& a, int prec, void* prep, cudaStream_t s);
+cudaError_t launch_sinr_links_tc(const SinrArgs& a, int prec, const void* prep, cudaStream_t s);
 // The SVD precoder forms H~_kk itself (re-reading the core G_kk once per
 // subcarrier tile from L2) when the core is at most 64 KB; larger cores (the
 // dense-channel comparator) go through a separate serving-link pass.

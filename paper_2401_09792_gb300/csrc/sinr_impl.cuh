@@ -1127,15 +1127,17 @@ __global__ void __launch_bounds__(kThreads) k_sinr_finalize(const SinrArgs A, in
   const bool ok = sinr_core<MG, LT>(R, Eself, Es, a, Lq, Zq, as, xs);
 
   if (kap < K) {
+    uint8_t pf = 0;
+    if (SVD)
+      for (int k = 0; k < J; ++k) pf |= A.pflag[(size_t)k * K + kap];
     const float num = pickf(as, a), den = pickf(xs, a);
-    float sv = ok ? num / den : __int_as_float(0x7fc00000);
+    const bool valid = ok && !(pf & TS_FLAG_TIMEOUT);
+    const float sv = valid ? num / den : __int_as_float(0x7fc00000);
     if (a < L) A.sinr[((size_t)i * K + kap) * L + a] = sv;
     if (A.flags != nullptr && a == 0) {
       uint8_t f = ok ? 0 : TS_FLAG_NOT_PD;
-      if (ok && !isfinite(sv)) f |= TS_FLAG_NONFINITE;
-      if (SVD)
-        for (int k = 0; k < J; ++k) f |= A.pflag[(size_t)k * K + kap];
-      A.flags[(size_t)i * K + kap] = f;
+      if (valid && !isfinite(sv)) f |= TS_FLAG_NONFINITE;
+      A.flags[(size_t)i * K + kap] = f | pf;
     }
   }
 }

@@ -21,7 +21,10 @@ LIB_PATH = os.path.join(_PKG, "libtuckersinr.so")
 TS_COEF_DENSE, TS_COEF_PATHS = 0, 1
 TS_OP_SINR_SVD, TS_OP_SINR_MMSE, TS_OP_DENSE_SVD, TS_OP_DENSE_MMSE = 0, 1, 2, 3
 TS_OP_SINR_SVD_ADJOINT, TS_OP_SINR_MMSE_ADJOINT, TS_OP_TUCKER_FIT = 4, 5, 6
+TS_OP_SINR_SVD_TF32, TS_OP_SINR_SVD_BF16X2 = 7, 8
+TS_PREC_FP32, TS_PREC_TF32, TS_PREC_BF16X2 = 0, 1, 2
 TS_FLAG_NOT_PD, TS_FLAG_NONFINITE, TS_FLAG_RANK_DEFICIENT, TS_FLAG_EIG_UNCONVERGED = 1, 2, 4, 8
+TS_FLAG_TIMEOUT = 16
 
 
 class TsError(RuntimeError):
@@ -78,6 +81,11 @@ _SIG = {
                                         _P, ctypes.c_size_t, _P]),
     "ts_sinr_svd_from_precoders": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.POINTER(ts_coef),
                                                   _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
+    "ts_sinr_svd_prec": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.POINTER(ts_coef), _P, _P, _P,
+                                        ctypes.c_int, _P, _P, _P, ctypes.c_size_t, _P]),
+    "ts_sinr_svd_from_precoders_prec": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.POINTER(ts_coef),
+                                                       _P, _P, _P, ctypes.c_int, _P, _P, _P,
+                                                       ctypes.c_size_t, _P]),
 }
 
 _lib = None
@@ -193,6 +201,24 @@ def ts_sinr_svd(d: Dims, coef: ts_coef, G, C, sigma2, sinr, flags, ws, stream=No
     _check("ts_sinr_svd", lib.ts_sinr_svd(ctypes.byref(d.c()), ctypes.byref(coef), _ptr(G), _ptr(C),
                                           _ptr(sigma2), _ptr(sinr), _ptr(flags), _ptr(ws),
                                           ws.numel(), _stream(stream)))
+
+
+def ts_sinr_svd_prec(d: Dims, coef: ts_coef, G, C, sigma2, precision: int, sinr, flags, ws,
+                     stream=None):
+    lib = load()
+    _check("ts_sinr_svd_prec",
+           lib.ts_sinr_svd_prec(ctypes.byref(d.c()), ctypes.byref(coef), _ptr(G), _ptr(C), _ptr(sigma2),
+                                int(precision), _ptr(sinr), _ptr(flags), _ptr(ws), ws.numel(),
+                                _stream(stream)))
+
+
+def ts_sinr_svd_from_precoders_prec(d: Dims, coef: ts_coef, G, C, sigma2, precision: int, sinr, flags,
+                                    ws, stream=None):
+    lib = load()
+    _check("ts_sinr_svd_from_precoders_prec",
+           lib.ts_sinr_svd_from_precoders_prec(ctypes.byref(d.c()), ctypes.byref(coef), _ptr(G), _ptr(C),
+                                               _ptr(sigma2), int(precision), _ptr(sinr), _ptr(flags),
+                                               _ptr(ws), ws.numel(), _stream(stream)))
 
 
 def ts_tucker_fit(d: Dims, X, S, init, A, B, C, G, g_hist, ws, stream=None):

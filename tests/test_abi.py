@@ -64,7 +64,28 @@ def test_workspace_sizes(lib):
     assert svd >= nch * P * 8 + 2 * K * n * L * 8 + 2 * K
     assert mmse >= nch * P * 8 + nch * p * m * L * 8
     assert svd % 256 == 0 and mmse % 256 == 0
+    assert lib.ts_workspace_bytes(ctypes.byref(d), 9) == 0
+    # tensor-core modes: the svd workspace plus the rewritten core (per link:
+    # TF32 2p K-elements of 4 bytes, BF16X2 6p of 2 bytes, per accumulator
+    # column 2 MG n)
+    tf32 = lib.ts_workspace_bytes(ctypes.byref(d), 7)
+    bf16 = lib.ts_workspace_bytes(ctypes.byref(d), 8)
+    assert tf32 >= svd + nch * (2 * m * n) * (2 * p) * 4
+    assert bf16 >= svd + nch * (2 * m * n) * (6 * p) * 2
+
+
+def test_tensor_core_modes_reject_unsupported_shapes(lib):
+    from paper_2401_09792_gb300 import tuckersinr as ts
+    d = _dims(M=16, m=16, L=16, N=32, n=16)
+    assert lib.ts_workspace_bytes(ctypes.byref(d), 0) > 0
     assert lib.ts_workspace_bytes(ctypes.byref(d), 7) == 0
+    coef = ts.ts_coef(0, 8, None, None)
+    # L > 8 and unknown precisions are refused before any launch
+    assert lib.ts_sinr_svd_prec(ctypes.byref(d), ctypes.byref(coef), 8, 8, 8, 1, 8, None, 256,
+                                1 << 30, None) == 6
+    d = _dims()
+    assert lib.ts_sinr_svd_prec(ctypes.byref(d), ctypes.byref(coef), 8, 8, 8, 5, 8, None, 256,
+                                1 << 30, None) == 6
 
 
 @pytest.mark.parametrize("bad", [dict(m=5), dict(L=5), dict(L=0), dict(m=17, M=17),
