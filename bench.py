@@ -220,7 +220,10 @@ def run_ours(args):
     coef, keep = ts.make_coef(alpha=dv["alpha"], tau=dv["tau"])
     sinr = torch.empty(J, K, L, device=dev)
     flags = torch.empty(J, K, dtype=torch.uint8, device=dev)
-    ws = ts.workspace(d, ts.TS_OP_SINR_SVD, dev)
+    prec_id = {"fp32": ts.TS_PREC_FP32, "tf32": ts.TS_PREC_TF32, "bf16x2": ts.TS_PREC_BF16X2}[args.precision]
+    ws_op = {"fp32": ts.TS_OP_SINR_SVD, "tf32": ts.TS_OP_SINR_SVD_TF32,
+             "bf16x2": ts.TS_OP_SINR_SVD_BF16X2}[args.precision]
+    ws = ts.workspace(d, ws_op, dev)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
@@ -232,12 +235,15 @@ def run_ours(args):
         if e1 is not None:
             e1.record(stream)
         ts.ts_set_timing_events(k0, k1)
-        ts.ts_sinr_svd_from_precoders(d, coef, dv["G"], dv["C"], dv["sigma2"], sinr, flags, ws, stream)
+        ts.ts_sinr_svd_from_precoders_prec(d, coef, dv["G"], dv["C"], dv["sigma2"], prec_id, sinr, flags,
+                                           ws, stream)
         ts.ts_set_timing_events(None, None)
         if e2 is not None:
             e2.record(stream)
 
-    launches_per_step = 4            # path phase steps, precoders (with the serving links), links, finalize
+    # path phase steps, precoders (with the serving links), links, finalize;
+    # tensor-core modes add the core rewrite (a memset and a kernel)
+    launches_per_step = 4 if prec_id == ts.TS_PREC_FP32 else 5
     for _ in range(args.warmup):
         flush.zero_()
         step()
@@ -267,14 +273,17 @@ def run_ours(args):
     total_ms = max_over_ranks(float(np.sum(step_ms)), world, dev)
     units = J * K
     value = whole_job_value(world, units, args.steps, total_ms)
-    assert int(flags.max().item()) == 0, "numerical flags raised in the timed steps"
+    assert int((flags & ts.TS_FLAG_ERRORS).max().item()) == 0, "numerical flags raised in the timed steps"
 
-    if args.step_only:
+    if args.step_only or prec_id != ts.TS_PREC_FP32:
         e2e_value = h2d = d2h = mm_ms = dense_value = dense_ms = dense_steps = None
+        prec = {}
     else:
         e2e_value, h2d, d2h, mm_ms, dense_value, dense_ms, dense_steps = _extras(
             args, ts, torch, dist, world, dev, w, tk, host, dv, coef, d, ws, sinr, flags, flush,
             stream, ev, units)
+        prec = _precision_variants(args, ts, torch, dev, w, dv, coef, d, sinr, flags, flush, stream,
+                                   ev, units)
     if rank != 0:
         if world > 1:
             dist.barrier()
@@ -282,7 +291,7 @@ def run_ours(args):
         return
     _report(args, ts, torch, world, dev, w, tk, alpha, tau, s2, d, coef, dv, ws, stream, units,
             value, total_ms, step_ms, link_ms, pre_ms, fin_ms, wall, clocks, launches_per_step,
-            e2e_value, h2d, d2h, mm_ms, dense_value, dense_ms, dense_steps)
+            e2e_value, h2d, d2h, mm_ms, dense_value, dense_ms, dense_steps, prec)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -363,17 +372,61 @@ def _extras(args, ts, torch, dist, world, dev, w, tk, host, dv, coef, d, ws, sin
     return e2e_value, h2d, d2h, mm_ms, dense_value, dense_ms, dense_steps
 
 
+def _precision_variants(args, ts, torch, dev, w, dv, coef, d, sinr, flags, flush, stream, ev, units):
+    """The same step with the interfering links' core contraction on the
+    tensor cores (TF32, BF16 hi+lo): throughput, link-pass time, and the
+    SINRs of one evaluation for the error report."""
+    out = {}
+    for name, prec, op in (("tf32", ts.TS_PREC_TF32, ts.TS_OP_SINR_SVD_TF32),
+                           ("bf16x2", ts.TS_PREC_BF16X2, ts.TS_OP_SINR_SVD_BF16X2)):
+        wsp = ts.workspace(d, op, dev)
+
+        def step(k0=None, k1=None):
+            ts.ts_svd_precoders(d, coef, dv["G"], dv["C"], wsp, stream)
+            ts.ts_set_timing_events(k0, k1)
+            ts.ts_sinr_svd_from_precoders_prec(d, coef, dv["G"], dv["C"], dv["sigma2"], prec, sinr,
+                                               flags, wsp, stream)
+            ts.ts_set_timing_events(None, None)
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        evs = [tuple(ev() for _ in range(4)) for _ in range(args.steps)]
+        for e in evs:
+            for x in e:
+                x.record(stream)      # create the events before the library records them
+        torch.cuda.synchronize()
+        for a, b, k0, k1 in evs:
+            flush.zero_()
+            a.record(stream)
+            step(k0, k1)
+            b.record(stream)
+        torch.cuda.synchronize()
+        total = float(np.sum([a.elapsed_time(b) for a, b, _, _ in evs]))
+        link = float(np.mean([k0.elapsed_time(k1) for _, _, k0, k1 in evs]))
+        assert int((flags & ts.TS_FLAG_ERRORS).max().item()) == 0, f"numerical flags raised in the {name} steps"
+        ts.ts_sinr_svd_prec(d, coef, dv["G"], dv["C"], dv["sigma2"], prec, sinr, None, wsp, stream)
+        torch.cuda.synchronize()
+        out[name] = {"value": units * args.steps / (total * 1e-3), "ms_per_step": total / args.steps,
+                     "link_ms": round(link, 5),
+                     "sinr": sinr.cpu().numpy().astype(np.float64)}
+        del wsp
+    return out
+
+
 def _report(args, ts, torch, world, dev, w, tk, alpha, tau, s2, d, coef, dv, ws, stream, units,
             value, total_ms, step_ms, link_ms, pre_ms, fin_ms, wall, clocks, launches_per_step,
-            e2e_value, h2d, d2h, mm_ms, dense_value, dense_ms, dense_steps):
+            e2e_value, h2d, d2h, mm_ms, dense_value, dense_ms, dense_steps, prec):
     pk = peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
     fp32_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12       # TFLOP/s, FFMA on every lane
     link_mean = float(np.mean(link_ms))
     achieved = link_flops(w, "svd") / (link_mean * 1e-3) / 1e12
-    traffic = recorded_traffic("k_sinr_link_blk", "mid")
-    roofline = {"kernel": "k_sinr_link_blk (svd)", "bound": "alu", "achieved": round(achieved, 3),
+    traffic = (recorded_traffic("k_sinr_link_blk", "mid") if args.precision == "fp32"
+               else recorded_traffic(f"k_sinr_link_tc_{args.precision}", "mid"))
+    kname = "k_sinr_link_blk (svd)" if args.precision == "fp32" else f"k_sinr_link_tc ({args.precision})"
+    roofline = {"kernel": kname, "bound": "alu", "achieved": round(achieved, 3),
                 "peak": round(fp32_peak, 2), "unit": "TFLOP/s", "frac": round(achieved / fp32_peak, 4),
                 "traffic": traffic,
                 "peak_basis": f"FP32 FFMA: {sms} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz "
@@ -385,7 +438,9 @@ def _report(args, ts, torch, world, dev, w, tk, alpha, tau, s2, d, coef, dv, ws,
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else f"f32 ({args.precision} core contraction)",
+        "data": "synthetic",
         "config": {**workload_config(w), "parallelism": f"independent systems x{world}"},
         "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d,
@@ -397,7 +452,12 @@ def _report(args, ts, torch, world, dev, w, tk, alpha, tau, s2, d, coef, dv, ws,
                       "links": round(link_mean, 5)},
         "variants": None if mm_ms is None else {
             "mmse_wideband_precoder": {"value": units * args.steps / (mm_ms * 1e-3),
-                                       "ms_per_step": mm_ms / args.steps}},
+                                       "ms_per_step": mm_ms / args.steps},
+            **{f"svd_{k}": {"value": v["value"], "ms_per_step": v["ms_per_step"],
+                            "link_ms": v["link_ms"],
+                            "what": "interfering links' core contraction on the tensor cores "
+                                    f"({k}), everything else FP32"}
+               for k, v in prec.items()}},
         "dense_comparator": None if dense_ms is None else {
             "value": dense_value, "unit": METRIC, "ms_per_step": dense_ms / dense_steps,
             "what": "same SVD-precoded SINR from the uncompressed channels "
@@ -405,12 +465,16 @@ def _report(args, ts, torch, world, dev, w, tk, alpha, tau, s2, d, coef, dv, ws,
             "tucker_over_dense": value / world / dense_value},
         "wall_s_timed_region": round(wall, 4),
     }
-    if args.step_only:
+    if args.step_only or args.precision != "fp32":
         for key in ("e2e", "variants", "dense_comparator"):
             line.pop(key)
     if world == 1 and not args.no_cpu_baseline:
-        gpu_out = _gpu_svd_sinr(ts, d, coef, dv, ws, stream)
-        line["cpu_baseline"], line["sinr_err"] = cpu_baseline(w, tk, alpha, tau, s2, gpu_out)
+        gpu_out = {"fp32": _gpu_svd_sinr(ts, d, coef, dv, ws, stream)}
+        gpu_out.update({k: v["sinr"] for k, v in prec.items()})
+        line["cpu_baseline"], errs = cpu_baseline(w, tk, alpha, tau, s2, gpu_out)
+        line["sinr_err"] = errs.pop("fp32", None)
+        for k, e in errs.items():
+            line["variants"][f"svd_{k}"]["sinr_err"] = e
     print(json.dumps(line), flush=True)
 
 
@@ -425,18 +489,21 @@ def _gpu_svd_sinr(ts, d, coef, dv, ws, stream):
 
 def cpu_baseline(w, tk, alpha, tau, s2, gpu_sinr=None, budget_s=12.0, kslice=128):
     """The FP64 oracle, as it stands, on subcarrier slices of the same system,
-    for about `budget_s` seconds; also the GPU result's error on those slices."""
+    for about `budget_s` seconds; also the error of each GPU result
+    (`gpu_sinr`: name -> SINR array) on those slices."""
     from oracle import sinr as S
     J = w.J
     coef = S.coefficients(alpha, tau, w.K, w.delta_f_hz)
     t0 = time.perf_counter()
     c0 = time.process_time()
-    done, errs, start, passes = 0, [], 0, 0
+    gpu_sinr = gpu_sinr or {}
+    done, errs, start, passes = 0, {k: [] for k in gpu_sinr}, 0, 0
     while time.perf_counter() - t0 < budget_s:
         sl = slice(start, min(start + kslice, w.K))
         ref = S.tucker_sinr(tk["G"], tk["C"], coef[:, :, sl], s2, w.L, "svd")
-        if gpu_sinr is not None and passes == 0:
-            errs.append(np.abs(gpu_sinr[:, sl] - ref) / np.abs(ref))
+        if passes == 0:
+            for k, g in gpu_sinr.items():
+                errs[k].append(np.abs(g[:, sl] - ref) / np.abs(ref))
         done += J * (sl.stop - sl.start)
         start = sl.stop
         if start >= w.K:
@@ -448,13 +515,15 @@ def cpu_baseline(w, tk, alpha, tau, s2, gpu_sinr=None, budget_s=12.0, kslice=128
             "sample": f"FP64 NumPy oracle, svd SINR of the same system in slices of "
                       f"{kslice} subcarriers, repeated for {wall:.1f} s wall ({done} "
                       f"subcarrier-SINRs; {os.cpu_count()} host cores visible)"}
-    err = None
-    if errs:
-        e = np.concatenate([x.ravel() for x in errs])
-        err = {"max_rel": float(e.max()), "p99_rel": float(np.percentile(e, 99)),
-               "median_rel": float(np.median(e)), "n": int(e.size),
-               "vs": "FP64 oracle on the cpu_baseline subcarriers"}
-    return base, err
+    out = {}
+    for k, lst in errs.items():
+        if not lst:
+            continue
+        e = np.concatenate([x.ravel() for x in lst])
+        out[k] = {"max_rel": float(e.max()), "p99_rel": float(np.percentile(e, 99)),
+                  "median_rel": float(np.median(e)), "n": int(e.size),
+                  "vs": "FP64 oracle on the cpu_baseline subcarriers"}
+    return base, out
 
 
 # ------------------------------------------------------------ reference arm
@@ -508,6 +577,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--step-only", action="store_true",
                     help="time only the SVD step (no end-to-end, variant or comparator runs)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16x2"],
+                    help="arithmetic of the interfering links' core contraction in the timed step "
+                         "(fp32: FMA pipe; tf32, bf16x2: tensor cores); implies --step-only")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -84,8 +84,11 @@ enum {
   TS_FLAG_RANK_DEFICIENT = 4, /* a serving link had a zero singular value
                                  among the top L (SVD precoding)              */
   TS_FLAG_EIG_UNCONVERGED = 8, /* the Jacobi eigensolver hit its sweep cap    */
-  TS_FLAG_TIMEOUT = 16        /* a bounded device wait of the tensor-core pass
+  TS_FLAG_TIMEOUT = 16,       /* a bounded device wait of the tensor-core pass
                                  gave up; the unit's SINR is NaN             */
+  TS_FLAG_REFINED = 32        /* informational: cond(R) was above the
+                                 refinement threshold and the SINR comes from
+                                 the FP64-residual refinement of the solves  */
 };
 
 /* Operations, for ts_workspace_bytes. */
@@ -129,6 +132,15 @@ int ts_abi_version(void);
  * before and right after their dominant kernel (the per-link rebuild and
  * covariance kernel).  NULL, NULL turns it off.  Not used otherwise. */
 void ts_set_timing_events(void* start, void* stop);
+
+/* Mixed-precision refinement of ill-conditioned solves (eq. 26-28): SINR
+ * calls on this host thread whose FP32 Cholesky factor of the
+ * interference-plus-noise covariance R shows cond(R) > cond_threshold
+ * (estimated from its diagonal) recompute that unit's solves with
+ * residuals accumulated in FP64 (two refinement steps of R^{-1} E_ii, then
+ * the L x L system in FP64) and set TS_FLAG_REFINED.  Default 1e3; a
+ * negative threshold turns refinement off. */
+void ts_set_refinement(float cond_threshold);
 
 /* Device workspace, in bytes, that operation `op` needs for sizes `d`.
  * Returns 0 for invalid sizes.  The caller allocates it (256-byte aligned)

@@ -7,6 +7,8 @@
 #include "kernels.h"
 #include "tuckersinr.h"
 
+#include <math.h>
+
 namespace {
 
 thread_local int g_last_cuda = 0;
@@ -14,6 +16,17 @@ thread_local int g_last_cuda = 0;
 // next SINR calls on this host thread (ts_set_timing_events)
 thread_local cudaEvent_t g_ev_start = nullptr;
 thread_local cudaEvent_t g_ev_stop = nullptr;
+// condition number of R above which a unit's solves are refined with FP64
+// residuals (ts_set_refinement); infinity turns refinement off
+thread_local float g_refine_cond = 1e3f;
+
+// Finalisation, then the FP64-residual refinement of the units it listed.
+cudaError_t finalize_refined(const ts::SinrArgs& a, bool svd, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(a.rcount, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = ts::launch_sinr_finalize(a, svd, s);
+  if (e == cudaSuccess && a.refine_cond < INFINITY) e = ts::launch_sinr_refine(a, svd, s);
+  return e;
+}
 
 // The per-link kernel (the dominant one) bracketed by the timing events,
 // then the finalisation.
@@ -22,7 +35,7 @@ cudaError_t links_then_finalize(const ts::SinrArgs& a, bool svd, cudaStream_t s)
   if (g_ev_start != nullptr) e = cudaEventRecord(g_ev_start, s);
   if (e == cudaSuccess) e = ts::launch_sinr_links(a, svd, s);
   if (e == cudaSuccess && g_ev_stop != nullptr) e = cudaEventRecord(g_ev_stop, s);
-  if (e == cudaSuccess) e = ts::launch_sinr_finalize(a, svd, s);
+  if (e == cudaSuccess) e = finalize_refined(a, svd, s);
   return e;
 }
 
@@ -54,7 +67,8 @@ int check_dims(const ts_dims* d) {
 
 // Workspace layout (byte offsets from the base, each 256-byte aligned).
 struct Workspace {
-  size_t turns = 0, V = 0, Hserv = 0, Eserv = 0, Rpart = 0, pflag = 0, F = 0, total = 0;
+  size_t turns = 0, V = 0, Hserv = 0, Eserv = 0, Rpart = 0, pflag = 0, F = 0, rlist = 0,
+         rcount = 0, total = 0;
 };
 
 Workspace carve(const ts_dims* d, int op) {
@@ -80,6 +94,10 @@ Workspace carve(const ts_dims* d, int op) {
     w.F = o;
     o = align_up(o + nch * d->p * d->m * d->L * sizeof(float2), 256);
   }
+  w.rlist = o;
+  o = align_up(o + (size_t)d->J * d->K * sizeof(int), 256);
+  w.rcount = o;
+  o = align_up(o + sizeof(int), 256);
   w.total = o;
   return w;
 }
@@ -87,7 +105,7 @@ Workspace carve(const ts_dims* d, int op) {
 // Reduced-precision workspace: the ts_sinr_svd workspace, then the core
 // rewritten as a tensor-core operand.
 size_t prec_workspace_bytes(const ts_dims* d, int prec) {
-  return carve(d, TS_OP_SINR_SVD).total + ts::tc_prep_bytes(d->J, d->m, d->L, d->n, d->p, prec);
+  return carve(d, TS_OP_SINR_SVD).total + ts::tc_prep_bytes(d->J, d->m, d->L, d->n, d->p, d->K, prec);
 }
 
 // Adjoint workspace (byte offsets, each 256-byte aligned).
@@ -166,6 +184,9 @@ ts::SinrArgs base_args(const ts_dims* d, const ts_coef* coef, const ts_c64* G, c
   a.sigma2 = sigma2;
   a.sinr = sinr;
   a.flags = flags;
+  a.rlist = reinterpret_cast<int*>(ws + w.rlist);
+  a.rcount = reinterpret_cast<int*>(ws + w.rcount);
+  a.refine_cond = g_refine_cond;
   return a;
 }
 
@@ -197,6 +218,10 @@ int ts_abi_version(void) { return 1; }
 void ts_set_timing_events(void* start, void* stop) {
   g_ev_start = static_cast<cudaEvent_t>(start);
   g_ev_stop = static_cast<cudaEvent_t>(stop);
+}
+
+void ts_set_refinement(float cond_threshold) {
+  g_refine_cond = cond_threshold < 0.f ? INFINITY : cond_threshold;
 }
 
 size_t ts_workspace_bytes(const ts_dims* d, int op) {
@@ -451,7 +476,7 @@ int svd_from_precoders_prec_impl(const ts_dims* d, const ts_coef* coef, const ts
   if (e == cudaSuccess && g_ev_start != nullptr) e = cudaEventRecord(g_ev_start, s);
   if (e == cudaSuccess) e = ts::launch_sinr_links_tc(a, prec, prep, s);
   if (e == cudaSuccess && g_ev_stop != nullptr) e = cudaEventRecord(g_ev_stop, s);
-  if (e == cudaSuccess) e = ts::launch_sinr_finalize(a, true, s);
+  if (e == cudaSuccess) e = finalize_refined(a, true, s);
   return cuda_status(e);
 }
 

@@ -32,6 +32,9 @@ struct SinrArgs {
   const float* sigma2;              // [J]
   float* sinr;                      // [J][K][L]
   uint8_t* flags;                   // [J][K] or nullptr
+  int* rlist;                       // units (i K + kappa) to refine (workspace) or nullptr
+  int* rcount;                      // length of rlist (workspace, zeroed before finalize)
+  float refine_cond;                // refine when the Cholesky diagonal gives cond(R) above this
 };
 
 // Launchers; each picks the template instance for (m, L) and returns the
@@ -47,6 +50,8 @@ cudaError_t launch_mmse_fold(const float2* G, const float2* Pt, int J, int m, in
 cudaError_t launch_svd_precoder(const SinrArgs& a, cudaStream_t s);
 cudaError_t launch_sinr_links(const SinrArgs& a, bool svd, cudaStream_t s);
 cudaError_t launch_sinr_finalize(const SinrArgs& a, bool svd, cudaStream_t s);
+// FP64-residual refinement of the units the finalize kernel listed (refine.cu)
+cudaError_t launch_sinr_refine(const SinrArgs& a, bool svd, cudaStream_t s);
 
 // Buffers of the adjoint pipeline (adjoint.cu); Pt == nullptr selects SVD
 // precoders (read from SinrArgs::Vmout/Uout/Sout).
@@ -67,10 +72,11 @@ struct AdjointWork {
 cudaError_t launch_sinr_rebuild(const SinrArgs& a, cudaStream_t s);
 cudaError_t launch_sinr_serving(const SinrArgs& a, cudaStream_t s);
 // Tensor-core interfering-link pass (reduced-precision modes, sinr_tc.cu):
-// shape support, bytes of the rewritten core, the core rewrite into `prep`
-// (once per call), and the link kernel.
+// shape support, bytes of the operands (the rewritten core of every link,
+// then the projections of the interfering links' subcarrier tiles), their
+// preparation into `prep` (once per call), and the link kernel.
 bool tc_supported(int m, int L, int p);
-size_t tc_prep_bytes(int J, int m, int L, int n, int p, int prec);
+size_t tc_prep_bytes(int J, int m, int L, int n, int p, int K, int prec);
 cudaError_t launch_core_prep(const SinrArgs& a, int prec, void* prep, cudaStream_t s);
 cudaError_t launch_sinr_links_tc(const SinrArgs& a, int prec, const void* prep, cudaStream_t s);
 // The SVD precoder forms H~_kk itself (re-reading the core G_kk once per

@@ -1125,6 +1125,22 @@ __global__ void __launch_bounds__(kThreads) k_sinr_finalize(const SinrArgs A, in
   float2 Lq[MG], Zq[LT];
   float as[LT], xs[LT];
   const bool ok = sinr_core<MG, LT>(R, Eself, Es, a, Lq, Zq, as, xs);
+  // ill-conditioned R (cond from the Cholesky diagonal, a lower bound) ->
+  // listed for the FP64-residual refinement pass
+  if (A.rlist != nullptr) {
+    const float d = a < m ? pick(R, a).x : 1.f;
+    float dmax = a < m ? d : 0.f, dmin = a < m ? d : INFINITY;
+#pragma unroll
+    for (int o = 1; o < MG; o <<= 1) {
+      dmax = fmaxf(dmax, __shfl_xor_sync(FULL, dmax, o, MG));
+      dmin = fminf(dmin, __shfl_xor_sync(FULL, dmin, o, MG));
+    }
+    const float c = (dmax / dmin) * (dmax / dmin);
+    if (ok && kap < K && a == 0 && c > A.refine_cond) {
+      const int pos = atomicAdd(A.rcount, 1);
+      if (pos < A.J * K) A.rlist[pos] = i * K + kap;
+    }
+  }
 
   if (kap < K) {
     uint8_t pf = 0;

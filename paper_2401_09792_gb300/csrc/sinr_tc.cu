@@ -15,12 +15,16 @@
 // swizzle in shared memory: 8-row x 16-byte core matrices, K-adjacent ones
 // 128 bytes apart (LBO), row groups 128 * K_bytes / 16 bytes apart (SBO).
 //
-// Per CTA (tile, UE i, interfering BS k): the projection writes the A
-// operand; the core is consumed in column blocks of CB = 4 columns of H~
-// (N = 8 MG accumulator columns per block), each block's operand fetched by
-// one bulk copy (cp.async.bulk + mbarrier transaction count) and multiplied
-// by one thread into one of two TMEM buffers, one block ahead of the
-// epilogue; the precoder rows of the block are staged by cp.async.  The
+// Operands are prepared once per call: k_core_prep rewrites every link's
+// core, k_tc_proj computes the projections w = c* C (FP32) of every
+// interfering link and subcarrier tile and writes them rounded or split.
+// Per CTA (tile, UE i, interfering BS k): the projection operand arrives by
+// one bulk copy; the core is consumed in column blocks of CB columns of H~
+// (CB = 4 for m <= 4, else 2; N = 2 MG CB accumulator columns), each block's
+// operand fetched by one bulk copy (cp.async.bulk + mbarrier transaction
+// count) into a three-slot ring two blocks ahead, and multiplied by one
+// thread into one of two TMEM buffers one block ahead of the epilogue; the
+// precoder rows of the block are staged by cp.async two blocks ahead.  The
 // epilogue thread (row group g, subcarrier t) reads its RPT rows of the H~
 // block from TMEM (tcgen05.ld) and accumulates E rows; at the end the E rows
 // are exchanged through shared memory and the partial covariance rows
@@ -36,7 +40,7 @@ namespace detail {
 namespace {
 
 constexpr int kTile = 128;     // subcarriers per CTA = MMA M = TMEM lanes
-constexpr int kCB = 4;         // H~ columns per accumulator block
+constexpr int kBStages = 3;    // core-operand ring (loads run two blocks ahead)
 constexpr long kSpinLimit = 1L << 24;
 
 struct TcPlan {
@@ -47,9 +51,12 @@ struct TcPlan {
   int SV;          // precoder stage row stride (float2), per subcarrier
   int off_A, off_B, off_V, off_bar, smem;   // byte offsets
   size_t prep_bytes_per_link;               // k_core_prep output per link
+  size_t a_bytes_per_tile;                  // k_tc_proj output per (link, tile)
 };
 
 __host__ __device__ constexpr int tc_rpt(int MG) { return MG < 4 ? MG : 4; }
+// H~ columns per accumulator block (N = 2 MG CB accumulator columns)
+__host__ __device__ constexpr int tc_cb(int MG) { return MG >= 8 ? 2 : 4; }
 
 inline TcPlan tc_plan(int MG, int LT, int n, int p, int prec) {
   TcPlan t;
@@ -57,12 +64,13 @@ inline TcPlan tc_plan(int MG, int LT, int n, int p, int prec) {
   const int kused = prec == TS_PREC_TF32 ? 2 * p : 6 * p;
   const int kq = 32 / t.ES;                      // elements per 32 bytes
   t.Kpad = (kused + kq - 1) / kq * kq;
-  t.Ntile = 2 * MG * kCB;
-  t.nblk = (n + kCB - 1) / kCB;
-  t.SV = kCB * LT + 2;
+  const int CB = tc_cb(MG);
+  t.Ntile = 2 * MG * CB;
+  t.nblk = (n + CB - 1) / CB;
+  t.SV = CB * LT + 2;
   int o = 0;
   t.off_A = o; o += kTile * t.Kpad * t.ES;
-  t.off_B = o; o += 2 * t.Ntile * t.Kpad * t.ES;
+  t.off_B = o; o += kBStages * t.Ntile * t.Kpad * t.ES;
   t.off_V = o; o += 2 * kTile * t.SV * 8;
   // E exchange at the end reuses the front of the buffer
   const int ex = kTile * MG * (LT * 8) + kTile * 16;
@@ -71,6 +79,7 @@ inline TcPlan tc_plan(int MG, int LT, int n, int p, int prec) {
   t.off_bar = o; o += 64;
   t.smem = o;
   t.prep_bytes_per_link = (size_t)t.nblk * t.Ntile * t.Kpad * t.ES;
+  t.a_bytes_per_tile = (size_t)kTile * t.Kpad * t.ES;
   return t;
 }
 
@@ -97,23 +106,6 @@ __device__ __forceinline__ float to_tf32(float x) {
   return __uint_as_float(r);
 }
 
-template <int PREC>
-__device__ __forceinline__ void store_split(unsigned char* base, int r, int k, int kused_seg,
-                                            int kbytes, float x, bool a_side) {
-  // TF32: one element at k.  BF16X2: segments [hi | lo | hi] (A side) or
-  // [hi | hi | lo] (B side), each kused_seg wide.
-  if (PREC == TS_PREC_TF32) {
-    *reinterpret_cast<float*>(base + kmajor_off(r, k * 4, kbytes)) = to_tf32(x);
-  } else {
-    const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-    const __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
-    const __nv_bfloat16 s1 = a_side ? lo : hi, s2 = a_side ? hi : lo;
-    *reinterpret_cast<__nv_bfloat16*>(base + kmajor_off(r, k * 2, kbytes)) = hi;
-    *reinterpret_cast<__nv_bfloat16*>(base + kmajor_off(r, (k + kused_seg) * 2, kbytes)) = s1;
-    *reinterpret_cast<__nv_bfloat16*>(base + kmajor_off(r, (k + 2 * kused_seg) * 2, kbytes)) = s2;
-  }
-}
-
 // bounded wait on an mbarrier phase; false on timeout
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   for (long it = 0; it < kSpinLimit; ++it) {
@@ -129,48 +121,181 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 // ------------------------------------------------------------ core operand
 // B operand of link ch, column block b, in the canonical layout: row
 // j = ((g CB + c) RPT + a_in) 2 + ri of the block (row a = g RPT + a_in,
-// column c0 + c of H~), k over [Re w | Im w] (x3 segments for BF16X2).
+// column c0 + c of H~), k over [Re w | Im w] (x3 segments for BF16X2):
+//   re row: [Re G ; -Im G],   im row: [Im G ; Re G]
+// (BF16X2: segments [hi | hi | lo]).  One thread writes one 16-byte chunk;
+// eight consecutive threads fill one 128-byte core matrix; padding is zero.
 template <int PREC>
-__global__ void k_core_prep(const float2* __restrict__ G, int nch, int m, int n, int p, int MG,
-                            int Ntile, int Kpad, int nblk, unsigned char* __restrict__ out) {
-  const int ES = PREC == TS_PREC_TF32 ? 4 : 2;
-  const int kbytes = Kpad * ES;
-  const int RPT = tc_rpt(MG);
-  const size_t per_block = (size_t)Ntile * kbytes;
-  const size_t total = (size_t)nch * nblk * Ntile * (2 * p);   // (row, k < 2p) pairs
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const int k = (int)(idx % (2 * p));
-    size_t rest = idx / (2 * p);
-    const int j = (int)(rest % Ntile);
-    rest /= Ntile;
-    const int b = (int)(rest % nblk);
-    const int ch = (int)(rest / nblk);
+__global__ void __launch_bounds__(256) k_core_prep(const float2* __restrict__ G, int m, int n, int p,
+                                                   int MG, int Ntile, int Kpad, int nblk, int nblocks,
+                                                   unsigned char* __restrict__ out) {
+  // y = ch * nblk + b: one operand block; threads over its chunks
+  constexpr int ES = PREC == TS_PREC_TF32 ? 4 : 2;
+  constexpr int EPC = 16 / ES;
+  const int kbytes = Kpad * ES, nkc = kbytes / 16;
+  const int RPT = tc_rpt(MG), CB = tc_cb(MG);
+  const int p2 = 2 * p, kused = PREC == TS_PREC_TF32 ? p2 : 3 * p2;
+  const int nchunk = Ntile * nkc;
+  for (int y = blockIdx.y; y < nblocks; y += gridDim.y)
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nchunk; idx += gridDim.x * blockDim.x) {
+    const int ch = y / nblk, b = y - ch * nblk;
+    unsigned char* blk = out + (size_t)y * Ntile * kbytes;
+    const int r = idx & 7, rest = idx >> 3;
+    const int rg = rest / nkc, kc = rest - rg * nkc;
+    const int j = rg * 8 + r;
     const int ri = j & 1, a_in = (j >> 1) % RPT, cg = (j >> 1) / RPT;
-    const int c = b * kCB + cg % kCB, g = cg / kCB;
-    const int a = g * RPT + a_in;
-    float x = 0.f;
-    if (a < m && c < n) {
-      const int q = k < p ? k : k - p;
-      const float2 gv = G[(((size_t)ch * p + q) * m + a) * n + c];
-      // re column: [Re G ; -Im G], im column: [Im G ; Re G]
-      x = ri == 0 ? (k < p ? gv.x : -gv.y) : (k < p ? gv.y : gv.x);
+    const int c = b * CB + cg % CB, a = (cg / CB) * RPT + a_in;
+    const bool live = a < m && c < n;
+    const float2* gcol = G + ((size_t)ch * p * m + a) * n + c;     // + q m n
+    float2 gv[EPC];
+#pragma unroll
+    for (int e = 0; e < EPC; ++e) {
+      int kk = kc * EPC + e;
+      kk = kk >= 2 * p2 ? kk - 2 * p2 : kk >= p2 ? kk - p2 : kk;
+      const int q = kk < p ? kk : kk - p;
+      gv[e] = live && kc * EPC + e < kused ? __ldg(gcol + (size_t)q * m * n) : cz();
     }
-    unsigned char* blk = out + ((size_t)ch * nblk + b) * per_block;
-    store_split<PREC>(blk, j, k, 2 * p, kbytes, x, false);
+    float x[EPC];
+#pragma unroll
+    for (int e = 0; e < EPC; ++e) {
+      const int k = kc * EPC + e;
+      const int kk = k >= 2 * p2 ? k - 2 * p2 : k >= p2 ? k - p2 : k;
+      // re row: [Re G ; -Im G], im row: [Im G ; Re G]
+      float v = ri == 0 ? (kk < p ? gv[e].x : -gv[e].y) : (kk < p ? gv[e].y : gv[e].x);
+      if (PREC == TS_PREC_BF16X2 && k >= 2 * p2) v -= __bfloat162float(__float2bfloat16_rn(v));
+      x[e] = v;
+    }
+    uint32_t words[4];
+    if (PREC == TS_PREC_TF32) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) words[e] = __float_as_uint(to_tf32(x[e % EPC]));
+    } else {
+#pragma unroll
+      for (int w = 0; w < 4; ++w)
+        words[w] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[(2 * w) % EPC])) |
+                   ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[(2 * w + 1) % EPC])) << 16);
+    }
+    *reinterpret_cast<uint4*>(blk + kmajor_off(j, kc * 16, kbytes)) =
+        make_uint4(words[0], words[1], words[2], words[3]);
   }
-  // padding of K beyond the used segments is zeroed by the host (memset)
+}
+
+// ------------------------------------------------------ projection operand
+// A operand of (interfering link (i, k), subcarrier tile): row t =
+// subcarrier kap0 + t, k over [Re w | Im w] with w = C_ik^T conj(c_ik(kappa))
+// (eq. 15) in FP32, then rounded to TF32 or split [hi | lo | hi] in BF16, in
+// the canonical K-major layout.  The coefficients of a chunk of 32 paths are
+// evaluated once per (subcarrier, path) into shared memory; thread (t, h)
+// accumulates w_q for q in [8 h, 8 h + 8).  The rows are then written as
+// 16-byte chunks (eight consecutive threads fill one 128-byte core matrix);
+// rows beyond K are zero.
+constexpr int kProjPC = 32;
+
+constexpr int kProjQ = 8;      // projections w_q per thread
+
+template <int PREC>
+__global__ void __launch_bounds__(4 * kTile) k_tc_proj(const SinrArgs A, int Kpad, unsigned char* __restrict__ out) {
+  constexpr int ES = PREC == TS_PREC_TF32 ? 4 : 2;
+  constexpr int EPC = 16 / ES;                  // elements per 16-byte chunk
+  extern __shared__ __align__(16) unsigned char smp[];
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int t = tid % kTile, h = tid / kTile;
+  const int i = blockIdx.y, z = blockIdx.z;
+  const int kap0 = blockIdx.x * kTile;
+  const int J = A.J, p = A.p, P = A.P, K = A.K;
+  const int k = z < i ? z : z + 1;
+  const int ch = i * J + k;
+  const int kbytes = Kpad * ES, nkc = kbytes / 16;
+  const int WS = 2 * p + 1;
+  float* wrow = reinterpret_cast<float*>(smp);                        // [kTile][2p + 1]
+  float2* cs = reinterpret_cast<float2*>(smp + ((kTile * WS * 4 + 15) & ~15));   // [kTile][PC + 1]
+  float2* sC = cs + kTile * (kProjPC + 1);                            // [PC][p] chunk of C_ik
+  const float2* Cch = A.C + (size_t)ch * P * p;
+  float2 acc[kProjQ];
+#pragma unroll
+  for (int u = 0; u < kProjQ; ++u) acc[u] = cz();
+  for (int P0 = 0; P0 < P; P0 += kProjPC) {
+    const int pc = min(kProjPC, P - P0);
+    __syncthreads();
+    for (int idx = tid; idx < pc * p; idx += nth) sC[idx] = Cch[(size_t)P0 * p + idx];
+    for (int idx = tid; idx < kTile * kProjPC; idx += nth) {
+      const int tt = idx / kProjPC, pp = idx % kProjPC;
+      const int kap = kap0 + tt;
+      float2 c = cz();
+      if (pp < pc && kap < K)
+        c = A.coef_mode == 0 ? A.coef[((size_t)ch * K + kap) * P + P0 + pp]
+                             : path_coef(A.coef[(size_t)ch * P + P0 + pp], A.turns[(size_t)ch * P + P0 + pp], kap);
+      cs[tt * (kProjPC + 1) + pp] = c;
+    }
+    __syncthreads();
+    const float2* crow_t = cs + t * (kProjPC + 1);
+    for (int pp = 0; pp < pc; ++pp) {
+      const float2 c = crow_t[pp];
+      const float2* Crow = sC + pp * p + kProjQ * h;
+#pragma unroll
+      for (int u = 0; u < kProjQ; ++u)
+        if (kProjQ * h + u < p) cmacc(acc[u], Crow[u], c);
+    }
+  }
+  float* wr = wrow + t * WS;
+#pragma unroll
+  for (int u = 0; u < kProjQ; ++u) {
+    const int q = kProjQ * h + u;
+    if (q < p) {
+      wr[q] = acc[u].x;
+      wr[p + q] = acc[u].y;
+    }
+  }
+  __syncthreads();
+  const int kused = PREC == TS_PREC_TF32 ? 2 * p : 6 * p;
+  unsigned char* dst = out + (((size_t)i * (J - 1) + z) * gridDim.x + blockIdx.x) * (size_t)kTile * kbytes;
+  const int p2 = 2 * p;
+  for (int idx = tid; idx < kTile * nkc; idx += nth) {
+    const int r = idx & 7, rest = idx >> 3;
+    const int rg = rest / nkc, kc = rest - rg * nkc;
+    const int row = rg * 8 + r;
+    const float* src = wrow + row * WS;
+    uint32_t words[4];
+    if (PREC == TS_PREC_TF32) {
+#pragma unroll
+      for (int e = 0; e < EPC; ++e) {
+        const int kk = kc * EPC + e;
+        words[e] = __float_as_uint(kk < kused ? to_tf32(src[kk]) : 0.f);
+      }
+    } else {
+      __nv_bfloat16 hv[8];
+#pragma unroll
+      for (int e = 0; e < EPC; ++e) {
+        const int kk = kc * EPC + e;
+        __nv_bfloat16 v = __float2bfloat16_rn(0.f);
+        if (kk < kused) {
+          const int seg = kk >= 2 * p2 ? 2 : kk >= p2 ? 1 : 0;
+          const float x = src[kk - seg * p2];
+          const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+          v = seg == 1 ? __float2bfloat16_rn(x - __bfloat162float(hi)) : hi;
+        }
+        hv[e] = v;
+      }
+#pragma unroll
+      for (int w = 0; w < 4; ++w)
+        words[w] = (uint32_t)__bfloat16_as_ushort(hv[2 * w]) | ((uint32_t)__bfloat16_as_ushort(hv[2 * w + 1]) << 16);
+    }
+    *reinterpret_cast<uint4*>(dst + kmajor_off(row, kc * 16, kbytes)) =
+        make_uint4(words[0], words[1], words[2], words[3]);
+  }
 }
 
 // ----------------------------------------------------------- link kernel
 template <int MG, int LT, int PREC>
 __global__ void __launch_bounds__(128 * (MG / tc_rpt(MG)))
-    k_sinr_link_tc(const SinrArgs A, const unsigned char* __restrict__ prep, TcPlan tp) {
+    k_sinr_link_tc(const SinrArgs A, const unsigned char* __restrict__ prep,
+                   const unsigned char* __restrict__ aop, TcPlan tp) {
   constexpr int RPT = tc_rpt(MG);
   constexpr int RG = MG / RPT;
   constexpr int NT = 128 * RG;
   constexpr int ES = PREC == TS_PREC_TF32 ? 4 : 2;
   constexpr int KMMA = 32 / ES;                 // K elements per MMA instruction
+  constexpr int kCB = tc_cb(MG);
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
@@ -178,7 +303,7 @@ __global__ void __launch_bounds__(128 * (MG / tc_rpt(MG)))
   const int g = warp / 4, t = (warp % 4) * 32 + lane;    // row group, subcarrier of the tile
   const int i = blockIdx.y, z = blockIdx.z;
   const int kap0 = blockIdx.x * kTile;
-  const int J = A.J, m = A.m, n = A.n, p = A.p, L = A.L, K = A.K, P = A.P;
+  const int J = A.J, m = A.m, n = A.n, L = A.L, K = A.K;
   const int k = z < i ? z : z + 1;
   const int ch = i * J + k;
   const int kbytes = tp.Kpad * ES;
@@ -186,15 +311,18 @@ __global__ void __launch_bounds__(128 * (MG / tc_rpt(MG)))
   unsigned char* sA = smem + tp.off_A;
   unsigned char* sB = smem + tp.off_B;
   float2* sV = reinterpret_cast<float2*>(smem + tp.off_V);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + tp.off_bar);   // [0,1] B loads, [2,3] MMA
-  const uint32_t bar_b0 = smem_u32(&bars[0]), bar_m0 = smem_u32(&bars[2]);
+  // mbarriers: [0, kBStages) core-operand loads, two MMA completions, the
+  // projection operand
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + tp.off_bar);
+  const uint32_t bar_b0 = smem_u32(&bars[0]), bar_m0 = smem_u32(&bars[kBStages]);
+  const uint32_t bar_a = smem_u32(&bars[kBStages + 2]);
   const size_t blk_bytes = (size_t)tp.Ntile * kbytes;
   const unsigned char* prep_ch = prep + (size_t)ch * nblk * blk_bytes;
   const bool wideV = (L % 2 == 0) && ((reinterpret_cast<uintptr_t>(A.V) & 15u) == 0);
 
   if (tid == 0) {
     abort_flag = 0;
-    for (int s = 0; s < 4; ++s)
+    for (int s = 0; s < kBStages + 3; ++s)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[s])));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -206,23 +334,25 @@ __global__ void __launch_bounds__(128 * (MG / tc_rpt(MG)))
   }
   __syncthreads();
 
-  // block loads: the B operand by one bulk copy (tid 0), the precoder rows
-  // V~_k(kappa)[c0 .. c0+CB)[0 .. L) of the tile by cp.async
-  auto issue_block = [&](int b) {
-    const int s = b & 1;
+  // core operand of block b: one bulk copy (tid 0) into ring slot b % 3
+  auto issue_B = [&](int b) {
+    if (b >= nblk || tid != 0) return;
+    const int s = b % kBStages;
+    const uint32_t bar = bar_b0 + 8 * s;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                 "r"((uint32_t)blk_bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(sB + s * blk_bytes)),
+        "l"(prep_ch + (size_t)b * blk_bytes), "r"((uint32_t)blk_bytes), "r"(bar)
+        : "memory");
+  };
+  // precoder rows V~_k(kappa)[c0 .. c0+CB)[0 .. L) of the tile for block b
+  // (cp.async by every thread, stage b % 2), one commit group per call
+  auto issue_V = [&](int b) {
     if (b < nblk) {
-      if (tid == 0) {
-        const uint32_t bar = bar_b0 + 8 * s;
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                     "r"((uint32_t)blk_bytes) : "memory");
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                smem_u32(sB + s * blk_bytes)),
-            "l"(prep_ch + (size_t)b * blk_bytes), "r"((uint32_t)blk_bytes), "r"(bar)
-            : "memory");
-      }
       const int c0 = b * kCB;
-      float2* dst = sV + s * kTile * tp.SV;
+      float2* dst = sV + (b & 1) * kTile * tp.SV;
       if (wideV) {
         constexpr int U = kCB * LT / 2;            // 16-byte units per subcarrier
         for (int idx = tid; idx < kTile * U; idx += NT) {
@@ -244,46 +374,25 @@ __global__ void __launch_bounds__(128 * (MG / tc_rpt(MG)))
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   };
-  issue_block(0);
-  issue_block(1);
-
-  // projection w = C^T conj(c(kappa)) (eq. 15) in FP32 -> A operand; thread
-  // (g, t) takes q = g, g + RG, ...
-  {
-    const int kap = kap0 + t;
-    const float2* Cch = A.C + (size_t)ch * P * p;
-    constexpr int QA = (32 + RG - 1) / RG;
-    float2 acc[QA];
-#pragma unroll
-    for (int u = 0; u < QA; ++u) acc[u] = cz();
-    if (kap < K) {
-      for (int pp = 0; pp < P; ++pp) {
-        const float2 c = A.coef_mode == 0
-                             ? A.coef[((size_t)ch * K + kap) * P + pp]
-                             : path_coef(A.coef[(size_t)ch * P + pp], A.turns[(size_t)ch * P + pp], kap);
-        const float2* crow = Cch + (size_t)pp * p;
-#pragma unroll
-        for (int u = 0; u < QA; ++u) {
-          const int q = g + u * RG;
-          if (q < p) cmacc(acc[u], __ldg(crow + q), c);
-        }
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < QA; ++u) {
-      const int q = g + u * RG;
-      if (q < p) {
-        store_split<PREC>(sA, t, q, 2 * p, kbytes, acc[u].x, true);
-        store_split<PREC>(sA, t, p + q, 2 * p, kbytes, acc[u].y, true);
-      }
-    }
-    // zero the K padding of this row
-    const int kused = PREC == TS_PREC_TF32 ? 2 * p : 6 * p;
-    for (int kk = kused + g; kk < tp.Kpad; kk += RG) {
-      if (ES == 4) *reinterpret_cast<float*>(sA + kmajor_off(t, kk * 4, kbytes)) = 0.f;
-      else *reinterpret_cast<__nv_bfloat16*>(sA + kmajor_off(t, kk * 2, kbytes)) = __float2bfloat16_rn(0.f);
-    }
+  // projection operand of the tile (one bulk copy), core operand of blocks
+  // 0..2, precoder rows of blocks 0, 1
+  const uint32_t a_bytes = (uint32_t)(kTile * kbytes);
+  if (tid == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a), "r"(a_bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(sA)),
+        "l"(aop + (((size_t)i * (J - 1) + z) * gridDim.x + blockIdx.x) * (size_t)a_bytes), "r"(a_bytes),
+        "r"(bar_a)
+        : "memory");
   }
+  issue_B(0);
+  issue_B(1);
+  issue_B(2);
+  issue_V(0);
+  issue_V(1);
+
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -296,11 +405,12 @@ __global__ void __launch_bounds__(128 * (MG / tc_rpt(MG)))
   const uint32_t sbo = 128u * (uint32_t)(kbytes >> 4);
   auto issue_mma = [&](int b) -> bool {
     // tid 0 only: wait for the block's operand, then K/KMMA instructions
-    const int s = b & 1;
+    const int s = b & 1, sb = b % kBStages;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!mbar_wait(bar_b0 + 8 * s, (uint32_t)((b >> 1) & 1))) return false;
+    if (b == 0 && !mbar_wait(bar_a, 0)) return false;
+    if (!mbar_wait(bar_b0 + 8 * sb, (uint32_t)((b / kBStages) & 1))) return false;
     const uint32_t d = tmem + (uint32_t)(s * tp.Ntile);
-    const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB + s * blk_bytes);
+    const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB + sb * blk_bytes);
     for (int ks = 0; ks < tp.Kpad / KMMA; ++ks) {
       const uint64_t ad = smem_desc(a0 + ks * 256, sbo);
       const uint64_t bd = smem_desc(b0 + ks * 256, sbo);
@@ -330,9 +440,11 @@ __global__ void __launch_bounds__(128 * (MG / tc_rpt(MG)))
   bool aborted = false;
   for (int b = 0; b < nblk; ++b) {
     const int s = b & 1;
+    // MMA(b + 1) into the other TMEM buffer, whose last reader (block b - 1)
+    // finished before the barrier that ended the previous iteration
     if (tid == 0 && b + 1 < nblk && !abort_flag && !issue_mma(b + 1)) abort_flag = 1;
     asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-    __syncthreads();
+    __syncthreads();                                                // rows of block b staged
     if (abort_flag) { aborted = true; break; }
     if (!mbar_wait(bar_m0 + 8 * s, (uint32_t)((b >> 1) & 1))) abort_flag = 1;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -351,14 +463,19 @@ __global__ void __launch_bounds__(128 * (MG / tc_rpt(MG)))
             "=r"(h[21]), "=r"(h[22]), "=r"(h[23]), "=r"(h[24]), "=r"(h[25]), "=r"(h[26]), "=r"(h[27]),
             "=r"(h[28]), "=r"(h[29]), "=r"(h[30]), "=r"(h[31])
           : "r"(taddr));
-    } else {
-      static_assert(NCOL == 16, "tcgen05.ld shape");
+    } else if constexpr (NCOL == 16) {
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
           : "=r"(h[0]), "=r"(h[1]), "=r"(h[2]), "=r"(h[3]), "=r"(h[4]), "=r"(h[5]), "=r"(h[6]),
             "=r"(h[7]), "=r"(h[8]), "=r"(h[9]), "=r"(h[10]), "=r"(h[11]), "=r"(h[12]), "=r"(h[13]),
             "=r"(h[14]), "=r"(h[15])
           : "r"(taddr));
+    } else {
+      static_assert(NCOL == 8, "tcgen05.ld shape");
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                   : "=r"(h[0]), "=r"(h[1]), "=r"(h[2]), "=r"(h[3]), "=r"(h[4]), "=r"(h[5]), "=r"(h[6]),
+                     "=r"(h[7])
+                   : "r"(taddr));
     }
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
     const float2* vrow = sV + s * kTile * tp.SV + t * tp.SV;
@@ -379,9 +496,11 @@ __global__ void __launch_bounds__(128 * (MG / tc_rpt(MG)))
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    issue_block(b + 2);
+    issue_B(b + 3);     // slot of block b: MMA(b) has completed
+    issue_V(b + 2);     // stage of block b: its epilogue is done
   }
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (abort_flag) aborted = true;
 
@@ -416,10 +535,9 @@ __global__ void __launch_bounds__(128 * (MG / tc_rpt(MG)))
     // pending bulk copies and MMAs get another bounded wait before the
     // accumulator memory is released
     if (tid == 0) {
-      for (int s = 0; s < 2; ++s) {
-        mbar_wait(bar_b0 + 8 * s, 0);
-        mbar_wait(bar_m0 + 8 * s, 0);
-      }
+      for (int s = 0; s < kBStages; ++s) mbar_wait(bar_b0 + 8 * s, 0);
+      for (int s = 0; s < 2; ++s) mbar_wait(bar_m0 + 8 * s, 0);
+      mbar_wait(bar_a, 0);
     }
     if (g == 0 && kap0 + t < K) A.pflag[(size_t)i * K + kap0 + t] |= TS_FLAG_TIMEOUT;
   }
@@ -430,17 +548,25 @@ __global__ void __launch_bounds__(128 * (MG / tc_rpt(MG)))
                  "r"(2 * tp.Ntile < 32 ? 32 : 2 * tp.Ntile));
 }
 
+// both operands: the core of every link and the projections of the
+// interfering links' tiles (each written in full, padding included)
 template <int PREC>
 cudaError_t launch_prep(const SinrArgs& A, int MG, int LT, unsigned char* prep, cudaStream_t s) {
   const TcPlan tp = tc_plan(MG, LT, A.n, A.p, PREC);
-  cudaError_t e = cudaMemsetAsync(prep, 0, tp.prep_bytes_per_link * (size_t)A.J * A.J, s);
+  const size_t bbytes = tp.prep_bytes_per_link * (size_t)A.J * A.J;
+  const int nchunk = tp.Ntile * (tp.Kpad * tp.ES / 16);
+  const int nblocks = A.J * A.J * tp.nblk;
+  dim3 pgrid((nchunk + 255) / 256, nblocks < 65535 ? nblocks : 65535);
+  k_core_prep<PREC><<<pgrid, 256, 0, s>>>(A.G, A.m, A.n, A.p, MG, tp.Ntile, tp.Kpad, tp.nblk, nblocks,
+                                          prep);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || A.J < 2) return e;
+  const int smem = ((kTile * (2 * A.p + 1) * 4 + 15) & ~15) + kTile * (kProjPC + 1) * 8 +
+                   kProjPC * A.p * 8;
+  e = cudaFuncSetAttribute(k_tc_proj<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  const size_t total = (size_t)A.J * A.J * tp.nblk * tp.Ntile * 2 * A.p;
-  const int threads = 256;
-  const size_t want = (total + threads - 1) / threads;
-  const int blocks = (int)(want < 152 * 16 ? want : 152 * 16);
-  k_core_prep<PREC><<<blocks, threads, 0, s>>>(A.G, A.J * A.J, A.m, A.n, A.p, MG, tp.Ntile, tp.Kpad,
-                                               tp.nblk, prep);
+  dim3 grid((A.K + kTile - 1) / kTile, A.J, A.J - 1);
+  k_tc_proj<PREC><<<grid, kTile * ((A.p + kProjQ - 1) / kProjQ), smem, s>>>(A, tp.Kpad, prep + bbytes);
   return cudaGetLastError();
 }
 
@@ -452,7 +578,8 @@ cudaError_t launch_tc(const SinrArgs& A, const unsigned char* prep, cudaStream_t
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, tp.smem);
   if (e != cudaSuccess) return e;
   dim3 grid((A.K + kTile - 1) / kTile, A.J, A.J - 1);
-  kern<<<grid, 128 * (MG / tc_rpt(MG)), tp.smem, s>>>(A, prep, tp);
+  const unsigned char* aop = prep + tp.prep_bytes_per_link * (size_t)A.J * A.J;
+  kern<<<grid, 128 * (MG / tc_rpt(MG)), tp.smem, s>>>(A, prep, aop, tp);
   return cudaGetLastError();
 }
 
@@ -475,9 +602,10 @@ bool tc_supported(int m, int L, int p) {
   return tp.smem <= 227 * 1024;
 }
 
-size_t tc_prep_bytes(int J, int m, int L, int n, int p, int prec) {
-  return detail::tc_plan(detail::tc_mg(m), detail::tc_lt(L), n, p, prec).prep_bytes_per_link *
-         (size_t)J * J;
+size_t tc_prep_bytes(int J, int m, int L, int n, int p, int K, int prec) {
+  const detail::TcPlan tp = detail::tc_plan(detail::tc_mg(m), detail::tc_lt(L), n, p, prec);
+  const size_t tiles = (size_t)(K + detail::kTile - 1) / detail::kTile;
+  return tp.prep_bytes_per_link * (size_t)J * J + tp.a_bytes_per_tile * tiles * J * (J - 1);
 }
 
 cudaError_t launch_core_prep(const SinrArgs& a, int prec, void* prep, cudaStream_t s) {

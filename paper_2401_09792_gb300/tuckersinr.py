@@ -25,6 +25,8 @@ TS_OP_SINR_SVD_TF32, TS_OP_SINR_SVD_BF16X2 = 7, 8
 TS_PREC_FP32, TS_PREC_TF32, TS_PREC_BF16X2 = 0, 1, 2
 TS_FLAG_NOT_PD, TS_FLAG_NONFINITE, TS_FLAG_RANK_DEFICIENT, TS_FLAG_EIG_UNCONVERGED = 1, 2, 4, 8
 TS_FLAG_TIMEOUT = 16
+TS_FLAG_REFINED = 32
+TS_FLAG_ERRORS = 0xFF & ~TS_FLAG_REFINED     # bits that report a problem (REFINED is informational)
 
 
 class TsError(RuntimeError):
@@ -57,6 +59,7 @@ _SIG = {
     "ts_last_cuda_error": (ctypes.c_int, []),
     "ts_abi_version": (ctypes.c_int, []),
     "ts_set_timing_events": (None, [_P, _P]),
+    "ts_set_refinement": (None, [ctypes.c_float]),
     "ts_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(ts_dims), ctypes.c_int]),
     "ts_coefficients": (ctypes.c_int, [ctypes.POINTER(ts_dims), _P, _P, _P, _P]),
     "ts_project_precoder": (ctypes.c_int, [ctypes.POINTER(ts_dims), _P, _P, _P, _P]),
@@ -148,6 +151,12 @@ def _stream(stream) -> int | None:
 def _check(fn: str, st: int):
     if st != 0:
         raise TsError(fn, st, _lib)
+
+
+def ts_set_refinement(cond_threshold: float):
+    """Condition number of R above which SINR units get FP64-residual
+    refinement on this thread (negative: off; default 1e3)."""
+    load().ts_set_refinement(float(cond_threshold))
 
 
 def ts_set_timing_events(start=None, stop=None):
