@@ -35,14 +35,20 @@ sys.path.insert(0, ROOT)
 
 from paper_2401_09792_gb300 import synth  # noqa: E402
 
-WORKLOAD = synth.MID
+WORKLOAD = synth.MID             # the default line; --workload selects another
+WORKLOAD_NAME = "mid"
 METRIC = "subcarrier-SINRs/s"
 FLUSH_BYTES = 256 << 20          # > 129 MB of L2
 
 
+def select_workload(name: str):
+    global WORKLOAD, WORKLOAD_NAME
+    WORKLOAD, WORKLOAD_NAME = synth.WORKLOADS[name], name
+
+
 def workload_config(w, precoder="svd"):
     return {
-        "workload": (f"mid: J={w.J} cells, M={w.M}, N={w.N}, P={w.P}, K={w.K} subcarriers, "
+        "workload": (f"{WORKLOAD_NAME}: J={w.J} cells, M={w.M}, N={w.N}, P={w.P}, K={w.K} subcarriers, "
                      f"ranks (m,n,p)=({w.m},{w.n},{w.p}), L={w.L} streams; {precoder}-precoded "
                      f"MMSE SINR; path-form coefficients; Tucker form drawn directly"),
         "precoder": precoder,
@@ -155,8 +161,8 @@ class ClockSampler:
 
 # ------------------------------------------------------- multi-rank host logic
 def rank_workload(rank: int):
-    """Each rank evaluates its own independent system: the mid workload with
-    the seed offset by the rank (weak scaling, no data-path collective)."""
+    """Each rank evaluates its own independent system: the selected workload
+    with the seed offset by the rank (weak scaling, no data-path collective)."""
     return synth.Workload(**{**WORKLOAD.__dict__, "seed": WORKLOAD.seed + rank})
 
 
@@ -284,6 +290,9 @@ def run_ours(args):
             stream, ev, units)
         prec = _precision_variants(args, ts, torch, dev, w, dv, coef, d, sinr, flags, flush, stream,
                                    ev, units)
+        if args.adjoint:
+            prec["adjoint"] = _adjoint_timing(args, ts, torch, dev, w, dv, coef, d, flush, stream, ev,
+                                              units)
     if rank != 0:
         if world > 1:
             dist.barrier()
@@ -350,6 +359,10 @@ def _extras(args, ts, torch, dist, world, dev, w, tk, host, dv, coef, d, ws, sin
 
     # ---- dense-channel comparator on the same system: full M x N channels per
     # subcarrier (eq. 9), precoders and solves at (M, N); same kernels, C = I
+    if ts.ts_workspace_bytes(d, ts.TS_OP_DENSE_SVD) == 0:
+        # the dense kernels stage one M x N channel per subcarrier: M <= 16,
+        # N <= 512, P <= 32
+        return e2e_value, h2d, d2h, mm_ms, None, None, None
     X = synth.channel_submatrices(w)
     Xd = torch.from_numpy(np.ascontiguousarray(np.transpose(X, (0, 1, 4, 2, 3))
                                                .reshape(J * J, P, w.M, w.N)).astype(np.complex64)).to(dev)
@@ -370,6 +383,33 @@ def _extras(args, ts, torch, dist, world, dev, w, tk, host, dv, coef, d, ws, sin
     dense_value = units * dense_steps / (dense_ms * 1e-3)
     del Xd, ws_d
     return e2e_value, h2d, d2h, mm_ms, dense_value, dense_ms, dense_steps
+
+
+def _adjoint_timing(args, ts, torch, dev, w, dv, coef, d, flush, stream, ev, units):
+    """The adjoint of the SVD-precoded SINR (dSINR -> dG, dC; the forward
+    quantities are recomputed inside), same timing discipline."""
+    dsinr = torch.ones(w.J, w.K, w.L, device=dev)
+    dG = torch.empty_like(dv["G"])
+    dC = torch.empty_like(dv["C"])
+    wsa = ts.workspace(d, ts.TS_OP_SINR_SVD_ADJOINT, dev)
+    for _ in range(args.warmup):
+        ts.ts_sinr_svd_adjoint(d, coef, dv["G"], dv["C"], dv["sigma2"], dsinr, dG, dC, None, wsa, stream)
+    torch.cuda.synchronize()
+    steps = max(3, args.steps // 10)
+    total = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        a, b = ev(), ev()
+        a.record(stream)
+        ts.ts_sinr_svd_adjoint(d, coef, dv["G"], dv["C"], dv["sigma2"], dsinr, dG, dC, None, wsa, stream)
+        b.record(stream)
+        b.synchronize()
+        total += a.elapsed_time(b)
+    del wsa
+    return {"value": units * steps / (total * 1e-3), "unit": "subcarrier-SINR gradients/s",
+            "ms_per_step": total / steps, "steps": steps,
+            "what": "d(sum_r dSINR_r SINR_r)/d(G, C), forward recomputed, workspace "
+                    f"{ts.ts_workspace_bytes(d, ts.TS_OP_SINR_SVD_ADJOINT) / 2**30:.2f} GiB"}
 
 
 def _precision_variants(args, ts, torch, dev, w, dv, coef, d, sinr, flags, flush, stream, ev, units):
@@ -423,8 +463,8 @@ def _report(args, ts, torch, world, dev, w, tk, alpha, tau, s2, d, coef, dv, ws,
     fp32_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12       # TFLOP/s, FFMA on every lane
     link_mean = float(np.mean(link_ms))
     achieved = link_flops(w, "svd") / (link_mean * 1e-3) / 1e12
-    traffic = (recorded_traffic("k_sinr_link_blk", "mid") if args.precision == "fp32"
-               else recorded_traffic(f"k_sinr_link_tc_{args.precision}", "mid"))
+    traffic = (recorded_traffic("k_sinr_link_blk", WORKLOAD_NAME) if args.precision == "fp32"
+               else recorded_traffic(f"k_sinr_link_tc_{args.precision}", WORKLOAD_NAME))
     kname = "k_sinr_link_blk (svd)" if args.precision == "fp32" else f"k_sinr_link_tc ({args.precision})"
     roofline = {"kernel": kname, "bound": "alu", "achieved": round(achieved, 3),
                 "peak": round(fp32_peak, 2), "unit": "TFLOP/s", "frac": round(achieved / fp32_peak, 4),
@@ -457,8 +497,10 @@ def _report(args, ts, torch, world, dev, w, tk, alpha, tau, s2, d, coef, dv, ws,
                             "link_ms": v["link_ms"],
                             "what": "interfering links' core contraction on the tensor cores "
                                     f"({k}), everything else FP32"}
-               for k, v in prec.items()}},
-        "dense_comparator": None if dense_ms is None else {
+               for k, v in prec.items() if k != "adjoint"},
+            **({"svd_adjoint": prec["adjoint"]} if "adjoint" in prec else {})},
+        "dense_comparator": {"unavailable": "dense kernels need M <= 16, N <= 512, P <= 32"}
+        if dense_ms is None else {
             "value": dense_value, "unit": METRIC, "ms_per_step": dense_ms / dense_steps,
             "what": "same SVD-precoded SINR from the uncompressed channels "
                     f"(M={w.M}, N={w.N}, P={w.P}) on the same GPU kernels",
@@ -470,7 +512,7 @@ def _report(args, ts, torch, world, dev, w, tk, alpha, tau, s2, d, coef, dv, ws,
             line.pop(key)
     if world == 1 and not args.no_cpu_baseline:
         gpu_out = {"fp32": _gpu_svd_sinr(ts, d, coef, dv, ws, stream)}
-        gpu_out.update({k: v["sinr"] for k, v in prec.items()})
+        gpu_out.update({k: v["sinr"] for k, v in prec.items() if "sinr" in v})
         line["cpu_baseline"], errs = cpu_baseline(w, tk, alpha, tau, s2, gpu_out)
         line["sinr_err"] = errs.pop("fp32", None)
         for k, e in errs.items():
@@ -577,12 +619,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--step-only", action="store_true",
                     help="time only the SVD step (no end-to-end, variant or comparator runs)")
+    ap.add_argument("--workload", default="mid", choices=sorted(synth.WORKLOADS),
+                    help="synthetic system of the timed step (default: mid, the headline)")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="also time the SVD-SINR adjoint (dSINR -> dG, dC) on the workload")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16x2"],
                     help="arithmetic of the interfering links' core contraction in the timed step "
                          "(fp32: FMA pipe; tf32, bf16x2: tensor cores); implies --step-only")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    select_workload(args.workload)
     if args.impl == "reference":
         run_reference(args)
     else:
