@@ -218,6 +218,64 @@ int ts_sinr_svd_from_precoders_prec(const ts_dims* d, const ts_coef* coef,
                                     float* sinr, uint8_t* flags, void* ws,
                                     size_t ws_bytes, void* stream);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent systems with their own sizes (numbers of cells, antennas,
+ * ranks, streams, subcarriers), evaluated by one graph launch.  The paper has
+ * no counterpart; it serves callers that evaluate many small systems per
+ * scheduling step, where one launch per kernel per system would dominate.
+ *
+ * ts_instance describes one system: its sizes, the operation
+ * (TS_OP_SINR_SVD or TS_OP_SINR_MMSE), the arithmetic of the SVD path's core
+ * contraction (TS_PREC_*; TS_PREC_FP32 for MMSE), and the device arrays of
+ * ts_sinr_svd / ts_sinr_mmse (Pt: MMSE only, else NULL; flags may be NULL).
+ */
+typedef struct {
+  ts_dims d;
+  int op;
+  int precision;
+  ts_coef coef;
+  const ts_c64* G;
+  const ts_c64* C;
+  const ts_c64* Pt;
+  const float* sigma2;
+  float* sinr;
+  uint8_t* flags;
+} ts_instance;
+
+typedef struct ts_batch_plan ts_batch_plan;   /* opaque */
+
+/* Device workspace for the whole batch: each instance's ts_workspace_bytes,
+ * 256-byte aligned, back to back.  0 if an instance is invalid. */
+size_t ts_batch_workspace_bytes(const ts_instance* inst, int n);
+
+/* Options of ts_batch_plan_create. */
+enum {
+  TS_BATCH_AUTOTUNE = 1   /* time the launch-shape candidates of every new
+                             shape class on its instance and keep the
+                             fastest (in the process-wide tuning table) */
+};
+
+/* Builds a plan for the n instances of `inst` (host array, copied): checks
+ * every instance (sizes, pointers, workspace) before any launch, optionally
+ * autotunes, then captures the instances' kernels into one CUDA graph --
+ * independent instances on four parallel branches -- and instantiates it.
+ * The device arrays must stay valid and in place for the plan's lifetime;
+ * their contents may change between launches.  Allocates host memory and
+ * CUDA streams, events and a graph (released by ts_batch_plan_destroy); no
+ * device memory of its own.  Autotuning runs the instances' kernels on
+ * their own data (outputs are overwritten by the next launch). */
+int ts_batch_plan_create(const ts_instance* inst, int n, void* ws, size_t ws_bytes, int options,
+                         ts_batch_plan** plan);
+/* One evaluation of every instance of the plan: one graph launch on
+ * `stream`.  Returns TS_ERR_CUDA if the launch fails. */
+int ts_batch_launch(ts_batch_plan* plan, void* stream);
+void ts_batch_plan_destroy(ts_batch_plan* plan);
+
+/* The process-wide tuning table (shape class -> launch-shape choice) as a
+ * text file, one class per line; load merges into the table. */
+int ts_autotune_save(const char* path);
+int ts_autotune_load(const char* path);
+
 /* Dense-channel comparator: the same SINR computed from the uncompressed
  * channel tensors, rebuilding the full M x N channel of every link and
  * subcarrier, H_ik(kappa) = X_ik x_3 c_ik(kappa)* (eq. 9), and running the

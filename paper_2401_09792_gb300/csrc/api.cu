@@ -19,6 +19,9 @@ thread_local cudaEvent_t g_ev_stop = nullptr;
 // condition number of R above which a unit's solves are refined with FP64
 // residuals (ts_set_refinement); infinity turns refinement off
 thread_local float g_refine_cond = 1e3f;
+// launch-shape choices of the batch planner (0: default heuristics)
+thread_local ts::Tuning g_tuning = {0, 0};
+thread_local bool g_timing_suspended = false;
 
 // Finalisation, then the FP64-residual refinement of the units it listed.
 cudaError_t finalize_refined(const ts::SinrArgs& a, bool svd, cudaStream_t s) {
@@ -32,9 +35,10 @@ cudaError_t finalize_refined(const ts::SinrArgs& a, bool svd, cudaStream_t s) {
 // then the finalisation.
 cudaError_t links_then_finalize(const ts::SinrArgs& a, bool svd, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
-  if (g_ev_start != nullptr) e = cudaEventRecord(g_ev_start, s);
+  const bool timed = g_ev_start != nullptr && g_ev_stop != nullptr && !g_timing_suspended;
+  if (timed) e = cudaEventRecord(g_ev_start, s);
   if (e == cudaSuccess) e = ts::launch_sinr_links(a, svd, s);
-  if (e == cudaSuccess && g_ev_stop != nullptr) e = cudaEventRecord(g_ev_stop, s);
+  if (e == cudaSuccess && timed) e = cudaEventRecord(g_ev_stop, s);
   if (e == cudaSuccess) e = finalize_refined(a, svd, s);
   return e;
 }
@@ -187,6 +191,8 @@ ts::SinrArgs base_args(const ts_dims* d, const ts_coef* coef, const ts_c64* G, c
   a.rlist = reinterpret_cast<int*>(ws + w.rlist);
   a.rcount = reinterpret_cast<int*>(ws + w.rcount);
   a.refine_cond = g_refine_cond;
+  a.link_variant = g_tuning.link_variant;
+  a.precoder_split = g_tuning.precoder_split;
   return a;
 }
 
@@ -194,6 +200,8 @@ ts::SinrArgs base_args(const ts_dims* d, const ts_coef* coef, const ts_c64* G, c
 
 namespace ts {
 int record_cuda_error(cudaError_t e) { return cuda_status(e); }
+void set_tuning(Tuning t) { g_tuning = t; }
+void suspend_timing(bool suspended) { g_timing_suspended = suspended; }
 }  // namespace ts
 
 extern "C" {
@@ -472,10 +480,11 @@ int svd_from_precoders_prec_impl(const ts_dims* d, const ts_coef* coef, const ts
   a.V = reinterpret_cast<float2*>(base + w.V);
   a.pflag = reinterpret_cast<uint8_t*>(base + w.pflag);
   void* prep = base + w.total;
+  const bool timed = g_ev_start != nullptr && g_ev_stop != nullptr && !g_timing_suspended;
   cudaError_t e = ts::launch_core_prep(a, prec, prep, s);
-  if (e == cudaSuccess && g_ev_start != nullptr) e = cudaEventRecord(g_ev_start, s);
+  if (e == cudaSuccess && timed) e = cudaEventRecord(g_ev_start, s);
   if (e == cudaSuccess) e = ts::launch_sinr_links_tc(a, prec, prep, s);
-  if (e == cudaSuccess && g_ev_stop != nullptr) e = cudaEventRecord(g_ev_stop, s);
+  if (e == cudaSuccess && timed) e = cudaEventRecord(g_ev_stop, s);
   if (e == cudaSuccess) e = finalize_refined(a, true, s);
   return cuda_status(e);
 }

@@ -35,7 +35,20 @@ struct SinrArgs {
   int* rlist;                       // units (i K + kappa) to refine (workspace) or nullptr
   int* rcount;                      // length of rlist (workspace, zeroed before finalize)
   float refine_cond;                // refine when the Cholesky diagonal gives cond(R) above this
+  // launch-shape choices (0: the default heuristics; set by the autotuner)
+  int link_variant;                 // svd links: 1 blocked two-row kernel, 2 one-row kernel
+  int precoder_split;               // precoder tile: subcarriers per CTA divided by 2^split
 };
+
+// Host-side hooks of the batch planner (api.cu): launch-shape choices applied
+// to the SINR calls that follow on this host thread, and a switch that makes
+// those calls ignore the ts_set_timing_events pair (while capturing a graph).
+struct Tuning {
+  int link_variant;
+  int precoder_split;
+};
+void set_tuning(Tuning t);
+void suspend_timing(bool suspended);
 
 // Launchers; each picks the template instance for (m, L) and returns the
 // launch status.  `smem_*` report the dynamic shared memory of a launch.

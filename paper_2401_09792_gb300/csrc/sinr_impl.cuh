@@ -1170,6 +1170,10 @@ cudaError_t run_precoder(const SinrArgs& A, cudaStream_t s) {
     T /= 2;
     pl = precoder_plan(MG, T, A.n, A.p, fused);
   }
+  for (int sp = 0; sp < A.precoder_split && T * MG > 32; ++sp) {
+    T /= 2;
+    pl = precoder_plan(MG, T, A.n, A.p, fused);
+  }
   const size_t smem = (size_t)pl.total * sizeof(float2);
   if (smem > kSmemBudget) return cudaErrorInvalidValue;
   auto kern = k_svd_precoder<MG, LT>;
@@ -1238,7 +1242,8 @@ cudaError_t launch_link_blocked(const SinrArgs& A, cudaStream_t s) {
 template <int MG, int LT>
 cudaError_t run_links(const SinrArgs& A, bool svd, cudaStream_t s) {
   if (svd) {
-    if (MG >= 4 && A.p <= 32) return launch_link_blocked<(MG >= 4 ? MG : 4), LT>(A, s);
+    if (MG >= 4 && A.p <= 32 && A.link_variant != 2)
+      return launch_link_blocked<(MG >= 4 ? MG : 4), LT>(A, s);
     return launch_link_mode<MG, LT, kModeSvd>(A, A.J - 1, s);
   }
   return launch_link_mode<MG, LT, kModeFold>(A, A.J, s);

@@ -53,6 +53,15 @@ class ts_coef(ctypes.Structure):
                 ("tau_s", ctypes.c_void_p)]
 
 
+class ts_instance(ctypes.Structure):
+    _fields_ = [("d", ts_dims), ("op", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("coef", ts_coef), ("G", ctypes.c_void_p), ("C", ctypes.c_void_p),
+                ("Pt", ctypes.c_void_p), ("sigma2", ctypes.c_void_p), ("sinr", ctypes.c_void_p),
+                ("flags", ctypes.c_void_p)]
+
+
+TS_BATCH_AUTOTUNE = 1
+
 _P = ctypes.c_void_p
 _SIG = {
     "ts_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -84,6 +93,13 @@ _SIG = {
                                         _P, ctypes.c_size_t, _P]),
     "ts_sinr_svd_from_precoders": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.POINTER(ts_coef),
                                                   _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
+    "ts_batch_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(ts_instance), ctypes.c_int]),
+    "ts_batch_plan_create": (ctypes.c_int, [ctypes.POINTER(ts_instance), ctypes.c_int, _P, ctypes.c_size_t,
+                                            ctypes.c_int, ctypes.POINTER(_P)]),
+    "ts_batch_launch": (ctypes.c_int, [_P, _P]),
+    "ts_batch_plan_destroy": (None, [_P]),
+    "ts_autotune_save": (ctypes.c_int, [ctypes.c_char_p]),
+    "ts_autotune_load": (ctypes.c_int, [ctypes.c_char_p]),
     "ts_sinr_svd_prec": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.POINTER(ts_coef), _P, _P, _P,
                                         ctypes.c_int, _P, _P, _P, ctypes.c_size_t, _P]),
     "ts_sinr_svd_from_precoders_prec": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.POINTER(ts_coef),
@@ -228,6 +244,49 @@ def ts_sinr_svd_from_precoders_prec(d: Dims, coef: ts_coef, G, C, sigma2, precis
            lib.ts_sinr_svd_from_precoders_prec(ctypes.byref(d.c()), ctypes.byref(coef), _ptr(G), _ptr(C),
                                                _ptr(sigma2), int(precision), _ptr(sinr), _ptr(flags),
                                                _ptr(ws), ws.numel(), _stream(stream)))
+
+
+def instance(d: Dims, op: int, coef: ts_coef, G, C, sigma2, sinr, flags=None, Pt=None,
+             precision: int = TS_PREC_FP32) -> ts_instance:
+    """One system of a batch (device tensors in the library's layouts)."""
+    return ts_instance(d.c(), op, precision, coef, _ptr(G), _ptr(C), _ptr(Pt), _ptr(sigma2), _ptr(sinr),
+                       _ptr(flags))
+
+
+class BatchPlan:
+    """ts_batch_plan_create / ts_batch_launch / ts_batch_plan_destroy."""
+
+    def __init__(self, instances, ws, autotune: bool = False):
+        lib = load()
+        self._arr = (ts_instance * len(instances))(*instances)
+        self._ws = ws
+        h = _P()
+        _check("ts_batch_plan_create",
+               lib.ts_batch_plan_create(self._arr, len(instances), _ptr(ws), ws.numel(),
+                                        TS_BATCH_AUTOTUNE if autotune else 0, ctypes.byref(h)))
+        self._h = h
+
+    def launch(self, stream=None):
+        _check("ts_batch_launch", load().ts_batch_launch(self._h, _stream(stream)))
+
+    def close(self):
+        if self._h:
+            load().ts_batch_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_workspace(instances, device="cuda") -> torch.Tensor:
+    arr = (ts_instance * len(instances))(*instances)
+    nb = load().ts_batch_workspace_bytes(arr, len(instances))
+    if nb == 0:
+        raise TsError("ts_batch_workspace_bytes", 1, load())
+    return torch.empty(nb, dtype=torch.uint8, device=device)
 
 
 def ts_tucker_fit(d: Dims, X, S, init, A, B, C, G, g_hist, ws, stream=None):

@@ -110,3 +110,41 @@ def test_null_and_alignment_checks(lib):
     assert lib.ts_sinr_svd(ctypes.byref(d), ctypes.byref(coef), 8, 8, 8, 8, None, 264, 1 << 30, None) == 3
     coef = ts.ts_coef(3, 8, None, None)
     assert lib.ts_sinr_svd(ctypes.byref(d), ctypes.byref(coef), 8, 8, 8, 8, None, 256, 1 << 30, None) == 6
+
+
+def _instance(ts, **kw):
+    d = _dims(**kw)
+    coef = ts.ts_coef(1, None, 8, 8)
+    return ts.ts_instance(d, 0, 0, coef, 8, 8, None, 8, 256, None)
+
+
+def test_batch_workspace_and_checks_before_launch(lib, tmp_path):
+    from paper_2401_09792_gb300 import tuckersinr as ts
+    good = [_instance(ts), _instance(ts, K=100, J=3)]
+    arr = (ts.ts_instance * 2)(*good)
+    total = lib.ts_batch_workspace_bytes(arr, 2)
+    each = [lib.ts_workspace_bytes(ctypes.byref(x.d), 0) for x in good]
+    assert total == sum((b + 255) // 256 * 256 for b in each)
+    bad = (ts.ts_instance * 2)(good[0], _instance(ts, m=5))
+    assert lib.ts_batch_workspace_bytes(bad, 2) == 0
+    h = ctypes.c_void_p()
+    # invalid sizes, an MMSE instance without precoder, a tensor-core MMSE
+    # instance and a short workspace are refused before any CUDA call
+    assert lib.ts_batch_plan_create(bad, 2, 256, 1 << 40, 0, ctypes.byref(h)) == 1
+    mm = _instance(ts)
+    mm.op = 1
+    assert lib.ts_batch_plan_create((ts.ts_instance * 1)(mm), 1, 256, 1 << 40, 0, ctypes.byref(h)) == 2
+    mm.Pt = 8
+    mm.precision = 1
+    assert lib.ts_batch_plan_create((ts.ts_instance * 1)(mm), 1, 256, 1 << 40, 0, ctypes.byref(h)) == 6
+    assert lib.ts_batch_plan_create(arr, 2, 256, total - 1, 0, ctypes.byref(h)) == 4
+    assert h.value is None
+
+
+def test_autotune_table_roundtrip(lib, tmp_path):
+    src = tmp_path / "in.txt"
+    src.write_text("op0_prec0_J8_m8_n32_p16_P32_L8_K1024_coef1 2 1\nbroken line\n")
+    assert lib.ts_autotune_load(str(src).encode()) == 0
+    out = tmp_path / "out.txt"
+    assert lib.ts_autotune_save(str(out).encode()) == 0
+    assert "op0_prec0_J8_m8_n32_p16_P32_L8_K1024_coef1 2 1" in out.read_text()
