@@ -568,6 +568,133 @@ def cpu_baseline(w, tk, alpha, tau, s2, gpu_sinr=None, budget_s=12.0, kslice=128
     return base, out
 
 
+# ------------------------------------------------------------ batch workload
+def batch_systems(count: int, seed: int = 0):
+    """Instances of the batching workload: N in {64,128,256,512}, M in {2,4,8},
+    K uniform in 256..3300, J uniform in 2..16, m = M, n in {16,32,64} (<= N),
+    p in {8,16,32}, P = 64, L = m; path-form coefficients; Tucker form drawn
+    directly; SVD precoding."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for j in range(count):
+        M = int(rng.choice([2, 4, 8]))
+        N = int(rng.choice([64, 128, 256, 512]))
+        n = int(min(N, rng.choice([16, 32, 64])))
+        out.append(synth.Workload(f"batch{j}", J=int(rng.integers(2, 17)), M=M, N=N, P=64,
+                                  K=int(rng.integers(256, 3301)), m=M, n=n, p=int(rng.choice([8, 16, 32])),
+                                  L=M, n_los=2, pdp_decay_s=300e-9, sigma2=None, seed=1000 + j))
+    return out
+
+
+def run_batch(args):
+    import torch
+
+    from paper_2401_09792_gb300 import tuckersinr as ts
+    import __graft_entry__
+    __graft_entry__.build()
+    ts.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    systems = batch_systems(args.batch_instances)
+    keep, insts, host = [], [], []
+    for w in systems:
+        tk = synth.direct_tucker(w)
+        alpha, tau = synth.path_gains_delays(w)
+        s2 = synth.noise_powers(w)
+        d = ts.Dims.of(w)
+        G = ts.core_to_device(tk["G"], dev)
+        C = ts.factor_to_device(tk["C"].reshape(w.J * w.J, w.P, w.p), dev)
+        al = ts.factor_to_device(alpha.reshape(w.J * w.J, w.P), dev)
+        ta = ts.real_to_device(tau.reshape(w.J * w.J, w.P), dev)
+        sig = ts.real_to_device(s2, dev)
+        cs, k = ts.make_coef(alpha=al, tau=ta)
+        sinr = torch.empty(w.J, w.K, w.L, device=dev)
+        flags = torch.empty(w.J, w.K, dtype=torch.uint8, device=dev)
+        insts.append(ts.instance(d, ts.TS_OP_SINR_SVD, cs, G, C, sig, sinr, flags))
+        keep.append((G, C, al, ta, sig, sinr, flags, k))
+        host.append((w, tk, alpha, tau, s2))
+    ws = ts.batch_workspace(insts, dev)
+    stream = torch.cuda.current_stream(dev)
+    t0 = time.perf_counter()
+    plan = ts.BatchPlan(insts, ws, autotune=True)
+    plan_s = time.perf_counter() - t0
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    for _ in range(args.warmup):
+        plan.launch(stream)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    time.sleep(0.5)
+    total = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = ev(), ev()
+        a.record(stream)
+        plan.launch(stream)
+        b.record(stream)
+        b.synchronize()
+        total += a.elapsed_time(b)
+    clocks = sampler.stop()
+    bad = sum(int((kp[6] & ts.TS_FLAG_ERRORS).max().item()) for kp in keep)
+    assert bad == 0, "numerical flags raised in the batch"
+    # the same instances one call after another on one stream, no graph,
+    # each on its slice of the batch workspace
+    slices, off = [], 0
+    for w in systems:
+        nb = ts.ts_workspace_bytes(ts.Dims.of(w), ts.TS_OP_SINR_SVD)
+        slices.append(ws[off:off + nb])
+        off += (nb + 255) // 256 * 256
+    seq_steps = max(1, args.steps // 2)
+    seq = 0.0
+    for _ in range(seq_steps):
+        flush.zero_()
+        a, b = ev(), ev()
+        a.record(stream)
+        for w, x, kp, wsi in zip(systems, insts, keep, slices):
+            ts.ts_sinr_svd(ts.Dims.of(w), x.coef, kp[0], kp[1], kp[4], kp[5], kp[6], wsi, stream)
+        b.record(stream)
+        b.synchronize()
+        seq += a.elapsed_time(b)
+    units = sum(w.J * w.K for w in systems)
+    # CPU oracle on a bounded sample: the first instances, 64-subcarrier slices
+    from oracle import sinr as S
+    c0, t1, done = time.process_time(), time.perf_counter(), 0
+    errs = []
+    for (w, tk, alpha, tau, s2), kp in zip(host, keep):
+        if time.perf_counter() - t1 > 12.0:
+            break
+        coef = S.coefficients(alpha, tau, min(w.K, 64), w.delta_f_hz)
+        ref = S.tucker_sinr(tk["G"], tk["C"], coef, s2, w.L, "svd")
+        got = kp[5][:, :coef.shape[2]].cpu().numpy().astype(np.float64)
+        errs.append((np.abs(got - ref) / np.abs(ref)).ravel())
+        done += w.J * coef.shape[2]
+    wall = time.perf_counter() - t1
+    e = np.concatenate(errs)
+    line = {
+        "metric": METRIC, "value": units * args.steps / (total * 1e-3), "unit": METRIC, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"batch: {len(systems)} systems, N in {{64..512}}, M in {{2,4,8}}, "
+                               "K in 256..3300, J in 2..16, ranks up to (8,64,32), P=64, L=m; "
+                               "svd-precoded MMSE SINR; one CUDA-graph launch per step",
+                   "units_per_step": units, "l2": "flushed before every timed step (256 MiB write)",
+                   "plan_seconds_incl_autotune": round(plan_s, 2),
+                   "workspace_gib": round(ws.numel() / 2**30, 2)},
+        "sequential_calls": {"ms_per_step": seq / seq_steps,
+                             "what": "the same systems as one ts_sinr_svd call each on one stream"},
+        "gpu_launches": None, "clocks": clocks,
+        "cpu_baseline": {"value": done / wall, "unit": METRIC,
+                         "cores": max(1, round((time.process_time() - c0) / wall)), "kind": "oracle",
+                         "sample": f"FP64 NumPy oracle on the first 64 subcarriers of the first "
+                                   f"{len(errs)} systems ({done} subcarrier-SINRs)"},
+        "sinr_err": {"max_rel": float(e.max()), "p99_rel": float(np.percentile(e, 99)),
+                     "median_rel": float(np.median(e)), "n": int(e.size)},
+    }
+    print(json.dumps(line), flush=True)
+    plan.close()
+
+
 # ------------------------------------------------------------ reference arm
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -619,8 +746,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--step-only", action="store_true",
                     help="time only the SVD step (no end-to-end, variant or comparator runs)")
-    ap.add_argument("--workload", default="mid", choices=sorted(synth.WORKLOADS),
+    ap.add_argument("--workload", default="mid", choices=sorted(synth.WORKLOADS) + ["batch"],
                     help="synthetic system of the timed step (default: mid, the headline)")
+    ap.add_argument("--batch-instances", type=int, default=512,
+                    help="systems of the batch workload")
     ap.add_argument("--adjoint", action="store_true",
                     help="also time the SVD-SINR adjoint (dSINR -> dG, dC) on the workload")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16x2"],
@@ -629,6 +758,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.workload == "batch":
+        run_batch(args)
+        return
     select_workload(args.workload)
     if args.impl == "reference":
         run_reference(args)
