@@ -381,8 +381,47 @@ def _extras(args, ts, torch, dist, world, dev, w, tk, host, dv, coef, d, ws, sin
         b.synchronize()
         dense_ms += a.elapsed_time(b)
     dense_value = units * dense_steps / (dense_ms * 1e-3)
+    _method_error.result = _method_error(ts, torch, dev, w, Xd, coef, dv, d, stream, ev)
     del Xd, ws_d
     return e2e_value, h2d, d2h, mm_ms, dense_value, dense_ms, dense_steps
+
+
+def _method_error(ts, torch, dev, w, Xd, coef, dv, d, stream, ev, sweeps=10):
+    """The paper's accuracy and storage figures on these channels: fit the
+    groupwise form (Algorithm 2) on the GPU, then e_c of eq. (30) between the
+    SINR of the fitted form and the dense-channel SINR, both on the GPU, and
+    the storage ratio of eq. (29).  With i.i.d. NLOS submatrices the channels
+    are far less compressible than the paper's 3GPP data."""
+    J, M, N, P, m, n, p = w.J, w.M, w.N, w.P, w.m, w.n, w.p
+    A = torch.empty(J, M, m, dtype=torch.complex64, device=dev)
+    B = torch.empty(J, N, n, dtype=torch.complex64, device=dev)
+    C = torch.empty(J * J, P, p, dtype=torch.complex64, device=dev)
+    G = torch.empty(J * J, p, m, n, dtype=torch.complex64, device=dev)
+    g = torch.empty(3 * sweeps + 1, dtype=torch.float64, device=dev)
+    wsf = ts.workspace(d, ts.TS_OP_TUCKER_FIT, dev)
+    a, b = ev(), ev()
+    a.record(stream)
+    ts.ts_tucker_fit(d, Xd, sweeps, 0, A, B, C, G, g, wsf, stream)
+    b.record(stream)
+    b.synchronize()
+    fit_ms = a.elapsed_time(b)
+    del wsf
+    s_t = torch.empty(J, w.K, w.L, device=dev)
+    s_d = torch.empty_like(s_t)
+    ts.ts_sinr_svd(d, coef, G, C, dv["sigma2"], s_t, None, ts.workspace(d, ts.TS_OP_SINR_SVD, dev), stream)
+    ts.ts_dense_sinr_svd(d, coef, Xd, dv["sigma2"], s_d, None, ts.workspace(d, ts.TS_OP_DENSE_SVD, dev),
+                         stream)
+    torch.cuda.synchronize()
+    st, sd = s_t.double(), s_d.double()
+    e_c = float(((st - sd).abs() / sd.abs()).mean().item())
+    x2 = float((Xd.abs() ** 2).sum().item())
+    dense_entries = J * J * M * N * P
+    tucker_entries = J * M * m + J * N * n + J * J * P * p + J * J * m * n * p
+    return {"e_c": e_c, "what": "eq. (30): mean |SINR_tucker - SINR_dense| / SINR_dense over "
+                                "UEs, subcarriers and streams; Tucker form fitted on the GPU "
+                                f"({sweeps} sweeps of Algorithm 2) from the synthetic channels",
+            "fit_ms": round(fit_ms, 2), "g_over_x2": float(g[-1].item()) / x2,
+            "storage_ratio": dense_entries / tucker_entries}
 
 
 def _adjoint_timing(args, ts, torch, dev, w, dv, coef, d, flush, stream, ev, units):
@@ -499,6 +538,7 @@ def _report(args, ts, torch, world, dev, w, tk, alpha, tau, s2, d, coef, dv, ws,
                                     f"({k}), everything else FP32"}
                for k, v in prec.items() if k != "adjoint"},
             **({"svd_adjoint": prec["adjoint"]} if "adjoint" in prec else {})},
+        "method": getattr(_method_error, "result", None),
         "dense_comparator": {"unavailable": "dense kernels need M <= 16, N <= 512, P <= 32"}
         if dense_ms is None else {
             "value": dense_value, "unit": METRIC, "ms_per_step": dense_ms / dense_steps,
@@ -508,8 +548,13 @@ def _report(args, ts, torch, world, dev, w, tk, alpha, tau, s2, d, coef, dv, ws,
         "wall_s_timed_region": round(wall, 4),
     }
     if args.step_only or args.precision != "fp32":
-        for key in ("e2e", "variants", "dense_comparator"):
+        for key in ("e2e", "variants", "dense_comparator", "method"):
             line.pop(key)
+    if world == 1 and not args.step_only:
+        pk_meas = ts.ts_device_peaks(stream)
+        line["device_peaks"] = {**{k: round(v, 2) for k, v in pk_meas.items()}, "unit": "TFLOP/s",
+                                "what": "measured by the library's microbenchmarks on this GPU"}
+        line["roofline"]["frac_of_measured_fp32"] = round(line["roofline"]["achieved"] / pk_meas["fp32_fma"], 4)
     if world == 1 and not args.no_cpu_baseline:
         gpu_out = {"fp32": _gpu_svd_sinr(ts, d, coef, dv, ws, stream)}
         gpu_out.update({k: v["sinr"] for k, v in prec.items() if "sinr" in v})

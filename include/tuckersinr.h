@@ -142,6 +142,14 @@ void ts_set_timing_events(void* start, void* stop);
  * negative threshold turns refinement off. */
 void ts_set_refinement(float cond_threshold);
 
+/* Measured throughput of the current device in TFLOP/s: FP32 FMA (chains of
+ * independent fmaf on every SM), TF32 tensor-core MMA (tcgen05, M = 128,
+ * N = 256, K = 8, FP32 accumulation in TMEM, one CTA per SM) and FP64 FMA.
+ * A diagnostics call (the paper has no counterpart): it allocates and frees
+ * a small scratch buffer and synchronises on `stream`; it runs a few
+ * milliseconds of work.  TS_ERR_CUDA if a tensor-core wait timed out. */
+int ts_device_peaks(double* fp32_tflops, double* tf32_tflops, double* fp64_tflops, void* stream);
+
 /* Device workspace, in bytes, that operation `op` needs for sizes `d`.
  * Returns 0 for invalid sizes.  The caller allocates it (256-byte aligned)
  * and passes it to the call; its contents need no initialisation. */

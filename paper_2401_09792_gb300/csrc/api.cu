@@ -24,8 +24,12 @@ thread_local ts::Tuning g_tuning = {0, 0};
 thread_local bool g_timing_suspended = false;
 
 // Finalisation, then the FP64-residual refinement of the units it listed.
+// The list counter is zeroed by the link kernel that precedes the finalize
+// kernel (one thread of its first CTA); only an SVD call with a single cell
+// has no link kernel and zeroes it here.
 cudaError_t finalize_refined(const ts::SinrArgs& a, bool svd, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(a.rcount, 0, sizeof(int), s);
+  cudaError_t e = cudaSuccess;
+  if (svd && a.J < 2) e = cudaMemsetAsync(a.rcount, 0, sizeof(int), s);
   if (e == cudaSuccess) e = ts::launch_sinr_finalize(a, svd, s);
   if (e == cudaSuccess && a.refine_cond < INFINITY) e = ts::launch_sinr_refine(a, svd, s);
   return e;
@@ -301,6 +305,8 @@ int adjoint_impl(const ts_dims* d, const ts_coef* coef, const ts_c64* G, const t
   Workspace fw;
   fw.turns = w.turns;
   ts::SinrArgs a = base_args(d, coef, G, C, sigma2, sinr, nullptr, base, fw);
+  a.rlist = nullptr;                 // no finalize pass here
+  a.rcount = nullptr;
   a.Hserv = reinterpret_cast<float2*>(base + w.Hall);
   a.serv_stride = d->J + 1;          // serving link (k, k) inside the all-link layout
   cudaError_t e = cudaSuccess;

@@ -612,6 +612,9 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link(const SinrArgs A, const 
   const int k = MODE == kModeSvd ? (z < i ? z : z + 1) : MODE == kModeServe ? i : z;
   const int ch = i * J + k;
   const int nchunk = CHUNKED ? (n + NC - 1) / NC : 1;
+  // the refinement list of the finalize kernel that follows starts empty
+  if (MODE != kModeRebuild && A.rcount != nullptr && tid == 0 && blockIdx.x == 0 && i == 0 && z == 0)
+    *A.rcount = 0;
   float2* Cs = sm + pl.off_Cs;
   float2* cs = sm + pl.off_cs;
   float2* ws = sm + pl.off_ws;
@@ -894,6 +897,8 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link_blk(const SinrArgs A, co
   float2* ws = sm + pl.off_ws;
   float2* stage0 = sm + pl.off_stage;
   const bool wide = pl.wide != 0;
+  // the refinement list of the finalize kernel that follows starts empty
+  if (A.rcount != nullptr && tid == 0 && blockIdx.x == 0 && i == 0 && z == 0) *A.rcount = 0;
 
   auto issue_chunk = [&](int cidx) {
     float2* buf = stage0 + (cidx & 1) * pl.stage;

@@ -322,6 +322,8 @@ __global__ void __launch_bounds__(128 * (MG / tc_rpt(MG)))
 
   if (tid == 0) {
     abort_flag = 0;
+    // the refinement list of the finalize kernel that follows starts empty
+    if (A.rcount != nullptr && blockIdx.x == 0 && i == 0 && z == 0) *A.rcount = 0;
     for (int s = 0; s < kBStages + 3; ++s)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[s])));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");

@@ -69,6 +69,8 @@ _SIG = {
     "ts_abi_version": (ctypes.c_int, []),
     "ts_set_timing_events": (None, [_P, _P]),
     "ts_set_refinement": (None, [ctypes.c_float]),
+    "ts_device_peaks": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double), _P]),
     "ts_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(ts_dims), ctypes.c_int]),
     "ts_coefficients": (ctypes.c_int, [ctypes.POINTER(ts_dims), _P, _P, _P, _P]),
     "ts_project_precoder": (ctypes.c_int, [ctypes.POINTER(ts_dims), _P, _P, _P, _P]),
@@ -167,6 +169,14 @@ def _stream(stream) -> int | None:
 def _check(fn: str, st: int):
     if st != 0:
         raise TsError(fn, st, _lib)
+
+
+def ts_device_peaks(stream=None) -> dict:
+    """Measured FP32 FMA, TF32 tensor-core and FP64 FMA throughput (TFLOP/s)."""
+    f32, t32, f64 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check("ts_device_peaks", load().ts_device_peaks(ctypes.byref(f32), ctypes.byref(t32),
+                                                     ctypes.byref(f64), _stream(stream)))
+    return {"fp32_fma": f32.value, "tf32_mma": t32.value, "fp64_fma": f64.value}
 
 
 def ts_set_refinement(cond_threshold: float):
