@@ -964,7 +964,8 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link_blk(const SinrArgs A, co
   __syncthreads();
 
   // projection w[t][q] = sum_P C[P][q] conj(c_P(kappa_t)) (eq. 15): QS threads
-  // per subcarrier, thread qs handles q = qs, qs + QS, ...
+  // (consecutive lanes) per subcarrier, thread qs handles q = qs, qs + QS, ...
+  // and evaluates the coefficient of every QS-th path, shared by shuffles
   {
     const int t = tid / QS, qs = tid % QS;
     const int kap_t = kap0 + t;
@@ -973,19 +974,29 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link_blk(const SinrArgs A, co
     for (int u = 0; u < QA; ++u) acc[u] = cz();
     const float2* pa = sm + pl.off_pa;
     const unsigned long long* pt = reinterpret_cast<const unsigned long long*>(sm + pl.off_pt);
-    for (int pp = 0; pp < P; ++pp) {
-      float2 c = cz();
-      if (kap_t < K)
-        c = A.coef_mode == 0 ? cs[t * P + pp] : path_coef(pa[pp], pt[pp], kap_t);
-      if (A.identity_C) {
+    for (int p0 = 0; p0 < P; p0 += QS) {
+      float2 mine = cz();
+      const int pm = p0 + qs;
+      if (kap_t < K && pm < P)
+        mine = A.coef_mode == 0 ? cs[t * P + pm] : path_coef(pa[pm], pt[pm], kap_t);
 #pragma unroll
-        for (int u = 0; u < QA; ++u)
-          if (qs + u * QS == pp) acc[u] = cconj(c);
-      } else {
-        const float2* crow = Cs + pp * p;
+      for (int r = 0; r < QS; ++r) {
+        const int pp = p0 + r;
+        float2 c = mine;
+        if (QS > 1) c = gshfl<QS>(mine, r);
+        if (pp >= P) break;                          // uniform over the warp
+        if (A.identity_C) {
 #pragma unroll
-        for (int u = 0; u < QA; ++u)
-          if (qs + u * QS < p) cmacc(acc[u], crow[qs + u * QS], c);
+          for (int u = 0; u < QA; ++u)
+            if (qs + u * QS == pp) acc[u] = cconj(c);
+        } else {
+          const float2* crow = Cs + pp * p;
+#pragma unroll
+          for (int u = 0; u < QA; ++u) {
+            if (u * QS >= p) break;                  // uniform over the warp
+            if (qs + u * QS < p) cmacc(acc[u], crow[qs + u * QS], c);
+          }
+        }
       }
     }
 #pragma unroll
