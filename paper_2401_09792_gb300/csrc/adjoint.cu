@@ -268,62 +268,152 @@ __global__ void k_adj_dPt(const SinrArgs A, const float2* gV, float2* dPt) {
   }
 }
 
-// dl/dG[ch][q][a][c] = sum_kappa conj(w_q(kappa)) dl/dH~(kappa)[a][c]
-constexpr int kPMax = 32;
-__global__ void k_adj_dG(const SinrArgs A, const float2* W, const float2* gH, float2* dG) {
-  const int m = A.m, n = A.n, p = A.p, K = A.K, J = A.J;
-  const size_t total = (size_t)J * J * m * n;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const int ac = (int)(idx % ((size_t)m * n));
-    const int ch = (int)(idx / ((size_t)m * n));
-    float2 acc[kPMax];
+constexpr int kPMax = 32;          // largest core rank p
+constexpr int kAdjKChunk = 32;     // subcarriers staged per step
+
+// dl/dG[ch][q][ac] = sum_kappa conj(w[ch][kappa][q]) dl/dH~[ch][kappa][ac]:
+// CTA (128 threads) per (column tile of 128, link ch, subcarrier split s),
+// thread per column ac with p accumulators; the w rows of each chunk of
+// subcarriers staged in shared memory.  Partial sums of split s go to
+// out[s][ch][q][ac] (out = dG when there is one split).
+__global__ void __launch_bounds__(128) k_adj_dG(const SinrArgs A, const float2* W, const float2* gH,
+                                                float2* out, int ksplit) {
+  __shared__ float2 ws[kAdjKChunk * kPMax];
+  const int m = A.m, n = A.n, p = A.p, K = A.K, mn = m * n;
+  const int tid = threadIdx.x, ac = blockIdx.x * 128 + tid;
+  const int ch = blockIdx.y, s = blockIdx.z;
+  const int kper = (K + ksplit - 1) / ksplit;
+  const int k0 = s * kper, k1 = min(K, k0 + kper);
+  float2 acc[kPMax];
 #pragma unroll
-    for (int q = 0; q < kPMax; ++q) acc[q] = cz();
-    for (int kap = 0; kap < K; ++kap) {
-      const float2 gh = gH[((size_t)ch * K + kap) * m * n + ac];
-      const float2* wr = W + ((size_t)ch * K + kap) * p;
+  for (int q = 0; q < kPMax; ++q) acc[q] = cz();
+  for (int kc = k0; kc < k1; kc += kAdjKChunk) {
+    const int nk = min(kAdjKChunk, k1 - kc);
+    __syncthreads();
+    for (int idx = tid; idx < nk * p; idx += 128) ws[idx] = W[((size_t)ch * K + kc) * p + idx];
+    __syncthreads();
+    if (ac < mn) {
+      const float2* gh = gH + ((size_t)ch * K + kc) * mn + ac;
+#pragma unroll 4
+      for (int t = 0; t < nk; ++t) {
+        const float2 h = gh[(size_t)t * mn];
 #pragma unroll
-      for (int q = 0; q < kPMax; ++q)
-        if (q < p) cmacc(acc[q], gh, wr[q]);
+        for (int q = 0; q < kPMax; ++q) {
+          if (q >= p) break;
+          cmacc(acc[q], h, ws[t * p + q]);
+        }
+      }
     }
+  }
+  if (ac < mn) {
+    const size_t nch = (size_t)A.J * A.J;
 #pragma unroll
-    for (int q = 0; q < kPMax; ++q)
-      if (q < p) dG[((size_t)ch * p + q) * m * n + ac] = acc[q];
+    for (int q = 0; q < kPMax; ++q) {
+      if (q >= p) break;
+      out[((s * nch + ch) * p + q) * mn + ac] = acc[q];
+    }
   }
 }
 
-// dl/dw[ch][kappa][q] = sum_{a,c} conj(G[ch][q][a][c]) dl/dH~(kappa)[a][c]
-__global__ void k_adj_gw(const SinrArgs A, const float2* gH, float2* gw) {
-  const int m = A.m, n = A.n, p = A.p, K = A.K, J = A.J;
-  const size_t total = (size_t)J * J * K * p;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const int q = (int)(idx % p);
-    const size_t r = idx / p;
-    const int kap = (int)(r % K);
-    const int ch = (int)(r / K);
-    const float2* gh = gH + ((size_t)ch * K + kap) * m * n;
-    const float2* gq = A.G + ((size_t)ch * p + q) * m * n;
-    float2 acc = cz();
-    for (int ac = 0; ac < m * n; ++ac) cmacc(acc, gh[ac], gq[ac]);
-    gw[idx] = acc;
+// dl/dw[ch][kappa][q] = sum_ac conj(G[ch][q][ac]) dl/dH~(kappa)[ac]: CTA of
+// eight warps per (link ch, tile of eight subcarriers), warp per subcarrier,
+// lanes over ac; the core is staged in shared memory 128 columns at a time
+// and each warp's p sums are reduced across its lanes by shuffles.
+constexpr int kGwCols = 128;
+__global__ void __launch_bounds__(256) k_adj_gw(const SinrArgs A, const float2* gH, float2* gw) {
+  __shared__ float2 gs[kPMax * kGwCols];
+  const int m = A.m, n = A.n, p = A.p, K = A.K, mn = m * n;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int ch = blockIdx.y;
+  const int kap = blockIdx.x * 8 + warp;
+  const float2* Gc = A.G + (size_t)ch * p * mn;
+  const float2* gh = gH + ((size_t)ch * K + (kap < K ? kap : 0)) * mn;
+  float2 acc[kPMax];
+#pragma unroll
+  for (int q = 0; q < kPMax; ++q) acc[q] = cz();
+  for (int c0 = 0; c0 < mn; c0 += kGwCols) {
+    const int nc = min(kGwCols, mn - c0);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < p * kGwCols; idx += 256) {
+      const int q = idx / kGwCols, c = idx - q * kGwCols;
+      gs[idx] = c < nc ? Gc[(size_t)q * mn + c0 + c] : cz();
+    }
+    __syncthreads();
+    for (int c = lane; c < nc; c += 32) {
+      const float2 h = gh[c0 + c];
+#pragma unroll
+      for (int q = 0; q < kPMax; ++q) {
+        if (q >= p) break;
+        cmacc(acc[q], h, gs[q * kGwCols + c]);
+      }
+    }
+  }
+  float2 mine = cz();
+#pragma unroll
+  for (int q = 0; q < kPMax; ++q) {
+    if (q >= p) break;
+    float2 v = acc[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      v.x += __shfl_xor_sync(FULL, v.x, o);
+      v.y += __shfl_xor_sync(FULL, v.y, o);
+    }
+    if (lane == q) mine = v;
+  }
+  if (kap < K && lane < p) gw[((size_t)ch * K + kap) * p + lane] = mine;
+}
+
+// dl/dC[ch][P][q] = sum_kappa c_P(kappa) dl/dw[ch][kappa][q]: CTA (256
+// threads) per (tile of 32 paths, link ch, subcarrier split s); thread
+// (path row, q group) with the q = qg, qg + 8, ... sums; the coefficients
+// and dl/dw rows of each chunk of subcarriers staged in shared memory.
+__global__ void __launch_bounds__(256) k_adj_dC(const SinrArgs A, const float2* gw, float2* out,
+                                                int ksplit) {
+  __shared__ float2 cs[kAdjKChunk * 32];
+  __shared__ float2 gs[kAdjKChunk * kPMax];
+  const int p = A.p, P = A.P, K = A.K;
+  const int tid = threadIdx.x, pr = tid / 8, qg = tid % 8;
+  const int P0 = blockIdx.x * 32, ch = blockIdx.y, s = blockIdx.z;
+  const int kper = (K + ksplit - 1) / ksplit;
+  const int k0 = s * kper, k1 = min(K, k0 + kper);
+  float2 acc[kPMax / 8];
+#pragma unroll
+  for (int u = 0; u < kPMax / 8; ++u) acc[u] = cz();
+  for (int kc = k0; kc < k1; kc += kAdjKChunk) {
+    const int nk = min(kAdjKChunk, k1 - kc);
+    __syncthreads();
+    for (int idx = tid; idx < nk * 32; idx += 256) {
+      const int t = idx / 32, r = idx % 32;
+      cs[idx] = P0 + r < P ? coef_at(A, ch, kc + t, P0 + r) : cz();
+    }
+    for (int idx = tid; idx < nk * p; idx += 256) gs[idx] = gw[((size_t)ch * K + kc) * p + idx];
+    __syncthreads();
+    for (int t = 0; t < nk; ++t) {
+      const float2 c = cs[t * 32 + pr];
+#pragma unroll
+      for (int u = 0; u < kPMax / 8; ++u) {
+        const int q = qg + 8 * u;
+        if (q < p) cmac(acc[u], c, gs[t * p + q]);
+      }
+    }
+  }
+  if (P0 + pr < P) {
+    const size_t nch = (size_t)A.J * A.J;
+#pragma unroll
+    for (int u = 0; u < kPMax / 8; ++u) {
+      const int q = qg + 8 * u;
+      if (q < p) out[((s * nch + ch) * P + P0 + pr) * p + q] = acc[u];
+    }
   }
 }
 
-// dl/dC[ch][P][q] = sum_kappa c_P(kappa) dl/dw[ch][kappa][q]
-__global__ void k_adj_dC(const SinrArgs A, const float2* gw, float2* dC) {
-  const int p = A.p, P = A.P, K = A.K, J = A.J;
-  const size_t total = (size_t)J * J * P * p;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+// out[i] = sum_s part[s][i], s in order
+__global__ void k_adj_sum(const float2* part, int splits, size_t count, float2* out) {
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < count;
        idx += (size_t)gridDim.x * blockDim.x) {
-    const int q = (int)(idx % p);
-    const size_t r = idx / p;
-    const int pp = (int)(r % P);
-    const int ch = (int)(r / P);
-    float2 acc = cz();
-    for (int kap = 0; kap < K; ++kap) cmac(acc, coef_at(A, ch, kap, pp), gw[((size_t)ch * K + kap) * p + q]);
-    dC[idx] = acc;
+    float2 acc = part[idx];
+    for (int s = 1; s < splits; ++s) acc = cadd(acc, part[(size_t)s * count + idx]);
+    out[idx] = acc;
   }
 }
 
@@ -396,12 +486,25 @@ cudaError_t launch_adjoint(const SinrArgs& A, const AdjointWork& w, cudaStream_t
     k_adj_dPt<<<blocks_for((size_t)A.J * A.n * A.L), 256, 0, s>>>(A, w.gV, w.dPt);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_adj_dG<<<blocks_for(nch * A.m * A.n, 128), 128, 0, s>>>(A, w.W, w.gH, w.dG);
+  const AdjointSplit sp = adjoint_split(A.J, A.m, A.n, A.p, A.P, A.K);
+  const size_t ng = nch * A.p * A.m * A.n, nc = nch * A.P * A.p;
+  k_adj_dG<<<dim3((A.m * A.n + 127) / 128, (unsigned)nch, sp.kg), 128, 0, s>>>(
+      A, w.W, w.gH, sp.kg > 1 ? w.part : w.dG, sp.kg);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_adj_gw<<<blocks_for(nch * A.K * A.p), 256, 0, s>>>(A, w.gH, w.gw);
+  if (sp.kg > 1) {
+    k_adj_sum<<<blocks_for(ng), 256, 0, s>>>(w.part, sp.kg, ng, w.dG);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  k_adj_gw<<<dim3((A.K + 7) / 8, (unsigned)nch), 256, 0, s>>>(A, w.gH, w.gw);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_adj_dC<<<blocks_for(nch * A.P * A.p), 256, 0, s>>>(A, w.gw, w.dC);
-  return cudaGetLastError();
+  k_adj_dC<<<dim3((A.P + 31) / 32, (unsigned)nch, sp.kc), 256, 0, s>>>(
+      A, w.gw, sp.kc > 1 ? w.part : w.dC, sp.kc);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (sp.kc > 1) {
+    k_adj_sum<<<blocks_for(nc), 256, 0, s>>>(w.part, sp.kc, nc, w.dC);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_project_precoder_adjoint(const float2* Pfull, const float2* dPt, int J, int N,

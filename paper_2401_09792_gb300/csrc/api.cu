@@ -119,7 +119,7 @@ size_t prec_workspace_bytes(const ts_dims* d, int prec) {
 // Adjoint workspace (byte offsets, each 256-byte aligned).
 struct AdjWorkspace {
   size_t turns = 0, Hall = 0, V = 0, Eserv = 0, pflag = 0, U = 0, S = 0, Vm = 0, W = 0, E = 0,
-         gE = 0, gH = 0, gV = 0, gw = 0, total = 0;
+         gE = 0, gH = 0, gV = 0, gw = 0, part = 0, total = 0;
 };
 
 AdjWorkspace carve_adjoint(const ts_dims* d, bool svd) {
@@ -143,6 +143,7 @@ AdjWorkspace carve_adjoint(const ts_dims* d, bool svd) {
   w.gH = take(nch * K * m * n * sizeof(float2));
   w.gV = take((size_t)d->J * K * n * L * sizeof(float2));
   w.gw = take(nch * K * p * sizeof(float2));
+  w.part = take(ts::adjoint_part_elems(d->J, d->m, d->n, d->p, d->P, d->K) * sizeof(float2));
   w.total = o;
   return w;
 }
@@ -336,6 +337,7 @@ int adjoint_impl(const ts_dims* d, const ts_coef* coef, const ts_c64* G, const t
     aw.gw = reinterpret_cast<float2*>(base + w.gw);
     aw.dG = reinterpret_cast<float2*>(dG);
     aw.dC = reinterpret_cast<float2*>(dC);
+    aw.part = reinterpret_cast<float2*>(base + w.part);
     aw.dPt = reinterpret_cast<float2*>(dPt);
     e = ts::launch_adjoint(a, aw, s);
   }

@@ -81,7 +81,32 @@ struct AdjointWork {
   float2* dG;              // [J*J][p][m][n]
   float2* dC;              // [J*J][P][p]
   float2* dPt;             // [J][n][L] (wideband)
+  float2* part;            // split-K partial sums of dG and dC (adjoint_part_elems)
 };
+// Split of the subcarrier sums of dl/dG and dl/dC over CTAs, so that small
+// systems still fill the GPU (partial sums are added in a fixed order).
+struct AdjointSplit {
+  int kg, kc;              // subcarrier splits of the dl/dG and dl/dC sums
+};
+inline AdjointSplit adjoint_split(int J, int m, int n, int p, int P, int K) {
+  const long nch = (long)J * J;
+  const long g_tiles = nch * ((m * n + 127) / 128), c_tiles = nch * ((P + 31) / 32);
+  auto pick = [&](long tiles) {
+    long s = (608 + tiles - 1) / tiles;             // at least four CTAs per SM
+    const long smax = (K + 63) / 64;                // at least 64 subcarriers per CTA
+    if (s > smax) s = smax;
+    if (s > 16) s = 16;
+    return (int)(s < 1 ? 1 : s);
+  };
+  return AdjointSplit{pick(g_tiles), pick(c_tiles)};
+}
+inline size_t adjoint_part_elems(int J, int m, int n, int p, int P, int K) {
+  const AdjointSplit sp = adjoint_split(J, m, n, p, P, K);
+  const size_t nch = (size_t)J * J;
+  const size_t g = sp.kg > 1 ? (size_t)sp.kg * nch * p * m * n : 0;
+  const size_t c = sp.kc > 1 ? (size_t)sp.kc * nch * P * p : 0;
+  return g > c ? g : c;
+}
 cudaError_t launch_sinr_rebuild(const SinrArgs& a, cudaStream_t s);
 cudaError_t launch_sinr_serving(const SinrArgs& a, cudaStream_t s);
 // Tensor-core interfering-link pass (reduced-precision modes, sinr_tc.cu):
