@@ -219,6 +219,85 @@ def fit_groupwise(X: np.ndarray, ranks: tuple, S: int = 10, init=None,
     return {"A": A, "B": B, "C": C, "G": G, "g": np.array(g)}
 
 
+# ------------------------------------------- the three models of Section 3.1
+# Which factor a link (i, k) uses: groupwise (eq. 14) A_i and B_k; shared
+# (eq. 12) one A and one B for every link; individual (eq. 10) A_ik and
+# B_ik of its own.  C_ik and G_ik are per link in all three.
+MODELS = ("groupwise", "shared", "individual")
+
+
+def factor_groups(J: int, model: str):
+    """(number of A factors, number of B factors, a(i, k), b(i, k))."""
+    if model == "groupwise":
+        return J, J, (lambda i, k: i), (lambda i, k: k)
+    if model == "shared":
+        return 1, 1, (lambda i, k: 0), (lambda i, k: 0)
+    if model == "individual":
+        return J * J, J * J, (lambda i, k: i * J + k), (lambda i, k: i * J + k)
+    raise ValueError(model)
+
+
+def fit_model(X: np.ndarray, ranks: tuple, model: str = "groupwise", S: int = 10,
+              history: bool = False):
+    """Algorithm 2 for any of the three models: every factor is the leading
+    eigenvectors of the mode Gram summed over the links that share it
+    (eq. 20-22 with the sums over the sharing links), initialised with the
+    other two factors set to the identity, then S Gauss-Seidel sweeps (all A,
+    all B, all C), and the core of eq. (17).  For the groupwise model this is
+    fit_groupwise.  Returns dict(A, B, C, G, g) with A: (nA, M, m),
+    B: (nB, N, n), C: (J, J, P, p), G: (J, J, m, n, p)."""
+    m, n, p = ranks
+    J = X.shape[0]
+    nA, nB, ga, gb = factor_groups(J, model)
+    links = [(i, k) for i in range(J) for k in range(J)]
+
+    def gram_sum(group_of, g, M_of):
+        return sum(M_of(i, k) @ M_of(i, k).conj().T for (i, k) in links if group_of(i, k) == g)
+
+    A = np.stack([principal_eigvecs(gram_sum(ga, g, lambda i, k: unfold(X[i, k], 0)), m)
+                  for g in range(nA)])
+    B = np.stack([principal_eigvecs(gram_sum(gb, g, lambda i, k: unfold(X[i, k], 1)), n)
+                  for g in range(nB)])
+    C = np.empty((J, J, X.shape[4], p), dtype=np.complex128)
+    for i, k in links:
+        X3 = unfold(X[i, k], 2)
+        C[i, k] = principal_eigvecs(X3 @ X3.conj().T, p)
+
+    def g_now():
+        return sum(fro2(core(X[i, k], A[ga(i, k)], B[gb(i, k)], C[i, k])) for i, k in links)
+
+    g = [g_now()] if history else []
+    for _ in range(S):
+        A = np.stack([principal_eigvecs(gram_sum(ga, g_, lambda i, k: _M1(X[i, k], B[gb(i, k)], C[i, k])), m)
+                      for g_ in range(nA)])
+        if history:
+            g.append(g_now())
+        B = np.stack([principal_eigvecs(gram_sum(gb, g_, lambda i, k: _M2(X[i, k], A[ga(i, k)], C[i, k])), n)
+                      for g_ in range(nB)])
+        if history:
+            g.append(g_now())
+        for i, k in links:
+            M3 = _M3(X[i, k], A[ga(i, k)], B[gb(i, k)])
+            C[i, k] = principal_eigvecs(M3 @ M3.conj().T, p)
+        if history:
+            g.append(g_now())
+    G = np.empty((J, J, m, n, p), dtype=np.complex128)
+    for i, k in links:
+        G[i, k] = core(X[i, k], A[ga(i, k)], B[gb(i, k)], C[i, k])
+    if not history:
+        g = [sum(fro2(G[i, k]) for i, k in links)]
+    return {"A": A, "B": B, "C": C, "G": G, "g": np.array(g)}
+
+
+def reconstruct_model(G, A, B, C, model: str) -> np.ndarray:
+    """X^_ik = G_ik x_1 A x_2 B x_3 C_ik with the model's factor of each link:
+    (J, J, M, N, P)."""
+    J = G.shape[0]
+    _, _, ga, gb = factor_groups(J, model)
+    return np.stack([np.stack([tucker_reconstruct(G[i, k], A[ga(i, k)], B[gb(i, k)], C[i, k])
+                               for k in range(J)]) for i in range(J)])
+
+
 # ------------------------------------------------- Table (Section 3.3), eq. 29
 def storage_original(J, K, M, N, P) -> int:
     """Complex entries of all channel tensors before compression (Table, Section 3.3)."""

@@ -169,3 +169,75 @@ def test_storage_ratio_table1():
     for model, J, M, N, P, K, m, n, p, rs in rows:
         got = T.storage_ratio(int(J), int(K), int(M), int(N), int(P), int(m), int(n), int(p), model)
         assert abs(got - float(rs)) < 1.5e-4, (model, got, rs)
+
+
+# ------------------------------------------- shared and individual models
+def _g_model(X, fit, model):
+    J = X.shape[0]
+    _, _, ga, gb = T.factor_groups(J, model)
+    return sum(T.fro2(T.core(X[i, k], fit["A"][ga(i, k)], fit["B"][gb(i, k)], fit["C"][i, k]))
+               for i in range(J) for k in range(J))
+
+
+def test_model_fit_groupwise_is_algorithm_2():
+    # the generic fit with groupwise groups reproduces fit_groupwise
+    rng = np.random.default_rng(21)
+    X = _small_system(rng, J=2, M=4, N=6, P=5)
+    a = T.fit_model(X, (2, 3, 2), "groupwise", S=3, history=True)
+    b = T.fit_groupwise(X, (2, 3, 2), S=3, history=True)
+    np.testing.assert_allclose(a["g"], b["g"], rtol=1e-12)
+
+
+def test_individual_init_is_hosvd_of_each_link():
+    # individual model, no sweep: every link's factors are its own HOSVD
+    # (Algorithm 1), whose subspaces come from numpy's SVD
+    rng = np.random.default_rng(22)
+    X = _small_system(rng, J=2, M=4, N=6, P=5)
+    fit = T.fit_model(X, (2, 3, 2), "individual", S=0)
+    for i in range(2):
+        for k in range(2):
+            _, A, B, C = T.hosvd(X[i, k], (2, 3, 2))
+            proj = lambda F: F @ F.conj().T  # noqa: E731
+            assert np.linalg.norm(proj(fit["A"][i * 2 + k]) - proj(A)) < 1e-9
+            assert np.linalg.norm(proj(fit["B"][i * 2 + k]) - proj(B)) < 1e-9
+            assert np.linalg.norm(proj(fit["C"][i, k]) - proj(C)) < 1e-9
+
+
+@pytest.mark.parametrize("model", ["shared", "individual"])
+def test_model_fit_identities(model):
+    rng = np.random.default_rng(23)
+    X = _small_system(rng, J=3, M=4, N=6, P=5)
+    fit = T.fit_model(X, (2, 3, 2), model, S=4, history=True)
+    g = fit["g"]
+    # every block update maximises g over its block: non-decreasing
+    assert np.all(np.diff(g) >= -1e-10 * g[0])
+    # eq. (18) with the model's factors, by explicit reconstruction
+    Xh = T.reconstruct_model(fit["G"], fit["A"], fit["B"], fit["C"], model)
+    f = T.fro2(X - Xh)
+    assert abs(f - (T.fro2(X) - g[-1])) < 1e-9 * T.fro2(X)
+    assert abs(g[-1] - _g_model(X, fit, model)) < 1e-9 * g[-1]
+    nA, nB, _, _ = T.factor_groups(3, model)
+    assert fit["A"].shape == (nA, 4, 2) and fit["B"].shape == (nB, 6, 3)
+
+
+def test_one_cell_models_coincide():
+    # with one cell every model has one A, one B and one link: the same fit
+    rng = np.random.default_rng(24)
+    X = _small_system(rng, J=1, M=5, N=6, P=4)
+    g = [T.fit_model(X, (2, 3, 2), mdl, S=3, history=True)["g"] for mdl in T.MODELS]
+    np.testing.assert_allclose(g[1], g[0], rtol=1e-12)
+    np.testing.assert_allclose(g[2], g[0], rtol=1e-12)
+
+
+def test_model_storage_order_and_accuracy_order():
+    # storage: shared < groupwise < individual entries (Table 1's R_s order);
+    # fit quality: individual >= groupwise >= shared at full convergence of a
+    # tiny system (more factors fit more)
+    rng = np.random.default_rng(25)
+    X = _small_system(rng, J=2, M=4, N=6, P=5)
+    g = {mdl: T.fit_model(X, (2, 3, 2), mdl, S=20)["g"][-1] for mdl in T.MODELS}
+    assert g["individual"] >= g["groupwise"] * (1 - 1e-9)
+    assert g["groupwise"] >= g["shared"] * (1 - 1e-9)
+    args = (2, 1, 4, 6, 5, 2, 3, 2)
+    assert (T.storage_ratio(*args, model="shared") > T.storage_ratio(*args, model="groupwise")
+            > T.storage_ratio(*args, model="individual"))
