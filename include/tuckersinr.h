@@ -101,7 +101,21 @@ enum {
   TS_OP_SINR_MMSE_ADJOINT = 5,
   TS_OP_TUCKER_FIT = 6,
   TS_OP_SINR_SVD_TF32 = 7,    /* ts_sinr_svd_prec with TS_PREC_TF32   */
-  TS_OP_SINR_SVD_BF16X2 = 8   /* ts_sinr_svd_prec with TS_PREC_BF16X2 */
+  TS_OP_SINR_SVD_BF16X2 = 8,  /* ts_sinr_svd_prec with TS_PREC_BF16X2 */
+  TS_OP_TUCKER_FIT_SHARED = 9,     /* ts_tucker_fit_model, TS_MODEL_SHARED     */
+  TS_OP_TUCKER_FIT_INDIVIDUAL = 10, /* ts_tucker_fit_model, TS_MODEL_INDIVIDUAL */
+  TS_OP_RECONSTRUCT = 11           /* ts_tucker_reconstruct                    */
+};
+
+/* The three compression models of Section 3.1: which links share the
+ * receive (A) and transmit (B) factors.  Groupwise (eq. 14): A_i for the
+ * links into UE i, B_k for the links out of BS k (J of each).  Shared
+ * (eq. 12): one A and one B for every link.  Individual (eq. 10): A_ik and
+ * B_ik per link (J^2 of each).  C_ik and G_ik are per link in all three. */
+enum {
+  TS_MODEL_GROUPWISE = 0,
+  TS_MODEL_SHARED = 1,
+  TS_MODEL_INDIVIDUAL = 2
 };
 
 /* Arithmetic of the core contraction H~ = G x_3 (c* C) (eq. 15) in
@@ -315,6 +329,25 @@ int ts_dense_sinr_mmse(const ts_dims* d, const ts_coef* coef, const ts_c64* X,
 int ts_tucker_fit(const ts_dims* d, const ts_c64* X, int S, int init, ts_c64* A,
                   ts_c64* B, ts_c64* C, ts_c64* G, double* g_hist, void* ws,
                   size_t ws_bytes, void* stream);
+
+/* Algorithm 2 for any of the three models (TS_MODEL_*): the same
+ * initialisation and Gauss-Seidel sweeps, each factor fitted from the mode
+ * Gram summed over the links that share it.  A: [nA][M][m], B: [nB][N][n]
+ * with nA = nB = J (groupwise), 1 (shared) or J^2 (individual, link i*J+k);
+ * other arguments as ts_tucker_fit (which is the groupwise model).
+ * ws: ts_workspace_bytes(d, TS_OP_TUCKER_FIT / _FIT_SHARED / _FIT_INDIVIDUAL). */
+int ts_tucker_fit_model(const ts_dims* d, const ts_c64* X, int S, int init, int model, ts_c64* A,
+                        ts_c64* B, ts_c64* C, ts_c64* G, double* g_hist, void* ws, size_t ws_bytes,
+                        void* stream);
+
+/* Reconstruction X^_ik = G_ik x_1 A x_2 B x_3 C_ik (eq. 10, 12, 14) with the
+ * model's factors, FP32: Xhat (out) [J*J][P][M][N] -- e.g. to evaluate a
+ * model whose factors do not cancel (individual) on the dense-channel path.
+ * Factor layouts as ts_tucker_fit_model; G: [J*J][p][m][n].
+ * ws: ts_workspace_bytes(d, TS_OP_RECONSTRUCT) bytes. */
+int ts_tucker_reconstruct(const ts_dims* d, int model, const ts_c64* A, const ts_c64* B,
+                          const ts_c64* C, const ts_c64* G, ts_c64* Xhat, void* ws,
+                          size_t ws_bytes, void* stream);
 
 /* Adjoints (vector-Jacobian products) of the compressed SINR.  The paper has
  * no adjoint; these differentiate its compressed SINR (eq. 15, 23-28) for a

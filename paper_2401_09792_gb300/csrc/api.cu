@@ -148,8 +148,8 @@ AdjWorkspace carve_adjoint(const ts_dims* d, bool svd) {
   return w;
 }
 
-ts::FitDims fit_dims(const ts_dims* d) {
-  return ts::FitDims{d->J, d->M, d->N, d->P, d->m, d->n, d->p};
+ts::FitDims fit_dims(const ts_dims* d, int model = TS_MODEL_GROUPWISE) {
+  return ts::FitDims{d->J, d->M, d->N, d->P, d->m, d->n, d->p, model};
 }
 
 // Sizes the fit accepts: ranks up to 64 (eigensolver block limit).
@@ -246,6 +246,13 @@ size_t ts_workspace_bytes(const ts_dims* d, int op) {
   }
   if (check_dims(d) != TS_OK) return 0;
   if (op == TS_OP_TUCKER_FIT) return fit_checks(d) == TS_OK ? ts::fit_workspace_bytes(fit_dims(d)) : 0;
+  if (op == TS_OP_TUCKER_FIT_SHARED || op == TS_OP_TUCKER_FIT_INDIVIDUAL)
+    return fit_checks(d) == TS_OK
+               ? ts::fit_workspace_bytes(fit_dims(d, op == TS_OP_TUCKER_FIT_SHARED ? TS_MODEL_SHARED
+                                                                                 : TS_MODEL_INDIVIDUAL))
+               : 0;
+  if (op == TS_OP_RECONSTRUCT)
+    return fit_checks(d) == TS_OK ? ts::reconstruct_workspace_bytes(fit_dims(d)) : 0;
   if (op == TS_OP_SINR_SVD_ADJOINT || op == TS_OP_SINR_MMSE_ADJOINT)
     return carve_adjoint(d, op == TS_OP_SINR_SVD_ADJOINT).total;
   if (op == TS_OP_SINR_SVD_TF32 || op == TS_OP_SINR_SVD_BF16X2)
@@ -365,19 +372,46 @@ int ts_sinr_mmse_adjoint(const ts_dims* d, const ts_coef* coef, const ts_c64* G,
 
 int ts_tucker_fit(const ts_dims* d, const ts_c64* X, int S, int init, ts_c64* A, ts_c64* B,
                   ts_c64* C, ts_c64* G, double* g_hist, void* ws, size_t ws_bytes, void* stream) {
+  return ts_tucker_fit_model(d, X, S, init, TS_MODEL_GROUPWISE, A, B, C, G, g_hist, ws, ws_bytes,
+                             stream);
+}
+
+int ts_tucker_fit_model(const ts_dims* d, const ts_c64* X, int S, int init, int model, ts_c64* A,
+                        ts_c64* B, ts_c64* C, ts_c64* G, double* g_hist, void* ws, size_t ws_bytes,
+                        void* stream) {
   int st = fit_checks(d);
   if (st != TS_OK) return st;
+  if (model != TS_MODEL_GROUPWISE && model != TS_MODEL_SHARED && model != TS_MODEL_INDIVIDUAL)
+    return TS_ERR_MODE;
   if (S < 0 || (init != 0 && init != 1)) return TS_ERR_MODE;
   if (X == nullptr || A == nullptr || B == nullptr || C == nullptr || G == nullptr) return TS_ERR_NULL;
   if (!aligned8(X) || !aligned8(A) || !aligned8(B) || !aligned8(C) || !aligned8(G) || !aligned8(g_hist))
     return TS_ERR_ALIGN;
-  const ts::FitDims f = fit_dims(d);
+  const ts::FitDims f = fit_dims(d, model);
   if (ws == nullptr || ws_bytes < ts::fit_workspace_bytes(f)) return TS_ERR_WORKSPACE;
   if (((uintptr_t)ws & 255u) != 0) return TS_ERR_ALIGN;
   return cuda_status(ts::launch_fit(f, reinterpret_cast<const float2*>(X), S, init,
                                     reinterpret_cast<float2*>(A), reinterpret_cast<float2*>(B),
                                     reinterpret_cast<float2*>(C), reinterpret_cast<float2*>(G),
                                     g_hist, ws, static_cast<cudaStream_t>(stream)));
+}
+
+int ts_tucker_reconstruct(const ts_dims* d, int model, const ts_c64* A, const ts_c64* B,
+                          const ts_c64* C, const ts_c64* G, ts_c64* Xhat, void* ws, size_t ws_bytes,
+                          void* stream) {
+  int st = fit_checks(d);
+  if (st != TS_OK) return st;
+  if (model != TS_MODEL_GROUPWISE && model != TS_MODEL_SHARED && model != TS_MODEL_INDIVIDUAL)
+    return TS_ERR_MODE;
+  if (A == nullptr || B == nullptr || C == nullptr || G == nullptr || Xhat == nullptr) return TS_ERR_NULL;
+  if (!aligned8(A) || !aligned8(B) || !aligned8(C) || !aligned8(G) || !aligned8(Xhat)) return TS_ERR_ALIGN;
+  const ts::FitDims f = fit_dims(d, model);
+  if (ws == nullptr || ws_bytes < ts::reconstruct_workspace_bytes(f)) return TS_ERR_WORKSPACE;
+  if (((uintptr_t)ws & 255u) != 0) return TS_ERR_ALIGN;
+  return cuda_status(ts::launch_reconstruct(
+      f, reinterpret_cast<const float2*>(A), reinterpret_cast<const float2*>(B),
+      reinterpret_cast<const float2*>(C), reinterpret_cast<const float2*>(G),
+      reinterpret_cast<float2*>(Xhat), ws, static_cast<cudaStream_t>(stream)));
 }
 
 int ts_project_precoder_adjoint(const ts_dims* d, const ts_c64* Pfull, const ts_c64* dPt,

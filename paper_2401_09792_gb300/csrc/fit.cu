@@ -1,4 +1,7 @@
-// Groupwise Tucker fit (Section 3.2, Algorithm 2) on the GPU, in FP64.
+// Groupwise Tucker fit (Section 3.2, Algorithm 2) on the GPU, in FP64, and
+// the same alternating update for the shared (eq. 12: one A, one B) and
+// individual (eq. 10: A_ik, B_ik per link) models: every factor is fitted
+// from the mode Gram summed over the links that share it.
 //
 // X_ik ~ G_ik x_1 A_i x_2 B_k x_3 C_ik (eq. 14) with one UE per cell: link
 // ch = i*J + k.  After the initialisation (eq. 20-22 with the other factors
@@ -59,10 +62,17 @@ int nblocks(size_t total) {
 // out = in x_mode U^H for every link l: the contracted index i of `mode`
 // (0: i1, 1: i2, 2: i3) becomes r, out[..r..] = sum_i conj(U[i][r]) in[..i..].
 // Dims of `in`: d1, d2, d3; the factor of link l is U + off(l) * dim * r
-// where off(l) = l / J (A_i), l % J (B_k) or l (C_ik) by `fsel`.
+// where off(l) is the link's A (fsel 0) or B (fsel 1) factor under `model`,
+// or l (C_ik, fsel 2).
+__device__ __forceinline__ int factor_of(int l, int J, int fsel, int model) {
+  if (fsel == 2 || model == 2) return l;
+  if (model == 1) return 0;
+  return fsel == 0 ? l / J : l % J;
+}
+
 template <typename TIn>
 __global__ void k_modeprod(const TIn* in, int nlink, int J, int d1, int d2, int d3, int mode,
-                           const double2* U, int fsel, int r, double2* out) {
+                           const double2* U, int fsel, int model, int r, double2* out) {
   const int o1 = mode == 0 ? r : d1, o2 = mode == 1 ? r : d2, o3 = mode == 2 ? r : d3;
   const int dim = mode == 0 ? d1 : mode == 1 ? d2 : d3;
   const size_t per = (size_t)o1 * o2 * o3;
@@ -75,7 +85,7 @@ __global__ void k_modeprod(const TIn* in, int nlink, int J, int d1, int d2, int 
     t /= o2;
     const int j1 = (int)(t % o1);
     const int j3 = (int)(t / o1);
-    const int f = fsel == 0 ? l / J : fsel == 1 ? l % J : l;
+    const int f = factor_of(l, J, fsel, model);
     const double2* Uf = U + (size_t)f * dim * r;
     const TIn* src = in + (size_t)l * d1 * d2 * d3;
     double2 acc = dz();
@@ -93,12 +103,16 @@ __global__ void k_modeprod(const TIn* in, int nlink, int J, int d1, int d2, int 
   }
 }
 
-// Summed mode Gram.  gmode 0: Gram_i = sum_k T_(1) T_(1)^H over links (i, k);
-// gmode 1: Gram_k = sum_i T_(2) T_(2)^H over links (i, k); gmode 2: one Gram
-// T_(3) T_(3)^H per link.  T is [l][d3][d1][d2].
-__global__ void k_gram(const double2* T, int J, int d1, int d2, int d3, int gmode, double2* Gm) {
+// Summed mode Gram.  gmode 0: one Gram T_(1) T_(1)^H per A factor, summed
+// over the links that share it (groupwise: links (i, k) for fixed i); gmode
+// 1: the same for B (groupwise: fixed k); gmode 2: one Gram T_(3) T_(3)^H per
+// link.  T is [l][d3][d1][d2].
+__global__ void k_gram(const double2* T, int J, int d1, int d2, int d3, int gmode, int model,
+                       double2* Gm) {
   const int dim = gmode == 0 ? d1 : gmode == 1 ? d2 : d3;
-  const int nmat = gmode == 2 ? J * J : J;
+  const int nmat = gmode == 2 ? J * J : fit_groups(J, model);
+  // links of group g: groupwise J of them, shared all J^2, individual one
+  const int nsum = gmode == 2 || model == 2 ? 1 : model == 1 ? J * J : J;
   const size_t total = (size_t)nmat * dim * dim;
   const size_t per = (size_t)d1 * d2 * d3;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
@@ -107,8 +121,8 @@ __global__ void k_gram(const double2* T, int J, int d1, int d2, int d3, int gmod
     const int a = (int)((idx / dim) % dim);
     const int g = (int)(idx / ((size_t)dim * dim));
     double2 acc = dz();
-    for (int s = 0; s < (gmode == 2 ? 1 : J); ++s) {
-      const int l = gmode == 0 ? g * J + s : gmode == 1 ? s * J + g : g;
+    for (int s = 0; s < nsum; ++s) {
+      const int l = gmode == 2 || model == 2 ? g : model == 1 ? s : gmode == 0 ? g * J + s : s * J + g;
       const double2* src = T + (size_t)l * per;
       if (gmode == 0) {
         for (int i3 = 0; i3 < d3; ++i3)
@@ -466,6 +480,71 @@ cudaError_t leading_eigvecs(const double2* S, int nmat, int D, int r, double2* F
 
 }  // namespace fit
 
+namespace fit {
+namespace {
+
+// One forward mode product per launch, FP32: out = in x_mode U with U the
+// link's factor ([dim_out][r], row-major), in [l][i3][i1][i2] with the
+// contracted index of `mode` running over r.
+__global__ void k_expand(const float2* in, int nlink, int J, int o1, int o2, int o3, int mode,
+                         const float2* U, int fsel, int model, int r, float2* out) {
+  const size_t per = (size_t)o1 * o2 * o3;
+  const size_t total = per * nlink;
+  const int i1n = mode == 0 ? r : o1, i2n = mode == 1 ? r : o2;
+  const int dim = mode == 0 ? o1 : mode == 1 ? o2 : o3;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int l = (int)(idx / per);
+    size_t t = idx - (size_t)l * per;
+    const int j2 = (int)(t % o2);
+    t /= o2;
+    const int j1 = (int)(t % o1);
+    const int j3 = (int)(t / o1);
+    const float2* Uf = U + (size_t)factor_of(l, J, fsel, model) * dim * r;
+    const size_t lin = (size_t)l * (mode == 0 ? (size_t)r * o2 * o3 : mode == 1 ? (size_t)o1 * r * o3
+                                                                               : (size_t)o1 * o2 * r);
+    float2 acc = make_float2(0.f, 0.f);
+    for (int q = 0; q < r; ++q) {
+      const float2 u = Uf[(size_t)(mode == 0 ? j1 : mode == 1 ? j2 : j3) * r + q];
+      const size_t src = mode == 0 ? ((size_t)j3 * i1n + q) * i2n + j2
+                       : mode == 1 ? ((size_t)j3 * i1n + j1) * i2n + q
+                                   : ((size_t)q * i1n + j1) * i2n + j2;
+      const float2 v = in[lin + src];
+      acc.x = fmaf(u.x, v.x, acc.x);
+      acc.x = fmaf(-u.y, v.y, acc.x);
+      acc.y = fmaf(u.x, v.y, acc.y);
+      acc.y = fmaf(u.y, v.x, acc.y);
+    }
+    out[idx] = acc;
+  }
+}
+
+}  // namespace
+}  // namespace fit
+
+size_t reconstruct_workspace_bytes(const FitDims& f) {
+  const size_t J2 = (size_t)f.J * f.J;
+  auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+  return al(J2 * f.p * f.M * f.n * sizeof(float2)) + al(J2 * f.p * f.M * f.N * sizeof(float2));
+}
+
+cudaError_t launch_reconstruct(const FitDims& f, const float2* A, const float2* B, const float2* C,
+                               const float2* G, float2* Xhat, void* ws, cudaStream_t s) {
+  using namespace fit;
+  const size_t J2 = (size_t)f.J * f.J;
+  auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+  float2* T1 = static_cast<float2*>(ws);                                   // [l][p][M][n]
+  float2* T2 = reinterpret_cast<float2*>(static_cast<char*>(ws) + al(J2 * f.p * f.M * f.n * sizeof(float2)));
+  // G [l][p][m][n] x_1 A -> [l][p][M][n] x_2 B -> [l][p][M][N] x_3 C -> [l][P][M][N]
+  k_expand<<<nblocks(J2 * f.p * f.M * f.n), 256, 0, s>>>(G, (int)J2, f.J, f.M, f.n, f.p, 0, A, 0, f.model,
+                                                         f.m, T1);
+  k_expand<<<nblocks(J2 * f.p * f.M * f.N), 256, 0, s>>>(T1, (int)J2, f.J, f.M, f.N, f.p, 1, B, 1, f.model,
+                                                         f.n, T2);
+  k_expand<<<nblocks(J2 * f.P * f.M * f.N), 256, 0, s>>>(T2, (int)J2, f.J, f.M, f.N, f.P, 2, C, 2, f.model,
+                                                         f.p, Xhat);
+  return cudaGetLastError();
+}
+
 size_t fit_workspace_bytes(const FitDims& f) {
   const size_t J2 = (size_t)f.J * f.J;
   auto al = [](size_t x) { return (x + 255) / 256 * 256; };
@@ -474,18 +553,19 @@ size_t fit_workspace_bytes(const FitDims& f) {
   size_t tb = J2 * f.P * (size_t)(f.M > f.m ? f.M : f.m) * (f.N > f.n ? f.N : f.n);
   const size_t big = (tmax > tb ? tmax : tb) * c16;
   const int Dmax = f.N > f.M ? (f.N > f.P ? f.N : f.P) : (f.M > f.P ? f.M : f.P);
-  const size_t gram = (J2 * f.P * f.P + (size_t)f.J * f.M * f.M + (size_t)f.J * f.N * f.N) * c16;
+  const size_t nG = fit_groups(f.J, f.model);
+  const size_t gram = (J2 * f.P * f.P + nG * f.M * f.M + nG * f.N * f.N) * c16;
   const size_t blk = (size_t)J2 * Dmax * (fit::kJacobiMax) * c16;
   return al(J2 * f.P * f.M * f.N * c16) + 2 * al(big) + al(gram) + 3 * al(blk) +
-         al(((size_t)f.J * f.M * f.m + (size_t)f.J * f.N * f.n + J2 * f.P * f.p) * c16) +
-         al(J2 * sizeof(double));
+         al((nG * f.M * f.m + nG * f.N * f.n + J2 * f.P * f.p) * c16) + al(J2 * sizeof(double));
 }
 
 cudaError_t launch_fit(const FitDims& f, const float2* X, int S, int init, float2* A, float2* B,
                        float2* C, float2* G, double* g_hist, void* ws, cudaStream_t s) {
   using namespace fit;
-  const int J = f.J, M = f.M, N = f.N, P = f.P, m = f.m, n = f.n, p = f.p;
+  const int J = f.J, M = f.M, N = f.N, P = f.P, m = f.m, n = f.n, p = f.p, model = f.model;
   const size_t J2 = (size_t)J * J;
+  const int nG = fit_groups(J, model);       // A and B factors
   auto al = [](size_t x) { return (x + 255) / 256 * 256; };
   const size_t c16 = sizeof(double2);
   char* base = static_cast<char*>(ws);
@@ -499,17 +579,17 @@ cudaError_t launch_fit(const FitDims& f, const float2* X, int S, int init, float
   double2* T1 = reinterpret_cast<double2*>(take(big));
   double2* T2 = reinterpret_cast<double2*>(take(big));
   double2* GC = reinterpret_cast<double2*>(
-      take((J2 * P * P + (size_t)J * M * M + (size_t)J * N * N) * c16));
+      take((J2 * P * P + (size_t)nG * M * M + (size_t)nG * N * N) * c16));
   double2* GA = GC + J2 * P * P;
-  double2* GB = GA + (size_t)J * M * M;
+  double2* GB = GA + (size_t)nG * M * M;
   const size_t blk = (size_t)J2 * Dmax * kJacobiMax * c16;
   double2* Qb = reinterpret_cast<double2*>(take(blk));
   double2* Yb = reinterpret_cast<double2*>(take(blk));
   double2* Tb = reinterpret_cast<double2*>(take(blk));
   double2* A64 = reinterpret_cast<double2*>(
-      take(((size_t)J * M * m + (size_t)J * N * n + J2 * P * p) * c16));
-  double2* B64 = A64 + (size_t)J * M * m;
-  double2* C64 = B64 + (size_t)J * N * n;
+      take(((size_t)nG * M * m + (size_t)nG * N * n + J2 * P * p) * c16));
+  double2* B64 = A64 + (size_t)nG * M * m;
+  double2* C64 = B64 + (size_t)nG * N * n;
   double* lsum = reinterpret_cast<double*>(take(J2 * sizeof(double)));
   const int iters = 40;
   cudaError_t e = cudaSuccess;
@@ -523,42 +603,42 @@ cudaError_t launch_fit(const FitDims& f, const float2* X, int S, int init, float
   TS_FIT_CHECK();
   // X x_1 A^H -> [P][m][N]; then x_3 C^H -> [p][m][N] ; Gram over mode 2 (B)
   auto update_B = [&](bool warm) -> cudaError_t {
-    k_modeprod<double2><<<nblocks(J2 * P * m * N), 256, 0, s>>>(Xd, (int)J2, J, M, N, P, 0, A64, 0, m, T1);
-    k_modeprod<double2><<<nblocks(J2 * p * m * N), 256, 0, s>>>(T1, (int)J2, J, m, N, P, 2, C64, 2, p, T2);
-    k_gram<<<nblocks((size_t)J * N * N), 256, 0, s>>>(T2, J, m, N, p, 1, GB);
-    return leading_eigvecs(GB, J, N, n, B64, lsum, warm, Qb, Yb, Tb, iters, s);
+    k_modeprod<double2><<<nblocks(J2 * P * m * N), 256, 0, s>>>(Xd, (int)J2, J, M, N, P, 0, A64, 0, model, m, T1);
+    k_modeprod<double2><<<nblocks(J2 * p * m * N), 256, 0, s>>>(T1, (int)J2, J, m, N, P, 2, C64, 2, model, p, T2);
+    k_gram<<<nblocks((size_t)nG * N * N), 256, 0, s>>>(T2, J, m, N, p, 1, model, GB);
+    return leading_eigvecs(GB, nG, N, n, B64, lsum, warm, Qb, Yb, Tb, iters, s);
   };
   auto update_A = [&](bool warm) -> cudaError_t {
-    k_modeprod<double2><<<nblocks(J2 * P * M * n), 256, 0, s>>>(Xd, (int)J2, J, M, N, P, 1, B64, 1, n, T1);
-    k_modeprod<double2><<<nblocks(J2 * p * M * n), 256, 0, s>>>(T1, (int)J2, J, M, n, P, 2, C64, 2, p, T2);
-    k_gram<<<nblocks((size_t)J * M * M), 256, 0, s>>>(T2, J, M, n, p, 0, GA);
-    return leading_eigvecs(GA, J, M, m, A64, lsum, warm, Qb, Yb, Tb, iters, s);
+    k_modeprod<double2><<<nblocks(J2 * P * M * n), 256, 0, s>>>(Xd, (int)J2, J, M, N, P, 1, B64, 1, model, n, T1);
+    k_modeprod<double2><<<nblocks(J2 * p * M * n), 256, 0, s>>>(T1, (int)J2, J, M, n, P, 2, C64, 2, model, p, T2);
+    k_gram<<<nblocks((size_t)nG * M * M), 256, 0, s>>>(T2, J, M, n, p, 0, model, GA);
+    return leading_eigvecs(GA, nG, M, m, A64, lsum, warm, Qb, Yb, Tb, iters, s);
   };
   auto update_C = [&](bool warm) -> cudaError_t {
-    k_modeprod<double2><<<nblocks(J2 * P * m * N), 256, 0, s>>>(Xd, (int)J2, J, M, N, P, 0, A64, 0, m, T1);
-    k_modeprod<double2><<<nblocks(J2 * P * m * n), 256, 0, s>>>(T1, (int)J2, J, m, N, P, 1, B64, 1, n, T2);
-    k_gram<<<nblocks(J2 * P * P), 256, 0, s>>>(T2, J, m, n, P, 2, GC);
+    k_modeprod<double2><<<nblocks(J2 * P * m * N), 256, 0, s>>>(Xd, (int)J2, J, M, N, P, 0, A64, 0, model, m, T1);
+    k_modeprod<double2><<<nblocks(J2 * P * m * n), 256, 0, s>>>(T1, (int)J2, J, m, N, P, 1, B64, 1, model, n, T2);
+    k_gram<<<nblocks(J2 * P * P), 256, 0, s>>>(T2, J, m, n, P, 2, model, GC);
     return leading_eigvecs(GC, (int)J2, P, p, C64, lsum, warm, Qb, Yb, Tb, iters, s);
   };
   if (init == 0) {
     // eq. (20)-(22) with the other factors set to the identity
-    k_gram<<<nblocks((size_t)J * M * M), 256, 0, s>>>(Xd, J, M, N, P, 0, GA);
-    if ((e = leading_eigvecs(GA, J, M, m, A64, lsum, false, Qb, Yb, Tb, iters, s)) != cudaSuccess) return e;
-    k_gram<<<nblocks((size_t)J * N * N), 256, 0, s>>>(Xd, J, M, N, P, 1, GB);
-    if ((e = leading_eigvecs(GB, J, N, n, B64, lsum, false, Qb, Yb, Tb, iters, s)) != cudaSuccess) return e;
-    k_gram<<<nblocks(J2 * P * P), 256, 0, s>>>(Xd, J, M, N, P, 2, GC);
+    k_gram<<<nblocks((size_t)nG * M * M), 256, 0, s>>>(Xd, J, M, N, P, 0, model, GA);
+    if ((e = leading_eigvecs(GA, nG, M, m, A64, lsum, false, Qb, Yb, Tb, iters, s)) != cudaSuccess) return e;
+    k_gram<<<nblocks((size_t)nG * N * N), 256, 0, s>>>(Xd, J, M, N, P, 1, model, GB);
+    if ((e = leading_eigvecs(GB, nG, N, n, B64, lsum, false, Qb, Yb, Tb, iters, s)) != cudaSuccess) return e;
+    k_gram<<<nblocks(J2 * P * P), 256, 0, s>>>(Xd, J, M, N, P, 2, model, GC);
     if ((e = leading_eigvecs(GC, (int)J2, P, p, C64, lsum, false, Qb, Yb, Tb, iters, s)) != cudaSuccess) return e;
   } else {
-    k_to_double<<<nblocks((size_t)J * M * m), 256, 0, s>>>(A, (size_t)J * M * m, A64);
-    k_to_double<<<nblocks((size_t)J * N * n), 256, 0, s>>>(B, (size_t)J * N * n, B64);
+    k_to_double<<<nblocks((size_t)nG * M * m), 256, 0, s>>>(A, (size_t)nG * M * m, A64);
+    k_to_double<<<nblocks((size_t)nG * N * n), 256, 0, s>>>(B, (size_t)nG * N * n, B64);
     k_to_double<<<nblocks(J2 * P * p), 256, 0, s>>>(C, J2 * P * p, C64);
   }
   TS_FIT_CHECK();
   // core (eq. 17) of the current factors: W = X x_1 A^H x_2 B^H, G = W x_3 C^H
   auto core = [&]() {
-    k_modeprod<double2><<<nblocks(J2 * P * m * N), 256, 0, s>>>(Xd, (int)J2, J, M, N, P, 0, A64, 0, m, T1);
-    k_modeprod<double2><<<nblocks(J2 * P * m * n), 256, 0, s>>>(T1, (int)J2, J, m, N, P, 1, B64, 1, n, T2);
-    k_modeprod<double2><<<nblocks(J2 * p * m * n), 256, 0, s>>>(T2, (int)J2, J, m, n, P, 2, C64, 2, p, T1);
+    k_modeprod<double2><<<nblocks(J2 * P * m * N), 256, 0, s>>>(Xd, (int)J2, J, M, N, P, 0, A64, 0, model, m, T1);
+    k_modeprod<double2><<<nblocks(J2 * P * m * n), 256, 0, s>>>(T1, (int)J2, J, m, N, P, 1, B64, 1, model, n, T2);
+    k_modeprod<double2><<<nblocks(J2 * p * m * n), 256, 0, s>>>(T2, (int)J2, J, m, n, P, 2, C64, 2, model, p, T1);
   };
   if (g_hist != nullptr) {
     core();
@@ -567,17 +647,17 @@ cudaError_t launch_fit(const FitDims& f, const float2* X, int S, int init, float
   }
   for (int sw = 0; sw < S; ++sw) {
     if ((e = update_A(true)) != cudaSuccess) return e;
-    if (g_hist != nullptr) k_sum_g<<<1, 32, 0, s>>>(lsum, J, g_hist, 1 + 3 * sw);
+    if (g_hist != nullptr) k_sum_g<<<1, 32, 0, s>>>(lsum, nG, g_hist, 1 + 3 * sw);
     if ((e = update_B(true)) != cudaSuccess) return e;
-    if (g_hist != nullptr) k_sum_g<<<1, 32, 0, s>>>(lsum, J, g_hist, 2 + 3 * sw);
+    if (g_hist != nullptr) k_sum_g<<<1, 32, 0, s>>>(lsum, nG, g_hist, 2 + 3 * sw);
     if ((e = update_C(true)) != cudaSuccess) return e;
     if (g_hist != nullptr) k_sum_g<<<1, 32, 0, s>>>(lsum, (int)J2, g_hist, 3 + 3 * sw);
     TS_FIT_CHECK();
   }
   core();
   k_to_float<<<nblocks(J2 * p * m * n), 256, 0, s>>>(T1, J2 * p * m * n, G);
-  k_to_float<<<nblocks((size_t)J * M * m), 256, 0, s>>>(A64, (size_t)J * M * m, A);
-  k_to_float<<<nblocks((size_t)J * N * n), 256, 0, s>>>(B64, (size_t)J * N * n, B);
+  k_to_float<<<nblocks((size_t)nG * M * m), 256, 0, s>>>(A64, (size_t)nG * M * m, A);
+  k_to_float<<<nblocks((size_t)nG * N * n), 256, 0, s>>>(B64, (size_t)nG * N * n, B);
   k_to_float<<<nblocks(J2 * P * p), 256, 0, s>>>(C64, J2 * P * p, C);
   return cudaGetLastError();
 #undef TS_FIT_CHECK

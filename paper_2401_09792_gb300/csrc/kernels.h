@@ -128,8 +128,15 @@ cudaError_t launch_project_precoder_adjoint(const float2* Pfull, const float2* d
 // Groupwise Tucker fit (fit.cu).
 struct FitDims {
   int J, M, N, P, m, n, p;
+  int model;   // TS_MODEL_GROUPWISE, _SHARED or _INDIVIDUAL: which links share A and B
 };
+// number of A (B) factors of a model
+__host__ __device__ inline int fit_groups(int J, int model) { return model == 1 ? 1 : model == 2 ? J * J : J; }
 size_t fit_workspace_bytes(const FitDims& f);
+// X^ = G x_1 A x_2 B x_3 C of every link with the model's factors (fit.cu)
+size_t reconstruct_workspace_bytes(const FitDims& f);
+cudaError_t launch_reconstruct(const FitDims& f, const float2* A, const float2* B, const float2* C,
+                               const float2* G, float2* Xhat, void* ws, cudaStream_t s);
 cudaError_t launch_fit(const FitDims& f, const float2* X, int S, int init, float2* A, float2* B,
                        float2* C, float2* G, double* g_hist, void* ws, cudaStream_t s);
 

@@ -22,6 +22,8 @@ TS_COEF_DENSE, TS_COEF_PATHS = 0, 1
 TS_OP_SINR_SVD, TS_OP_SINR_MMSE, TS_OP_DENSE_SVD, TS_OP_DENSE_MMSE = 0, 1, 2, 3
 TS_OP_SINR_SVD_ADJOINT, TS_OP_SINR_MMSE_ADJOINT, TS_OP_TUCKER_FIT = 4, 5, 6
 TS_OP_SINR_SVD_TF32, TS_OP_SINR_SVD_BF16X2 = 7, 8
+TS_OP_TUCKER_FIT_SHARED, TS_OP_TUCKER_FIT_INDIVIDUAL, TS_OP_RECONSTRUCT = 9, 10, 11
+TS_MODEL_GROUPWISE, TS_MODEL_SHARED, TS_MODEL_INDIVIDUAL = 0, 1, 2
 TS_PREC_FP32, TS_PREC_TF32, TS_PREC_BF16X2 = 0, 1, 2
 TS_FLAG_NOT_PD, TS_FLAG_NONFINITE, TS_FLAG_RANK_DEFICIENT, TS_FLAG_EIG_UNCONVERGED = 1, 2, 4, 8
 TS_FLAG_TIMEOUT = 16
@@ -84,6 +86,10 @@ _SIG = {
                                           _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "ts_tucker_fit": (ctypes.c_int, [ctypes.POINTER(ts_dims), _P, ctypes.c_int, ctypes.c_int, _P, _P,
                                      _P, _P, _P, _P, ctypes.c_size_t, _P]),
+    "ts_tucker_fit_model": (ctypes.c_int, [ctypes.POINTER(ts_dims), _P, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_int, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
+    "ts_tucker_reconstruct": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.c_int, _P, _P, _P, _P, _P,
+                                             _P, ctypes.c_size_t, _P]),
     "ts_sinr_svd_adjoint": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.POINTER(ts_coef), _P, _P,
                                            _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "ts_sinr_mmse_adjoint": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.POINTER(ts_coef), _P, _P,
@@ -304,6 +310,20 @@ def ts_tucker_fit(d: Dims, X, S, init, A, B, C, G, g_hist, ws, stream=None):
     _check("ts_tucker_fit", lib.ts_tucker_fit(ctypes.byref(d.c()), _ptr(X), S, init, _ptr(A), _ptr(B),
                                               _ptr(C), _ptr(G), _ptr(g_hist), _ptr(ws), ws.numel(),
                                               _stream(stream)))
+
+
+def ts_tucker_fit_model(d: Dims, X, S, init, model, A, B, C, G, g_hist, ws, stream=None):
+    lib = load()
+    _check("ts_tucker_fit_model",
+           lib.ts_tucker_fit_model(ctypes.byref(d.c()), _ptr(X), S, init, model, _ptr(A), _ptr(B), _ptr(C),
+                                   _ptr(G), _ptr(g_hist), _ptr(ws), ws.numel(), _stream(stream)))
+
+
+def ts_tucker_reconstruct(d: Dims, model, A, B, C, G, Xhat, ws, stream=None):
+    lib = load()
+    _check("ts_tucker_reconstruct",
+           lib.ts_tucker_reconstruct(ctypes.byref(d.c()), model, _ptr(A), _ptr(B), _ptr(C), _ptr(G),
+                                     _ptr(Xhat), _ptr(ws), ws.numel(), _stream(stream)))
 
 
 def ts_sinr_svd_adjoint(d: Dims, coef: ts_coef, G, C, sigma2, dsinr, dG, dC, sinr, ws, stream=None):

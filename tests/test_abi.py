@@ -64,7 +64,15 @@ def test_workspace_sizes(lib):
     assert svd >= nch * P * 8 + 2 * K * n * L * 8 + 2 * K
     assert mmse >= nch * P * 8 + nch * p * m * L * 8
     assert svd % 256 == 0 and mmse % 256 == 0
-    assert lib.ts_workspace_bytes(ctypes.byref(d), 9) == 0
+    assert lib.ts_workspace_bytes(ctypes.byref(d), 12) == 0
+    # the fit per model: the summed-Gram buffers grow with the number of factors
+    # (shared 1, groupwise J, individual J^2); the reconstruction holds the two
+    # intermediate products G x_1 A and (G x_1 A) x_2 B
+    fit = [lib.ts_workspace_bytes(ctypes.byref(d), op) for op in (9, 6, 10)]
+    assert 0 < fit[0] <= fit[1] <= fit[2]
+    rec = lib.ts_workspace_bytes(ctypes.byref(d), 11)
+    M, N = 4, 32
+    assert rec >= nch * p * M * n * 8 + nch * p * M * N * 8
     # tensor-core modes: the svd workspace plus the rewritten core (per link:
     # TF32 2p K-elements of 4 bytes, BF16X2 6p of 2 bytes, per accumulator
     # column 2 MG n)
