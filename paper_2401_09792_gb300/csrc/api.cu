@@ -59,18 +59,28 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 bool aligned8(const void* p) { return ((uintptr_t)p & 7u) == 0; }
 
 // Sizes the SINR kernels accept.
-int check_dims(const ts_dims* d) {
+int check_dims(const ts_dims* d, bool identity = false) {
   if (d == nullptr) return TS_ERR_NULL;
   if (d->J < 1 || d->M < 1 || d->N < 1 || d->P < 1 || d->K < 1) return TS_ERR_DIMS;
   if (d->m < 1 || d->n < 1 || d->p < 1 || d->L < 1) return TS_ERR_DIMS;
   if (d->m > d->M || d->n > d->N || d->p > d->P) return TS_ERR_DIMS;
   if (d->m > ts::kMaxRankM) return TS_ERR_DIMS;
   if (d->L > d->m || d->L > d->n) return TS_ERR_DIMS;
-  // staging limits of the kernels: C_ik (P x p) and one H~ (m x n) per
-  // subcarrier live in shared memory
-  if (d->P > 1024 || d->p > 32 || (int64_t)d->P * d->p > 8192 || d->n > 512) return TS_ERR_DIMS;
+  // staging limits of the kernels: one H~ (m x n) per subcarrier and the
+  // projections w [subcarrier tile][p] live in shared memory
+  // (the dense-channel comparator, C = I, keeps no projections: p = P <= 1024)
+  if (d->P > 1024 || (!identity && d->p > ts::kMaxRankPWide) || d->n > 512) return TS_ERR_DIMS;
   if ((int64_t)d->J * d->J > 65535 || d->J > 65535) return TS_ERR_DIMS;
   return TS_OK;
+}
+
+// The wideband-precoder path and the adjoints stage C_ik (P x p) and a core
+// column chunk whole: p <= 32 and P p <= 8192.  The SVD path streams larger
+// cores through the wide-core kernel.
+int check_narrow(const ts_dims* d) {
+  const int st = check_dims(d);
+  if (st != TS_OK) return st;
+  return ts::wide_core(d->P, d->p) ? TS_ERR_DIMS : TS_OK;
 }
 
 // Workspace layout (byte offsets from the base, each 256-byte aligned).
@@ -241,7 +251,7 @@ size_t ts_workspace_bytes(const ts_dims* d, int op) {
   if (d == nullptr) return 0;
   if (op == TS_OP_DENSE_SVD || op == TS_OP_DENSE_MMSE) {
     const ts_dims e = dense_dims(d);
-    if (check_dims(&e) != TS_OK) return 0;
+    if ((op == TS_OP_DENSE_SVD ? check_dims(&e, true) : check_narrow(&e)) != TS_OK) return 0;
     return carve(&e, op == TS_OP_DENSE_SVD ? TS_OP_SINR_SVD : TS_OP_SINR_MMSE).total;
   }
   if (check_dims(d) != TS_OK) return 0;
@@ -254,9 +264,10 @@ size_t ts_workspace_bytes(const ts_dims* d, int op) {
   if (op == TS_OP_RECONSTRUCT)
     return fit_checks(d) == TS_OK ? ts::reconstruct_workspace_bytes(fit_dims(d)) : 0;
   if (op == TS_OP_SINR_SVD_ADJOINT || op == TS_OP_SINR_MMSE_ADJOINT)
-    return carve_adjoint(d, op == TS_OP_SINR_SVD_ADJOINT).total;
+    return check_narrow(d) == TS_OK ? carve_adjoint(d, op == TS_OP_SINR_SVD_ADJOINT).total : 0;
+  if (op == TS_OP_SINR_MMSE && check_narrow(d) != TS_OK) return 0;
   if (op == TS_OP_SINR_SVD_TF32 || op == TS_OP_SINR_SVD_BF16X2)
-    return ts::tc_supported(d->m, d->L, d->p)
+    return ts::tc_supported(d->m, d->L, d->p) && check_narrow(d) == TS_OK
                ? prec_workspace_bytes(d, op == TS_OP_SINR_SVD_TF32 ? TS_PREC_TF32 : TS_PREC_BF16X2)
                : 0;
   if (op != TS_OP_SINR_SVD && op != TS_OP_SINR_MMSE) return 0;
@@ -294,7 +305,7 @@ int adjoint_impl(const ts_dims* d, const ts_coef* coef, const ts_c64* G, const t
                  const ts_c64* Pt, const float* sigma2, const float* dsinr, ts_c64* dG, ts_c64* dC,
                  ts_c64* dPt, float* sinr, void* ws, size_t ws_bytes, void* stream) {
   const bool svd = Pt == nullptr;
-  int st = check_dims(d);
+  int st = check_narrow(d);
   if (st != TS_OK) return st;
   st = check_coef(coef);
   if (st != TS_OK) return st;
@@ -442,7 +453,7 @@ ts_dims dense_dims(const ts_dims* d) {
 int sinr_common_checks(const ts_dims* d, const ts_coef* coef, const ts_c64* G, const ts_c64* C,
                        bool identity, const float* sigma2, float* sinr, void* ws, size_t ws_bytes,
                        int op) {
-  int st = check_dims(d);
+  int st = op == TS_OP_SINR_MMSE ? check_narrow(d) : check_dims(d, identity);
   if (st != TS_OK) return st;
   st = check_coef(coef);
   if (st != TS_OK) return st;
@@ -533,7 +544,7 @@ int svd_from_precoders_prec_impl(const ts_dims* d, const ts_coef* coef, const ts
 
 int check_prec(const ts_dims* d, int precision) {
   if (precision != TS_PREC_TF32 && precision != TS_PREC_BF16X2) return TS_ERR_MODE;
-  int st = check_dims(d);
+  int st = check_narrow(d);
   if (st != TS_OK) return st;
   return ts::tc_supported(d->m, d->L, d->p) ? TS_OK : TS_ERR_MODE;
 }

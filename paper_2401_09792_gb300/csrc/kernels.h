@@ -121,6 +121,12 @@ cudaError_t launch_sinr_links_tc(const SinrArgs& a, int prec, const void* prep, 
 // subcarrier tile from L2) when the core is at most 64 KB; larger cores (the
 // dense-channel comparator) go through a separate serving-link pass.
 inline bool precoder_fuses_serve(int m, int n, int p) { return (long long)m * n * p <= 8192; }
+// Cores the narrow link kernels cannot stage (C_ik and a full core column
+// chunk in shared memory): the SVD path runs the wide-core kernel, which
+// streams the core in slabs and reads C_ik from L2.
+__host__ __device__ inline bool wide_core(int P, int p) { return p > 32 || (long long)P * p > 8192; }
+// Largest rank p of the wide-core kernel (w [T][p] in shared memory).
+constexpr int kMaxRankPWide = 256;
 cudaError_t launch_adjoint(const SinrArgs& a, const AdjointWork& w, cudaStream_t s);
 cudaError_t launch_project_precoder_adjoint(const float2* Pfull, const float2* dPt, int J, int N,
                                             int n, int L, float2* dB, cudaStream_t s);

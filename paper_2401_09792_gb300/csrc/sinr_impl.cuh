@@ -1104,6 +1104,294 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link_blk(const SinrArgs A, co
   }
 }
 
+// Wide-core variant of the blocked link pass, for ranks beyond what the
+// narrow kernels stage (p > 32 or P p > 8192): the paper's compressed sizes
+// (p ~ 100-200 of P ~ 400 paths) and the dense-channel comparator at large P.
+// Same thread layout as k_sinr_link_blk (two subcarriers and two rows per
+// lane).  The projection w = c* C reads C_ik from L2 in chunks of 32 columns
+// and keeps w [T][p] in shared memory; the core then streams through shared
+// memory in stages of (column chunk, kWideQC slabs G[q]), double-buffered,
+// and the H~ accumulators of a column chunk persist across its slabs.
+// Dense-channel comparator (C = I, p = P): w = c* is evaluated per stage
+// into the stage buffer instead.  SERVE: the serving link (k = i), whose
+// rows H~_ii(kappa) go to Hserv for the precoder kernel; otherwise the
+// interfering links' partial covariances, as in k_sinr_link_blk.
+constexpr int kWideQC = 16;
+
+struct WidePlan {
+  int T, nq, SG, SV, WS, wide;
+  int off_ws, off_stage, stage, off_Gs, off_Vs, off_Wc, total;
+};
+
+__host__ __device__ inline WidePlan wide_plan(int MG, int LT, int p, bool identity, bool serve) {
+  constexpr int NC = 4;
+  WidePlan pl;
+  pl.T = 2 * kThreads / (MG / 2);
+  pl.nq = (p + kWideQC - 1) / kWideQC;
+  pl.SG = NC + 2;
+  pl.SV = NC * LT + 2;
+  pl.WS = kWideQC + 1;
+  pl.wide = 0;
+  int o = 0;
+  pl.off_ws = o;
+  if (!identity) o += pl.T * (p + 1);
+  o = (o + 1) & ~1;
+  pl.off_stage = o;
+  int so = 0;
+  pl.off_Gs = so; so += kWideQC * MG * pl.SG;
+  pl.off_Vs = so; if (!serve) so += pl.T * pl.SV;
+  pl.off_Wc = so; if (identity) so += pl.T * pl.WS;
+  so = (so + 1) & ~1;
+  pl.stage = so;
+  const int es = (kThreads / (MG / 2)) * (2 * MG * LT + 2);
+  o += (2 * so > es ? 2 * so : es);
+  pl.total = o;
+  return pl;
+}
+
+template <int MG, int LT, bool SERVE>
+__global__ void __launch_bounds__(kThreads) k_sinr_link_wide(const SinrArgs A, const WidePlan pl) {
+  constexpr int NC = 4;
+  constexpr int GL = MG / 2;
+  constexpr int T = 2 * kThreads / GL;
+  constexpr int QS = kThreads / T;          // threads per subcarrier in the projection
+  constexpr int QA = 32 / QS;               // projection accumulators per thread and chunk
+  constexpr int QC = kWideQC;
+  extern __shared__ __align__(16) float2 sm[];
+  const int tid = threadIdx.x;
+  const int gp = tid / GL, j = tid % GL;
+  const int i = blockIdx.y, z = blockIdx.z;
+  const int kap0 = blockIdx.x * T;
+  const int J = A.J, m = A.m, n = A.n, p = A.p, L = A.L, K = A.K, P = A.P;
+  const int k = SERVE ? i : (z < i ? z : z + 1);
+  const int ch = i * J + k;
+  const int nq = pl.nq;
+  const int nstage = ((n + NC - 1) / NC) * nq;
+  const bool ident = A.identity_C;
+  float2* ws = sm + pl.off_ws;
+  float2* stage0 = sm + pl.off_stage;
+  const bool wide = pl.wide != 0;
+  if (!SERVE && A.rcount != nullptr && tid == 0 && blockIdx.x == 0 && i == 0 && z == 0) *A.rcount = 0;
+
+  // c_q(kappa) of this link (dense tile or path form), from global memory
+  auto coef_at = [&](int kap, int q) -> float2 {
+    return A.coef_mode == 0 ? A.coef[((size_t)ch * K + kap) * P + q]
+                            : path_coef(__ldg(A.coef + (size_t)ch * P + q),
+                                        __ldg(A.turns + (size_t)ch * P + q), kap);
+  };
+
+  auto issue_stage = [&](int st) {
+    float2* buf = stage0 + (st & 1) * pl.stage;
+    const int cidx = st / nq, qi = st - cidx * nq;
+    const int c0 = cidx * NC, q0 = qi * QC;
+    const int qc = min(QC, p - q0);
+    const float2* Gch = A.G + (size_t)ch * p * m * n;
+    if (wide) {
+      constexpr int GU = MG * NC / 2;                 // 16-byte units per slab
+      const int cc = 2 * (tid % (NC / 2)), aa = (tid / (NC / 2)) % MG;
+      const bool rowok = aa < m && c0 + cc < n;
+      for (int ql = tid / GU; ql < qc; ql += kThreads / GU)
+        cp_async16(buf + pl.off_Gs + (ql * MG + aa) * pl.SG + cc,
+                   rowok ? Gch + ((size_t)(q0 + ql) * m + aa) * n + c0 + cc : A.G, rowok);
+      if (!SERVE && qi == nq - 1) {
+        constexpr int VU = NC * LT / 2;
+        const int l = 2 * (tid % (LT / 2)), vc = (tid / (LT / 2)) % NC;
+        const bool colok = c0 + vc < n && l < L;
+        for (int t = tid / VU; t < T; t += kThreads / VU) {
+          const bool ok = colok && kap0 + t < K;
+          cp_async16(buf + pl.off_Vs + t * pl.SV + vc * LT + l,
+                     ok ? A.V + (((size_t)k * K + kap0 + t) * n + c0 + vc) * L + l : A.V, ok);
+        }
+      }
+    } else {
+      for (int idx = tid; idx < qc * MG * NC; idx += kThreads) {
+        const int cc = idx % NC, aa = (idx / NC) % MG, ql = idx / (NC * MG);
+        const int c = c0 + cc;
+        const bool ok = aa < m && c < n;
+        cp_async8(buf + pl.off_Gs + (ql * MG + aa) * pl.SG + cc,
+                  ok ? Gch + ((size_t)(q0 + ql) * m + aa) * n + c : A.G, ok);
+      }
+      if (!SERVE && qi == nq - 1) {
+        for (int idx = tid; idx < T * NC * LT; idx += kThreads) {
+          const int l = idx % LT, cc = (idx / LT) % NC, t = idx / (LT * NC);
+          const int kk2 = kap0 + t, c = c0 + cc;
+          const bool ok = kk2 < K && c < n && l < L;
+          cp_async8(buf + pl.off_Vs + t * pl.SV + cc * LT + l,
+                    ok ? A.V + (((size_t)k * K + kk2) * n + c) * L + l : A.V, ok);
+        }
+      }
+    }
+    if (ident) {
+      // dense channel: w_q = conj(c_q(kappa)) for the slab
+      for (int idx = tid; idx < T * qc; idx += kThreads) {
+        const int t = idx / qc, ql = idx - t * qc;
+        buf[pl.off_Wc + t * pl.WS + ql] = kap0 + t < K ? cconj(coef_at(kap0 + t, q0 + ql)) : cz();
+      }
+    }
+  };
+
+  issue_stage(0);
+  cp_async_commit();
+  if (nstage > 1) issue_stage(1);
+  cp_async_commit();
+
+  if (!ident) {
+    // projection w[t][q] = sum_P C[P][q] conj(c_P(kappa_t)) (eq. 15) in chunks
+    // of 32 columns; QS consecutive lanes per subcarrier share the path
+    // coefficients by shuffles
+    const int t = tid / QS, qs = tid % QS;
+    const int kap_t = kap0 + t;
+    const float2* Cch = A.C + (size_t)ch * P * p;
+    for (int qb = 0; qb < p; qb += 32) {
+      float2 acc[QA];
+#pragma unroll
+      for (int u = 0; u < QA; ++u) acc[u] = cz();
+      for (int p0 = 0; p0 < P; p0 += QS) {
+        float2 mine = cz();
+        const int pm = p0 + qs;
+        if (kap_t < K && pm < P) mine = coef_at(kap_t, pm);
+#pragma unroll
+        for (int r = 0; r < QS; ++r) {
+          const int pp = p0 + r;
+          float2 c = mine;
+          if (QS > 1) c = gshfl<QS>(mine, r);
+          if (pp >= P) break;                        // uniform over the warp
+          const float2* crow = Cch + (size_t)pp * p + qb;
+#pragma unroll
+          for (int u = 0; u < QA; ++u)
+            if (qb + qs + u * QS < p) cmacc(acc[u], __ldg(crow + qs + u * QS), c);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < QA; ++u)
+        if (qb + qs + u * QS < p) ws[t * (p + 1) + qb + qs + u * QS] = acc[u];
+    }
+  }
+  cp_async_wait<1>();
+  __syncthreads();
+
+  float2 E[2][2][LT];   // [subcarrier of the pair][row j, j + GL][stream]
+#pragma unroll
+  for (int x = 0; x < 2; ++x)
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int l = 0; l < LT; ++l) E[x][r][l] = cz();
+  float2 h[2][2][NC];
+  for (int st = 0; st < nstage; ++st) {
+    if (st > 0) {
+      if (st + 1 < nstage) issue_stage(st + 1);
+      cp_async_commit();
+      cp_async_wait<1>();
+      __syncthreads();
+    }
+    const float2* buf = stage0 + (st & 1) * pl.stage;
+    const int cidx = st / nq, qi = st - cidx * nq;
+    const int q0 = qi * QC, qc = min(QC, p - q0);
+    if (qi == 0) {
+#pragma unroll
+      for (int x = 0; x < 2; ++x)
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+          for (int cc = 0; cc < NC; ++cc) h[x][r][cc] = cz();
+    }
+    const float2* w0 = ident ? buf + pl.off_Wc + (2 * gp) * pl.WS : ws + (2 * gp) * (p + 1) + q0;
+    const float2* w1 = w0 + (ident ? pl.WS : p + 1);
+    const float2* g0 = buf + pl.off_Gs + j * pl.SG;
+    const float2* g1 = g0 + GL * pl.SG;
+#pragma unroll 4
+    for (int q = 0; q < qc; ++q) {
+      const float2 wa = w0[q], wb = w1[q];
+      const float4* ga = reinterpret_cast<const float4*>(g0 + q * MG * pl.SG);
+      const float4* gb = reinterpret_cast<const float4*>(g1 + q * MG * pl.SG);
+#pragma unroll
+      for (int c2 = 0; c2 < NC / 2; ++c2) {
+        const float4 u = ga[c2], v = gb[c2];
+        const float2 u0 = make_float2(u.x, u.y), u1 = make_float2(u.z, u.w);
+        const float2 v0 = make_float2(v.x, v.y), v1 = make_float2(v.z, v.w);
+        cmac(h[0][0][2 * c2], wa, u0);
+        cmac(h[0][0][2 * c2 + 1], wa, u1);
+        cmac(h[1][0][2 * c2], wb, u0);
+        cmac(h[1][0][2 * c2 + 1], wb, u1);
+        cmac(h[0][1][2 * c2], wa, v0);
+        cmac(h[0][1][2 * c2 + 1], wa, v1);
+        cmac(h[1][1][2 * c2], wb, v0);
+        cmac(h[1][1][2 * c2 + 1], wb, v1);
+      }
+    }
+    if (qi == nq - 1) {
+      const int c0 = cidx * NC;
+      if (SERVE) {
+#pragma unroll
+        for (int x = 0; x < 2; ++x) {
+          const int kap = kap0 + 2 * gp + x;
+#pragma unroll
+          for (int r = 0; r < 2; ++r) {
+            const int a = j + r * GL;
+            if (kap >= K || a >= m) continue;
+            float2* Hrow = A.Hserv + (((size_t)i * K + kap) * m + a) * n;
+#pragma unroll
+            for (int cc = 0; cc < NC; ++cc)
+              if (c0 + cc < n) Hrow[c0 + cc] = h[x][r][cc];
+          }
+        }
+      } else {
+        const float2* va = buf + pl.off_Vs + (2 * gp) * pl.SV;
+        const float2* vb = va + pl.SV;
+#pragma unroll
+        for (int cc = 0; cc < NC; ++cc) {
+#pragma unroll
+          for (int l2 = 0; l2 < LT / 2; ++l2) {
+            const float4 x = reinterpret_cast<const float4*>(va + cc * LT)[l2];
+            const float4 y = reinterpret_cast<const float4*>(vb + cc * LT)[l2];
+            const float2 x0 = make_float2(x.x, x.y), x1 = make_float2(x.z, x.w);
+            const float2 y0 = make_float2(y.x, y.y), y1 = make_float2(y.z, y.w);
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+              cmac(E[0][r][2 * l2], h[0][r][cc], x0);
+              cmac(E[0][r][2 * l2 + 1], h[0][r][cc], x1);
+              cmac(E[1][r][2 * l2], h[1][r][cc], y0);
+              cmac(E[1][r][2 * l2 + 1], h[1][r][cc], y1);
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();   // this buffer is refilled two stages later
+  }
+  cp_async_wait<0>();
+  if (SERVE) return;
+
+  // partial covariance rows (E E*)[a][b], b < m (eq. 25), for both subcarriers
+  float2* Es = stage0 + gp * (2 * MG * LT + 2);
+#pragma unroll
+  for (int x = 0; x < 2; ++x)
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int l = 0; l < LT; ++l) Es[(x * MG + j + r * GL) * LT + l] = E[x][r][l];
+  __syncwarp();
+#pragma unroll
+  for (int x = 0; x < 2; ++x) {
+    const int kap = kap0 + 2 * gp + x;
+    if (kap >= K) continue;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int a = j + r * GL;
+      if (a >= m) continue;
+      float2* Rout = A.Rpart + ((((size_t)i * (J - 1) + z) * K + kap) * m + a) * m;
+      for (int b = 0; b < m; ++b) {
+        float2 acc = cz();
+        const float2* eb = Es + (x * MG + b) * LT;
+#pragma unroll
+        for (int l = 0; l < LT; ++l) cmacc(acc, E[x][r][l], eb[l]);
+        Rout[b] = acc;
+      }
+    }
+  }
+}
+
 // k_sinr_finalize: one group of MG lanes per (UE i, subcarrier): sums the
 // partial covariances, adds the noise (eq. 25) and evaluates the SINR.
 template <int MG, int LT, bool SVD>
@@ -1253,10 +1541,27 @@ cudaError_t launch_link_blocked(const SinrArgs& A, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// svd: interfering links (the blocked kernel for m > 2); wideband precoder:
-// every link
+template <int MG, int LT, bool SERVE>
+cudaError_t launch_link_wide(const SinrArgs& A, cudaStream_t s) {
+  if (!SERVE && A.J < 2) return cudaSuccess;
+  WidePlan pl = wide_plan(MG, LT, A.p, A.identity_C, SERVE);
+  const size_t smem = (size_t)pl.total * sizeof(float2);
+  if (smem > kSmemBudget) return cudaErrorInvalidValue;
+  pl.wide = (A.n % 2 == 0) && (A.L % 2 == 0) && (((uintptr_t)A.G & 15u) == 0) &&
+            (((uintptr_t)A.V & 15u) == 0 || SERVE);
+  dim3 grid((A.K + pl.T - 1) / pl.T, A.J, SERVE ? 1 : A.J - 1);
+  auto kern = k_sinr_link_wide<MG, LT, SERVE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, kThreads, smem, s>>>(A, pl);
+  return cudaGetLastError();
+}
+
+// svd: interfering links (the blocked kernel for m > 2, the wide-core kernel
+// for cores the narrow kernels cannot stage); wideband precoder: every link
 template <int MG, int LT>
 cudaError_t run_links(const SinrArgs& A, bool svd, cudaStream_t s) {
+  if (svd && wide_core(A.P, A.p)) return launch_link_wide<(MG <= 8 ? 8 : 16), LT, false>(A, s);
   if (svd) {
     if (MG >= 4 && A.p <= 32 && A.link_variant != 2)
       return launch_link_blocked<(MG >= 4 ? MG : 4), LT>(A, s);
@@ -1269,6 +1574,7 @@ cudaError_t run_links(const SinrArgs& A, bool svd, cudaStream_t s) {
 // workspace, for the precoder to read
 template <int MG, int LT>
 cudaError_t run_serving(const SinrArgs& A, cudaStream_t s) {
+  if (wide_core(A.P, A.p)) return launch_link_wide<(MG <= 8 ? 8 : 16), LT, true>(A, s);
   return launch_link_mode<MG, LT, kModeServe>(A, 1, s);
 }
 

@@ -82,6 +82,21 @@ def test_workspace_sizes(lib):
     assert bf16 >= svd + nch * (2 * m * n) * (6 * p) * 2
 
 
+def test_wide_cores_only_on_the_svd_path(lib):
+    # p > 32 or P p > 8192: the SVD path streams the core (wide-core kernel);
+    # the wideband-precoder path, the adjoints and the tensor-core modes stage
+    # C_ik whole and refuse such sizes
+    for kw in (dict(p=33, P=40), dict(p=20, P=512), dict(p=256, P=401, n=8)):
+        d = _dims(**kw)
+        assert lib.ts_workspace_bytes(ctypes.byref(d), 0) > 0, kw
+        for op in (1, 4, 5, 7, 8):
+            assert lib.ts_workspace_bytes(ctypes.byref(d), op) == 0, (kw, op)
+    # the dense comparator keeps no projections: P up to 1024
+    d = _dims(P=1024, p=4)
+    assert lib.ts_workspace_bytes(ctypes.byref(d), 2) > 0
+    assert lib.ts_workspace_bytes(ctypes.byref(d), 3) == 0
+
+
 def test_tensor_core_modes_reject_unsupported_shapes(lib):
     from paper_2401_09792_gb300 import tuckersinr as ts
     d = _dims(M=16, m=16, L=16, N=32, n=16)
@@ -97,7 +112,8 @@ def test_tensor_core_modes_reject_unsupported_shapes(lib):
 
 
 @pytest.mark.parametrize("bad", [dict(m=5), dict(L=5), dict(L=0), dict(m=17, M=17),
-                                 dict(n=33), dict(p=9), dict(p=33, P=40), dict(K=0), dict(J=0)])
+                                 dict(n=33), dict(p=9), dict(p=257, P=300), dict(P=1025),
+                                 dict(K=0), dict(J=0)])
 def test_invalid_dims_rejected_before_launch(lib, bad):
     d = _dims(**bad)
     assert lib.ts_workspace_bytes(ctypes.byref(d), 0) == 0
