@@ -178,6 +178,41 @@ def dense_sinr(X, coef, sigma2, L, precoder="svd", Pfull=None, form="stable"):
     return sinr_from_channels(dense_channels(X, coef), sigma2, L, precoder, Pfull, form)
 
 
+# ---------------------------------------------- several UEs per cell (Section 4)
+def sinr_from_channels_multiuser(Hs, sigma2, L, form="stable"):
+    """SVD-precoded SINR with U UEs per cell, as in the paper's experiments
+    (Section 4: only the first UE of every other cell causes inter-cell
+    interference; no intra-cell interference).
+
+    Hs (U, J, J, K, rows, cols): Hs[u, i, k] is the channel from BS k to UE u
+    of cell i; sigma2 (U, J).  UE (i, u) is served by BS i with the top-L
+    right singular vectors of its own link Hs[u, i, i] (eq. 7); every other
+    BS k transmits to its first UE, with the precoder of Hs[0, k, k].
+    Returns (U, J, K, L)."""
+    U, J = Hs.shape[:2]
+    V0 = np.stack([svd_precoder(Hs[0, k, k], L) for k in range(J)])
+    out = []
+    for u in range(U):
+        Vu = V0 if u == 0 else np.stack([svd_precoder(Hs[u, k, k], L) for k in range(J)])
+        E = np.stack([np.stack([Hs[u, i, k] @ (Vu[k] if k == i else V0[k]) for k in range(J)])
+                      for i in range(J)])
+        out.append((sinr_stable if form == "stable" else sinr_literal)(E, sigma2[u]))
+    return np.stack(out)
+
+
+def tucker_sinr_multiuser(G, C, coef, sigma2, L, form="stable"):
+    """Compressed form of sinr_from_channels_multiuser: G (U, J, J, m, n, p),
+    C (U, J, J, P, p), coef (U, J, J, K, P), sigma2 (U, J)."""
+    Hs = np.stack([compressed_channels(G[u], C[u], coef[u]) for u in range(G.shape[0])])
+    return sinr_from_channels_multiuser(Hs, sigma2, L, form)
+
+
+def dense_sinr_multiuser(X, coef, sigma2, L, form="stable"):
+    """Dense form: X (U, J, J, M, N, P)."""
+    Hs = np.stack([dense_channels(X[u], coef[u]) for u in range(X.shape[0])])
+    return sinr_from_channels_multiuser(Hs, sigma2, L, form)
+
+
 # -------------------------------------------------------------------- eq. 30
 def mean_relative_error(sinr_ref: np.ndarray, sinr_cmp: np.ndarray) -> float:
     """e_c of eq. (30): mean over streams, UEs (and subcarriers) of |S - S~| / S."""

@@ -51,6 +51,7 @@ class Workload:
     sigma2_range: tuple = (1e-3, 1.0)
     delta_f_hz: float = 15e3
     seed: int = 0
+    U: int = 1        # UEs per cell (UE groups; group 0 = the first UE of every cell)
     extra: dict = field(default_factory=dict)
 
 
@@ -87,15 +88,22 @@ def _ula(n: int, theta: float) -> np.ndarray:
     return np.exp(1j * np.pi * np.arange(n) * np.sin(theta))
 
 
-def channel_submatrices(w: Workload) -> np.ndarray:
-    """X[i, k] in C^{M x N x P}: the submatrices of eq. (2) stacked on mode 3.
+def ue_key(ue: int) -> tuple:
+    """Extra seed-path entries of UE group `ue` (UE ue of every cell); the
+    first UEs (ue = 0) draw exactly the single-UE system."""
+    return () if ue == 0 else (1000 + int(ue),)
+
+
+def channel_submatrices(w: Workload, ue: int = 0) -> np.ndarray:
+    """X[i, k] in C^{M x N x P}: the submatrices of eq. (2) stacked on mode 3,
+    for UE `ue` of every cell.
 
     Returns shape (J, J, M, N, P), complex128.
     """
     X = np.empty((w.J, w.J, w.M, w.N, w.P), dtype=np.complex128)
     for i in range(w.J):
         for k in range(w.J):
-            rng = _rng(w.seed, 1, i, k)
+            rng = _rng(w.seed, 1, i, k, *ue_key(ue))
             for q in range(w.P):
                 if q < w.n_los:
                     th, ph = rng.uniform(-np.pi / 2, np.pi / 2, 2)
@@ -105,13 +113,13 @@ def channel_submatrices(w: Workload) -> np.ndarray:
     return X
 
 
-def path_gains_delays(w: Workload) -> tuple[np.ndarray, np.ndarray]:
+def path_gains_delays(w: Workload, ue: int = 0) -> tuple[np.ndarray, np.ndarray]:
     """alpha[i, k, P] complex128 and tau[i, k, P] seconds (float32 values)."""
     alpha = np.empty((w.J, w.J, w.P), dtype=np.complex128)
     tau = np.empty((w.J, w.J, w.P), dtype=np.float64)
     for i in range(w.J):
         for k in range(w.J):
-            rng = _rng(w.seed, 2, i, k)
+            rng = _rng(w.seed, 2, i, k, *ue_key(ue))
             t = rng.uniform(0.0, w.tau_max_s, w.P).astype(np.float32).astype(np.float64)
             var = np.ones(w.P) if w.pdp_decay_s is None else np.exp(-t / w.pdp_decay_s)
             a = _cn(rng, w.P) * np.sqrt(var)
@@ -120,11 +128,11 @@ def path_gains_delays(w: Workload) -> tuple[np.ndarray, np.ndarray]:
     return alpha, tau
 
 
-def noise_powers(w: Workload) -> np.ndarray:
+def noise_powers(w: Workload, ue: int = 0) -> np.ndarray:
     """sigma2[i] per UE (float32 values)."""
     if w.sigma2 is not None:
         return np.full(w.J, np.float32(w.sigma2), dtype=np.float64)
-    rng = _rng(w.seed, 3)
+    rng = _rng(w.seed, 3, *ue_key(ue))
     lo, hi = np.log(w.sigma2_range[0]), np.log(w.sigma2_range[1])
     return np.exp(rng.uniform(lo, hi, w.J)).astype(np.float32).astype(np.float64)
 
@@ -142,14 +150,16 @@ def wideband_precoders(w: Workload) -> np.ndarray:
     return np.stack([orthonormal(_rng(w.seed, 4, k), w.N, w.L) for k in range(w.J)])
 
 
-def direct_tucker(w: Workload, decay=(0.85, 0.97, 0.9)) -> dict:
+def direct_tucker(w: Workload, decay=(0.85, 0.97, 0.9), ue: int = 0) -> dict:
     """A Tucker form drawn directly, without fitting any channel.
 
     A[i] (M x m), B[k] (N x n), C[i, k] (P x p) have orthonormal columns;
     G[i, k] (m x n x p) is CN(0, 1) scaled by decay[0]**a * decay[1]**b *
     decay[2]**q along its three modes.  All values are complex64-representable.
+    For UE group `ue` the receive factors A, the C and the cores are its own;
+    the transmit factors B (one per BS) are the same for every group.
     """
-    A = np.stack([orthonormal(_rng(w.seed, 5, i), w.M, w.m) for i in range(w.J)])
+    A = np.stack([orthonormal(_rng(w.seed, 5, i, *ue_key(ue)), w.M, w.m) for i in range(w.J)])
     B = np.stack([orthonormal(_rng(w.seed, 6, k), w.N, w.n) for k in range(w.J)])
     C = np.empty((w.J, w.J, w.P, w.p), dtype=np.complex128)
     G = np.empty((w.J, w.J, w.m, w.n, w.p), dtype=np.complex128)
@@ -159,7 +169,7 @@ def direct_tucker(w: Workload, decay=(0.85, 0.97, 0.9)) -> dict:
     scale = sa[:, None, None] * sb[None, :, None] * sq[None, None, :]
     for i in range(w.J):
         for k in range(w.J):
-            C[i, k] = orthonormal(_rng(w.seed, 7, i, k), w.P, w.p)
-            G[i, k] = _cn(_rng(w.seed, 8, i, k), (w.m, w.n, w.p)) * scale
+            C[i, k] = orthonormal(_rng(w.seed, 7, i, k, *ue_key(ue)), w.P, w.p)
+            G[i, k] = _cn(_rng(w.seed, 8, i, k, *ue_key(ue)), (w.m, w.n, w.p)) * scale
     c64 = lambda x: x.astype(np.complex64).astype(np.complex128)  # noqa: E731
     return {"A": c64(A), "B": c64(B), "C": c64(C), "G": c64(G)}

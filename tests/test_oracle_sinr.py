@@ -212,3 +212,68 @@ def test_small_workload_end_to_end_fit_then_sinr():
     assert comp.shape == dense.shape == (w.J, w.K, w.L)
     assert np.all(comp > 0) and np.all(dense > 0)
     assert np.isfinite(S.mean_relative_error(dense, comp))
+
+
+# --------------------------------------------- several UEs per cell (Section 4)
+def _multiuser_system(seed, U=3, J=3, M=4, N=10, P=6, m=3, n=5, p=4, K=4, L=2):
+    rng = np.random.default_rng(seed)
+    A = np.stack([[_orth(rng, M, m) for _ in range(J)] for _ in range(U)])      # per UE
+    B = np.stack([_orth(rng, N, n) for _ in range(J)])                          # per BS
+    C = np.stack([[[_orth(rng, P, p) for _ in range(J)] for _ in range(J)] for _ in range(U)])
+    G = _rand(rng, (U, J, J, m, n, p))
+    coef = _rand(rng, (U, J, J, K, P))
+    s2 = rng.uniform(0.05, 1.0, (U, J))
+    return A, B, C, G, coef, s2
+
+
+def test_multiuser_first_group_is_the_single_ue_system():
+    A, B, C, G, coef, s2 = _multiuser_system(11)
+    got = S.tucker_sinr_multiuser(G, C, coef, s2, 2)
+    np.testing.assert_allclose(got[0], S.tucker_sinr(G[0], C[0], coef[0], s2[0], 2, "svd"), rtol=1e-12)
+
+
+def test_multiuser_interference_comes_from_the_first_ues_precoders():
+    # UE (i, 1) with UE (i, 0)'s links and noise has UE (i, 0)'s SINR; the
+    # serving link of UE (k, 1) changes no other UE's SINR (BS k interferes
+    # with its first UE's precoder), while that of UE (k, 0) does
+    A, B, C, G, coef, s2 = _multiuser_system(12)
+    G[1], C[1], coef[1], s2[1] = G[0], C[0], coef[0], s2[0]
+    base = S.tucker_sinr_multiuser(G, C, coef, s2, 2)
+    np.testing.assert_allclose(base[1], base[0], rtol=1e-12)
+    rng = np.random.default_rng(3)
+    G1 = G.copy()
+    G1[1, 2, 2] = _rand(rng, G1[1, 2, 2].shape)
+    moved = S.tucker_sinr_multiuser(G1, C, coef, s2, 2)
+    np.testing.assert_allclose(moved[0], base[0], rtol=1e-12)
+    np.testing.assert_allclose(moved[1, :2], base[1, :2], rtol=1e-12)
+    assert np.max(np.abs(moved[1, 2] - base[1, 2]) / base[1, 2]) > 1e-3
+    G0 = G.copy()
+    G0[0, 2, 2] = _rand(rng, G0[0, 2, 2].shape)
+    moved0 = S.tucker_sinr_multiuser(G0, C, coef, s2, 2)
+    assert np.max(np.abs(moved0[2, :2] - base[2, :2]) / base[2, :2]) > 1e-3
+
+
+def test_multiuser_literal_equals_stable_and_brute_force():
+    A, B, C, G, coef, s2 = _multiuser_system(13, U=2, J=2, m=2, n=2, p=2, L=1)
+    lit = S.tucker_sinr_multiuser(G, C, coef, s2, 1, "literal")
+    stb = S.tucker_sinr_multiuser(G, C, coef, s2, 1, "stable")
+    np.testing.assert_allclose(stb, lit, rtol=1e-10)
+    # UE (0, 1), subcarrier 0, by hand: 2 x 2 channels, rank-one precoders
+    H = lambda u, i, k: S.compressed_channel(G[u, i, k], C[u, i, k], coef[u, i, k])[0]  # noqa: E731
+    top = lambda M_: np.linalg.svd(M_)[2][0].conj()                                    # noqa: E731
+    h_s = H(1, 0, 0) @ top(H(1, 0, 0))
+    h_i = H(1, 0, 1) @ top(H(0, 1, 1))
+    Q = np.outer(h_s, h_s.conj()) + np.outer(h_i, h_i.conj()) + s2[1, 0] * np.eye(2)
+    w = np.linalg.inv(Q) @ h_s
+    s = abs(w.conj() @ h_s) ** 2
+    assert abs(stb[1, 0, 0, 0] - s / (np.real(w.conj() @ Q @ w) - s)) < 1e-10 * stb[1, 0, 0, 0]
+
+
+def test_multiuser_factor_cancellation():
+    # A per UE, B per BS: the dense path on X^ equals the compressed path
+    A, B, C, G, coef, s2 = _multiuser_system(14)
+    U, J = G.shape[:2]
+    Xh = np.stack([np.stack([np.stack([T.tucker_reconstruct(G[u, i, k], A[u, i], B[k], C[u, i, k])
+                                       for k in range(J)]) for i in range(J)]) for u in range(U)])
+    np.testing.assert_allclose(S.tucker_sinr_multiuser(G, C, coef, s2, 2),
+                               S.dense_sinr_multiuser(Xh, coef, s2, 2), rtol=1e-10)
