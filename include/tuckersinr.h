@@ -109,7 +109,9 @@ enum {
   TS_OP_SINR_SVD_BF16X2 = 8,  /* ts_sinr_svd_prec with TS_PREC_BF16X2 */
   TS_OP_TUCKER_FIT_SHARED = 9,     /* ts_tucker_fit_model, TS_MODEL_SHARED     */
   TS_OP_TUCKER_FIT_INDIVIDUAL = 10, /* ts_tucker_fit_model, TS_MODEL_INDIVIDUAL */
-  TS_OP_RECONSTRUCT = 11           /* ts_tucker_reconstruct                    */
+  TS_OP_RECONSTRUCT = 11,          /* ts_tucker_reconstruct                    */
+  TS_OP_SINR_SVD_MULTIUSER = 12,   /* ts_sinr_svd_multiuser (any U)            */
+  TS_OP_DENSE_SVD_MULTIUSER = 13   /* ts_dense_sinr_svd_multiuser (any U)      */
 };
 
 /* The three compression models of Section 3.1: which links share the
@@ -302,6 +304,29 @@ void ts_batch_plan_destroy(ts_batch_plan* plan);
  * text file, one class per line; load merges into the table. */
 int ts_autotune_save(const char* path);
 int ts_autotune_load(const char* path);
+
+/* SVD-precoded SINR with U UEs per cell, as in the paper's experiments
+ * (Section 4): UE u of cell i is served by BS i with the top-L right singular
+ * vectors of its own link; only the first UE of every other cell causes
+ * inter-cell interference (BS k transmits with its first UE's precoder) and
+ * there is no intra-cell interference.  Every array holds U UE groups of the
+ * single-UE layout, group u = UE u of every cell: G [U][J*J][p][m][n],
+ * C [U][J*J][P][p], coef [U][J*J][K][P] (dense) or alpha, tau [U][J*J][P]
+ * (paths), sigma2 [U][J], sinr (out) [U][J][K][L], flags (out, may be NULL)
+ * [U][J][K].  U = 1 is ts_sinr_svd.  FP32, sizes as ts_sinr_svd (wide cores
+ * included).  ws: ts_workspace_bytes(d, TS_OP_SINR_SVD_MULTIUSER) bytes, the
+ * same for every U (two single-UE workspaces: the first UEs' precoders stay
+ * in the first while the other groups reuse the second). */
+int ts_sinr_svd_multiuser(const ts_dims* d, int U, const ts_coef* coef, const ts_c64* G,
+                          const ts_c64* C, const float* sigma2, float* sinr, uint8_t* flags,
+                          void* ws, size_t ws_bytes, void* stream);
+
+/* The same on the uncompressed channels X [U][J*J][P][M][N] (the dense
+ * comparator; d's M, N, P are used, P <= 1024).
+ * ws: ts_workspace_bytes(d, TS_OP_DENSE_SVD_MULTIUSER) bytes. */
+int ts_dense_sinr_svd_multiuser(const ts_dims* d, int U, const ts_coef* coef, const ts_c64* X,
+                                const float* sigma2, float* sinr, uint8_t* flags, void* ws,
+                                size_t ws_bytes, void* stream);
 
 /* Dense-channel comparator: the same SINR computed from the uncompressed
  * channel tensors, rebuilding the full M x N channel of every link and

@@ -249,6 +249,11 @@ void ts_set_refinement(float cond_threshold) {
 
 size_t ts_workspace_bytes(const ts_dims* d, int op) {
   if (d == nullptr) return 0;
+  if (op == TS_OP_SINR_SVD_MULTIUSER || op == TS_OP_DENSE_SVD_MULTIUSER) {
+    const ts_dims e = op == TS_OP_DENSE_SVD_MULTIUSER ? dense_dims(d) : *d;
+    if (check_dims(&e, op == TS_OP_DENSE_SVD_MULTIUSER) != TS_OK) return 0;
+    return 2 * carve(&e, TS_OP_SINR_SVD).total;
+  }
   if (op == TS_OP_DENSE_SVD || op == TS_OP_DENSE_MMSE) {
     const ts_dims e = dense_dims(d);
     if ((op == TS_OP_DENSE_SVD ? check_dims(&e, true) : check_narrow(&e)) != TS_OK) return 0;
@@ -564,9 +569,66 @@ int svd_from_precoders_impl(const ts_dims* d, const ts_coef* coef, const ts_c64*
   return cuda_status(links_then_finalize(a, true, s));
 }
 
+// U UEs per cell (Section 4): UE group u holds UE u of every cell, its links
+// at G + u J^2 p m n (likewise C, the coefficients, sigma2, sinr, flags).
+// Every BS k interferes with its first UE's precoder: the u = 0 pass keeps
+// its precoders V_0 in the first half of the workspace; each later group
+// computes its own serving precoders, serving effective channels and flags
+// in the second half and reads V_0 for its interfering links.
+int svd_multiuser_impl(const ts_dims* d, int U, const ts_coef* coef, const ts_c64* G,
+                       const ts_c64* C, bool identity, const float* sigma2, float* sinr,
+                       uint8_t* flags, void* ws, size_t ws_bytes, void* stream) {
+  if (U < 1) return TS_ERR_DIMS;
+  int st = sinr_common_checks(d, coef, G, C, identity, sigma2, sinr, ws, ws_bytes, TS_OP_SINR_SVD);
+  if (st != TS_OK) return st;
+  const Workspace w = carve(d, TS_OP_SINR_SVD);
+  if (ws_bytes < 2 * w.total) return TS_ERR_WORKSPACE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t nch = (size_t)d->J * d->J;
+  char* base0 = static_cast<char*>(ws);
+  for (int u = 0; u < U; ++u) {
+    ts_coef cu = *coef;
+    if (cu.mode == TS_COEF_DENSE) {
+      cu.c = coef->c + (size_t)u * nch * d->K * d->P;
+    } else {
+      cu.alpha = coef->alpha + (size_t)u * nch * d->P;
+      cu.tau_s = coef->tau_s + (size_t)u * nch * d->P;
+    }
+    const ts_c64* Gu = G + (size_t)u * nch * d->p * d->m * d->n;
+    const ts_c64* Cu = identity ? nullptr : C + (size_t)u * nch * d->P * d->p;
+    char* base = base0 + (u == 0 ? 0 : w.total);
+    st = svd_precoders_impl(d, &cu, Gu, Cu, identity, base, w.total, stream);
+    if (st != TS_OK) return st;
+    ts::SinrArgs a = base_args(d, &cu, Gu, Cu, sigma2 + (size_t)u * d->J,
+                               sinr + (size_t)u * d->J * d->K * d->L,
+                               flags == nullptr ? nullptr : flags + (size_t)u * d->J * d->K, base, w);
+    a.identity_C = identity;
+    a.V = reinterpret_cast<float2*>(base0 + w.V);
+    a.pflag = reinterpret_cast<uint8_t*>(base + w.pflag);
+    const int e = cuda_status(links_then_finalize(a, true, s));
+    if (e != TS_OK) return e;
+  }
+  return TS_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+int ts_sinr_svd_multiuser(const ts_dims* d, int U, const ts_coef* coef, const ts_c64* G,
+                          const ts_c64* C, const float* sigma2, float* sinr, uint8_t* flags,
+                          void* ws, size_t ws_bytes, void* stream) {
+  return svd_multiuser_impl(d, U, coef, G, C, false, sigma2, sinr, flags, ws, ws_bytes, stream);
+}
+
+int ts_dense_sinr_svd_multiuser(const ts_dims* d, int U, const ts_coef* coef, const ts_c64* X,
+                                const float* sigma2, float* sinr, uint8_t* flags, void* ws,
+                                size_t ws_bytes, void* stream) {
+  if (d == nullptr) return TS_ERR_NULL;
+  const ts_dims e = dense_dims(d);
+  return svd_multiuser_impl(&e, U, coef, X, nullptr, true, sigma2, sinr, flags, ws, ws_bytes,
+                            stream);
+}
 
 int ts_sinr_mmse(const ts_dims* d, const ts_coef* coef, const ts_c64* G, const ts_c64* C,
                  const ts_c64* Pt, const float* sigma2, float* sinr, uint8_t* flags, void* ws,

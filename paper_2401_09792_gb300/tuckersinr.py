@@ -24,6 +24,7 @@ TS_OP_SINR_SVD_ADJOINT, TS_OP_SINR_MMSE_ADJOINT, TS_OP_TUCKER_FIT = 4, 5, 6
 TS_OP_SINR_SVD_TF32, TS_OP_SINR_SVD_BF16X2 = 7, 8
 TS_OP_TUCKER_FIT_SHARED, TS_OP_TUCKER_FIT_INDIVIDUAL, TS_OP_RECONSTRUCT = 9, 10, 11
 TS_MODEL_GROUPWISE, TS_MODEL_SHARED, TS_MODEL_INDIVIDUAL = 0, 1, 2
+TS_OP_SINR_SVD_MULTIUSER, TS_OP_DENSE_SVD_MULTIUSER = 12, 13
 TS_PREC_FP32, TS_PREC_TF32, TS_PREC_BF16X2 = 0, 1, 2
 TS_FLAG_NOT_PD, TS_FLAG_NONFINITE, TS_FLAG_RANK_DEFICIENT, TS_FLAG_EIG_UNCONVERGED = 1, 2, 4, 8
 TS_FLAG_TIMEOUT = 16
@@ -86,6 +87,12 @@ _SIG = {
                                           _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "ts_tucker_fit": (ctypes.c_int, [ctypes.POINTER(ts_dims), _P, ctypes.c_int, ctypes.c_int, _P, _P,
                                      _P, _P, _P, _P, ctypes.c_size_t, _P]),
+    "ts_sinr_svd_multiuser": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.c_int,
+                                             ctypes.POINTER(ts_coef), _P, _P, _P, _P, _P, _P,
+                                             ctypes.c_size_t, _P]),
+    "ts_dense_sinr_svd_multiuser": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.c_int,
+                                                   ctypes.POINTER(ts_coef), _P, _P, _P, _P, _P,
+                                                   ctypes.c_size_t, _P]),
     "ts_tucker_fit_model": (ctypes.c_int, [ctypes.POINTER(ts_dims), _P, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_int, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "ts_tucker_reconstruct": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.c_int, _P, _P, _P, _P, _P,
@@ -310,6 +317,22 @@ def ts_tucker_fit(d: Dims, X, S, init, A, B, C, G, g_hist, ws, stream=None):
     _check("ts_tucker_fit", lib.ts_tucker_fit(ctypes.byref(d.c()), _ptr(X), S, init, _ptr(A), _ptr(B),
                                               _ptr(C), _ptr(G), _ptr(g_hist), _ptr(ws), ws.numel(),
                                               _stream(stream)))
+
+
+def ts_sinr_svd_multiuser(d: Dims, U, coef: ts_coef, G, C, sigma2, sinr, flags, ws, stream=None):
+    lib = load()
+    _check("ts_sinr_svd_multiuser",
+           lib.ts_sinr_svd_multiuser(ctypes.byref(d.c()), U, ctypes.byref(coef), _ptr(G), _ptr(C),
+                                     _ptr(sigma2), _ptr(sinr), _ptr(flags), _ptr(ws), ws.numel(),
+                                     _stream(stream)))
+
+
+def ts_dense_sinr_svd_multiuser(d: Dims, U, coef: ts_coef, X, sigma2, sinr, flags, ws, stream=None):
+    lib = load()
+    _check("ts_dense_sinr_svd_multiuser",
+           lib.ts_dense_sinr_svd_multiuser(ctypes.byref(d.c()), U, ctypes.byref(coef), _ptr(X),
+                                           _ptr(sigma2), _ptr(sinr), _ptr(flags), _ptr(ws),
+                                           ws.numel(), _stream(stream)))
 
 
 def ts_tucker_fit_model(d: Dims, X, S, init, model, A, B, C, G, g_hist, ws, stream=None):

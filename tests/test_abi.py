@@ -64,7 +64,10 @@ def test_workspace_sizes(lib):
     assert svd >= nch * P * 8 + 2 * K * n * L * 8 + 2 * K
     assert mmse >= nch * P * 8 + nch * p * m * L * 8
     assert svd % 256 == 0 and mmse % 256 == 0
-    assert lib.ts_workspace_bytes(ctypes.byref(d), 12) == 0
+    assert lib.ts_workspace_bytes(ctypes.byref(d), 99) == 0
+    # several UEs per cell: two single-UE workspaces, whatever U
+    assert lib.ts_workspace_bytes(ctypes.byref(d), 12) == 2 * svd
+    assert lib.ts_workspace_bytes(ctypes.byref(d), 13) == 2 * lib.ts_workspace_bytes(ctypes.byref(d), 2)
     # the fit per model: the summed-Gram buffers grow with the number of factors
     # (shared 1, groupwise J, individual J^2); the reconstruction holds the two
     # intermediate products G x_1 A and (G x_1 A) x_2 B
