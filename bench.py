@@ -47,13 +47,15 @@ def select_workload(name: str):
 
 
 def workload_config(w, precoder="svd"):
+    cells = (f"J={w.J} cells" if w.U == 1 else
+             f"J={w.J} cells x U={w.U} UEs, first-UE inter-cell interference")
     return {
-        "workload": (f"{WORKLOAD_NAME}: J={w.J} cells, M={w.M}, N={w.N}, P={w.P}, K={w.K} subcarriers, "
+        "workload": (f"{WORKLOAD_NAME}: {cells}, M={w.M}, N={w.N}, P={w.P}, K={w.K} subcarriers, "
                      f"ranks (m,n,p)=({w.m},{w.n},{w.p}), L={w.L} streams; {precoder}-precoded "
                      f"MMSE SINR; path-form coefficients; Tucker form drawn directly"),
         "precoder": precoder,
         "l2": "flushed before every timed step (256 MiB write)",
-        "units_per_step": w.J * w.K,
+        "units_per_step": w.U * w.J * w.K,
     }
 
 
@@ -791,6 +793,184 @@ def run_batch(args):
     plan.close()
 
 
+def run_multiuser(args):
+    """The paper's own system sizes (Section 4): J = 21 cells, U UEs per
+    cell with first-UE inter-cell interference, (M, N, P) = (8, 256, 401)
+    and the paper's compressed sizes; Tucker form drawn directly (fitting
+    ~15 GB of channels per UE group is an offline step the paper does once).
+    Reports the compressed-path throughput, the wide-core link kernel
+    against the FP32 roofline, the dense-channel comparator on the
+    reconstructed channels X^ (the same SINR up to rounding: A and B cancel)
+    as the speedup R_t = t_dense / t_compressed, and R_s of eq. (29)."""
+    import torch
+
+    from oracle import tucker as T
+    from paper_2401_09792_gb300 import tuckersinr as ts
+    import __graft_entry__
+    __graft_entry__.build()
+    ts.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    w = WORKLOAD
+    U, J, K, L, P, M, N, m, n, p = w.U, w.J, w.K, w.L, w.P, w.M, w.N, w.m, w.n, w.p
+    nl = J * J
+    d = ts.Dims.of(w)
+    t_setup = time.perf_counter()
+    c64 = dict(dtype=torch.complex64, device=dev)
+    Gd = torch.empty(U * nl, p, m, n, **c64)
+    Cd = torch.empty(U * nl, P, p, **c64)
+    Ad = torch.empty(U, J, M, m, **c64)
+    ad = torch.empty(U * nl, P, **c64)
+    td = torch.empty(U * nl, P, dtype=torch.float32, device=dev)
+    sd = torch.empty(U * J, dtype=torch.float32, device=dev)
+    host = {}                                 # UE groups 0 and 1 for the oracle sample
+    for u in range(U):
+        tk = synth.direct_tucker(w, ue=u)
+        alpha, tau = synth.path_gains_delays(w, ue=u)
+        s2 = synth.noise_powers(w, ue=u)
+        Gd[u * nl:(u + 1) * nl] = ts.core_to_device(tk["G"], dev)
+        Cd[u * nl:(u + 1) * nl] = ts.factor_to_device(tk["C"].reshape(nl, P, p), dev)
+        Ad[u] = ts.factor_to_device(tk["A"], dev)
+        ad[u * nl:(u + 1) * nl] = ts.factor_to_device(alpha.reshape(nl, P), dev)
+        td[u * nl:(u + 1) * nl] = ts.real_to_device(tau.reshape(nl, P), dev)
+        sd[u * J:(u + 1) * J] = ts.real_to_device(s2, dev)
+        if u == 0:
+            Bd = ts.factor_to_device(tk["B"], dev)
+        if u < 2:
+            host[u] = (tk["G"], tk["C"], alpha, tau, s2)
+        del tk
+    cs, keep = ts.make_coef(alpha=ad, tau=td)
+    sinr = torch.empty(U, J, K, L, device=dev)
+    flags = torch.empty(U, J, K, dtype=torch.uint8, device=dev)
+    ws = ts.workspace(d, ts.TS_OP_SINR_SVD_MULTIUSER, dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    setup_s = time.perf_counter() - t_setup
+
+    def step():
+        ts.ts_sinr_svd_multiuser(d, U, cs, Gd, Cd, sd, sinr, flags, ws, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    time.sleep(0.5)
+    total, link_ms = 0.0, []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b, k0, k1 = ev(), ev(), ev(), ev()
+        k0.record(stream)
+        k1.record(stream)
+        a.record(stream)
+        ts.ts_set_timing_events(k0, k1)        # the last UE group's link pass
+        step()
+        ts.ts_set_timing_events(None, None)
+        b.record(stream)
+        b.synchronize()
+        total += a.elapsed_time(b)
+        link_ms.append(k0.elapsed_time(k1))
+    clocks = sampler.stop()
+    assert int((flags & ts.TS_FLAG_ERRORS).max().item()) == 0, "numerical flags raised"
+    units = U * J * K
+    value = units * args.steps / (total * 1e-3)
+
+    # dense comparator on X^ (exact Tucker form, so the same SINR up to rounding)
+    Xh = torch.empty(U * nl, P, M, N, **c64)
+    wsr = ts.workspace(d, ts.TS_OP_RECONSTRUCT, dev)
+    for u in range(U):
+        ts.ts_tucker_reconstruct(d, ts.TS_MODEL_GROUPWISE, Ad[u], Bd, Cd[u * nl:(u + 1) * nl],
+                                 Gd[u * nl:(u + 1) * nl], Xh[u * nl:(u + 1) * nl], wsr, stream)
+    del wsr
+    sinr_d = torch.empty_like(sinr)
+    flags_d = torch.empty_like(flags)
+    wsd = ts.workspace(d, ts.TS_OP_DENSE_SVD_MULTIUSER, dev)
+
+    def dense_step():
+        ts.ts_dense_sinr_svd_multiuser(d, U, cs, Xh, sd, sinr_d, flags_d, wsd, stream)
+
+    dense_step()
+    torch.cuda.synchronize()
+    dsteps = max(3, args.steps // 10)
+    dense_ms = 0.0
+    for _ in range(dsteps):
+        flush.zero_()
+        a, b = ev(), ev()
+        a.record(stream)
+        dense_step()
+        b.record(stream)
+        b.synchronize()
+        dense_ms += a.elapsed_time(b)
+    step()
+    torch.cuda.synchronize()
+    st, sdn = sinr.double(), sinr_d.double()
+    agree = float(((st - sdn).abs() / sdn.abs()).max().item())
+    del Xh, wsd
+
+    # the FP64 oracle on UE groups 0 and 1 (their SINRs depend on no other
+    # group) and slices of 2 subcarriers, about 12 s
+    from oracle import sinr as S
+    G2 = np.stack([host[u][0] for u in range(min(U, 2))])
+    C2 = np.stack([host[u][1] for u in range(min(U, 2))])
+    s22 = np.stack([host[u][4] for u in range(min(U, 2))])
+    got = sinr[:min(U, 2)].cpu().numpy().astype(np.float64)
+    coef_all = np.stack([S.coefficients(host[u][2], host[u][3], K, w.delta_f_hz)
+                         for u in range(min(U, 2))])
+    kslice, start, done, errs = 2, 0, 0, []
+    c0, t1 = time.process_time(), time.perf_counter()
+    while time.perf_counter() - t1 < 12.0:
+        ks = [(start + j) % K for j in range(kslice)]
+        coef = coef_all[:, :, :, ks]
+        ref = S.tucker_sinr_multiuser(G2, C2, coef, s22, L)
+        if len(errs) < 4:
+            errs.append((np.abs(got[:, :, ks] - ref) / np.abs(ref)).ravel())
+        done += min(U, 2) * J * kslice
+        start += kslice
+    wall = time.perf_counter() - t1
+    e = np.concatenate(errs)
+    pk = peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    fp32_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12
+    lf = link_flops(w, "svd")
+    lmean = float(np.mean(link_ms))
+    achieved = lf / (lmean * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": (f"{WORKLOAD_NAME}: J={J} cells x U={U} UEs, first-UE inter-cell "
+                                f"interference, M={M}, N={N}, P={P}, K={K} subcarriers, ranks "
+                                f"(m,n,p)=({m},{n},{p}), L={L}; svd-precoded MMSE SINR; path-form "
+                                "coefficients; Tucker form drawn directly"),
+                   "units_per_step": units, "l2": "flushed before every timed step (256 MiB write)",
+                   "setup_seconds": round(setup_s, 1)},
+        "roofline": {"kernel": "k_sinr_link_wide (svd)", "bound": "alu", "achieved": round(achieved, 3),
+                     "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
+                     "frac": round(achieved / fp32_peak, 4),
+                     "traffic": recorded_traffic("k_sinr_link_wide", WORKLOAD_NAME),
+                     "flops_per_launch": lf, "kernel_ms": round(lmean, 4),
+                     "peak_basis": f"FP32 FFMA: {sms} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz",
+                     "launch": "one UE group (J(J-1) interfering links x K subcarriers)"},
+        "gpu_launches": 6 * U * args.steps,
+        "clocks": clocks,
+        "dense_comparator": {"value": units * dsteps / (dense_ms * 1e-3), "unit": METRIC,
+                             "ms_per_step": dense_ms / dsteps,
+                             "what": f"the same SINR from X^ = G x1 A x2 B x3 C (M={M}, N={N}, "
+                                     f"P={P}) on the same GPU kernels",
+                             "max_rel_diff_vs_compressed": agree},
+        "R_t": (dense_ms / dsteps) / (total / args.steps),
+        "R_s": T.storage_ratio(J, U, M, N, P, m, n, p, "groupwise"),
+        "cpu_baseline": {"value": done / wall, "unit": METRIC,
+                         "cores": max(1, round((time.process_time() - c0) / wall)), "kind": "oracle",
+                         "sample": f"FP64 NumPy oracle, UE groups 0-{min(U, 2) - 1} on slices of "
+                                   f"{kslice} subcarriers for 12 s ({done} subcarrier-SINRs)"},
+        "sinr_err": {"max_rel": float(e.max()), "median_rel": float(np.median(e)), "n": int(e.size)},
+    }
+    print(json.dumps(line), flush=True)
+    del keep
+
+
 # ------------------------------------------------------------ reference arm
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -798,15 +978,31 @@ def run_reference(args):
         return
     from oracle import sinr as S
     w = WORKLOAD
-    tk = synth.direct_tucker(w)
-    alpha, tau = synth.path_gains_delays(w)
-    s2 = synth.noise_powers(w)
-    coef = S.coefficients(alpha, tau, w.K, w.delta_f_hz)
-    kslice = 128
+    if w.U > 1:
+        # UE groups 0 and 1 (the SINRs of group u depend on groups 0 and u only)
+        groups = [synth.direct_tucker(w, ue=u) for u in range(2)]
+        pg = [synth.path_gains_delays(w, ue=u) for u in range(2)]
+        Gm = np.stack([t["G"] for t in groups])
+        Cm = np.stack([t["C"] for t in groups])
+        s2m = np.stack([synth.noise_powers(w, ue=u) for u in range(2)])
+        coefm = np.stack([S.coefficients(a, t, w.K, w.delta_f_hz) for a, t in pg])
+        kslice = 2
 
-    def one(start):
-        sl = slice(start % w.K, start % w.K + kslice)
-        S.tucker_sinr(tk["G"], tk["C"], coef[:, :, sl], s2, w.L, "svd")
+        def one(start):
+            sl = slice(start % w.K, start % w.K + kslice)
+            S.tucker_sinr_multiuser(Gm, Cm, coefm[:, :, :, sl], s2m, w.L)
+        units_per = 2 * w.J * kslice
+    else:
+        tk = synth.direct_tucker(w)
+        alpha, tau = synth.path_gains_delays(w)
+        s2 = synth.noise_powers(w)
+        coef = S.coefficients(alpha, tau, w.K, w.delta_f_hz)
+        kslice = 128
+
+        def one(start):
+            sl = slice(start % w.K, start % w.K + kslice)
+            S.tucker_sinr(tk["G"], tk["C"], coef[:, :, sl], s2, w.L, "svd")
+        units_per = w.J * kslice
 
     for s in range(args.warmup):
         one(s * kslice)
@@ -816,7 +1012,7 @@ def run_reference(args):
         one(s * kslice)
     wall = time.perf_counter() - t0
     cpu = time.process_time() - c0
-    units = w.J * kslice * args.steps
+    units = units_per * args.steps
     value = units / wall
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 1,
@@ -826,7 +1022,8 @@ def run_reference(args):
         "cpu_baseline": {"value": value, "unit": METRIC, "cores": max(1, round(cpu / wall)),
                          "kind": "oracle",
                          "sample": f"each step: FP64 NumPy oracle on {kslice} of the {w.K} "
-                                   f"subcarriers ({w.J * kslice} subcarrier-SINRs); "
+                                   f"subcarriers ({units_per} subcarrier-SINRs"
+                                   f"{', UE groups 0 and 1' if w.U > 1 else ''}); "
                                    f"{os.cpu_count()} host cores visible"},
         "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -860,6 +1057,8 @@ def main():
     select_workload(args.workload)
     if args.impl == "reference":
         run_reference(args)
+    elif WORKLOAD.U > 1:
+        run_multiuser(args)
     else:
         run_ours(args)
 

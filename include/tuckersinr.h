@@ -373,7 +373,8 @@ int ts_tucker_fit_model(const ts_dims* d, const ts_c64* X, int S, int init, int 
 /* Reconstruction X^_ik = G_ik x_1 A x_2 B x_3 C_ik (eq. 10, 12, 14) with the
  * model's factors, FP32: Xhat (out) [J*J][P][M][N] -- e.g. to evaluate a
  * model whose factors do not cancel (individual) on the dense-channel path.
- * Factor layouts as ts_tucker_fit_model; G: [J*J][p][m][n].
+ * Factor layouts as ts_tucker_fit_model; G: [J*J][p][m][n].  Any ranks up
+ * to the dimensions (M, N, P <= 4096, J <= 256).
  * ws: ts_workspace_bytes(d, TS_OP_RECONSTRUCT) bytes. */
 int ts_tucker_reconstruct(const ts_dims* d, int model, const ts_c64* A, const ts_c64* B,
                           const ts_c64* C, const ts_c64* G, ts_c64* Xhat, void* ws,

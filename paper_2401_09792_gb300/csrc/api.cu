@@ -172,6 +172,16 @@ int fit_checks(const ts_dims* d) {
   return TS_OK;
 }
 
+// Sizes the reconstruction accepts: any ranks up to the dimensions (a plain
+// mode-product chain; no eigensolver block limit).
+int reconstruct_checks(const ts_dims* d) {
+  if (d == nullptr) return TS_ERR_NULL;
+  if (d->J < 1 || d->M < 1 || d->N < 1 || d->P < 1) return TS_ERR_DIMS;
+  if (d->m < 1 || d->n < 1 || d->p < 1 || d->m > d->M || d->n > d->N || d->p > d->P) return TS_ERR_DIMS;
+  if (d->M > 4096 || d->N > 4096 || d->P > 4096 || d->J > 256) return TS_ERR_DIMS;
+  return TS_OK;
+}
+
 int check_coef(const ts_coef* c) {
   if (c == nullptr) return TS_ERR_NULL;
   if (c->mode == TS_COEF_DENSE) {
@@ -267,7 +277,7 @@ size_t ts_workspace_bytes(const ts_dims* d, int op) {
                                                                                  : TS_MODEL_INDIVIDUAL))
                : 0;
   if (op == TS_OP_RECONSTRUCT)
-    return fit_checks(d) == TS_OK ? ts::reconstruct_workspace_bytes(fit_dims(d)) : 0;
+    return reconstruct_checks(d) == TS_OK ? ts::reconstruct_workspace_bytes(fit_dims(d)) : 0;
   if (op == TS_OP_SINR_SVD_ADJOINT || op == TS_OP_SINR_MMSE_ADJOINT)
     return check_narrow(d) == TS_OK ? carve_adjoint(d, op == TS_OP_SINR_SVD_ADJOINT).total : 0;
   if (op == TS_OP_SINR_MMSE && check_narrow(d) != TS_OK) return 0;
@@ -415,7 +425,7 @@ int ts_tucker_fit_model(const ts_dims* d, const ts_c64* X, int S, int init, int 
 int ts_tucker_reconstruct(const ts_dims* d, int model, const ts_c64* A, const ts_c64* B,
                           const ts_c64* C, const ts_c64* G, ts_c64* Xhat, void* ws, size_t ws_bytes,
                           void* stream) {
-  int st = fit_checks(d);
+  int st = reconstruct_checks(d);
   if (st != TS_OK) return st;
   if (model != TS_MODEL_GROUPWISE && model != TS_MODEL_SHARED && model != TS_MODEL_INDIVIDUAL)
     return TS_ERR_MODE;

@@ -1108,22 +1108,25 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link_blk(const SinrArgs A, co
 // narrow kernels stage (p > 32 or P p > 8192): the paper's compressed sizes
 // (p ~ 100-200 of P ~ 400 paths) and the dense-channel comparator at large P.
 // Same thread layout as k_sinr_link_blk (two subcarriers and two rows per
-// lane).  The projection w = c* C reads C_ik from L2 in chunks of 32 columns
-// and keeps w [T][p] in shared memory; the core then streams through shared
-// memory in stages of (column chunk, kWideQC slabs G[q]), double-buffered,
-// and the H~ accumulators of a column chunk persist across its slabs.
-// Dense-channel comparator (C = I, p = P): w = c* is evaluated per stage
-// into the stage buffer instead.  SERVE: the serving link (k = i), whose
-// rows H~_ii(kappa) go to Hserv for the precoder kernel; otherwise the
-// interfering links' partial covariances, as in k_sinr_link_blk.
+// lane).  The projection w = c* C streams C_ik and the path coefficients
+// through shared memory in double-buffered chunks of PC paths and keeps
+// w [T][p] in shared memory; the core then streams in stages of (column
+// chunk, kWideQC slabs G[q]), double-buffered, and the H~ accumulators of a
+// column chunk persist across its slabs.  Dense-channel comparator (C = I,
+// p = P): w = c* is evaluated per stage into the stage buffer instead.
+// SERVE: the serving link (k = i), whose rows H~_ii(kappa) go to Hserv for
+// the precoder kernel, with the column chunks split over grid z (columns are
+// independent there); otherwise the interfering links' partial covariances,
+// as in k_sinr_link_blk.
 constexpr int kWideQC = 16;
 
 struct WidePlan {
-  int T, nq, SG, SV, WS, wide;
-  int off_ws, off_stage, stage, off_Gs, off_Vs, off_Wc, total;
+  int T, nq, SG, SV, WS, PC, wide, cps;
+  int off_ws, off_stage, stage, off_Gs, off_Vs, off_Wc, proj, off_Cc, off_cc, total;
 };
 
-__host__ __device__ inline WidePlan wide_plan(int MG, int LT, int p, bool identity, bool serve) {
+__host__ __device__ inline WidePlan wide_plan(int MG, int LT, int p, bool identity, bool serve,
+                                              int PC) {
   constexpr int NC = 4;
   WidePlan pl;
   pl.T = 2 * kThreads / (MG / 2);
@@ -1131,7 +1134,9 @@ __host__ __device__ inline WidePlan wide_plan(int MG, int LT, int p, bool identi
   pl.SG = NC + 2;
   pl.SV = NC * LT + 2;
   pl.WS = kWideQC + 1;
+  pl.PC = PC;
   pl.wide = 0;
+  pl.cps = 1 << 30;
   int o = 0;
   pl.off_ws = o;
   if (!identity) o += pl.T * (p + 1);
@@ -1143,8 +1148,15 @@ __host__ __device__ inline WidePlan wide_plan(int MG, int LT, int p, bool identi
   pl.off_Wc = so; if (identity) so += pl.T * pl.WS;
   so = (so + 1) & ~1;
   pl.stage = so;
+  // projection buffers (C chunk [PC][p], coefficient chunk [T][PC + 1]),
+  // sharing the region of the stage buffers (used one after the other)
+  pl.off_Cc = 0;
+  pl.off_cc = (PC * p + 1) & ~1;
+  pl.proj = identity ? 0 : ((pl.off_cc + pl.T * (PC + 1) + 1) & ~1);
   const int es = (kThreads / (MG / 2)) * (2 * MG * LT + 2);
-  o += (2 * so > es ? 2 * so : es);
+  int region = 2 * so > es ? 2 * so : es;
+  if (2 * pl.proj > region) region = 2 * pl.proj;
+  o += region;
   pl.total = o;
   return pl;
 }
@@ -1155,7 +1167,7 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link_wide(const SinrArgs A, c
   constexpr int GL = MG / 2;
   constexpr int T = 2 * kThreads / GL;
   constexpr int QS = kThreads / T;          // threads per subcarrier in the projection
-  constexpr int QA = 32 / QS;               // projection accumulators per thread and chunk
+  constexpr int QA = 32 / QS;               // projection outputs per thread and 32-column block
   constexpr int QC = kWideQC;
   extern __shared__ __align__(16) float2 sm[];
   const int tid = threadIdx.x;
@@ -1166,12 +1178,16 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link_wide(const SinrArgs A, c
   const int k = SERVE ? i : (z < i ? z : z + 1);
   const int ch = i * J + k;
   const int nq = pl.nq;
-  const int nstage = ((n + NC - 1) / NC) * nq;
+  const int nchunk = (n + NC - 1) / NC;
+  const int cbeg = SERVE ? z * pl.cps : 0;
+  const int cend = SERVE ? min(nchunk, cbeg + pl.cps) : nchunk;
+  const int nstage = (cend - cbeg) * nq;
   const bool ident = A.identity_C;
   float2* ws = sm + pl.off_ws;
   float2* stage0 = sm + pl.off_stage;
   const bool wide = pl.wide != 0;
   if (!SERVE && A.rcount != nullptr && tid == 0 && blockIdx.x == 0 && i == 0 && z == 0) *A.rcount = 0;
+  if (nstage <= 0) return;                  // an empty column slice (uniform over the CTA)
 
   // c_q(kappa) of this link (dense tile or path form), from global memory
   auto coef_at = [&](int kap, int q) -> float2 {
@@ -1182,7 +1198,7 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link_wide(const SinrArgs A, c
 
   auto issue_stage = [&](int st) {
     float2* buf = stage0 + (st & 1) * pl.stage;
-    const int cidx = st / nq, qi = st - cidx * nq;
+    const int cidx = cbeg + st / nq, qi = st % nq;
     const int c0 = cidx * NC, q0 = qi * QC;
     const int qc = min(QC, p - q0);
     const float2* Gch = A.G + (size_t)ch * p * m * n;
@@ -1230,43 +1246,70 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link_wide(const SinrArgs A, c
     }
   };
 
+  if (!ident) {
+    // projection w[t][q] = sum_P C[P][q] conj(c_P(kappa_t)) (eq. 15), chunks
+    // of PC paths: C rows by asynchronous copies, coefficients evaluated
+    // into shared memory, one chunk ahead of the accumulation.  Thread
+    // (t, qs) owns columns qb + qs QA + u of each 32-column block.
+    const int PC = pl.PC;
+    const int npc = (P + PC - 1) / PC;
+    const float2* Cch = A.C + (size_t)ch * P * p;
+    const bool c16 = (p % 2 == 0) && (((uintptr_t)A.C & 15u) == 0);
+    auto issue_proj = [&](int ci) {
+      float2* buf = stage0 + (ci & 1) * pl.proj;
+      const int P0 = ci * PC, pc = min(PC, P - P0);
+      const float2* src = Cch + (size_t)P0 * p;
+      if (c16) {
+        for (int idx = 2 * tid; idx < pc * p; idx += 2 * kThreads)
+          cp_async16(buf + pl.off_Cc + idx, src + idx, true);
+      } else {
+        for (int idx = tid; idx < pc * p; idx += kThreads) cp_async8(buf + pl.off_Cc + idx, src + idx, true);
+      }
+      for (int idx = tid; idx < T * PC; idx += kThreads) {
+        const int t = idx / PC, pp = idx - t * PC;
+        buf[pl.off_cc + t * (PC + 1) + pp] =
+            (pp < pc && kap0 + t < K) ? coef_at(kap0 + t, P0 + pp) : cz();
+      }
+    };
+    const int t = tid / QS, qs = tid % QS;
+    issue_proj(0);
+    cp_async_commit();
+    for (int ci = 0; ci < npc; ++ci) {
+      if (ci + 1 < npc) issue_proj(ci + 1);
+      cp_async_commit();
+      cp_async_wait<1>();
+      __syncthreads();
+      const float2* buf = stage0 + (ci & 1) * pl.proj;
+      const int pc = min(PC, P - ci * PC);
+      const float2* crow = buf + pl.off_cc + t * (PC + 1);
+      for (int qb = 0; qb < p; qb += 32) {
+        const int q0 = qb + qs * QA;
+        if (q0 >= p) continue;
+        float2 acc[QA];
+#pragma unroll
+        for (int u = 0; u < QA; ++u) acc[u] = cz();
+        const float2* Cb = buf + pl.off_Cc + q0;
+        for (int pp = 0; pp < pc; ++pp) {
+          const float2 c = crow[pp];
+          const float2* Cr = Cb + pp * p;
+#pragma unroll
+          for (int u = 0; u < QA; ++u)
+            if (q0 + u < p) cmacc(acc[u], Cr[u], c);
+        }
+        float2* wout = ws + t * (p + 1) + q0;
+#pragma unroll
+        for (int u = 0; u < QA; ++u)
+          if (q0 + u < p) wout[u] = ci == 0 ? acc[u] : cadd(wout[u], acc[u]);
+      }
+      __syncthreads();     // this buffer is refilled two chunks later
+    }
+    cp_async_wait<0>();
+  }
+
   issue_stage(0);
   cp_async_commit();
   if (nstage > 1) issue_stage(1);
   cp_async_commit();
-
-  if (!ident) {
-    // projection w[t][q] = sum_P C[P][q] conj(c_P(kappa_t)) (eq. 15) in chunks
-    // of 32 columns; QS consecutive lanes per subcarrier share the path
-    // coefficients by shuffles
-    const int t = tid / QS, qs = tid % QS;
-    const int kap_t = kap0 + t;
-    const float2* Cch = A.C + (size_t)ch * P * p;
-    for (int qb = 0; qb < p; qb += 32) {
-      float2 acc[QA];
-#pragma unroll
-      for (int u = 0; u < QA; ++u) acc[u] = cz();
-      for (int p0 = 0; p0 < P; p0 += QS) {
-        float2 mine = cz();
-        const int pm = p0 + qs;
-        if (kap_t < K && pm < P) mine = coef_at(kap_t, pm);
-#pragma unroll
-        for (int r = 0; r < QS; ++r) {
-          const int pp = p0 + r;
-          float2 c = mine;
-          if (QS > 1) c = gshfl<QS>(mine, r);
-          if (pp >= P) break;                        // uniform over the warp
-          const float2* crow = Cch + (size_t)pp * p + qb;
-#pragma unroll
-          for (int u = 0; u < QA; ++u)
-            if (qb + qs + u * QS < p) cmacc(acc[u], __ldg(crow + qs + u * QS), c);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < QA; ++u)
-        if (qb + qs + u * QS < p) ws[t * (p + 1) + qb + qs + u * QS] = acc[u];
-    }
-  }
   cp_async_wait<1>();
   __syncthreads();
 
@@ -1286,7 +1329,7 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link_wide(const SinrArgs A, c
       __syncthreads();
     }
     const float2* buf = stage0 + (st & 1) * pl.stage;
-    const int cidx = st / nq, qi = st - cidx * nq;
+    const int cidx = cbeg + st / nq, qi = st % nq;
     const int q0 = qi * QC, qc = min(QC, p - q0);
     if (qi == 0) {
 #pragma unroll
@@ -1544,12 +1587,30 @@ cudaError_t launch_link_blocked(const SinrArgs& A, cudaStream_t s) {
 template <int MG, int LT, bool SERVE>
 cudaError_t launch_link_wide(const SinrArgs& A, cudaStream_t s) {
   if (!SERVE && A.J < 2) return cudaSuccess;
-  WidePlan pl = wide_plan(MG, LT, A.p, A.identity_C, SERVE);
+  // projection chunk: 16 paths, fewer while the CTA would not fit its budget
+  int PC = 16;
+  WidePlan pl = wide_plan(MG, LT, A.p, A.identity_C, SERVE, PC);
+  while (PC > 2 && (size_t)pl.total * sizeof(float2) > kSmemBudget) {
+    PC /= 2;
+    pl = wide_plan(MG, LT, A.p, A.identity_C, SERVE, PC);
+  }
   const size_t smem = (size_t)pl.total * sizeof(float2);
   if (smem > kSmemBudget) return cudaErrorInvalidValue;
   pl.wide = (A.n % 2 == 0) && (A.L % 2 == 0) && (((uintptr_t)A.G & 15u) == 0) &&
             (((uintptr_t)A.V & 15u) == 0 || SERVE);
-  dim3 grid((A.K + pl.T - 1) / pl.T, A.J, SERVE ? 1 : A.J - 1);
+  const int tiles = (A.K + pl.T - 1) / pl.T;
+  int nz = SERVE ? 1 : A.J - 1;
+  if (SERVE) {
+    // the serving links alone are J CTAs per tile: split their column
+    // chunks so that about two CTAs per SM run
+    const int nchunk = (A.n + 3) / 4;
+    int slices = (2 * 152 + A.J * tiles - 1) / (A.J * tiles);
+    if (slices > nchunk) slices = nchunk;
+    if (slices < 1) slices = 1;
+    pl.cps = (nchunk + slices - 1) / slices;
+    nz = (nchunk + pl.cps - 1) / pl.cps;
+  }
+  dim3 grid(tiles, A.J, nz);
   auto kern = k_sinr_link_wide<MG, LT, SERVE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

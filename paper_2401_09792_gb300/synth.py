@@ -68,7 +68,17 @@ DIFFERENTIATION = Workload("diff J16 M16 N1024 P64 K3300 r(16,96,32) L8", J=16, 
                            P=64, K=3300, m=16, n=96, p=32, L=8, n_los=2,
                            pdp_decay_s=300e-9, sigma2=None)
 
-WORKLOADS = {"small": SMALL, "mid": MID, "precision": PRECISION, "diff": DIFFERENTIATION}
+# The paper's own system sizes (Section 4, table of compression results,
+# (M, N, P) = (8, 256, 401)): 21 cells with 5 or 10 UEs per cell and the
+# compressed sizes the paper tunes for them; the paper gives no subcarrier
+# count or stream count, so K = 64 subcarriers and L = 4 streams.
+PAPER_U5 = Workload("paper J21 U5 M8 N256 P401 K64 r(8,130,120) L4", J=21, M=8, N=256, P=401,
+                    K=64, m=8, n=130, p=120, L=4, n_los=2, pdp_decay_s=300e-9, sigma2=None, U=5)
+PAPER_U10 = Workload("paper J21 U10 M8 N256 P401 K64 r(8,140,140) L4", J=21, M=8, N=256, P=401,
+                     K=64, m=8, n=140, p=140, L=4, n_los=2, pdp_decay_s=300e-9, sigma2=None, U=10)
+
+WORKLOADS = {"small": SMALL, "mid": MID, "precision": PRECISION, "diff": DIFFERENTIATION,
+             "paper_u5": PAPER_U5, "paper_u10": PAPER_U10}
 
 
 def _rng(seed: int, *path: int) -> np.random.Generator:
