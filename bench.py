@@ -19,6 +19,7 @@ oracle on the same workload instead (rank 0 only).
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import os
@@ -385,6 +386,15 @@ def _extras(args, ts, torch, dist, world, dev, w, tk, host, dv, coef, d, ws, sin
     dense_value = units * dense_steps / (dense_ms * 1e-3)
     _method_error.result = _method_error(ts, torch, dev, w, Xd, coef, dv, d, stream, ev, flush,
                                          dense_ms / dense_steps)
+    # the same on spatially correlated NLOS channels (compressible in modes
+    # 1 and 2, as measured array channels are)
+    del Xd
+    wc = synth.MID_CORR if w == synth.MID else dataclasses.replace(w, nlos_corr=synth.MID_CORR.nlos_corr)
+    Xd = ts.channels_to_device(synth.channel_submatrices(wc), dev)
+    corr = _method_error(ts, torch, dev, w, Xd, coef, dv, d, stream, ev, flush, dense_ms / dense_steps)
+    corr["channels"] = (f"NLOS Kronecker model, exponential correlation {wc.nlos_corr[0]} (UE array) "
+                        f"and {wc.nlos_corr[1]} (BS array)")
+    _method_error.result["correlated_channels"] = corr
     del Xd, ws_d
     return e2e_value, h2d, d2h, mm_ms, dense_value, dense_ms, dense_steps
 
@@ -971,6 +981,91 @@ def run_multiuser(args):
     del keep
 
 
+def run_rank_sweep(args):
+    """Fig. 5 of the paper on synthetic channels: vary the compressed column
+    count n with (m, p) fixed, then p with (m, n) fixed, and report for
+    every point the storage ratio R_s (eq. 29), the GPU speedup
+    R_t = t_dense / t_compressed of the SVD-precoded SINR, and e_c (eq. 30)
+    of the groupwise form fitted on the GPU (Algorithm 2, 10 sweeps)."""
+    import torch
+
+    from oracle import tucker as T
+    from paper_2401_09792_gb300 import tuckersinr as ts
+    import __graft_entry__
+    __graft_entry__.build()
+    ts.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    w = WORKLOAD
+    J, K, L, M, N, P = w.J, w.K, w.L, w.M, w.N, w.P
+    alpha, tau = synth.path_gains_delays(w)
+    s2 = synth.noise_powers(w)
+    al = ts.factor_to_device(alpha.reshape(J * J, P), dev)
+    ta = ts.real_to_device(tau.reshape(J * J, P), dev)
+    sig = ts.real_to_device(s2, dev)
+    cs, keep = ts.make_coef(alpha=al, tau=ta)
+    Xd = ts.channels_to_device(synth.channel_submatrices(w), dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(reps):
+            flush.zero_()
+            a, b = ev(), ev()
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / reps
+
+    d0 = ts.Dims.of(w)
+    s_d = torch.empty(J, K, L, device=dev)
+    wsd = ts.workspace(d0, ts.TS_OP_DENSE_SVD, dev)
+    t_dense = timed(lambda: ts.ts_dense_sinr_svd(d0, cs, Xd, sig, s_d, None, wsd, stream))
+    sd = s_d.double()
+    del wsd
+    m0, n0, p0 = w.m, w.n, w.p
+    points = [(m0, n, p0) for n in (8, 16, 24, 32, 48, 64) if n <= N and L <= n] + \
+             [(m0, n0, p) for p in (2, 4, 8, 16, 24, 32) if p <= P and p != p0]
+    rows = []
+    for (m, n, p) in points:
+        d = ts.Dims(J, M, N, P, m, n, p, K, L)
+        A = torch.empty(J, M, m, dtype=torch.complex64, device=dev)
+        B = torch.empty(J, N, n, dtype=torch.complex64, device=dev)
+        C = torch.empty(J * J, P, p, dtype=torch.complex64, device=dev)
+        G = torch.empty(J * J, p, m, n, dtype=torch.complex64, device=dev)
+        g = torch.empty(31, dtype=torch.float64, device=dev)
+        wsf = ts.workspace(d, ts.TS_OP_TUCKER_FIT, dev)
+        t0 = time.perf_counter()
+        ts.ts_tucker_fit(d, Xd, 10, 0, A, B, C, G, g, wsf, stream)
+        torch.cuda.synchronize()
+        fit_s = time.perf_counter() - t0
+        del wsf
+        s_t = torch.empty(J, K, L, device=dev)
+        wss = ts.workspace(d, ts.TS_OP_SINR_SVD, dev)
+        t_t = timed(lambda: ts.ts_sinr_svd(d, cs, G, C, sig, s_t, None, wss, stream))
+        st = s_t.double()
+        rows.append({"m": m, "n": n, "p": p,
+                     "R_s": T.storage_ratio(J, 1, M, N, P, m, n, p, "groupwise"),
+                     "R_t": t_dense / t_t, "sinr_ms": round(t_t, 4),
+                     "e_c": float(((st - sd).abs() / sd.abs()).mean().item()),
+                     "g_over_x2": float(g[-1].item()) / float((Xd.abs() ** 2).sum().item()),
+                     "fit_s": round(fit_s, 2)})
+        del A, B, C, G, wss
+    line = {"metric": "rank sweep (Fig. 5 analogue)", "workload": workload_config(w)["workload"],
+            "dense_sinr_ms": round(t_dense, 4), "points": rows,
+            "what": "n swept with (m, p) fixed, then p with (m, n) fixed; Tucker form fitted on the "
+                    "GPU from the synthetic channels; R_t and e_c against the dense-channel SINR "
+                    "on the same GPU kernels"}
+    print(json.dumps(line), flush=True)
+    del keep
+
+
 # ------------------------------------------------------------ reference arm
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -1043,6 +1138,9 @@ def main():
                     help="synthetic system of the timed step (default: mid, the headline)")
     ap.add_argument("--batch-instances", type=int, default=512,
                     help="systems of the batch workload")
+    ap.add_argument("--rank-sweep", action="store_true",
+                    help="sweep the compressed sizes n, then p, on the workload (default mid_corr): "
+                         "R_s, R_t and e_c per point")
     ap.add_argument("--adjoint", action="store_true",
                     help="also time the SVD-SINR adjoint (dSINR -> dG, dC) on the workload")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16x2"],
@@ -1053,6 +1151,10 @@ def main():
         args.warmup = 3
     if args.workload == "batch":
         run_batch(args)
+        return
+    if args.rank_sweep:
+        select_workload("mid_corr" if args.workload == "mid" else args.workload)
+        run_rank_sweep(args)
         return
     select_workload(args.workload)
     if args.impl == "reference":

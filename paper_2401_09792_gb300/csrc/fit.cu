@@ -158,8 +158,8 @@ k_jacobi(const double2* Sin, int D, int r, double2* out, double* lsum, const dou
   double2* S = js;                      // D x SD
   double2* U = S + D * SD;              // D x SD
   double2* rcs = U + D * SD;            // (c, s) per pair
-  double2* rph = rcs + kJacobiMax / 2 + 1;   // e per pair; later the column phases
-  int* pq = reinterpret_cast<int*>(rph + kJacobiMax / 2 + 1);
+  double2* rph = rcs + kJacobiMax / 2 + 1;   // e per pair; later the r <= D column phases
+  int* pq = reinterpret_cast<int*>(rph + kJacobiMax);
   double* red = reinterpret_cast<double*>(pq + kJacobiMax + 2);
   const int mat = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
   const double2* src = Sin + (size_t)mat * D * D;
@@ -446,9 +446,11 @@ __global__ void k_norm2(const double2* T, size_t count, double* g_hist, int slot
 cudaError_t leading_eigvecs(const double2* S, int nmat, int D, int r, double2* F, double* lsum,
                             bool warm, double2* Qbuf, double2* Ybuf, double2* Tbuf, int iters,
                             cudaStream_t s) {
+  // S, U; (c, s) per pair; e per pair, later one phase per kept column;
+  // pair indices, later the eigenvalue order; reduction scratch
   const size_t jsm = (size_t)2 * kJacobiMax * (kJacobiMax + 1) * sizeof(double2) +
-                     2 * (kJacobiMax / 2 + 1) * sizeof(double2) + (kJacobiMax + 2) * sizeof(int) +
-                     80 * sizeof(double);
+                     (kJacobiMax / 2 + 1 + kJacobiMax) * sizeof(double2) +
+                     (kJacobiMax + 2) * sizeof(int) + 80 * sizeof(double);
   cudaError_t e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jsm);
   if (e != cudaSuccess) return e;
   if (D <= kJacobiMax) {

@@ -25,7 +25,7 @@ complex128 / float64 here; the binding casts them to the device layout.
 """
 from __future__ import annotations
 
-from dataclasses import dataclass, field
+from dataclasses import dataclass, field, replace
 
 import numpy as np
 
@@ -52,6 +52,10 @@ class Workload:
     delta_f_hz: float = 15e3
     seed: int = 0
     U: int = 1        # UEs per cell (UE groups; group 0 = the first UE of every cell)
+    # NLOS submatrices: None = i.i.d. CN(0, 1) entries; (rho_rx, rho_tx) =
+    # Kronecker model R_rx^{1/2} W R_tx^{1/2} with exponential correlation
+    # R[a, b] = rho^|a - b| across the UE and the BS array
+    nlos_corr: tuple | None = None
     extra: dict = field(default_factory=dict)
 
 
@@ -77,8 +81,14 @@ PAPER_U5 = Workload("paper J21 U5 M8 N256 P401 K64 r(8,130,120) L4", J=21, M=8, 
 PAPER_U10 = Workload("paper J21 U10 M8 N256 P401 K64 r(8,140,140) L4", J=21, M=8, N=256, P=401,
                      K=64, m=8, n=140, p=140, L=4, n_los=2, pdp_decay_s=300e-9, sigma2=None, U=10)
 
+# The mid system with spatially correlated NLOS submatrices (exponential
+# correlation 0.7 across the 8 UE antennas, 0.95 across the 256 BS antennas):
+# compressible in modes 1 and 2, as measured array channels are.
+MID_CORR = replace(MID, name="mid-corr J8 M8 N256 P32 K1024 r(8,32,16) L8 rho(0.7,0.95)",
+                   nlos_corr=(0.7, 0.95))
+
 WORKLOADS = {"small": SMALL, "mid": MID, "precision": PRECISION, "diff": DIFFERENTIATION,
-             "paper_u5": PAPER_U5, "paper_u10": PAPER_U10}
+             "paper_u5": PAPER_U5, "paper_u10": PAPER_U10, "mid_corr": MID_CORR}
 
 
 def _rng(seed: int, *path: int) -> np.random.Generator:
@@ -111,6 +121,8 @@ def channel_submatrices(w: Workload, ue: int = 0) -> np.ndarray:
     Returns shape (J, J, M, N, P), complex128.
     """
     X = np.empty((w.J, w.J, w.M, w.N, w.P), dtype=np.complex128)
+    if w.nlos_corr is not None:
+        Sr, St = (_exp_corr_sqrt(d, rho) for d, rho in zip((w.M, w.N), w.nlos_corr))
     for i in range(w.J):
         for k in range(w.J):
             rng = _rng(w.seed, 1, i, k, *ue_key(ue))
@@ -118,9 +130,20 @@ def channel_submatrices(w: Workload, ue: int = 0) -> np.ndarray:
                 if q < w.n_los:
                     th, ph = rng.uniform(-np.pi / 2, np.pi / 2, 2)
                     X[i, k, :, :, q] = np.outer(_ula(w.M, th), np.conj(_ula(w.N, ph)))
-                else:
+                elif w.nlos_corr is None:
                     X[i, k, :, :, q] = _cn(rng, (w.M, w.N))
+                else:
+                    X[i, k, :, :, q] = Sr @ _cn(rng, (w.M, w.N)) @ St
     return X
+
+
+def _exp_corr_sqrt(d: int, rho: float) -> np.ndarray:
+    """Symmetric square root of the d x d exponential correlation matrix
+    R[a, b] = rho^|a - b| (real, positive definite for 0 <= rho < 1)."""
+    a = np.arange(d)
+    R = float(rho) ** np.abs(a[:, None] - a[None, :])
+    lam, V = np.linalg.eigh(R)
+    return (V * np.sqrt(np.maximum(lam, 0.0))) @ V.T
 
 
 def path_gains_delays(w: Workload, ue: int = 0) -> tuple[np.ndarray, np.ndarray]:

@@ -80,3 +80,13 @@ def test_fit_full_rank_reconstructs():
     A, B, C, G, g = _gpu_fit(X, (3, 5, 4), 1)
     f = T.objective_f(X, A, B, C, G)
     assert f < 1e-9 * T.fro2(X)
+
+
+@pytest.mark.parametrize("N", [64, 128])
+def test_fit_ranks_above_half_the_jacobi_block(N):
+    # kept ranks r > 36: the Jacobi kernel keeps one phase per kept column
+    # (N = 64: every Gram by Jacobi, r = 48 of 64; N = 128: the B Grams by
+    # subspace iteration with a 72-column block and a Rayleigh-Ritz Jacobi
+    # keeping 48)
+    w = dataclasses.replace(synth.SMALL, J=2, M=4, N=N, P=64, m=4, n=48, p=48, K=8, L=2)
+    _check(w, S=2, gtol=1e-6)
