@@ -47,6 +47,11 @@ def select_workload(name: str):
     WORKLOAD, WORKLOAD_NAME = synth.WORKLOADS[name], name
 
 
+def set_ue_groups(U: int):
+    global WORKLOAD
+    WORKLOAD = dataclasses.replace(WORKLOAD, U=max(1, int(U)))
+
+
 def workload_config(w, precoder="svd"):
     cells = (f"J={w.J} cells" if w.U == 1 else
              f"J={w.J} cells x U={w.U} UEs, first-UE inter-cell interference")
@@ -96,18 +101,29 @@ def peaks():
         return {}
 
 
-def kernel_source_hash() -> str:
+# the sources each profiled kernel is built from (its summary under
+# profiles/ stays valid while none of them changes)
+KERNEL_SOURCES = {
+    "k_sinr_link_blk": ("sinr_impl.cuh", "common.cuh", "kernels.h"),
+    "k_svd_precoder": ("sinr_impl.cuh", "common.cuh", "kernels.h"),
+    "k_sinr_finalize": ("sinr_impl.cuh", "common.cuh", "kernels.h"),
+    "k_sinr_link_wide": ("sinr_wide.cuh", "sinr_impl.cuh", "common.cuh", "kernels.h"),
+    "k_sinr_link_tc_tf32": ("sinr_tc.cu", "common.cuh", "kernels.h"),
+    "k_sinr_link_tc_bf16x2": ("sinr_tc.cu", "common.cuh", "kernels.h"),
+}
+
+
+def kernel_source_hash(kernel: str) -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2401_09792_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, name), "rb").read())
+    for name in KERNEL_SOURCES[kernel]:
+        h.update(open(os.path.join(csrc, name), "rb").read())
     return h.hexdigest()[:16]
 
 
 def recorded_traffic(kernel: str, workload: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources; else None."""
+    on the current sources of that kernel; else None."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     try:
         text = open(path).read()
@@ -115,7 +131,7 @@ def recorded_traffic(kernel: str, workload: str):
         return None
     mh = re.search(r"kernel_source_hash:\s*(\w+)", text)
     mb = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    if not mh or not mb or mh.group(1) != kernel_source_hash():
+    if not mh or not mb or mh.group(1) != kernel_source_hash(kernel):
         return None
     return float(mb.group(1))
 
@@ -884,6 +900,14 @@ def run_multiuser(args):
     assert int((flags & ts.TS_FLAG_ERRORS).max().item()) == 0, "numerical flags raised"
     units = U * J * K
     value = units * args.steps / (total * 1e-3)
+    if args.step_only:
+        print(json.dumps({"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 1,
+                          "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": total / args.steps, "higher_is_better": True,
+                          "link_ms": float(np.mean(link_ms)), "clocks": clocks,
+                          "config": {"workload": WORKLOAD_NAME, "U": U}}), flush=True)
+        del keep
+        return
 
     # dense comparator on X^ (exact Tucker form, so the same SINR up to rounding)
     Xh = torch.empty(U * nl, P, M, N, **c64)
@@ -1138,6 +1162,8 @@ def main():
                     help="synthetic system of the timed step (default: mid, the headline)")
     ap.add_argument("--batch-instances", type=int, default=512,
                     help="systems of the batch workload")
+    ap.add_argument("--ue-groups", type=int, default=None,
+                    help="UEs per cell of a several-UE workload (default: the workload's)")
     ap.add_argument("--rank-sweep", action="store_true",
                     help="sweep the compressed sizes n, then p, on the workload (default mid_corr): "
                          "R_s, R_t and e_c per point")
@@ -1157,9 +1183,12 @@ def main():
         run_rank_sweep(args)
         return
     select_workload(args.workload)
+    several = WORKLOAD.U > 1
+    if args.ue_groups is not None:
+        set_ue_groups(args.ue_groups)
     if args.impl == "reference":
         run_reference(args)
-    elif WORKLOAD.U > 1:
+    elif several:
         run_multiuser(args)
     else:
         run_ours(args)

@@ -1,0 +1,374 @@
+// Wide-core link kernel of the SVD path (included by sinr_impl.cuh, whose
+// helpers it uses: path_coef, the cp.async wrappers, kThreads, kSmemBudget).
+#pragma once
+
+namespace ts {
+namespace detail {
+
+// Wide-core variant of the blocked link pass, for ranks beyond what the
+// narrow kernels stage (p > 32 or P p > 8192): the paper's compressed sizes
+// (p ~ 100-200 of P ~ 400 paths) and the dense-channel comparator at large P.
+// Same thread layout as k_sinr_link_blk (two subcarriers and two rows per
+// lane).  The projection w = c* C streams C_ik and the path coefficients
+// through shared memory in double-buffered chunks of PC paths and keeps
+// w [T][p] in shared memory; the core then streams in stages of (column
+// chunk, kWideQC slabs G[q]), double-buffered, and the H~ accumulators of a
+// column chunk persist across its slabs.  Dense-channel comparator (C = I,
+// p = P): w = c* is evaluated per stage into the stage buffer instead.
+// SERVE: the serving link (k = i), whose rows H~_ii(kappa) go to Hserv for
+// the precoder kernel, with the column chunks split over grid z (columns are
+// independent there); otherwise the interfering links' partial covariances,
+// as in k_sinr_link_blk.
+constexpr int kWideQC = 16;
+
+struct WidePlan {
+  int T, nq, SG, SV, WS, PC, wide, cps;
+  int off_ws, off_stage, stage, off_Gs, off_Vs, off_Wc, proj, off_Cc, off_cc, total;
+};
+
+__host__ __device__ inline WidePlan wide_plan(int MG, int LT, int p, bool identity, bool serve,
+                                              int PC) {
+  constexpr int NC = 4;
+  WidePlan pl;
+  pl.T = 2 * kThreads / (MG / 2);
+  pl.nq = (p + kWideQC - 1) / kWideQC;
+  pl.SG = NC + 2;
+  pl.SV = NC * LT + 2;
+  pl.WS = kWideQC + 1;
+  pl.PC = PC;
+  pl.wide = 0;
+  pl.cps = 1 << 30;
+  int o = 0;
+  pl.off_ws = o;
+  if (!identity) o += pl.T * (p + 1);
+  o = (o + 1) & ~1;
+  pl.off_stage = o;
+  int so = 0;
+  pl.off_Gs = so; so += kWideQC * MG * pl.SG;
+  pl.off_Vs = so; if (!serve) so += pl.T * pl.SV;
+  pl.off_Wc = so; if (identity) so += pl.T * pl.WS;
+  so = (so + 1) & ~1;
+  pl.stage = so;
+  // projection buffers (C chunk [PC][p], coefficient chunk [T][PC + 1]),
+  // sharing the region of the stage buffers (used one after the other)
+  pl.off_Cc = 0;
+  pl.off_cc = (PC * p + 1) & ~1;
+  pl.proj = identity ? 0 : ((pl.off_cc + pl.T * (PC + 1) + 1) & ~1);
+  const int es = (kThreads / (MG / 2)) * (2 * MG * LT + 2);
+  int region = 2 * so > es ? 2 * so : es;
+  if (2 * pl.proj > region) region = 2 * pl.proj;
+  o += region;
+  pl.total = o;
+  return pl;
+}
+
+template <int MG, int LT, bool SERVE>
+__global__ void __launch_bounds__(kThreads) k_sinr_link_wide(const SinrArgs A, const WidePlan pl) {
+  constexpr int NC = 4;
+  constexpr int GL = MG / 2;
+  constexpr int T = 2 * kThreads / GL;
+  constexpr int QS = kThreads / T;          // threads per subcarrier in the projection
+  constexpr int QA = 32 / QS;               // projection outputs per thread and 32-column block
+  constexpr int QC = kWideQC;
+  extern __shared__ __align__(16) float2 sm[];
+  const int tid = threadIdx.x;
+  const int gp = tid / GL, j = tid % GL;
+  const int i = blockIdx.y, z = blockIdx.z;
+  const int kap0 = blockIdx.x * T;
+  const int J = A.J, m = A.m, n = A.n, p = A.p, L = A.L, K = A.K, P = A.P;
+  const int k = SERVE ? i : (z < i ? z : z + 1);
+  const int ch = i * J + k;
+  const int nq = pl.nq;
+  const int nchunk = (n + NC - 1) / NC;
+  const int cbeg = SERVE ? z * pl.cps : 0;
+  const int cend = SERVE ? min(nchunk, cbeg + pl.cps) : nchunk;
+  const int nstage = (cend - cbeg) * nq;
+  const bool ident = A.identity_C;
+  float2* ws = sm + pl.off_ws;
+  float2* stage0 = sm + pl.off_stage;
+  const bool wide = pl.wide != 0;
+  if (!SERVE && A.rcount != nullptr && tid == 0 && blockIdx.x == 0 && i == 0 && z == 0) *A.rcount = 0;
+  if (nstage <= 0) return;                  // an empty column slice (uniform over the CTA)
+
+  // c_q(kappa) of this link (dense tile or path form), from global memory
+  auto coef_at = [&](int kap, int q) -> float2 {
+    return A.coef_mode == 0 ? A.coef[((size_t)ch * K + kap) * P + q]
+                            : path_coef(__ldg(A.coef + (size_t)ch * P + q),
+                                        __ldg(A.turns + (size_t)ch * P + q), kap);
+  };
+
+  auto issue_stage = [&](int st) {
+    float2* buf = stage0 + (st & 1) * pl.stage;
+    const int cidx = cbeg + st / nq, qi = st % nq;
+    const int c0 = cidx * NC, q0 = qi * QC;
+    const int qc = min(QC, p - q0);
+    const float2* Gch = A.G + (size_t)ch * p * m * n;
+    if (wide) {
+      constexpr int GU = MG * NC / 2;                 // 16-byte units per slab
+      const int cc = 2 * (tid % (NC / 2)), aa = (tid / (NC / 2)) % MG;
+      const bool rowok = aa < m && c0 + cc < n;
+      for (int ql = tid / GU; ql < qc; ql += kThreads / GU)
+        cp_async16(buf + pl.off_Gs + (ql * MG + aa) * pl.SG + cc,
+                   rowok ? Gch + ((size_t)(q0 + ql) * m + aa) * n + c0 + cc : A.G, rowok);
+      if (!SERVE && qi == nq - 1) {
+        constexpr int VU = NC * LT / 2;
+        const int l = 2 * (tid % (LT / 2)), vc = (tid / (LT / 2)) % NC;
+        const bool colok = c0 + vc < n && l < L;
+        for (int t = tid / VU; t < T; t += kThreads / VU) {
+          const bool ok = colok && kap0 + t < K;
+          cp_async16(buf + pl.off_Vs + t * pl.SV + vc * LT + l,
+                     ok ? A.V + (((size_t)k * K + kap0 + t) * n + c0 + vc) * L + l : A.V, ok);
+        }
+      }
+    } else {
+      for (int idx = tid; idx < qc * MG * NC; idx += kThreads) {
+        const int cc = idx % NC, aa = (idx / NC) % MG, ql = idx / (NC * MG);
+        const int c = c0 + cc;
+        const bool ok = aa < m && c < n;
+        cp_async8(buf + pl.off_Gs + (ql * MG + aa) * pl.SG + cc,
+                  ok ? Gch + ((size_t)(q0 + ql) * m + aa) * n + c : A.G, ok);
+      }
+      if (!SERVE && qi == nq - 1) {
+        for (int idx = tid; idx < T * NC * LT; idx += kThreads) {
+          const int l = idx % LT, cc = (idx / LT) % NC, t = idx / (LT * NC);
+          const int kk2 = kap0 + t, c = c0 + cc;
+          const bool ok = kk2 < K && c < n && l < L;
+          cp_async8(buf + pl.off_Vs + t * pl.SV + cc * LT + l,
+                    ok ? A.V + (((size_t)k * K + kk2) * n + c) * L + l : A.V, ok);
+        }
+      }
+    }
+    if (ident) {
+      // dense channel: w_q = conj(c_q(kappa)) for the slab
+      for (int idx = tid; idx < T * qc; idx += kThreads) {
+        const int t = idx / qc, ql = idx - t * qc;
+        buf[pl.off_Wc + t * pl.WS + ql] = kap0 + t < K ? cconj(coef_at(kap0 + t, q0 + ql)) : cz();
+      }
+    }
+  };
+
+  if (!ident) {
+    // projection w[t][q] = sum_P C[P][q] conj(c_P(kappa_t)) (eq. 15), chunks
+    // of PC paths: C rows by asynchronous copies, coefficients evaluated
+    // into shared memory, one chunk ahead of the accumulation.  Thread
+    // (t, qs) owns columns qb + qs QA + u of each 32-column block.
+    const int PC = pl.PC;
+    const int npc = (P + PC - 1) / PC;
+    const float2* Cch = A.C + (size_t)ch * P * p;
+    const bool c16 = (p % 2 == 0) && (((uintptr_t)A.C & 15u) == 0);
+    auto issue_proj = [&](int ci) {
+      float2* buf = stage0 + (ci & 1) * pl.proj;
+      const int P0 = ci * PC, pc = min(PC, P - P0);
+      const float2* src = Cch + (size_t)P0 * p;
+      if (c16) {
+        for (int idx = 2 * tid; idx < pc * p; idx += 2 * kThreads)
+          cp_async16(buf + pl.off_Cc + idx, src + idx, true);
+      } else {
+        for (int idx = tid; idx < pc * p; idx += kThreads) cp_async8(buf + pl.off_Cc + idx, src + idx, true);
+      }
+      for (int idx = tid; idx < T * PC; idx += kThreads) {
+        const int t = idx / PC, pp = idx - t * PC;
+        buf[pl.off_cc + t * (PC + 1) + pp] =
+            (pp < pc && kap0 + t < K) ? coef_at(kap0 + t, P0 + pp) : cz();
+      }
+    };
+    const int t = tid / QS, qs = tid % QS;
+    issue_proj(0);
+    cp_async_commit();
+    for (int ci = 0; ci < npc; ++ci) {
+      if (ci + 1 < npc) issue_proj(ci + 1);
+      cp_async_commit();
+      cp_async_wait<1>();
+      __syncthreads();
+      const float2* buf = stage0 + (ci & 1) * pl.proj;
+      const int pc = min(PC, P - ci * PC);
+      const float2* crow = buf + pl.off_cc + t * (PC + 1);
+      for (int qb = 0; qb < p; qb += 32) {
+        const int q0 = qb + qs * QA;
+        if (q0 >= p) continue;
+        float2 acc[QA];
+#pragma unroll
+        for (int u = 0; u < QA; ++u) acc[u] = cz();
+        const float2* Cb = buf + pl.off_Cc + q0;
+        for (int pp = 0; pp < pc; ++pp) {
+          const float2 c = crow[pp];
+          const float2* Cr = Cb + pp * p;
+#pragma unroll
+          for (int u = 0; u < QA; ++u)
+            if (q0 + u < p) cmacc(acc[u], Cr[u], c);
+        }
+        float2* wout = ws + t * (p + 1) + q0;
+#pragma unroll
+        for (int u = 0; u < QA; ++u)
+          if (q0 + u < p) wout[u] = ci == 0 ? acc[u] : cadd(wout[u], acc[u]);
+      }
+      __syncthreads();     // this buffer is refilled two chunks later
+    }
+    cp_async_wait<0>();
+  }
+
+  issue_stage(0);
+  cp_async_commit();
+  if (nstage > 1) issue_stage(1);
+  cp_async_commit();
+  cp_async_wait<1>();
+  __syncthreads();
+
+  float2 E[2][2][LT];   // [subcarrier of the pair][row j, j + GL][stream]
+#pragma unroll
+  for (int x = 0; x < 2; ++x)
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int l = 0; l < LT; ++l) E[x][r][l] = cz();
+  float2 h[2][2][NC];
+  for (int st = 0; st < nstage; ++st) {
+    if (st > 0) {
+      if (st + 1 < nstage) issue_stage(st + 1);
+      cp_async_commit();
+      cp_async_wait<1>();
+      __syncthreads();
+    }
+    const float2* buf = stage0 + (st & 1) * pl.stage;
+    const int cidx = cbeg + st / nq, qi = st % nq;
+    const int q0 = qi * QC, qc = min(QC, p - q0);
+    if (qi == 0) {
+#pragma unroll
+      for (int x = 0; x < 2; ++x)
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+          for (int cc = 0; cc < NC; ++cc) h[x][r][cc] = cz();
+    }
+    const float2* w0 = ident ? buf + pl.off_Wc + (2 * gp) * pl.WS : ws + (2 * gp) * (p + 1) + q0;
+    const float2* w1 = w0 + (ident ? pl.WS : p + 1);
+    const float2* g0 = buf + pl.off_Gs + j * pl.SG;
+    const float2* g1 = g0 + GL * pl.SG;
+#pragma unroll 4
+    for (int q = 0; q < qc; ++q) {
+      const float2 wa = w0[q], wb = w1[q];
+      const float4* ga = reinterpret_cast<const float4*>(g0 + q * MG * pl.SG);
+      const float4* gb = reinterpret_cast<const float4*>(g1 + q * MG * pl.SG);
+#pragma unroll
+      for (int c2 = 0; c2 < NC / 2; ++c2) {
+        const float4 u = ga[c2], v = gb[c2];
+        const float2 u0 = make_float2(u.x, u.y), u1 = make_float2(u.z, u.w);
+        const float2 v0 = make_float2(v.x, v.y), v1 = make_float2(v.z, v.w);
+        cmac(h[0][0][2 * c2], wa, u0);
+        cmac(h[0][0][2 * c2 + 1], wa, u1);
+        cmac(h[1][0][2 * c2], wb, u0);
+        cmac(h[1][0][2 * c2 + 1], wb, u1);
+        cmac(h[0][1][2 * c2], wa, v0);
+        cmac(h[0][1][2 * c2 + 1], wa, v1);
+        cmac(h[1][1][2 * c2], wb, v0);
+        cmac(h[1][1][2 * c2 + 1], wb, v1);
+      }
+    }
+    if (qi == nq - 1) {
+      const int c0 = cidx * NC;
+      if (SERVE) {
+#pragma unroll
+        for (int x = 0; x < 2; ++x) {
+          const int kap = kap0 + 2 * gp + x;
+#pragma unroll
+          for (int r = 0; r < 2; ++r) {
+            const int a = j + r * GL;
+            if (kap >= K || a >= m) continue;
+            float2* Hrow = A.Hserv + (((size_t)i * K + kap) * m + a) * n;
+#pragma unroll
+            for (int cc = 0; cc < NC; ++cc)
+              if (c0 + cc < n) Hrow[c0 + cc] = h[x][r][cc];
+          }
+        }
+      } else {
+        const float2* va = buf + pl.off_Vs + (2 * gp) * pl.SV;
+        const float2* vb = va + pl.SV;
+#pragma unroll
+        for (int cc = 0; cc < NC; ++cc) {
+#pragma unroll
+          for (int l2 = 0; l2 < LT / 2; ++l2) {
+            const float4 x = reinterpret_cast<const float4*>(va + cc * LT)[l2];
+            const float4 y = reinterpret_cast<const float4*>(vb + cc * LT)[l2];
+            const float2 x0 = make_float2(x.x, x.y), x1 = make_float2(x.z, x.w);
+            const float2 y0 = make_float2(y.x, y.y), y1 = make_float2(y.z, y.w);
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+              cmac(E[0][r][2 * l2], h[0][r][cc], x0);
+              cmac(E[0][r][2 * l2 + 1], h[0][r][cc], x1);
+              cmac(E[1][r][2 * l2], h[1][r][cc], y0);
+              cmac(E[1][r][2 * l2 + 1], h[1][r][cc], y1);
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();   // this buffer is refilled two stages later
+  }
+  cp_async_wait<0>();
+  if (SERVE) return;
+
+  // partial covariance rows (E E*)[a][b], b < m (eq. 25), for both subcarriers
+  float2* Es = stage0 + gp * (2 * MG * LT + 2);
+#pragma unroll
+  for (int x = 0; x < 2; ++x)
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int l = 0; l < LT; ++l) Es[(x * MG + j + r * GL) * LT + l] = E[x][r][l];
+  __syncwarp();
+#pragma unroll
+  for (int x = 0; x < 2; ++x) {
+    const int kap = kap0 + 2 * gp + x;
+    if (kap >= K) continue;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int a = j + r * GL;
+      if (a >= m) continue;
+      float2* Rout = A.Rpart + ((((size_t)i * (J - 1) + z) * K + kap) * m + a) * m;
+      for (int b = 0; b < m; ++b) {
+        float2 acc = cz();
+        const float2* eb = Es + (x * MG + b) * LT;
+#pragma unroll
+        for (int l = 0; l < LT; ++l) cmacc(acc, E[x][r][l], eb[l]);
+        Rout[b] = acc;
+      }
+    }
+  }
+}
+
+template <int MG, int LT, bool SERVE>
+cudaError_t launch_link_wide(const SinrArgs& A, cudaStream_t s) {
+  if (!SERVE && A.J < 2) return cudaSuccess;
+  // projection chunk: 16 paths, fewer while the CTA would not fit its budget
+  int PC = 16;
+  WidePlan pl = wide_plan(MG, LT, A.p, A.identity_C, SERVE, PC);
+  while (PC > 2 && (size_t)pl.total * sizeof(float2) > kSmemBudget) {
+    PC /= 2;
+    pl = wide_plan(MG, LT, A.p, A.identity_C, SERVE, PC);
+  }
+  const size_t smem = (size_t)pl.total * sizeof(float2);
+  if (smem > kSmemBudget) return cudaErrorInvalidValue;
+  pl.wide = (A.n % 2 == 0) && (A.L % 2 == 0) && (((uintptr_t)A.G & 15u) == 0) &&
+            (((uintptr_t)A.V & 15u) == 0 || SERVE);
+  const int tiles = (A.K + pl.T - 1) / pl.T;
+  int nz = SERVE ? 1 : A.J - 1;
+  if (SERVE) {
+    // the serving links alone are J CTAs per tile: split their column
+    // chunks so that about two CTAs per SM run
+    const int nchunk = (A.n + 3) / 4;
+    int slices = (2 * 152 + A.J * tiles - 1) / (A.J * tiles);
+    if (slices > nchunk) slices = nchunk;
+    if (slices < 1) slices = 1;
+    pl.cps = (nchunk + slices - 1) / slices;
+    nz = (nchunk + pl.cps - 1) / pl.cps;
+  }
+  dim3 grid(tiles, A.J, nz);
+  auto kern = k_sinr_link_wide<MG, LT, SERVE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, kThreads, smem, s>>>(A, pl);
+  return cudaGetLastError();
+}
+
+}  // namespace detail
+}  // namespace ts
