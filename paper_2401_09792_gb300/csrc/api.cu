@@ -85,7 +85,7 @@ int check_narrow(const ts_dims* d) {
 
 // Workspace layout (byte offsets from the base, each 256-byte aligned).
 struct Workspace {
-  size_t turns = 0, V = 0, Hserv = 0, Eserv = 0, Rpart = 0, pflag = 0, F = 0, rlist = 0,
+  size_t turns = 0, V = 0, Hserv = 0, Wserv = 0, Eserv = 0, Rpart = 0, pflag = 0, F = 0, rlist = 0,
          rcount = 0, total = 0;
 };
 
@@ -105,6 +105,10 @@ Workspace carve(const ts_dims* d, int op) {
     if (!ts::precoder_fuses_serve(d->m, d->n, d->p)) {
       w.Hserv = o;
       o = align_up(o + (size_t)d->J * d->K * d->m * d->n * sizeof(float2), 256);
+      if (ts::wide_core(d->P, d->p)) {
+        w.Wserv = o;
+        o = align_up(o + (size_t)d->J * d->K * d->p * sizeof(float2), 256);
+      }
     }
     w.pflag = o;
     o = align_up(o + (size_t)d->J * d->K, 256);
@@ -529,6 +533,7 @@ int svd_precoders_impl(const ts_dims* d, const ts_coef* coef, const ts_c64* G, c
   if (!a.fuse_serve) {
     a.Hserv = reinterpret_cast<float2*>(base + w.Hserv);
     a.serv_stride = 1;
+    if (w.Wserv != 0 && !identity) a.Wserv = reinterpret_cast<float2*>(base + w.Wserv);
     if (e == cudaSuccess) e = ts::launch_sinr_serving(a, s);
   }
   if (e == cudaSuccess) e = ts::launch_svd_precoder(a, s);

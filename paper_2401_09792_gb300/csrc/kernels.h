@@ -24,6 +24,8 @@ struct SinrArgs {
                                     // [J*J][K][m][n] (adjoint)
   int serv_stride;                  // serving link k at Hserv[(k * serv_stride) * K + kappa]
   int fuse_serve;                   // svd precoder forms H~_kk itself (Hserv unused)
+  float2* Wserv;                    // wide cores: serving links' projections c* C,
+                                    // [J][K][p] (workspace), or nullptr
   float2* Uout;                     // adjoint: left singular vectors [J][K][m][m] (or nullptr)
   float* Sout;                      // adjoint: singular values [J][K][m]
   float2* Vmout;                    // adjoint: right singular vectors [J][K][n][m]

@@ -147,7 +147,14 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link_wide(const SinrArgs A, c
     }
   };
 
-  if (!ident) {
+  if (SERVE && A.Wserv != nullptr) {
+    // the serving links' projections come from k_wide_proj
+    const float2* src = A.Wserv + ((size_t)i * K + kap0) * p;
+    for (int idx = tid; idx < T * p; idx += kThreads) {
+      const int t = idx / p, q = idx - t * p;
+      ws[t * (p + 1) + q] = kap0 + t < K ? src[idx] : cz();
+    }
+  } else if (!ident) {
     // projection w[t][q] = sum_P C[P][q] conj(c_P(kappa_t)) (eq. 15), chunks
     // of PC paths: C rows by asynchronous copies, coefficients evaluated
     // into shared memory, one chunk ahead of the accumulation.  Thread
@@ -336,6 +343,82 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link_wide(const SinrArgs A, c
   }
 }
 
+// Projections of the serving links for the wide-core serving pass, whose
+// column slices would otherwise each recompute them: CTA (tile, BS i,
+// 32-column block) accumulates w[t][q] = sum_P C_ii[P][q] conj(c_P(kappa_t))
+// (eq. 15) in registers over double-buffered chunks of C rows and path
+// coefficients, then writes Wserv[i][kappa][q].
+constexpr int kProjT = 64;           // subcarriers per CTA
+template <int T>
+__global__ void __launch_bounds__(kThreads) k_wide_proj(const SinrArgs A, const WidePlan pl) {
+  constexpr int QS = kThreads / T, QA = 32 / QS;
+  extern __shared__ __align__(16) float2 sm[];
+  const int tid = threadIdx.x;
+  const int i = blockIdx.y;
+  const int kap0 = blockIdx.x * T;
+  const int qb = blockIdx.z * 32;
+  const int J = A.J, p = A.p, K = A.K, P = A.P;
+  const int ch = i * J + i;
+  const int PC = pl.PC;
+  const int npc = (P + PC - 1) / PC;
+  const float2* Cch = A.C + (size_t)ch * P * p;
+  const bool c16 = (p % 2 == 0) && (((uintptr_t)A.C & 15u) == 0);
+  auto coef_at = [&](int kap, int q) -> float2 {
+    return A.coef_mode == 0 ? A.coef[((size_t)ch * K + kap) * P + q]
+                            : path_coef(__ldg(A.coef + (size_t)ch * P + q),
+                                        __ldg(A.turns + (size_t)ch * P + q), kap);
+  };
+  auto issue = [&](int ci) {
+    float2* buf = sm + (ci & 1) * pl.proj;
+    const int P0 = ci * PC, pc = min(PC, P - P0);
+    const float2* src = Cch + (size_t)P0 * p;
+    if (c16) {
+      for (int idx = 2 * tid; idx < pc * p; idx += 2 * kThreads)
+        cp_async16(buf + pl.off_Cc + idx, src + idx, true);
+    } else {
+      for (int idx = tid; idx < pc * p; idx += kThreads) cp_async8(buf + pl.off_Cc + idx, src + idx, true);
+    }
+    for (int idx = tid; idx < T * PC; idx += kThreads) {
+      const int t = idx / PC, pp = idx - t * PC;
+      buf[pl.off_cc + t * (PC + 1) + pp] = (pp < pc && kap0 + t < K) ? coef_at(kap0 + t, P0 + pp) : cz();
+    }
+  };
+  const int t = tid / QS, qs = tid % QS;
+  const int q0 = qb + qs * QA;
+  float2 acc[QA];
+#pragma unroll
+  for (int u = 0; u < QA; ++u) acc[u] = cz();
+  issue(0);
+  cp_async_commit();
+  for (int ci = 0; ci < npc; ++ci) {
+    if (ci + 1 < npc) issue(ci + 1);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    const float2* buf = sm + (ci & 1) * pl.proj;
+    const int pc = min(PC, P - ci * PC);
+    const float2* crow = buf + pl.off_cc + t * (PC + 1);
+    const float2* Cb = buf + pl.off_Cc + q0;
+    if (q0 < p) {
+      for (int pp = 0; pp < pc; ++pp) {
+        const float2 c = crow[pp];
+        const float2* Cr = Cb + pp * p;
+#pragma unroll
+        for (int u = 0; u < QA; ++u)
+          if (q0 + u < p) cmacc(acc[u], Cr[u], c);
+      }
+    }
+    __syncthreads();     // this buffer is refilled two chunks later
+  }
+  cp_async_wait<0>();
+  if (kap0 + t < K) {
+    float2* out = A.Wserv + ((size_t)i * K + kap0 + t) * p;
+#pragma unroll
+    for (int u = 0; u < QA; ++u)
+      if (q0 + u < p) out[q0 + u] = acc[u];
+  }
+}
+
 template <int MG, int LT, bool SERVE>
 cudaError_t launch_link_wide(const SinrArgs& A, cudaStream_t s) {
   if (!SERVE && A.J < 2) return cudaSuccess;
@@ -352,6 +435,23 @@ cudaError_t launch_link_wide(const SinrArgs& A, cudaStream_t s) {
             (((uintptr_t)A.V & 15u) == 0 || SERVE);
   const int tiles = (A.K + pl.T - 1) / pl.T;
   int nz = SERVE ? 1 : A.J - 1;
+  if (SERVE && A.Wserv != nullptr) {
+    // the projections once per (tile, serving link, 32 columns)
+    int PCp = 16;
+    WidePlan pp = wide_plan(8, 2, A.p, false, true, PCp);
+    while (PCp > 2 && (size_t)2 * pp.proj * sizeof(float2) > kSmemBudget) {
+      PCp /= 2;
+      pp = wide_plan(8, 2, A.p, false, true, PCp);
+    }
+    const size_t psm = (size_t)2 * pp.proj * sizeof(float2);
+    if (psm > kSmemBudget) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_wide_proj<kProjT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)psm);
+    if (e != cudaSuccess) return e;
+    dim3 pgrid((A.K + kProjT - 1) / kProjT, A.J, (A.p + 31) / 32);
+    k_wide_proj<kProjT><<<pgrid, kThreads, psm, s>>>(A, pp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   if (SERVE) {
     // the serving links alone are J CTAs per tile: split their column
     // chunks so that about two CTAs per SM run
