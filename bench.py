@@ -93,6 +93,16 @@ def precoder_flops(w) -> int:
     return int(8 * w.K * J * (P * p + m * n * p + m * m * n + m * n * L))
 
 
+def svd_launches(w, tensor_cores=False) -> int:
+    """Kernels one SVD-precoded SINR call launches (path-form coefficients):
+    phase steps, [serving pass (+ its projections for wide cores)],
+    precoders, [core operand, projection operand,] links, finalize, refine."""
+    fused = w.m * w.n * w.p <= 8192
+    wide = w.p > 32 or w.P * w.p > 8192
+    serve = 0 if fused else (2 if wide else 1)
+    return 1 + serve + 1 + (3 if tensor_cores else 1) + 2
+
+
 # ----------------------------------------------------------------- helpers
 def peaks():
     try:
@@ -268,7 +278,7 @@ def run_ours(args):
 
     # path phase steps, precoders (with the serving links), links, finalize;
     # tensor-core modes add the core rewrite (a memset and a kernel)
-    launches_per_step = 4 if prec_id == ts.TS_PREC_FP32 else 5
+    launches_per_step = svd_launches(w, prec_id != ts.TS_PREC_FP32)
     for _ in range(args.warmup):
         flush.zero_()
         step()
@@ -807,7 +817,7 @@ def run_batch(args):
                    "workspace_gib": round(ws.numel() / 2**30, 2)},
         "sequential_calls": {"ms_per_step": seq / seq_steps,
                              "what": "the same systems as one ts_sinr_svd call each on one stream"},
-        "gpu_launches": None, "clocks": clocks,
+        "gpu_launches": sum(svd_launches(w) for w in systems) * args.steps, "clocks": clocks,
         "cpu_baseline": {"value": done / wall, "unit": METRIC,
                          "cores": max(1, round((time.process_time() - c0) / wall)), "kind": "oracle",
                          "sample": f"FP64 NumPy oracle on the first 64 subcarriers of the first "
@@ -986,7 +996,7 @@ def run_multiuser(args):
                      "flops_per_launch": lf, "kernel_ms": round(lmean, 4),
                      "peak_basis": f"FP32 FFMA: {sms} SMs x 128 lanes x 2 flop x {sm_max:.0f} MHz",
                      "launch": "one UE group (J(J-1) interfering links x K subcarriers)"},
-        "gpu_launches": 6 * U * args.steps,
+        "gpu_launches": svd_launches(w) * U * args.steps,
         "clocks": clocks,
         "dense_comparator": {"value": units * dsteps / (dense_ms * 1e-3), "unit": METRIC,
                              "ms_per_step": dense_ms / dsteps,
