@@ -163,6 +163,15 @@ void ts_set_timing_events(void* start, void* stop);
  * negative threshold turns refinement off. */
 void ts_set_refinement(float cond_threshold);
 
+/* Inner iterations of the fit's eigensolves for factors whose mode dimension
+ * exceeds 72 (block subspace iteration with Cholesky-QR, then a
+ * Rayleigh-Ritz step): `iterations` per update warm-started from the current
+ * factor, three times as many for the initialisation.  Default 40; fewer
+ * trade accuracy of each block update of Algorithm 2 for time (the outer
+ * sweeps keep refining the factors).  Applies to the fit calls that follow
+ * on this host thread; iterations <= 0 restores the default. */
+void ts_set_fit_iterations(int iterations);
+
 /* Measured throughput of the current device in TFLOP/s: FP32 FMA (chains of
  * independent fmaf on every SM), TF32 tensor-core MMA (tcgen05, M = 128,
  * N = 256, K = 8, FP32 accumulation in TMEM, one CTA per SM) and FP64 FMA.

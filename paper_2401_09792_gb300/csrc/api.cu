@@ -19,6 +19,7 @@ thread_local cudaEvent_t g_ev_stop = nullptr;
 // condition number of R above which a unit's solves are refined with FP64
 // residuals (ts_set_refinement); infinity turns refinement off
 thread_local float g_refine_cond = 1e3f;
+thread_local int g_fit_iters = 40;
 // launch-shape choices of the batch planner (0: default heuristics)
 thread_local ts::Tuning g_tuning = {0, 0};
 thread_local bool g_timing_suspended = false;
@@ -163,7 +164,7 @@ AdjWorkspace carve_adjoint(const ts_dims* d, bool svd) {
 }
 
 ts::FitDims fit_dims(const ts_dims* d, int model = TS_MODEL_GROUPWISE) {
-  return ts::FitDims{d->J, d->M, d->N, d->P, d->m, d->n, d->p, model};
+  return ts::FitDims{d->J, d->M, d->N, d->P, d->m, d->n, d->p, model, g_fit_iters};
 }
 
 // Sizes the fit accepts: ranks up to 64 (eigensolver block limit).
@@ -256,6 +257,8 @@ void ts_set_timing_events(void* start, void* stop) {
   g_ev_start = static_cast<cudaEvent_t>(start);
   g_ev_stop = static_cast<cudaEvent_t>(stop);
 }
+
+void ts_set_fit_iterations(int iterations) { g_fit_iters = iterations > 0 ? iterations : 40; }
 
 void ts_set_refinement(float cond_threshold) {
   g_refine_cond = cond_threshold < 0.f ? INFINITY : cond_threshold;

@@ -593,7 +593,7 @@ cudaError_t launch_fit(const FitDims& f, const float2* X, int S, int init, float
   double2* B64 = A64 + (size_t)nG * M * m;
   double2* C64 = B64 + (size_t)nG * N * n;
   double* lsum = reinterpret_cast<double*>(take(J2 * sizeof(double)));
-  const int iters = 40;
+  const int iters = f.iters > 0 ? f.iters : 40;
   cudaError_t e = cudaSuccess;
 #define TS_FIT_CHECK()                            \
   do {                                            \

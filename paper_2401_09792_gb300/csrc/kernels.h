@@ -137,6 +137,7 @@ cudaError_t launch_project_precoder_adjoint(const float2* Pfull, const float2* d
 struct FitDims {
   int J, M, N, P, m, n, p;
   int model;   // TS_MODEL_GROUPWISE, _SHARED or _INDIVIDUAL: which links share A and B
+  int iters;   // block subspace iterations per warm eigensolve (three times as many cold)
 };
 // number of A (B) factors of a model
 __host__ __device__ inline int fit_groups(int J, int model) { return model == 1 ? 1 : model == 2 ? J * J : J; }

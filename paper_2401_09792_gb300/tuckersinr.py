@@ -93,6 +93,7 @@ _SIG = {
     "ts_dense_sinr_svd_multiuser": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.c_int,
                                                    ctypes.POINTER(ts_coef), _P, _P, _P, _P, _P,
                                                    ctypes.c_size_t, _P]),
+    "ts_set_fit_iterations": (None, [ctypes.c_int]),
     "ts_tucker_fit_model": (ctypes.c_int, [ctypes.POINTER(ts_dims), _P, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_int, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "ts_tucker_reconstruct": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.c_int, _P, _P, _P, _P, _P,
@@ -333,6 +334,10 @@ def ts_dense_sinr_svd_multiuser(d: Dims, U, coef: ts_coef, X, sigma2, sinr, flag
            lib.ts_dense_sinr_svd_multiuser(ctypes.byref(d.c()), U, ctypes.byref(coef), _ptr(X),
                                            _ptr(sigma2), _ptr(sinr), _ptr(flags), _ptr(ws),
                                            ws.numel(), _stream(stream)))
+
+
+def ts_set_fit_iterations(iterations: int):
+    load().ts_set_fit_iterations(int(iterations))
 
 
 def ts_tucker_fit_model(d: Dims, X, S, init, model, A, B, C, G, g_hist, ws, stream=None):
