@@ -323,9 +323,15 @@ int ts_autotune_load(const char* path);
  * C [U][J*J][P][p], coef [U][J*J][K][P] (dense) or alpha, tau [U][J*J][P]
  * (paths), sigma2 [U][J], sinr (out) [U][J][K][L], flags (out, may be NULL)
  * [U][J][K].  U = 1 is ts_sinr_svd.  FP32, sizes as ts_sinr_svd (wide cores
- * included).  ws: ts_workspace_bytes(d, TS_OP_SINR_SVD_MULTIUSER) bytes, the
- * same for every U (two single-UE workspaces: the first UEs' precoders stay
- * in the first while the other groups reuse the second). */
+ * included).  ws: at least ts_workspace_bytes(d, TS_OP_SINR_SVD_MULTIUSER)
+ * bytes = two single-UE workspaces (the first UEs' precoders stay in the
+ * first while the other groups, one after the other, reuse the second).
+ * With U single-UE workspaces (U / 2 times that size) the groups after the
+ * first run concurrently on up to four library-owned side streams, created
+ * on the first such call on a device and kept; `stream` waits for them
+ * before the call's work is complete.  Either way the results are the same
+ * bit for bit.  To capture such a call in a CUDA graph, make one uncaptured
+ * call first (stream creation) and capture in relaxed mode. */
 int ts_sinr_svd_multiuser(const ts_dims* d, int U, const ts_coef* coef, const ts_c64* G,
                           const ts_c64* C, const float* sigma2, float* sinr, uint8_t* flags,
                           void* ws, size_t ws_bytes, void* stream);

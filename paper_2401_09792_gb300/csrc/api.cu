@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
+#include <vector>
 
 #include "kernels.h"
 #include "tuckersinr.h"
@@ -23,6 +25,28 @@ thread_local int g_fit_iters = 40;
 // launch-shape choices of the batch planner (0: default heuristics)
 thread_local ts::Tuning g_tuning = {0, 0};
 thread_local bool g_timing_suspended = false;
+
+// Side streams on which the UE groups of a several-UE call run concurrently
+// (created on first use per device, kept for the life of the process).
+constexpr int kSideStreams = 4;
+std::mutex g_side_mu;
+std::vector<std::vector<cudaStream_t>> g_side;
+
+cudaError_t side_streams(cudaStream_t* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(g_side_mu);
+  if ((int)g_side.size() <= dev) g_side.resize(dev + 1);
+  std::vector<cudaStream_t>& v = g_side[dev];
+  while ((int)v.size() < kSideStreams) {
+    cudaStream_t st = nullptr;
+    if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    v.push_back(st);
+  }
+  for (int j = 0; j < kSideStreams; ++j) out[j] = v[j];
+  return cudaSuccess;
+}
 
 // Finalisation, then the FP64-residual refinement of the units it listed.
 // The list counter is zeroed by the link kernel that precedes the finalize
@@ -589,10 +613,12 @@ int svd_from_precoders_impl(const ts_dims* d, const ts_coef* coef, const ts_c64*
 
 // U UEs per cell (Section 4): UE group u holds UE u of every cell, its links
 // at G + u J^2 p m n (likewise C, the coefficients, sigma2, sinr, flags).
-// Every BS k interferes with its first UE's precoder: the u = 0 pass keeps
-// its precoders V_0 in the first half of the workspace; each later group
-// computes its own serving precoders, serving effective channels and flags
-// in the second half and reads V_0 for its interfering links.
+// Every BS k interferes with its first UE's precoder, so group 0's
+// precoders V_0 stay in the first single-UE workspace and every group reads
+// them for its interfering links.  With two single-UE workspaces the groups
+// run one after the other, the later ones reusing the second; with one per
+// group (U of them) groups 1.. run concurrently on side streams once V_0 is
+// ready, each in its own, and the caller's stream waits for all of them.
 int svd_multiuser_impl(const ts_dims* d, int U, const ts_coef* coef, const ts_c64* G,
                        const ts_c64* C, bool identity, const float* sigma2, float* sinr,
                        uint8_t* flags, void* ws, size_t ws_bytes, void* stream) {
@@ -601,10 +627,11 @@ int svd_multiuser_impl(const ts_dims* d, int U, const ts_coef* coef, const ts_c6
   if (st != TS_OK) return st;
   const Workspace w = carve(d, TS_OP_SINR_SVD);
   if (ws_bytes < 2 * w.total) return TS_ERR_WORKSPACE;
+  const bool concurrent = U > 1 && ws_bytes >= (size_t)U * w.total;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t nch = (size_t)d->J * d->J;
   char* base0 = static_cast<char*>(ws);
-  for (int u = 0; u < U; ++u) {
+  auto group_coef = [&](int u) {
     ts_coef cu = *coef;
     if (cu.mode == TS_COEF_DENSE) {
       cu.c = coef->c + (size_t)u * nch * d->K * d->P;
@@ -612,21 +639,64 @@ int svd_multiuser_impl(const ts_dims* d, int U, const ts_coef* coef, const ts_c6
       cu.alpha = coef->alpha + (size_t)u * nch * d->P;
       cu.tau_s = coef->tau_s + (size_t)u * nch * d->P;
     }
+    return cu;
+  };
+  // one UE group: its precoders (serving effective channels, flags) in
+  // `base`, its links against V_0, its finalisation
+  auto run_group = [&](int u, char* base, cudaStream_t gs) -> int {
+    const ts_coef cu = group_coef(u);
     const ts_c64* Gu = G + (size_t)u * nch * d->p * d->m * d->n;
     const ts_c64* Cu = identity ? nullptr : C + (size_t)u * nch * d->P * d->p;
-    char* base = base0 + (u == 0 ? 0 : w.total);
-    st = svd_precoders_impl(d, &cu, Gu, Cu, identity, base, w.total, stream);
-    if (st != TS_OK) return st;
+    int r = svd_precoders_impl(d, &cu, Gu, Cu, identity, base, w.total, gs);
+    if (r != TS_OK) return r;
     ts::SinrArgs a = base_args(d, &cu, Gu, Cu, sigma2 + (size_t)u * d->J,
                                sinr + (size_t)u * d->J * d->K * d->L,
                                flags == nullptr ? nullptr : flags + (size_t)u * d->J * d->K, base, w);
     a.identity_C = identity;
     a.V = reinterpret_cast<float2*>(base0 + w.V);
     a.pflag = reinterpret_cast<uint8_t*>(base + w.pflag);
-    const int e = cuda_status(links_then_finalize(a, true, s));
-    if (e != TS_OK) return e;
+    return cuda_status(links_then_finalize(a, true, gs));
+  };
+  if (!concurrent) {
+    for (int u = 0; u < U; ++u) {
+      const int r = run_group(u, base0 + (u == 0 ? 0 : w.total), s);
+      if (r != TS_OK) return r;
+    }
+    return TS_OK;
   }
-  return TS_OK;
+  cudaStream_t side[kSideStreams];
+  cudaError_t e = side_streams(side);
+  if (e != cudaSuccess) return cuda_status(e);
+  const int nside = U - 1 < kSideStreams ? U - 1 : kSideStreams;
+  // group 0: precoders, then V_0 is published to the side streams
+  const ts_coef c0 = group_coef(0);
+  st = svd_precoders_impl(d, &c0, G, C, identity, base0, w.total, stream);
+  if (st != TS_OK) return st;
+  cudaEvent_t ev[kSideStreams + 1] = {};
+  for (int j = 0; j <= nside && e == cudaSuccess; ++j)
+    e = cudaEventCreateWithFlags(&ev[j], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
+  for (int j = 0; j < nside && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(side[j], ev[0], 0);
+  if (e == cudaSuccess) {
+    ts::SinrArgs a = base_args(d, &c0, G, C, sigma2, sinr, flags, base0, w);
+    a.identity_C = identity;
+    a.V = reinterpret_cast<float2*>(base0 + w.V);
+    a.pflag = reinterpret_cast<uint8_t*>(base0 + w.pflag);
+    e = links_then_finalize(a, true, s);
+  }
+  for (int u = 1; u < U && e == cudaSuccess; ++u) {
+    st = run_group(u, base0 + (size_t)u * w.total, side[(u - 1) % nside]);
+    if (st != TS_OK) break;
+  }
+  // the caller's stream waits for every side stream
+  for (int j = 0; j < nside && e == cudaSuccess && st == TS_OK; ++j) {
+    e = cudaEventRecord(ev[1 + j], side[j]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[1 + j], 0);
+  }
+  for (int j = 0; j <= nside; ++j)
+    if (ev[j] != nullptr) cudaEventDestroy(ev[j]);       // released once complete
+  if (e != cudaSuccess) return cuda_status(e);
+  return st;
 }
 
 }  // namespace
