@@ -422,9 +422,14 @@ __global__ void __launch_bounds__(kThreads) k_wide_proj(const SinrArgs A, const 
 template <int MG, int LT, bool SERVE>
 cudaError_t launch_link_wide(const SinrArgs& A, cudaStream_t s) {
   if (!SERVE && A.J < 2) return cudaSuccess;
-  // projection chunk: 16 paths, fewer while the CTA would not fit its budget
+  // projection chunk: the largest of 16, 8, 4, 2 paths with which two CTAs
+  // share an SM (113 KB each), else the largest within the CTA budget
   int PC = 16;
   WidePlan pl = wide_plan(MG, LT, A.p, A.identity_C, SERVE, PC);
+  for (int pc = 16; pc >= 2; pc /= 2) {
+    const WidePlan t = wide_plan(MG, LT, A.p, A.identity_C, SERVE, pc);
+    if ((size_t)t.total * sizeof(float2) <= 113 * 1024) { PC = pc; pl = t; break; }
+  }
   while (PC > 2 && (size_t)pl.total * sizeof(float2) > kSmemBudget) {
     PC /= 2;
     pl = wide_plan(MG, LT, A.p, A.identity_C, SERVE, PC);
