@@ -22,16 +22,19 @@ namespace detail {
 constexpr int kWideQC = 16;
 
 struct WidePlan {
-  int T, nq, SG, SV, WS, PC, wide, cps;
+  int T, QR, SG, SV, WS, PC, wide, cps;
   int off_ws, off_stage, stage, off_Gs, off_Vs, off_Wc, proj, off_Cc, off_cc, total;
 };
 
+// QR: the columns of w = c* C held at once (p, or a multiple of 32 below p:
+// the link pass then runs in p / QR passes over the core, each accumulating
+// E += H~[q-range] V~, which is linear in the core's mode-3 slabs).
 __host__ __device__ inline WidePlan wide_plan(int MG, int LT, int p, bool identity, bool serve,
-                                              int PC) {
+                                              int PC, int QR) {
   constexpr int NC = 4;
   WidePlan pl;
   pl.T = 2 * kThreads / (MG / 2);
-  pl.nq = (p + kWideQC - 1) / kWideQC;
+  pl.QR = QR;
   pl.SG = NC + 2;
   pl.SV = NC * LT + 2;
   pl.WS = kWideQC + 1;
@@ -40,7 +43,7 @@ __host__ __device__ inline WidePlan wide_plan(int MG, int LT, int p, bool identi
   pl.cps = 1 << 30;
   int o = 0;
   pl.off_ws = o;
-  if (!identity) o += pl.T * (p + 1);
+  if (!identity) o += pl.T * (QR + 1);
   o = (o + 1) & ~1;
   pl.off_stage = o;
   int so = 0;
@@ -49,10 +52,10 @@ __host__ __device__ inline WidePlan wide_plan(int MG, int LT, int p, bool identi
   pl.off_Wc = so; if (identity) so += pl.T * pl.WS;
   so = (so + 1) & ~1;
   pl.stage = so;
-  // projection buffers (C chunk [PC][p], coefficient chunk [T][PC + 1]),
+  // projection buffers (C chunk [PC][QR], coefficient chunk [T][PC + 1]),
   // sharing the region of the stage buffers (used one after the other)
   pl.off_Cc = 0;
-  pl.off_cc = (PC * p + 1) & ~1;
+  pl.off_cc = (PC * QR + 1) & ~1;
   pl.proj = identity ? 0 : ((pl.off_cc + pl.T * (PC + 1) + 1) & ~1);
   const int es = (kThreads / (MG / 2)) * (2 * MG * LT + 2);
   int region = 2 * so > es ? 2 * so : es;
@@ -78,17 +81,16 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link_wide(const SinrArgs A, c
   const int J = A.J, m = A.m, n = A.n, p = A.p, L = A.L, K = A.K, P = A.P;
   const int k = SERVE ? i : (z < i ? z : z + 1);
   const int ch = i * J + k;
-  const int nq = pl.nq;
+  const int QR = pl.QR;
   const int nchunk = (n + NC - 1) / NC;
   const int cbeg = SERVE ? z * pl.cps : 0;
   const int cend = SERVE ? min(nchunk, cbeg + pl.cps) : nchunk;
-  const int nstage = (cend - cbeg) * nq;
   const bool ident = A.identity_C;
   float2* ws = sm + pl.off_ws;
   float2* stage0 = sm + pl.off_stage;
   const bool wide = pl.wide != 0;
   if (!SERVE && A.rcount != nullptr && tid == 0 && blockIdx.x == 0 && i == 0 && z == 0) *A.rcount = 0;
-  if (nstage <= 0) return;                  // an empty column slice (uniform over the CTA)
+  if (cend <= cbeg) return;                 // an empty column slice (uniform over the CTA)
 
   // c_q(kappa) of this link (dense tile or path form), from global memory
   auto coef_at = [&](int kap, int q) -> float2 {
@@ -97,11 +99,13 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link_wide(const SinrArgs A, c
                                         __ldg(A.turns + (size_t)ch * P + q), kap);
   };
 
+  // the current pass: columns [qlo, qlo + qn) of w, nq slabs per column chunk
+  int qlo = 0, qn = 0, nq = 1;
   auto issue_stage = [&](int st) {
     float2* buf = stage0 + (st & 1) * pl.stage;
     const int cidx = cbeg + st / nq, qi = st % nq;
-    const int c0 = cidx * NC, q0 = qi * QC;
-    const int qc = min(QC, p - q0);
+    const int c0 = cidx * NC, q0 = qlo + qi * QC;
+    const int qc = min(QC, qlo + qn - q0);
     const float2* Gch = A.G + (size_t)ch * p * m * n;
     if (wide) {
       constexpr int GU = MG * NC / 2;                 // 16-byte units per slab
@@ -147,80 +151,6 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link_wide(const SinrArgs A, c
     }
   };
 
-  if (SERVE && A.Wserv != nullptr) {
-    // the serving links' projections come from k_wide_proj
-    const float2* src = A.Wserv + ((size_t)i * K + kap0) * p;
-    for (int idx = tid; idx < T * p; idx += kThreads) {
-      const int t = idx / p, q = idx - t * p;
-      ws[t * (p + 1) + q] = kap0 + t < K ? src[idx] : cz();
-    }
-  } else if (!ident) {
-    // projection w[t][q] = sum_P C[P][q] conj(c_P(kappa_t)) (eq. 15), chunks
-    // of PC paths: C rows by asynchronous copies, coefficients evaluated
-    // into shared memory, one chunk ahead of the accumulation.  Thread
-    // (t, qs) owns columns qb + qs QA + u of each 32-column block.
-    const int PC = pl.PC;
-    const int npc = (P + PC - 1) / PC;
-    const float2* Cch = A.C + (size_t)ch * P * p;
-    const bool c16 = (p % 2 == 0) && (((uintptr_t)A.C & 15u) == 0);
-    auto issue_proj = [&](int ci) {
-      float2* buf = stage0 + (ci & 1) * pl.proj;
-      const int P0 = ci * PC, pc = min(PC, P - P0);
-      const float2* src = Cch + (size_t)P0 * p;
-      if (c16) {
-        for (int idx = 2 * tid; idx < pc * p; idx += 2 * kThreads)
-          cp_async16(buf + pl.off_Cc + idx, src + idx, true);
-      } else {
-        for (int idx = tid; idx < pc * p; idx += kThreads) cp_async8(buf + pl.off_Cc + idx, src + idx, true);
-      }
-      for (int idx = tid; idx < T * PC; idx += kThreads) {
-        const int t = idx / PC, pp = idx - t * PC;
-        buf[pl.off_cc + t * (PC + 1) + pp] =
-            (pp < pc && kap0 + t < K) ? coef_at(kap0 + t, P0 + pp) : cz();
-      }
-    };
-    const int t = tid / QS, qs = tid % QS;
-    issue_proj(0);
-    cp_async_commit();
-    for (int ci = 0; ci < npc; ++ci) {
-      if (ci + 1 < npc) issue_proj(ci + 1);
-      cp_async_commit();
-      cp_async_wait<1>();
-      __syncthreads();
-      const float2* buf = stage0 + (ci & 1) * pl.proj;
-      const int pc = min(PC, P - ci * PC);
-      const float2* crow = buf + pl.off_cc + t * (PC + 1);
-      for (int qb = 0; qb < p; qb += 32) {
-        const int q0 = qb + qs * QA;
-        if (q0 >= p) continue;
-        float2 acc[QA];
-#pragma unroll
-        for (int u = 0; u < QA; ++u) acc[u] = cz();
-        const float2* Cb = buf + pl.off_Cc + q0;
-        for (int pp = 0; pp < pc; ++pp) {
-          const float2 c = crow[pp];
-          const float2* Cr = Cb + pp * p;
-#pragma unroll
-          for (int u = 0; u < QA; ++u)
-            if (q0 + u < p) cmacc(acc[u], Cr[u], c);
-        }
-        float2* wout = ws + t * (p + 1) + q0;
-#pragma unroll
-        for (int u = 0; u < QA; ++u)
-          if (q0 + u < p) wout[u] = ci == 0 ? acc[u] : cadd(wout[u], acc[u]);
-      }
-      __syncthreads();     // this buffer is refilled two chunks later
-    }
-    cp_async_wait<0>();
-  }
-
-  issue_stage(0);
-  cp_async_commit();
-  if (nstage > 1) issue_stage(1);
-  cp_async_commit();
-  cp_async_wait<1>();
-  __syncthreads();
-
   float2 E[2][2][LT];   // [subcarrier of the pair][row j, j + GL][stream]
 #pragma unroll
   for (int x = 0; x < 2; ++x)
@@ -229,89 +159,176 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link_wide(const SinrArgs A, c
 #pragma unroll
       for (int l = 0; l < LT; ++l) E[x][r][l] = cz();
   float2 h[2][2][NC];
-  for (int st = 0; st < nstage; ++st) {
-    if (st > 0) {
-      if (st + 1 < nstage) issue_stage(st + 1);
-      cp_async_commit();
-      cp_async_wait<1>();
-      __syncthreads();
-    }
-    const float2* buf = stage0 + (st & 1) * pl.stage;
-    const int cidx = cbeg + st / nq, qi = st % nq;
-    const int q0 = qi * QC, qc = min(QC, p - q0);
-    if (qi == 0) {
-#pragma unroll
-      for (int x = 0; x < 2; ++x)
-#pragma unroll
-        for (int r = 0; r < 2; ++r)
-#pragma unroll
-          for (int cc = 0; cc < NC; ++cc) h[x][r][cc] = cz();
-    }
-    const float2* w0 = ident ? buf + pl.off_Wc + (2 * gp) * pl.WS : ws + (2 * gp) * (p + 1) + q0;
-    const float2* w1 = w0 + (ident ? pl.WS : p + 1);
-    const float2* g0 = buf + pl.off_Gs + j * pl.SG;
-    const float2* g1 = g0 + GL * pl.SG;
-#pragma unroll 4
-    for (int q = 0; q < qc; ++q) {
-      const float2 wa = w0[q], wb = w1[q];
-      const float4* ga = reinterpret_cast<const float4*>(g0 + q * MG * pl.SG);
-      const float4* gb = reinterpret_cast<const float4*>(g1 + q * MG * pl.SG);
-#pragma unroll
-      for (int c2 = 0; c2 < NC / 2; ++c2) {
-        const float4 u = ga[c2], v = gb[c2];
-        const float2 u0 = make_float2(u.x, u.y), u1 = make_float2(u.z, u.w);
-        const float2 v0 = make_float2(v.x, v.y), v1 = make_float2(v.z, v.w);
-        cmac(h[0][0][2 * c2], wa, u0);
-        cmac(h[0][0][2 * c2 + 1], wa, u1);
-        cmac(h[1][0][2 * c2], wb, u0);
-        cmac(h[1][0][2 * c2 + 1], wb, u1);
-        cmac(h[0][1][2 * c2], wa, v0);
-        cmac(h[0][1][2 * c2 + 1], wa, v1);
-        cmac(h[1][1][2 * c2], wb, v0);
-        cmac(h[1][1][2 * c2 + 1], wb, v1);
+
+  for (qlo = 0; qlo < p; qlo += QR) {
+    qn = min(QR, p - qlo);
+    nq = (qn + QC - 1) / QC;
+    const int nstage = (cend - cbeg) * nq;
+    if (SERVE && A.Wserv != nullptr) {
+      // the serving links' projections come from k_wide_proj (one pass)
+      const float2* src = A.Wserv + ((size_t)i * K + kap0) * p;
+      for (int idx = tid; idx < T * p; idx += kThreads) {
+        const int t = idx / p, q = idx - t * p;
+        ws[t * (QR + 1) + q] = kap0 + t < K ? src[idx] : cz();
       }
-    }
-    if (qi == nq - 1) {
-      const int c0 = cidx * NC;
-      if (SERVE) {
-#pragma unroll
-        for (int x = 0; x < 2; ++x) {
-          const int kap = kap0 + 2 * gp + x;
-#pragma unroll
-          for (int r = 0; r < 2; ++r) {
-            const int a = j + r * GL;
-            if (kap >= K || a >= m) continue;
-            float2* Hrow = A.Hserv + (((size_t)i * K + kap) * m + a) * n;
-#pragma unroll
-            for (int cc = 0; cc < NC; ++cc)
-              if (c0 + cc < n) Hrow[c0 + cc] = h[x][r][cc];
+    } else if (!ident) {
+      // projection w[t][q] = sum_P C[P][q] conj(c_P(kappa_t)) (eq. 15) for
+      // the pass's columns, in chunks of PC paths: C rows by asynchronous
+      // copies, coefficients evaluated into shared memory, one chunk ahead
+      // of the accumulation.  Thread (t, qs) owns columns qb + qs QA + u of
+      // each 32-column block.
+      const int PC = pl.PC;
+      const int npc = (P + PC - 1) / PC;
+      const float2* Cch = A.C + (size_t)ch * P * p + qlo;
+      const bool c16 = (p % 2 == 0) && (((uintptr_t)A.C & 15u) == 0);
+      auto issue_proj = [&](int ci) {
+        float2* buf = stage0 + (ci & 1) * pl.proj;
+        const int P0 = ci * PC, pc = min(PC, P - P0);
+        const float2* src = Cch + (size_t)P0 * p;
+        if (c16) {
+          for (int idx = 2 * tid; idx < pc * qn; idx += 2 * kThreads) {
+            const int row = idx / qn, col = idx - row * qn;
+            cp_async16(buf + pl.off_Cc + row * QR + col, src + (size_t)row * p + col, true);
+          }
+        } else {
+          for (int idx = tid; idx < pc * qn; idx += kThreads) {
+            const int row = idx / qn, col = idx - row * qn;
+            cp_async8(buf + pl.off_Cc + row * QR + col, src + (size_t)row * p + col, true);
           }
         }
-      } else {
-        const float2* va = buf + pl.off_Vs + (2 * gp) * pl.SV;
-        const float2* vb = va + pl.SV;
+        for (int idx = tid; idx < T * PC; idx += kThreads) {
+          const int t = idx / PC, pp = idx - t * PC;
+          buf[pl.off_cc + t * (PC + 1) + pp] =
+              (pp < pc && kap0 + t < K) ? coef_at(kap0 + t, P0 + pp) : cz();
+        }
+      };
+      const int t = tid / QS, qs = tid % QS;
+      issue_proj(0);
+      cp_async_commit();
+      for (int ci = 0; ci < npc; ++ci) {
+        if (ci + 1 < npc) issue_proj(ci + 1);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        const float2* buf = stage0 + (ci & 1) * pl.proj;
+        const int pc = min(PC, P - ci * PC);
+        const float2* crow = buf + pl.off_cc + t * (PC + 1);
+        for (int qb = 0; qb < qn; qb += 32) {
+          const int q0 = qb + qs * QA;
+          if (q0 >= qn) continue;
+          float2 acc[QA];
 #pragma unroll
-        for (int cc = 0; cc < NC; ++cc) {
+          for (int u = 0; u < QA; ++u) acc[u] = cz();
+          const float2* Cb = buf + pl.off_Cc + q0;
+          for (int pp = 0; pp < pc; ++pp) {
+            const float2 c = crow[pp];
+            const float2* Cr = Cb + pp * QR;
 #pragma unroll
-          for (int l2 = 0; l2 < LT / 2; ++l2) {
-            const float4 x = reinterpret_cast<const float4*>(va + cc * LT)[l2];
-            const float4 y = reinterpret_cast<const float4*>(vb + cc * LT)[l2];
-            const float2 x0 = make_float2(x.x, x.y), x1 = make_float2(x.z, x.w);
-            const float2 y0 = make_float2(y.x, y.y), y1 = make_float2(y.z, y.w);
+            for (int u = 0; u < QA; ++u)
+              if (q0 + u < qn) cmacc(acc[u], Cr[u], c);
+          }
+          float2* wout = ws + t * (QR + 1) + q0;
+#pragma unroll
+          for (int u = 0; u < QA; ++u)
+            if (q0 + u < qn) wout[u] = ci == 0 ? acc[u] : cadd(wout[u], acc[u]);
+        }
+        __syncthreads();     // this buffer is refilled two chunks later
+      }
+      cp_async_wait<0>();
+    }
+
+    issue_stage(0);
+    cp_async_commit();
+    if (nstage > 1) issue_stage(1);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+
+    for (int st = 0; st < nstage; ++st) {
+      if (st > 0) {
+        if (st + 1 < nstage) issue_stage(st + 1);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+      }
+      const float2* buf = stage0 + (st & 1) * pl.stage;
+      const int cidx = cbeg + st / nq, qi = st % nq;
+      const int q0 = qlo + qi * QC, qc = min(QC, qlo + qn - q0);
+      if (qi == 0) {
+#pragma unroll
+        for (int x = 0; x < 2; ++x)
+#pragma unroll
+          for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int cc = 0; cc < NC; ++cc) h[x][r][cc] = cz();
+      }
+      const float2* w0 = ident ? buf + pl.off_Wc + (2 * gp) * pl.WS
+                               : ws + (2 * gp) * (QR + 1) + (q0 - qlo);
+      const float2* w1 = w0 + (ident ? pl.WS : QR + 1);
+      const float2* g0 = buf + pl.off_Gs + j * pl.SG;
+      const float2* g1 = g0 + GL * pl.SG;
+#pragma unroll 4
+      for (int q = 0; q < qc; ++q) {
+        const float2 wa = w0[q], wb = w1[q];
+        const float4* ga = reinterpret_cast<const float4*>(g0 + q * MG * pl.SG);
+        const float4* gb = reinterpret_cast<const float4*>(g1 + q * MG * pl.SG);
+#pragma unroll
+        for (int c2 = 0; c2 < NC / 2; ++c2) {
+          const float4 u = ga[c2], v = gb[c2];
+          const float2 u0 = make_float2(u.x, u.y), u1 = make_float2(u.z, u.w);
+          const float2 v0 = make_float2(v.x, v.y), v1 = make_float2(v.z, v.w);
+          cmac(h[0][0][2 * c2], wa, u0);
+          cmac(h[0][0][2 * c2 + 1], wa, u1);
+          cmac(h[1][0][2 * c2], wb, u0);
+          cmac(h[1][0][2 * c2 + 1], wb, u1);
+          cmac(h[0][1][2 * c2], wa, v0);
+          cmac(h[0][1][2 * c2 + 1], wa, v1);
+          cmac(h[1][1][2 * c2], wb, v0);
+          cmac(h[1][1][2 * c2 + 1], wb, v1);
+        }
+      }
+      if (qi == nq - 1) {
+        const int c0 = cidx * NC;
+        if (SERVE) {
+#pragma unroll
+          for (int x = 0; x < 2; ++x) {
+            const int kap = kap0 + 2 * gp + x;
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
-              cmac(E[0][r][2 * l2], h[0][r][cc], x0);
-              cmac(E[0][r][2 * l2 + 1], h[0][r][cc], x1);
-              cmac(E[1][r][2 * l2], h[1][r][cc], y0);
-              cmac(E[1][r][2 * l2 + 1], h[1][r][cc], y1);
+              const int a = j + r * GL;
+              if (kap >= K || a >= m) continue;
+              float2* Hrow = A.Hserv + (((size_t)i * K + kap) * m + a) * n;
+#pragma unroll
+              for (int cc = 0; cc < NC; ++cc)
+                if (c0 + cc < n) Hrow[c0 + cc] = h[x][r][cc];
+            }
+          }
+        } else {
+          const float2* va = buf + pl.off_Vs + (2 * gp) * pl.SV;
+          const float2* vb = va + pl.SV;
+#pragma unroll
+          for (int cc = 0; cc < NC; ++cc) {
+#pragma unroll
+            for (int l2 = 0; l2 < LT / 2; ++l2) {
+              const float4 x = reinterpret_cast<const float4*>(va + cc * LT)[l2];
+              const float4 y = reinterpret_cast<const float4*>(vb + cc * LT)[l2];
+              const float2 x0 = make_float2(x.x, x.y), x1 = make_float2(x.z, x.w);
+              const float2 y0 = make_float2(y.x, y.y), y1 = make_float2(y.z, y.w);
+#pragma unroll
+              for (int r = 0; r < 2; ++r) {
+                cmac(E[0][r][2 * l2], h[0][r][cc], x0);
+                cmac(E[0][r][2 * l2 + 1], h[0][r][cc], x1);
+                cmac(E[1][r][2 * l2], h[1][r][cc], y0);
+                cmac(E[1][r][2 * l2 + 1], h[1][r][cc], y1);
+              }
             }
           }
         }
       }
+      __syncthreads();   // this buffer is refilled two stages later
     }
-    __syncthreads();   // this buffer is refilled two stages later
+    cp_async_wait<0>();
   }
-  cp_async_wait<0>();
   if (SERVE) return;
 
   // partial covariance rows (E E*)[a][b], b < m (eq. 25), for both subcarriers
@@ -422,17 +439,29 @@ __global__ void __launch_bounds__(kThreads) k_wide_proj(const SinrArgs A, const 
 template <int MG, int LT, bool SERVE>
 cudaError_t launch_link_wide(const SinrArgs& A, cudaStream_t s) {
   if (!SERVE && A.J < 2) return cudaSuccess;
-  // projection chunk: the largest of 16, 8, 4, 2 paths with which two CTAs
-  // share an SM (113 KB each), else the largest within the CTA budget
-  int PC = 16;
-  WidePlan pl = wide_plan(MG, LT, A.p, A.identity_C, SERVE, PC);
-  for (int pc = 16; pc >= 2; pc /= 2) {
-    const WidePlan t = wide_plan(MG, LT, A.p, A.identity_C, SERVE, pc);
-    if ((size_t)t.total * sizeof(float2) <= 113 * 1024) { PC = pc; pl = t; break; }
-  }
-  while (PC > 2 && (size_t)pl.total * sizeof(float2) > kSmemBudget) {
-    PC /= 2;
-    pl = wide_plan(MG, LT, A.p, A.identity_C, SERVE, PC);
+  // shared memory decides how many CTAs share an SM (3 within 75 KB, 2
+  // within 113 KB): take the plan with the most CTAs per SM, then the fewest
+  // passes over the core (columns of w held at once: p, or 128, 64, 32 for
+  // the interfering links), then the largest projection chunk (16 .. 2 paths)
+  const bool passes = !SERVE && !A.identity_C;
+  WidePlan pl = wide_plan(MG, LT, A.p, A.identity_C, SERVE, 2, A.p);
+  int best_ctas = -1, best_passes = 1 << 30, best_pc = 0;
+  for (int qr : {A.p, 128, 64, 32}) {
+    if (qr != A.p && (!passes || qr >= A.p)) continue;
+    const int npass = (A.p + qr - 1) / qr;
+    for (int pc = 16; pc >= 2; pc /= 2) {
+      const WidePlan t = wide_plan(MG, LT, A.p, A.identity_C, SERVE, pc, qr);
+      const size_t bytes = (size_t)t.total * sizeof(float2);
+      if (bytes > kSmemBudget) continue;
+      const int ctas = bytes <= 75 * 1024 ? 3 : bytes <= 113 * 1024 ? 2 : 1;
+      if (ctas > best_ctas || (ctas == best_ctas && (npass < best_passes ||
+                                                     (npass == best_passes && pc > best_pc)))) {
+        best_ctas = ctas;
+        best_passes = npass;
+        best_pc = pc;
+        pl = t;
+      }
+    }
   }
   const size_t smem = (size_t)pl.total * sizeof(float2);
   if (smem > kSmemBudget) return cudaErrorInvalidValue;
@@ -443,10 +472,10 @@ cudaError_t launch_link_wide(const SinrArgs& A, cudaStream_t s) {
   if (SERVE && A.Wserv != nullptr) {
     // the projections once per (tile, serving link, 32 columns)
     int PCp = 16;
-    WidePlan pp = wide_plan(8, 2, A.p, false, true, PCp);
+    WidePlan pp = wide_plan(8, 2, A.p, false, true, PCp, A.p);
     while (PCp > 2 && (size_t)2 * pp.proj * sizeof(float2) > kSmemBudget) {
       PCp /= 2;
-      pp = wide_plan(8, 2, A.p, false, true, PCp);
+      pp = wide_plan(8, 2, A.p, false, true, PCp, A.p);
     }
     const size_t psm = (size_t)2 * pp.proj * sizeof(float2);
     if (psm > kSmemBudget) return cudaErrorInvalidValue;
