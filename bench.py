@@ -390,7 +390,7 @@ def _extras(args, ts, torch, dist, world, dev, w, tk, host, dv, coef, d, ws, sin
     # subcarrier (eq. 9), precoders and solves at (M, N); same kernels, C = I
     if ts.ts_workspace_bytes(d, ts.TS_OP_DENSE_SVD) == 0:
         # the dense kernels stage one M x N channel per subcarrier: M <= 16,
-        # N <= 512, P <= 32
+        # N <= 512, P <= 1024
         return e2e_value, h2d, d2h, mm_ms, None, None, None
     X = synth.channel_submatrices(w)
     Xd = torch.from_numpy(np.ascontiguousarray(np.transpose(X, (0, 1, 4, 2, 3))
@@ -659,7 +659,7 @@ def _report(args, ts, torch, world, dev, w, tk, alpha, tau, s2, d, coef, dv, ws,
                for k, v in prec.items() if k != "adjoint"},
             **({"svd_adjoint": prec["adjoint"]} if "adjoint" in prec else {})},
         "method": getattr(_method_error, "result", None),
-        "dense_comparator": {"unavailable": "dense kernels need M <= 16, N <= 512, P <= 32"}
+        "dense_comparator": {"unavailable": "dense kernels need M <= 16, N <= 512, P <= 1024"}
         if dense_ms is None else {
             "value": dense_value, "unit": METRIC, "ms_per_step": dense_ms / dense_steps,
             "what": "same SVD-precoded SINR from the uncompressed channels "
