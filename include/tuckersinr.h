@@ -172,6 +172,15 @@ void ts_set_refinement(float cond_threshold);
  * on this host thread; iterations <= 0 restores the default. */
 void ts_set_fit_iterations(int iterations);
 
+/* Self-test of the bounded mbarrier wait that the tensor-core kernel uses
+ * for its operand copies and MMA completions: one thread waits on an
+ * mbarrier phase that nothing completes (arrive = 0) or that it completes
+ * first (arrive != 0), for at most `limit` tries (1 .. 2^24), and writes
+ * *out (device int) = 1 if the wait gave up, 0 if the phase completed.
+ * The context stays usable after a give-up; the SINR kernels turn one into
+ * TS_FLAG_TIMEOUT and NaN for the units concerned. */
+int ts_selftest_bounded_wait(long long limit, int arrive, int* out, void* stream);
+
 /* Measured throughput of the current device in TFLOP/s: FP32 FMA (chains of
  * independent fmaf on every SM), TF32 tensor-core MMA (tcgen05, M = 128,
  * N = 256, K = 8, FP32 accumulation in TMEM, one CTA per SM) and FP64 FMA.

@@ -107,8 +107,8 @@ __device__ __forceinline__ float to_tf32(float x) {
 }
 
 // bounded wait on an mbarrier phase; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (long it = 0; it < kSpinLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait_limit(uint32_t bar, uint32_t parity, long limit) {
+  for (long it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                  "selp.u32 %0, 1, 0, p;\n}\n"
@@ -116,6 +116,27 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     if (done) return true;
   }
   return false;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  return mbar_wait_limit(bar, parity, kSpinLimit);
+}
+
+// Self-test of the bounded wait the tensor-core kernel relies on: one
+// thread waits on phase 0 of an mbarrier of count 1 that nothing arrives at
+// (arrive == 0) or that it arrives at first (arrive != 0), for at most
+// `limit` tries; out[0] = 1 if the wait gave up, 0 if the phase completed.
+__global__ void k_wait_selftest(long limit, int arrive, int* out) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  const uint32_t b = smem_u32(&bar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b));
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  if (arrive) {
+    uint64_t state;
+    asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(b) : "memory");
+    (void)state;
+  }
+  out[0] = mbar_wait_limit(b, 0, limit) ? 0 : 1;
 }
 
 // ------------------------------------------------------------ core operand
@@ -634,3 +655,12 @@ cudaError_t launch_sinr_links_tc(const SinrArgs& a, int prec, const void* prep, 
 }
 
 }  // namespace ts
+
+extern "C" int ts_selftest_bounded_wait(long long limit, int arrive, int* out, void* stream) {
+  if (out == nullptr) return TS_ERR_NULL;
+  if (((uintptr_t)out & 3u) != 0) return TS_ERR_ALIGN;
+  if (limit < 1 || limit > (1LL << 24)) return TS_ERR_DIMS;
+  ts::detail::k_wait_selftest<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>((long)limit, arrive, out);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? TS_OK : ts::record_cuda_error(e);
+}

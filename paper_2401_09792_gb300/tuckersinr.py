@@ -19,6 +19,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libtuckersinr.so")
 
 TS_COEF_DENSE, TS_COEF_PATHS = 0, 1
+TS_OK, TS_ERR_DIMS, TS_ERR_NULL, TS_ERR_ALIGN, TS_ERR_WORKSPACE = 0, 1, 2, 3, 4
 TS_OP_SINR_SVD, TS_OP_SINR_MMSE, TS_OP_DENSE_SVD, TS_OP_DENSE_MMSE = 0, 1, 2, 3
 TS_OP_SINR_SVD_ADJOINT, TS_OP_SINR_MMSE_ADJOINT, TS_OP_TUCKER_FIT = 4, 5, 6
 TS_OP_SINR_SVD_TF32, TS_OP_SINR_SVD_BF16X2 = 7, 8
@@ -94,6 +95,7 @@ _SIG = {
                                                    ctypes.POINTER(ts_coef), _P, _P, _P, _P, _P,
                                                    ctypes.c_size_t, _P]),
     "ts_set_fit_iterations": (None, [ctypes.c_int]),
+    "ts_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_int, _P, _P]),
     "ts_tucker_fit_model": (ctypes.c_int, [ctypes.POINTER(ts_dims), _P, ctypes.c_int, ctypes.c_int,
                                            ctypes.c_int, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "ts_tucker_reconstruct": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.c_int, _P, _P, _P, _P, _P,
@@ -334,6 +336,11 @@ def ts_dense_sinr_svd_multiuser(d: Dims, U, coef: ts_coef, X, sigma2, sinr, flag
            lib.ts_dense_sinr_svd_multiuser(ctypes.byref(d.c()), U, ctypes.byref(coef), _ptr(X),
                                            _ptr(sigma2), _ptr(sinr), _ptr(flags), _ptr(ws),
                                            ws.numel(), _stream(stream)))
+
+
+def ts_selftest_bounded_wait(limit: int, arrive: bool, out, stream=None):
+    _check("ts_selftest_bounded_wait",
+           load().ts_selftest_bounded_wait(int(limit), 1 if arrive else 0, _ptr(out), _stream(stream)))
 
 
 def ts_set_fit_iterations(iterations: int):
