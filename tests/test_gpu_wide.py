@@ -47,6 +47,10 @@ CASES = {
     "p20_P512": _wl("wide p20 P512", P=512, p=20, n=16, K=64),      # p <= 32 but P p > 8192
     "m3": _wl("wide m3", M=4, m=3, L=2, p=40, n=20),                 # rows masked in the group
     "m12": _wl("wide m12", M=16, m=12, L=8, p=36, n=24, K=33),      # 16-lane groups
+    "odd": _wl("wide odd", m=7, n=23, L=3, p=40, K=45),             # 8-byte copies (odd n, L)
+    "one_cell_one_subcarrier": _wl("wide J1 K1", J=1, K=1),         # no interferers, one subcarrier
+    "m1": _wl("wide m1", M=2, m=1, L=1, n=5, p=40, K=20),           # rank-one rows, one stream
+    "p256": _wl("wide p256", M=4, m=4, L=2, n=8, P=300, p=256, K=40),  # the largest rank, many passes
 }
 
 
@@ -73,10 +77,10 @@ def test_wide_paths_reject_the_narrow_only_operations():
     assert ts.ts_workspace_bytes(dd, ts.TS_OP_SINR_SVD_TF32) == 0
 
 
-@pytest.mark.parametrize("P,N,M", [(64, 48, 8), (401, 32, 4)])
+@pytest.mark.parametrize("P,N,M", [(64, 48, 8), (401, 32, 4), (1024, 8, 2)])
 def test_dense_comparator_at_large_P(P, N, M):
     # C = I, p = P: the wide kernel evaluates w = c* per slab
-    w = _wl(f"dense P{P}", P=P, N=N, M=M, m=M, n=16, p=16, L=2, K=70)
+    w = _wl(f"dense P{P}", P=P, N=N, M=M, m=M, n=min(16, N), p=16, L=2, K=70)
     case = Case(w).with_channels()
     got, flags = case.gpu_dense_sinr("svd", "paths")
     assert np.all((flags & ts.TS_FLAG_ERRORS) == 0)
