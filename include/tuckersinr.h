@@ -374,12 +374,13 @@ int ts_dense_sinr_mmse(const ts_dims* d, const ts_coef* coef, const ts_c64* X,
  * (eq. 20), then all B_k (eq. 21), then all C_ik (eq. 22), each the leading
  * eigenvectors of a summed mode Gram -- and the core (eq. 17) once at the
  * end.  Eigensolvers: cyclic Jacobi for Gram dimensions <= 72, block subspace
- * iteration with a Rayleigh-Ritz step above that.
+ * iteration with a Rayleigh-Ritz step above that (blocks beyond 72 columns
+ * in global scratch; a block that would span the Gram solves it directly).
  * X: [J*J][P][M][N] (link i*J+k, submatrices of eq. 2 stacked on mode 3);
  * A (out, or in for init = 1): [J][M][m]; B: [J][N][n]; C: [J*J][P][p];
  * G (out): [J*J][p][m][n]; g_hist (device, may be NULL): 3 S + 1 doubles,
  * the objective g of eq. (19) after the initialisation and after every block
- * update.  Ranks up to 64.  ws: ts_workspace_bytes(d, TS_OP_TUCKER_FIT). */
+ * update.  Ranks up to 256.  ws: ts_workspace_bytes(d, TS_OP_TUCKER_FIT). */
 int ts_tucker_fit(const ts_dims* d, const ts_c64* X, int S, int init, ts_c64* A,
                   ts_c64* B, ts_c64* C, ts_c64* G, double* g_hist, void* ws,
                   size_t ws_bytes, void* stream);

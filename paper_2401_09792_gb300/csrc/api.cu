@@ -191,12 +191,13 @@ ts::FitDims fit_dims(const ts_dims* d, int model = TS_MODEL_GROUPWISE) {
   return ts::FitDims{d->J, d->M, d->N, d->P, d->m, d->n, d->p, model, g_fit_iters};
 }
 
-// Sizes the fit accepts: ranks up to 64 (eigensolver block limit).
+// Sizes the fit accepts: ranks up to 256 (the eigensolver blocks stay within
+// 512 columns).
 int fit_checks(const ts_dims* d) {
   if (d == nullptr) return TS_ERR_NULL;
   if (d->J < 1 || d->M < 1 || d->N < 1 || d->P < 1) return TS_ERR_DIMS;
   if (d->m < 1 || d->n < 1 || d->p < 1 || d->m > d->M || d->n > d->N || d->p > d->P) return TS_ERR_DIMS;
-  if (d->m > 64 || d->n > 64 || d->p > 64) return TS_ERR_DIMS;
+  if (d->m > 256 || d->n > 256 || d->p > 256) return TS_ERR_DIMS;
   if (d->M > 4096 || d->N > 4096 || d->P > 4096 || d->J > 256) return TS_ERR_DIMS;
   return TS_OK;
 }

@@ -18,7 +18,9 @@
 // Eigensolvers: cyclic Jacobi with a round-robin ordering in one CTA for
 // dimensions <= kJacobiMax; above that, block subspace iteration with
 // Cholesky-QR and a Rayleigh-Ritz step (Jacobi on the block) warm-started
-// from the current factor.
+// from the current factor.  Blocks wider than kJacobiMax (ranks above 56)
+// keep the Jacobi matrices and the Cholesky factor in global scratch; when
+// the block would span the whole space the Gram itself goes to Jacobi.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -142,26 +144,32 @@ __global__ void k_gram(const double2* T, int J, int d1, int d2, int d3, int gmod
   }
 }
 
-// Cyclic Jacobi on one Hermitian D x D matrix per CTA (D <= kJacobiMax),
-// round-robin ordering, FP64.  Writes the r leading eigenvectors (descending
+// Cyclic Jacobi on one Hermitian D x D matrix per CTA, round-robin
+// ordering, FP64.  Writes the r leading eigenvectors (descending
 // eigenvalues, each column's largest-modulus entry made real positive) to
 // out[mat] ([D][r]) and the sum of the r leading eigenvalues to lsum[mat].
 // With `basis` non-null the eigenvectors are mapped through it first:
 // out = basis[mat] ([N][D]) * eigvecs (Rayleigh-Ritz), out is [N][r].
+// The matrix and its rotation accumulator live in shared memory for
+// D <= kJacobiMax, else (GLOB) in the CTA's slice of the global scratch
+// `gs` (2 D (D + 1) entries per matrix, L2-resident); the per-pair
+// rotations stay in shared memory either way.
 constexpr int kJacobiMax = 72;
 constexpr int kJacobiThreads = 256;
+template <bool GLOB>
 __global__ void __launch_bounds__(kJacobiThreads)
 k_jacobi(const double2* Sin, int D, int r, double2* out, double* lsum, const double2* basis,
-         int N) {
+         int N, double2* gs) {
   extern __shared__ __align__(16) double2 js[];
   const int SD = D + 1;
-  double2* S = js;                      // D x SD
-  double2* U = S + D * SD;              // D x SD
-  double2* rcs = U + D * SD;            // (c, s) per pair
-  double2* rph = rcs + kJacobiMax / 2 + 1;   // e per pair; later the r <= D column phases
-  int* pq = reinterpret_cast<int*>(rph + kJacobiMax);
-  double* red = reinterpret_cast<double*>(pq + kJacobiMax + 2);
+  const int Dcap = GLOB ? D : kJacobiMax;
   const int mat = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
+  double2* S = GLOB ? gs + (size_t)mat * 2 * D * SD : js;   // D x SD
+  double2* U = S + D * SD;                                  // D x SD
+  double2* rcs = GLOB ? js : U + D * SD;                    // (c, s) per pair
+  double2* rph = rcs + Dcap / 2 + 1;    // e per pair; later the r <= D column phases
+  int* pq = reinterpret_cast<int*>(rph + Dcap);
+  double* red = reinterpret_cast<double*>(pq + Dcap + 2);
   const double2* src = Sin + (size_t)mat * D * D;
   for (int t = tid; t < D * D; t += nth) {
     const int a = t / D, b = t - a * D;
@@ -332,12 +340,14 @@ __global__ void k_gemm_qhy(const double2* Q, const double2* Y, int nmat, int N, 
 }
 
 // Orthonormalise the columns of Y[mat] (N x c) in place into Q: Cholesky-QR
-// (R^H R = Y^H Y, Q = Y R^{-1}); one CTA per matrix, c <= kJacobiMax.
-__global__ void __launch_bounds__(kJacobiThreads) k_cholqr(double2* Y, int N, int c) {
+// (R^H R = Y^H Y, Q = Y R^{-1}); one CTA per matrix.  R in shared memory
+// for c <= kJacobiMax, else (GLOB) in the CTA's slice of the global scratch.
+template <bool GLOB>
+__global__ void __launch_bounds__(kJacobiThreads) k_cholqr(double2* Y, int N, int c, double2* gs) {
   extern __shared__ __align__(16) double2 cs[];
   const int SC = c + 1;
-  double2* R = cs;                         // c x SC
   const int mat = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
+  double2* R = GLOB ? gs + (size_t)mat * c * SC : cs;     // c x SC
   double2* Ym = Y + (size_t)mat * N * c;
   for (int t = tid; t < c * c; t += nth) {
     const int i = t / c, j = t - i * c;
@@ -367,17 +377,32 @@ __global__ void __launch_bounds__(kJacobiThreads) k_cholqr(double2* Y, int N, in
     __syncthreads();
   }
   // Q = Y L^{-H}: each row y (1 x c) solves q L^H = y by forward substitution
-  for (int a = tid; a < N; a += nth) {
-    double2 q[kJacobiMax];
-    for (int j = 0; j < c; ++j) {
-      double2 v = Ym[(size_t)a * c + j];
-      for (int k = 0; k < j; ++k) {
-        const double2 pr = dmul(q[k], dconj(R[j * SC + k]));
-        v = make_double2(v.x - pr.x, v.y - pr.y);
+  if (GLOB) {
+    // in place: q_j overwrites y_j once the q_k, k < j, it needs are written
+    for (int a = tid; a < N; a += nth) {
+      double2* row = Ym + (size_t)a * c;
+      for (int j = 0; j < c; ++j) {
+        double2 v = row[j];
+        for (int k = 0; k < j; ++k) {
+          const double2 pr = dmul(row[k], dconj(R[j * SC + k]));
+          v = make_double2(v.x - pr.x, v.y - pr.y);
+        }
+        row[j] = dscale(v, 1.0 / R[j * SC + j].x);
       }
-      q[j] = dscale(v, 1.0 / R[j * SC + j].x);
     }
-    for (int j = 0; j < c; ++j) Ym[(size_t)a * c + j] = q[j];
+  } else {
+    for (int a = tid; a < N; a += nth) {
+      double2 q[kJacobiMax];
+      for (int j = 0; j < c; ++j) {
+        double2 v = Ym[(size_t)a * c + j];
+        for (int k = 0; k < j; ++k) {
+          const double2 pr = dmul(q[k], dconj(R[j * SC + k]));
+          v = make_double2(v.x - pr.x, v.y - pr.y);
+        }
+        q[j] = dscale(v, 1.0 / R[j * SC + j].x);
+      }
+      for (int j = 0; j < c; ++j) Ym[(size_t)a * c + j] = q[j];
+    }
   }
 }
 
@@ -441,42 +466,93 @@ __global__ void k_norm2(const double2* T, size_t count, double* g_hist, int slot
 
 }  // namespace
 
+// Columns of the subspace-iteration block for a D x D eigenproblem keeping r
+// (0: D <= kJacobiMax, solved directly in shared memory).  Oversampled to
+// max(r + 16, 2 r) while that fits the shared-memory block, else to
+// kJacobiMax while r + 16 does, else (large ranks) to min(D, max(r + 16,
+// 2 r)) with the block kept in global memory.
+int eig_block(int D, int r) {
+  if (D <= kJacobiMax) return 0;
+  int c = r + 16 > 2 * r ? r + 16 : 2 * r;
+  if (c > kJacobiMax && r + 16 <= kJacobiMax) c = kJacobiMax;
+  return c > D ? D : c;
+}
+
+size_t jacobi_smem(int D, bool glob) {
+  const int Dcap = glob ? D : kJacobiMax;
+  return (glob ? 0 : (size_t)2 * kJacobiMax * (kJacobiMax + 1) * sizeof(double2)) +
+         (size_t)(Dcap / 2 + 1 + Dcap) * sizeof(double2) + (size_t)(Dcap + 2) * sizeof(int) +
+         80 * sizeof(double);
+}
+
+// Entries of the subspace blocks (Q, Y, T each) and of the global Jacobi /
+// Cholesky-QR scratch that the fit's three factor updates need.
+void eig_sizes(const FitDims& f, size_t& blk, size_t& gsz) {
+  const size_t J2 = (size_t)f.J * f.J, nG = fit_groups(f.J, f.model);
+  blk = 1;
+  gsz = 1;
+  auto need = [&](int D, int r, size_t nmat) {
+    const int c = eig_block(D, r);
+    if (c == 0) return;
+    if (c < D && nmat * D * c > blk) blk = nmat * D * c;
+    if (c > kJacobiMax && nmat * 2 * c * (c + 1) > gsz) gsz = nmat * 2 * (size_t)c * (c + 1);
+  };
+  need(f.M, f.m, nG);
+  need(f.N, f.n, nG);
+  need(f.P, f.p, J2);
+}
+
 // Leading r eigenvectors of nmat Hermitian D x D matrices S (FP64) into F
 // ([nmat][D][r]), their eigenvalue sums into lsum.  `warm`: F holds a start.
+// gscratch: 2 c (c + 1) entries per matrix for blocks beyond kJacobiMax.
 cudaError_t leading_eigvecs(const double2* S, int nmat, int D, int r, double2* F, double* lsum,
                             bool warm, double2* Qbuf, double2* Ybuf, double2* Tbuf, int iters,
-                            cudaStream_t s) {
-  // S, U; (c, s) per pair; e per pair, later one phase per kept column;
-  // pair indices, later the eigenvalue order; reduction scratch
-  const size_t jsm = (size_t)2 * kJacobiMax * (kJacobiMax + 1) * sizeof(double2) +
-                     (kJacobiMax / 2 + 1 + kJacobiMax) * sizeof(double2) +
-                     (kJacobiMax + 2) * sizeof(int) + 80 * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jsm);
+                            double2* gscratch, cudaStream_t s) {
+  const size_t jsm = jacobi_smem(D, false);
+  cudaError_t e = cudaFuncSetAttribute(k_jacobi<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)jsm);
   if (e != cudaSuccess) return e;
   if (D <= kJacobiMax) {
-    k_jacobi<<<nmat, kJacobiThreads, jsm, s>>>(S, D, r, F, lsum, nullptr, 0);
+    k_jacobi<false><<<nmat, kJacobiThreads, jsm, s>>>(S, D, r, F, lsum, nullptr, 0, nullptr);
     return cudaGetLastError();
   }
-  // block subspace iteration on c = max(r + 16, 2 r) columns (at most
-  // kJacobiMax); a cold start (initialisation) runs three times as long
-  int c = r + 16 > 2 * r ? r + 16 : 2 * r;
-  if (c > kJacobiMax) c = kJacobiMax;
-  if (c > D) c = D;
+  const int c = eig_block(D, r);
+  const bool glob = c > kJacobiMax;
+  if (c == D) {
+    // the block would be the whole space: solve S itself
+    k_jacobi<true><<<nmat, kJacobiThreads, jacobi_smem(D, true), s>>>(S, D, r, F, lsum, nullptr, 0,
+                                                                      gscratch);
+    return cudaGetLastError();
+  }
+  // block subspace iteration on c columns; a cold start (initialisation)
+  // runs three times as long
   if (!warm) iters *= 3;
   k_start_block<<<nblocks((size_t)nmat * D * c), 256, 0, s>>>(warm ? F : nullptr, nmat, D, r, c, Qbuf);
-  const size_t qsm = (size_t)c * (c + 1) * sizeof(double2);
-  e = cudaFuncSetAttribute(k_cholqr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsm);
-  if (e != cudaSuccess) return e;
-  k_cholqr<<<nmat, kJacobiThreads, qsm, s>>>(Qbuf, D, c);
+  const size_t qsm = glob ? 0 : (size_t)c * (c + 1) * sizeof(double2);
+  if (!glob) {
+    e = cudaFuncSetAttribute(k_cholqr<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsm);
+    if (e != cudaSuccess) return e;
+  }
+  auto cholqr = [&](double2* Yb) {
+    if (glob)
+      k_cholqr<true><<<nmat, kJacobiThreads, 0, s>>>(Yb, D, c, gscratch);
+    else
+      k_cholqr<false><<<nmat, kJacobiThreads, qsm, s>>>(Yb, D, c, nullptr);
+  };
+  cholqr(Qbuf);
   for (int it = 0; it < iters; ++it) {
     k_gemm_sq<<<nblocks((size_t)nmat * D * c), 256, 0, s>>>(S, Qbuf, nmat, D, c, Ybuf);
-    k_cholqr<<<nmat, kJacobiThreads, qsm, s>>>(Ybuf, D, c);
+    cholqr(Ybuf);
     double2* t = Qbuf; Qbuf = Ybuf; Ybuf = t;
   }
   // Rayleigh-Ritz: T = Q^H S Q, eigenvectors of T mapped through Q
   k_gemm_sq<<<nblocks((size_t)nmat * D * c), 256, 0, s>>>(S, Qbuf, nmat, D, c, Ybuf);
   k_gemm_qhy<<<nblocks((size_t)nmat * c * c), 256, 0, s>>>(Qbuf, Ybuf, nmat, D, c, Tbuf);
-  k_jacobi<<<nmat, kJacobiThreads, jsm, s>>>(Tbuf, c, r, F, lsum, Qbuf, D);
+  if (glob)
+    k_jacobi<true><<<nmat, kJacobiThreads, jacobi_smem(c, true), s>>>(Tbuf, c, r, F, lsum, Qbuf, D,
+                                                                      gscratch);
+  else
+    k_jacobi<false><<<nmat, kJacobiThreads, jsm, s>>>(Tbuf, c, r, F, lsum, Qbuf, D, nullptr);
   return cudaGetLastError();
 }
 
@@ -554,11 +630,11 @@ size_t fit_workspace_bytes(const FitDims& f) {
   size_t tmax = J2 * f.P * f.M * f.N;                         // X in FP64 (largest tensor)
   size_t tb = J2 * f.P * (size_t)(f.M > f.m ? f.M : f.m) * (f.N > f.n ? f.N : f.n);
   const size_t big = (tmax > tb ? tmax : tb) * c16;
-  const int Dmax = f.N > f.M ? (f.N > f.P ? f.N : f.P) : (f.M > f.P ? f.M : f.P);
   const size_t nG = fit_groups(f.J, f.model);
   const size_t gram = (J2 * f.P * f.P + nG * f.M * f.M + nG * f.N * f.N) * c16;
-  const size_t blk = (size_t)J2 * Dmax * (fit::kJacobiMax) * c16;
-  return al(J2 * f.P * f.M * f.N * c16) + 2 * al(big) + al(gram) + 3 * al(blk) +
+  size_t blk = 0, gsz = 0;
+  fit::eig_sizes(f, blk, gsz);
+  return al(J2 * f.P * f.M * f.N * c16) + 2 * al(big) + al(gram) + 3 * al(blk * c16) + al(gsz * c16) +
          al((nG * f.M * f.m + nG * f.N * f.n + J2 * f.P * f.p) * c16) + al(J2 * sizeof(double));
 }
 
@@ -576,7 +652,6 @@ cudaError_t launch_fit(const FitDims& f, const float2* X, int S, int init, float
   size_t tmax = J2 * P * M * N;
   size_t tb = J2 * P * (size_t)(M > m ? M : m) * (N > n ? N : n);
   const size_t big = (tmax > tb ? tmax : tb) * c16;
-  const int Dmax = N > M ? (N > P ? N : P) : (M > P ? M : P);
   double2* Xd = reinterpret_cast<double2*>(take(J2 * P * M * N * c16));
   double2* T1 = reinterpret_cast<double2*>(take(big));
   double2* T2 = reinterpret_cast<double2*>(take(big));
@@ -584,10 +659,12 @@ cudaError_t launch_fit(const FitDims& f, const float2* X, int S, int init, float
       take((J2 * P * P + (size_t)nG * M * M + (size_t)nG * N * N) * c16));
   double2* GA = GC + J2 * P * P;
   double2* GB = GA + (size_t)nG * M * M;
-  const size_t blk = (size_t)J2 * Dmax * kJacobiMax * c16;
-  double2* Qb = reinterpret_cast<double2*>(take(blk));
-  double2* Yb = reinterpret_cast<double2*>(take(blk));
-  double2* Tb = reinterpret_cast<double2*>(take(blk));
+  size_t blk = 0, gsz = 0;
+  eig_sizes(f, blk, gsz);
+  double2* Qb = reinterpret_cast<double2*>(take(blk * c16));
+  double2* Yb = reinterpret_cast<double2*>(take(blk * c16));
+  double2* Tb = reinterpret_cast<double2*>(take(blk * c16));
+  double2* gs = reinterpret_cast<double2*>(take(gsz * c16));
   double2* A64 = reinterpret_cast<double2*>(
       take(((size_t)nG * M * m + (size_t)nG * N * n + J2 * P * p) * c16));
   double2* B64 = A64 + (size_t)nG * M * m;
@@ -608,28 +685,28 @@ cudaError_t launch_fit(const FitDims& f, const float2* X, int S, int init, float
     k_modeprod<double2><<<nblocks(J2 * P * m * N), 256, 0, s>>>(Xd, (int)J2, J, M, N, P, 0, A64, 0, model, m, T1);
     k_modeprod<double2><<<nblocks(J2 * p * m * N), 256, 0, s>>>(T1, (int)J2, J, m, N, P, 2, C64, 2, model, p, T2);
     k_gram<<<nblocks((size_t)nG * N * N), 256, 0, s>>>(T2, J, m, N, p, 1, model, GB);
-    return leading_eigvecs(GB, nG, N, n, B64, lsum, warm, Qb, Yb, Tb, iters, s);
+    return leading_eigvecs(GB, nG, N, n, B64, lsum, warm, Qb, Yb, Tb, iters, gs, s);
   };
   auto update_A = [&](bool warm) -> cudaError_t {
     k_modeprod<double2><<<nblocks(J2 * P * M * n), 256, 0, s>>>(Xd, (int)J2, J, M, N, P, 1, B64, 1, model, n, T1);
     k_modeprod<double2><<<nblocks(J2 * p * M * n), 256, 0, s>>>(T1, (int)J2, J, M, n, P, 2, C64, 2, model, p, T2);
     k_gram<<<nblocks((size_t)nG * M * M), 256, 0, s>>>(T2, J, M, n, p, 0, model, GA);
-    return leading_eigvecs(GA, nG, M, m, A64, lsum, warm, Qb, Yb, Tb, iters, s);
+    return leading_eigvecs(GA, nG, M, m, A64, lsum, warm, Qb, Yb, Tb, iters, gs, s);
   };
   auto update_C = [&](bool warm) -> cudaError_t {
     k_modeprod<double2><<<nblocks(J2 * P * m * N), 256, 0, s>>>(Xd, (int)J2, J, M, N, P, 0, A64, 0, model, m, T1);
     k_modeprod<double2><<<nblocks(J2 * P * m * n), 256, 0, s>>>(T1, (int)J2, J, m, N, P, 1, B64, 1, model, n, T2);
     k_gram<<<nblocks(J2 * P * P), 256, 0, s>>>(T2, J, m, n, P, 2, model, GC);
-    return leading_eigvecs(GC, (int)J2, P, p, C64, lsum, warm, Qb, Yb, Tb, iters, s);
+    return leading_eigvecs(GC, (int)J2, P, p, C64, lsum, warm, Qb, Yb, Tb, iters, gs, s);
   };
   if (init == 0) {
     // eq. (20)-(22) with the other factors set to the identity
     k_gram<<<nblocks((size_t)nG * M * M), 256, 0, s>>>(Xd, J, M, N, P, 0, model, GA);
-    if ((e = leading_eigvecs(GA, nG, M, m, A64, lsum, false, Qb, Yb, Tb, iters, s)) != cudaSuccess) return e;
+    if ((e = leading_eigvecs(GA, nG, M, m, A64, lsum, false, Qb, Yb, Tb, iters, gs, s)) != cudaSuccess) return e;
     k_gram<<<nblocks((size_t)nG * N * N), 256, 0, s>>>(Xd, J, M, N, P, 1, model, GB);
-    if ((e = leading_eigvecs(GB, nG, N, n, B64, lsum, false, Qb, Yb, Tb, iters, s)) != cudaSuccess) return e;
+    if ((e = leading_eigvecs(GB, nG, N, n, B64, lsum, false, Qb, Yb, Tb, iters, gs, s)) != cudaSuccess) return e;
     k_gram<<<nblocks(J2 * P * P), 256, 0, s>>>(Xd, J, M, N, P, 2, model, GC);
-    if ((e = leading_eigvecs(GC, (int)J2, P, p, C64, lsum, false, Qb, Yb, Tb, iters, s)) != cudaSuccess) return e;
+    if ((e = leading_eigvecs(GC, (int)J2, P, p, C64, lsum, false, Qb, Yb, Tb, iters, gs, s)) != cudaSuccess) return e;
   } else {
     k_to_double<<<nblocks((size_t)nG * M * m), 256, 0, s>>>(A, (size_t)nG * M * m, A64);
     k_to_double<<<nblocks((size_t)nG * N * n), 256, 0, s>>>(B, (size_t)nG * N * n, B64);

@@ -113,3 +113,13 @@ def test_fewer_inner_iterations():
     gG = sum(T.fro2(G[i, k]) for i in range(w.J) for k in range(w.J))
     assert abs(f - (T.fro2(X) - gG)) < 1e-5 * T.fro2(X)
     assert abs(g2[-1] - g40[-1]) < 0.05 * g40[-1]
+
+
+@pytest.mark.parametrize("N,n", [(256, 64), (100, 64)])
+def test_fit_large_ranks(N, n):
+    # ranks above 56: the subspace block (N = 256: 128 columns), its
+    # Cholesky-QR and the Rayleigh-Ritz Jacobi in global scratch, or (N = 100)
+    # a block that would span the whole Gram, which the global Jacobi then
+    # solves directly (likewise the P = 80 C Grams keeping p = 60)
+    w = dataclasses.replace(synth.SMALL, J=2, M=4, N=N, P=80, m=4, n=n, p=60, K=8, L=2)
+    _check(w, S=2, gtol=1e-6)
