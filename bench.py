@@ -1057,6 +1057,75 @@ def run_multiuser(args):
     del keep
 
 
+def run_paper_method(args):
+    """e_c (eq. 30) at the paper's sizes: the groupwise form fitted on the GPU
+    (Algorithm 2, `sweeps` sweeps, 8 inner iterations per large eigensolve)
+    from synthetic channels of the first UE of every cell (J = 21, (M, N, P)
+    and the workload's ranks; spatially correlated NLOS submatrices), then
+    the SVD-precoded SINR from the fitted form against the dense-channel
+    SINR on the same channels, both on the GPU; with the fit's time per
+    sweep and the storage ratio of eq. (29)."""
+    import torch
+
+    from oracle import tucker as T
+    from paper_2401_09792_gb300 import tuckersinr as ts
+    import __graft_entry__
+    __graft_entry__.build()
+    ts.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    w = dataclasses.replace(WORKLOAD, U=1, nlos_corr=synth.MID_CORR.nlos_corr)
+    J, K, L, M, N, P, m, n, p = w.J, w.K, w.L, w.M, w.N, w.P, w.m, w.n, w.p
+    sweeps = 3
+    t0 = time.perf_counter()
+    Xd = ts.channels_to_device(synth.channel_submatrices(w), dev)
+    gen_s = time.perf_counter() - t0
+    alpha, tau = synth.path_gains_delays(w)
+    s2 = synth.noise_powers(w)
+    al = ts.factor_to_device(alpha.reshape(J * J, P), dev)
+    ta = ts.real_to_device(tau.reshape(J * J, P), dev)
+    sig = ts.real_to_device(s2, dev)
+    cs, keep = ts.make_coef(alpha=al, tau=ta)
+    d = ts.Dims.of(w)
+    stream = torch.cuda.current_stream(dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    c64 = dict(dtype=torch.complex64, device=dev)
+    A = torch.empty(J, M, m, **c64)
+    B = torch.empty(J, N, n, **c64)
+    C = torch.empty(J * J, P, p, **c64)
+    G = torch.empty(J * J, p, m, n, **c64)
+    g = torch.empty(3 * sweeps + 1, dtype=torch.float64, device=dev)
+    wsf = ts.workspace(d, ts.TS_OP_TUCKER_FIT, dev)
+    ts.ts_set_fit_iterations(8)
+    a, b = ev(), ev()
+    a.record(stream)
+    ts.ts_tucker_fit(d, Xd, sweeps, 0, A, B, C, G, g, wsf, stream)
+    b.record(stream)
+    b.synchronize()
+    ts.ts_set_fit_iterations(0)
+    fit_ms = a.elapsed_time(b)
+    del wsf
+    s_t = torch.empty(J, K, L, device=dev)
+    s_d = torch.empty_like(s_t)
+    ts.ts_sinr_svd(d, cs, G, C, sig, s_t, None, ts.workspace(d, ts.TS_OP_SINR_SVD, dev), stream)
+    ts.ts_dense_sinr_svd(d, cs, Xd, sig, s_d, None, ts.workspace(d, ts.TS_OP_DENSE_SVD, dev), stream)
+    torch.cuda.synchronize()
+    st, sd = s_t.double(), s_d.double()
+    x2 = float((Xd.abs() ** 2).sum().item())
+    line = {"metric": "e_c at the paper's sizes (eq. 30)",
+            "workload": (f"{WORKLOAD_NAME} first UEs: J={J}, M={M}, N={N}, P={P}, K={K} subcarriers, "
+                         f"ranks ({m},{n},{p}), L={L}; NLOS correlation {w.nlos_corr}"),
+            "e_c": float(((st - sd).abs() / sd.abs()).mean().item()),
+            "g_over_x2": float(g[-1].item()) / x2, "g_history": [float(v) / x2 for v in g.cpu().tolist()],
+            "fit_ms": round(fit_ms, 1), "fit_ms_per_sweep": round(fit_ms / sweeps, 1),
+            "fit_sweeps": sweeps, "fit_inner_iterations": 8,
+            "R_s_one_ue_per_cell": T.storage_ratio(J, 1, M, N, P, m, n, p, "groupwise"),
+            "channel_generation_s": round(gen_s, 1),
+            "what": "Tucker form fitted on the GPU from the synthetic channels; both SINRs on the GPU"}
+    print(json.dumps(line), flush=True)
+    del keep
+
+
 def run_rank_sweep(args):
     """Fig. 5 of the paper on synthetic channels: vary the compressed column
     count n with (m, p) fixed, then p with (m, n) fixed, and report for
@@ -1216,6 +1285,8 @@ def main():
                     help="systems of the batch workload")
     ap.add_argument("--ue-groups", type=int, default=None,
                     help="UEs per cell of a several-UE workload (default: the workload's)")
+    ap.add_argument("--paper-method", action="store_true",
+                    help="paper-scale workloads: fit the first UEs' channels on the GPU and report e_c")
     ap.add_argument("--rank-sweep", action="store_true",
                     help="sweep the compressed sizes n, then p, on the workload (default mid_corr): "
                          "R_s, R_t and e_c per point")
@@ -1240,6 +1311,8 @@ def main():
         set_ue_groups(args.ue_groups)
     if args.impl == "reference":
         run_reference(args)
+    elif several and args.paper_method:
+        run_paper_method(args)
     elif several:
         run_multiuser(args)
     else:
