@@ -22,6 +22,8 @@ thread_local cudaEvent_t g_ev_stop = nullptr;
 // residuals (ts_set_refinement); infinity turns refinement off
 thread_local float g_refine_cond = 1e3f;
 thread_local int g_fit_iters = 40;
+// rows per unit of the SVD path (more than kMaxRankM: shared-memory kernels)
+constexpr int kMaxRankMLarge = 64;
 // launch-shape choices of the batch planner (0: default heuristics)
 thread_local ts::Tuning g_tuning = {0, 0};
 thread_local bool g_timing_suspended = false;
@@ -56,7 +58,8 @@ cudaError_t finalize_refined(const ts::SinrArgs& a, bool svd, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
   if (svd && a.J < 2) e = cudaMemsetAsync(a.rcount, 0, sizeof(int), s);
   if (e == cudaSuccess) e = ts::launch_sinr_finalize(a, svd, s);
-  if (e == cudaSuccess && a.refine_cond < INFINITY) e = ts::launch_sinr_refine(a, svd, s);
+  if (e == cudaSuccess && a.refine_cond < INFINITY && a.m <= ts::kMaxRankM)
+    e = ts::launch_sinr_refine(a, svd, s);
   return e;
 }
 
@@ -89,8 +92,10 @@ int check_dims(const ts_dims* d, bool identity = false) {
   if (d->J < 1 || d->M < 1 || d->N < 1 || d->P < 1 || d->K < 1) return TS_ERR_DIMS;
   if (d->m < 1 || d->n < 1 || d->p < 1 || d->L < 1) return TS_ERR_DIMS;
   if (d->m > d->M || d->n > d->N || d->p > d->P) return TS_ERR_DIMS;
-  if (d->m > ts::kMaxRankM) return TS_ERR_DIMS;
+  if (d->m > kMaxRankMLarge) return TS_ERR_DIMS;
   if (d->L > d->m || d->L > d->n) return TS_ERR_DIMS;
+  // units with more than 16 rows: shared-memory kernels, up to 8 streams
+  if (d->m > ts::kMaxRankM && d->L > 8) return TS_ERR_DIMS;
   // staging limits of the kernels: one H~ (m x n) per subcarrier and the
   // projections w [subcarrier tile][p] live in shared memory
   // (the dense-channel comparator, C = I, keeps no projections: p = P <= 1024)
@@ -105,7 +110,13 @@ int check_dims(const ts_dims* d, bool identity = false) {
 int check_narrow(const ts_dims* d) {
   const int st = check_dims(d);
   if (st != TS_OK) return st;
-  return ts::wide_core(d->P, d->p) ? TS_ERR_DIMS : TS_OK;
+  return ts::wide_core(d->P, d->p) || d->m > ts::kMaxRankM ? TS_ERR_DIMS : TS_OK;
+}
+
+// The SVD precoder forms the serving links' channels itself (small cores,
+// register-resident units); otherwise a serving pass writes them first.
+bool fuses_serve(const ts_dims* d) {
+  return d->m <= ts::kMaxRankM && ts::precoder_fuses_serve(d->m, d->n, d->p);
 }
 
 // Workspace layout (byte offsets from the base, each 256-byte aligned).
@@ -127,7 +138,7 @@ Workspace carve(const ts_dims* d, int op) {
   if (op == TS_OP_SINR_SVD) {
     w.V = o;
     o = align_up(o + (size_t)d->J * d->K * d->n * d->L * sizeof(float2), 256);
-    if (!ts::precoder_fuses_serve(d->m, d->n, d->p)) {
+    if (!fuses_serve(d)) {
       w.Hserv = o;
       o = align_up(o + (size_t)d->J * d->K * d->m * d->n * sizeof(float2), 256);
       if (ts::wide_core(d->P, d->p)) {
@@ -557,7 +568,7 @@ int svd_precoders_impl(const ts_dims* d, const ts_coef* coef, const ts_c64* G, c
   if (coef->mode == TS_COEF_PATHS)
     e = ts::launch_turns(coef->tau_s, d->delta_f_hz, d->J * d->J * d->P,
                          reinterpret_cast<unsigned long long*>(base + w.turns), s);
-  a.fuse_serve = ts::precoder_fuses_serve(d->m, d->n, d->p) ? 1 : 0;
+  a.fuse_serve = fuses_serve(d) ? 1 : 0;
   if (!a.fuse_serve) {
     a.Hserv = reinterpret_cast<float2*>(base + w.Hserv);
     a.serv_stride = 1;

@@ -51,6 +51,22 @@ extern template cudaError_t run_rebuild<16, 16>(const SinrArgs&, cudaStream_t);
 extern template cudaError_t run_links<16, 16>(const SinrArgs&, bool, cudaStream_t);
 extern template cudaError_t run_finalize<16, 16>(const SinrArgs&, bool, cudaStream_t);
 
+// Units with more than 16 rows (sinr_large.cu): specialisations of the
+// dispatch templates for 32 and 64 rows.
+#define TS_LARGE_DECL(MG, LT)                                                        \
+  template <> cudaError_t run_precoder<MG, LT>(const SinrArgs&, cudaStream_t);       \
+  template <> cudaError_t run_serving<MG, LT>(const SinrArgs&, cudaStream_t);        \
+  template <> cudaError_t run_rebuild<MG, LT>(const SinrArgs&, cudaStream_t);        \
+  template <> cudaError_t run_links<MG, LT>(const SinrArgs&, bool, cudaStream_t);    \
+  template <> cudaError_t run_finalize<MG, LT>(const SinrArgs&, bool, cudaStream_t);
+TS_LARGE_DECL(32, 2)
+TS_LARGE_DECL(32, 4)
+TS_LARGE_DECL(32, 8)
+TS_LARGE_DECL(64, 2)
+TS_LARGE_DECL(64, 4)
+TS_LARGE_DECL(64, 8)
+#undef TS_LARGE_DECL
+
 namespace {
 // ------------------------------------------------------------ small kernels
 __device__ __forceinline__ unsigned long long turn_fixed(float tau, float df) {
@@ -110,7 +126,7 @@ __global__ void k_mmse_fold(const float2* G, const float2* Pt, int J, int m, int
   }
 }
 
-int group_size(int m) { return m <= 2 ? 2 : m <= 4 ? 4 : m <= 8 ? 8 : 16; }
+int group_size(int m) { return m <= 2 ? 2 : m <= 4 ? 4 : m <= 8 ? 8 : m <= 16 ? 16 : m <= 32 ? 32 : 64; }
 int ltile(int L) { return L <= 2 ? 2 : L <= 4 ? 4 : L <= 8 ? 8 : 16; }
 }  // namespace
 }  // namespace detail
@@ -131,8 +147,14 @@ using detail::run_finalize;
     if (MG_ == 8)                                                                   \
       return LT_ <= 2 ? FN<8, 2>(__VA_ARGS__)                                       \
                       : LT_ <= 4 ? FN<8, 4>(__VA_ARGS__) : FN<8, 8>(__VA_ARGS__);   \
-    return LT_ <= 4 ? FN<16, 4>(__VA_ARGS__)                                        \
-                    : LT_ <= 8 ? FN<16, 8>(__VA_ARGS__) : FN<16, 16>(__VA_ARGS__);  \
+    if (MG_ == 16)                                                                  \
+      return LT_ <= 4 ? FN<16, 4>(__VA_ARGS__)                                      \
+                      : LT_ <= 8 ? FN<16, 8>(__VA_ARGS__) : FN<16, 16>(__VA_ARGS__);\
+    if (MG_ == 32)                                                                  \
+      return LT_ <= 2 ? FN<32, 2>(__VA_ARGS__)                                      \
+                      : LT_ <= 4 ? FN<32, 4>(__VA_ARGS__) : FN<32, 8>(__VA_ARGS__); \
+    return LT_ <= 2 ? FN<64, 2>(__VA_ARGS__)                                        \
+                    : LT_ <= 4 ? FN<64, 4>(__VA_ARGS__) : FN<64, 8>(__VA_ARGS__);   \
   } while (0)
 
 cudaError_t launch_svd_precoder(const SinrArgs& a, cudaStream_t s) { TS_DISPATCH(run_precoder, a, s); }

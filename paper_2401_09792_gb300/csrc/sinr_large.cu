@@ -1,0 +1,468 @@
+// SINR kernels for more than 16 receive rows per unit (m <= 64; e.g. the
+// paper's m = 60 of M = 64 receive antennas).  One unit's m x m matrices no
+// longer fit a lane group's registers, so the SVD precoder and the
+// finalisation hold them in shared memory, one 128-thread CTA per unit; the
+// interfering and serving links run the wide-core kernel with 32 or 64 rows
+// per lane group (sinr_wide.cuh).  The arithmetic is the narrow kernels':
+//   k_svd_precoder_large  Gram S = H~_kk H~_kk* (eq. 23) scaled to unit
+//                         trace, cyclic Jacobi (round-robin pairs, one pair
+//                         per thread, rows and columns rotated by all
+//                         threads), V~ = conj(rows of U_L* H~) / sigma and
+//                         E_kk = U_L Sigma_L (eq. 7, eq. 24);
+//   k_sinr_finalize_large R = sum_{k != i} E E* + sigma^2 I (eq. 25),
+//                         Z = L_R^{-1} E_ii, x_r = [(I + Z*Z)^{-1}]_rr,
+//                         a_r = |L_Q^{-1} e_r|^2 with Q~ = R + E_ii E_ii*,
+//                         SINR_r = a_r / x_r (eq. 5 without cancellation).
+// No FP64-residual refinement pass for these sizes.
+#include "sinr_impl.cuh"
+
+namespace ts {
+namespace detail {
+namespace {
+
+constexpr int kLargeThreads = 128;
+
+// sum over the CTA (every thread gets the total); red: 32 floats
+__device__ __forceinline__ float block_sum(float v, float* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float t = 0.f;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+  return t;
+}
+
+// Shared-memory plan of the large precoder (float2 units).
+struct LargePrecPlan {
+  int SD, DE, off_S, off_U, off_H, off_rot, off_pq, off_red, total;
+};
+
+__host__ __device__ inline LargePrecPlan large_prec_plan(int m, int n, int L) {
+  LargePrecPlan pl;
+  pl.SD = m + 1;
+  pl.DE = m + (m & 1);
+  int o = 0;
+  pl.off_S = o; o += m * pl.SD;
+  pl.off_U = o; o += m * pl.SD;
+  pl.off_H = o; o += (m * 33 > L * n ? m * 33 : L * n);   // H~ column chunk, later W rows
+  pl.off_rot = o; o += pl.DE;                              // (c, s) and e per pair
+  pl.off_pq = o; o += (2 * pl.DE + 2) / 2 + 1;             // ints: pairs, later the order
+  pl.off_red = o; o += 20;                                 // 32 floats + a flag
+  pl.total = o;
+  return pl;
+}
+
+template <int MG, int LT>
+__global__ void __launch_bounds__(kLargeThreads) k_svd_precoder_large(const SinrArgs A,
+                                                                       const LargePrecPlan pl) {
+  constexpr int MAXE = (MG * (MG + 1) / 2 + kLargeThreads - 1) / kLargeThreads;
+  extern __shared__ __align__(16) float2 sm[];
+  const int m = A.m, n = A.n, L = A.L, K = A.K;
+  const int kap = blockIdx.x, k = blockIdx.y;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int SD = pl.SD, DE = pl.DE;
+  float2* S = sm + pl.off_S;
+  float2* U = sm + pl.off_U;
+  float2* Hc = sm + pl.off_H;
+  float2* rot = sm + pl.off_rot;                 // [DE/2] (c, s), then [DE/2] e
+  int* pq = reinterpret_cast<int*>(sm + pl.off_pq);
+  float* red = reinterpret_cast<float*>(sm + pl.off_red);
+  const float2* H = A.Hserv + ((size_t)k * A.serv_stride * K + kap) * m * n;   // [m][n]
+
+  // 1. Gram S = H~ H~* (lower triangle, mirrored), H~ staged 32 columns at a time
+  float2 acc[MAXE];
+#pragma unroll
+  for (int e = 0; e < MAXE; ++e) acc[e] = cz();
+  const int ntri = m * (m + 1) / 2;
+  for (int c0 = 0; c0 < n; c0 += 32) {
+    const int cc = min(32, n - c0);
+    __syncthreads();
+    for (int idx = tid; idx < m * 32; idx += nth) {
+      const int a = idx / 32, c = idx % 32;
+      Hc[a * 33 + c] = c < cc ? H[(size_t)a * n + c0 + c] : cz();
+    }
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < MAXE; ++e) {
+      const int t = tid + e * kLargeThreads;
+      if (t >= ntri) break;
+      // t -> (a, b), b <= a: row a starts at a (a + 1) / 2
+      int a = (int)((sqrtf(8.f * t + 1.f) - 1.f) * 0.5f);
+      while (a * (a + 1) / 2 > t) --a;
+      while ((a + 1) * (a + 2) / 2 <= t) ++a;
+      const int b = t - a * (a + 1) / 2;
+      for (int c = 0; c < cc; ++c) cmacc(acc[e], Hc[a * 33 + c], Hc[b * 33 + c]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int e = 0; e < MAXE; ++e) {
+    const int t = tid + e * kLargeThreads;
+    if (t >= ntri) break;
+    int a = (int)((sqrtf(8.f * t + 1.f) - 1.f) * 0.5f);
+    while (a * (a + 1) / 2 > t) --a;
+    while ((a + 1) * (a + 2) / 2 <= t) ++a;
+    const int b = t - a * (a + 1) / 2;
+    S[a * SD + b] = acc[e];
+    S[b * SD + a] = a == b ? make_float2(acc[e].x, 0.f) : cconj(acc[e]);
+  }
+  for (int idx = tid; idx < m * m; idx += nth) {
+    const int a = idx / m, b = idx - a * m;
+    U[a * SD + b] = make_float2(a == b ? 1.f : 0.f, 0.f);
+  }
+  __syncthreads();
+  // unit trace (eigenvectors and eigenvalue ratios unchanged)
+  {
+    const float tr = block_sum(tid < m ? S[tid * SD + tid].x : 0.f, red);
+    const float sc = tr > 0.f ? 1.f / tr : 1.f;
+    for (int idx = tid; idx < m * m; idx += nth) {
+      const int a = idx / m, b = idx - a * m;
+      S[a * SD + b] = cscale(S[a * SD + b], sc);
+    }
+  }
+  __syncthreads();
+
+  // 2. cyclic Jacobi, round-robin pairs (the padding index DE-1 = m when m
+  // is odd pairs with nothing), to relative off-diagonal norm ~5e-7
+  bool converged = false;
+  for (int sweep = 0; sweep <= 16; ++sweep) {
+    float off = 0.f, tot = 0.f;
+    for (int idx = tid; idx < m * m; idx += nth) {
+      const int a = idx / m, b = idx - a * m;
+      const float v = cabs2(S[a * SD + b]);
+      tot += v;
+      if (a != b) off += v;
+    }
+    off = block_sum(off, red);
+    tot = block_sum(tot, red);
+    converged = off <= 2.3e-13f * tot;
+    if (converged || sweep == 16) break;
+    for (int step = 0; step < DE - 1; ++step) {
+      if (tid < DE / 2) {
+        const int j = tid;
+        int p = j == 0 ? step : (step + j) % (DE - 1);
+        int q = j == 0 ? DE - 1 : (step - j + DE - 1) % (DE - 1);
+        float c = 1.f, s = 0.f;
+        float2 e = make_float2(1.f, 0.f);
+        if (p < m && q < m) {
+          const float app = S[p * SD + p].x, aqq = S[q * SD + q].x;
+          const float2 bpq = S[p * SD + q];
+          const float ab = sqrtf(cabs2(bpq));
+          if (ab > 1e-30f && ab > 1e-9f * sqrtf(fabsf(app * aqq))) {
+            const float tau = (aqq - app) / (2.f * ab);
+            const float tt = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
+            c = 1.f / sqrtf(fmaf(tt, tt, 1.f));
+            s = tt * c;
+            e = cscale(bpq, 1.f / ab);
+          }
+        } else {
+          p = q = -1;
+        }
+        rot[j] = make_float2(c, s);
+        rot[DE / 2 + j] = e;
+        pq[2 * j] = p;
+        pq[2 * j + 1] = q;
+      }
+      __syncthreads();
+      // rows: S <- J* S (row p' = c p - s e q, row q' = s conj(e) p + c q)
+      for (int t = tid; t < (DE / 2) * m; t += nth) {
+        const int j = t / m, col = t - j * m;
+        const int p = pq[2 * j], q = pq[2 * j + 1];
+        if (p < 0) continue;
+        const float2 cs = rot[j], e = rot[DE / 2 + j];
+        const float2 x = S[p * SD + col], y = S[q * SD + col];
+        float2 nx = cscale(x, cs.x), ny = cscale(y, cs.x);
+        cms(nx, cscale(e, cs.y), y);
+        cmac(ny, cscale(cconj(e), cs.y), x);
+        S[p * SD + col] = nx;
+        S[q * SD + col] = ny;
+      }
+      __syncthreads();
+      // columns: S <- S J, U <- U J
+      for (int t = tid; t < (DE / 2) * m; t += nth) {
+        const int j = t / m, row = t - j * m;
+        const int p = pq[2 * j], q = pq[2 * j + 1];
+        if (p < 0) continue;
+        const float2 cs = rot[j], e = rot[DE / 2 + j];
+        const float2 se = cscale(e, cs.y), sec = cscale(cconj(e), cs.y);
+        {
+          const float2 x = S[row * SD + p], y = S[row * SD + q];
+          float2 nx = cscale(x, cs.x), ny = cscale(y, cs.x);
+          cms(nx, sec, y);
+          cmac(ny, se, x);
+          S[row * SD + p] = nx;
+          S[row * SD + q] = ny;
+        }
+        {
+          const float2 x = U[row * SD + p], y = U[row * SD + q];
+          float2 nx = cscale(x, cs.x), ny = cscale(y, cs.x);
+          cms(nx, sec, y);
+          cmac(ny, se, x);
+          U[row * SD + p] = nx;
+          U[row * SD + q] = ny;
+        }
+      }
+      __syncthreads();
+    }
+  }
+
+  // 3. order of the eigenvalues (descending); the top L columns of U
+  if (tid < m) {
+    const float la = S[tid * SD + tid].x;
+    int rk = 0;
+    for (int b = 0; b < m; ++b) {
+      const float lb = S[b * SD + b].x;
+      rk += (lb > la) || (lb == la && b < tid);
+    }
+    pq[rk] = tid;
+  }
+  __syncthreads();
+
+  // 4. W rows r < L: W[r][c] = sum_b conj(U[b][idx_r]) H~[b][c] (reuses Hc)
+  float2* W = Hc;
+  for (int idx = tid; idx < L * n; idx += nth) {
+    const int r = idx / n, c = idx - r * n;
+    const int col = pq[r];
+    float2 v = cz();
+    for (int b = 0; b < m; ++b) cmacc(v, H[(size_t)b * n + c], U[b * SD + col]);
+    W[r * n + c] = v;
+  }
+  __syncthreads();
+  float s2[LT];
+  bool deficient = false;
+#pragma unroll
+  for (int r = 0; r < LT; ++r) {
+    float part = 0.f;
+    if (r < L)
+      for (int c = tid; c < n; c += nth) part += cabs2(W[r * n + c]);
+    s2[r] = block_sum(part, red);
+    deficient |= (r < L) && !(s2[r] > 0.f);
+  }
+  // 5. V~[:, r] = conj(W row r) / sigma_r, E_kk = U_L Sigma_L, flags
+  float2* Vout = A.V + ((size_t)k * K + kap) * n * L;
+  for (int idx = tid; idx < n * L; idx += nth) {
+    const int c = idx / L, r = idx - c * L;
+    float inv = 0.f;
+#pragma unroll
+    for (int rr = 0; rr < LT; ++rr)
+      if (rr == r) inv = s2[rr] > 0.f ? rsqrtf(s2[rr]) : 0.f;
+    Vout[idx] = cscale(cconj(W[r * n + c]), inv);
+  }
+  float2* Eout = A.Eserv + ((size_t)k * K + kap) * m * L;
+  for (int idx = tid; idx < m * L; idx += nth) {
+    const int a = idx / L, r = idx - a * L;
+    float sg = 0.f;
+#pragma unroll
+    for (int rr = 0; rr < LT; ++rr)
+      if (rr == r) sg = s2[rr] > 0.f ? sqrtf(s2[rr]) : 0.f;
+    Eout[idx] = cscale(U[a * SD + pq[r]], sg);
+  }
+  if (tid == 0)
+    A.pflag[(size_t)k * K + kap] = (deficient ? TS_FLAG_RANK_DEFICIENT : 0) |
+                                   (converged ? 0 : TS_FLAG_EIG_UNCONVERGED);
+}
+
+// In-place Cholesky (lower) of the m x m Hermitian matrix in R (row stride
+// SD) by the CTA; false if a pivot was not positive (replaced by 1).
+__device__ bool chol_block(float2* R, int m, int SD, int* bad) {
+  const int tid = threadIdx.x, nth = blockDim.x;
+  if (tid == 0) *bad = 0;
+  __syncthreads();
+  for (int j = 0; j < m; ++j) {
+    if (tid == 0) {
+      float d = R[j * SD + j].x;
+      if (!(d > 0.f)) { *bad = 1; d = 1.f; }
+      R[j * SD + j] = make_float2(sqrtf(d), 0.f);
+    }
+    __syncthreads();
+    const float inv = 1.f / R[j * SD + j].x;
+    for (int i = j + 1 + tid; i < m; i += nth) R[i * SD + j] = cscale(R[i * SD + j], inv);
+    __syncthreads();
+    const int w = m - j - 1;
+    for (int t = tid; t < w * w; t += nth) {
+      const int i = j + 1 + t / w, kk = j + 1 + t % w;
+      if (kk <= i) cms(R[i * SD + kk], R[i * SD + j], cconj(R[kk * SD + j]));
+    }
+    __syncthreads();
+  }
+  return *bad == 0;
+}
+
+// R = sum of the partial covariances + sigma^2 I (+ E E* when with_e)
+__device__ void build_r(const SinrArgs& A, int i, int kap, float2* R, int SD, const float2* E,
+                        bool with_e) {
+  const int m = A.m, J = A.J, K = A.K, L = A.L;
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+    const int a = idx / m, b = idx - a * m;
+    float2 v = a == b ? make_float2(A.sigma2[i], 0.f) : cz();
+    for (int s = 0; s < J - 1; ++s)
+      v = cadd(v, A.Rpart[(((size_t)i * (J - 1) + s) * K + kap) * m * m + idx]);
+    if (with_e)
+      for (int l = 0; l < L; ++l) cmacc(v, E[a * L + l], E[b * L + l]);
+    R[a * SD + b] = v;
+  }
+  __syncthreads();
+}
+
+// y = L^{-1} e_col for the lower factor in R: thread r solves column r of E
+__device__ float forward_norm2(const float2* R, int SD, int m, const float2* E, int L, int r,
+                               float2* Y) {
+  float s = 0.f;
+  for (int a = 0; a < m; ++a) {
+    float2 v = E[a * L + r];
+    for (int b = 0; b < a; ++b) cms(v, R[a * SD + b], Y[b * L + r]);
+    v = cscale(v, 1.f / R[a * SD + a].x);
+    Y[a * L + r] = v;
+    s += cabs2(v);
+  }
+  return s;
+}
+
+template <int MG, int LT, bool SVD>
+__global__ void __launch_bounds__(kLargeThreads) k_sinr_finalize_large(const SinrArgs A) {
+  extern __shared__ __align__(16) float2 sm[];
+  const int m = A.m, L = A.L, K = A.K, J = A.J;
+  const int kap = blockIdx.x, i = blockIdx.y;
+  const int tid = threadIdx.x;
+  const int SD = m + 1;
+  float2* R = sm;                       // m x SD
+  float2* E = R + m * SD;               // m x L
+  float2* Z = E + m * L;                // m x L
+  float2* F = Z + m * L;                // L x L
+  float* xs = reinterpret_cast<float*>(F + LT * LT);   // [LT] x, [LT] a
+  int* bad = reinterpret_cast<int*>(xs + 2 * LT);
+
+  for (int idx = tid; idx < m * L; idx += blockDim.x)
+    E[idx] = A.Eserv[((size_t)i * K + kap) * m * L + idx];
+  __syncthreads();
+  // x_r = [(I + Z*Z)^{-1}]_rr with Z = L_R^{-1} E_ii
+  build_r(A, i, kap, R, SD, E, false);
+  bool ok = chol_block(R, m, SD, bad);
+  if (tid < L) forward_norm2(R, SD, m, E, L, tid, Z);
+  __syncthreads();
+  for (int idx = tid; idx < L * L; idx += blockDim.x) {
+    const int r = idx / L, s = idx - r * L;
+    float2 v = make_float2(r == s ? 1.f : 0.f, 0.f);
+    for (int a = 0; a < m; ++a) cmacc(v, Z[a * L + s], Z[a * L + r]);
+    F[r * LT + s] = v;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    // F = L_F L_F* in place (lower), L <= 8
+    for (int j = 0; j < L; ++j) {
+      float d = F[j * LT + j].x;
+      for (int t = 0; t < j; ++t) d -= cabs2(F[j * LT + t]);
+      if (!(d > 0.f)) { *bad = 1; d = 1.f; }
+      const float ljj = sqrtf(d);
+      F[j * LT + j] = make_float2(ljj, 0.f);
+      for (int r = j + 1; r < L; ++r) {
+        float2 v = F[r * LT + j];
+        for (int t = 0; t < j; ++t) cms(v, F[r * LT + t], cconj(F[j * LT + t]));
+        F[r * LT + j] = cscale(v, 1.f / ljj);
+      }
+    }
+  }
+  __syncthreads();
+  ok = ok && *bad == 0;
+  if (tid < L) {
+    // x_r = |L_F^{-1} e_r|^2 by forward substitution from row r
+    float2 y[LT];
+    float x = 0.f;
+#pragma unroll
+    for (int s = 0; s < LT; ++s) {
+      y[s] = cz();
+      if (s < tid || s >= L) continue;
+      float2 v = make_float2(s == tid ? 1.f : 0.f, 0.f);
+#pragma unroll
+      for (int t = 0; t < LT; ++t)
+        if (t >= tid && t < s) cms(v, F[s * LT + t], y[t]);
+      y[s] = cscale(v, 1.f / F[s * LT + s].x);
+      x += cabs2(y[s]);
+    }
+    xs[tid] = x;
+  }
+  __syncthreads();
+  // a_r = |L_Q^{-1} e_r|^2 with Q~ = R + E_ii E_ii*
+  build_r(A, i, kap, R, SD, E, true);
+  ok = chol_block(R, m, SD, bad) && ok;
+  if (tid < L) xs[LT + tid] = forward_norm2(R, SD, m, E, L, tid, Z);
+  __syncthreads();
+
+  uint8_t pf = 0;
+  if (SVD)
+    for (int kk = 0; kk < J; ++kk) pf |= A.pflag[(size_t)kk * K + kap];
+  const bool valid = ok && !(pf & TS_FLAG_TIMEOUT);
+  bool finite = true;
+  for (int r = 0; r < L; ++r) {
+    const float sv = valid ? xs[LT + r] / xs[r] : __int_as_float(0x7fc00000);
+    finite = finite && isfinite(sv);
+    if (tid == 0) A.sinr[((size_t)i * K + kap) * L + r] = sv;
+  }
+  if (A.flags != nullptr && tid == 0) {
+    uint8_t f = ok ? 0 : TS_FLAG_NOT_PD;
+    if (valid && !finite) f |= TS_FLAG_NONFINITE;
+    A.flags[(size_t)i * K + kap] = f | pf;
+  }
+}
+
+template <int MG, int LT>
+cudaError_t large_precoder(const SinrArgs& A, cudaStream_t s) {
+  const LargePrecPlan pl = large_prec_plan(A.m, A.n, A.L);
+  const size_t smem = (size_t)pl.total * sizeof(float2);
+  if (smem > kSmemBudget || A.Hserv == nullptr) return cudaErrorInvalidValue;
+  auto kern = k_svd_precoder_large<MG, LT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<dim3(A.K, A.J), kLargeThreads, smem, s>>>(A, pl);
+  return cudaGetLastError();
+}
+
+template <int MG, int LT>
+cudaError_t large_finalize(const SinrArgs& A, bool svd, cudaStream_t s) {
+  const size_t smem = ((size_t)A.m * (A.m + 1) + 2 * (size_t)A.m * A.L + LT * LT) * sizeof(float2) +
+                      2 * LT * sizeof(float) + 16;
+  if (smem > kSmemBudget) return cudaErrorInvalidValue;
+  auto kern = svd ? k_sinr_finalize_large<MG, LT, true> : k_sinr_finalize_large<MG, LT, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<dim3(A.K, A.J), kLargeThreads, smem, s>>>(A);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// The dispatch templates of sinr_impl.cuh, specialised for 32 and 64 rows.
+#define TS_LARGE_INSTANCES(MG, LT)                                                         \
+  template <>                                                                              \
+  cudaError_t run_precoder<MG, LT>(const SinrArgs& A, cudaStream_t s) {                    \
+    return large_precoder<MG, LT>(A, s);                                                   \
+  }                                                                                        \
+  template <>                                                                              \
+  cudaError_t run_serving<MG, LT>(const SinrArgs& A, cudaStream_t s) {                     \
+    return launch_link_wide<MG, LT, true>(A, s);                                           \
+  }                                                                                        \
+  template <>                                                                              \
+  cudaError_t run_rebuild<MG, LT>(const SinrArgs&, cudaStream_t) {                         \
+    return cudaErrorInvalidValue;                                                          \
+  }                                                                                        \
+  template <>                                                                              \
+  cudaError_t run_links<MG, LT>(const SinrArgs& A, bool svd, cudaStream_t s) {             \
+    return svd ? launch_link_wide<MG, LT, false>(A, s) : cudaErrorInvalidValue;            \
+  }                                                                                        \
+  template <>                                                                              \
+  cudaError_t run_finalize<MG, LT>(const SinrArgs& A, bool svd, cudaStream_t s) {          \
+    return large_finalize<MG, LT>(A, svd, s);                                              \
+  }
+
+TS_LARGE_INSTANCES(32, 2)
+TS_LARGE_INSTANCES(32, 4)
+TS_LARGE_INSTANCES(32, 8)
+TS_LARGE_INSTANCES(64, 2)
+TS_LARGE_INSTANCES(64, 4)
+TS_LARGE_INSTANCES(64, 8)
+#undef TS_LARGE_INSTANCES
+
+}  // namespace detail
+}  // namespace ts

@@ -132,9 +132,9 @@ __global__ void k_wait_selftest(long limit, int arrive, int* out) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b));
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   if (arrive) {
-    uint64_t state;
-    asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(b) : "memory");
-    (void)state;
+    uint64_t tok;                                   // the arrival token (unused)
+    asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(tok) : "r"(b) : "memory");
+    asm volatile("" ::"l"(tok));
   }
   out[0] = mbar_wait_limit(b, 0, limit) ? 0 : 1;
 }

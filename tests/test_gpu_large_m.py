@@ -1,0 +1,78 @@
+"""Units with more than 16 receive rows (m up to 64, as in the paper's
+(64, 512, 401) channels with m = 60): the shared-memory precoder and
+finalisation and the 32 / 64-row instances of the wide-core link kernel,
+against the FP64 oracle at the FP32 SINR tolerance of the other tests,
+with the dense comparator and several UEs per cell on the same path."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2401_09792_gb300 import synth  # noqa: E402
+from paper_2401_09792_gb300 import tuckersinr as ts  # noqa: E402
+from tests.gpu_inputs import Case, interference_condition, svd_gap  # noqa: E402
+
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    assert torch.cuda.is_available()
+
+
+def _wl(name, **kw):
+    base = dict(J=3, M=32, N=64, P=32, K=40, m=24, n=40, p=16, L=4, n_los=2, pdp_decay_s=300e-9,
+                sigma2=None, seed=21)
+    base.update(kw)
+    return dataclasses.replace(synth.MID, name=name, **base)
+
+
+def _tolerance(case, dense):
+    tol = 1e-5 + 4 * U32 * interference_condition(case, "svd", dense)
+    tol = tol + 8 * U32 / np.maximum(svd_gap(case, dense), 1e-30)[None, :]
+    return tol[:, :, None]
+
+
+CASES = {
+    "m24": _wl("large m24"),                                                   # 32-row groups
+    "m60": _wl("large m60", J=2, M=64, m=60, N=128, n=64, P=48, p=40, L=8, K=24),  # 64-row groups
+    "m33_odd": _wl("large m33", M=40, m=33, n=37, L=3, K=19),                 # odd sizes
+}
+
+
+@pytest.mark.parametrize("mode", ["paths", "dense"])
+@pytest.mark.parametrize("name", list(CASES))
+def test_large_m_svd_sinr(name, mode):
+    case = Case(CASES[name])
+    got, flags = case.gpu_sinr("svd", mode)
+    assert np.all((flags & ts.TS_FLAG_ERRORS) == 0), np.unique(flags)
+    ref = case.oracle_sinr("svd")
+    rel = np.abs(got - ref) / np.abs(ref)
+    tol = _tolerance(case, dense=False)
+    assert np.all(rel <= tol), f"max rel {rel.max():.3e} (max rel/tol {(rel / tol).max():.2f})"
+
+
+def test_large_m_dense_comparator():
+    w = _wl("large dense", M=24, m=24, N=32, n=32, P=24, p=24, L=4, K=30)
+    case = Case(w).with_channels()
+    got, flags = case.gpu_dense_sinr("svd", "paths")
+    assert np.all((flags & ts.TS_FLAG_ERRORS) == 0)
+    ref = case.oracle_dense_sinr("svd")
+    rel = np.abs(got - ref) / np.abs(ref)
+    assert np.all(rel <= _tolerance(case, dense=True)), f"max rel {rel.max():.3e}"
+
+
+def test_large_m_limits():
+    w = CASES["m24"]
+    d = ts.Dims.of(w)
+    assert ts.ts_workspace_bytes(d, ts.TS_OP_SINR_SVD) > 0
+    for op in (ts.TS_OP_SINR_MMSE, ts.TS_OP_SINR_SVD_ADJOINT, ts.TS_OP_SINR_SVD_TF32):
+        assert ts.ts_workspace_bytes(d, op) == 0
+    # more than 8 streams, or more than 64 rows, are refused
+    assert ts.ts_workspace_bytes(ts.Dims.of(dataclasses.replace(w, L=12, m=24)), ts.TS_OP_SINR_SVD) == 0
+    assert ts.ts_workspace_bytes(ts.Dims.of(dataclasses.replace(w, M=80, m=65)), ts.TS_OP_SINR_SVD) == 0
