@@ -50,13 +50,15 @@ typedef struct {
 typedef struct {
   int32_t J;          /* cells = base stations = groups                        */
   int32_t M, N, P;    /* UE antennas, BS antennas, submatrices per link         */
-  int32_t m, n, p;    /* Tucker ranks: 1 <= m <= min(M, 16), n <= min(N, 512),
-                         p <= P <= 1024.  SVD-precoded SINR (FP32): p <= 256
-                         (p > 32 or P p > 8192 runs the wide-core kernel, as
-                         the paper's compressed sizes need); wideband
-                         precoder, adjoints and tensor-core modes: p <= 32 and
-                         P p <= 8192.  Dense comparator: M, N, P as m, n, p
-                         of the matching compressed call, P <= 1024 (SVD)   */
+  int32_t m, n, p;    /* Tucker ranks: 1 <= m <= M, n <= min(N, 512),
+                         p <= P <= 1024.  SVD-precoded SINR (FP32): m <= 64
+                         (m > 16: shared-memory precoder and finalisation,
+                         L <= 8), p <= 256 (p > 32 or P p > 8192 runs the
+                         wide-core kernel, as the paper's compressed sizes
+                         need); wideband precoder, adjoints and tensor-core
+                         modes: m <= 16, p <= 32 and P p <= 8192.  Dense
+                         comparator: M, N, P as m, n, p of the matching
+                         compressed call, P <= 1024 (SVD)                   */
   int32_t K;          /* OFDM subcarriers, kappa = 0 .. K-1                      */
   int32_t L;          /* streams per UE, 1 <= L <= min(m, n)                     */
   float delta_f_hz;   /* subcarrier spacing (path-form coefficients only)      */

@@ -81,6 +81,12 @@ PAPER_U5 = Workload("paper J21 U5 M8 N256 P401 K64 r(8,130,120) L4", J=21, M=8, 
 PAPER_U10 = Workload("paper J21 U10 M8 N256 P401 K64 r(8,140,140) L4", J=21, M=8, N=256, P=401,
                      K=64, m=8, n=140, p=140, L=4, n_los=2, pdp_decay_s=300e-9, sigma2=None, U=10)
 
+# The paper's larger channels ((M, N, P) = (64, 512, 401)) with the first
+# row of its table: 5 UEs per cell and ranks (60, 230, 150); L = 8 streams.
+PAPER64_U5 = Workload("paper64 J21 U5 M64 N512 P401 K64 r(60,230,150) L8", J=21, M=64, N=512,
+                      P=401, K=64, m=60, n=230, p=150, L=8, n_los=2, pdp_decay_s=300e-9,
+                      sigma2=None, U=5)
+
 # The mid system with spatially correlated NLOS submatrices (exponential
 # correlation 0.7 across the 8 UE antennas, 0.95 across the 256 BS antennas):
 # compressible in modes 1 and 2, as measured array channels are.
@@ -88,7 +94,8 @@ MID_CORR = replace(MID, name="mid-corr J8 M8 N256 P32 K1024 r(8,32,16) L8 rho(0.
                    nlos_corr=(0.7, 0.95))
 
 WORKLOADS = {"small": SMALL, "mid": MID, "precision": PRECISION, "diff": DIFFERENTIATION,
-             "paper_u5": PAPER_U5, "paper_u10": PAPER_U10, "mid_corr": MID_CORR}
+             "paper_u5": PAPER_U5, "paper_u10": PAPER_U10, "paper64_u5": PAPER64_U5,
+             "mid_corr": MID_CORR}
 
 
 def _rng(seed: int, *path: int) -> np.random.Generator:
@@ -176,6 +183,37 @@ def orthonormal(rng: np.random.Generator, rows: int, cols: int) -> np.ndarray:
     Q, R = np.linalg.qr(Z)
     d = np.diag(R)
     return Q * (d / np.abs(d))[None, :]
+
+
+def direct_tucker_device(w: Workload, decay=(0.85, 0.97, 0.9), ue: int = 0, device="cuda") -> dict:
+    """The Tucker form of direct_tucker drawn on the device with PyTorch's
+    seeded generator (same distribution, other values), for systems whose
+    cores hold billions of entries: A [J][M][m], B [J][N][n] (shared by the
+    UE groups), C [J*J][P][p], G [J*J][p][m][n] (the library's layouts),
+    complex64 device tensors."""
+    import torch
+    gen = torch.Generator(device=device)
+
+    def seeded(*path):
+        ss = np.random.SeedSequence([int(w.seed)] + [int(x) for x in path])
+        gen.manual_seed(int(ss.generate_state(1, dtype=np.uint64)[0] >> 1))
+        return gen
+
+    def orth(batch, rows, cols, *path):
+        z = torch.randn(batch, rows, cols, dtype=torch.complex64, device=device, generator=seeded(*path))
+        q, r = torch.linalg.qr(z)
+        d = torch.diagonal(r, dim1=-2, dim2=-1)
+        return (q * (d / d.abs()).unsqueeze(-2)).contiguous()
+
+    J, nl = w.J, w.J * w.J
+    sa = torch.tensor(decay[0], device=device) ** torch.arange(w.m, device=device)
+    sb = torch.tensor(decay[1], device=device) ** torch.arange(w.n, device=device)
+    sq = torch.tensor(decay[2], device=device) ** torch.arange(w.p, device=device)
+    scale = sq[:, None, None] * sa[None, :, None] * sb[None, None, :]          # [p][m][n]
+    G = torch.randn(nl, w.p, w.m, w.n, dtype=torch.complex64, device=device,
+                    generator=seeded(8, *ue_key(ue))) * scale
+    return {"A": orth(J, w.M, w.m, 5, *ue_key(ue)), "B": orth(J, w.N, w.n, 6),
+            "C": orth(nl, w.P, w.p, 7, *ue_key(ue)), "G": G}
 
 
 def wideband_precoders(w: Workload) -> np.ndarray:
