@@ -7,7 +7,7 @@ experiments (Section 4: only the first UE of each other cell interferes, no
 intra-cell interference): UE i receives L streams from BS i; every other BS k
 interferes with the L streams it sends to its own UE.
 
-Readings of points the paper leaves open (each is restated in the design doc):
+Readings of points the paper leaves open:
   * subcarrier model: c_p(kappa) = conj(alpha_p exp(-j 2 pi kappa df tau_p)),
     kappa = 0..K-1, so that eq. (9), H = X x_3 c*, gives
     H(kappa) = sum_p alpha_p exp(-j 2 pi kappa df tau_p) X_p;
