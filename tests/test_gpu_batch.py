@@ -132,3 +132,24 @@ def test_autotuned_batch(tmp_path):
             for c, op, prec in systems if op == ts.TS_OP_SINR_SVD}
     assert keys <= {ln.split()[0] for ln in lines}
     plan.close()
+
+
+def test_batch_with_wide_and_large_instances():
+    # a batch mixing a narrow system, a wide-core one (p = 48 of P = 64) and
+    # one with 24 receive rows: each instance equals its single call
+    base = dict(n_los=2, pdp_decay_s=300e-9, sigma2=None, sigma2_range=(1e-3, 1.0))
+    ws_ = [dataclasses.replace(synth.SMALL, name="narrow", J=3, K=50, seed=201, **base),
+           dataclasses.replace(synth.SMALL, name="wide", J=3, M=8, m=8, N=64, n=24, P=64, p=48,
+                               L=4, K=70, seed=202, **base),
+           dataclasses.replace(synth.SMALL, name="large", J=2, M=32, m=24, N=64, n=40, P=32, p=16,
+                               L=4, K=33, seed=203, **base)]
+    systems = [(Case(w), ts.TS_OP_SINR_SVD, ts.TS_PREC_FP32) for w in ws_]
+    insts, outs, keep = _instances(systems)
+    plan = ts.BatchPlan(insts, ts.batch_workspace(insts))
+    plan.launch()
+    torch.cuda.synchronize()
+    for (case, op, prec), (sinr, flags), (_, Pt) in zip(systems, outs, keep):
+        got = sinr.cpu().numpy().astype(np.float64)
+        assert np.all((flags.cpu().numpy() & ts.TS_FLAG_ERRORS) == 0)
+        np.testing.assert_array_equal(got, _single(case, op, prec, Pt))
+    plan.close()
