@@ -42,6 +42,7 @@ CASES = {
     "m24": _wl("large m24"),                                                   # 32-row groups
     "m60": _wl("large m60", J=2, M=64, m=60, N=128, n=64, P=48, p=40, L=8, K=24),  # 64-row groups
     "m33_odd": _wl("large m33", M=40, m=33, n=37, L=3, K=19),                 # odd sizes
+    "one_cell_one_subcarrier": _wl("large J1 K1", J=1, K=1, L=1),             # no interferers
 }
 
 
