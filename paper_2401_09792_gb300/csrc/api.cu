@@ -700,10 +700,13 @@ int svd_multiuser_impl(const ts_dims* d, int U, const ts_coef* coef, const ts_c6
     st = run_group(u, base0 + (size_t)u * w.total, side[(u - 1) % nside]);
     if (st != TS_OK) break;
   }
-  // the caller's stream waits for every side stream
-  for (int j = 0; j < nside && e == cudaSuccess && st == TS_OK; ++j) {
-    e = cudaEventRecord(ev[1 + j], side[j]);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[1 + j], 0);
+  // the caller's stream waits for every side stream, also after a failed
+  // group (work already queued there must not outlive the caller's buffers)
+  for (int j = 0; j < nside; ++j) {
+    if (ev[1 + j] == nullptr) continue;
+    const cudaError_t er = cudaEventRecord(ev[1 + j], side[j]);
+    const cudaError_t ew = er == cudaSuccess ? cudaStreamWaitEvent(s, ev[1 + j], 0) : er;
+    if (e == cudaSuccess) e = ew;
   }
   for (int j = 0; j <= nside; ++j)
     if (ev[j] != nullptr) cudaEventDestroy(ev[j]);       // released once complete
