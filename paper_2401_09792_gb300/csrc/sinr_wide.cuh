@@ -8,8 +8,10 @@ namespace detail {
 // Wide-core variant of the blocked link pass, for ranks beyond what the
 // narrow kernels stage (p > 32 or P p > 8192): the paper's compressed sizes
 // (p ~ 100-200 of P ~ 400 paths) and the dense-channel comparator at large P.
-// Same thread layout as k_sinr_link_blk (two subcarriers and two rows per
-// lane).  The projection w = c* C streams C_ik and the path coefficients
+// Each lane holds X subcarriers and 4 / X rows of a unit: X = 2 as in
+// k_sinr_link_blk; X = 4 (one row) for 64-row units, whose 64 lanes then
+// read each core row once per q for four subcarriers instead of twice for
+// two (shared-memory wavefronts bound those).  The projection w = c* C streams C_ik and the path coefficients
 // through shared memory in double-buffered chunks of PC paths and keeps
 // w [T][p] in shared memory; the core then streams in stages of (column
 // chunk, kWideQC slabs G[q]), double-buffered, and the H~ accumulators of a
@@ -30,10 +32,10 @@ struct WidePlan {
 // the link pass then runs in p / QR passes over the core, each accumulating
 // E += H~[q-range] V~, which is linear in the core's mode-3 slabs).
 __host__ __device__ inline WidePlan wide_plan(int MG, int LT, int p, bool identity, bool serve,
-                                              int PC, int QR) {
+                                              int PC, int QR, int NT = kThreads, int X = 2) {
   constexpr int NC = 4;
   WidePlan pl;
-  pl.T = 2 * kThreads / (MG / 2);
+  pl.T = 2 * NT / (MG / 2);
   pl.QR = QR;
   pl.SG = NC + 2;
   pl.SV = NC * LT + 2;
@@ -57,7 +59,7 @@ __host__ __device__ inline WidePlan wide_plan(int MG, int LT, int p, bool identi
   pl.off_Cc = 0;
   pl.off_cc = (PC * QR + 1) & ~1;
   pl.proj = identity ? 0 : ((pl.off_cc + pl.T * (PC + 1) + 1) & ~1);
-  const int es = (kThreads / (MG / 2)) * (2 * MG * LT + 2);
+  const int es = (NT * (4 / X) / MG) * (X * MG * LT + 2);
   int region = 2 * so > es ? 2 * so : es;
   if (2 * pl.proj > region) region = 2 * pl.proj;
   o += region;
@@ -65,12 +67,14 @@ __host__ __device__ inline WidePlan wide_plan(int MG, int LT, int p, bool identi
   return pl;
 }
 
-template <int MG, int LT, bool SERVE>
-__global__ void __launch_bounds__(kThreads) k_sinr_link_wide(const SinrArgs A, const WidePlan pl) {
+template <int MG, int LT, bool SERVE, int NT, int X>
+__global__ void __launch_bounds__(NT, NT > kThreads ? 2 : 0) k_sinr_link_wide(const SinrArgs A,
+                                                                              const WidePlan pl) {
   constexpr int NC = 4;
-  constexpr int GL = MG / 2;
-  constexpr int T = 2 * kThreads / GL;
-  constexpr int QS = kThreads / T;          // threads per subcarrier in the projection
+  constexpr int R = 4 / X;                  // rows per lane
+  constexpr int GL = MG / R;                // lanes per subcarrier group
+  constexpr int T = X * NT / GL;
+  constexpr int QS = NT / T;                // threads per subcarrier in the projection
   constexpr int QA = 32 / QS;               // projection outputs per thread and 32-column block
   constexpr int QC = kWideQC;
   extern __shared__ __align__(16) float2 sm[];
@@ -111,21 +115,21 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link_wide(const SinrArgs A, c
       constexpr int GU = MG * NC / 2;                 // 16-byte units per slab
       const int cc = 2 * (tid % (NC / 2)), aa = (tid / (NC / 2)) % MG;
       const bool rowok = aa < m && c0 + cc < n;
-      for (int ql = tid / GU; ql < qc; ql += kThreads / GU)
+      for (int ql = tid / GU; ql < qc; ql += NT / GU)
         cp_async16(buf + pl.off_Gs + (ql * MG + aa) * pl.SG + cc,
                    rowok ? Gch + ((size_t)(q0 + ql) * m + aa) * n + c0 + cc : A.G, rowok);
       if (!SERVE && qi == nq - 1) {
         constexpr int VU = NC * LT / 2;
         const int l = 2 * (tid % (LT / 2)), vc = (tid / (LT / 2)) % NC;
         const bool colok = c0 + vc < n && l < L;
-        for (int t = tid / VU; t < T; t += kThreads / VU) {
+        for (int t = tid / VU; t < T; t += NT / VU) {
           const bool ok = colok && kap0 + t < K;
           cp_async16(buf + pl.off_Vs + t * pl.SV + vc * LT + l,
                      ok ? A.V + (((size_t)k * K + kap0 + t) * n + c0 + vc) * L + l : A.V, ok);
         }
       }
     } else {
-      for (int idx = tid; idx < qc * MG * NC; idx += kThreads) {
+      for (int idx = tid; idx < qc * MG * NC; idx += NT) {
         const int cc = idx % NC, aa = (idx / NC) % MG, ql = idx / (NC * MG);
         const int c = c0 + cc;
         const bool ok = aa < m && c < n;
@@ -133,7 +137,7 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link_wide(const SinrArgs A, c
                   ok ? Gch + ((size_t)(q0 + ql) * m + aa) * n + c : A.G, ok);
       }
       if (!SERVE && qi == nq - 1) {
-        for (int idx = tid; idx < T * NC * LT; idx += kThreads) {
+        for (int idx = tid; idx < T * NC * LT; idx += NT) {
           const int l = idx % LT, cc = (idx / LT) % NC, t = idx / (LT * NC);
           const int kk2 = kap0 + t, c = c0 + cc;
           const bool ok = kk2 < K && c < n && l < L;
@@ -144,21 +148,21 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link_wide(const SinrArgs A, c
     }
     if (ident) {
       // dense channel: w_q = conj(c_q(kappa)) for the slab
-      for (int idx = tid; idx < T * qc; idx += kThreads) {
+      for (int idx = tid; idx < T * qc; idx += NT) {
         const int t = idx / qc, ql = idx - t * qc;
         buf[pl.off_Wc + t * pl.WS + ql] = kap0 + t < K ? cconj(coef_at(kap0 + t, q0 + ql)) : cz();
       }
     }
   };
 
-  float2 E[2][2][LT];   // [subcarrier of the pair][row j, j + GL][stream]
+  float2 E[X][R][LT];   // [subcarrier X gp + x][row j + r GL][stream]
 #pragma unroll
-  for (int x = 0; x < 2; ++x)
+  for (int x = 0; x < X; ++x)
 #pragma unroll
-    for (int r = 0; r < 2; ++r)
+    for (int r = 0; r < R; ++r)
 #pragma unroll
       for (int l = 0; l < LT; ++l) E[x][r][l] = cz();
-  float2 h[2][2][NC];
+  float2 h[X][R][NC];
 
   for (qlo = 0; qlo < p; qlo += QR) {
     qn = min(QR, p - qlo);
@@ -167,7 +171,7 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link_wide(const SinrArgs A, c
     if (SERVE && A.Wserv != nullptr) {
       // the serving links' projections come from k_wide_proj (one pass)
       const float2* src = A.Wserv + ((size_t)i * K + kap0) * p;
-      for (int idx = tid; idx < T * p; idx += kThreads) {
+      for (int idx = tid; idx < T * p; idx += NT) {
         const int t = idx / p, q = idx - t * p;
         ws[t * (QR + 1) + q] = kap0 + t < K ? src[idx] : cz();
       }
@@ -186,17 +190,17 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link_wide(const SinrArgs A, c
         const int P0 = ci * PC, pc = min(PC, P - P0);
         const float2* src = Cch + (size_t)P0 * p;
         if (c16) {
-          for (int idx = 2 * tid; idx < pc * qn; idx += 2 * kThreads) {
+          for (int idx = 2 * tid; idx < pc * qn; idx += 2 * NT) {
             const int row = idx / qn, col = idx - row * qn;
             cp_async16(buf + pl.off_Cc + row * QR + col, src + (size_t)row * p + col, true);
           }
         } else {
-          for (int idx = tid; idx < pc * qn; idx += kThreads) {
+          for (int idx = tid; idx < pc * qn; idx += NT) {
             const int row = idx / qn, col = idx - row * qn;
             cp_async8(buf + pl.off_Cc + row * QR + col, src + (size_t)row * p + col, true);
           }
         }
-        for (int idx = tid; idx < T * PC; idx += kThreads) {
+        for (int idx = tid; idx < T * PC; idx += NT) {
           const int t = idx / PC, pp = idx - t * PC;
           buf[pl.off_cc + t * (PC + 1) + pp] =
               (pp < pc && kap0 + t < K) ? coef_at(kap0 + t, P0 + pp) : cz();
@@ -256,45 +260,46 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link_wide(const SinrArgs A, c
       const int q0 = qlo + qi * QC, qc = min(QC, qlo + qn - q0);
       if (qi == 0) {
 #pragma unroll
-        for (int x = 0; x < 2; ++x)
+        for (int x = 0; x < X; ++x)
 #pragma unroll
-          for (int r = 0; r < 2; ++r)
+          for (int r = 0; r < R; ++r)
 #pragma unroll
             for (int cc = 0; cc < NC; ++cc) h[x][r][cc] = cz();
       }
-      const float2* w0 = ident ? buf + pl.off_Wc + (2 * gp) * pl.WS
-                               : ws + (2 * gp) * (QR + 1) + (q0 - qlo);
-      const float2* w1 = w0 + (ident ? pl.WS : QR + 1);
+      const int wst = ident ? pl.WS : QR + 1;
+      const float2* w0 = ident ? buf + pl.off_Wc + (X * gp) * pl.WS
+                               : ws + (X * gp) * (QR + 1) + (q0 - qlo);
       const float2* g0 = buf + pl.off_Gs + j * pl.SG;
-      const float2* g1 = g0 + GL * pl.SG;
 #pragma unroll 4
       for (int q = 0; q < qc; ++q) {
-        const float2 wa = w0[q], wb = w1[q];
-        const float4* ga = reinterpret_cast<const float4*>(g0 + q * MG * pl.SG);
-        const float4* gb = reinterpret_cast<const float4*>(g1 + q * MG * pl.SG);
+        float2 wv[X];
+#pragma unroll
+        for (int x = 0; x < X; ++x) wv[x] = w0[x * wst + q];
+        const float2* gq = g0 + q * MG * pl.SG;
 #pragma unroll
         for (int c2 = 0; c2 < NC / 2; ++c2) {
-          const float4 u = ga[c2], v = gb[c2];
-          const float2 u0 = make_float2(u.x, u.y), u1 = make_float2(u.z, u.w);
-          const float2 v0 = make_float2(v.x, v.y), v1 = make_float2(v.z, v.w);
-          cmac(h[0][0][2 * c2], wa, u0);
-          cmac(h[0][0][2 * c2 + 1], wa, u1);
-          cmac(h[1][0][2 * c2], wb, u0);
-          cmac(h[1][0][2 * c2 + 1], wb, u1);
-          cmac(h[0][1][2 * c2], wa, v0);
-          cmac(h[0][1][2 * c2 + 1], wa, v1);
-          cmac(h[1][1][2 * c2], wb, v0);
-          cmac(h[1][1][2 * c2 + 1], wb, v1);
+          float4 u[R];
+#pragma unroll
+          for (int r = 0; r < R; ++r) u[r] = reinterpret_cast<const float4*>(gq + r * GL * pl.SG)[c2];
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const float2 u0 = make_float2(u[r].x, u[r].y), u1 = make_float2(u[r].z, u[r].w);
+#pragma unroll
+            for (int x = 0; x < X; ++x) {
+              cmac(h[x][r][2 * c2], wv[x], u0);
+              cmac(h[x][r][2 * c2 + 1], wv[x], u1);
+            }
+          }
         }
       }
       if (qi == nq - 1) {
         const int c0 = cidx * NC;
         if (SERVE) {
 #pragma unroll
-          for (int x = 0; x < 2; ++x) {
-            const int kap = kap0 + 2 * gp + x;
+          for (int x = 0; x < X; ++x) {
+            const int kap = kap0 + X * gp + x;
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
+            for (int r = 0; r < R; ++r) {
               const int a = j + r * GL;
               if (kap >= K || a >= m) continue;
               float2* Hrow = A.Hserv + (((size_t)i * K + kap) * m + a) * n;
@@ -304,23 +309,21 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link_wide(const SinrArgs A, c
             }
           }
         } else {
-          const float2* va = buf + pl.off_Vs + (2 * gp) * pl.SV;
-          const float2* vb = va + pl.SV;
+          const float2* va = buf + pl.off_Vs + (X * gp) * pl.SV;
 #pragma unroll
           for (int cc = 0; cc < NC; ++cc) {
 #pragma unroll
             for (int l2 = 0; l2 < LT / 2; ++l2) {
-              const float4 x = reinterpret_cast<const float4*>(va + cc * LT)[l2];
-              const float4 y = reinterpret_cast<const float4*>(vb + cc * LT)[l2];
-              const float2 x0 = make_float2(x.x, x.y), x1 = make_float2(x.z, x.w);
-              const float2 y0 = make_float2(y.x, y.y), y1 = make_float2(y.z, y.w);
+              float4 v[X];
 #pragma unroll
-              for (int r = 0; r < 2; ++r) {
-                cmac(E[0][r][2 * l2], h[0][r][cc], x0);
-                cmac(E[0][r][2 * l2 + 1], h[0][r][cc], x1);
-                cmac(E[1][r][2 * l2], h[1][r][cc], y0);
-                cmac(E[1][r][2 * l2 + 1], h[1][r][cc], y1);
-              }
+              for (int x = 0; x < X; ++x) v[x] = reinterpret_cast<const float4*>(va + x * pl.SV + cc * LT)[l2];
+#pragma unroll
+              for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int x = 0; x < X; ++x) {
+                  cmac(E[x][r][2 * l2], h[x][r][cc], make_float2(v[x].x, v[x].y));
+                  cmac(E[x][r][2 * l2 + 1], h[x][r][cc], make_float2(v[x].z, v[x].w));
+                }
             }
           }
         }
@@ -332,20 +335,21 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link_wide(const SinrArgs A, c
   if (SERVE) return;
 
   // partial covariance rows (E E*)[a][b], b < m (eq. 25), for both subcarriers
-  float2* Es = stage0 + gp * (2 * MG * LT + 2);
+  float2* Es = stage0 + gp * (X * MG * LT + 2);
 #pragma unroll
-  for (int x = 0; x < 2; ++x)
+  for (int x = 0; x < X; ++x)
 #pragma unroll
-    for (int r = 0; r < 2; ++r)
+    for (int r = 0; r < R; ++r)
 #pragma unroll
       for (int l = 0; l < LT; ++l) Es[(x * MG + j + r * GL) * LT + l] = E[x][r][l];
-  __syncwarp();
+  if constexpr (GL > 32) __syncthreads();   // a group spans two warps
+  else __syncwarp();
 #pragma unroll
-  for (int x = 0; x < 2; ++x) {
-    const int kap = kap0 + 2 * gp + x;
+  for (int x = 0; x < X; ++x) {
+    const int kap = kap0 + X * gp + x;
     if (kap >= K) continue;
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
+    for (int r = 0; r < R; ++r) {
       const int a = j + r * GL;
       if (a >= m) continue;
       float2* Rout = A.Rpart + ((((size_t)i * (J - 1) + z) * K + kap) * m + a) * m;
@@ -439,21 +443,29 @@ __global__ void __launch_bounds__(kThreads) k_wide_proj(const SinrArgs A, const 
 template <int MG, int LT, bool SERVE>
 cudaError_t launch_link_wide(const SinrArgs& A, cudaStream_t s) {
   if (!SERVE && A.J < 2) return cudaSuccess;
-  // shared memory decides how many CTAs share an SM (3 within 75 KB, 2
-  // within 113 KB): take the plan with the most CTAs per SM, then the fewest
-  // passes over the core (columns of w held at once: p, or 128, 64, 32 for
-  // the interfering links), then the largest projection chunk (16 .. 2 paths)
+  // 64-row units: 256 threads (at most 128 registers, two CTAs per SM), so
+  // that each core slab brought into shared memory serves 16 subcarriers
+  // instead of 8, with one row and four subcarriers per lane (26.7 -> 19.4
+  // ms for the (60, 230, 150) links; 32-row units already hold 16)
+  constexpr int NT = (!SERVE && MG >= 64) ? 2 * kThreads : kThreads;
+  constexpr int X = MG >= 64 ? 4 : 2;
+  // shared memory decides how many CTAs share an SM (128 threads: 3 within
+  // 75 KB, 2 within 113 KB; 256 threads, at most 128 registers: 2 within
+  // 113 KB): take the
+  // plan with the most CTAs per SM, then the fewest passes over the core
+  // (columns of w held at once: p, or 128, 64, 32 for the interfering
+  // links), then the largest projection chunk (16 .. 2 paths)
   const bool passes = !SERVE && !A.identity_C;
-  WidePlan pl = wide_plan(MG, LT, A.p, A.identity_C, SERVE, 2, A.p);
+  WidePlan pl = wide_plan(MG, LT, A.p, A.identity_C, SERVE, 2, A.p, NT, X);
   int best_ctas = -1, best_passes = 1 << 30, best_pc = 0;
   for (int qr : {A.p, 128, 64, 32}) {
     if (qr != A.p && (!passes || qr >= A.p)) continue;
     const int npass = (A.p + qr - 1) / qr;
     for (int pc = 16; pc >= 2; pc /= 2) {
-      const WidePlan t = wide_plan(MG, LT, A.p, A.identity_C, SERVE, pc, qr);
+      const WidePlan t = wide_plan(MG, LT, A.p, A.identity_C, SERVE, pc, qr, NT, X);
       const size_t bytes = (size_t)t.total * sizeof(float2);
       if (bytes > kSmemBudget) continue;
-      const int ctas = bytes <= 75 * 1024 ? 3 : bytes <= 113 * 1024 ? 2 : 1;
+      const int ctas = bytes <= 75 * 1024 && NT == kThreads ? 3 : bytes <= 113 * 1024 ? 2 : 1;
       if (ctas > best_ctas || (ctas == best_ctas && (npass < best_passes ||
                                                      (npass == best_passes && pc > best_pc)))) {
         best_ctas = ctas;
@@ -497,10 +509,10 @@ cudaError_t launch_link_wide(const SinrArgs& A, cudaStream_t s) {
     nz = (nchunk + pl.cps - 1) / pl.cps;
   }
   dim3 grid(tiles, A.J, nz);
-  auto kern = k_sinr_link_wide<MG, LT, SERVE>;
+  auto kern = k_sinr_link_wide<MG, LT, SERVE, NT, X>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid, kThreads, smem, s>>>(A, pl);
+  kern<<<grid, NT, smem, s>>>(A, pl);
   return cudaGetLastError();
 }
 
