@@ -42,6 +42,9 @@ CASES = {
     "m24": _wl("large m24"),                                                   # 32-row groups
     "m60": _wl("large m60", J=2, M=64, m=60, N=128, n=64, P=48, p=40, L=8, K=24),  # 64-row groups
     "m33_odd": _wl("large m33", M=40, m=33, n=37, L=3, K=19),                 # odd sizes
+    # 64-row groups, rows masked, odd n and L, three subcarrier tiles of 16
+    # with a ragged last one (256 threads, four subcarriers per lane)
+    "m49_odd": _wl("large m49", M=56, m=49, N=64, n=45, P=40, p=36, L=3, K=37),
     "one_cell_one_subcarrier": _wl("large J1 K1", J=1, K=1, L=1),             # no interferers
 }
 
@@ -58,8 +61,9 @@ def test_large_m_svd_sinr(name, mode):
     assert np.all(rel <= tol), f"max rel {rel.max():.3e} (max rel/tol {(rel / tol).max():.2f})"
 
 
-def test_large_m_dense_comparator():
-    w = _wl("large dense", M=24, m=24, N=32, n=32, P=24, p=24, L=4, K=30)
+@pytest.mark.parametrize("M", [24, 64])
+def test_large_m_dense_comparator(M):
+    w = _wl(f"large dense M{M}", M=M, m=M, N=32, n=32, P=24 if M < 64 else 40, p=24, L=4, K=30)
     case = Case(w).with_channels()
     got, flags = case.gpu_dense_sinr("svd", "paths")
     assert np.all((flags & ts.TS_FLAG_ERRORS) == 0)
