@@ -191,7 +191,8 @@ cudaError_t run_refine(const SinrArgs& A, bool svd, cudaStream_t s) {
 
 cudaError_t launch_sinr_refine(const SinrArgs& a, bool svd, cudaStream_t s) {
   const int MG = a.m <= 2 ? 2 : a.m <= 4 ? 4 : a.m <= 8 ? 8 : 16;
-  const int LT = a.L <= 2 ? 2 : a.L <= 4 ? 4 : a.L <= 8 ? 8 : 16;
+  // the stream tiles of the SINR kernels: 16-lane groups start at 4
+  const int LT = a.L <= 2 && MG < 16 ? 2 : a.L <= 4 ? 4 : a.L <= 8 ? 8 : 16;
   switch (MG * 100 + LT) {
     case 202: return run_refine<2, 2>(a, svd, s);
     case 402: return run_refine<4, 2>(a, svd, s);

@@ -125,7 +125,14 @@ __global__ void __launch_bounds__(kLargeThreads) k_svd_precoder_large(const Sinr
   __syncthreads();
 
   // 2. cyclic Jacobi, round-robin pairs (the padding index DE-1 = m when m
-  // is odd pairs with nothing), to relative off-diagonal norm ~5e-7
+  // is odd pairs with nothing), to relative off-diagonal norm ~5e-7.  Pairs
+  // whose diagonal entries are both below m u of the trace lie in the
+  // numerical null space of the FP32 Gram (rank n < m, or weaker): their
+  // rotations only mix null vectors among themselves, at rounding level,
+  // and leave the kept eigenvectors alone, so they are neither rotated nor
+  // counted (otherwise a null cluster of rank-deficient links converges
+  // linearly from rounding noise and exhausts the sweeps).
+  const float eps_null = (float)m * 5.9604645e-8f;     // m 2^-24 of the unit trace
   bool converged = false;
   for (int sweep = 0; sweep <= 16; ++sweep) {
     float off = 0.f, tot = 0.f;
@@ -133,7 +140,7 @@ __global__ void __launch_bounds__(kLargeThreads) k_svd_precoder_large(const Sinr
       const int a = idx / m, b = idx - a * m;
       const float v = cabs2(S[a * SD + b]);
       tot += v;
-      if (a != b) off += v;
+      if (a != b && fmaxf(S[a * SD + a].x, S[b * SD + b].x) > eps_null) off += v;
     }
     off = block_sum(off, red);
     tot = block_sum(tot, red);
@@ -150,7 +157,7 @@ __global__ void __launch_bounds__(kLargeThreads) k_svd_precoder_large(const Sinr
           const float app = S[p * SD + p].x, aqq = S[q * SD + q].x;
           const float2 bpq = S[p * SD + q];
           const float ab = sqrtf(cabs2(bpq));
-          if (ab > 1e-30f && ab > 1e-9f * sqrtf(fabsf(app * aqq))) {
+          if (ab > 1e-30f && ab > 1e-9f * sqrtf(fabsf(app * aqq)) && fmaxf(app, aqq) > eps_null) {
             const float tau = (aqq - app) / (2.f * ab);
             const float tt = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
             c = 1.f / sqrtf(fmaf(tt, tt, 1.f));

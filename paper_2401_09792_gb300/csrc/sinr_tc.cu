@@ -613,20 +613,21 @@ cudaError_t launch_tc_prec(const SinrArgs& A, int prec, const unsigned char* pre
 }
 
 inline int tc_mg(int m) { return m <= 2 ? 2 : m <= 4 ? 4 : m <= 8 ? 8 : 16; }
-inline int tc_lt(int L) { return L <= 2 ? 2 : L <= 4 ? 4 : 8; }
+// stream tiles as in the FP32 kernels: 16-lane groups start at 4
+inline int tc_lt(int m, int L) { return L <= 2 && m <= 8 ? 2 : L <= 4 ? 4 : 8; }
 
 }  // namespace
 }  // namespace detail
 
 bool tc_supported(int m, int L, int p) {
-  const int MG = detail::tc_mg(m), LT = detail::tc_lt(L);
+  const int MG = detail::tc_mg(m), LT = detail::tc_lt(m, L);
   if (m > 16 || L > 8 || LT > MG || p > 32) return false;
   const detail::TcPlan tp = detail::tc_plan(MG, LT, 512, p, TS_PREC_BF16X2);
   return tp.smem <= 227 * 1024;
 }
 
 size_t tc_prep_bytes(int J, int m, int L, int n, int p, int K, int prec) {
-  const detail::TcPlan tp = detail::tc_plan(detail::tc_mg(m), detail::tc_lt(L), n, p, prec);
+  const detail::TcPlan tp = detail::tc_plan(detail::tc_mg(m), detail::tc_lt(m, L), n, p, prec);
   const size_t tiles = (size_t)(K + detail::kTile - 1) / detail::kTile;
   return tp.prep_bytes_per_link * (size_t)J * J + tp.a_bytes_per_tile * tiles * J * (J - 1);
 }
@@ -634,14 +635,14 @@ size_t tc_prep_bytes(int J, int m, int L, int n, int p, int K, int prec) {
 cudaError_t launch_core_prep(const SinrArgs& a, int prec, void* prep, cudaStream_t s) {
   using namespace detail;
   unsigned char* pp = static_cast<unsigned char*>(prep);
-  return prec == TS_PREC_TF32 ? launch_prep<TS_PREC_TF32>(a, tc_mg(a.m), tc_lt(a.L), pp, s)
-                              : launch_prep<TS_PREC_BF16X2>(a, tc_mg(a.m), tc_lt(a.L), pp, s);
+  return prec == TS_PREC_TF32 ? launch_prep<TS_PREC_TF32>(a, tc_mg(a.m), tc_lt(a.m, a.L), pp, s)
+                              : launch_prep<TS_PREC_BF16X2>(a, tc_mg(a.m), tc_lt(a.m, a.L), pp, s);
 }
 
 cudaError_t launch_sinr_links_tc(const SinrArgs& a, int prec, const void* prep, cudaStream_t s) {
   using namespace detail;
   const unsigned char* pp = static_cast<const unsigned char*>(prep);
-  switch (tc_mg(a.m) * 100 + tc_lt(a.L)) {
+  switch (tc_mg(a.m) * 100 + tc_lt(a.m, a.L)) {
     case 202: return launch_tc_prec<2, 2>(a, prec, pp, s);
     case 402: return launch_tc_prec<4, 2>(a, prec, pp, s);
     case 404: return launch_tc_prec<4, 4>(a, prec, pp, s);

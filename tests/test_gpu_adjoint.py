@@ -68,11 +68,13 @@ def _gpu_adjoint(case, precoder, ds):
 
 
 @pytest.mark.parametrize("precoder", ["svd", "mmse"])
-@pytest.mark.parametrize("shape", ["small", "odd"])
+@pytest.mark.parametrize("shape", ["small", "odd", "m12_L2"])
 def test_adjoint_matches_oracle(precoder, shape):
     base = workload(synth.SMALL, K=16)
     if shape == "odd":
         base = workload(synth.SMALL, J=3, M=3, m=3, n=7, N=12, P=5, p=3, L=2, K=9)
+    if shape == "m12_L2":                   # 16-lane groups with two streams
+        base = workload(synth.SMALL, J=2, M=16, m=12, N=24, n=12, P=6, p=4, L=2, K=8)
     case = Case(base)
     ds = _dsinr(base)
     ref = AD.tucker_sinr_vjp(case.tk["G"], case.tk["C"], case.coef, case.s2, base.L, ds, precoder,

@@ -45,6 +45,8 @@ CASES = {
     # 64-row groups, rows masked, odd n and L, three subcarrier tiles of 16
     # with a ragged last one (256 threads, four subcarriers per lane)
     "m49_odd": _wl("large m49", M=56, m=49, N=64, n=45, P=40, p=36, L=3, K=37),
+    # more rows than columns: the Gram of every serving link has rank n < m
+    "m40_n12": _wl("large m40 n12", M=40, m=40, N=16, n=12, L=4),
     "one_cell_one_subcarrier": _wl("large J1 K1", J=1, K=1, L=1),             # no interferers
 }
 

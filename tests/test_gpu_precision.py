@@ -122,6 +122,7 @@ EDGE = {
     "ragged_K": dict(K=200),                      # one full tile of 128 and a ragged one
     "odd_m_n_p": dict(J=3, M=3, m=3, n=7, N=12, P=5, p=3, L=2, K=9),
     "m16_L8": dict(J=3, M=16, m=16, L=8, N=80, n=64, P=40, p=32, K=130),
+    "m12_L2": dict(J=3, M=16, m=12, L=2, N=40, n=24, P=10, p=5, K=33),   # 16-lane groups, L <= 2
     "m2": dict(M=2, m=2, L=2, n=8, N=16, K=64),
     "single_cell": dict(J=1, K=5),
 }

@@ -81,11 +81,12 @@ def test_ill_conditioned_units_are_refined(precoder):
 
 
 @pytest.mark.parametrize("precoder", ["svd", "mmse"])
-@pytest.mark.parametrize("shape", ["small", "odd", "m16"])
+@pytest.mark.parametrize("shape", ["small", "odd", "m16", "m12_L2"])
 def test_refining_every_unit_matches_oracle(precoder, shape):
     w = {"small": synth.SMALL,
          "odd": workload(synth.SMALL, J=3, M=3, m=3, n=7, N=12, P=5, p=3, L=2, K=9),
-         "m16": workload(synth.SMALL, J=2, M=16, m=16, L=8, N=40, n=24, P=10, p=5, K=33)}[shape]
+         "m16": workload(synth.SMALL, J=2, M=16, m=16, L=8, N=40, n=24, P=10, p=5, K=33),
+         "m12_L2": workload(synth.SMALL, J=2, M=16, m=12, L=2, N=40, n=24, P=10, p=5, K=33)}[shape]
     case = Case(w)
     got, flags = _run(case, precoder, 0.0)
     assert np.all(flags == ts.TS_FLAG_REFINED)

@@ -78,6 +78,9 @@ EDGE = {
     "m2_full": dict(M=2, m=2, L=2, n=2, N=8),
     "max_m16": dict(J=2, M=16, m=16, L=16, N=24, n=16, P=6, p=3, K=40),
     "m16_L8_n24": dict(J=3, M=16, m=12, L=8, N=40, n=24, P=10, p=5, K=33),
+    # more rows than columns: the m x m Gram of every link has rank n < m
+    "m_above_n": dict(M=16, m=16, N=8, n=4, L=2),
+    "m8_n2": dict(M=8, m=8, N=4, n=2, L=1),
 }
 
 
