@@ -133,6 +133,7 @@ __global__ void __launch_bounds__(kLargeThreads) k_svd_precoder_large(const Sinr
   // counted (otherwise a null cluster of rank-deficient links converges
   // linearly from rounding noise and exhausts the sweeps).
   const float eps_null = (float)m * 5.9604645e-8f;     // m 2^-24 of the unit trace
+  const int lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
   bool converged = false;
   for (int sweep = 0; sweep <= 16; ++sweep) {
     float off = 0.f, tot = 0.f;
@@ -146,13 +147,18 @@ __global__ void __launch_bounds__(kLargeThreads) k_svd_precoder_large(const Sinr
     tot = block_sum(tot, red);
     converged = off <= 2.3e-13f * tot;
     if (converged || sweep == 16) break;
+    // one step: the DE/2 disjoint pairs of the round-robin ordering; their
+    // rotations by one thread each, then the rows of S and the columns of S
+    // and U, lane j of every warp on pair j (its rotation loaded once) and
+    // the warps over the columns (rows), without index divisions
     for (int step = 0; step < DE - 1; ++step) {
       if (tid < DE / 2) {
         const int j = tid;
         int p = j == 0 ? step : (step + j) % (DE - 1);
         int q = j == 0 ? DE - 1 : (step - j + DE - 1) % (DE - 1);
-        float c = 1.f, s = 0.f;
+        float c = 1.f, sn = 0.f;
         float2 e = make_float2(1.f, 0.f);
+        bool act = false;
         if (p < m && q < m) {
           const float app = S[p * SD + p].x, aqq = S[q * SD + q].x;
           const float2 bpq = S[p * SD + q];
@@ -161,56 +167,61 @@ __global__ void __launch_bounds__(kLargeThreads) k_svd_precoder_large(const Sinr
             const float tau = (aqq - app) / (2.f * ab);
             const float tt = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
             c = 1.f / sqrtf(fmaf(tt, tt, 1.f));
-            s = tt * c;
+            sn = tt * c;
             e = cscale(bpq, 1.f / ab);
+            act = true;
           }
-        } else {
-          p = q = -1;
         }
-        rot[j] = make_float2(c, s);
+        rot[j] = make_float2(c, sn);
         rot[DE / 2 + j] = e;
-        pq[2 * j] = p;
+        pq[2 * j] = act ? p : -1;
         pq[2 * j + 1] = q;
       }
       __syncthreads();
-      // rows: S <- J* S (row p' = c p - s e q, row q' = s conj(e) p + c q)
-      for (int t = tid; t < (DE / 2) * m; t += nth) {
-        const int j = t / m, col = t - j * m;
-        const int p = pq[2 * j], q = pq[2 * j + 1];
-        if (p < 0) continue;
+      const int j = lane;
+      const bool mine = j < DE / 2 && pq[2 * j] >= 0;
+      int p = 0, q = 0;
+      float c = 1.f;
+      float2 se = cz(), sec = cz();
+      if (mine) {
+        p = pq[2 * j];
+        q = pq[2 * j + 1];
         const float2 cs = rot[j], e = rot[DE / 2 + j];
-        const float2 x = S[p * SD + col], y = S[q * SD + col];
-        float2 nx = cscale(x, cs.x), ny = cscale(y, cs.x);
-        cms(nx, cscale(e, cs.y), y);
-        cmac(ny, cscale(cconj(e), cs.y), x);
-        S[p * SD + col] = nx;
-        S[q * SD + col] = ny;
+        c = cs.x;
+        se = cscale(e, cs.y);
+        sec = cscale(cconj(e), cs.y);
       }
+      // rows: S <- J* S (row p' = c p - s e q, row q' = s conj(e) p + c q)
+      if (mine)
+        for (int col = warp; col < m; col += nwarp) {
+          const float2 x = S[p * SD + col], y = S[q * SD + col];
+          float2 nx = cscale(x, c), ny = cscale(y, c);
+          cms(nx, se, y);
+          cmac(ny, sec, x);
+          S[p * SD + col] = nx;
+          S[q * SD + col] = ny;
+        }
       __syncthreads();
       // columns: S <- S J, U <- U J
-      for (int t = tid; t < (DE / 2) * m; t += nth) {
-        const int j = t / m, row = t - j * m;
-        const int p = pq[2 * j], q = pq[2 * j + 1];
-        if (p < 0) continue;
-        const float2 cs = rot[j], e = rot[DE / 2 + j];
-        const float2 se = cscale(e, cs.y), sec = cscale(cconj(e), cs.y);
-        {
-          const float2 x = S[row * SD + p], y = S[row * SD + q];
-          float2 nx = cscale(x, cs.x), ny = cscale(y, cs.x);
-          cms(nx, sec, y);
-          cmac(ny, se, x);
-          S[row * SD + p] = nx;
-          S[row * SD + q] = ny;
+      if (mine)
+        for (int row = warp; row < m; row += nwarp) {
+          {
+            const float2 x = S[row * SD + p], y = S[row * SD + q];
+            float2 nx = cscale(x, c), ny = cscale(y, c);
+            cms(nx, sec, y);
+            cmac(ny, se, x);
+            S[row * SD + p] = nx;
+            S[row * SD + q] = ny;
+          }
+          {
+            const float2 x = U[row * SD + p], y = U[row * SD + q];
+            float2 nx = cscale(x, c), ny = cscale(y, c);
+            cms(nx, sec, y);
+            cmac(ny, se, x);
+            U[row * SD + p] = nx;
+            U[row * SD + q] = ny;
+          }
         }
-        {
-          const float2 x = U[row * SD + p], y = U[row * SD + q];
-          float2 nx = cscale(x, cs.x), ny = cscale(y, cs.x);
-          cms(nx, sec, y);
-          cmac(ny, se, x);
-          U[row * SD + p] = nx;
-          U[row * SD + q] = ny;
-        }
-      }
       __syncthreads();
     }
   }

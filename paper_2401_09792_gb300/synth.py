@@ -87,6 +87,10 @@ PAPER64_U5 = Workload("paper64 J21 U5 M64 N512 P401 K64 r(60,230,150) L8", J=21,
                       P=401, K=64, m=60, n=230, p=150, L=8, n_los=2, pdp_decay_s=300e-9,
                       sigma2=None, U=5)
 
+# The same channels and ranks with 8 cells: a few GB on the device, the
+# size for profiling the 64-row kernels.
+PAPER64_J8 = replace(PAPER64_U5, name="paper64-j8 J8 U5 M64 N512 P401 K64 r(60,230,150) L8", J=8)
+
 # The mid system with spatially correlated NLOS submatrices (exponential
 # correlation 0.7 across the 8 UE antennas, 0.95 across the 256 BS antennas):
 # compressible in modes 1 and 2, as measured array channels are.
@@ -95,7 +99,7 @@ MID_CORR = replace(MID, name="mid-corr J8 M8 N256 P32 K1024 r(8,32,16) L8 rho(0.
 
 WORKLOADS = {"small": SMALL, "mid": MID, "precision": PRECISION, "diff": DIFFERENTIATION,
              "paper_u5": PAPER_U5, "paper_u10": PAPER_U10, "paper64_u5": PAPER64_U5,
-             "mid_corr": MID_CORR}
+             "paper64_j8": PAPER64_J8, "mid_corr": MID_CORR}
 
 
 def _rng(seed: int, *path: int) -> np.random.Generator:
