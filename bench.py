@@ -128,11 +128,19 @@ KERNEL_SOURCES = {
 }
 
 
+def _code_only(text: str) -> str:
+    """C++/CUDA source without comments, trailing blanks and empty lines: a
+    comment edit leaves a kernel's hash (and its captured profile) valid."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(ln.rstrip() for ln in text.splitlines() if ln.strip())
+
+
 def kernel_source_hash(kernel: str) -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2401_09792_gb300", "csrc")
     for name in KERNEL_SOURCES[kernel]:
-        h.update(open(os.path.join(csrc, name), "rb").read())
+        h.update(_code_only(open(os.path.join(csrc, name)).read()).encode())
     return h.hexdigest()[:16]
 
 

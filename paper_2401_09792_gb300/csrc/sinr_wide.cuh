@@ -10,10 +10,11 @@ namespace detail {
 // (p ~ 100-200 of P ~ 400 paths) and the dense-channel comparator at large P.
 // Each lane holds X subcarriers and 4 / X rows of a unit: X = 2 as in
 // k_sinr_link_blk; X = 4 (one row) for 64-row units, whose 64 lanes then
-// read each core row once per q for four subcarriers instead of twice for
-// two (shared-memory wavefronts bound those).  The projection w = c* C streams C_ik and the path coefficients
-// through shared memory in double-buffered chunks of PC paths and keeps
-// w [T][p] in shared memory; the core then streams in stages of (column
+// read each core row from shared memory once per q for four subcarriers.
+// NT threads per CTA: 256 for 64-row units (16 subcarriers per CTA, so that
+// each core slab brought in serves 16), else 128.  The projection w = c* C
+// streams C_ik and the path coefficients through shared memory in
+// double-buffered chunks of PC paths and keeps w [T][p] in shared memory; the core then streams in stages of (column
 // chunk, kWideQC slabs G[q]), double-buffered, and the H~ accumulators of a
 // column chunk persist across its slabs.  Dense-channel comparator (C = I,
 // p = P): w = c* is evaluated per stage into the stage buffer instead.
@@ -446,7 +447,8 @@ cudaError_t launch_link_wide(const SinrArgs& A, cudaStream_t s) {
   // 64-row units: 256 threads (at most 128 registers, two CTAs per SM), so
   // that each core slab brought into shared memory serves 16 subcarriers
   // instead of 8, with one row and four subcarriers per lane (26.7 -> 19.4
-  // ms for the (60, 230, 150) links; 32-row units already hold 16)
+  // ms for the 420 links of (60, 230, 150) units; 32-row units already hold
+  // 16 subcarriers per 128-thread CTA)
   constexpr int NT = (!SERVE && MG >= 64) ? 2 * kThreads : kThreads;
   constexpr int X = MG >= 64 ? 4 : 2;
   // shared memory decides how many CTAs share an SM (128 threads: 3 within
