@@ -5,10 +5,10 @@
 // interfering and serving links run the wide-core kernel with 32 or 64 rows
 // per lane group (sinr_wide.cuh).  The arithmetic is the narrow kernels':
 //   k_svd_precoder_large  Gram S = H~_kk H~_kk* (eq. 23) scaled to unit
-//                         trace, cyclic Jacobi (round-robin pairs, one pair
-//                         per thread, rows and columns rotated by all
-//                         threads), V~ = conj(rows of U_L* H~) / sigma and
-//                         E_kk = U_L Sigma_L (eq. 7, eq. 24);
+//                         trace, cyclic Jacobi (round-robin pairs; each
+//                         rotation by one thread, its rows and columns by
+//                         lane j of every warp), V~ = conj(rows of U_L* H~)
+//                         / sigma and E_kk = U_L Sigma_L (eq. 7, eq. 24);
 //   k_sinr_finalize_large R = sum_{k != i} E E* + sigma^2 I (eq. 25),
 //                         Z = L_R^{-1} E_ii, x_r = [(I + Z*Z)^{-1}]_rr,
 //                         a_r = |L_Q^{-1} e_r|^2 with Q~ = R + E_ii E_ii*,
