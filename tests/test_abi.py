@@ -175,3 +175,19 @@ def test_autotune_table_roundtrip(lib, tmp_path):
     out = tmp_path / "out.txt"
     assert lib.ts_autotune_save(str(out).encode()) == 0
     assert "op0_prec0_J8_m8_n32_p16_P32_L8_K1024_coef1 2 1" in out.read_text()
+
+
+def test_multiuser_checks_before_launch(lib):
+    from paper_2401_09792_gb300 import tuckersinr as ts
+    d = _dims()
+    coef = ts.ts_coef(0, 8, None, None)
+    single = lib.ts_workspace_bytes(ctypes.byref(d), ts.TS_OP_SINR_SVD)
+    assert lib.ts_workspace_bytes(ctypes.byref(d), ts.TS_OP_SINR_SVD_MULTIUSER) == 2 * single
+    f = lib.ts_sinr_svd_multiuser
+    # no UE group; a missing core; one single-group workspace (two are needed)
+    assert f(ctypes.byref(d), 0, ctypes.byref(coef), 8, 8, 8, 8, None, 256, 1 << 30, None) == 1
+    assert f(ctypes.byref(d), 2, ctypes.byref(coef), None, 8, 8, 8, None, 256, 1 << 30, None) == 2
+    assert f(ctypes.byref(d), 2, ctypes.byref(coef), 8, 8, 8, 8, None, 256, single, None) == 4
+    g = lib.ts_dense_sinr_svd_multiuser
+    assert g(ctypes.byref(d), 0, ctypes.byref(coef), 8, 8, 8, None, 256, 1 << 30, None) == 1
+    assert g(None, 1, ctypes.byref(coef), 8, 8, 8, None, 256, 1 << 30, None) == 2
