@@ -191,3 +191,28 @@ def test_multiuser_checks_before_launch(lib):
     g = lib.ts_dense_sinr_svd_multiuser
     assert g(ctypes.byref(d), 0, ctypes.byref(coef), 8, 8, 8, None, 256, 1 << 30, None) == 1
     assert g(None, 1, ctypes.byref(coef), 8, 8, 8, None, 256, 1 << 30, None) == 2
+
+
+def test_fit_and_reconstruct_checks_before_launch(lib):
+    from paper_2401_09792_gb300 import tuckersinr as ts
+    # the fit takes ranks up to 256 (its eigensolver blocks); the
+    # reconstruction any ranks up to the dimensions
+    big = _dims(M=8, m=8, N=300, n=257, P=8, p=4)
+    for op in (ts.TS_OP_TUCKER_FIT, ts.TS_OP_TUCKER_FIT_SHARED, ts.TS_OP_TUCKER_FIT_INDIVIDUAL):
+        assert lib.ts_workspace_bytes(ctypes.byref(big), op) == 0
+        assert lib.ts_workspace_bytes(ctypes.byref(_dims(n=8, N=300)), op) > 0
+    assert lib.ts_workspace_bytes(ctypes.byref(big), ts.TS_OP_RECONSTRUCT) > 0
+    d = _dims()
+    fit = lib.ts_tucker_fit_model
+    # oversized ranks, unknown model, negative sweep count, missing core,
+    # misaligned factor, short workspace: all refused before any launch
+    assert fit(ctypes.byref(big), 8, 1, 0, 0, 8, 8, 8, 8, 8, 256, 1 << 30, None) == 1
+    assert fit(ctypes.byref(d), 8, 1, 0, 3, 8, 8, 8, 8, 8, 256, 1 << 30, None) == 6
+    assert fit(ctypes.byref(d), 8, -1, 0, 0, 8, 8, 8, 8, 8, 256, 1 << 30, None) == 6
+    assert fit(ctypes.byref(d), 8, 1, 0, 0, 8, 8, 8, None, 8, 256, 1 << 30, None) == 2
+    assert fit(ctypes.byref(d), 8, 1, 0, 0, 12, 8, 8, 8, 8, 256, 1 << 30, None) == 3
+    assert fit(ctypes.byref(d), 8, 1, 0, 0, 8, 8, 8, 8, 8, 256, 16, None) == 4
+    rec = lib.ts_tucker_reconstruct
+    assert rec(ctypes.byref(d), 7, 8, 8, 8, 8, 8, 256, 1 << 30, None) == 6
+    assert rec(ctypes.byref(d), 0, 8, 8, 8, 8, None, 256, 1 << 30, None) == 2
+    assert rec(ctypes.byref(d), 0, 8, 8, 8, 8, 8, 256, 16, None) == 4
