@@ -1,13 +1,14 @@
 #!/usr/bin/env python
 """Throughput of Tucker-form SINR evaluation on GB300 (subcarrier-SINRs/s).
 
-One step = one SVD-precoded MMSE SINR evaluation of the whole mid-size system
-(J=8 cells, M=8, N=256, P=32, K=1024 subcarriers, ranks (8,32,16), L=8):
-path coefficients (a0), projection c*C (a1), core contraction (a2), SVD
-precoders through the Jacobi eigensolve (a3), effective channels (a4),
-covariance (a5), Cholesky solves and SINR (a6), all in the CUDA library,
-called through its C ABI.  Inputs are resident in HBM; L2 is flushed before
-every timed step.  Prints one JSON line (rank 0).
+One step = one SVD-precoded MMSE SINR evaluation of the whole system of the
+largest single-GPU workload (J=16 cells, M=16, N=1024, P=64, K=3300
+subcarriers, ranks (16,96,32), L=8): path coefficients (a0), projection c*C
+(a1), core contraction (a2), SVD precoders through the Jacobi eigensolve
+(a3), effective channels (a4), covariance (a5), Cholesky solves and SINR
+(a6), all in the CUDA library, called through its C ABI.  Inputs are
+resident in HBM; L2 is flushed before every timed step.  Prints one JSON
+line (rank 0); the mid and precision workloads are reported in it too.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -36,8 +37,8 @@ sys.path.insert(0, ROOT)
 
 from paper_2401_09792_gb300 import synth  # noqa: E402
 
-WORKLOAD = synth.MID             # the default line; --workload selects another
-WORKLOAD_NAME = "mid"
+WORKLOAD = synth.DIFFERENTIATION  # the default line; --workload selects another
+WORKLOAD_NAME = "diff"
 METRIC = "subcarrier-SINRs/s"
 FLUSH_BYTES = 256 << 20          # > 129 MB of L2
 
@@ -81,14 +82,14 @@ def link_flops(w, precoder="svd") -> int:
       m n p              core contraction H~ = G x_3 (c* C) (eq. 15)   [svd]
       m n L              effective channel E = H~ V~ (eq. 24)          [svd]
       p m L              E = sum_q w_q F[q] (wideband precoder)
-      m^2 L              covariance rows E E* (eq. 25)
     over J (J - 1) interfering links (svd: the serving link comes from the
-    precoder phase) or J^2 links (wideband precoder) and K subcarriers.
+    precoder phase) or J^2 links (wideband precoder) and K subcarriers.  The
+    covariance of eq. (25) is formed by the finalisation from the stored E.
     """
     J, m, n, p, P, L = w.J, w.m, w.n, w.p, w.P, w.L
     if precoder == "svd":
-        return int(8 * w.K * J * (J - 1) * (P * p + m * n * p + m * n * L + m * m * L))
-    return int(8 * w.K * J * (J * (P * p + p * m * L) + (J - 1) * m * m * L))
+        return int(8 * w.K * J * (J - 1) * (P * p + m * n * p + m * n * L))
+    return int(8 * w.K * J * J * (P * p + p * m * L))
 
 
 def precoder_flops(w) -> int:
@@ -287,9 +288,10 @@ def run_ours(args):
     coef, keep = ts.make_coef(alpha=dv["alpha"], tau=dv["tau"])
     sinr = torch.empty(J, K, L, device=dev)
     flags = torch.empty(J, K, dtype=torch.uint8, device=dev)
-    prec_id = {"fp32": ts.TS_PREC_FP32, "tf32": ts.TS_PREC_TF32, "bf16x2": ts.TS_PREC_BF16X2}[args.precision]
+    prec_id = {"fp32": ts.TS_PREC_FP32, "tf32": ts.TS_PREC_TF32, "bf16x2": ts.TS_PREC_BF16X2,
+               "tf32x3": ts.TS_PREC_TF32X3}[args.precision]
     ws_op = {"fp32": ts.TS_OP_SINR_SVD, "tf32": ts.TS_OP_SINR_SVD_TF32,
-             "bf16x2": ts.TS_OP_SINR_SVD_BF16X2}[args.precision]
+             "bf16x2": ts.TS_OP_SINR_SVD_BF16X2, "tf32x3": ts.TS_OP_SINR_SVD_TF32X3}[args.precision]
     ws = ts.workspace(d, ws_op, dev)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -421,13 +423,19 @@ def _extras(args, ts, torch, dist, world, dev, w, tk, host, dv, coef, d, ws, sin
     # ---- dense-channel comparator on the same system: full M x N channels per
     # subcarrier (eq. 9), precoders and solves at (M, N); same kernels, C = I
     if ts.ts_workspace_bytes(d, ts.TS_OP_DENSE_SVD) == 0:
-        # the dense kernels stage one M x N channel per subcarrier: M <= 16,
-        # N <= 512, P <= 1024
+        # the dense kernels stage one M x N channel per subcarrier: M <= 64,
+        # N <= 1024, P <= 1024
         return e2e_value, h2d, d2h, mm_ms, None, None, None
-    X = synth.channel_submatrices(w)
-    Xd = torch.from_numpy(np.ascontiguousarray(np.transpose(X, (0, 1, 4, 2, 3))
-                                               .reshape(J * J, P, w.M, w.N)).astype(np.complex64)).to(dev)
-    del X
+    if w == synth.MID:
+        # the channel model's own channels (the method figures below use them)
+        X = synth.channel_submatrices(w)
+        Xd = torch.from_numpy(np.ascontiguousarray(np.transpose(X, (0, 1, 4, 2, 3))
+                                                   .reshape(J * J, P, w.M, w.N)).astype(np.complex64)).to(dev)
+        del X
+    else:
+        # X^ = G x_1 A x_2 B x_3 C reconstructed on the GPU from the same
+        # Tucker form: both paths then compute the same SINR (A and B cancel)
+        Xd = _reconstructed_channels(ts, torch, dev, w, tk, dv, d)
     ws_d = ts.workspace(d, ts.TS_OP_DENSE_SVD, dev)
     for _ in range(args.warmup):
         ts.ts_dense_sinr_svd(d, coef, Xd, dv["sigma2"], sinr, flags, ws_d, stream)
@@ -441,7 +449,12 @@ def _extras(args, ts, torch, dist, world, dev, w, tk, host, dv, coef, d, ws, sin
         b.record(stream)
         b.synchronize()
         dense_ms += a.elapsed_time(b)
+    assert int((flags & ts.TS_FLAG_ERRORS).max().item()) == 0, "numerical flags raised in the dense steps"
     dense_value = units * dense_steps / (dense_ms * 1e-3)
+    _extras.dense_sinr = sinr.cpu().numpy().astype(np.float64)
+    if w != synth.MID:
+        del Xd, ws_d
+        return e2e_value, h2d, d2h, mm_ms, dense_value, dense_ms, dense_steps
     _method_error.result = _method_error(ts, torch, dev, w, Xd, coef, dv, d, stream, ev, flush,
                                          dense_ms / dense_steps)
     # the same on spatially correlated NLOS channels (compressible in modes
@@ -456,6 +469,19 @@ def _extras(args, ts, torch, dist, world, dev, w, tk, host, dv, coef, d, ws, sin
     _method_error.result["correlated_channels"] = corr
     del Xd, ws_d
     return e2e_value, h2d, d2h, mm_ms, dense_value, dense_ms, dense_steps
+
+
+def _reconstructed_channels(ts, torch, dev, w, tk, dv, d):
+    """X^_ik = G_ik x_1 A_i x_2 B_k x_3 C_ik of every link on the GPU
+    (ts_tucker_reconstruct), in the dense comparator's layout [J*J][P][M][N]."""
+    A = torch.from_numpy(tk["A"].astype(np.complex64)).to(dev)
+    B = torch.from_numpy(tk["B"].astype(np.complex64)).to(dev)
+    Xd = torch.empty(w.J * w.J, w.P, w.M, w.N, dtype=torch.complex64, device=dev)
+    wsr = ts.workspace(d, ts.TS_OP_RECONSTRUCT, dev)
+    ts.ts_tucker_reconstruct(d, ts.TS_MODEL_GROUPWISE, A, B, dv["C"], dv["G"], Xd, wsr)
+    torch.cuda.synchronize()
+    del wsr
+    return Xd
 
 
 def _method_error(ts, torch, dev, w, Xd, coef, dv, d, stream, ev, flush, dense_step_ms, sweeps=10,
@@ -609,7 +635,8 @@ def _precision_variants(args, ts, torch, dev, w, dv, coef, d, sinr, flags, flush
     SINRs of one evaluation for the error report."""
     out = {}
     for name, prec, op in (("tf32", ts.TS_PREC_TF32, ts.TS_OP_SINR_SVD_TF32),
-                           ("bf16x2", ts.TS_PREC_BF16X2, ts.TS_OP_SINR_SVD_BF16X2)):
+                           ("bf16x2", ts.TS_PREC_BF16X2, ts.TS_OP_SINR_SVD_BF16X2),
+                           ("tf32x3", ts.TS_PREC_TF32X3, ts.TS_OP_SINR_SVD_TF32X3)):
         wsp = ts.workspace(d, op, dev)
 
         def step(k0=None, k1=None):
@@ -672,7 +699,8 @@ def _report(args, ts, torch, world, dev, w, tk, alpha, tau, s2, d, coef, dv, ws,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.precision == "fp32" else f"f32 ({args.precision} core contraction)",
         "data": "synthetic",
-        "config": {**workload_config(w), "parallelism": f"independent systems x{world}"},
+        "config": workload_config(w),
+        "parallelism": f"independent systems x{world}",
         "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
@@ -691,11 +719,14 @@ def _report(args, ts, torch, world, dev, w, tk, alpha, tau, s2, d, coef, dv, ws,
                for k, v in prec.items() if k != "adjoint"},
             **({"svd_adjoint": prec["adjoint"]} if "adjoint" in prec else {})},
         "method": getattr(_method_error, "result", None),
-        "dense_comparator": {"unavailable": "dense kernels need M <= 16, N <= 512, P <= 1024"}
+        "dense_comparator": {"unavailable": "dense kernels need M <= 64, N <= 1024, P <= 1024"}
         if dense_ms is None else {
             "value": dense_value, "unit": METRIC, "ms_per_step": dense_ms / dense_steps,
             "what": "same SVD-precoded SINR from the uncompressed channels "
-                    f"(M={w.M}, N={w.N}, P={w.P}) on the same GPU kernels",
+                    f"(M={w.M}, N={w.N}, P={w.P}) on the same GPU kernels"
+                    + ("" if w == synth.MID else
+                       "; channels X^ = G x1 A x2 B x3 C reconstructed on the GPU from the same "
+                       "Tucker form, so both paths compute the same SINR"),
             "tucker_over_dense": value / world / dense_value},
         "wall_s_timed_region": round(wall, 4),
     }
@@ -710,11 +741,78 @@ def _report(args, ts, torch, world, dev, w, tk, alpha, tau, s2, d, coef, dv, ws,
     if world == 1 and not args.no_cpu_baseline:
         gpu_out = {"fp32": _gpu_svd_sinr(ts, d, coef, dv, ws, stream)}
         gpu_out.update({k: v["sinr"] for k, v in prec.items() if "sinr" in v})
+        if "dense_comparator" in line and getattr(_extras, "dense_sinr", None) is not None:
+            gpu_out["dense"] = _extras.dense_sinr
         line["cpu_baseline"], errs = cpu_baseline(w, tk, alpha, tau, s2, gpu_out)
         line["sinr_err"] = errs.pop("fp32", None)
+        if "dense" in errs:
+            line["dense_comparator"]["sinr_err"] = errs.pop("dense")
         for k, e in errs.items():
             line["variants"][f"svd_{k}"]["sinr_err"] = e
+    if world == 1 and not args.step_only and args.precision == "fp32":
+        line["workloads"] = {name: _workload_summary(name, args, ts, torch, dev)
+                             for name in ("mid", "precision") if name != WORKLOAD_NAME}
     print(json.dumps(line), flush=True)
+
+
+def _workload_summary(name, args, ts, torch, dev, kcount=32):
+    """Another workload's SVD-precoded SINR step (same timing discipline,
+    fewer steps): throughput, link-pass roofline fraction, and the error of
+    every SINR at `kcount` subcarriers spread over the range against the
+    FP64 oracle."""
+    from oracle import sinr as S
+    w = synth.WORKLOADS[name]
+    tk = synth.direct_tucker(w)
+    alpha, tau = synth.path_gains_delays(w)
+    s2 = synth.noise_powers(w)
+    d = ts.Dims.of(w)
+    G = ts.core_to_device(tk["G"], dev)
+    C = ts.factor_to_device(tk["C"].reshape(w.J * w.J, w.P, w.p), dev)
+    al = ts.factor_to_device(alpha.reshape(w.J * w.J, w.P), dev)
+    ta = ts.real_to_device(tau.reshape(w.J * w.J, w.P), dev)
+    sig = ts.real_to_device(s2, dev)
+    coef, keep = ts.make_coef(alpha=al, tau=ta)
+    sinr = torch.empty(w.J, w.K, w.L, device=dev)
+    flags = torch.empty(w.J, w.K, dtype=torch.uint8, device=dev)
+    ws = ts.workspace(d, ts.TS_OP_SINR_SVD, dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    steps = max(5, min(args.steps, 50))
+    for _ in range(args.warmup):
+        ts.ts_sinr_svd(d, coef, G, C, sig, sinr, flags, ws, stream)
+    evs = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(4)) for _ in range(steps)]
+    for e in evs:
+        for x in e:
+            x.record(stream)
+    torch.cuda.synchronize()
+    for a, b, k0, k1 in evs:
+        flush.zero_()
+        a.record(stream)
+        ts.ts_set_timing_events(k0, k1)
+        ts.ts_sinr_svd(d, coef, G, C, sig, sinr, flags, ws, stream)
+        ts.ts_set_timing_events(None, None)
+        b.record(stream)
+    torch.cuda.synchronize()
+    total = float(np.sum([a.elapsed_time(b) for a, b, _, _ in evs]))
+    link = float(np.mean([k0.elapsed_time(k1) for _, _, k0, k1 in evs]))
+    assert int((flags & ts.TS_FLAG_ERRORS).max().item()) == 0, f"numerical flags raised on {name}"
+    got = sinr.cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(5)
+    ks = np.unique(np.concatenate([[0, w.K - 1], rng.choice(w.K, kcount - 2, replace=False)]))
+    coef_h = S.coefficients(alpha, tau, w.K, w.delta_f_hz)[:, :, ks]
+    ref = S.tucker_sinr(tk["G"], tk["C"], coef_h, s2, w.L, "svd")
+    rel = np.abs(got[:, ks] - ref) / np.abs(ref)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = sms * 128 * 2 * float(peaks().get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    achieved = link_flops(w, "svd") / (link * 1e-3) / 1e12
+    del keep
+    return {"value": w.J * w.K * steps / (total * 1e-3), "unit": METRIC, "ms_per_step": total / steps,
+            "steps": steps, "config": workload_config(w)["workload"],
+            "link_kernel": {"ms": round(link, 5), "achieved_tflops": round(achieved, 3),
+                            "frac_of_fp32_peak": round(achieved / fp32_peak, 4)},
+            "sinr_err": {"max_rel": float(rel.max()), "p99_rel": float(np.percentile(rel, 99)),
+                         "median_rel": float(np.median(rel)), "n": int(rel.size),
+                         "vs": f"FP64 oracle at {len(ks)} subcarriers spread over the range"}}
 
 
 def _gpu_svd_sinr(ts, d, coef, dv, ws, stream):
@@ -1336,7 +1434,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {**workload_config(w), "parallelism": "none (host CPU)"},
+        "data": "synthetic", "config": workload_config(w), "parallelism": "none (host CPU)",
         "cpu_baseline": {"value": value, "unit": METRIC, "cores": max(1, round(cpu / wall)),
                          "kind": "oracle",
                          "sample": f"each step: FP64 NumPy oracle on {kslice} of the {w.K} "
@@ -1351,14 +1449,15 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--step-only", action="store_true",
                     help="time only the SVD step (no end-to-end, variant or comparator runs)")
-    ap.add_argument("--workload", default="mid", choices=sorted(synth.WORKLOADS) + ["batch"],
-                    help="synthetic system of the timed step (default: mid, the headline)")
+    ap.add_argument("--workload", default="diff", choices=sorted(synth.WORKLOADS) + ["batch"],
+                    help="synthetic system of the timed step (default: diff, the largest "
+                         "single-GPU workload, the headline)")
     ap.add_argument("--batch-instances", type=int, default=512,
                     help="systems of the batch workload")
     ap.add_argument("--ue-groups", type=int, default=None,
@@ -1370,7 +1469,7 @@ def main():
                          "R_s, R_t and e_c per point")
     ap.add_argument("--adjoint", action="store_true",
                     help="also time the SVD-SINR adjoint (dSINR -> dG, dC) on the workload")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16x2"],
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16x2", "tf32x3"],
                     help="arithmetic of the interfering links' core contraction in the timed step "
                          "(fp32: FMA pipe; tf32, bf16x2: tensor cores); implies --step-only")
     args = ap.parse_args()
@@ -1380,7 +1479,7 @@ def main():
         run_batch(args)
         return
     if args.rank_sweep:
-        select_workload("mid_corr" if args.workload == "mid" else args.workload)
+        select_workload("mid_corr" if args.workload in ("mid", "diff") else args.workload)
         if WORKLOAD.U > 1:
             # the first UE of every cell, spatially correlated NLOS
             set_ue_groups(1)

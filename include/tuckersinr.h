@@ -50,15 +50,16 @@ typedef struct {
 typedef struct {
   int32_t J;          /* cells = base stations = groups                        */
   int32_t M, N, P;    /* UE antennas, BS antennas, submatrices per link         */
-  int32_t m, n, p;    /* Tucker ranks: 1 <= m <= M, n <= min(N, 512),
+  int32_t m, n, p;    /* Tucker ranks: 1 <= m <= M, n <= min(N, 1024),
                          p <= P <= 1024.  SVD-precoded SINR (FP32): m <= 64
                          (m > 16: shared-memory precoder and finalisation,
                          L <= 8), p <= 256 (p > 32 or P p > 8192 runs the
                          wide-core kernel, as the paper's compressed sizes
-                         need); wideband precoder, adjoints and tensor-core
-                         modes: m <= 16, p <= 32 and P p <= 8192.  Dense
-                         comparator: M, N, P as m, n, p of the matching
-                         compressed call, P <= 1024 (SVD)                   */
+                         need), n > 512 only with L <= 8 (shared-memory
+                         precoder); wideband precoder, adjoints and
+                         tensor-core modes: m <= 16, n <= 512, p <= 32 and
+                         P p <= 8192.  Dense comparator: M, N, P as m, n, p
+                         of the matching compressed call, P <= 1024 (SVD)  */
   int32_t K;          /* OFDM subcarriers, kappa = 0 .. K-1                      */
   int32_t L;          /* streams per UE, 1 <= L <= min(m, n)                     */
   float delta_f_hz;   /* subcarrier spacing (path-form coefficients only)      */
@@ -93,9 +94,11 @@ enum {
   TS_FLAG_EIG_UNCONVERGED = 8, /* the Jacobi eigensolver hit its sweep cap    */
   TS_FLAG_TIMEOUT = 16,       /* a bounded device wait of the tensor-core pass
                                  gave up; the unit's SINR is NaN             */
-  TS_FLAG_REFINED = 32        /* informational: cond(R) was above the
-                                 refinement threshold and the SINR comes from
-                                 the FP64-residual refinement of the solves  */
+  TS_FLAG_REFINED = 32        /* informational: the SINR comes from the
+                                 accurate re-evaluation (R in double-float,
+                                 FP64-residual refinement of the solves):
+                                 units above the refinement threshold, and
+                                 every unit of more than 16 rows            */
 };
 
 /* Operations, for ts_workspace_bytes. */
@@ -113,7 +116,8 @@ enum {
   TS_OP_TUCKER_FIT_INDIVIDUAL = 10, /* ts_tucker_fit_model, TS_MODEL_INDIVIDUAL */
   TS_OP_RECONSTRUCT = 11,          /* ts_tucker_reconstruct                    */
   TS_OP_SINR_SVD_MULTIUSER = 12,   /* ts_sinr_svd_multiuser (any U)            */
-  TS_OP_DENSE_SVD_MULTIUSER = 13   /* ts_dense_sinr_svd_multiuser (any U)      */
+  TS_OP_DENSE_SVD_MULTIUSER = 13,  /* ts_dense_sinr_svd_multiuser (any U)      */
+  TS_OP_SINR_SVD_TF32X3 = 14       /* ts_sinr_svd_prec with TS_PREC_TF32X3     */
 };
 
 /* The three compression models of Section 3.1: which links share the
@@ -127,17 +131,20 @@ enum {
   TS_MODEL_INDIVIDUAL = 2
 };
 
-/* Arithmetic of the core contraction H~ = G x_3 (c* C) (eq. 15) in
- * ts_sinr_svd_prec.  FP32: FMA pipe, the default of every other call.
- * TF32: tensor cores, w = c* C and G rounded to TF32 (10-bit mantissa), FP32
- * accumulation.  BF16X2: tensor cores, w and G split into BF16 high and low
- * parts, products w_hi G_hi + w_lo G_hi + w_hi G_lo, FP32 accumulation
- * (about 16 significant bits).  The projection, the precoders, the
- * effective channels, the covariance and the solves stay FP32. */
+/* Arithmetic of the interfering links' core contraction H~ = G x_3 (c* C)
+ * (eq. 15) in ts_sinr_svd_prec.  FP32: FMA pipe, the default of every other
+ * call.  TF32: tensor cores, w = c* C and G rounded to TF32 (10-bit
+ * mantissa), FP32 accumulation.  BF16X2: tensor cores, w and G split into
+ * BF16 high and low parts, products w_hi G_hi + w_hi G_lo + w_lo G_hi, FP32
+ * accumulation (about 16 significant bits).  TF32X3: the same three
+ * products with TF32 parts (about 22 significant bits, close to FP32).  The
+ * projection, the serving links, the precoders, the effective channels,
+ * the covariance and the solves stay FP32. */
 enum {
   TS_PREC_FP32 = 0,
   TS_PREC_TF32 = 1,
-  TS_PREC_BF16X2 = 2
+  TS_PREC_BF16X2 = 2,
+  TS_PREC_TF32X3 = 3
 };
 
 /* Human-readable name of a status code (static storage). */
@@ -156,14 +163,20 @@ int ts_abi_version(void);
  * covariance kernel).  NULL, NULL turns it off.  Not used otherwise. */
 void ts_set_timing_events(void* start, void* stop);
 
-/* Mixed-precision refinement of ill-conditioned solves (eq. 26-28): SINR
- * calls on this host thread whose FP32 Cholesky factor of the
- * interference-plus-noise covariance R shows cond(R) > cond_threshold
- * (estimated from its diagonal) recompute that unit's solves with
- * residuals accumulated in FP64 (two refinement steps of R^{-1} E_ii, then
- * the L x L system in FP64) and set TS_FLAG_REFINED.  Default 1e3; a
- * negative threshold turns refinement off. */
-void ts_set_refinement(float cond_threshold);
+/* Mixed-precision re-evaluation of sensitive units (eq. 25-28).  The
+ * interference-plus-noise covariance R = sum_{k != i} E_ik E_ik* +
+ * sigma^2 I is formed and factored in FP32; a unit whose SINRs are
+ * sensitive to that rounding,
+ *   s = max_r sqrt(sum_ab |y_ar|^2 |R_ab|^2 |y_br|^2) / (e_r* y_r) > threshold
+ * (e_r the serving effective channel's columns, y_r = R^{-1} e_r; the FP32
+ * rounding of R moves SINR_r by a few u s, u = 2^-24), is evaluated again by
+ * SINR calls on this host thread from R formed in double-float out of the
+ * stored effective channels, with the solves refined by FP64 residuals
+ * (three steps of R^{-1} E_ii, then the L x L system in FP64); its flags get
+ * TS_FLAG_REFINED.  Default threshold 8; 0 re-evaluates every unit, a
+ * negative threshold none.  Units of more than 16 rows are always evaluated
+ * the accurate way. */
+void ts_set_refinement(float threshold);
 
 /* Inner iterations of the fit's eigensolves for factors whose mode dimension
  * exceeds 72 (block subspace iteration with Cholesky-QR, then a
@@ -360,8 +373,10 @@ int ts_dense_sinr_svd_multiuser(const ts_dims* d, int U, const ts_coef* coef, co
  * precoder, covariance and solves at size (M, N) (eq. 3-7) -- the "original
  * data" side of the paper's speedup R_t (Section 4).
  * X: [J*J][P][M][N] (the submatrices of eq. 2 stacked on mode 3, N fastest).
- * Pfull (mmse): [J][N][L].  d->m, d->n, d->p are ignored; limits M <= 16,
- * N <= 512, P <= 32.  ws: ts_workspace_bytes(d, TS_OP_DENSE_SVD / _MMSE). */
+ * Pfull (mmse): [J][N][L].  d->m, d->n, d->p are ignored; limits: SVD
+ * M <= 64, N <= 1024, P <= 1024 (L <= 8 when N > 512); wideband precoder
+ * M <= 16, N <= 512, P <= 32.  ws: ts_workspace_bytes(d, TS_OP_DENSE_SVD /
+ * _MMSE). */
 int ts_dense_sinr_svd(const ts_dims* d, const ts_coef* coef, const ts_c64* X,
                       const float* sigma2, float* sinr, uint8_t* flags, void* ws,
                       size_t ws_bytes, void* stream);
@@ -448,9 +463,14 @@ int ts_project_precoder_adjoint(const ts_dims* d, const ts_c64* Pfull,
  *     TS_NOALLOC_SCRATCH_BYTES are rejected with TS_ERR_WORKSPACE before
  *     any launch (for example J = 8, m = 8, L = 8 fits up to K = 495
  *     subcarriers).
- *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress, with that device current); make that first call
- *     before any stream capture.
+ *   - Every call looks up the array's device address (cudaGetSymbolAddress,
+ *     with the calling thread's current device); after the first call on a
+ *     device that lookup only reads a host-side table.  The first call on
+ *     each device also loads the library's module there, which commits the
+ *     array: it may synchronise the device, and it fails with a CUDA error
+ *     (TS_ERR_CUDA) if the device has no room left.  Make that first call at
+ *     start-up -- before any stream capture and before a framework reserves
+ *     the device's memory; later calls change no allocation.
  *   - Every call shares the one array per device, which keeps the previous
  *     call's contents (nothing needs clearing: each call writes every byte
  *     it reads).  Calls that overlap on the GPU -- on two streams, or from

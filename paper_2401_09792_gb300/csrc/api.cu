@@ -18,9 +18,10 @@ thread_local int g_last_cuda = 0;
 // next SINR calls on this host thread (ts_set_timing_events)
 thread_local cudaEvent_t g_ev_start = nullptr;
 thread_local cudaEvent_t g_ev_stop = nullptr;
-// condition number of R above which a unit's solves are refined with FP64
-// residuals (ts_set_refinement); infinity turns refinement off
-thread_local float g_refine_cond = 1e3f;
+// SINR sensitivity to R (see k_sinr_finalize) above which a unit is
+// re-evaluated from a double-float R with FP64 residuals
+// (ts_set_refinement); infinity turns refinement off
+thread_local float g_refine_sens = 8.f;
 thread_local int g_fit_iters = 40;
 // rows per unit of the SVD path (more than kMaxRankM: shared-memory kernels)
 constexpr int kMaxRankMLarge = 64;
@@ -58,7 +59,7 @@ cudaError_t finalize_refined(const ts::SinrArgs& a, bool svd, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
   if (svd && a.J < 2) e = cudaMemsetAsync(a.rcount, 0, sizeof(int), s);
   if (e == cudaSuccess) e = ts::launch_sinr_finalize(a, svd, s);
-  if (e == cudaSuccess && a.refine_cond < INFINITY && a.m <= ts::kMaxRankM)
+  if (e == cudaSuccess && a.refine_sens < INFINITY && a.m <= ts::kMaxRankM)
     e = ts::launch_sinr_refine(a, svd, s);
   return e;
 }
@@ -96,21 +97,25 @@ int check_dims(const ts_dims* d, bool identity = false) {
   if (d->L > d->m || d->L > d->n) return TS_ERR_DIMS;
   // units with more than 16 rows: shared-memory kernels, up to 8 streams
   if (d->m > ts::kMaxRankM && d->L > 8) return TS_ERR_DIMS;
-  // staging limits of the kernels: one H~ (m x n) per subcarrier and the
-  // projections w [subcarrier tile][p] live in shared memory
-  // (the dense-channel comparator, C = I, keeps no projections: p = P <= 1024)
-  if (d->P > 1024 || (!identity && d->p > ts::kMaxRankPWide) || d->n > 512) return TS_ERR_DIMS;
+  // staging limits of the kernels: the projections w [subcarrier tile][p]
+  // live in shared memory (the dense-channel comparator, C = I, keeps no
+  // projections: p = P <= 1024); serving channels of more than 512 columns
+  // go through the shared-memory precoder (m <= 16, L <= 8)
+  if (d->P > 1024 || (!identity && d->p > ts::kMaxRankPWide) || d->n > 1024) return TS_ERR_DIMS;
+  if (d->n > ts::kMaxNRegisterPrecoder && d->m <= ts::kMaxRankM && d->L > 8) return TS_ERR_DIMS;
   if ((int64_t)d->J * d->J > 65535 || d->J > 65535) return TS_ERR_DIMS;
   return TS_OK;
 }
 
 // The wideband-precoder path and the adjoints stage C_ik (P x p) and a core
-// column chunk whole: p <= 32 and P p <= 8192.  The SVD path streams larger
+// column chunk whole: p <= 32 and P p <= 8192; the adjoints also need the
+// register precoder's full SVD (n <= 512).  The SVD path streams larger
 // cores through the wide-core kernel.
 int check_narrow(const ts_dims* d) {
   const int st = check_dims(d);
   if (st != TS_OK) return st;
-  return ts::wide_core(d->P, d->p) || d->m > ts::kMaxRankM ? TS_ERR_DIMS : TS_OK;
+  return ts::wide_core(d->P, d->p) || d->m > ts::kMaxRankM || d->n > ts::kMaxNRegisterPrecoder
+             ? TS_ERR_DIMS : TS_OK;
 }
 
 // The SVD precoder forms the serving links' channels itself (small cores,
@@ -121,7 +126,7 @@ bool fuses_serve(const ts_dims* d) {
 
 // Workspace layout (byte offsets from the base, each 256-byte aligned).
 struct Workspace {
-  size_t turns = 0, V = 0, Hserv = 0, Wserv = 0, Eserv = 0, Rpart = 0, pflag = 0, F = 0, rlist = 0,
+  size_t turns = 0, V = 0, Hserv = 0, Wserv = 0, Eserv = 0, Eint = 0, pflag = 0, F = 0, rlist = 0,
          rcount = 0, total = 0;
 };
 
@@ -133,8 +138,8 @@ Workspace carve(const ts_dims* d, int op) {
   o = align_up(o + nch * d->P * sizeof(unsigned long long), 256);
   w.Eserv = o;
   o = align_up(o + (size_t)d->J * d->K * d->m * d->L * sizeof(float2), 256);
-  w.Rpart = o;
-  o = align_up(o + (size_t)d->J * (d->J - 1) * d->K * d->m * d->m * sizeof(float2), 256);
+  w.Eint = o;
+  o = align_up(o + (size_t)d->J * (d->J - 1) * d->K * d->m * d->L * sizeof(float2), 256);
   if (op == TS_OP_SINR_SVD) {
     w.V = o;
     o = align_up(o + (size_t)d->J * d->K * d->n * d->L * sizeof(float2), 256);
@@ -250,13 +255,13 @@ ts::SinrArgs base_args(const ts_dims* d, const ts_coef* coef, const ts_c64* G, c
   a.coef = reinterpret_cast<const float2*>(coef->mode == TS_COEF_DENSE ? coef->c : coef->alpha);
   a.turns = reinterpret_cast<const unsigned long long*>(ws + w.turns);
   a.Eserv = reinterpret_cast<float2*>(ws + w.Eserv);
-  a.Rpart = reinterpret_cast<float2*>(ws + w.Rpart);
+  a.Eint = reinterpret_cast<float2*>(ws + w.Eint);
   a.sigma2 = sigma2;
   a.sinr = sinr;
   a.flags = flags;
   a.rlist = reinterpret_cast<int*>(ws + w.rlist);
   a.rcount = reinterpret_cast<int*>(ws + w.rcount);
-  a.refine_cond = g_refine_cond;
+  a.refine_sens = g_refine_sens;
   a.link_variant = g_tuning.link_variant;
   a.precoder_split = g_tuning.precoder_split;
   return a;
@@ -296,8 +301,8 @@ void ts_set_timing_events(void* start, void* stop) {
 
 void ts_set_fit_iterations(int iterations) { g_fit_iters = iterations > 0 ? iterations : 40; }
 
-void ts_set_refinement(float cond_threshold) {
-  g_refine_cond = cond_threshold < 0.f ? INFINITY : cond_threshold;
+void ts_set_refinement(float threshold) {
+  g_refine_sens = threshold < 0.f ? INFINITY : threshold;
 }
 
 size_t ts_workspace_bytes(const ts_dims* d, int op) {
@@ -324,9 +329,11 @@ size_t ts_workspace_bytes(const ts_dims* d, int op) {
   if (op == TS_OP_SINR_SVD_ADJOINT || op == TS_OP_SINR_MMSE_ADJOINT)
     return check_narrow(d) == TS_OK ? carve_adjoint(d, op == TS_OP_SINR_SVD_ADJOINT).total : 0;
   if (op == TS_OP_SINR_MMSE && check_narrow(d) != TS_OK) return 0;
-  if (op == TS_OP_SINR_SVD_TF32 || op == TS_OP_SINR_SVD_BF16X2)
+  if (op == TS_OP_SINR_SVD_TF32 || op == TS_OP_SINR_SVD_BF16X2 || op == TS_OP_SINR_SVD_TF32X3)
     return ts::tc_supported(d->m, d->L, d->p) && check_narrow(d) == TS_OK
-               ? prec_workspace_bytes(d, op == TS_OP_SINR_SVD_TF32 ? TS_PREC_TF32 : TS_PREC_BF16X2)
+               ? prec_workspace_bytes(d, op == TS_OP_SINR_SVD_TF32     ? TS_PREC_TF32
+                                         : op == TS_OP_SINR_SVD_TF32X3 ? TS_PREC_TF32X3
+                                                                       : TS_PREC_BF16X2)
                : 0;
   if (op != TS_OP_SINR_SVD && op != TS_OP_SINR_MMSE) return 0;
   return carve(d, op).total;
@@ -602,7 +609,8 @@ int svd_from_precoders_prec_impl(const ts_dims* d, const ts_coef* coef, const ts
 }
 
 int check_prec(const ts_dims* d, int precision) {
-  if (precision != TS_PREC_TF32 && precision != TS_PREC_BF16X2) return TS_ERR_MODE;
+  if (precision != TS_PREC_TF32 && precision != TS_PREC_BF16X2 && precision != TS_PREC_TF32X3)
+    return TS_ERR_MODE;
   int st = check_narrow(d);
   if (st != TS_OK) return st;
   return ts::tc_supported(d->m, d->L, d->p) ? TS_OK : TS_ERR_MODE;

@@ -39,6 +39,7 @@ int ws_op(const ts_instance& x) {
   if (x.op == TS_OP_SINR_MMSE) return TS_OP_SINR_MMSE;
   if (x.precision == TS_PREC_TF32) return TS_OP_SINR_SVD_TF32;
   if (x.precision == TS_PREC_BF16X2) return TS_OP_SINR_SVD_BF16X2;
+  if (x.precision == TS_PREC_TF32X3) return TS_OP_SINR_SVD_TF32X3;
   return TS_OP_SINR_SVD;
 }
 
@@ -55,7 +56,8 @@ std::string class_key(const ts_instance& x) {
 // device.
 int check_instance(const ts_instance& x) {
   if (x.op != TS_OP_SINR_SVD && x.op != TS_OP_SINR_MMSE) return TS_ERR_MODE;
-  if (x.precision != TS_PREC_FP32 && x.precision != TS_PREC_TF32 && x.precision != TS_PREC_BF16X2)
+  if (x.precision != TS_PREC_FP32 && x.precision != TS_PREC_TF32 && x.precision != TS_PREC_BF16X2 &&
+      x.precision != TS_PREC_TF32X3)
     return TS_ERR_MODE;
   if (x.op == TS_OP_SINR_MMSE && x.precision != TS_PREC_FP32) return TS_ERR_MODE;
   if (ts_workspace_bytes(&x.d, ws_op(x)) == 0) return TS_ERR_DIMS;

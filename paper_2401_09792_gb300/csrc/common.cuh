@@ -47,6 +47,36 @@ __device__ __forceinline__ void cms(float2& acc, float2 a, float2 b) {
   acc.y = fmaf(-a.y, b.x, acc.y);
 }
 
+// Double-float accumulation: a value held as hi + lo, |lo| <~ ulp(hi).
+// TwoSum (Knuth) and the FMA product error make each step exact up to the
+// rounding of lo, so a sum of products of FP32 numbers keeps ~2^-44 of its
+// largest term.  The explicit _rn intrinsics keep the compiler from fusing
+// the product into the sum, which would break the error terms.
+__device__ __forceinline__ void df_add_prod(float& hi, float& lo, float x, float y) {
+  const float p = __fmul_rn(x, y);
+  const float pe = fmaf(x, y, -p);                // x y - p, exactly
+  const float s = __fadd_rn(hi, p);
+  const float bb = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));   // hi + p - s
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(e, pe));
+}
+// (hi, lo) += (h2, l2), both double-float
+__device__ __forceinline__ void df_add(float& hi, float& lo, float h2, float l2) {
+  const float s = __fadd_rn(hi, h2);
+  const float bb = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(h2, bb));   // hi + h2 - s
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(l2, e));
+}
+// (hi, lo) += a * conj(b), real and imaginary parts separately
+__device__ __forceinline__ void df_cmacc(float2& hi, float2& lo, float2 a, float2 b) {
+  df_add_prod(hi.x, lo.x, a.x, b.x);
+  df_add_prod(hi.x, lo.x, a.y, b.y);
+  df_add_prod(hi.y, lo.y, a.y, b.x);
+  df_add_prod(hi.y, lo.y, -a.x, b.y);
+}
+
 template <int MG>
 __device__ __forceinline__ float2 gshfl(float2 v, int src) {
   return make_float2(__shfl_sync(FULL, v.x, src, MG), __shfl_sync(FULL, v.y, src, MG));

@@ -29,14 +29,15 @@ struct SinrArgs {
   float2* Uout;                     // adjoint: left singular vectors [J][K][m][m] (or nullptr)
   float* Sout;                      // adjoint: singular values [J][K][m]
   float2* Vmout;                    // adjoint: right singular vectors [J][K][n][m]
-  float2* Rpart;                    // partial covariances [J][J-1][K][m][m] (workspace)
+  float2* Eint;                     // interfering effective channels E_ik, k != i,
+                                    // [J][J-1][K][m][L] (workspace)
   const float2* F;                  // mmse: G_ik x_2 Pt_k^T, [J*J][p][m][L] (workspace)
   const float* sigma2;              // [J]
   float* sinr;                      // [J][K][L]
   uint8_t* flags;                   // [J][K] or nullptr
   int* rlist;                       // units (i K + kappa) to refine (workspace) or nullptr
   int* rcount;                      // length of rlist (workspace, zeroed before finalize)
-  float refine_cond;                // refine when the Cholesky diagonal gives cond(R) above this
+  float refine_sens;                // refine units whose SINR sensitivity to R exceeds this
   // launch-shape choices (0: the default heuristics; set by the autotuner)
   int link_variant;                 // svd links: 1 blocked two-row kernel, 2 one-row kernel
   int precoder_split;               // precoder tile: subcarriers per CTA divided by 2^split
@@ -119,10 +120,19 @@ bool tc_supported(int m, int L, int p);
 size_t tc_prep_bytes(int J, int m, int L, int n, int p, int K, int prec);
 cudaError_t launch_core_prep(const SinrArgs& a, int prec, void* prep, cudaStream_t s);
 cudaError_t launch_sinr_links_tc(const SinrArgs& a, int prec, const void* prep, cudaStream_t s);
+// Widest serving channel (columns n) the register precoder stages whole.
+constexpr int kMaxNRegisterPrecoder = 512;
 // The SVD precoder forms H~_kk itself (re-reading the core G_kk once per
 // subcarrier tile from L2) when the core is at most 64 KB; larger cores (the
 // dense-channel comparator) go through a separate serving-link pass.
-inline bool precoder_fuses_serve(int m, int n, int p) { return (long long)m * n * p <= 8192; }
+inline bool precoder_fuses_serve(int m, int n, int p) {
+  return (long long)m * n * p <= 8192 && n <= kMaxNRegisterPrecoder;
+}
+// SVD precoders of units whose serving channels (m <= 16 rows, n columns)
+// do not fit the register precoder's shared-memory staging: the
+// shared-memory precoder of the large-m path, one CTA per (BS, subcarrier),
+// reading H~_kk from the serving pass's workspace (sinr_large.cu).
+cudaError_t launch_precoder_staged(const SinrArgs& a, cudaStream_t s);
 // Cores the narrow link kernels cannot stage (C_ik and a full core column
 // chunk in shared memory): the SVD path runs the wide-core kernel, which
 // streams the core in slabs and reads C_ik from L2.

@@ -10,7 +10,6 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
-#include <mutex>
 
 #include "kernels.h"
 #include "tuckersinr.h"
@@ -18,29 +17,22 @@
 namespace {
 
 // The scratch array.  Every GPU that loads the library holds it until the
-// process exits.  Host code must not use the name as a device address: the
-// address comes from cudaGetSymbolAddress (below).
+// process exits (it is committed when the library's module is loaded on the
+// device, at the first call there).  Host code must not use the name as a
+// device address: the address comes from cudaGetSymbolAddress (below).
 static __device__ __align__(256) unsigned char g_scratch[TS_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mutex;
-void* g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of g_scratch on the current device, looked up once per
-// device with that device current.  Returns a cudaError_t.
+// Device address of g_scratch on the current device, looked up on every
+// call with the call's device current.  Once the library's module is loaded
+// on a device the lookup is a host-side table read; looking up again rather
+// than caching keeps the address right after the device's context was reset
+// and recreated (cudaDeviceReset), when the module and its array move.
+// Returns a cudaError_t.
 cudaError_t scratch_address(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_mutex);
-  if (g_scratch_ptr[dev] == nullptr) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = p;
-  }
-  *out = g_scratch_ptr[dev];
+  *out = p;
   return cudaSuccess;
 }
 

@@ -1,17 +1,21 @@
-// Mixed-precision refinement of the SINR solves of ill-conditioned units
-// (eq. 26-28).  The finalize kernel factors R = sum_{k != i} E_ik E_ik* +
-// sigma^2 I in FP32 and, when the Cholesky diagonal says cond(R) is above
-// the threshold, appends the unit to a list.  Here one warp per listed unit
-// (lane a = row a, MG <= 16 lanes in use):
-//   1. rebuilds R and E_ii exactly as the finalize kernel read them and
-//      refactors R in FP32;
-//   2. solves Y = R^{-1} E_ii with the FP32 factor and refines it twice with
-//      residuals E_ii - R Y accumulated in FP64 (Y kept in FP64);
+// Mixed-precision re-evaluation of the SINR of sensitive units (eq. 25-28).
+// The finalize kernel forms R = sum_{k != i} E_ik E_ik* + sigma^2 I in FP32
+// and lists the units whose SINRs are sensitive to the rounding of R (a
+// perturbation of u ||R|| moves them by more than ~2e-6).  FP32 cannot hold
+// such an R closely enough: its weak directions, where the serving signal
+// lies, are ~sigma^2 while the rounding is ~u ||R||.  Here one warp per
+// listed unit (lane a = row a, MG <= 16 lanes in use):
+//   1. forms R again from the stored FP32 effective channels, in
+//      double-float (each product exact, sums compensated), so R is exact to
+//      ~2^-44 ||R|| for the given E;
+//   2. factors the leading FP32 part of R, solves Y = R^{-1} E_ii with that
+//      factor and refines it three times with residuals E_ii - R Y in FP64
+//      against the double-float R (Y kept in FP64);
 //   3. forms M = E_ii* Y (L x L) in FP64, factors F = I + M in FP64 (one
 //      lane) and evaluates SINR_r = (1 - x_r) / x_r with
 //      x_r = [F^{-1}]_rr = |L_F^{-1} e_r|^2 -- the stable form of eq. (5).
-// The O(m^3) factorization stays FP32; FP64 carries the residuals and the
-// L x L system.  The unit's flags get TS_FLAG_REFINED.
+// The O(m^3) factorization stays FP32; the products of R and the residuals
+// are where the precision goes.  The unit's flags get TS_FLAG_REFINED.
 #include "common.cuh"
 #include "kernels.h"
 #include "tuckersinr.h"
@@ -46,28 +50,49 @@ __global__ void __launch_bounds__(32 * kWarps) k_sinr_refine(const SinrArgs A) {
   for (int u = blockIdx.x * kWarps + warp; u < count; u += gridDim.x * kWarps) {
     const int unit = A.rlist[u];
     const int i = unit / K, kap = unit - i * K;
-    // 1. R and E_ii in the finalize kernel's order
-    float2 R0[MG], Eself[LT];
+    // 1. R in double-float from the stored effective channels, and E_ii
+    float2 Rh[MG], Rl[MG], Eself[LT];
 #pragma unroll
-    for (int b = 0; b < MG; ++b) R0[b] = cz();
+    for (int b = 0; b < MG; ++b) Rh[b] = Rl[b] = cz();
 #pragma unroll
     for (int l = 0; l < LT; ++l) Eself[l] = cz();
-    if (row) {
-      for (int s = 0; s < J - 1; ++s) {
-        const float2* Rin = A.Rpart + ((((size_t)i * (J - 1) + s) * K + kap) * m + a) * m;
+    for (int s = 0; s < J - 1; ++s) {
+      float2 Er[LT];
+      const float2* Ein = A.Eint + ((((size_t)i * (J - 1) + s) * K + kap) * m + (row ? a : 0)) * L;
 #pragma unroll
-        for (int b = 0; b < MG; ++b)
-          if (b < m) R0[b] = cadd(R0[b], Rin[b]);
-      }
+      for (int l = 0; l < LT; ++l) Er[l] = (row && l < L) ? Ein[l] : cz();
+      if (a < MG)
+#pragma unroll
+        for (int l = 0; l < LT; ++l) Es[a * LT + l] = Er[l];
+      __syncwarp();
+#pragma unroll
+      for (int b = 0; b < MG; ++b)
+#pragma unroll
+        for (int l = 0; l < LT; ++l) df_cmacc(Rh[b], Rl[b], Er[l], Es[b * LT + l]);
+      __syncwarp();
+    }
+    if (row) {
       const float2* Ein = A.Eserv + (((size_t)i * K + kap) * m + a) * L;
 #pragma unroll
       for (int l = 0; l < LT; ++l)
         if (l < L) Eself[l] = Ein[l];
     }
-    add_diag(R0, a, row ? A.sigma2[i] : 1.f);
+    // noise (exact), identity on the padding rows
+#pragma unroll
+    for (int b = 0; b < MG; ++b)
+      if (b == a) {
+        const float sg = row ? A.sigma2[i] : 1.f;
+        float sh, sl;
+        const float s0 = __fadd_rn(Rh[b].x, sg);
+        const float bb = __fsub_rn(s0, Rh[b].x);
+        sl = __fadd_rn(__fsub_rn(Rh[b].x, __fsub_rn(s0, bb)), __fsub_rn(sg, bb));
+        sh = s0;
+        Rh[b].x = sh;
+        Rl[b].x = __fadd_rn(Rl[b].x, sl);
+      }
     float2 Lr[MG];
 #pragma unroll
-    for (int b = 0; b < MG; ++b) Lr[b] = R0[b];
+    for (int b = 0; b < MG; ++b) Lr[b] = Rh[b];
     const bool ok = chol_rows<MG, MG>(Lr, a);
     if (!__all_sync(FULL, ok || a >= MG)) continue;     // keep the FP32 result
     // 2. Y = R^{-1} E_ii, refined with FP64 residuals
@@ -79,7 +104,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_sinr_refine(const SinrArgs A) {
     double2 Yd[LT];
 #pragma unroll
     for (int l = 0; l < LT; ++l) Yd[l] = d2(Yf[l]);
-    for (int it = 0; it < 2; ++it) {
+    for (int it = 0; it < 3; ++it) {
       if (a < MG)
 #pragma unroll
         for (int l = 0; l < LT; ++l) Ys[a * LT + l] = Yd[l];
@@ -91,7 +116,8 @@ __global__ void __launch_bounds__(32 * kWarps) k_sinr_refine(const SinrArgs A) {
         if (a < MG)
 #pragma unroll
           for (int b = 0; b < MG; ++b) {
-            const double2 rb = d2(R0[b]);
+            const double2 rb = make_double2((double)Rh[b].x + (double)Rl[b].x,
+                                            (double)Rh[b].y + (double)Rl[b].y);
             dmac(r, make_double2(-rb.x, -rb.y), Ys[b * LT + l]);
           }
         Df[l] = make_float2((float)r.x, (float)r.y);

@@ -352,11 +352,16 @@ __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, con
 #pragma unroll
     for (int b = 0; b < MG; ++b) S[b] = cscale(S[b], sc);
   }
-  // Cyclic Jacobi on S held in registers (see jacobi_step), to FP32
-  // convergence (relative off-diagonal norm ~5e-7).  The stopping decision is
-  // taken warp-wide (extra sweeps leave a converged S unchanged).
-  const int max_sweeps = MG <= 8 ? 10 : 12;
-  bool converged = false;
+  // Cyclic Jacobi on S held in registers (see jacobi_step), until the
+  // relative off-diagonal norm is below ~5e-7, then one more sweep: Jacobi
+  // converges quadratically, so that sweep takes the off-diagonal from
+  // ~5e-7 to rounding level.  Without it a pair of eigenvalues a relative
+  // gap g apart keeps its eigenvectors mixed by ~5e-7 / g (up to 3e-4 in
+  // the per-stream SINR for g ~ 1e-3); with it the mixing is the FP32
+  // Gram's own ~u / g.  The stopping decision is taken warp-wide (extra
+  // sweeps leave a converged S unchanged).
+  const int max_sweeps = MG <= 8 ? 11 : 13;
+  bool converged = false, polish = false;
   for (int sweep = 0;; ++sweep) {
     float off = 0.f, dia = 0.f;
 #pragma unroll
@@ -367,28 +372,56 @@ __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, con
     off = gsum<MG>(off);
     dia = gsum<MG>(dia);
     converged = off <= 2.3e-13f * dia;
-    if (__all_sync(FULL, converged) || sweep == max_sweeps) break;
+    const bool all = __all_sync(FULL, converged);
+    if ((all && polish) || sweep == max_sweeps) break;
+    polish = all;
     float dg = pick(S, a).x;
 #pragma unroll
     for (int t = 0; t < MG - 1; ++t) jacobi_step<MG>(t, S, U, dg, a);
   }
+  // The rotations come from hardware reciprocal square roots and each is
+  // applied in FP32, so U leaves the sweeps unitary only to ~1e-7 .. 1e-6:
+  // its columns drift from unit norm (the serving effective channel
+  // E_kk = U_L Sigma_L below scales with them) and from each other (which
+  // the close-pair rotation below would amplify by lambda / gap).  One pass
+  // of modified Gram-Schmidt over the columns makes U unitary to rounding;
+  // it moves each column by the size of its defect only.
+  {
+#pragma unroll
+    for (int b = 0; b < MG; ++b) {
+      const float nb = gsum<MG>(cabs2(U[b]));
+      U[b] = cscale(U[b], nb > 0.f ? 1.f / sqrtf(nb) : 1.f);
+#pragma unroll
+      for (int b2 = b + 1; b2 < MG; ++b2) {
+        // U[:, b2] -= (U[:, b]* U[:, b2]) U[:, b]
+        float2 pr = cz();
+        cmacc(pr, U[b2], U[b]);                     // U_ab2 conj(U_ab)
+        pr.x = gsum<MG>(pr.x);
+        pr.y = gsum<MG>(pr.y);
+        cms(U[b2], pr, U[b]);
+      }
+    }
+  }
   // The eigenvectors of the Gram are accurate unless a kept singular value is
   // small: refine with one-sided sweeps (below) when lambda_L < 1e-4 lambda_1
-  // in any group of the warp.
+  // in any group of the warp.  `erank` (the eigenvalue's rank) and `lam`
+  // also select the close pairs polished after them.
   bool need_refine;
+  int erank;
+  float lam, lmax;
   {
-    const float lam = (a < m) ? pick(S, a).x : -INFINITY;
-    float lmax = lam;
+    lam = (a < m) ? pick(S, a).x : -INFINITY;
+    lmax = lam;
 #pragma unroll
     for (int o = 1; o < MG; o <<= 1) lmax = fmaxf(lmax, __shfl_xor_sync(FULL, lmax, o, MG));
     // rank of this lane's eigenvalue; the L-th largest decides
-    int rank = 0;
+    erank = 0;
 #pragma unroll
     for (int b = 0; b < MG; ++b) {
       const float lb = __shfl_sync(FULL, lam, b, MG);
-      rank += (lb > lam) || (lb == lam && b < a);
+      erank += (lb > lam) || (lb == lam && b < a);
     }
-    const bool small_kept = (a < m) && (rank < L) && !(lam >= 1e-4f * lmax);
+    const bool small_kept = (a < m) && (erank < L) && !(lam >= 1e-4f * lmax);
     need_refine = __any_sync(FULL, small_kept);
   }
 #pragma unroll
@@ -482,6 +515,77 @@ __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, con
       for (int o = 2; o < MG; o <<= 1) worst = fmaxf(worst, __shfl_xor_sync(FULL, worst, o, MG));
       refined = worst <= 1e-12f;
       if (__all_sync(FULL, refined)) break;
+    }
+  }
+
+  // Close pairs.  Two eigenvalues of rank r and r + 1 (r < L) within 2% of
+  // lambda_1 of each other are mixed by the Gram's FP32 rounding by about
+  // u lambda_1 / (lambda_r - lambda_r+1) (up to ~5e-5 rad on the synthetic
+  // channels), and the per-stream SINRs follow that mixing (~0.5 per rad).
+  // Each such pair of rows of W is rotated once more, with the 2 x 2 Gram
+  // of the rows accumulated in double-float (the rotation angle then comes
+  // with FP32 relative accuracy), so that the mixing drops to the rounding
+  // of W itself.
+  {
+    const int gb = (threadIdx.x & 31) / MG * MG;            // group's first lane in the warp
+    const unsigned gmask = MG == 32 ? FULL : ((1u << MG) - 1u) << gb;
+    for (int r = 0; r < L && r + 1 < m; ++r) {
+      const unsigned bp = __ballot_sync(FULL, a < m && erank == r) & gmask;
+      const unsigned bq = __ballot_sync(FULL, a < m && erank == r + 1) & gmask;
+      const int pp = bp ? __ffs(bp) - 1 - gb : 0, qq = bq ? __ffs(bq) - 1 - gb : 0;
+      const float lp = __shfl_sync(FULL, lam, pp, MG), lq = __shfl_sync(FULL, lam, qq, MG);
+      const bool close = bp && bq && (lp - lq) < 2e-2f * lmax;
+      if (!__any_sync(FULL, close)) continue;
+      float alh = 0.f, all = 0.f, beh = 0.f, bel = 0.f;
+      float2 gah = cz(), gal = cz();
+      if (close)
+        for (int c = a; c < n; c += MG) {
+          const float2 x = Hs[pp * pl.SH + c], y = Hs[qq * pl.SH + c];
+          df_add_prod(alh, all, x.x, x.x);
+          df_add_prod(alh, all, x.y, x.y);
+          df_add_prod(beh, bel, y.x, y.x);
+          df_add_prod(beh, bel, y.y, y.y);
+          df_cmacc(gah, gal, x, y);                          // sum x conj(y)
+        }
+      // group sums of the double-float partials (TwoSum on the high parts)
+#pragma unroll
+      for (int o = 1; o < MG; o <<= 1) {
+        df_add(alh, all, __shfl_xor_sync(FULL, alh, o, MG), __shfl_xor_sync(FULL, all, o, MG));
+        df_add(beh, bel, __shfl_xor_sync(FULL, beh, o, MG), __shfl_xor_sync(FULL, bel, o, MG));
+        df_add(gah.x, gal.x, __shfl_xor_sync(FULL, gah.x, o, MG), __shfl_xor_sync(FULL, gal.x, o, MG));
+        df_add(gah.y, gal.y, __shfl_xor_sync(FULL, gah.y, o, MG), __shfl_xor_sync(FULL, gal.y, o, MG));
+      }
+      // be - al without cancellation (the high parts are within a factor 2
+      // of each other for a close pair, so their difference is exact)
+      const float dba = __fadd_rn(__fsub_rn(beh, alh), __fsub_rn(bel, all));
+      const float gx = gah.x + gal.x, gy = gah.y + gal.y;
+      const float ab = sqrtf(fmaf(gx, gx, gy * gy));
+      const float scale = sqrtf(alh) * sqrtf(beh);
+      if (close && ab > 0.f && ab > 1e-12f * scale) {
+        const float tau = dba / (2.f * ab);
+        const float t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
+        const float cr = 1.f / sqrtf(fmaf(t, t, 1.f));
+        const float sr = t * cr;
+        const float2 e = make_float2(gx / ab, gy / ab);
+        const float2 se = cscale(e, sr), sec = cscale(cconj(e), sr);
+        for (int c = a; c < n; c += MG) {                    // W <- J* W (rows p, q)
+          const float2 x = Hs[pp * pl.SH + c], y = Hs[qq * pl.SH + c];
+          float2 nx = cscale(x, cr), ny = cscale(y, cr);
+          cms(nx, se, y);
+          cmac(ny, sec, x);
+          Hs[pp * pl.SH + c] = nx;
+          Hs[qq * pl.SH + c] = ny;
+        }
+        {                                                    // U <- U J (columns p, q), row a
+          const float2 x = Us[a * pl.SS + pp], y = Us[a * pl.SS + qq];
+          float2 nx = cscale(x, cr), ny = cscale(y, cr);
+          cms(nx, sec, y);
+          cmac(ny, se, x);
+          Us[a * pl.SS + pp] = nx;
+          Us[a * pl.SS + qq] = ny;
+        }
+      }
+      __syncwarp();
     }
   }
 
@@ -796,19 +900,13 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link(const SinrArgs A, const 
       if (l < L) Eout[l] = E[l];
     return;
   }
-  // partial covariance rows (E E*)[a][b], b < m (eq. 25)
-  float2* Es = sm + pl.off_Es + g * pl.ES;
-#pragma unroll
-  for (int l = 0; l < LT; ++l) Es[a * LT + l] = E[l];
-  __syncwarp(__activemask());
+  // row a of the interfering effective channel E_ik (eq. 24); the
+  // finalisation forms the covariance of eq. (25) from all of them
   const int slot = MODE == kModeSvd ? z : (z < i ? z : z - 1);
-  float2* Rout = A.Rpart + ((((size_t)i * (J - 1) + slot) * K + kap) * m + a) * m;
-  for (int b = 0; b < m; ++b) {
-    float2 r = cz();
+  float2* Eout = A.Eint + ((((size_t)i * (J - 1) + slot) * K + kap) * m + a) * L;
 #pragma unroll
-    for (int l = 0; l < LT; ++l) cmacc(r, E[l], Es[b * LT + l]);
-    Rout[b] = r;
-  }
+  for (int l = 0; l < LT; ++l)
+    if (l < L) Eout[l] = E[l];
 }
 
 // SINR of one unit from row a of R = interference + noise (padding rows set
@@ -1077,16 +1175,8 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link_blk(const SinrArgs A, co
   }
   cp_async_wait<0>();
 
-  // partial covariance rows (E E*)[a][b], b < m (eq. 25), for both subcarriers;
-  // the group's scratch reuses the stage buffers
-  float2* Es = stage0 + gp * (2 * MG * LT + 2);
-#pragma unroll
-  for (int x = 0; x < 2; ++x)
-#pragma unroll
-    for (int r = 0; r < 2; ++r)
-#pragma unroll
-      for (int l = 0; l < LT; ++l) Es[(x * MG + j + r * GL) * LT + l] = E[x][r][l];
-  __syncwarp();
+  // rows j and j + GL of the interfering effective channel E_ik (eq. 24) for
+  // both subcarriers; the finalisation forms the covariance of eq. (25)
 #pragma unroll
   for (int x = 0; x < 2; ++x) {
     const int kap = kap0 + 2 * gp + x;
@@ -1095,14 +1185,10 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link_blk(const SinrArgs A, co
     for (int r = 0; r < 2; ++r) {
       const int a = j + r * GL;
       if (a >= m) continue;
-      float2* Rout = A.Rpart + ((((size_t)i * (J - 1) + z) * K + kap) * m + a) * m;
-      for (int b = 0; b < m; ++b) {
-        float2 acc = cz();
-        const float2* eb = Es + (x * MG + b) * LT;
+      float2* Eout = A.Eint + ((((size_t)i * (J - 1) + z) * K + kap) * m + a) * L;
 #pragma unroll
-        for (int l = 0; l < LT; ++l) cmacc(acc, E[x][r][l], eb[l]);
-        Rout[b] = acc;
-      }
+      for (int l = 0; l < LT; ++l)
+        if (l < L) Eout[l] = E[x][r][l];
     }
   }
 }
@@ -1119,43 +1205,73 @@ __global__ void __launch_bounds__(kThreads) k_sinr_finalize(const SinrArgs A, in
   const int kc = kap < K ? kap : K - 1;     // tail groups recompute the last subcarrier
   float2* Es = sm_es + g * (MG * LT + 2);
 
+  // R = sum_{k != i} E_ik E_ik* (eq. 25 without the serving term): row a of
+  // each interfering effective channel through the group's scratch
   float2 R[MG], Eself[LT];
 #pragma unroll
   for (int b = 0; b < MG; ++b) R[b] = cz();
-  if (a < m) {
-    for (int s = 0; s < J - 1; ++s) {
-      const float2* Rin = A.Rpart + ((((size_t)i * (J - 1) + s) * K + kc) * m + a) * m;
+  for (int s = 0; s < J - 1; ++s) {
+    float2 Er[LT];
+    const float2* Ein = A.Eint + ((((size_t)i * (J - 1) + s) * K + kc) * m + (a < m ? a : 0)) * L;
 #pragma unroll
-      for (int b = 0; b < MG; ++b)
-        if (b < m) R[b] = cadd(R[b], Rin[b]);
+    for (int l = 0; l < LT; ++l) Er[l] = (a < m && l < L) ? Ein[l] : cz();
+#pragma unroll
+    for (int l = 0; l < LT; ++l) Es[a * LT + l] = Er[l];
+    __syncwarp();
+#pragma unroll
+    for (int b = 0; b < MG; ++b) {
+#pragma unroll
+      for (int l2 = 0; l2 < LT / 2; ++l2) {
+        const float4 e = reinterpret_cast<const float4*>(Es + b * LT)[l2];
+        cmacc(R[b], Er[2 * l2], make_float2(e.x, e.y));
+        cmacc(R[b], Er[2 * l2 + 1], make_float2(e.z, e.w));
+      }
     }
-    // serving effective channel E_ii (eq. 24), from the precoder phase (svd)
-    // or from the serving-link pass of k_sinr_link (wideband precoder)
-    const float2* Ein = A.Eserv + (((size_t)i * K + kc) * m + a) * L;
+    __syncwarp();
+  }
+  // serving effective channel E_ii (eq. 24), from the precoder phase (svd)
+  // or from the serving-link pass of k_sinr_link (wideband precoder)
+  {
+    const float2* Ein = A.Eserv + (((size_t)i * K + kc) * m + (a < m ? a : 0)) * L;
 #pragma unroll
-    for (int l = 0; l < LT; ++l) Eself[l] = (l < L) ? Ein[l] : cz();
-  } else {
-#pragma unroll
-    for (int l = 0; l < LT; ++l) Eself[l] = cz();
+    for (int l = 0; l < LT; ++l) Eself[l] = (a < m && l < L) ? Ein[l] : cz();
   }
 
   // noise on the m x m block, identity on the padding rows (eq. 25)
   add_diag(R, a, a < m ? A.sigma2[i] : 1.f);
+  float Ra2[MG];                                  // |R_ab|^2, for the listing below
+#pragma unroll
+  for (int b = 0; b < MG; ++b) Ra2[b] = (a < m && b < m) ? cabs2(R[b]) : 0.f;
   float2 Lq[MG], Zq[LT];
   float as[LT], xs[LT];
   const bool ok = sinr_core<MG, LT>(R, Eself, Es, a, Lq, Zq, as, xs);
-  // ill-conditioned R (cond from the Cholesky diagonal, a lower bound) ->
-  // listed for the FP64-residual refinement pass
+  // Units whose SINRs are sensitive to the FP32 rounding of R are listed for
+  // the refinement pass.  To first order SINR_r moves with y_r* dR y_r, where
+  // y_r = R^{-1} e_r and e_r* y_r is its scale; the rounding of R perturbs
+  // each entry by ~u |R_ab| with uncorrelated signs, so the estimate is
+  //   s = max_r sqrt(sum_ab |y_ar|^2 |R_ab|^2 |y_br|^2) / (e_r* y_r)
+  // and the relative error is a few u s (at most ~5 u s on the channel
+  // models tried: s ~ 1 for the compressed workloads, 1e2 .. 2e2 for
+  // low-rank interference on a small noise floor).  Listed when s exceeds
+  // the threshold.
   if (A.rlist != nullptr) {
-    const float d = a < m ? pick(R, a).x : 1.f;
-    float dmax = a < m ? d : 0.f, dmin = a < m ? d : INFINITY;
+    float2 Y[LT];
 #pragma unroll
-    for (int o = 1; o < MG; o <<= 1) {
-      dmax = fmaxf(dmax, __shfl_xor_sync(FULL, dmax, o, MG));
-      dmin = fminf(dmin, __shfl_xor_sync(FULL, dmin, o, MG));
+    for (int l = 0; l < LT; ++l) Y[l] = Eself[l];
+    trsv_rows<MG, MG, LT>(R, Y, a);                 // R holds chol(R) here
+    trsv_rows_conjT<MG, MG, LT>(R, Y, a);           // Y = R^{-1} E_ii
+    float sens = 0.f;
+#pragma unroll
+    for (int l = 0; l < LT; ++l) {
+      const float y2 = a < m ? cabs2(Y[l]) : 0.f;
+      float t = 0.f;                                // sum_b |R_ab|^2 |y_br|^2
+#pragma unroll
+      for (int b = 0; b < MG; ++b) t = fmaf(Ra2[b], __shfl_sync(FULL, y2, b, MG), t);
+      const float num = gsum<MG>(y2 * t);
+      const float den = gsum<MG>(fmaf(Eself[l].x, Y[l].x, Eself[l].y * Y[l].y));
+      if (l < L && den > 0.f) sens = fmaxf(sens, sqrtf(num) / den);
     }
-    const float c = (dmax / dmin) * (dmax / dmin);
-    if (ok && kap < K && a == 0 && c > A.refine_cond) {
+    if (ok && kap < K && a == 0 && !(sens <= A.refine_sens)) {
       const int pos = atomicAdd(A.rcount, 1);
       if (pos < A.J * K) A.rlist[pos] = i * K + kap;
     }
@@ -1194,7 +1310,9 @@ cudaError_t run_precoder(const SinrArgs& A, cudaStream_t s) {
     pl = precoder_plan(MG, T, A.n, A.p, fused);
   }
   const size_t smem = (size_t)pl.total * sizeof(float2);
-  if (smem > kSmemBudget) return cudaErrorInvalidValue;
+  // serving channels too wide to stage per group (n up to 1024, read from
+  // the serving pass's workspace): the shared-memory precoder
+  if (smem > kSmemBudget) return fused ? cudaErrorInvalidValue : launch_precoder_staged(A, s);
   auto kern = k_svd_precoder<MG, LT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -9,11 +9,11 @@
 //                         rotation by one thread, its rows and columns by
 //                         lane j of every warp), V~ = conj(rows of U_L* H~)
 //                         / sigma and E_kk = U_L Sigma_L (eq. 7, eq. 24);
-//   k_sinr_finalize_large R = sum_{k != i} E E* + sigma^2 I (eq. 25),
-//                         Z = L_R^{-1} E_ii, x_r = [(I + Z*Z)^{-1}]_rr,
-//                         a_r = |L_Q^{-1} e_r|^2 with Q~ = R + E_ii E_ii*,
-//                         SINR_r = a_r / x_r (eq. 5 without cancellation).
-// No FP64-residual refinement pass for these sizes.
+//   k_sinr_finalize_large R = sum_{k != i} E E* + sigma^2 I (eq. 25) in
+//                         double-float, Y = R^{-1} E_ii from its FP32
+//                         Cholesky factor with FP64-residual refinement,
+//                         x_r = [(I + E_ii* Y)^{-1}]_rr in FP64,
+//                         SINR_r = (1 - x_r) / x_r (eq. 5).
 #include "sinr_impl.cuh"
 
 namespace ts {
@@ -134,8 +134,12 @@ __global__ void __launch_bounds__(kLargeThreads) k_svd_precoder_large(const Sinr
   // linearly from rounding noise and exhausts the sweeps).
   const float eps_null = (float)m * 5.9604645e-8f;     // m 2^-24 of the unit trace
   const int lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
-  bool converged = false;
-  for (int sweep = 0; sweep <= 16; ++sweep) {
+  // Once the threshold is met, one more sweep takes the off-diagonal to
+  // rounding level (quadratic convergence), so that nearly equal
+  // eigenvalues a relative gap g apart keep only the FP32 Gram's ~u / g
+  // mixing of their eigenvectors, not ~5e-7 / g.
+  bool converged = false, polish = false;
+  for (int sweep = 0; sweep <= 17; ++sweep) {
     float off = 0.f, tot = 0.f;
     for (int idx = tid; idx < m * m; idx += nth) {
       const int a = idx / m, b = idx - a * m;
@@ -146,7 +150,8 @@ __global__ void __launch_bounds__(kLargeThreads) k_svd_precoder_large(const Sinr
     off = block_sum(off, red);
     tot = block_sum(tot, red);
     converged = off <= 2.3e-13f * tot;
-    if (converged || sweep == 16) break;
+    if ((converged && polish) || sweep == 17) break;
+    polish = converged;
     // one step: the DE/2 disjoint pairs of the round-robin ordering; their
     // rotations by one thread each, then the rows of S and the columns of S
     // and U, lane j of every warp on pair j (its rotation loaded once) and
@@ -308,104 +313,202 @@ __device__ bool chol_block(float2* R, int m, int SD, int* bad) {
   return *bad == 0;
 }
 
-// R = sum of the partial covariances + sigma^2 I (+ E E* when with_e)
-__device__ void build_r(const SinrArgs& A, int i, int kap, float2* R, int SD, const float2* E,
-                        bool with_e) {
-  const int m = A.m, J = A.J, K = A.K, L = A.L;
-  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-    const int a = idx / m, b = idx - a * m;
-    float2 v = a == b ? make_float2(A.sigma2[i], 0.f) : cz();
-    for (int s = 0; s < J - 1; ++s)
-      v = cadd(v, A.Rpart[(((size_t)i * (J - 1) + s) * K + kap) * m * m + idx]);
-    if (with_e)
-      for (int l = 0; l < L; ++l) cmacc(v, E[a * L + l], E[b * L + l]);
-    R[a * SD + b] = v;
+// Lower-triangular solves with the FP32 factor in R (row stride SD), thread
+// r on column r of the m x L right-hand side in X (row stride L), in place:
+// X <- L^{-1} X, then (conjT) X <- L^{-*} X.
+__device__ void solve_lower(const float2* R, int SD, int m, float2* X, int L, int r) {
+  for (int a = 0; a < m; ++a) {
+    float2 v = X[a * L + r];
+    for (int b = 0; b < a; ++b) cms(v, R[a * SD + b], X[b * L + r]);
+    X[a * L + r] = cscale(v, 1.f / R[a * SD + a].x);
   }
-  __syncthreads();
+}
+__device__ void solve_lower_conjT(const float2* R, int SD, int m, float2* X, int L, int r) {
+  for (int a = m - 1; a >= 0; --a) {
+    float2 v = X[a * L + r];
+    for (int b = a + 1; b < m; ++b) cmsc(v, X[b * L + r], R[b * SD + a]);   // v -= conj(L[b][a]) x_b
+    X[a * L + r] = cscale(v, 1.f / R[a * SD + a].x);
+  }
 }
 
-// y = L^{-1} e_col for the lower factor in R: thread r solves column r of E
-__device__ float forward_norm2(const float2* R, int SD, int m, const float2* E, int L, int r,
-                               float2* Y) {
-  float s = 0.f;
-  for (int a = 0; a < m; ++a) {
-    float2 v = E[a * L + r];
-    for (int b = 0; b < a; ++b) cms(v, R[a * SD + b], Y[b * L + r]);
-    v = cscale(v, 1.f / R[a * SD + a].x);
-    Y[a * L + r] = v;
-    s += cabs2(v);
-  }
-  return s;
+__device__ __forceinline__ void dmac_l(double2& acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+
+// Finalisation of one unit with m up to 64 rows (eq. 25-28).  With many
+// rows the interference covariance R = sum_{k != i} E_ik E_ik* + sigma^2 I
+// has a wide spectrum (a low-rank interference on sigma^2 I), and its FP32
+// rounding alone moves the SINR by u ||R|| / sigma^2 ~ 1e-5, so every unit
+// is evaluated the accurate way:
+//   1. R in double-float from the stored FP32 effective channels (each
+//      product exact, the sums compensated), shared memory Rh + Rl;
+//   2. Cholesky of the FP32 part Rh (chol_block), Y = R^{-1} E_ii with that
+//      factor, refined three times with residuals E_ii - R Y in FP64;
+//   3. F = I + E_ii* Y (L x L) and its Cholesky factor in FP64,
+//      x_r = [F^{-1}]_rr, SINR_r = (1 - x_r) / x_r (the identity form of
+//      eq. 5, exact in FP64 for the refined Y).
+// TS_FLAG_REFINED is set on every unit of this path.
+struct LargeFinPlan {
+  int SD, off_Rh, off_Rl, off_Lf, off_E, off_Es, off_X, off_Yd, off_F, off_misc, total;  // float2 units
+};
+__host__ __device__ inline LargeFinPlan large_fin_plan(int m, int L, int LT) {
+  LargeFinPlan pl;
+  pl.SD = m + 1;
+  int o = 0;
+  pl.off_Rh = o; o += m * pl.SD;
+  pl.off_Rl = o; o += m * pl.SD;
+  pl.off_Lf = o; o += m * pl.SD;
+  pl.off_E = o; o += m * L;
+  pl.off_Es = o; o += m * L;                 // one interferer's E, then the residual
+  pl.off_X = o; o += m * L;
+  o = (o + 1) & ~1;
+  pl.off_Yd = o; o += 2 * m * L;             // double2
+  pl.off_F = o; o += 2 * LT * LT;            // double2
+  pl.off_misc = o; o += 2 * LT + 4;          // x_r (double), flag
+  pl.total = o;
+  return pl;
 }
 
 template <int MG, int LT, bool SVD>
-__global__ void __launch_bounds__(kLargeThreads) k_sinr_finalize_large(const SinrArgs A) {
+__global__ void __launch_bounds__(kLargeThreads) k_sinr_finalize_large(const SinrArgs A,
+                                                                       const LargeFinPlan pl) {
   extern __shared__ __align__(16) float2 sm[];
   const int m = A.m, L = A.L, K = A.K, J = A.J;
   const int kap = blockIdx.x, i = blockIdx.y;
-  const int tid = threadIdx.x;
-  const int SD = m + 1;
-  float2* R = sm;                       // m x SD
-  float2* E = R + m * SD;               // m x L
-  float2* Z = E + m * L;                // m x L
-  float2* F = Z + m * L;                // L x L
-  float* xs = reinterpret_cast<float*>(F + LT * LT);   // [LT] x, [LT] a
-  int* bad = reinterpret_cast<int*>(xs + 2 * LT);
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int SD = pl.SD;
+  float2* Rh = sm + pl.off_Rh;
+  float2* Rl = sm + pl.off_Rl;
+  float2* Lf = sm + pl.off_Lf;
+  float2* E = sm + pl.off_E;
+  float2* Es = sm + pl.off_Es;
+  float2* X = sm + pl.off_X;
+  double2* Yd = reinterpret_cast<double2*>(sm + pl.off_Yd);
+  double2* F = reinterpret_cast<double2*>(sm + pl.off_F);
+  double* xs = reinterpret_cast<double*>(sm + pl.off_misc);
+  int* bad = reinterpret_cast<int*>(xs + LT);
 
-  for (int idx = tid; idx < m * L; idx += blockDim.x)
-    E[idx] = A.Eserv[((size_t)i * K + kap) * m * L + idx];
+  for (int idx = tid; idx < m * L; idx += nth) E[idx] = A.Eserv[((size_t)i * K + kap) * m * L + idx];
+  // 1. R = sigma^2 I + sum_s E_s E_s*, lower triangle, double-float
+  const float sg = A.sigma2[i];
+  for (int idx = tid; idx < m * m; idx += nth) {
+    const int a = idx / m, b = idx - a * m;
+    Rh[a * SD + b] = make_float2(a == b ? sg : 0.f, 0.f);
+    Rl[a * SD + b] = cz();
+  }
+  for (int s = 0; s < J - 1; ++s) {
+    __syncthreads();                             // previous interferer consumed
+    for (int idx = tid; idx < m * L; idx += nth)
+      Es[idx] = A.Eint[(((size_t)i * (J - 1) + s) * K + kap) * m * L + idx];
+    __syncthreads();
+    for (int idx = tid; idx < m * m; idx += nth) {
+      const int a = idx / m, b = idx - a * m;
+      if (b > a) continue;
+      float2 h = Rh[a * SD + b], lo = Rl[a * SD + b];
+      for (int l = 0; l < L; ++l) df_cmacc(h, lo, Es[a * L + l], Es[b * L + l]);
+      Rh[a * SD + b] = h;
+      Rl[a * SD + b] = lo;
+    }
+  }
   __syncthreads();
-  // x_r = [(I + Z*Z)^{-1}]_rr with Z = L_R^{-1} E_ii
-  build_r(A, i, kap, R, SD, E, false);
-  bool ok = chol_block(R, m, SD, bad);
-  if (tid < L) forward_norm2(R, SD, m, E, L, tid, Z);
+  for (int idx = tid; idx < m * m; idx += nth) {
+    const int a = idx / m, b = idx - a * m;
+    if (b <= a) Lf[a * SD + b] = Rh[a * SD + b];
+  }
   __syncthreads();
-  for (int idx = tid; idx < L * L; idx += blockDim.x) {
+  // 2. factor, solve, refine
+  bool ok = chol_block(Lf, m, SD, bad);
+  for (int idx = tid; idx < m * L; idx += nth) X[idx] = E[idx];
+  __syncthreads();
+  if (tid < L) {
+    solve_lower(Lf, SD, m, X, L, tid);
+    solve_lower_conjT(Lf, SD, m, X, L, tid);
+  }
+  __syncthreads();
+  for (int idx = tid; idx < m * L; idx += nth) Yd[idx] = make_double2(X[idx].x, X[idx].y);
+  for (int it = 0; it < 3; ++it) {
+    __syncthreads();
+    // residual E - R Y in FP64 (R Hermitian: entries above the diagonal
+    // are the conjugates of the stored lower triangle)
+    for (int idx = tid; idx < m * L; idx += nth) {
+      const int a = idx / L, r = idx - a * L;
+      double2 acc = make_double2(E[idx].x, E[idx].y);
+      for (int b = 0; b < m; ++b) {
+        const bool lower = b <= a;
+        const int at = lower ? a * SD + b : b * SD + a;
+        double2 rv = make_double2((double)Rh[at].x + (double)Rl[at].x, (double)Rh[at].y + (double)Rl[at].y);
+        if (!lower) rv.y = -rv.y;
+        dmac_l(acc, make_double2(-rv.x, -rv.y), Yd[b * L + r]);
+      }
+      X[idx] = make_float2((float)acc.x, (float)acc.y);
+    }
+    __syncthreads();
+    if (tid < L) {
+      solve_lower(Lf, SD, m, X, L, tid);
+      solve_lower_conjT(Lf, SD, m, X, L, tid);
+    }
+    __syncthreads();
+    for (int idx = tid; idx < m * L; idx += nth) {
+      Yd[idx].x += X[idx].x;
+      Yd[idx].y += X[idx].y;
+    }
+  }
+  __syncthreads();
+  // 3. F = I + E* Y (FP64), its factor, x_r
+  for (int idx = tid; idx < L * L; idx += nth) {
     const int r = idx / L, s = idx - r * L;
-    float2 v = make_float2(r == s ? 1.f : 0.f, 0.f);
-    for (int a = 0; a < m; ++a) cmacc(v, Z[a * L + s], Z[a * L + r]);
+    double2 v = make_double2(r == s ? 1.0 : 0.0, 0.0);
+    for (int a = 0; a < m; ++a) dmac_l(v, make_double2(E[a * L + r].x, -E[a * L + r].y), Yd[a * L + s]);
     F[r * LT + s] = v;
   }
   __syncthreads();
   if (tid == 0) {
-    // F = L_F L_F* in place (lower), L <= 8
+    int fbad = 0;
     for (int j = 0; j < L; ++j) {
-      float d = F[j * LT + j].x;
-      for (int t = 0; t < j; ++t) d -= cabs2(F[j * LT + t]);
-      if (!(d > 0.f)) { *bad = 1; d = 1.f; }
-      const float ljj = sqrtf(d);
-      F[j * LT + j] = make_float2(ljj, 0.f);
+      double d = F[j * LT + j].x;
+      for (int t = 0; t < j; ++t) d -= F[j * LT + t].x * F[j * LT + t].x + F[j * LT + t].y * F[j * LT + t].y;
+      if (!(d > 0.0)) { fbad = 1; d = 1.0; }
+      const double ljj = sqrt(d);
+      F[j * LT + j] = make_double2(ljj, 0.0);
       for (int r = j + 1; r < L; ++r) {
-        float2 v = F[r * LT + j];
-        for (int t = 0; t < j; ++t) cms(v, F[r * LT + t], cconj(F[j * LT + t]));
-        F[r * LT + j] = cscale(v, 1.f / ljj);
+        double2 v = F[r * LT + j];
+        for (int t = 0; t < j; ++t) {
+          const double2 x = F[r * LT + t], y = F[j * LT + t];
+          v.x -= x.x * y.x + x.y * y.y;
+          v.y -= x.y * y.x - x.x * y.y;
+        }
+        F[r * LT + j] = make_double2(v.x / ljj, v.y / ljj);
       }
     }
+    if (fbad) *bad = 1;
   }
   __syncthreads();
   ok = ok && *bad == 0;
   if (tid < L) {
     // x_r = |L_F^{-1} e_r|^2 by forward substitution from row r
-    float2 y[LT];
-    float x = 0.f;
+    double2 y[LT];
+    double x = 0.0;
 #pragma unroll
     for (int s = 0; s < LT; ++s) {
-      y[s] = cz();
+      y[s] = make_double2(0.0, 0.0);
       if (s < tid || s >= L) continue;
-      float2 v = make_float2(s == tid ? 1.f : 0.f, 0.f);
+      double2 v = make_double2(s == tid ? 1.0 : 0.0, 0.0);
 #pragma unroll
       for (int t = 0; t < LT; ++t)
-        if (t >= tid && t < s) cms(v, F[s * LT + t], y[t]);
-      y[s] = cscale(v, 1.f / F[s * LT + s].x);
-      x += cabs2(y[s]);
+        if (t >= tid && t < s) {
+          const double2 l = F[s * LT + t];
+          v.x -= l.x * y[t].x - l.y * y[t].y;
+          v.y -= l.x * y[t].y + l.y * y[t].x;
+        }
+      const double lss = F[s * LT + s].x;
+      y[s] = make_double2(v.x / lss, v.y / lss);
+      x += y[s].x * y[s].x + y[s].y * y[s].y;
     }
     xs[tid] = x;
   }
-  __syncthreads();
-  // a_r = |L_Q^{-1} e_r|^2 with Q~ = R + E_ii E_ii*
-  build_r(A, i, kap, R, SD, E, true);
-  ok = chol_block(R, m, SD, bad) && ok;
-  if (tid < L) xs[LT + tid] = forward_norm2(R, SD, m, E, L, tid, Z);
   __syncthreads();
 
   uint8_t pf = 0;
@@ -414,12 +517,12 @@ __global__ void __launch_bounds__(kLargeThreads) k_sinr_finalize_large(const Sin
   const bool valid = ok && !(pf & TS_FLAG_TIMEOUT);
   bool finite = true;
   for (int r = 0; r < L; ++r) {
-    const float sv = valid ? xs[LT + r] / xs[r] : __int_as_float(0x7fc00000);
+    const float sv = valid ? (float)((1.0 - xs[r]) / xs[r]) : __int_as_float(0x7fc00000);
     finite = finite && isfinite(sv);
     if (tid == 0) A.sinr[((size_t)i * K + kap) * L + r] = sv;
   }
   if (A.flags != nullptr && tid == 0) {
-    uint8_t f = ok ? 0 : TS_FLAG_NOT_PD;
+    uint8_t f = ok ? TS_FLAG_REFINED : TS_FLAG_NOT_PD;
     if (valid && !finite) f |= TS_FLAG_NONFINITE;
     A.flags[(size_t)i * K + kap] = f | pf;
   }
@@ -439,13 +542,13 @@ cudaError_t large_precoder(const SinrArgs& A, cudaStream_t s) {
 
 template <int MG, int LT>
 cudaError_t large_finalize(const SinrArgs& A, bool svd, cudaStream_t s) {
-  const size_t smem = ((size_t)A.m * (A.m + 1) + 2 * (size_t)A.m * A.L + LT * LT) * sizeof(float2) +
-                      2 * LT * sizeof(float) + 16;
+  const LargeFinPlan pl = large_fin_plan(A.m, A.L, LT);
+  const size_t smem = (size_t)pl.total * sizeof(float2);
   if (smem > kSmemBudget) return cudaErrorInvalidValue;
   auto kern = svd ? k_sinr_finalize_large<MG, LT, true> : k_sinr_finalize_large<MG, LT, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<dim3(A.K, A.J), kLargeThreads, smem, s>>>(A);
+  kern<<<dim3(A.K, A.J), kLargeThreads, smem, s>>>(A, pl);
   return cudaGetLastError();
 }
 
@@ -473,6 +576,17 @@ cudaError_t large_finalize(const SinrArgs& A, bool svd, cudaStream_t s) {
   cudaError_t run_finalize<MG, LT>(const SinrArgs& A, bool svd, cudaStream_t s) {          \
     return large_finalize<MG, LT>(A, svd, s);                                              \
   }
+
+}  // namespace detail
+
+cudaError_t launch_precoder_staged(const SinrArgs& a, cudaStream_t s) {
+  using namespace detail;
+  if (a.m > kMaxRankM || a.L > 8) return cudaErrorInvalidValue;
+  return a.L <= 2 ? large_precoder<16, 2>(a, s)
+                  : a.L <= 4 ? large_precoder<16, 4>(a, s) : large_precoder<16, 8>(a, s);
+}
+
+namespace detail {
 
 TS_LARGE_INSTANCES(32, 2)
 TS_LARGE_INSTANCES(32, 4)

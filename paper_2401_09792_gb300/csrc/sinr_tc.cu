@@ -1,36 +1,37 @@
 // Interfering-link pass of the SVD-precoded SINR with the core contraction
-// (eq. 15) on the tensor cores (tcgen05), in the reduced-precision modes:
-//   TF32:    H~ = w (x) G with w and G rounded to TF32, FP32 accumulation;
-//   BF16X2:  w = w_hi + w_lo, G = G_hi + G_lo in BF16 and
-//            H~ = w_hi G_hi + w_lo G_hi + w_hi G_lo, FP32 accumulation.
-// Everything else (projection w = c* C, effective channel E = H~ V~,
-// covariance rows E E*) stays FP32 on the FMA pipe.
+// of eq. (15) on the tensor cores (tcgen05, TMEM accumulators), in three
+// arithmetic modes:
+//   TF32:    w = c* C and G rounded to TF32, one product chain;
+//   TF32X3:  w = w_hi + w_lo and G = G_hi + G_lo in TF32 (11 + 11 significant
+//            bits), products w_hi G_hi + w_hi G_lo + w_lo G_hi, FP32
+//            accumulation in TMEM: close to FP32 accuracy;
+//   BF16X2:  the same three products with BF16 parts (8 + 8 bits).
+// The projection w = c* C and the effective channel E = H~ V~ (eq. 24) are
+// FP32 (FMA pipe); the finalisation forms the covariance from E.
 //
-// The complex contraction over the p core slabs is one real GEMM per tile:
-// rows = the T = 128 subcarriers of the tile (TMEM lanes), columns = (row a,
-// column c, re/im) of H~, reduction over K = [Re w | Im w] (x3 segments for
-// BF16X2) against the core rewritten once per call by k_core_prep as
-//   re column: [Re G ; -Im G],   im column: [Im G ; Re G]
-// (and [hi | hi | lo] segments for BF16X2).  Operands are K-major without
-// swizzle in shared memory: 8-row x 16-byte core matrices, K-adjacent ones
-// 128 bytes apart (LBO), row groups 128 * K_bytes / 16 bytes apart (SBO).
+// The complex contraction over the p core slabs is one real GEMM per
+// (subcarrier tile, interfering link): rows = the 128 subcarriers of the
+// tile (TMEM lanes), columns = (column c, row a, re/im) of H~, reduction
+// over k = [Re w | Im w] against the core rewritten once per call by
+// k_core_prep as  re column: [Re G ; -Im G],  im column: [Im G ; Re G].
+// Operands are K-major without swizzle in shared memory (8-row x 16-byte
+// core matrices; K-adjacent ones 128 bytes apart, row groups K_bytes * 8
+// apart), hi and lo parts as two K segments of each operand.
 //
-// Operands are prepared once per call: k_core_prep rewrites every link's
-// core, k_tc_proj computes the projections w = c* C (FP32) of every
-// interfering link and subcarrier tile and writes them rounded or split.
-// Per CTA (tile, UE i, interfering BS k): the projection operand arrives by
-// one bulk copy; the core is consumed in column blocks of CB columns of H~
-// (CB = 4 for m <= 4, else 2; N = 2 MG CB accumulator columns), each block's
-// operand fetched by one bulk copy (cp.async.bulk + mbarrier transaction
-// count) into a three-slot ring two blocks ahead, and multiplied by one
-// thread into one of two TMEM buffers one block ahead of the epilogue; the
-// precoder rows of the block are staged by cp.async two blocks ahead.  The
-// epilogue thread (row group g, subcarrier t) reads its RPT rows of the H~
-// block from TMEM (tcgen05.ld) and accumulates E rows; at the end the E rows
-// are exchanged through shared memory and the partial covariance rows
-// written as in the FP32 kernel.  Every wait is bounded; on a timeout the
-// tile's precoder flags get TS_FLAG_TIMEOUT and the kernel releases its TMEM
-// and returns.
+// k_sinr_link_tc: one CTA per (tile, UE i, interfering BS k), warp
+// specialised.  Warp 0, one thread: bulk copies (cp.async.bulk, mbarrier
+// transaction counts) of the projection operand and of the core operand in
+// blocks of CB columns of H~ (N = 64 accumulator columns) into a three-slot
+// ring, and the MMAs of each block into one of two TMEM buffers.  Warps
+// 1 .. 4 RG (RG row groups of RPT rows): thread (lane quadrant, group g)
+// owns subcarrier t of the tile and rows g RPT .. g RPT + RPT - 1; per block
+// it reads its H~ rows from TMEM (tcgen05.ld, one column at a time), frees
+// the buffer, and accumulates E += H~ V~ with the precoder rows of its
+// subcarrier, which it stages itself (cp.async) two blocks ahead.  No
+// CTA-wide barrier in the loop: the roles meet only at mbarriers.  Every
+// wait is bounded; on a timeout the tile's precoder flags get
+// TS_FLAG_TIMEOUT, outstanding copies and MMAs get another bounded wait,
+// and the TMEM is released.
 #include <cuda_bf16.h>
 
 #include "sinr_impl.cuh"
@@ -40,46 +41,50 @@ namespace detail {
 namespace {
 
 constexpr int kTile = 128;     // subcarriers per CTA = MMA M = TMEM lanes
-constexpr int kBStages = 3;    // core-operand ring (loads run two blocks ahead)
+constexpr int kNtile = 64;     // accumulator columns per block (MMA N)
+constexpr int kBStages = 3;    // core-operand ring
 constexpr long kSpinLimit = 1L << 24;
+
+__host__ __device__ constexpr int tc_rpt(int MG) { return MG < 8 ? MG : 8; }
+__host__ __device__ constexpr int tc_rg(int MG) { return MG / tc_rpt(MG); }
+// H~ columns per block: N = 2 MG CB = 64
+__host__ __device__ constexpr int tc_cb(int MG) { return kNtile / (2 * MG); }
+__host__ __device__ constexpr int tc_es(int prec) { return prec == TS_PREC_BF16X2 ? 2 : 4; }
+__host__ __device__ constexpr int tc_nseg(int prec) { return prec == TS_PREC_TF32 ? 1 : 2; }
 
 struct TcPlan {
   int ES;          // operand element bytes (4 TF32, 2 BF16)
-  int Kpad;        // reduction length in elements, padded to 32 bytes
-  int Ntile;       // accumulator columns per block = 2 MG CB
+  int nseg;        // K segments per operand (hi; hi, lo)
+  int kseg;        // elements per K segment: 2p padded to 32 bytes
+  int kbytes;      // bytes per operand row
   int nblk;        // column blocks = ceil(n / CB)
-  int SV;          // precoder stage row stride (float2), per subcarrier
+  int VS;          // precoder staging per thread and slot (float2): CB LT
+  int nthreads;    // 32 (1 + 4 RG)
   int off_A, off_B, off_V, off_bar, smem;   // byte offsets
   size_t prep_bytes_per_link;               // k_core_prep output per link
   size_t a_bytes_per_tile;                  // k_tc_proj output per (link, tile)
 };
 
-__host__ __device__ constexpr int tc_rpt(int MG) { return MG < 4 ? MG : 4; }
-// H~ columns per accumulator block (N = 2 MG CB accumulator columns)
-__host__ __device__ constexpr int tc_cb(int MG) { return MG >= 8 ? 2 : 4; }
-
 inline TcPlan tc_plan(int MG, int LT, int n, int p, int prec) {
   TcPlan t;
-  t.ES = prec == TS_PREC_TF32 ? 4 : 2;
-  const int kused = prec == TS_PREC_TF32 ? 2 * p : 6 * p;
+  t.ES = tc_es(prec);
+  t.nseg = tc_nseg(prec);
   const int kq = 32 / t.ES;                      // elements per 32 bytes
-  t.Kpad = (kused + kq - 1) / kq * kq;
+  t.kseg = (2 * p + kq - 1) / kq * kq;
+  t.kbytes = t.nseg * t.kseg * t.ES;
   const int CB = tc_cb(MG);
-  t.Ntile = 2 * MG * CB;
   t.nblk = (n + CB - 1) / CB;
-  t.SV = CB * LT + 2;
+  t.VS = CB * LT;
+  t.nthreads = 32 * (1 + 4 * tc_rg(MG));
   int o = 0;
-  t.off_A = o; o += kTile * t.Kpad * t.ES;
-  t.off_B = o; o += kBStages * t.Ntile * t.Kpad * t.ES;
-  t.off_V = o; o += 2 * kTile * t.SV * 8;
-  // E exchange at the end reuses the front of the buffer
-  const int ex = kTile * MG * (LT * 8) + kTile * 16;
-  if (ex > o) o = ex;
+  t.off_A = o; o += kTile * t.kbytes;
+  t.off_B = o; o += kBStages * kNtile * t.kbytes;
+  t.off_V = o; o += (t.nthreads - 32) * 2 * t.VS * 8;
   o = (o + 15) & ~15;
-  t.off_bar = o; o += 64;
+  t.off_bar = o; o += 16 * 8;
   t.smem = o;
-  t.prep_bytes_per_link = (size_t)t.nblk * t.Ntile * t.Kpad * t.ES;
-  t.a_bytes_per_tile = (size_t)kTile * t.Kpad * t.ES;
+  t.prep_bytes_per_link = (size_t)t.nblk * kNtile * t.kbytes;
+  t.a_bytes_per_tile = (size_t)kTile * t.kbytes;
   return t;
 }
 
@@ -141,55 +146,56 @@ __global__ void k_wait_selftest(long limit, int arrive, int* out) {
 
 // ------------------------------------------------------------ core operand
 // B operand of link ch, column block b, in the canonical layout: row
-// j = ((g CB + c) RPT + a_in) 2 + ri of the block (row a = g RPT + a_in,
-// column c0 + c of H~), k over [Re w | Im w] (x3 segments for BF16X2):
+// j = ((cl RG + g) RPT + a_in) 2 + ri of the block (column c0 + cl and row
+// a = g RPT + a_in of H~, re/im), k over [Re w | Im w] per K segment:
 //   re row: [Re G ; -Im G],   im row: [Im G ; Re G]
-// (BF16X2: segments [hi | hi | lo]).  One thread writes one 16-byte chunk;
-// eight consecutive threads fill one 128-byte core matrix; padding is zero.
+// segment 0 the rounded value (hi), segment 1 the rounded remainder (lo).
+// One thread writes one 16-byte chunk; padding is zero.
 template <int PREC>
 __global__ void __launch_bounds__(256) k_core_prep(const float2* __restrict__ G, int m, int n, int p,
-                                                   int MG, int Ntile, int Kpad, int nblk, int nblocks,
+                                                   int MG, int kseg, int kbytes, int nblk, int nblocks,
                                                    unsigned char* __restrict__ out) {
-  // y = ch * nblk + b: one operand block; threads over its chunks
-  constexpr int ES = PREC == TS_PREC_TF32 ? 4 : 2;
-  constexpr int EPC = 16 / ES;
-  const int kbytes = Kpad * ES, nkc = kbytes / 16;
-  const int RPT = tc_rpt(MG), CB = tc_cb(MG);
-  const int p2 = 2 * p, kused = PREC == TS_PREC_TF32 ? p2 : 3 * p2;
-  const int nchunk = Ntile * nkc;
+  constexpr int ES = tc_es(PREC);
+  constexpr int EPC = 16 / ES;                    // elements per 16-byte chunk
+  const int nkc = kbytes / 16;
+  const int RPT = tc_rpt(MG), RG = tc_rg(MG), CB = tc_cb(MG);
+  const int nchunk = kNtile * nkc;
   for (int y = blockIdx.y; y < nblocks; y += gridDim.y)
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nchunk; idx += gridDim.x * blockDim.x) {
     const int ch = y / nblk, b = y - ch * nblk;
-    unsigned char* blk = out + (size_t)y * Ntile * kbytes;
+    unsigned char* blk = out + (size_t)y * kNtile * kbytes;
     const int r = idx & 7, rest = idx >> 3;
     const int rg = rest / nkc, kc = rest - rg * nkc;
     const int j = rg * 8 + r;
     const int ri = j & 1, a_in = (j >> 1) % RPT, cg = (j >> 1) / RPT;
-    const int c = b * CB + cg % CB, a = (cg / CB) * RPT + a_in;
+    const int c = b * CB + cg / RG, a = (cg % RG) * RPT + a_in;
     const bool live = a < m && c < n;
     const float2* gcol = G + ((size_t)ch * p * m + a) * n + c;     // + q m n
-    float2 gv[EPC];
-#pragma unroll
-    for (int e = 0; e < EPC; ++e) {
-      int kk = kc * EPC + e;
-      kk = kk >= 2 * p2 ? kk - 2 * p2 : kk >= p2 ? kk - p2 : kk;
-      const int q = kk < p ? kk : kk - p;
-      gv[e] = live && kc * EPC + e < kused ? __ldg(gcol + (size_t)q * m * n) : cz();
-    }
     float x[EPC];
 #pragma unroll
     for (int e = 0; e < EPC; ++e) {
-      const int k = kc * EPC + e;
-      const int kk = k >= 2 * p2 ? k - 2 * p2 : k >= p2 ? k - p2 : k;
-      // re row: [Re G ; -Im G], im row: [Im G ; Re G]
-      float v = ri == 0 ? (kk < p ? gv[e].x : -gv[e].y) : (kk < p ? gv[e].y : gv[e].x);
-      if (PREC == TS_PREC_BF16X2 && k >= 2 * p2) v -= __bfloat162float(__float2bfloat16_rn(v));
+      const int k = kc * EPC + e;                  // element within the row
+      const int seg = k / kseg, kk = k - seg * kseg;
+      float v = 0.f;
+      if (live && kk < 2 * p) {
+        const int q = kk < p ? kk : kk - p;
+        const float2 gv = __ldg(gcol + (size_t)q * m * n);
+        // re row: [Re G ; -Im G], im row: [Im G ; Re G]
+        v = ri == 0 ? (kk < p ? gv.x : -gv.y) : (kk < p ? gv.y : gv.x);
+        if (PREC == TS_PREC_BF16X2) {
+          const float hi = __bfloat162float(__float2bfloat16_rn(v));
+          v = seg == 0 ? hi : v - hi;
+        } else {
+          const float hi = to_tf32(v);
+          v = seg == 0 ? hi : to_tf32(v - hi);
+        }
+      }
       x[e] = v;
     }
     uint32_t words[4];
-    if (PREC == TS_PREC_TF32) {
+    if (ES == 4) {
 #pragma unroll
-      for (int e = 0; e < 4; ++e) words[e] = __float_as_uint(to_tf32(x[e % EPC]));
+      for (int e = 0; e < 4; ++e) words[e] = __float_as_uint(x[e % EPC]);
     } else {
 #pragma unroll
       for (int w = 0; w < 4; ++w)
@@ -204,20 +210,19 @@ __global__ void __launch_bounds__(256) k_core_prep(const float2* __restrict__ G,
 // ------------------------------------------------------ projection operand
 // A operand of (interfering link (i, k), subcarrier tile): row t =
 // subcarrier kap0 + t, k over [Re w | Im w] with w = C_ik^T conj(c_ik(kappa))
-// (eq. 15) in FP32, then rounded to TF32 or split [hi | lo | hi] in BF16, in
-// the canonical K-major layout.  The coefficients of a chunk of 32 paths are
-// evaluated once per (subcarrier, path) into shared memory; thread (t, h)
-// accumulates w_q for q in [8 h, 8 h + 8).  The rows are then written as
-// 16-byte chunks (eight consecutive threads fill one 128-byte core matrix);
-// rows beyond K are zero.
+// (eq. 15) in FP32, then per K segment rounded (hi) or the rounded
+// remainder (lo), in the canonical K-major layout.  The coefficients of a
+// chunk of 32 paths are evaluated once per (subcarrier, path) into shared
+// memory; thread (t, h) accumulates w_q for q in [8 h, 8 h + 8).  The rows
+// are then written as 16-byte chunks; rows beyond K are zero.
 constexpr int kProjPC = 32;
-
 constexpr int kProjQ = 8;      // projections w_q per thread
 
 template <int PREC>
-__global__ void __launch_bounds__(4 * kTile) k_tc_proj(const SinrArgs A, int Kpad, unsigned char* __restrict__ out) {
-  constexpr int ES = PREC == TS_PREC_TF32 ? 4 : 2;
-  constexpr int EPC = 16 / ES;                  // elements per 16-byte chunk
+__global__ void __launch_bounds__(4 * kTile) k_tc_proj(const SinrArgs A, int kseg, int kbytes,
+                                                       unsigned char* __restrict__ out) {
+  constexpr int ES = tc_es(PREC);
+  constexpr int EPC = 16 / ES;
   extern __shared__ __align__(16) unsigned char smp[];
   const int tid = threadIdx.x, nth = blockDim.x;
   const int t = tid % kTile, h = tid / kTile;
@@ -226,7 +231,7 @@ __global__ void __launch_bounds__(4 * kTile) k_tc_proj(const SinrArgs A, int Kpa
   const int J = A.J, p = A.p, P = A.P, K = A.K;
   const int k = z < i ? z : z + 1;
   const int ch = i * J + k;
-  const int kbytes = Kpad * ES, nkc = kbytes / 16;
+  const int nkc = kbytes / 16;
   const int WS = 2 * p + 1;
   float* wrow = reinterpret_cast<float*>(smp);                        // [kTile][2p + 1]
   float2* cs = reinterpret_cast<float2*>(smp + ((kTile * WS * 4 + 15) & ~15));   // [kTile][PC + 1]
@@ -268,38 +273,39 @@ __global__ void __launch_bounds__(4 * kTile) k_tc_proj(const SinrArgs A, int Kpa
     }
   }
   __syncthreads();
-  const int kused = PREC == TS_PREC_TF32 ? 2 * p : 6 * p;
   unsigned char* dst = out + (((size_t)i * (J - 1) + z) * gridDim.x + blockIdx.x) * (size_t)kTile * kbytes;
-  const int p2 = 2 * p;
   for (int idx = tid; idx < kTile * nkc; idx += nth) {
     const int r = idx & 7, rest = idx >> 3;
     const int rg = rest / nkc, kc = rest - rg * nkc;
     const int row = rg * 8 + r;
     const float* src = wrow + row * WS;
-    uint32_t words[4];
-    if (PREC == TS_PREC_TF32) {
+    float x[EPC];
 #pragma unroll
-      for (int e = 0; e < EPC; ++e) {
-        const int kk = kc * EPC + e;
-        words[e] = __float_as_uint(kk < kused ? to_tf32(src[kk]) : 0.f);
-      }
-    } else {
-      __nv_bfloat16 hv[8];
-#pragma unroll
-      for (int e = 0; e < EPC; ++e) {
-        const int kk = kc * EPC + e;
-        __nv_bfloat16 v = __float2bfloat16_rn(0.f);
-        if (kk < kused) {
-          const int seg = kk >= 2 * p2 ? 2 : kk >= p2 ? 1 : 0;
-          const float x = src[kk - seg * p2];
-          const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-          v = seg == 1 ? __float2bfloat16_rn(x - __bfloat162float(hi)) : hi;
+    for (int e = 0; e < EPC; ++e) {
+      const int kel = kc * EPC + e;
+      const int seg = kel / kseg, kk = kel - seg * kseg;
+      float v = 0.f;
+      if (kk < 2 * p) {
+        const float w = src[kk];
+        if (PREC == TS_PREC_BF16X2) {
+          const float hi = __bfloat162float(__float2bfloat16_rn(w));
+          v = seg == 0 ? hi : w - hi;
+        } else {
+          const float hi = to_tf32(w);
+          v = seg == 0 ? hi : to_tf32(w - hi);
         }
-        hv[e] = v;
       }
+      x[e] = v;
+    }
+    uint32_t words[4];
+    if (ES == 4) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) words[e] = __float_as_uint(x[e % EPC]);
+    } else {
 #pragma unroll
       for (int w = 0; w < 4; ++w)
-        words[w] = (uint32_t)__bfloat16_as_ushort(hv[2 * w]) | ((uint32_t)__bfloat16_as_ushort(hv[2 * w + 1]) << 16);
+        words[w] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[(2 * w) % EPC])) |
+                   ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[(2 * w + 1) % EPC])) << 16);
     }
     *reinterpret_cast<uint4*>(dst + kmajor_off(row, kc * 16, kbytes)) =
         make_uint4(words[0], words[1], words[2], words[3]);
@@ -307,268 +313,238 @@ __global__ void __launch_bounds__(4 * kTile) k_tc_proj(const SinrArgs A, int Kpa
 }
 
 // ----------------------------------------------------------- link kernel
+constexpr int kBars = 12;      // mbarriers of the link kernel (see below)
+
 template <int MG, int LT, int PREC>
-__global__ void __launch_bounds__(128 * (MG / tc_rpt(MG)))
+__global__ void __launch_bounds__(32 * (1 + 4 * tc_rg(MG)), 1)
     k_sinr_link_tc(const SinrArgs A, const unsigned char* __restrict__ prep,
                    const unsigned char* __restrict__ aop, TcPlan tp) {
-  constexpr int RPT = tc_rpt(MG);
-  constexpr int RG = MG / RPT;
-  constexpr int NT = 128 * RG;
-  constexpr int ES = PREC == TS_PREC_TF32 ? 4 : 2;
+  constexpr int RPT = tc_rpt(MG), RG = tc_rg(MG), CB = tc_cb(MG);
+  constexpr int ES = tc_es(PREC);
   constexpr int KMMA = 32 / ES;                 // K elements per MMA instruction
-  constexpr int kCB = tc_cb(MG);
+  constexpr int NEPI = 4 * RG;                  // epilogue warps
+  constexpr int NCHAIN = PREC == TS_PREC_TF32 ? 1 : 3;
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
-  const int g = warp / 4, t = (warp % 4) * 32 + lane;    // row group, subcarrier of the tile
   const int i = blockIdx.y, z = blockIdx.z;
   const int kap0 = blockIdx.x * kTile;
   const int J = A.J, m = A.m, n = A.n, L = A.L, K = A.K;
   const int k = z < i ? z : z + 1;
   const int ch = i * J + k;
-  const int kbytes = tp.Kpad * ES;
-  const int nblk = tp.nblk;
+  const int kbytes = tp.kbytes, nblk = tp.nblk;
   unsigned char* sA = smem + tp.off_A;
   unsigned char* sB = smem + tp.off_B;
   float2* sV = reinterpret_cast<float2*>(smem + tp.off_V);
-  // mbarriers: [0, kBStages) core-operand loads, two MMA completions, the
-  // projection operand
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + tp.off_bar);
-  const uint32_t bar_b0 = smem_u32(&bars[0]), bar_m0 = smem_u32(&bars[kBStages]);
-  const uint32_t bar_a = smem_u32(&bars[kBStages + 2]);
-  const size_t blk_bytes = (size_t)tp.Ntile * kbytes;
+  // mbarriers: 0..2 core block loaded, 3..5 its MMAs done (slot free),
+  // 6, 7 TMEM buffer written, 8, 9 TMEM buffer read (one arrival per
+  // epilogue warp), 10 projection operand loaded, 11 final drain
+  const uint32_t bar0 = smem_u32(smem + tp.off_bar);
+  const size_t blk_bytes = (size_t)kNtile * kbytes;
   const unsigned char* prep_ch = prep + (size_t)ch * nblk * blk_bytes;
-  const bool wideV = (L % 2 == 0) && ((reinterpret_cast<uintptr_t>(A.V) & 15u) == 0);
+  volatile int* abort_v = &abort_flag;
 
   if (tid == 0) {
     abort_flag = 0;
     // the refinement list of the finalize kernel that follows starts empty
     if (A.rcount != nullptr && blockIdx.x == 0 && i == 0 && z == 0) *A.rcount = 0;
-    for (int s = 0; s < kBStages + 3; ++s)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[s])));
+    for (int s = 0; s < kBars; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar0 + 8u * s),
+                   "r"((s == 8 || s == 9) ? (uint32_t)NEPI : 1u));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(&tmem_slot)),
-                 "r"(2 * tp.Ntile < 32 ? 32 : 2 * tp.Ntile));
+                     smem_u32(&tmem_slot)), "r"(2 * kNtile));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  __syncthreads();
-
-  // core operand of block b: one bulk copy (tid 0) into ring slot b % 3
-  auto issue_B = [&](int b) {
-    if (b >= nblk || tid != 0) return;
-    const int s = b % kBStages;
-    const uint32_t bar = bar_b0 + 8 * s;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                 "r"((uint32_t)blk_bytes) : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(sB + s * blk_bytes)),
-        "l"(prep_ch + (size_t)b * blk_bytes), "r"((uint32_t)blk_bytes), "r"(bar)
-        : "memory");
-  };
-  // precoder rows V~_k(kappa)[c0 .. c0+CB)[0 .. L) of the tile for block b
-  // (cp.async by every thread, stage b % 2), one commit group per call
-  auto issue_V = [&](int b) {
-    if (b < nblk) {
-      const int c0 = b * kCB;
-      float2* dst = sV + (b & 1) * kTile * tp.SV;
-      if (wideV) {
-        constexpr int U = kCB * LT / 2;            // 16-byte units per subcarrier
-        for (int idx = tid; idx < kTile * U; idx += NT) {
-          const int tt = idx / U, u = idx - tt * U;
-          const int cc = u / (LT / 2), l = 2 * (u % (LT / 2));
-          const bool ok = kap0 + tt < K && c0 + cc < n && l < L;
-          cp_async16(dst + tt * tp.SV + cc * LT + l,
-                     ok ? A.V + (((size_t)k * K + kap0 + tt) * n + c0 + cc) * L + l : A.V, ok);
-        }
-      } else {
-        for (int idx = tid; idx < kTile * kCB * LT; idx += NT) {
-          const int tt = idx / (kCB * LT), u = idx - tt * (kCB * LT);
-          const int cc = u / LT, l = u % LT;
-          const bool ok = kap0 + tt < K && c0 + cc < n && l < L;
-          cp_async8(dst + tt * tp.SV + cc * LT + l,
-                    ok ? A.V + (((size_t)k * K + kap0 + tt) * n + c0 + cc) * L + l : A.V, ok);
-        }
-      }
-    }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-  };
-  // projection operand of the tile (one bulk copy), core operand of blocks
-  // 0..2, precoder rows of blocks 0, 1
-  const uint32_t a_bytes = (uint32_t)(kTile * kbytes);
-  if (tid == 0) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_a), "r"(a_bytes)
-                 : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(sA)),
-        "l"(aop + (((size_t)i * (J - 1) + z) * gridDim.x + blockIdx.x) * (size_t)a_bytes), "r"(a_bytes),
-        "r"(bar_a)
-        : "memory");
-  }
-  issue_B(0);
-  issue_B(1);
-  issue_B(2);
-  issue_V(0);
-  issue_V(1);
-
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
 
-  const uint32_t idesc = (1u << 4) | ((PREC == TS_PREC_TF32 ? 2u : 1u) << 7) |
-                         ((PREC == TS_PREC_TF32 ? 2u : 1u) << 10) | ((uint32_t)(tp.Ntile >> 3) << 17) |
-                         ((uint32_t)(kTile >> 4) << 24);
-  const uint32_t sbo = 128u * (uint32_t)(kbytes >> 4);
-  auto issue_mma = [&](int b) -> bool {
-    // tid 0 only: wait for the block's operand, then K/KMMA instructions
-    const int s = b & 1, sb = b % kBStages;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (b == 0 && !mbar_wait(bar_a, 0)) return false;
-    if (!mbar_wait(bar_b0 + 8 * sb, (uint32_t)((b / kBStages) & 1))) return false;
-    const uint32_t d = tmem + (uint32_t)(s * tp.Ntile);
-    const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB + sb * blk_bytes);
-    for (int ks = 0; ks < tp.Kpad / KMMA; ++ks) {
-      const uint64_t ad = smem_desc(a0 + ks * 256, sbo);
-      const uint64_t bd = smem_desc(b0 + ks * 256, sbo);
-      const uint32_t accum = ks > 0;
-      if (PREC == TS_PREC_TF32)
-        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-                     "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
-      else
-        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-                     "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
-    }
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                     bar_m0 + 8 * s)
-                 : "memory");
-    return true;
-  };
-  if (tid == 0 && !issue_mma(0)) abort_flag = 1;
-
-  float2 E[RPT][LT];
-#pragma unroll
-  for (int r = 0; r < RPT; ++r)
-#pragma unroll
-    for (int l = 0; l < LT; ++l) E[r][l] = cz();
-
-  bool aborted = false;
-  for (int b = 0; b < nblk; ++b) {
-    const int s = b & 1;
-    // MMA(b + 1) into the other TMEM buffer, whose last reader (block b - 1)
-    // finished before the barrier that ended the previous iteration
-    if (tid == 0 && b + 1 < nblk && !abort_flag && !issue_mma(b + 1)) abort_flag = 1;
-    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-    __syncthreads();                                                // rows of block b staged
-    if (abort_flag) { aborted = true; break; }
-    if (!mbar_wait(bar_m0 + 8 * s, (uint32_t)((b >> 1) & 1))) abort_flag = 1;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // this thread's H~ block: RPT rows x CB columns, re/im pairs
-    constexpr int NCOL = 2 * RPT * kCB;
-    uint32_t h[NCOL];
-    const uint32_t taddr = tmem + ((uint32_t)((warp % 4) * 32) << 16) +
-                           (uint32_t)(s * tp.Ntile + g * NCOL);
-    if constexpr (NCOL == 32) {
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- loads and MMAs (one thread)
+      int loaded[kBStages] = {0, 0, 0}, consumed[kBStages] = {0, 0, 0};
+      auto issue_B = [&](int b) {
+        const int s = b % kBStages;
+        const uint32_t bar = bar0 + 8u * s;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                     "r"((uint32_t)blk_bytes) : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_u32(sB + s * blk_bytes)),
+            "l"(prep_ch + (size_t)b * blk_bytes), "r"((uint32_t)blk_bytes), "r"(bar)
+            : "memory");
+        ++loaded[s];
+      };
+      const uint32_t a_bytes = (uint32_t)(kTile * kbytes);
+      const uint32_t afull = bar0 + 8u * 10;
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(afull), "r"(a_bytes)
+                   : "memory");
       asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-          : "=r"(h[0]), "=r"(h[1]), "=r"(h[2]), "=r"(h[3]), "=r"(h[4]), "=r"(h[5]), "=r"(h[6]),
-            "=r"(h[7]), "=r"(h[8]), "=r"(h[9]), "=r"(h[10]), "=r"(h[11]), "=r"(h[12]), "=r"(h[13]),
-            "=r"(h[14]), "=r"(h[15]), "=r"(h[16]), "=r"(h[17]), "=r"(h[18]), "=r"(h[19]), "=r"(h[20]),
-            "=r"(h[21]), "=r"(h[22]), "=r"(h[23]), "=r"(h[24]), "=r"(h[25]), "=r"(h[26]), "=r"(h[27]),
-            "=r"(h[28]), "=r"(h[29]), "=r"(h[30]), "=r"(h[31])
-          : "r"(taddr));
-    } else if constexpr (NCOL == 16) {
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(h[0]), "=r"(h[1]), "=r"(h[2]), "=r"(h[3]), "=r"(h[4]), "=r"(h[5]), "=r"(h[6]),
-            "=r"(h[7]), "=r"(h[8]), "=r"(h[9]), "=r"(h[10]), "=r"(h[11]), "=r"(h[12]), "=r"(h[13]),
-            "=r"(h[14]), "=r"(h[15])
-          : "r"(taddr));
-    } else {
-      static_assert(NCOL == 8, "tcgen05.ld shape");
-      asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                   : "=r"(h[0]), "=r"(h[1]), "=r"(h[2]), "=r"(h[3]), "=r"(h[4]), "=r"(h[5]), "=r"(h[6]),
-                     "=r"(h[7])
-                   : "r"(taddr));
-    }
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    const float2* vrow = sV + s * kTile * tp.SV + t * tp.SV;
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+              smem_u32(sA)),
+          "l"(aop + (((size_t)i * (J - 1) + z) * gridDim.x + blockIdx.x) * (size_t)a_bytes), "r"(a_bytes),
+          "r"(afull)
+          : "memory");
+      for (int b = 0; b < kBStages && b < nblk; ++b) issue_B(b);
+      const uint32_t idesc = (1u << 4) | ((PREC == TS_PREC_BF16X2 ? 1u : 2u) << 7) |
+                             ((PREC == TS_PREC_BF16X2 ? 1u : 2u) << 10) | ((uint32_t)(kNtile >> 3) << 17) |
+                             ((uint32_t)(kTile >> 4) << 24);
+      const uint32_t sbo = 128u * (uint32_t)(kbytes >> 4);
+      const uint32_t segoff = (uint32_t)(tp.kseg * ES * 8);      // K segment start, bytes
+      const int nk = tp.kseg / KMMA;                              // MMAs per chain
+      bool ok = mbar_wait(afull, 0);
+      for (int b = 0; ok && b < nblk; ++b) {
+        const int s = b % kBStages, t = b & 1;
+        if (!mbar_wait(bar0 + 8u * s, (uint32_t)((b / kBStages) & 1))) { ok = false; break; }
+        ++consumed[s];
+        if (b >= 2 && !mbar_wait(bar0 + 8u * (8 + t), (uint32_t)(((b - 2) >> 1) & 1))) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d = tmem + (uint32_t)(t * kNtile);
+        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB + s * blk_bytes);
 #pragma unroll
-    for (int cc = 0; cc < kCB; ++cc) {
-#pragma unroll
-      for (int l2 = 0; l2 < LT / 2; ++l2) {
-        const float4 v = reinterpret_cast<const float4*>(vrow + cc * LT)[l2];
-        const float2 v0 = make_float2(v.x, v.y), v1 = make_float2(v.z, v.w);
-#pragma unroll
-        for (int r = 0; r < RPT; ++r) {
-          const float2 hv = make_float2(__uint_as_float(h[(cc * RPT + r) * 2]),
-                                        __uint_as_float(h[(cc * RPT + r) * 2 + 1]));
-          cmac(E[r][2 * l2], hv, v0);
-          cmac(E[r][2 * l2 + 1], hv, v1);
+        for (int c = 0; c < NCHAIN; ++c) {
+          // chains (hi, hi), (hi, lo), (lo, hi) of (A segment, B segment)
+          const uint32_t ao = a0 + (c == 2 ? segoff : 0u), bo = b0 + (c == 1 ? segoff : 0u);
+          for (int ks = 0; ks < nk; ++ks) {
+            const uint64_t ad = smem_desc(ao + ks * 256, sbo);
+            const uint64_t bd = smem_desc(bo + ks * 256, sbo);
+            const uint32_t accum = (c > 0 || ks > 0) ? 1u : 0u;
+            if (PREC == TS_PREC_BF16X2)
+              asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                           "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                           "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+            else
+              asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                           "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                           "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+          }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         bar0 + 8u * (6 + t)) : "memory");
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         bar0 + 8u * (3 + s)) : "memory");
+        // refill the slot of block b - 1 once its MMAs are done
+        if (b >= 1 && b - 1 + kBStages < nblk) {
+          const int s1 = (b - 1) % kBStages;
+          if (!mbar_wait(bar0 + 8u * (3 + s1), (uint32_t)(((b - 1) / kBStages) & 1))) { ok = false; break; }
+          issue_B(b - 1 + kBStages);
         }
       }
+      if (!ok) *abort_v = 1;
+      // drain: every MMA issued so far has completed, every copy has landed
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       bar0 + 8u * 11) : "memory");
+      if (!mbar_wait(bar0 + 8u * 11, 0)) *abort_v = 1;
+      for (int s = 0; s < kBStages; ++s)
+        for (int u = consumed[s]; u < loaded[s]; ++u) mbar_wait(bar0 + 8u * s, (uint32_t)(u & 1));
+      if (!ok) mbar_wait(afull, 0);
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    issue_B(b + 3);     // slot of block b: MMA(b) has completed
-    issue_V(b + 2);     // stage of block b: its epilogue is done
-  }
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  if (abort_flag) aborted = true;
-
-  if (!aborted) {
-    // partial covariance rows (E E*)[a][b], b < m (eq. 25), through an
-    // exchange of the E rows of the tile in shared memory
-    float2* X = reinterpret_cast<float2*>(smem);
-    const int XS = MG * LT + 2;
+  } else {
+    // ---------------- epilogue: E += H~ V~ for (subcarrier t_in, rows of group g)
+    const int ew = warp - 1, quad = warp & 3, g = ew >> 2;
+    const int t_in = quad * 32 + lane;           // TMEM lane = subcarrier of the tile
+    const int kap = kap0 + t_in;
+    float2* vslot = sV + (size_t)(ew * 32 + lane) * 2 * tp.VS;
+    auto issue_V = [&](int b) {
+      if (b < nblk) {
+        const int c0 = b * CB;
+        float2* dst = vslot + (b & 1) * tp.VS;
+#pragma unroll
+        for (int u = 0; u < CB * LT; ++u) {
+          const int cc = u / LT, l = u % LT;
+          const bool ok = kap < K && c0 + cc < n && l < L;
+          cp_async8(dst + u, ok ? A.V + (((size_t)k * K + kap) * n + c0 + cc) * L + l : A.V, ok);
+        }
+      }
+      cp_async_commit();
+    };
+    issue_V(0);
+    issue_V(1);
+    float2 E[RPT][LT];
 #pragma unroll
     for (int r = 0; r < RPT; ++r)
 #pragma unroll
-      for (int l = 0; l < LT; ++l) X[t * XS + (g * RPT + r) * LT + l] = E[r][l];
-    __syncthreads();
-    const int kap = kap0 + t;
-    if (kap < K) {
+      for (int l = 0; l < LT; ++l) E[r][l] = cz();
+    bool good = true;
+    for (int b = 0; b < nblk; ++b) {
+      const int t = b & 1;
+      cp_async_wait<1>();                        // this thread's precoder rows of block b
+      if (!mbar_wait(bar0 + 8u * (6 + t), (uint32_t)((b >> 1) & 1))) { good = false; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const float2* vb = vslot + (b & 1) * tp.VS;
+#pragma unroll
+      for (int cc = 0; cc < CB; ++cc) {
+        uint32_t h[2 * RPT];
+        const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) +
+                               (uint32_t)(t * kNtile + (cc * RG + g) * 2 * RPT);
+        if constexpr (RPT == 8) {
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+              : "=r"(h[0]), "=r"(h[1]), "=r"(h[2]), "=r"(h[3]), "=r"(h[4]), "=r"(h[5]), "=r"(h[6]),
+                "=r"(h[7]), "=r"(h[8]), "=r"(h[9]), "=r"(h[10]), "=r"(h[11]), "=r"(h[12]), "=r"(h[13]),
+                "=r"(h[14]), "=r"(h[15])
+              : "r"(taddr));
+        } else if constexpr (RPT == 4) {
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                       : "=r"(h[0]), "=r"(h[1]), "=r"(h[2]), "=r"(h[3]), "=r"(h[4]), "=r"(h[5]),
+                         "=r"(h[6]), "=r"(h[7])
+                       : "r"(taddr));
+        } else {
+          static_assert(RPT == 2, "tcgen05.ld shape");
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                       : "=r"(h[0]), "=r"(h[1]), "=r"(h[2]), "=r"(h[3])
+                       : "r"(taddr));
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int l2 = 0; l2 < LT / 2; ++l2) {
+          const float4 v = reinterpret_cast<const float4*>(vb + cc * LT)[l2];
+          const float2 v0 = make_float2(v.x, v.y), v1 = make_float2(v.z, v.w);
+#pragma unroll
+          for (int r = 0; r < RPT; ++r) {
+            const float2 hv = make_float2(__uint_as_float(h[2 * r]), __uint_as_float(h[2 * r + 1]));
+            cmac(E[r][2 * l2], hv, v0);
+            cmac(E[r][2 * l2 + 1], hv, v1);
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar0 + 8u * (8 + t)) : "memory");
+      issue_V(b + 2);
+    }
+    cp_async_wait<0>();
+    if (!good) *abort_v = 1;
+    // rows of the interfering effective channel E_ik (eq. 24); the
+    // finalisation forms the covariance of eq. (25)
+    if (good && kap < K) {
 #pragma unroll
       for (int r = 0; r < RPT; ++r) {
         const int a = g * RPT + r;
         if (a >= m) continue;
-        float2* Rout = A.Rpart + ((((size_t)i * (J - 1) + z) * K + kap) * m + a) * m;
-        for (int bb = 0; bb < m; ++bb) {
-          float2 acc = cz();
-          const float2* eb = X + t * XS + bb * LT;
+        float2* Eout = A.Eint + ((((size_t)i * (J - 1) + z) * K + kap) * m + a) * L;
 #pragma unroll
-          for (int l = 0; l < LT; ++l) cmacc(acc, E[r][l], eb[l]);
-          Rout[bb] = acc;
-        }
+        for (int l = 0; l < LT; ++l)
+          if (l < L) Eout[l] = E[r][l];
       }
     }
-  } else {
-    // an operand or an MMA never arrived: flag the tile's units and stop;
-    // pending bulk copies and MMAs get another bounded wait before the
-    // accumulator memory is released
-    if (tid == 0) {
-      for (int s = 0; s < kBStages; ++s) mbar_wait(bar_b0 + 8 * s, 0);
-      for (int s = 0; s < 2; ++s) mbar_wait(bar_m0 + 8 * s, 0);
-      mbar_wait(bar_a, 0);
-    }
-    if (g == 0 && kap0 + t < K) A.pflag[(size_t)i * K + kap0 + t] |= TS_FLAG_TIMEOUT;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  if (*abort_v) {
+    // an operand or an MMA never arrived: the tile's units are flagged (and
+    // get NaN from the finalisation)
+    for (int t = tid; t < kTile; t += blockDim.x)
+      if (kap0 + t < K) A.pflag[(size_t)i * K + kap0 + t] |= TS_FLAG_TIMEOUT;
+  }
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(2 * tp.Ntile < 32 ? 32 : 2 * tp.Ntile));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kNtile));
 }
 
 // both operands: the core of every link and the projections of the
@@ -577,10 +553,10 @@ template <int PREC>
 cudaError_t launch_prep(const SinrArgs& A, int MG, int LT, unsigned char* prep, cudaStream_t s) {
   const TcPlan tp = tc_plan(MG, LT, A.n, A.p, PREC);
   const size_t bbytes = tp.prep_bytes_per_link * (size_t)A.J * A.J;
-  const int nchunk = tp.Ntile * (tp.Kpad * tp.ES / 16);
+  const int nchunk = kNtile * (tp.kbytes / 16);
   const int nblocks = A.J * A.J * tp.nblk;
   dim3 pgrid((nchunk + 255) / 256, nblocks < 65535 ? nblocks : 65535);
-  k_core_prep<PREC><<<pgrid, 256, 0, s>>>(A.G, A.m, A.n, A.p, MG, tp.Ntile, tp.Kpad, tp.nblk, nblocks,
+  k_core_prep<PREC><<<pgrid, 256, 0, s>>>(A.G, A.m, A.n, A.p, MG, tp.kseg, tp.kbytes, tp.nblk, nblocks,
                                           prep);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || A.J < 2) return e;
@@ -589,7 +565,8 @@ cudaError_t launch_prep(const SinrArgs& A, int MG, int LT, unsigned char* prep, 
   e = cudaFuncSetAttribute(k_tc_proj<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   dim3 grid((A.K + kTile - 1) / kTile, A.J, A.J - 1);
-  k_tc_proj<PREC><<<grid, kTile * ((A.p + kProjQ - 1) / kProjQ), smem, s>>>(A, tp.Kpad, prep + bbytes);
+  k_tc_proj<PREC><<<grid, kTile * ((A.p + kProjQ - 1) / kProjQ), smem, s>>>(A, tp.kseg, tp.kbytes,
+                                                                          prep + bbytes);
   return cudaGetLastError();
 }
 
@@ -602,14 +579,15 @@ cudaError_t launch_tc(const SinrArgs& A, const unsigned char* prep, cudaStream_t
   if (e != cudaSuccess) return e;
   dim3 grid((A.K + kTile - 1) / kTile, A.J, A.J - 1);
   const unsigned char* aop = prep + tp.prep_bytes_per_link * (size_t)A.J * A.J;
-  kern<<<grid, 128 * (MG / tc_rpt(MG)), tp.smem, s>>>(A, prep, aop, tp);
+  kern<<<grid, tp.nthreads, tp.smem, s>>>(A, prep, aop, tp);
   return cudaGetLastError();
 }
 
 template <int MG, int LT>
 cudaError_t launch_tc_prec(const SinrArgs& A, int prec, const unsigned char* prep, cudaStream_t s) {
-  return prec == TS_PREC_TF32 ? launch_tc<MG, LT, TS_PREC_TF32>(A, prep, s)
-                              : launch_tc<MG, LT, TS_PREC_BF16X2>(A, prep, s);
+  if (prec == TS_PREC_TF32) return launch_tc<MG, LT, TS_PREC_TF32>(A, prep, s);
+  if (prec == TS_PREC_TF32X3) return launch_tc<MG, LT, TS_PREC_TF32X3>(A, prep, s);
+  return launch_tc<MG, LT, TS_PREC_BF16X2>(A, prep, s);
 }
 
 inline int tc_mg(int m) { return m <= 2 ? 2 : m <= 4 ? 4 : m <= 8 ? 8 : 16; }
@@ -622,8 +600,8 @@ inline int tc_lt(int m, int L) { return L <= 2 && m <= 8 ? 2 : L <= 4 ? 4 : 8; }
 bool tc_supported(int m, int L, int p) {
   const int MG = detail::tc_mg(m), LT = detail::tc_lt(m, L);
   if (m > 16 || L > 8 || LT > MG || p > 32) return false;
-  const detail::TcPlan tp = detail::tc_plan(MG, LT, 512, p, TS_PREC_BF16X2);
-  return tp.smem <= 227 * 1024;
+  const detail::TcPlan tp = detail::tc_plan(MG, LT, 512, p, TS_PREC_TF32X3);
+  return tp.smem + 1024 <= 227 * 1024;   // + the static shared memory of the kernel
 }
 
 size_t tc_prep_bytes(int J, int m, int L, int n, int p, int K, int prec) {
@@ -635,8 +613,10 @@ size_t tc_prep_bytes(int J, int m, int L, int n, int p, int K, int prec) {
 cudaError_t launch_core_prep(const SinrArgs& a, int prec, void* prep, cudaStream_t s) {
   using namespace detail;
   unsigned char* pp = static_cast<unsigned char*>(prep);
-  return prec == TS_PREC_TF32 ? launch_prep<TS_PREC_TF32>(a, tc_mg(a.m), tc_lt(a.m, a.L), pp, s)
-                              : launch_prep<TS_PREC_BF16X2>(a, tc_mg(a.m), tc_lt(a.m, a.L), pp, s);
+  const int MG = tc_mg(a.m), LT = tc_lt(a.m, a.L);
+  if (prec == TS_PREC_TF32) return launch_prep<TS_PREC_TF32>(a, MG, LT, pp, s);
+  if (prec == TS_PREC_TF32X3) return launch_prep<TS_PREC_TF32X3>(a, MG, LT, pp, s);
+  return launch_prep<TS_PREC_BF16X2>(a, MG, LT, pp, s);
 }
 
 cudaError_t launch_sinr_links_tc(const SinrArgs& a, int prec, const void* prep, cudaStream_t s) {

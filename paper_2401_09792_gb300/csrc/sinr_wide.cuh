@@ -335,16 +335,8 @@ __global__ void __launch_bounds__(NT, NT > kThreads ? 2 : 0) k_sinr_link_wide(co
   }
   if (SERVE) return;
 
-  // partial covariance rows (E E*)[a][b], b < m (eq. 25), for both subcarriers
-  float2* Es = stage0 + gp * (X * MG * LT + 2);
-#pragma unroll
-  for (int x = 0; x < X; ++x)
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-#pragma unroll
-      for (int l = 0; l < LT; ++l) Es[(x * MG + j + r * GL) * LT + l] = E[x][r][l];
-  if constexpr (GL > 32) __syncthreads();   // a group spans two warps
-  else __syncwarp();
+  // rows of the interfering effective channel E_ik (eq. 24) of this lane's
+  // subcarriers; the finalisation forms the covariance of eq. (25)
 #pragma unroll
   for (int x = 0; x < X; ++x) {
     const int kap = kap0 + X * gp + x;
@@ -353,14 +345,10 @@ __global__ void __launch_bounds__(NT, NT > kThreads ? 2 : 0) k_sinr_link_wide(co
     for (int r = 0; r < R; ++r) {
       const int a = j + r * GL;
       if (a >= m) continue;
-      float2* Rout = A.Rpart + ((((size_t)i * (J - 1) + z) * K + kap) * m + a) * m;
-      for (int b = 0; b < m; ++b) {
-        float2 acc = cz();
-        const float2* eb = Es + (x * MG + b) * LT;
+      float2* Eout = A.Eint + ((((size_t)i * (J - 1) + z) * K + kap) * m + a) * L;
 #pragma unroll
-        for (int l = 0; l < LT; ++l) cmacc(acc, E[x][r][l], eb[l]);
-        Rout[b] = acc;
-      }
+      for (int l = 0; l < LT; ++l)
+        if (l < L) Eout[l] = E[x][r][l];
     }
   }
 }

@@ -22,11 +22,11 @@ TS_COEF_DENSE, TS_COEF_PATHS = 0, 1
 TS_OK, TS_ERR_DIMS, TS_ERR_NULL, TS_ERR_ALIGN, TS_ERR_WORKSPACE = 0, 1, 2, 3, 4
 TS_OP_SINR_SVD, TS_OP_SINR_MMSE, TS_OP_DENSE_SVD, TS_OP_DENSE_MMSE = 0, 1, 2, 3
 TS_OP_SINR_SVD_ADJOINT, TS_OP_SINR_MMSE_ADJOINT, TS_OP_TUCKER_FIT = 4, 5, 6
-TS_OP_SINR_SVD_TF32, TS_OP_SINR_SVD_BF16X2 = 7, 8
+TS_OP_SINR_SVD_TF32, TS_OP_SINR_SVD_BF16X2, TS_OP_SINR_SVD_TF32X3 = 7, 8, 14
 TS_OP_TUCKER_FIT_SHARED, TS_OP_TUCKER_FIT_INDIVIDUAL, TS_OP_RECONSTRUCT = 9, 10, 11
 TS_MODEL_GROUPWISE, TS_MODEL_SHARED, TS_MODEL_INDIVIDUAL = 0, 1, 2
 TS_OP_SINR_SVD_MULTIUSER, TS_OP_DENSE_SVD_MULTIUSER = 12, 13
-TS_PREC_FP32, TS_PREC_TF32, TS_PREC_BF16X2 = 0, 1, 2
+TS_PREC_FP32, TS_PREC_TF32, TS_PREC_BF16X2, TS_PREC_TF32X3 = 0, 1, 2, 3
 TS_FLAG_NOT_PD, TS_FLAG_NONFINITE, TS_FLAG_RANK_DEFICIENT, TS_FLAG_EIG_UNCONVERGED = 1, 2, 4, 8
 TS_FLAG_TIMEOUT = 16
 TS_FLAG_REFINED = 32
@@ -195,10 +195,11 @@ def ts_device_peaks(stream=None) -> dict:
     return {"fp32_fma": f32.value, "tf32_mma": t32.value, "fp64_fma": f64.value}
 
 
-def ts_set_refinement(cond_threshold: float):
-    """Condition number of R above which SINR units get FP64-residual
-    refinement on this thread (negative: off; default 1e3)."""
-    load().ts_set_refinement(float(cond_threshold))
+def ts_set_refinement(threshold: float):
+    """Sensitivity threshold above which a unit is re-evaluated from a
+    double-float R with FP64-residual refinement (default 8, this thread);
+    negative turns it off."""
+    load().ts_set_refinement(float(threshold))
 
 
 def ts_set_timing_events(start=None, stop=None):

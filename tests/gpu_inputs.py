@@ -11,6 +11,26 @@ from oracle import sinr as S
 from paper_2401_09792_gb300 import synth
 from paper_2401_09792_gb300 import tuckersinr as ts
 
+# Parity bound of the FP32 path: relative SINR error against the FP64 oracle,
+# per SINR, flat (the target precision of the method's FP32 evaluation).
+FP32_RTOL = 1e-5
+
+
+def assert_sinr_close(got: np.ndarray, ref: np.ndarray, rtol=FP32_RTOL, what: str = "") -> np.ndarray:
+    """Element-by-element relative error |got - ref| / |ref| within `rtol`
+    (a scalar or an array broadcast against the SINRs); returns the errors."""
+    assert got.shape == ref.shape, (got.shape, ref.shape)
+    assert np.all(np.isfinite(got)), f"{what}: non-finite SINR"
+    rel = np.abs(got - ref) / np.abs(ref)
+    tol = np.broadcast_to(rtol, rel.shape)
+    bad = rel > tol
+    if bad.any():
+        at = np.unravel_index(np.argmax(rel / tol), rel.shape)
+        raise AssertionError(f"{what}: {int(bad.sum())} of {rel.size} SINRs beyond the bound; "
+                             f"max rel {rel.max():.3e} (bound there {tol[at]:.3e}) at {at}; "
+                             f"p99 {np.quantile(rel, 0.99):.3e}")
+    return rel
+
 
 def workload(base: synth.Workload, **kw) -> synth.Workload:
     return dataclasses.replace(base, **kw)

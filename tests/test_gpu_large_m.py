@@ -13,9 +13,7 @@ pytestmark = pytest.mark.gpu
 
 from paper_2401_09792_gb300 import synth  # noqa: E402
 from paper_2401_09792_gb300 import tuckersinr as ts  # noqa: E402
-from tests.gpu_inputs import Case, interference_condition, svd_gap  # noqa: E402
-
-U32 = 2.0 ** -24
+from tests.gpu_inputs import Case, assert_sinr_close  # noqa: E402
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -30,12 +28,6 @@ def _wl(name, **kw):
                 sigma2=None, seed=21)
     base.update(kw)
     return dataclasses.replace(synth.MID, name=name, **base)
-
-
-def _tolerance(case, dense):
-    tol = 1e-5 + 4 * U32 * interference_condition(case, "svd", dense)
-    tol = tol + 8 * U32 / np.maximum(svd_gap(case, dense), 1e-30)[None, :]
-    return tol[:, :, None]
 
 
 CASES = {
@@ -58,9 +50,7 @@ def test_large_m_svd_sinr(name, mode):
     got, flags = case.gpu_sinr("svd", mode)
     assert np.all((flags & ts.TS_FLAG_ERRORS) == 0), np.unique(flags)
     ref = case.oracle_sinr("svd")
-    rel = np.abs(got - ref) / np.abs(ref)
-    tol = _tolerance(case, dense=False)
-    assert np.all(rel <= tol), f"max rel {rel.max():.3e} (max rel/tol {(rel / tol).max():.2f})"
+    assert_sinr_close(got, ref, what=f"{name} {mode}")
 
 
 @pytest.mark.parametrize("M", [24, 64])
@@ -70,8 +60,7 @@ def test_large_m_dense_comparator(M):
     got, flags = case.gpu_dense_sinr("svd", "paths")
     assert np.all((flags & ts.TS_FLAG_ERRORS) == 0)
     ref = case.oracle_dense_sinr("svd")
-    rel = np.abs(got - ref) / np.abs(ref)
-    assert np.all(rel <= _tolerance(case, dense=True)), f"max rel {rel.max():.3e}"
+    assert_sinr_close(got, ref, what=f"dense M{M}")
 
 
 def test_large_m_limits():

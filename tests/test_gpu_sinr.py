@@ -1,18 +1,11 @@
 """Parity of the CUDA SINR path (through the C ABI) with the FP64 oracle.
 
-Tolerances (FP32 arithmetic on the GPU, complex128 in the oracle), per SINR,
-relative, with u = 2^-24:
-    1e-5 + 4 u cond(R)          (+ 8 u / gap for SVD precoding)
-where cond(R) is the condition number of the UE's interference-plus-noise
-covariance R = sum_{k != i} E_ik E_ik* + sigma^2 I and gap is the smallest
-relative gap (to the largest) between the squared singular values that the
-serving links' precoders must separate.  Rounding the effective channels
-to FP32 moves the SINR by ~u cond(R), and the precoder columns by ~u / gap,
-whatever the algorithm; for well-conditioned results (cond(R) <= 10,
-gap >= 0.1) the bound is below 1.3e-5.
+Tolerance: every SINR within 1e-5 relative of the oracle (FP32 arithmetic on
+the GPU, complex128 in the oracle, the same complex64 inputs).  FP32
+rounding of the compressed channels alone moves the SINR by ~5e-7 at these
+sizes (the oracle's own channels rounded to complex64), so the bound leaves
+room for the eigensolve and the solves but not for an unconverged precoder.
 """
-import dataclasses
-
 import numpy as np
 import pytest
 
@@ -22,9 +15,7 @@ pytestmark = pytest.mark.gpu
 from oracle import sinr as S  # noqa: E402
 from paper_2401_09792_gb300 import synth  # noqa: E402
 from paper_2401_09792_gb300 import tuckersinr as ts  # noqa: E402
-from tests.gpu_inputs import Case, interference_condition, svd_gap, workload  # noqa: E402
-
-U32 = 2.0 ** -24
+from tests.gpu_inputs import Case, assert_sinr_close, workload  # noqa: E402
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -37,22 +28,8 @@ def _lib():
 def _check(case: Case, precoder: str, mode: str):
     got, flags = case.gpu_sinr(precoder, mode)
     ref = case.oracle_sinr(precoder)
-    assert np.all(np.isfinite(got)), "non-finite SINR"
     assert np.all((flags & ts.TS_FLAG_ERRORS) == 0), np.unique(flags)
-    rel = np.abs(got - ref) / np.abs(ref)
-    tol = _tolerance(case, precoder, rel.shape, dense=False)
-    bad = rel > tol
-    assert not bad.any(), (f"{bad.sum()} of {rel.size} SINRs out of tolerance; "
-                           f"max rel {rel.max():.3e}, at {np.unravel_index(np.argmax(rel / tol), rel.shape)}")
-    return rel
-
-
-def _tolerance(case, precoder, shape, dense):
-    cond = interference_condition(case, precoder, dense)              # (J, K)
-    tol = 1e-5 + 4 * U32 * cond
-    if precoder == "svd":
-        tol = tol + 8 * U32 / np.maximum(svd_gap(case, dense), 1e-30)[None, :]
-    return np.broadcast_to(tol[:, :, None], shape)
+    return assert_sinr_close(got, ref, what=f"{case.w.name} {precoder} {mode}")
 
 
 @pytest.mark.parametrize("precoder", ["svd", "mmse"])
@@ -119,11 +96,8 @@ def test_nonfinite_input_flags_and_nan():
 def _check_dense(case: Case, precoder: str):
     got, flags = case.gpu_dense_sinr(precoder, "paths")
     ref = case.oracle_dense_sinr(precoder)
-    assert np.all(np.isfinite(got)) and np.all((flags & ts.TS_FLAG_ERRORS) == 0)
-    rel = np.abs(got - ref) / np.abs(ref)
-    tol = _tolerance(case, precoder, rel.shape, dense=True)
-    bad = rel > tol
-    assert not bad.any(), f"{bad.sum()} dense SINRs out of tolerance; max rel {rel.max():.3e}"
+    assert np.all((flags & ts.TS_FLAG_ERRORS) == 0)
+    assert_sinr_close(got, ref, what=f"dense {case.w.name} {precoder}")
 
 
 @pytest.mark.parametrize("precoder", ["svd", "mmse"])
@@ -151,4 +125,4 @@ def test_factor_cancellation_on_gpu(precoder):
     case.with_channels(Xh)
     comp, _ = case.gpu_sinr(precoder, "paths")
     dense, _ = case.gpu_dense_sinr(precoder, "paths")
-    np.testing.assert_allclose(dense, comp, rtol=2e-4)
+    np.testing.assert_allclose(dense, comp, rtol=2e-5)   # both within 1e-5 of one oracle value
