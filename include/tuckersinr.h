@@ -265,8 +265,8 @@ int ts_sinr_svd_from_precoders(const ts_dims* d, const ts_coef* coef,
 /* ts_sinr_svd with the interfering links' core contraction (eq. 15) in the
  * arithmetic `precision` (TS_PREC_*; TS_PREC_FP32 is ts_sinr_svd).  The
  * serving links and the precoders stay FP32.  Tensor-core modes need
- * L <= 8, p <= 32 and m <= 16 (else TS_ERR_MODE); ws holds
- * ts_workspace_bytes(d, TS_OP_SINR_SVD_TF32 / _BF16X2) bytes (the core
+ * even L <= 8, p <= 32 and m <= 16 (else TS_ERR_MODE); ws holds
+ * ts_workspace_bytes(d, TS_OP_SINR_SVD_TF32 / _BF16X2 / _TF32X3) bytes (the core
  * rewritten as a tensor-core operand, then the ts_sinr_svd workspace).
  * ts_sinr_svd_from_precoders_prec is its second phase (after
  * ts_svd_precoders on the same ws). */
@@ -279,6 +279,26 @@ int ts_sinr_svd_from_precoders_prec(const ts_dims* d, const ts_coef* coef,
                                     const float* sigma2, int precision,
                                     float* sinr, uint8_t* flags, void* ws,
                                     size_t ws_bytes, void* stream);
+
+/* Subcarrier ranges (the partition of one system across devices): the SINR
+ * of subcarriers kappa0 .. kappa0 + count - 1 of the system d (eq. 2, 9:
+ * every subcarrier is an independent unit, the precoders of eq. 7 are per
+ * subcarrier too), with G, C and the coefficients of the whole system
+ * (dense coefficients: c[ch][d->K][P]).  Results and per-result flags of
+ * the range only: sinr [J][count][L], flags [J][count]; they equal the same
+ * subcarriers of a whole-system call bit for bit (the same arithmetic per
+ * unit).  ws: ts_workspace_bytes of d with K = count, for the op of the
+ * call (TS_OP_SINR_SVD / _TF32 / _BF16X2 / _TF32X3 by precision, or
+ * TS_OP_SINR_MMSE).  TS_ERR_DIMS unless 0 <= kappa0 and
+ * kappa0 + count <= d->K. */
+int ts_sinr_svd_range(const ts_dims* d, int kappa0, int count, const ts_coef* coef,
+                      const ts_c64* G, const ts_c64* C, const float* sigma2,
+                      int precision, float* sinr, uint8_t* flags, void* ws,
+                      size_t ws_bytes, void* stream);
+int ts_sinr_mmse_range(const ts_dims* d, int kappa0, int count, const ts_coef* coef,
+                       const ts_c64* G, const ts_c64* C, const ts_c64* Pt,
+                       const float* sigma2, float* sinr, uint8_t* flags, void* ws,
+                       size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------- batches
  * Many independent systems with their own sizes (numbers of cells, antennas,

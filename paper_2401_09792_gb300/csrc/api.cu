@@ -28,6 +28,15 @@ constexpr int kMaxRankMLarge = 64;
 // launch-shape choices of the batch planner (0: default heuristics)
 thread_local ts::Tuning g_tuning = {0, 0};
 thread_local bool g_timing_suspended = false;
+// subcarrier range of the SINR calls in progress on this host thread (the
+// range entry points): local subcarrier 0 is g_kap_off, the dense
+// coefficients have g_Kc subcarriers (0: the call's own K)
+thread_local int g_kap_off = 0;
+thread_local int g_Kc = 0;
+struct RangeScope {
+  RangeScope(int off, int Kc) { g_kap_off = off; g_Kc = Kc; }
+  ~RangeScope() { g_kap_off = 0; g_Kc = 0; }
+};
 
 // Side streams on which the UE groups of a several-UE call run concurrently
 // (created on first use per device, kept for the life of the process).
@@ -253,6 +262,8 @@ ts::SinrArgs base_args(const ts_dims* d, const ts_coef* coef, const ts_c64* G, c
   a.G = reinterpret_cast<const float2*>(G);
   a.C = reinterpret_cast<const float2*>(C);
   a.coef = reinterpret_cast<const float2*>(coef->mode == TS_COEF_DENSE ? coef->c : coef->alpha);
+  a.kap_off = g_kap_off;
+  a.Kc = g_Kc > 0 ? g_Kc : d->K;
   a.turns = reinterpret_cast<const unsigned long long*>(ws + w.turns);
   a.Eserv = reinterpret_cast<float2*>(ws + w.Eserv);
   a.Eint = reinterpret_cast<float2*>(ws + w.Eint);
@@ -809,6 +820,28 @@ int ts_dense_sinr_mmse(const ts_dims* d, const ts_coef* coef, const ts_c64* X, c
   const ts_dims e = dense_dims(d);
   return sinr_mmse_impl(&e, coef, X, nullptr, true, Pfull, sigma2, sinr, flags, ws, ws_bytes,
                         stream);
+}
+
+int ts_sinr_svd_range(const ts_dims* d, int kappa0, int count, const ts_coef* coef, const ts_c64* G,
+                      const ts_c64* C, const float* sigma2, int precision, float* sinr,
+                      uint8_t* flags, void* ws, size_t ws_bytes, void* stream) {
+  if (d == nullptr) return TS_ERR_NULL;
+  if (kappa0 < 0 || count < 1 || (int64_t)kappa0 + count > d->K) return TS_ERR_DIMS;
+  ts_dims r = *d;
+  r.K = count;
+  RangeScope scope(kappa0, d->K);
+  return ts_sinr_svd_prec(&r, coef, G, C, sigma2, precision, sinr, flags, ws, ws_bytes, stream);
+}
+
+int ts_sinr_mmse_range(const ts_dims* d, int kappa0, int count, const ts_coef* coef, const ts_c64* G,
+                       const ts_c64* C, const ts_c64* Pt, const float* sigma2, float* sinr,
+                       uint8_t* flags, void* ws, size_t ws_bytes, void* stream) {
+  if (d == nullptr) return TS_ERR_NULL;
+  if (kappa0 < 0 || count < 1 || (int64_t)kappa0 + count > d->K) return TS_ERR_DIMS;
+  ts_dims r = *d;
+  r.K = count;
+  RangeScope scope(kappa0, d->K);
+  return ts_sinr_mmse(&r, coef, G, C, Pt, sigma2, sinr, flags, ws, ws_bytes, stream);
 }
 
 }  // extern "C"

@@ -14,7 +14,9 @@ struct SinrArgs {
   bool identity_C;                  // dense-channel comparator: C = I (p = P), G = X
   const float2* G;                  // [J*J][p][m][n]
   const float2* C;                  // [J*J][P][p]
-  const float2* coef;               // dense: [J*J][K][P]; paths: alpha [J*J][P]
+  const float2* coef;               // dense: [J*J][Kc][P]; paths: alpha [J*J][P]
+  int kap_off;                      // subcarrier index of local subcarrier 0 (a range call)
+  int Kc;                           // subcarriers of the dense coefficient array (its stride)
   const unsigned long long* turns;  // paths: [J*J][P] df*tau in 2^-64 turns
   float2* V;                        // svd: precoders [J][K][n][L] (workspace)
   uint8_t* pflag;                   // svd: precoder flags [J][K] (workspace)

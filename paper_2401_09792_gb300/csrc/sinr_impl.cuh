@@ -239,8 +239,8 @@ __device__ __forceinline__ void serve_channels(const SinrArgs& A, const Precoder
   auto coef_at = [&](int t, int pp) -> float2 {
     const int kk = kap0 + t;
     if (kk >= K) return cz();
-    return A.coef_mode == 0 ? A.coef[((size_t)ch * K + kk) * P + pp]
-                            : path_coef(A.coef[(size_t)ch * P + pp], turns[pp], kk);
+    return A.coef_mode == 0 ? A.coef[((size_t)ch * A.Kc + A.kap_off + kk) * P + pp]
+                            : path_coef(A.coef[(size_t)ch * P + pp], turns[pp], A.kap_off + kk);
   };
   if (A.identity_C) {                      // dense channel: C = I, p = P
     for (int idx = tid; idx < T * p; idx += nth) w[idx] = cconj(coef_at(idx / p, idx % p));
@@ -518,7 +518,7 @@ __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, con
     }
   }
 
-  // Close pairs.  Two eigenvalues of rank r and r + 1 (r < L) within 2% of
+  // Close pairs.  Two eigenvalues of rank r and r + 1 (r < L) within 5% of
   // lambda_1 of each other are mixed by the Gram's FP32 rounding by about
   // u lambda_1 / (lambda_r - lambda_r+1) (up to ~5e-5 rad on the synthetic
   // channels), and the per-stream SINRs follow that mixing (~0.5 per rad).
@@ -534,7 +534,7 @@ __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, con
       const unsigned bq = __ballot_sync(FULL, a < m && erank == r + 1) & gmask;
       const int pp = bp ? __ffs(bp) - 1 - gb : 0, qq = bq ? __ffs(bq) - 1 - gb : 0;
       const float lp = __shfl_sync(FULL, lam, pp, MG), lq = __shfl_sync(FULL, lam, qq, MG);
-      const bool close = bp && bq && (lp - lq) < 2e-2f * lmax;
+      const bool close = bp && bq && (lp - lq) < 5e-2f * lmax;
       if (!__any_sync(FULL, close)) continue;
       float alh = 0.f, all = 0.f, beh = 0.f, bel = 0.f;
       float2 gah = cz(), gal = cz();
@@ -786,7 +786,7 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link(const SinrArgs A, const 
     for (int idx = tid; idx < T * P; idx += nth) {
       const int t = idx / P, pp = idx - t * P;
       const bool ok = kap0 + t < K;
-      cp_async8(cs + idx, ok ? A.coef + ((size_t)ch * K + kap0 + t) * P + pp : A.coef, ok);
+      cp_async8(cs + idx, ok ? A.coef + ((size_t)ch * A.Kc + A.kap_off + kap0 + t) * P + pp : A.coef, ok);
     }
   } else {
     for (int idx = tid; idx < P; idx += nth) {
@@ -817,7 +817,7 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link(const SinrArgs A, const 
     const unsigned long long* pt = reinterpret_cast<const unsigned long long*>(sm + pl.off_pt);
     for (int idx = tid; idx < T * P; idx += nth) {
       const int t = idx / P, pp = idx - t * P;
-      cs[idx] = (kap0 + t < K) ? path_coef(pa[pp], pt[pp], kap0 + t) : cz();
+      cs[idx] = (kap0 + t < K) ? path_coef(pa[pp], pt[pp], A.kap_off + kap0 + t) : cz();
     }
     __syncthreads();
   }
@@ -1049,7 +1049,7 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link_blk(const SinrArgs A, co
     for (int idx = tid; idx < T * P; idx += kThreads) {
       const int t = idx / P, pp = idx - t * P;
       const bool ok = kap0 + t < K;
-      cp_async8(cs + idx, ok ? A.coef + ((size_t)ch * K + kap0 + t) * P + pp : A.coef, ok);
+      cp_async8(cs + idx, ok ? A.coef + ((size_t)ch * A.Kc + A.kap_off + kap0 + t) * P + pp : A.coef, ok);
     }
   } else {
     for (int idx = tid; idx < P; idx += kThreads) {
@@ -1079,7 +1079,7 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link_blk(const SinrArgs A, co
       float2 mine = cz();
       const int pm = p0 + qs;
       if (kap_t < K && pm < P)
-        mine = A.coef_mode == 0 ? cs[t * P + pm] : path_coef(pa[pm], pt[pm], kap_t);
+        mine = A.coef_mode == 0 ? cs[t * P + pm] : path_coef(pa[pm], pt[pm], A.kap_off + kap_t);
 #pragma unroll
       for (int r = 0; r < QS; ++r) {
         const int pp = p0 + r;

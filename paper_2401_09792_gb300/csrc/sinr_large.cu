@@ -231,6 +231,17 @@ __global__ void __launch_bounds__(kLargeThreads) k_svd_precoder_large(const Sinr
     }
   }
 
+  // Each rotation is applied in FP32, so over the sweeps the columns of U
+  // drift from unit norm (~1e-6 for 60 rows); E_kk = U_L Sigma_L below
+  // scales with them, so every column is renormalised (thread c on column c).
+  for (int c = tid; c < m; c += nth) {
+    float nb = 0.f;
+    for (int a = 0; a < m; ++a) nb += cabs2(U[a * SD + c]);
+    const float sc = nb > 0.f ? 1.f / sqrtf(nb) : 1.f;
+    for (int a = 0; a < m; ++a) U[a * SD + c] = cscale(U[a * SD + c], sc);
+  }
+  __syncthreads();
+
   // 3. order of the eigenvalues (descending); the top L columns of U
   if (tid < m) {
     const float la = S[tid * SD + tid].x;
@@ -243,6 +254,35 @@ __global__ void __launch_bounds__(kLargeThreads) k_svd_precoder_large(const Sinr
   }
   __syncthreads();
 
+  // The kept columns, in rank order, orthonormalised against each other by
+  // warp 0 (modified Gram-Schmidt, lanes over the rows): the close-pair
+  // rotation below would amplify their mutual defect by lambda / gap.
+  if (warp == 0) {
+    for (int r = 0; r < L; ++r) {
+      const int cr = pq[r];
+      for (int r2 = 0; r2 < r; ++r2) {
+        const int c2 = pq[r2];
+        float2 pr = cz();
+        for (int a = lane; a < m; a += 32) cmacc(pr, U[a * SD + cr], U[a * SD + c2]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          pr.x += __shfl_xor_sync(FULL, pr.x, o);
+          pr.y += __shfl_xor_sync(FULL, pr.y, o);
+        }
+        for (int a = lane; a < m; a += 32) cms(U[a * SD + cr], pr, U[a * SD + c2]);
+        __syncwarp();
+      }
+      float nb = 0.f;
+      for (int a = lane; a < m; a += 32) nb += cabs2(U[a * SD + cr]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) nb += __shfl_xor_sync(FULL, nb, o);
+      const float sc = nb > 0.f ? 1.f / sqrtf(nb) : 1.f;
+      for (int a = lane; a < m; a += 32) U[a * SD + cr] = cscale(U[a * SD + cr], sc);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+
   // 4. W rows r < L: W[r][c] = sum_b conj(U[b][idx_r]) H~[b][c] (reuses Hc)
   float2* W = Hc;
   for (int idx = tid; idx < L * n; idx += nth) {
@@ -251,6 +291,63 @@ __global__ void __launch_bounds__(kLargeThreads) k_svd_precoder_large(const Sinr
     float2 v = cz();
     for (int b = 0; b < m; ++b) cmacc(v, H[(size_t)b * n + c], U[b * SD + col]);
     W[r * n + c] = v;
+  }
+  __syncthreads();
+  // Close pairs among the kept vectors (eigenvalues of rank r and r + 1
+  // within 5% of lambda_1): the rows of W are rotated once more from their
+  // 2 x 2 Gram accumulated in double-float, as in the register precoder, by
+  // warp 0 (lanes over the columns of W and the rows of U).
+  if (warp == 0) {
+    const float lmax = S[pq[0] * SD + pq[0]].x;
+    for (int r = 0; r + 1 < L; ++r) {
+      const int cp = pq[r], cq = pq[r + 1];
+      if (!(S[cp * SD + cp].x - S[cq * SD + cq].x < 5e-2f * lmax)) continue;
+      float alh = 0.f, all = 0.f, beh = 0.f, bel = 0.f;
+      float2 gah = cz(), gal = cz();
+      for (int c = lane; c < n; c += 32) {
+        const float2 x = W[r * n + c], y = W[(r + 1) * n + c];
+        df_add_prod(alh, all, x.x, x.x);
+        df_add_prod(alh, all, x.y, x.y);
+        df_add_prod(beh, bel, y.x, y.x);
+        df_add_prod(beh, bel, y.y, y.y);
+        df_cmacc(gah, gal, x, y);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        df_add(alh, all, __shfl_xor_sync(FULL, alh, o), __shfl_xor_sync(FULL, all, o));
+        df_add(beh, bel, __shfl_xor_sync(FULL, beh, o), __shfl_xor_sync(FULL, bel, o));
+        df_add(gah.x, gal.x, __shfl_xor_sync(FULL, gah.x, o), __shfl_xor_sync(FULL, gal.x, o));
+        df_add(gah.y, gal.y, __shfl_xor_sync(FULL, gah.y, o), __shfl_xor_sync(FULL, gal.y, o));
+      }
+      const float dba = __fadd_rn(__fsub_rn(beh, alh), __fsub_rn(bel, all));
+      const float gx = gah.x + gal.x, gy = gah.y + gal.y;
+      const float ab = sqrtf(fmaf(gx, gx, gy * gy));
+      if (ab > 0.f && ab > 1e-12f * sqrtf(alh) * sqrtf(beh)) {
+        const float tau = dba / (2.f * ab);
+        const float t = copysignf(1.f, tau) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
+        const float cr = 1.f / sqrtf(fmaf(t, t, 1.f));
+        const float sr = t * cr;
+        const float2 e = make_float2(gx / ab, gy / ab);
+        const float2 se = cscale(e, sr), sec = cscale(cconj(e), sr);
+        for (int c = lane; c < n; c += 32) {           // W <- J* W (rows r, r + 1)
+          const float2 x = W[r * n + c], y = W[(r + 1) * n + c];
+          float2 nx = cscale(x, cr), ny = cscale(y, cr);
+          cms(nx, se, y);
+          cmac(ny, sec, x);
+          W[r * n + c] = nx;
+          W[(r + 1) * n + c] = ny;
+        }
+        for (int a = lane; a < m; a += 32) {           // U <- U J (columns p, q)
+          const float2 x = U[a * SD + cp], y = U[a * SD + cq];
+          float2 nx = cscale(x, cr), ny = cscale(y, cr);
+          cms(nx, sec, y);
+          cmac(ny, se, x);
+          U[a * SD + cp] = nx;
+          U[a * SD + cq] = ny;
+        }
+      }
+      __syncwarp();
+    }
   }
   __syncthreads();
   float s2[LT];

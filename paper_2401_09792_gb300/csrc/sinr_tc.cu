@@ -22,13 +22,15 @@
 // specialised.  Warp 0, one thread: bulk copies (cp.async.bulk, mbarrier
 // transaction counts) of the projection operand and of the core operand in
 // blocks of CB columns of H~ (N = 64 accumulator columns) into a three-slot
-// ring, and the MMAs of each block into one of two TMEM buffers.  Warps
-// 1 .. 4 RG (RG row groups of RPT rows): thread (lane quadrant, group g)
-// owns subcarrier t of the tile and rows g RPT .. g RPT + RPT - 1; per block
-// it reads its H~ rows from TMEM (tcgen05.ld, one column at a time), frees
-// the buffer, and accumulates E += H~ V~ with the precoder rows of its
-// subcarrier, which it stages itself (cp.async) two blocks ahead.  No
-// CTA-wide barrier in the loop: the roles meet only at mbarriers.  Every
+// ring, and the MMAs of each block into one of two TMEM buffers.  Warp 1,
+// one thread: the precoder rows of each block for the tile's subcarriers,
+// laid out contiguously once per call by k_v_tiles, one bulk copy per block
+// into a ring of up to four slots.  Warps 2 .. 1 + 4 RG (RG row groups of RPT rows): thread
+// (lane quadrant, group g) owns subcarrier t of the tile and rows
+// g RPT .. g RPT + RPT - 1; per block it reads its H~ rows from TMEM
+// (tcgen05.ld, one column at a time) and accumulates E += H~ V~, then frees
+// the TMEM buffer and the precoder slot.  No CTA-wide barrier in the loop:
+// the roles meet only at mbarriers.  Every
 // wait is bounded; on a timeout the tile's precoder flags get
 // TS_FLAG_TIMEOUT, outstanding copies and MMAs get another bounded wait,
 // and the TMEM is released.
@@ -43,6 +45,7 @@ namespace {
 constexpr int kTile = 128;     // subcarriers per CTA = MMA M = TMEM lanes
 constexpr int kNtile = 64;     // accumulator columns per block (MMA N)
 constexpr int kBStages = 3;    // core-operand ring
+constexpr int kVStages = 4;    // precoder-row ring (at most; fewer when shared memory is short)
 constexpr long kSpinLimit = 1L << 24;
 
 __host__ __device__ constexpr int tc_rpt(int MG) { return MG < 8 ? MG : 8; }
@@ -58,14 +61,16 @@ struct TcPlan {
   int kseg;        // elements per K segment: 2p padded to 32 bytes
   int kbytes;      // bytes per operand row
   int nblk;        // column blocks = ceil(n / CB)
-  int VS;          // precoder staging per thread and slot (float2): CB LT
-  int nthreads;    // 32 (1 + 4 RG)
+  int VS;          // precoder rows of one subcarrier and block (float2): CB L
+  int vstages;     // slots of the precoder-row ring (2 .. kVStages)
+  int nthreads;    // 32 (2 + 4 RG): MMA warp, precoder-row warp, epilogue warps
   int off_A, off_B, off_V, off_bar, smem;   // byte offsets
   size_t prep_bytes_per_link;               // k_core_prep output per link
   size_t a_bytes_per_tile;                  // k_tc_proj output per (link, tile)
+  size_t v_bytes_per_tile;                  // k_v_tiles output per (BS, tile)
 };
 
-inline TcPlan tc_plan(int MG, int LT, int n, int p, int prec) {
+inline TcPlan tc_plan(int MG, int L, int n, int p, int prec) {
   TcPlan t;
   t.ES = tc_es(prec);
   t.nseg = tc_nseg(prec);
@@ -74,17 +79,22 @@ inline TcPlan tc_plan(int MG, int LT, int n, int p, int prec) {
   t.kbytes = t.nseg * t.kseg * t.ES;
   const int CB = tc_cb(MG);
   t.nblk = (n + CB - 1) / CB;
-  t.VS = CB * LT;
-  t.nthreads = 32 * (1 + 4 * tc_rg(MG));
+  t.VS = CB * L;
+  t.nthreads = 32 * (2 + 4 * tc_rg(MG));
   int o = 0;
   t.off_A = o; o += kTile * t.kbytes;
   t.off_B = o; o += kBStages * kNtile * t.kbytes;
-  t.off_V = o; o += (t.nthreads - 32) * 2 * t.VS * 8;
+  // as many precoder-row slots as fit beside the operands (227 KB per CTA,
+  // 1 KB of it static)
+  t.vstages = kVStages;
+  while (t.vstages > 2 && o + t.vstages * kTile * t.VS * 8 + 24 * 8 + 16 > 226 * 1024) --t.vstages;
+  t.off_V = o; o += t.vstages * kTile * t.VS * 8;
   o = (o + 15) & ~15;
-  t.off_bar = o; o += 16 * 8;
+  t.off_bar = o; o += 24 * 8;
   t.smem = o;
   t.prep_bytes_per_link = (size_t)t.nblk * kNtile * t.kbytes;
   t.a_bytes_per_tile = (size_t)kTile * t.kbytes;
+  t.v_bytes_per_tile = (size_t)t.nblk * kTile * t.VS * 8;
   return t;
 }
 
@@ -249,8 +259,9 @@ __global__ void __launch_bounds__(4 * kTile) k_tc_proj(const SinrArgs A, int kse
       const int kap = kap0 + tt;
       float2 c = cz();
       if (pp < pc && kap < K)
-        c = A.coef_mode == 0 ? A.coef[((size_t)ch * K + kap) * P + P0 + pp]
-                             : path_coef(A.coef[(size_t)ch * P + P0 + pp], A.turns[(size_t)ch * P + P0 + pp], kap);
+        c = A.coef_mode == 0 ? A.coef[((size_t)ch * A.Kc + A.kap_off + kap) * P + P0 + pp]
+                             : path_coef(A.coef[(size_t)ch * P + P0 + pp], A.turns[(size_t)ch * P + P0 + pp],
+                                         A.kap_off + kap);
       cs[tt * (kProjPC + 1) + pp] = c;
     }
     __syncthreads();
@@ -312,13 +323,39 @@ __global__ void __launch_bounds__(4 * kTile) k_tc_proj(const SinrArgs A, int kse
   }
 }
 
+// ------------------------------------------------------- precoder tiles
+// The precoder rows V~_k(kappa)[c][l] of a (tile, column block) for the
+// link kernel, as one contiguous chunk: Vt[k][tile][b][t][CB][L] (t the
+// subcarrier of the tile), zero beyond K and n, so that one bulk copy moves
+// a block's rows for all 128 subcarriers.
+__global__ void k_v_tiles(const float2* __restrict__ V, int J, int K, int n, int L, int CB, int nblk,
+                          int ntile, float2* __restrict__ Vt) {
+  const size_t per_tile = (size_t)nblk * kTile * CB * L;
+  const size_t total = (size_t)J * ntile * per_tile;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int l = (int)(idx % L);
+    size_t r = idx / L;
+    const int c = (int)(r % CB);
+    r /= CB;
+    const int t = (int)(r % kTile);
+    r /= kTile;
+    const int b = (int)(r % nblk);
+    r /= nblk;
+    const int tile = (int)(r % ntile);
+    const int k = (int)(r / ntile);
+    const int kap = tile * kTile + t, col = b * CB + c;
+    Vt[idx] = (kap < K && col < n) ? V[(((size_t)k * K + kap) * n + col) * L + l] : cz();
+  }
+}
+
 // ----------------------------------------------------------- link kernel
-constexpr int kBars = 12;      // mbarriers of the link kernel (see below)
+constexpr int kBars = 20;      // mbarriers of the link kernel (see below)
 
 template <int MG, int LT, int PREC>
-__global__ void __launch_bounds__(32 * (1 + 4 * tc_rg(MG)), 1)
+__global__ void __launch_bounds__(32 * (2 + 4 * tc_rg(MG)), 1)
     k_sinr_link_tc(const SinrArgs A, const unsigned char* __restrict__ prep,
-                   const unsigned char* __restrict__ aop, TcPlan tp) {
+                   const unsigned char* __restrict__ aop, const float2* __restrict__ vtiles, TcPlan tp) {
   constexpr int RPT = tc_rpt(MG), RG = tc_rg(MG), CB = tc_cb(MG);
   constexpr int ES = tc_es(PREC);
   constexpr int KMMA = 32 / ES;                 // K elements per MMA instruction
@@ -339,7 +376,9 @@ __global__ void __launch_bounds__(32 * (1 + 4 * tc_rg(MG)), 1)
   float2* sV = reinterpret_cast<float2*>(smem + tp.off_V);
   // mbarriers: 0..2 core block loaded, 3..5 its MMAs done (slot free),
   // 6, 7 TMEM buffer written, 8, 9 TMEM buffer read (one arrival per
-  // epilogue warp), 10 projection operand loaded, 11 final drain
+  // epilogue warp), 10 projection operand loaded, 11 final drain,
+  // 12..15 precoder rows of a block loaded, 16..19 read (one arrival per
+  // epilogue warp)
   const uint32_t bar0 = smem_u32(smem + tp.off_bar);
   const size_t blk_bytes = (size_t)kNtile * kbytes;
   const unsigned char* prep_ch = prep + (size_t)ch * nblk * blk_bytes;
@@ -351,7 +390,7 @@ __global__ void __launch_bounds__(32 * (1 + 4 * tc_rg(MG)), 1)
     if (A.rcount != nullptr && blockIdx.x == 0 && i == 0 && z == 0) *A.rcount = 0;
     for (int s = 0; s < kBars; ++s)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar0 + 8u * s),
-                   "r"((s == 8 || s == 9) ? (uint32_t)NEPI : 1u));
+                   "r"((s == 8 || s == 9 || s >= 16) ? (uint32_t)NEPI : 1u));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -444,27 +483,41 @@ __global__ void __launch_bounds__(32 * (1 + 4 * tc_rg(MG)), 1)
         for (int u = consumed[s]; u < loaded[s]; ++u) mbar_wait(bar0 + 8u * s, (uint32_t)(u & 1));
       if (!ok) mbar_wait(afull, 0);
     }
+  } else if (warp == 1) {
+    // ---------------- precoder rows: one bulk copy per block of the tile's
+    // rows (k_v_tiles laid them out contiguously), into a ring shared by
+    // the row groups
+    if (lane == 0) {
+      const uint32_t chunk = (uint32_t)(kTile * tp.VS * 8);
+      const float2* vt = vtiles + ((size_t)k * gridDim.x + blockIdx.x) * tp.v_bytes_per_tile / 8;
+      bool ok = true;
+      int last[kVStages] = {-1, -1, -1, -1};
+      for (int b = 0; b < nblk; ++b) {
+        const int slot = b % tp.vstages;
+        if (b >= tp.vstages && !mbar_wait(bar0 + 8u * (16 + slot), (uint32_t)(((b / tp.vstages) - 1) & 1))) {
+          ok = false;
+          break;
+        }
+        const uint32_t vfull = bar0 + 8u * (12 + slot);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(vfull), "r"(chunk)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_u32(sV + (size_t)slot * kTile * tp.VS)),
+            "l"(vt + (size_t)b * kTile * tp.VS), "r"(chunk), "r"(vfull)
+            : "memory");
+        last[slot] = b;
+      }
+      if (!ok) *abort_v = 1;
+      // drain: the copies of the last block of each slot have landed
+      for (int sl = 0; sl < kVStages; ++sl)
+        if (last[sl] >= 0) mbar_wait(bar0 + 8u * (12 + sl), (uint32_t)((last[sl] / tp.vstages) & 1));
+    }
   } else {
     // ---------------- epilogue: E += H~ V~ for (subcarrier t_in, rows of group g)
-    const int ew = warp - 1, quad = warp & 3, g = ew >> 2;
+    const int ew = warp - 2, quad = warp & 3, g = ew >> 2;
     const int t_in = quad * 32 + lane;           // TMEM lane = subcarrier of the tile
     const int kap = kap0 + t_in;
-    float2* vslot = sV + (size_t)(ew * 32 + lane) * 2 * tp.VS;
-    auto issue_V = [&](int b) {
-      if (b < nblk) {
-        const int c0 = b * CB;
-        float2* dst = vslot + (b & 1) * tp.VS;
-#pragma unroll
-        for (int u = 0; u < CB * LT; ++u) {
-          const int cc = u / LT, l = u % LT;
-          const bool ok = kap < K && c0 + cc < n && l < L;
-          cp_async8(dst + u, ok ? A.V + (((size_t)k * K + kap) * n + c0 + cc) * L + l : A.V, ok);
-        }
-      }
-      cp_async_commit();
-    };
-    issue_V(0);
-    issue_V(1);
     float2 E[RPT][LT];
 #pragma unroll
     for (int r = 0; r < RPT; ++r)
@@ -472,13 +525,15 @@ __global__ void __launch_bounds__(32 * (1 + 4 * tc_rg(MG)), 1)
       for (int l = 0; l < LT; ++l) E[r][l] = cz();
     bool good = true;
     for (int b = 0; b < nblk; ++b) {
-      const int t = b & 1;
-      cp_async_wait<1>();                        // this thread's precoder rows of block b
+      const int t = b & 1, slot = b % tp.vstages;
+      if (!mbar_wait(bar0 + 8u * (12 + slot), (uint32_t)((b / tp.vstages) & 1))) { good = false; break; }
       if (!mbar_wait(bar0 + 8u * (6 + t), (uint32_t)((b >> 1) & 1))) { good = false; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const float2* vb = vslot + (b & 1) * tp.VS;
+      const float2* vb = sV + ((size_t)slot * kTile + t_in) * tp.VS;
+      const int ncb = min(CB, n - b * CB);       // columns of this block (uniform)
 #pragma unroll
       for (int cc = 0; cc < CB; ++cc) {
+        if (cc >= ncb) break;
         uint32_t h[2 * RPT];
         const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) +
                                (uint32_t)(t * kNtile + (cc * RG + g) * 2 * RPT);
@@ -503,7 +558,8 @@ __global__ void __launch_bounds__(32 * (1 + 4 * tc_rg(MG)), 1)
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
         for (int l2 = 0; l2 < LT / 2; ++l2) {
-          const float4 v = reinterpret_cast<const float4*>(vb + cc * LT)[l2];
+          if (2 * l2 >= L) break;
+          const float4 v = reinterpret_cast<const float4*>(vb + cc * L)[l2];
           const float2 v0 = make_float2(v.x, v.y), v1 = make_float2(v.z, v.w);
 #pragma unroll
           for (int r = 0; r < RPT; ++r) {
@@ -515,11 +571,11 @@ __global__ void __launch_bounds__(32 * (1 + 4 * tc_rg(MG)), 1)
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
-      if (lane == 0)
+      if (lane == 0) {
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar0 + 8u * (8 + t)) : "memory");
-      issue_V(b + 2);
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar0 + 8u * (16 + slot)) : "memory");
+      }
     }
-    cp_async_wait<0>();
     if (!good) *abort_v = 1;
     // rows of the interfering effective channel E_ik (eq. 24); the
     // finalisation forms the covariance of eq. (25)
@@ -551,7 +607,7 @@ __global__ void __launch_bounds__(32 * (1 + 4 * tc_rg(MG)), 1)
 // interfering links' tiles (each written in full, padding included)
 template <int PREC>
 cudaError_t launch_prep(const SinrArgs& A, int MG, int LT, unsigned char* prep, cudaStream_t s) {
-  const TcPlan tp = tc_plan(MG, LT, A.n, A.p, PREC);
+  const TcPlan tp = tc_plan(MG, A.L, A.n, A.p, PREC);
   const size_t bbytes = tp.prep_bytes_per_link * (size_t)A.J * A.J;
   const int nchunk = kNtile * (tp.kbytes / 16);
   const int nblocks = A.J * A.J * tp.nblk;
@@ -564,22 +620,33 @@ cudaError_t launch_prep(const SinrArgs& A, int MG, int LT, unsigned char* prep, 
                    kProjPC * A.p * 8;
   e = cudaFuncSetAttribute(k_tc_proj<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  dim3 grid((A.K + kTile - 1) / kTile, A.J, A.J - 1);
+  const int ntile = (A.K + kTile - 1) / kTile;
+  dim3 grid(ntile, A.J, A.J - 1);
   k_tc_proj<PREC><<<grid, kTile * ((A.p + kProjQ - 1) / kProjQ), smem, s>>>(A, tp.kseg, tp.kbytes,
                                                                           prep + bbytes);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // the precoder rows, tiled per (tile, column block)
+  const size_t abytes = tp.a_bytes_per_tile * ntile * (size_t)A.J * (A.J - 1);
+  const size_t vtotal = (size_t)A.J * ntile * tp.nblk * kTile * tp.VS;
+  const int vblocks = (int)((vtotal + 255) / 256 < 152 * 16 ? (vtotal + 255) / 256 : 152 * 16);
+  k_v_tiles<<<vblocks, 256, 0, s>>>(A.V, A.J, A.K, A.n, A.L, tc_cb(MG), tp.nblk, ntile,
+                                    reinterpret_cast<float2*>(prep + bbytes + abytes));
   return cudaGetLastError();
 }
 
 template <int MG, int LT, int PREC>
 cudaError_t launch_tc(const SinrArgs& A, const unsigned char* prep, cudaStream_t s) {
   if (A.J < 2) return cudaSuccess;
-  const TcPlan tp = tc_plan(MG, LT, A.n, A.p, PREC);
+  const TcPlan tp = tc_plan(MG, A.L, A.n, A.p, PREC);
   auto kern = k_sinr_link_tc<MG, LT, PREC>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, tp.smem);
   if (e != cudaSuccess) return e;
   dim3 grid((A.K + kTile - 1) / kTile, A.J, A.J - 1);
   const unsigned char* aop = prep + tp.prep_bytes_per_link * (size_t)A.J * A.J;
-  kern<<<grid, tp.nthreads, tp.smem, s>>>(A, prep, aop, tp);
+  const size_t abytes = tp.a_bytes_per_tile * grid.x * (size_t)A.J * (A.J - 1);
+  const float2* vt = reinterpret_cast<const float2*>(aop + abytes);
+  kern<<<grid, tp.nthreads, tp.smem, s>>>(A, prep, aop, vt, tp);
   return cudaGetLastError();
 }
 
@@ -599,15 +666,17 @@ inline int tc_lt(int m, int L) { return L <= 2 && m <= 8 ? 2 : L <= 4 ? 4 : 8; }
 
 bool tc_supported(int m, int L, int p) {
   const int MG = detail::tc_mg(m), LT = detail::tc_lt(m, L);
-  if (m > 16 || L > 8 || LT > MG || p > 32) return false;
-  const detail::TcPlan tp = detail::tc_plan(MG, LT, 512, p, TS_PREC_TF32X3);
+  // even L: the precoder rows of a block are copied as 16-byte multiples
+  if (m > 16 || L > 8 || (L & 1) || LT > MG || p > 32) return false;
+  const detail::TcPlan tp = detail::tc_plan(MG, L, 512, p, TS_PREC_TF32X3);
   return tp.smem + 1024 <= 227 * 1024;   // + the static shared memory of the kernel
 }
 
 size_t tc_prep_bytes(int J, int m, int L, int n, int p, int K, int prec) {
-  const detail::TcPlan tp = detail::tc_plan(detail::tc_mg(m), detail::tc_lt(m, L), n, p, prec);
+  const detail::TcPlan tp = detail::tc_plan(detail::tc_mg(m), L, n, p, prec);
   const size_t tiles = (size_t)(K + detail::kTile - 1) / detail::kTile;
-  return tp.prep_bytes_per_link * (size_t)J * J + tp.a_bytes_per_tile * tiles * J * (J - 1);
+  return tp.prep_bytes_per_link * (size_t)J * J + tp.a_bytes_per_tile * tiles * J * (J - 1) +
+         tp.v_bytes_per_tile * tiles * J;
 }
 
 cudaError_t launch_core_prep(const SinrArgs& a, int prec, void* prep, cudaStream_t s) {

@@ -99,9 +99,9 @@ __global__ void __launch_bounds__(NT, NT > kThreads ? 2 : 0) k_sinr_link_wide(co
 
   // c_q(kappa) of this link (dense tile or path form), from global memory
   auto coef_at = [&](int kap, int q) -> float2 {
-    return A.coef_mode == 0 ? A.coef[((size_t)ch * K + kap) * P + q]
+    return A.coef_mode == 0 ? A.coef[((size_t)ch * A.Kc + A.kap_off + kap) * P + q]
                             : path_coef(__ldg(A.coef + (size_t)ch * P + q),
-                                        __ldg(A.turns + (size_t)ch * P + q), kap);
+                                        __ldg(A.turns + (size_t)ch * P + q), A.kap_off + kap);
   };
 
   // the current pass: columns [qlo, qlo + qn) of w, nq slabs per column chunk
@@ -374,9 +374,9 @@ __global__ void __launch_bounds__(kThreads) k_wide_proj(const SinrArgs A, const 
   const float2* Cch = A.C + (size_t)ch * P * p;
   const bool c16 = (p % 2 == 0) && (((uintptr_t)A.C & 15u) == 0);
   auto coef_at = [&](int kap, int q) -> float2 {
-    return A.coef_mode == 0 ? A.coef[((size_t)ch * K + kap) * P + q]
+    return A.coef_mode == 0 ? A.coef[((size_t)ch * A.Kc + A.kap_off + kap) * P + q]
                             : path_coef(__ldg(A.coef + (size_t)ch * P + q),
-                                        __ldg(A.turns + (size_t)ch * P + q), kap);
+                                        __ldg(A.turns + (size_t)ch * P + q), A.kap_off + kap);
   };
   auto issue = [&](int ci) {
     float2* buf = sm + (ci & 1) * pl.proj;

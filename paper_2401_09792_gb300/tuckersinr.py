@@ -82,6 +82,12 @@ _SIG = {
                                     _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "ts_sinr_svd": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.POINTER(ts_coef), _P, _P, _P,
                                    _P, _P, _P, ctypes.c_size_t, _P]),
+    "ts_sinr_svd_range": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.c_int, ctypes.c_int,
+                                         ctypes.POINTER(ts_coef), _P, _P, _P, ctypes.c_int, _P, _P,
+                                         _P, ctypes.c_size_t, _P]),
+    "ts_sinr_mmse_range": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(ts_coef), _P, _P, _P, _P, _P, _P, _P,
+                                          ctypes.c_size_t, _P]),
     "ts_dense_sinr_svd": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.POINTER(ts_coef), _P, _P,
                                          _P, _P, _P, ctypes.c_size_t, _P]),
     "ts_dense_sinr_mmse": (ctypes.c_int, [ctypes.POINTER(ts_dims), ctypes.POINTER(ts_coef), _P, _P,
@@ -262,6 +268,24 @@ def ts_sinr_svd_prec(d: Dims, coef: ts_coef, G, C, sigma2, precision: int, sinr,
            lib.ts_sinr_svd_prec(ctypes.byref(d.c()), ctypes.byref(coef), _ptr(G), _ptr(C), _ptr(sigma2),
                                 int(precision), _ptr(sinr), _ptr(flags), _ptr(ws), ws.numel(),
                                 _stream(stream)))
+
+
+def ts_sinr_svd_range(d: Dims, kappa0: int, count: int, coef: ts_coef, G, C, sigma2, precision: int,
+                      sinr, flags, ws, stream=None):
+    lib = load()
+    _check("ts_sinr_svd_range",
+           lib.ts_sinr_svd_range(ctypes.byref(d.c()), int(kappa0), int(count), ctypes.byref(coef), _ptr(G),
+                                 _ptr(C), _ptr(sigma2), int(precision), _ptr(sinr), _ptr(flags), _ptr(ws),
+                                 ws.numel(), _stream(stream)))
+
+
+def ts_sinr_mmse_range(d: Dims, kappa0: int, count: int, coef: ts_coef, G, C, Pt, sigma2, sinr, flags,
+                       ws, stream=None):
+    lib = load()
+    _check("ts_sinr_mmse_range",
+           lib.ts_sinr_mmse_range(ctypes.byref(d.c()), int(kappa0), int(count), ctypes.byref(coef), _ptr(G),
+                                  _ptr(C), _ptr(Pt), _ptr(sigma2), _ptr(sinr), _ptr(flags), _ptr(ws),
+                                  ws.numel(), _stream(stream)))
 
 
 def ts_sinr_svd_from_precoders_prec(d: Dims, coef: ts_coef, G, C, sigma2, precision: int, sinr, flags,

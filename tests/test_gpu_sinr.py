@@ -5,6 +5,10 @@ the GPU, complex128 in the oracle, the same complex64 inputs).  FP32
 rounding of the compressed channels alone moves the SINR by ~5e-7 at these
 sizes (the oracle's own channels rounded to complex64), so the bound leaves
 room for the eigensolve and the solves but not for an unconverged precoder.
+The one exception is a stream whose serving singular value is below 1e-2 of
+the largest (only the square L = m = n edge case has them): its SINR is
+fixed by the complex64 inputs only to ~u sigma_1 / sigma_r, and gets that
+on top (tests/gpu_inputs.py, weak_stream_rtol).
 """
 import numpy as np
 import pytest
@@ -15,7 +19,7 @@ pytestmark = pytest.mark.gpu
 from oracle import sinr as S  # noqa: E402
 from paper_2401_09792_gb300 import synth  # noqa: E402
 from paper_2401_09792_gb300 import tuckersinr as ts  # noqa: E402
-from tests.gpu_inputs import Case, assert_sinr_close, workload  # noqa: E402
+from tests.gpu_inputs import Case, assert_sinr_close, weak_stream_rtol, workload  # noqa: E402
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -29,7 +33,8 @@ def _check(case: Case, precoder: str, mode: str):
     got, flags = case.gpu_sinr(precoder, mode)
     ref = case.oracle_sinr(precoder)
     assert np.all((flags & ts.TS_FLAG_ERRORS) == 0), np.unique(flags)
-    return assert_sinr_close(got, ref, what=f"{case.w.name} {precoder} {mode}")
+    return assert_sinr_close(got, ref, weak_stream_rtol(case, precoder=precoder),
+                             what=f"{case.w.name} {precoder} {mode}")
 
 
 @pytest.mark.parametrize("precoder", ["svd", "mmse"])
@@ -97,7 +102,8 @@ def _check_dense(case: Case, precoder: str):
     got, flags = case.gpu_dense_sinr(precoder, "paths")
     ref = case.oracle_dense_sinr(precoder)
     assert np.all((flags & ts.TS_FLAG_ERRORS) == 0)
-    assert_sinr_close(got, ref, what=f"dense {case.w.name} {precoder}")
+    assert_sinr_close(got, ref, weak_stream_rtol(case, dense=True, precoder=precoder),
+                      what=f"dense {case.w.name} {precoder}")
 
 
 @pytest.mark.parametrize("precoder", ["svd", "mmse"])
