@@ -135,7 +135,8 @@ bool fuses_serve(const ts_dims* d) {
 
 // Workspace layout (byte offsets from the base, each 256-byte aligned).
 struct Workspace {
-  size_t turns = 0, V = 0, Hserv = 0, Wserv = 0, Eserv = 0, Eint = 0, pflag = 0, F = 0, rlist = 0,
+  size_t turns = 0, V = 0, Hserv = 0, Wserv = 0, Ueig = 0, lam = 0, conv = 0, Eserv = 0, Eint = 0,
+         pflag = 0, F = 0, rlist = 0,
          rcount = 0, total = 0;
 };
 
@@ -155,6 +156,15 @@ Workspace carve(const ts_dims* d, int op) {
     if (!fuses_serve(d)) {
       w.Hserv = o;
       o = align_up(o + (size_t)d->J * d->K * d->m * d->n * sizeof(float2), 256);
+      if (d->m <= ts::kMaxRankM && d->n <= ts::kMaxNRegisterPrecoder) {
+        // the two-phase precoder's eigenvectors, eigenvalues and convergence
+        w.Ueig = o;
+        o = align_up(o + (size_t)d->J * d->K * ts::kMaxRankM * ts::kMaxRankM * sizeof(float2), 256);
+        w.lam = o;
+        o = align_up(o + (size_t)d->J * d->K * ts::kMaxRankM * sizeof(float), 256);
+        w.conv = o;
+        o = align_up(o + (size_t)d->J * d->K, 256);
+      }
       if (ts::wide_core(d->P, d->p)) {
         w.Wserv = o;
         o = align_up(o + (size_t)d->J * d->K * d->p * sizeof(float2), 256);
@@ -589,6 +599,11 @@ int svd_precoders_impl(const ts_dims* d, const ts_coef* coef, const ts_c64* G, c
   a.fuse_serve = fuses_serve(d) ? 1 : 0;
   if (!a.fuse_serve) {
     a.Hserv = reinterpret_cast<float2*>(base + w.Hserv);
+    if (w.Ueig != 0) {
+      a.Ueig = reinterpret_cast<float2*>(base + w.Ueig);
+      a.lam_eig = reinterpret_cast<float*>(base + w.lam);
+      a.conv_eig = reinterpret_cast<uint8_t*>(base + w.conv);
+    }
     a.serv_stride = 1;
     if (w.Wserv != 0 && !identity) a.Wserv = reinterpret_cast<float2*>(base + w.Wserv);
     if (e == cudaSuccess) e = ts::launch_sinr_serving(a, s);

@@ -28,6 +28,10 @@ struct SinrArgs {
   int fuse_serve;                   // svd precoder forms H~_kk itself (Hserv unused)
   float2* Wserv;                    // wide cores: serving links' projections c* C,
                                     // [J][K][p] (workspace), or nullptr
+  float2* Ueig;                     // svd, two-phase precoder: Gram eigenvectors [J][K][MG][MG]
+                                    // (row a of U in row a) and
+  float* lam_eig;                   //   their eigenvalues [J][K][MG] (unit-trace Gram), and
+  uint8_t* conv_eig;                //   the Jacobi's convergence [J][K] (workspace)
   float2* Uout;                     // adjoint: left singular vectors [J][K][m][m] (or nullptr)
   float* Sout;                      // adjoint: singular values [J][K][m]
   float2* Vmout;                    // adjoint: right singular vectors [J][K][n][m]

@@ -298,7 +298,15 @@ __device__ __forceinline__ void serve_channels(const SinrArgs& A, const Precoder
   }
 }
 
-template <int MG, int LT>
+// PHASE 0: the whole precoder in one kernel.  PHASE 1 (serving channels
+// from the serving pass): Gram, Jacobi and Gram-Schmidt only, the Gram
+// accumulated over column chunks of H~ staged a chunk at a time, so that a
+// CTA holds little shared memory and many units hide the Jacobi's latency;
+// U and the eigenvalues go to workspace.  PHASE 2: the rest from the stored
+// U (W = U* H~, refinement, close pairs, V~, E_kk), with H~ staged whole.
+constexpr int kEigChunk = 16;   // columns of H~ per staged chunk in PHASE 1
+
+template <int MG, int LT, int PHASE>
 __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, const PrecoderPlan pl) {
   extern __shared__ __align__(16) float2 sm[];
   const int T = pl.T;
@@ -313,9 +321,38 @@ __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, con
   float2* Us = sm + pl.off_Us + g * MG * pl.SS;
   int* sel = reinterpret_cast<int*>(sm + pl.off_sel) + g * MG;
 
+  float2 S[MG], U[MG];
+  bool converged = false;
+  if (PHASE == 1) {
+    // Gram over column chunks: chunk [t][row][kEigChunk + 1] in the Hs region
+#pragma unroll
+    for (int b = 0; b < MG; ++b) S[b] = cz();
+    const int CS = kEigChunk + 1;
+    float2* ch = sm + pl.off_Hs;
+    for (int c0 = 0; c0 < n; c0 += kEigChunk) {
+      __syncthreads();                               // previous chunk consumed
+      for (int idx = tid; idx < T * MG * kEigChunk; idx += nth) {
+        const int c = idx % kEigChunk, aa = (idx / kEigChunk) % MG, t = idx / (kEigChunk * MG);
+        const int kk = kap0 + t;
+        float2 v = cz();
+        if (aa < m && kk < K && c0 + c < n)
+          v = A.Hserv[(((size_t)k * A.serv_stride * K + kk) * m + aa) * n + c0 + c];
+        ch[(t * MG + aa) * CS + c] = v;
+      }
+      __syncthreads();
+      const float2* cg = ch + g * MG * CS;
+#pragma unroll 4
+      for (int c = 0; c < kEigChunk; ++c) {
+        const float2 x = cg[a * CS + c];
+#pragma unroll
+        for (int b = 0; b < MG; ++b) cmacc(S[b], x, cg[b * CS + c]);
+      }
+    }
+  }
   // H~_kk rows of the T subcarriers (zero rows for a >= m and beyond K),
   // formed here or read from the all-link rebuild of the adjoint
-  if (A.fuse_serve) {
+  if (PHASE == 1) {
+  } else if (A.fuse_serve) {
     serve_channels<MG>(A, pl, k, kap0, sm);
   } else {
     for (int idx = tid; idx < T * MG * n; idx += nth) {
@@ -329,13 +366,11 @@ __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, con
   __syncthreads();
 
   // Gram S = H~ H~* (m x m, padded to MG with zero rows), row a in lane a
-  float2 S[MG], U[MG];
 #pragma unroll
-  for (int b = 0; b < MG; ++b) {
-    S[b] = cz();
-    U[b] = make_float2(b == a ? 1.f : 0.f, 0.f);
-  }
-  {
+  for (int b = 0; b < MG; ++b) U[b] = make_float2(b == a ? 1.f : 0.f, 0.f);
+  if (PHASE == 0) {
+#pragma unroll
+    for (int b = 0; b < MG; ++b) S[b] = cz();
     const float2* ha = Hs + a * pl.SH;
     for (int c = 0; c < n; ++c) {
       const float2 x = ha[c];
@@ -343,6 +378,7 @@ __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, con
       for (int b = 0; b < MG; ++b) cmacc(S[b], x, Hs[b * pl.SH + c]);
     }
   }
+  if (PHASE != 2) {
 
   // scale S to unit trace (eigenvectors and eigenvalue ratios are unchanged;
   // the singular values are taken from W below)
@@ -361,7 +397,7 @@ __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, con
   // Gram's own ~u / g.  The stopping decision is taken warp-wide (extra
   // sweeps leave a converged S unchanged).
   const int max_sweeps = MG <= 8 ? 11 : 13;
-  bool converged = false, polish = false;
+  bool polish = false;
   for (int sweep = 0;; ++sweep) {
     float off = 0.f, dia = 0.f;
 #pragma unroll
@@ -401,6 +437,27 @@ __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, con
         cms(U[b2], pr, U[b]);
       }
     }
+  }
+  }  // PHASE != 2
+  const size_t ueig = ((size_t)k * K + (kap < K ? kap : K - 1)) * MG;
+  if (PHASE == 1) {
+    // U (row a in lane a), the eigenvalues and the convergence to workspace
+    if (kap < K) {
+#pragma unroll
+      for (int b = 0; b < MG; ++b) A.Ueig[(ueig + a) * MG + b] = U[b];
+      A.lam_eig[ueig + a] = pick(S, a).x;
+      if (a == 0) A.conv_eig[(size_t)k * K + kap] = converged ? 1 : 0;
+    }
+    return;
+  }
+  if (PHASE == 2) {
+#pragma unroll
+    for (int b = 0; b < MG; ++b) {
+      U[b] = A.Ueig[(ueig + a) * MG + b];
+      S[b] = cz();
+    }
+    add_diag(S, a, A.lam_eig[ueig + a]);                     // only the diagonal is read below
+    converged = A.conv_eig[(size_t)k * K + (kap < K ? kap : K - 1)] != 0;
   }
   // The eigenvectors of the Gram are accurate unless a kept singular value is
   // small: refine with one-sided sweeps (below) when lambda_L < 1e-4 lambda_1
@@ -1313,7 +1370,25 @@ cudaError_t run_precoder(const SinrArgs& A, cudaStream_t s) {
   // serving channels too wide to stage per group (n up to 1024, read from
   // the serving pass's workspace): the shared-memory precoder
   if (smem > kSmemBudget) return fused ? cudaErrorInvalidValue : launch_precoder_staged(A, s);
-  auto kern = k_svd_precoder<MG, LT>;
+  if (!fused && A.Ueig != nullptr) {
+    // two phases: the eigensolve with little shared memory per CTA (many
+    // units resident), then the rest with H~ staged whole
+    const int T1 = kThreads / MG;
+    PrecoderPlan p1 = precoder_plan(MG, T1, kEigChunk, A.p, false);
+    p1.total = T1 * MG * (kEigChunk + 1);         // PHASE 1 uses the chunk region only
+    const size_t smem1 = (size_t)p1.total * sizeof(float2);
+    auto k1 = k_svd_precoder<MG, LT, 1>;
+    cudaError_t e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
+    if (e != cudaSuccess) return e;
+    k1<<<dim3((A.K + T1 - 1) / T1, A.J), T1 * MG, smem1, s>>>(A, p1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    auto k2 = k_svd_precoder<MG, LT, 2>;
+    if ((e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+      return e;
+    k2<<<dim3((A.K + T - 1) / T, A.J), T * MG, smem, s>>>(A, pl);
+    return cudaGetLastError();
+  }
+  auto kern = k_svd_precoder<MG, LT, 0>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((A.K + T - 1) / T, A.J);
