@@ -12,10 +12,12 @@ line (rank 0); the mid and precision workloads are reported in it too.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Under torchrun every rank evaluates its own independent system (weak
-scaling, no collective on the data path); the value is all ranks' SINRs
-divided by the slowest rank's time.  `--impl reference` times the FP64 CPU
-oracle on the same workload instead (rank 0 only).
+Under torchrun the ranks share one system of N times the subcarriers, G, C
+and the path coefficients replicated, and every rank evaluates its own
+range of K subcarriers (weak scaling, no collective on the data path); the
+value is all ranks' SINRs divided by the slowest rank's time.
+`--impl reference` times the FP64 CPU oracle on the same workload instead
+(rank 0 only).
 """
 from __future__ import annotations
 
@@ -280,10 +282,18 @@ class ClockSampler:
 
 
 # ------------------------------------------------------- multi-rank host logic
-def rank_workload(rank: int):
-    """Each rank evaluates its own independent system: the selected workload
-    with the seed offset by the rank (weak scaling, no data-path collective)."""
-    return synth.Workload(**{**WORKLOAD.__dict__, "seed": WORKLOAD.seed + rank})
+def partition_workload(world: int):
+    """The one system the ranks share: the selected workload with `world`
+    times its subcarriers.  Every rank holds its G, C and path coefficients
+    (replicated) and evaluates one contiguous range of WORKLOAD.K subcarriers
+    with the range entry points (weak scaling, no data-path collective)."""
+    return synth.Workload(**{**WORKLOAD.__dict__, "K": WORKLOAD.K * world})
+
+
+def rank_range(rank: int, world: int) -> tuple[int, int]:
+    """[k0, k1) of the shared system's subcarriers evaluated by `rank`."""
+    from paper_2401_09792_gb300 import partition
+    return partition.subcarrier_ranges(WORKLOAD.K * world, world)[rank]
 
 
 def max_over_ranks(x: float, world: int, device=None) -> float:
@@ -328,8 +338,12 @@ def run_ours(args):
     barrier()
     ts.load()
 
-    w = rank_workload(rank)
+    # this rank's view of the shared system: its K subcarriers from kappa0 on
+    w = WORKLOAD
+    kappa0, kappa1 = rank_range(rank, world)
+    d_all = ts.Dims.of(partition_workload(world))
     J, K, L, P = w.J, w.K, w.L, w.P
+    assert kappa1 - kappa0 == K
     tk = synth.direct_tucker(w)
     alpha, tau = synth.path_gains_delays(w)
     s2 = synth.noise_powers(w)
@@ -358,13 +372,23 @@ def run_ours(args):
     def step(e0=None, e1=None, e2=None, k0=None, k1=None):
         if e0 is not None:
             e0.record(stream)
-        ts.ts_svd_precoders(d, coef, dv["G"], dv["C"], ws, stream)
-        if e1 is not None:
-            e1.record(stream)
-        ts.ts_set_timing_events(k0, k1)
-        ts.ts_sinr_svd_from_precoders_prec(d, coef, dv["G"], dv["C"], dv["sigma2"], prec_id, sinr, flags,
-                                           ws, stream)
-        ts.ts_set_timing_events(None, None)
+        if world > 1:
+            # one range of the shared system (the precoder and link phases
+            # are one call here, so the phase split is not reported)
+            if e1 is not None:
+                e1.record(stream)
+            ts.ts_set_timing_events(k0, k1)
+            ts.ts_sinr_svd_range(d_all, kappa0, K, coef, dv["G"], dv["C"], dv["sigma2"], prec_id,
+                                 sinr, flags, ws, stream)
+            ts.ts_set_timing_events(None, None)
+        else:
+            ts.ts_svd_precoders(d, coef, dv["G"], dv["C"], ws, stream)
+            if e1 is not None:
+                e1.record(stream)
+            ts.ts_set_timing_events(k0, k1)
+            ts.ts_sinr_svd_from_precoders_prec(d, coef, dv["G"], dv["C"], dv["sigma2"], prec_id, sinr,
+                                               flags, ws, stream)
+            ts.ts_set_timing_events(None, None)
         if e2 is not None:
             e2.record(stream)
 
@@ -747,7 +771,9 @@ def _report(args, ts, torch, world, dev, w, tk, alpha, tau, s2, d, coef, dv, ws,
         "dtype": "f32" if args.precision == "fp32" else f"f32 + {args.precision} (tensor-core core contraction)",
         "data": "synthetic",
         "config": workload_config(w),
-        "parallelism": f"independent systems x{world}",
+        "parallelism": (f"subcarrier partition x{world}: one system of {world} x {w.K} subcarriers, "
+                        f"G, C and the path coefficients replicated, a range of {w.K} per rank"
+                        if world > 1 else "one GPU"),
         "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},

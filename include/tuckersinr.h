@@ -94,11 +94,17 @@ enum {
   TS_FLAG_EIG_UNCONVERGED = 8, /* the Jacobi eigensolver hit its sweep cap    */
   TS_FLAG_TIMEOUT = 16,       /* a bounded device wait of the tensor-core pass
                                  gave up; the unit's SINR is NaN             */
-  TS_FLAG_REFINED = 32        /* informational: the SINR comes from the
+  TS_FLAG_REFINED = 32,       /* informational: the SINR comes from the
                                  accurate re-evaluation (R in double-float,
                                  FP64-residual refinement of the solves):
                                  units above the refinement threshold, and
                                  every unit of more than 16 rows            */
+  TS_FLAG_PRECODER_REFINED = 64 /* informational (SVD precoders): a serving
+                                 link at this subcarrier had two adjacent
+                                 squared singular values among its L + 1
+                                 largest within 5e-3 of the largest, and its
+                                 precoder was recomputed in FP64 (with the
+                                 refinement threshold >= 0)                  */
 };
 
 /* Operations, for ts_workspace_bytes. */

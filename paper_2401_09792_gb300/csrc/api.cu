@@ -135,9 +135,8 @@ bool fuses_serve(const ts_dims* d) {
 
 // Workspace layout (byte offsets from the base, each 256-byte aligned).
 struct Workspace {
-  size_t turns = 0, V = 0, Hserv = 0, Wserv = 0, Ueig = 0, lam = 0, conv = 0, Eserv = 0, Eint = 0,
-         pflag = 0, F = 0, rlist = 0,
-         rcount = 0, total = 0;
+  size_t turns = 0, V = 0, Hserv = 0, Wserv = 0, Ueig = 0, lam = 0, conv = 0, Uclose = 0,
+         cmask = 0, Eserv = 0, Eint = 0, pflag = 0, F = 0, rlist = 0, rcount = 0, total = 0;
 };
 
 Workspace carve(const ts_dims* d, int op) {
@@ -172,6 +171,14 @@ Workspace carve(const ts_dims* d, int op) {
     }
     w.pflag = o;
     o = align_up(o + (size_t)d->J * d->K, 256);
+    if (d->m <= 16) {
+      // vectors of the units listed for the close-pair refinement
+      const int R = d->L + 1 < d->m ? d->L + 1 : d->m;
+      w.Uclose = o;
+      o = align_up(o + (size_t)d->J * d->K * R * d->m * sizeof(float2), 256);
+      w.cmask = o;
+      o = align_up(o + (size_t)d->J * d->K * sizeof(int), 256);
+    }
   } else {
     w.F = o;
     o = align_up(o + nch * d->p * d->m * d->L * sizeof(float2), 256);
@@ -608,7 +615,17 @@ int svd_precoders_impl(const ts_dims* d, const ts_coef* coef, const ts_c64* G, c
     if (w.Wserv != 0 && !identity) a.Wserv = reinterpret_cast<float2*>(base + w.Wserv);
     if (e == cudaSuccess) e = ts::launch_sinr_serving(a, s);
   }
+  // units with a close pair of singular values are listed by the precoder
+  // kernels and their precoders refined from H~ in double-float (off with
+  // the refinement)
+  a.list_close = a.refine_sens < INFINITY && w.Uclose != 0 ? 1 : 0;
+  if (a.list_close) {
+    a.Uclose = reinterpret_cast<float2*>(base + w.Uclose);
+    a.close_mask = reinterpret_cast<int*>(base + w.cmask);
+  }
+  if (e == cudaSuccess && a.list_close) e = cudaMemsetAsync(a.rcount, 0, sizeof(int), s);
   if (e == cudaSuccess) e = ts::launch_svd_precoder(a, s);
+  if (e == cudaSuccess && a.list_close) e = ts::launch_precoder_refine(a, s);
   return cuda_status(e);
 }
 

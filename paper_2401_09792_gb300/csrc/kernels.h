@@ -41,9 +41,15 @@ struct SinrArgs {
   const float* sigma2;              // [J]
   float* sinr;                      // [J][K][L]
   uint8_t* flags;                   // [J][K] or nullptr
-  int* rlist;                       // units (i K + kappa) to refine (workspace) or nullptr
+  int* rlist;                       // units (i K + kappa) to refine (workspace) or nullptr;
+                                    // in the precoder phase, units (k K + kappa) whose
+                                    // precoder is recomputed in FP64
   int* rcount;                      // length of rlist (workspace, zeroed before finalize)
   float refine_sens;                // refine units whose SINR sensitivity to R exceeds this
+  int list_close;                   // svd precoders: list units with a close pair (below)
+  float2* Uclose;                   // the listed units' left singular vectors of ranks
+                                    // 0 .. min(L + 1, m) - 1, [J*K][min(L+1,m)][m] (workspace)
+  int* close_mask;                  // and their close pairs, bit r for (r, r + 1) [J*K]
   // launch-shape choices (0: the default heuristics; set by the autotuner)
   int link_variant;                 // svd links: 1 blocked two-row kernel, 2 one-row kernel
   int precoder_split;               // precoder tile: subcarriers per CTA divided by 2^split
@@ -74,6 +80,21 @@ cudaError_t launch_sinr_links(const SinrArgs& a, bool svd, cudaStream_t s);
 cudaError_t launch_sinr_finalize(const SinrArgs& a, bool svd, cudaStream_t s);
 // FP64-residual refinement of the units the finalize kernel listed (refine.cu)
 cudaError_t launch_sinr_refine(const SinrArgs& a, bool svd, cudaStream_t s);
+
+// Close pairs of the SVD precoders.  Two adjacent eigenvalues lambda_r,
+// lambda_r+1 of the Gram H~ H~* (r < L, the first discarded one included)
+// less than kPolishWindow lambda_1 apart get one more rotation from their
+// rows of W = U* H~; less than kPrecoderCloseGap lambda_1 apart, the unit is
+// listed (when SinrArgs::list_close is set, m <= 16) with its vectors in
+// Uclose, and its precoder refined from H~ formed in double-float
+// (precoder_refine.cu).
+// Pairs whose smaller eigenvalue is below kPrecoderWeak lambda_1 are not
+// refined (their vectors' absolute FP32 error, not the pair's mixing, is
+// what limits such streams).
+constexpr float kPolishWindow = 0.15f;
+constexpr float kPrecoderCloseGap = 5e-3f;
+constexpr float kPrecoderWeak = 1e-2f;
+cudaError_t launch_precoder_refine(const SinrArgs& a, cudaStream_t s);
 
 // Buffers of the adjoint pipeline (adjoint.cu); Pt == nullptr selects SVD
 // precoders (read from SinrArgs::Vmout/Uout/Sout).

@@ -575,14 +575,18 @@ __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, con
     }
   }
 
-  // Close pairs.  Two eigenvalues of rank r and r + 1 (r < L) within 5% of
-  // lambda_1 of each other are mixed by the Gram's FP32 rounding by about
-  // u lambda_1 / (lambda_r - lambda_r+1) (up to ~5e-5 rad on the synthetic
-  // channels), and the per-stream SINRs follow that mixing (~0.5 per rad).
-  // Each such pair of rows of W is rotated once more, with the 2 x 2 Gram
-  // of the rows accumulated in double-float (the rotation angle then comes
-  // with FP32 relative accuracy), so that the mixing drops to the rounding
-  // of W itself.
+  // Close pairs.  Two eigenvalues of rank r and r + 1 (r < L) within
+  // kPolishWindow lambda_1 of each other are mixed by the Gram's FP32
+  // rounding by about u lambda_1 / (lambda_r - lambda_r+1), and the
+  // per-stream SINRs follow that mixing (~0.5 per rad; ~7 u lambda_1 / gap in
+  // the SINR without this step).  Each such pair of rows of W is rotated once
+  // more, with the 2 x 2 Gram of the rows accumulated in double-float (the
+  // rotation angle then comes with FP32 relative accuracy), so that the
+  // mixing drops to what the FP32 rounding of H~ itself leaves, ~0.4 u
+  // lambda_1 / gap in the SINR.  Pairs closer than kPrecoderCloseGap
+  // lambda_1 (where even that exceeds ~5e-6) list the unit for the FP64
+  // precoder.
+  int close_mask = 0;                       // bit r: the pair (r, r + 1) is close
   {
     const int gb = (threadIdx.x & 31) / MG * MG;            // group's first lane in the warp
     const unsigned gmask = MG == 32 ? FULL : ((1u << MG) - 1u) << gb;
@@ -591,7 +595,9 @@ __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, con
       const unsigned bq = __ballot_sync(FULL, a < m && erank == r + 1) & gmask;
       const int pp = bp ? __ffs(bp) - 1 - gb : 0, qq = bq ? __ffs(bq) - 1 - gb : 0;
       const float lp = __shfl_sync(FULL, lam, pp, MG), lq = __shfl_sync(FULL, lam, qq, MG);
-      const bool close = bp && bq && (lp - lq) < 5e-2f * lmax;
+      const bool close = bp && bq && (lp - lq) < kPolishWindow * lmax;
+      if (bp && bq && (lp - lq) < kPrecoderCloseGap * lmax && lq >= kPrecoderWeak * lmax)
+        close_mask |= 1 << r;
       if (!__any_sync(FULL, close)) continue;
       float alh = 0.f, all = 0.f, beh = 0.f, bel = 0.f;
       float2 gah = cz(), gal = cz();
@@ -693,6 +699,7 @@ __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, con
     if (a == 0)
       A.pflag[(size_t)k * K + kap] = (deficient ? TS_FLAG_RANK_DEFICIENT : 0) |
                                      ((converged || refined) ? 0 : TS_FLAG_EIG_UNCONVERGED);
+
     if (A.Uout != nullptr && a < m) {
       // the full SVD of H~_kk for the adjoint: lane a writes singular triplet a
       const int ia = sel[a];
@@ -703,6 +710,23 @@ __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, con
       for (int b = 0; b < m; ++b) A.Uout[(base * m + b) * m + a] = Us[b * pl.SS + ia];
       for (int c = 0; c < n; ++c)
         A.Vmout[(base * n + c) * m + a] = cscale(cconj(Hs[ia * pl.SH + c]), isg);
+    }
+  }
+  // a unit with a close pair: listed with its left singular vectors of ranks
+  // 0 .. min(L + 1, m) - 1 for the double-float refinement
+  {
+    const bool lst = close_mask != 0 && A.list_close && kap < K;
+    int pos = -1;
+    if (lst && a == 0) pos = atomicAdd(A.rcount, 1);
+    pos = __shfl_sync(FULL, pos, 0, MG);
+    if (lst && pos >= 0 && pos < A.J * K) {
+      const int R = min(L + 1, m);
+      if (a < m)
+        for (int r = 0; r < R; ++r) A.Uclose[((size_t)pos * R + r) * m + a] = Us[a * pl.SS + sel[r]];
+      if (a == 0) {
+        A.rlist[pos] = k * K + kap;
+        A.close_mask[pos] = close_mask;
+      }
     }
   }
 }

@@ -4,10 +4,11 @@
 // finalisation hold them in shared memory, one 128-thread CTA per unit; the
 // interfering and serving links run the wide-core kernel with 32 or 64 rows
 // per lane group (sinr_wide.cuh).  The arithmetic is the narrow kernels':
-//   k_svd_precoder_large  Gram S = H~_kk H~_kk* (eq. 23) scaled to unit
-//                         trace, cyclic Jacobi (round-robin pairs; each
-//                         rotation by one thread, its rows and columns by
-//                         lane j of every warp), V~ = conj(rows of U_L* H~)
+//   k_svd_precoder_large  Gram S = H~_kk H~_kk* (eq. 23) summed in
+//                         double-float and scaled to unit trace, cyclic
+//                         Jacobi (round-robin pairs; each rotation by one
+//                         thread, its rows and columns by lane j of every
+//                         warp), V~ = conj(rows of U_L* H~)
 //                         / sigma and E_kk = U_L Sigma_L (eq. 7, eq. 24);
 //   k_sinr_finalize_large R = sum_{k != i} E E* + sigma^2 I (eq. 25) in
 //                         double-float, Y = R^{-1} E_ii from its FP32
@@ -46,7 +47,8 @@ __host__ __device__ inline LargePrecPlan large_prec_plan(int m, int n, int L) {
   int o = 0;
   pl.off_S = o; o += m * pl.SD;
   pl.off_U = o; o += m * pl.SD;
-  pl.off_H = o; o += (m * 33 > L * n ? m * 33 : L * n);   // H~ column chunk, later W rows
+  const int Lw = L < m ? L + 1 : m;                         // W rows: the kept ones and the next
+  pl.off_H = o; o += (m * 33 > Lw * n ? m * 33 : Lw * n);  // H~ column chunk, later W rows
   pl.off_rot = o; o += pl.DE;                              // (c, s) and e per pair
   pl.off_pq = o; o += (2 * pl.DE + 2) / 2 + 1;             // ints: pairs, later the order
   pl.off_red = o; o += 20;                                 // 32 floats + a flag
@@ -71,10 +73,15 @@ __global__ void __launch_bounds__(kLargeThreads) k_svd_precoder_large(const Sinr
   float* red = reinterpret_cast<float*>(sm + pl.off_red);
   const float2* H = A.Hserv + ((size_t)k * A.serv_stride * K + kap) * m * n;   // [m][n]
 
-  // 1. Gram S = H~ H~* (lower triangle, mirrored), H~ staged 32 columns at a time
-  float2 acc[MAXE];
+  // 1. Gram S = H~ H~* (lower triangle, mirrored), H~ staged 32 columns at a
+  // time, accumulated in double-float (each product exact, the sums
+  // compensated) and rounded once: a plain FP32 sum over n columns carries
+  // ~sqrt(n) u ||S|| of rounding (n up to 1024 here), which mixes
+  // eigenvectors a relative gap g apart by that over g and moves the
+  // per-stream SINRs by up to ~1e-5; one rounding leaves ~u ||S||.
+  float2 acc[MAXE], acl[MAXE];
 #pragma unroll
-  for (int e = 0; e < MAXE; ++e) acc[e] = cz();
+  for (int e = 0; e < MAXE; ++e) acc[e] = acl[e] = cz();
   const int ntri = m * (m + 1) / 2;
   for (int c0 = 0; c0 < n; c0 += 32) {
     const int cc = min(32, n - c0);
@@ -93,7 +100,7 @@ __global__ void __launch_bounds__(kLargeThreads) k_svd_precoder_large(const Sinr
       while (a * (a + 1) / 2 > t) --a;
       while ((a + 1) * (a + 2) / 2 <= t) ++a;
       const int b = t - a * (a + 1) / 2;
-      for (int c = 0; c < cc; ++c) cmacc(acc[e], Hc[a * 33 + c], Hc[b * 33 + c]);
+      for (int c = 0; c < cc; ++c) df_cmacc(acc[e], acl[e], Hc[a * 33 + c], Hc[b * 33 + c]);
     }
   }
   __syncthreads();
@@ -105,8 +112,9 @@ __global__ void __launch_bounds__(kLargeThreads) k_svd_precoder_large(const Sinr
     while (a * (a + 1) / 2 > t) --a;
     while ((a + 1) * (a + 2) / 2 <= t) ++a;
     const int b = t - a * (a + 1) / 2;
-    S[a * SD + b] = acc[e];
-    S[b * SD + a] = a == b ? make_float2(acc[e].x, 0.f) : cconj(acc[e]);
+    const float2 v = make_float2(acc[e].x + acl[e].x, acc[e].y + acl[e].y);
+    S[a * SD + b] = v;
+    S[b * SD + a] = a == b ? make_float2(v.x, 0.f) : cconj(v);
   }
   for (int idx = tid; idx < m * m; idx += nth) {
     const int a = idx / m, b = idx - a * m;
@@ -254,11 +262,13 @@ __global__ void __launch_bounds__(kLargeThreads) k_svd_precoder_large(const Sinr
   }
   __syncthreads();
 
-  // The kept columns, in rank order, orthonormalised against each other by
-  // warp 0 (modified Gram-Schmidt, lanes over the rows): the close-pair
-  // rotation below would amplify their mutual defect by lambda / gap.
+  // The kept columns and the next one (Lw of them), in rank order,
+  // orthonormalised against each other by warp 0 (modified Gram-Schmidt,
+  // lanes over the rows): the close-pair rotation below would amplify their
+  // mutual defect by lambda / gap.
+  const int Lw = L < m ? L + 1 : m;
   if (warp == 0) {
-    for (int r = 0; r < L; ++r) {
+    for (int r = 0; r < Lw; ++r) {
       const int cr = pq[r];
       for (int r2 = 0; r2 < r; ++r2) {
         const int c2 = pq[r2];
@@ -283,9 +293,9 @@ __global__ void __launch_bounds__(kLargeThreads) k_svd_precoder_large(const Sinr
   }
   __syncthreads();
 
-  // 4. W rows r < L: W[r][c] = sum_b conj(U[b][idx_r]) H~[b][c] (reuses Hc)
+  // 4. W rows r < Lw: W[r][c] = sum_b conj(U[b][idx_r]) H~[b][c] (reuses Hc)
   float2* W = Hc;
-  for (int idx = tid; idx < L * n; idx += nth) {
+  for (int idx = tid; idx < Lw * n; idx += nth) {
     const int r = idx / n, c = idx - r * n;
     const int col = pq[r];
     float2 v = cz();
@@ -293,15 +303,26 @@ __global__ void __launch_bounds__(kLargeThreads) k_svd_precoder_large(const Sinr
     W[r * n + c] = v;
   }
   __syncthreads();
-  // Close pairs among the kept vectors (eigenvalues of rank r and r + 1
-  // within 5% of lambda_1): the rows of W are rotated once more from their
-  // 2 x 2 Gram accumulated in double-float, as in the register precoder, by
-  // warp 0 (lanes over the columns of W and the rows of U).
+  // Close pairs among the kept vectors and the first discarded one
+  // (eigenvalues of rank r and r + 1 within kPolishWindow lambda_1): the
+  // rows of W are rotated once more from their 2 x 2 Gram accumulated in
+  // double-float, as in the register precoder, by warp 0 (lanes over the
+  // columns of W and the rows of U).
+  // With at most 16 rows, pairs closer than kPrecoderCloseGap lambda_1, the
+  // first discarded eigenvalue included, list the unit (with its vectors of
+  // ranks 0 .. min(L + 1, m) - 1, after this step) for the double-float
+  // refinement.
   if (warp == 0) {
     const float lmax = S[pq[0] * SD + pq[0]].x;
-    for (int r = 0; r + 1 < L; ++r) {
+    int close_mask = 0;                     // bit r: the pair (r, r + 1) is close
+    if (A.list_close && m <= 16)
+      for (int r = 0; r < L && r + 1 < m; ++r) {
+        const float lr = S[pq[r] * SD + pq[r]].x, ls = S[pq[r + 1] * SD + pq[r + 1]].x;
+        if (lr - ls < kPrecoderCloseGap * lmax && ls >= kPrecoderWeak * lmax) close_mask |= 1 << r;
+      }
+    for (int r = 0; r + 1 < Lw; ++r) {
       const int cp = pq[r], cq = pq[r + 1];
-      if (!(S[cp * SD + cp].x - S[cq * SD + cq].x < 5e-2f * lmax)) continue;
+      if (!(S[cp * SD + cp].x - S[cq * SD + cq].x < kPolishWindow * lmax)) continue;
       float alh = 0.f, all = 0.f, beh = 0.f, bel = 0.f;
       float2 gah = cz(), gal = cz();
       for (int c = lane; c < n; c += 32) {
@@ -347,6 +368,20 @@ __global__ void __launch_bounds__(kLargeThreads) k_svd_precoder_large(const Sinr
         }
       }
       __syncwarp();
+    }
+    int pos = -1;
+    if (close_mask != 0 && lane == 0) pos = atomicAdd(A.rcount, 1);
+    pos = __shfl_sync(FULL, pos, 0);
+    if (pos >= 0 && pos < A.J * K) {
+      const int R = min(L + 1, m);
+      for (int i2 = lane; i2 < R * m; i2 += 32) {
+        const int r = i2 / m, a = i2 - r * m;
+        A.Uclose[((size_t)pos * R + r) * m + a] = U[a * SD + pq[r]];
+      }
+      if (lane == 0) {
+        A.rlist[pos] = k * K + kap;
+        A.close_mask[pos] = close_mask;
+      }
     }
   }
   __syncthreads();

@@ -30,7 +30,9 @@ TS_PREC_FP32, TS_PREC_TF32, TS_PREC_BF16X2, TS_PREC_TF32X3 = 0, 1, 2, 3
 TS_FLAG_NOT_PD, TS_FLAG_NONFINITE, TS_FLAG_RANK_DEFICIENT, TS_FLAG_EIG_UNCONVERGED = 1, 2, 4, 8
 TS_FLAG_TIMEOUT = 16
 TS_FLAG_REFINED = 32
-TS_FLAG_ERRORS = 0xFF & ~TS_FLAG_REFINED     # bits that report a problem (REFINED is informational)
+TS_FLAG_PRECODER_REFINED = 64
+# bits that report a problem (the two REFINED bits are informational)
+TS_FLAG_ERRORS = 0xFF & ~(TS_FLAG_REFINED | TS_FLAG_PRECODER_REFINED)
 
 
 class TsError(RuntimeError):

@@ -1,7 +1,8 @@
 """Host logic of bench.py's multi-rank path (one process per GPU, weak
 scaling), run as two gloo ranks on the CPU: every rank gets the slowest
-rank's time, the whole-job value counts all ranks' units, each rank draws its
-own system, and the reference arm runs on rank 0 only."""
+rank's time, the whole-job value counts all ranks' units, the ranks share
+one system (same draws) and evaluate disjoint subcarrier ranges that cover
+it, and the reference arm runs on rank 0 only."""
 import os
 import subprocess
 import sys
@@ -25,10 +26,11 @@ def _worker(rank, world, port, out):
     try:
         local_ms = 10.0 + 7.5 * rank
         slowest = bench.max_over_ranks(local_ms, world)
-        w = bench.rank_workload(rank)
+        w = bench.partition_workload(world)
         alpha, _ = synth.path_gains_delays(w)
-        out.put((rank, slowest, w.seed, complex(alpha.ravel()[0]),
-                 bench.whole_job_value(world, w.J * w.K, 3, slowest)))
+        k0, k1 = bench.rank_range(rank, world)
+        out.put((rank, slowest, (k0, k1, w.K), complex(alpha.ravel()[0]),
+                 bench.whole_job_value(world, k1 - k0, 3, slowest)))
     finally:
         dist.destroy_process_group()
 
@@ -40,7 +42,7 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def test_two_gloo_ranks_max_time_and_independent_systems():
+def test_two_gloo_ranks_max_time_and_subcarrier_partition():
     world = 2
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
@@ -52,13 +54,15 @@ def test_two_gloo_ranks_max_time_and_independent_systems():
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    (r0, t0, s0, a0, v0), (r1, t1, s1, a1, v1) = res
+    (r0, t0, g0, a0, v0), (r1, t1, g1, a1, v1) = res
     assert (r0, r1) == (0, 1)
     assert t0 == t1 == 17.5                       # both ranks see the slowest rank's time
-    assert s0 != s1 and a0 != a1                  # independent systems per rank
+    assert a0 == a1                               # one shared system
     import bench
     w = bench.WORKLOAD
-    assert v0 == v1 == pytest.approx(2 * w.J * w.K * 3 / 17.5e-3)
+    # disjoint ranges of WORKLOAD.K subcarriers covering the shared 2 K
+    assert g0 == (0, w.K, 2 * w.K) and g1 == (w.K, 2 * w.K, 2 * w.K)
+    assert v0 == v1 == pytest.approx(2 * w.K * 3 / 17.5e-3)
 
 
 def test_single_rank_is_identity():
