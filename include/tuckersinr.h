@@ -332,8 +332,10 @@ typedef struct {
 
 typedef struct ts_batch_plan ts_batch_plan;   /* opaque */
 
-/* Device workspace for the whole batch: each instance's ts_workspace_bytes,
- * 256-byte aligned, back to back.  0 if an instance is invalid. */
+/* Device workspace for the whole batch: four slots, 256-byte aligned, back
+ * to back; slot b is as large as the largest ts_workspace_bytes of the
+ * instances j with j % 4 == b, which run one after the other on graph
+ * branch b and share it.  0 if an instance is invalid. */
 size_t ts_batch_workspace_bytes(const ts_instance* inst, int n);
 
 /* Options of ts_batch_plan_create. */

@@ -2,7 +2,8 @@
 // planner checks every instance, optionally autotunes the launch shapes of
 // each new shape class, and captures all instances' kernels into one CUDA
 // graph (instances spread over four parallel branches, so that small systems
-// overlap); ts_batch_launch replays it with one graph launch.
+// overlap; the instances of a branch share its workspace slot);
+// ts_batch_launch replays it with one graph launch.
 //
 // Autotuning knobs (SinrArgs): the interfering-link kernel of the FP32 SVD
 // path (two rows x two subcarriers per lane, or one row per lane) and the
@@ -44,6 +45,27 @@ int ws_op(const ts_instance& x) {
 }
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Workspace slots: instance j runs on branch j % kBranches, and the instances
+// of one branch run one after the other, so they share that branch's slot
+// (each call writes every byte of scratch it reads before reading it).
+// slot[b] = offset of branch b's slot; returns the total, 0 if an instance
+// is invalid.
+size_t slot_layout(const ts_instance* inst, int n, size_t* slot, size_t* slot_bytes) {
+  size_t need[kBranches] = {};
+  for (int j = 0; j < n; ++j) {
+    const size_t b = ts_workspace_bytes(&inst[j].d, ws_op(inst[j]));
+    if (b == 0) return 0;
+    if (b > need[j % kBranches]) need[j % kBranches] = b;
+  }
+  size_t o = 0;
+  for (int b = 0; b < kBranches; ++b) {
+    slot[b] = o;
+    slot_bytes[b] = need[b];
+    o += align256(need[b]);
+  }
+  return o;
+}
 
 std::string class_key(const ts_instance& x) {
   char buf[160];
@@ -147,12 +169,10 @@ extern "C" {
 
 size_t ts_batch_workspace_bytes(const ts_instance* inst, int n) {
   if (inst == nullptr || n < 1) return 0;
-  size_t total = 0;
-  for (int j = 0; j < n; ++j) {
+  for (int j = 0; j < n; ++j)
     if (check_instance(inst[j]) != TS_OK) return 0;
-    total += align256(ts_workspace_bytes(&inst[j].d, ws_op(inst[j])));
-  }
-  return total;
+  size_t slot[kBranches], slot_bytes[kBranches];
+  return slot_layout(inst, n, slot, slot_bytes);
 }
 
 int ts_batch_plan_create(const ts_instance* inst, int n, void* ws, size_t ws_bytes, int options,
@@ -160,14 +180,16 @@ int ts_batch_plan_create(const ts_instance* inst, int n, void* ws, size_t ws_byt
   if (plan == nullptr || inst == nullptr || ws == nullptr) return TS_ERR_NULL;
   *plan = nullptr;
   if (n < 1) return TS_ERR_DIMS;
-  std::vector<size_t> off(n), bytes(n);
-  size_t o = 0;
   for (int j = 0; j < n; ++j) {
     const int st = check_instance(inst[j]);
     if (st != TS_OK) return st;
-    bytes[j] = ts_workspace_bytes(&inst[j].d, ws_op(inst[j]));
-    off[j] = o;
-    o += align256(bytes[j]);
+  }
+  size_t slot[kBranches], slot_bytes[kBranches];
+  const size_t o = slot_layout(inst, n, slot, slot_bytes);
+  std::vector<size_t> off(n), bytes(n);
+  for (int j = 0; j < n; ++j) {
+    off[j] = slot[j % kBranches];
+    bytes[j] = slot_bytes[j % kBranches];
   }
   if (ws_bytes < o) return TS_ERR_WORKSPACE;
   if (((uintptr_t)ws & 255u) != 0) return TS_ERR_ALIGN;

@@ -1058,7 +1058,9 @@ __device__ __forceinline__ bool sinr_core(float2 (&R)[MG], const float2 (&Eself)
 // addresses, so reuse has to happen in registers).  128 threads, T = 512/MG
 // subcarriers per CTA, column chunks of NC = 4.  Path-form coefficients are
 // evaluated inside the projection, so only dense coefficients are staged.
-template <int MG, int LT>
+// SERVE: the serving links instead (grid z = 1), writing the rows of H~_kk
+// to workspace for the precoder (no precoders, no E).
+template <int MG, int LT, bool SERVE>
 __global__ void __launch_bounds__(kThreads) k_sinr_link_blk(const SinrArgs A, const LinkPlan pl) {
   constexpr int NC = 4;
   constexpr int GL = MG / 2;
@@ -1071,7 +1073,7 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link_blk(const SinrArgs A, co
   const int i = blockIdx.y, z = blockIdx.z;
   const int kap0 = blockIdx.x * T;
   const int J = A.J, m = A.m, n = A.n, p = A.p, L = A.L, K = A.K, P = A.P;
-  const int k = z < i ? z : z + 1;
+  const int k = SERVE ? i : (z < i ? z : z + 1);
   const int ch = i * J + k;
   const int nchunk = (n + NC - 1) / NC;
   float2* Cs = sm + pl.off_Cs;
@@ -1080,7 +1082,7 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link_blk(const SinrArgs A, co
   float2* stage0 = sm + pl.off_stage;
   const bool wide = pl.wide != 0;
   // the refinement list of the finalize kernel that follows starts empty
-  if (A.rcount != nullptr && tid == 0 && blockIdx.x == 0 && i == 0 && z == 0) *A.rcount = 0;
+  if (!SERVE && A.rcount != nullptr && tid == 0 && blockIdx.x == 0 && i == 0 && z == 0) *A.rcount = 0;
 
   auto issue_chunk = [&](int cidx) {
     float2* buf = stage0 + (cidx & 1) * pl.stage;
@@ -1096,6 +1098,7 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link_blk(const SinrArgs A, co
       const int dstep = (kThreads / GU) * MG * pl.SG;
       for (int q = tid / GU; q < p; q += kThreads / GU, src += sstep, dst += dstep)
         cp_async16(dst, rowok ? src : A.G, rowok);
+      if (SERVE) return;
       constexpr int VU = NC * LT / 2;
       const int l = 2 * (tid % (LT / 2)), vc = (tid / (LT / 2)) % NC;
       const bool colok = c0 + vc < n && l < L;
@@ -1113,6 +1116,7 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link_blk(const SinrArgs A, co
       cp_async8(buf + pl.off_Gs + (q * MG + aa) * pl.SG + cc,
                 ok ? Gch + ((size_t)q * m + aa) * n + c : A.G, ok);
     }
+    if (SERVE) return;
     for (int idx = tid; idx < T * NC * LT; idx += kThreads) {
       const int l = idx % LT, cc = (idx / LT) % NC, t = idx / (LT * NC);
       const int kk2 = kap0 + t, c = c0 + cc;
@@ -1233,6 +1237,25 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link_blk(const SinrArgs A, co
         cmac(h[1][1][2 * c2 + 1], wb, v1);
       }
     }
+    if (SERVE) {
+      // rows j and j + GL of H~_kk for both subcarriers, NC columns each
+      const int c0 = cidx * NC;
+#pragma unroll
+      for (int x = 0; x < 2; ++x) {
+        const int kap = kap0 + 2 * gp + x;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const int a = j + r * GL;
+          if (kap >= K || a >= m) continue;
+          float2* Hrow = A.Hserv + (((size_t)i * K + kap) * m + a) * n;
+#pragma unroll
+          for (int cc = 0; cc < NC; ++cc)
+            if (c0 + cc < n) Hrow[c0 + cc] = h[x][r][cc];
+        }
+      }
+      __syncthreads();   // this buffer is refilled two chunks later
+      continue;
+    }
     const float2* va = buf + pl.off_Vs + (2 * gp) * pl.SV;
     const float2* vb = va + pl.SV;
 #pragma unroll
@@ -1255,6 +1278,7 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link_blk(const SinrArgs A, co
     __syncthreads();   // this buffer is refilled two chunks later
   }
   cp_async_wait<0>();
+  if (SERVE) return;
 
   // rows j and j + GL of the interfering effective channel E_ik (eq. 24) for
   // both subcarriers; the finalisation forms the covariance of eq. (25)
@@ -1444,12 +1468,12 @@ cudaError_t launch_link_mode(const SinrArgs& A, int nz, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int MG, int LT>
+template <int MG, int LT, bool SERVE = false>
 cudaError_t launch_link_blocked(const SinrArgs& A, cudaStream_t s) {
   constexpr int NC = 4;
   constexpr int T = 2 * kThreads / (MG / 2);
-  if (A.J < 2) return cudaSuccess;
-  LinkPlan pl = link_plan(MG, LT, T, NC, A.P, A.p, kModeSvd);
+  if (!SERVE && A.J < 2) return cudaSuccess;
+  LinkPlan pl = link_plan(MG, LT, T, NC, A.P, A.p, SERVE ? kModeServe : kModeSvd);
   // the coefficient tile is only staged for dense coefficients
   if (A.coef_mode != 0) {
     const int shrink = T * A.P;
@@ -1462,11 +1486,13 @@ cudaError_t launch_link_blocked(const SinrArgs& A, cudaStream_t s) {
   if (es > 2 * pl.stage) pl.total += es - 2 * pl.stage;
   const size_t smem = (size_t)pl.total * sizeof(float2);
   // large dense coefficient tiles: the unblocked kernel shrinks its tile
-  if (smem > kSmemBudget) return launch_link_mode<MG, LT, kModeSvd>(A, A.J - 1, s);
+  if (smem > kSmemBudget)
+    return SERVE ? launch_link_mode<MG, LT, kModeServe>(A, 1, s)
+                 : launch_link_mode<MG, LT, kModeSvd>(A, A.J - 1, s);
   pl.wide = (A.n % 2 == 0) && (A.L % 2 == 0) && LT >= 2 && (((uintptr_t)A.G & 15u) == 0) &&
-            (((uintptr_t)A.V & 15u) == 0);
-  dim3 grid((A.K + T - 1) / T, A.J, A.J - 1);
-  auto kern = k_sinr_link_blk<MG, LT>;
+            (SERVE || ((uintptr_t)A.V & 15u) == 0);
+  dim3 grid((A.K + T - 1) / T, A.J, SERVE ? 1 : A.J - 1);
+  auto kern = k_sinr_link_blk<MG, LT, SERVE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, kThreads, smem, s>>>(A, pl);
@@ -1499,6 +1525,8 @@ cudaError_t run_links(const SinrArgs& A, bool svd, cudaStream_t s) {
 template <int MG, int LT>
 cudaError_t run_serving(const SinrArgs& A, cudaStream_t s) {
   if (wide_core(A.P, A.p)) return launch_link_wide<(MG <= 8 ? 8 : 16), LT, true>(A, s);
+  if (MG >= 4 && A.p <= 32 && A.link_variant != 2)
+    return launch_link_blocked<(MG >= 4 ? MG : 4), LT, true>(A, s);
   return launch_link_mode<MG, LT, kModeServe>(A, 1, s);
 }
 

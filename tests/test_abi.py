@@ -151,7 +151,13 @@ def test_batch_workspace_and_checks_before_launch(lib, tmp_path):
     arr = (ts.ts_instance * 2)(*good)
     total = lib.ts_batch_workspace_bytes(arr, 2)
     each = [lib.ts_workspace_bytes(ctypes.byref(x.d), 0) for x in good]
-    assert total == sum((b + 255) // 256 * 256 for b in each)
+    assert total == sum((b + 255) // 256 * 256 for b in each)      # two branches, one each
+    # instances j and j + 4 share branch j's slot: its size is their maximum
+    six = [_instance(ts, K=10 + 20 * j) for j in range(6)]
+    arr6 = (ts.ts_instance * 6)(*six)
+    b6 = [lib.ts_workspace_bytes(ctypes.byref(x.d), 0) for x in six]
+    slots = [max(b6[j] for j in range(6) if j % 4 == b) for b in range(4)]
+    assert lib.ts_batch_workspace_bytes(arr6, 6) == sum((b + 255) // 256 * 256 for b in slots)
     bad = (ts.ts_instance * 2)(good[0], _instance(ts, m=5))
     assert lib.ts_batch_workspace_bytes(bad, 2) == 0
     h = ctypes.c_void_p()
