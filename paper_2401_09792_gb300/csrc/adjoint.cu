@@ -109,9 +109,9 @@ __global__ void __launch_bounds__(kThreads) k_adj_units(const SinrArgs A, const 
     }
   }
   add_diag(R, a, a < m ? A.sigma2[i] : 1.f);
-  float2 Lq[MG], Y[LT];
+  float2 Lq[MG], Y[LT], Zr[LT];
   float as[LT], xs[LT];
-  const bool ok = sinr_core<MG, LT>(R, Eself, Es, a, Lq, Y, as, xs);
+  const bool ok = sinr_core<MG, LT>(R, Eself, Es, a, Lq, Y, as, xs, Zr);
   trsv_rows_conjT<MG, MG, LT>(Lq, Y, a);       // Y = Q~^{-1} E_ii
   float gam[LT];
 #pragma unroll

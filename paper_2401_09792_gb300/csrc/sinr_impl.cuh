@@ -187,6 +187,106 @@ __device__ __forceinline__ void jacobi_step(const int t, float2 (&S)[MG], float2
   }
 }
 
+// The same sweep for 16 rows in a "conveyor" ordering whose code does not
+// depend on the step.  Register slot s of every lane holds column
+// cv_col(s, t) at step t, and the pairs of step t are the columns in slots
+// (2j, 2j + 1); after each step the slot contents move one place along the
+// 15-cycle of slots other than slot 1 (a circle-method round robin: every
+// pair of columns meets once in 15 steps).  Three steps are unrolled, their
+// pair slots fixed at compile time relative to the layout at the start of
+// the three, which is then rotated in registers; the whole sweep is a loop
+// of five such bodies (15 unrolled steps would not fit the instruction
+// cache).  Slots and columns coincide at the start of every sweep.
+__host__ __device__ constexpr int cv_cyc(int k) { return k == 0 ? 0 : k <= 7 ? 2 * k + 1 : 2 * (15 - k); }
+__host__ __device__ constexpr int cv_pos(int s) { return s == 0 ? 0 : (s & 1) ? (s - 1) / 2 : 15 - s / 2; }
+__host__ __device__ constexpr int cv_col(int s, int t) {
+  return s == 1 ? 1 : cv_cyc(((cv_pos(s) - t) % 15 + 15) % 15);
+}
+__host__ __device__ constexpr int cv_slot(int c, int t) { return c == 1 ? 1 : cv_cyc((cv_pos(c) + t) % 15); }
+
+template <int TT>
+__device__ __forceinline__ void conveyor_step16(const int t0, float2 (&S)[16], float2 (&U)[16],
+                                                float& dg, int a) {
+  constexpr int MG = 16;
+  const int t = t0 + TT;
+  const int sa = cv_slot(a, t);
+  const int b = cv_col(sa ^ 1, t);                // partner row
+  const bool is_p = (sa & 1) == 0;
+  const float d_other = __shfl_sync(FULL, dg, b, MG);
+  const float2 mine = pick(S, cv_slot(b, t0));    // S_ab in the layout of step t0
+  const float2 theirs = gshfl<MG>(mine, b);
+  const float app = is_p ? dg : d_other, aqq = is_p ? d_other : dg;
+  const float2 bpq = is_p ? mine : theirs;
+  const float ab2 = cabs2(bpq);
+  float c = 1.f;
+  float2 se = cz();                        // s e^{i phi}
+  if (ab2 > 1e-36f && ab2 > 1e-18f * fabsf(app * aqq)) {
+    const float r = rsqrtf(ab2);           // 1 / |b|
+    const float tau = 0.5f * (aqq - app) * r;
+    const float at = fabsf(tau);
+    const float h = fmaf(tau, tau, 1.f);
+    const float tm = at > 1e15f ? __fdividef(0.5f, at) : __fdividef(1.f, at + h * rsqrtf(h));
+    const float tt = copysignf(tm, tau);
+    c = rsqrtf(fmaf(tt, tt, 1.f));
+    se = cscale(bpq, tt * c * r);
+    const float tb = tt * (ab2 * r);
+    dg = is_p ? app - tb : aqq + tb;
+  }
+  {
+    const float2 f = is_p ? make_float2(-se.x, -se.y) : cconj(se);
+#pragma unroll
+    for (int k = 0; k < MG; ++k) {
+      const float2 other = gshfl<MG>(S[k], b);
+      float2 v = cscale(S[k], c);
+      cmac(v, f, other);
+      S[k] = v;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < MG / 2; ++j) {
+    const int ps = cv_col(2 * j, TT), qs = cv_col(2 * j + 1, TT);   // slots (compile time)
+    const int src = cv_col(2 * j, t);                                // lane p of the pair
+    const float cj = __shfl_sync(FULL, c, src, MG);
+    const float2 se_j = gshfl<MG>(se, src), sec_j = cconj(se_j);
+    {
+      const float2 x = S[ps], y = S[qs];
+      float2 nx = cscale(x, cj), ny = cscale(y, cj);
+      cms(nx, sec_j, y);
+      cmac(ny, se_j, x);
+      S[ps] = nx;
+      S[qs] = ny;
+    }
+    {
+      const float2 x = U[ps], y = U[qs];
+      float2 nx = cscale(x, cj), ny = cscale(y, cj);
+      cms(nx, sec_j, y);
+      cmac(ny, se_j, x);
+      U[ps] = nx;
+      U[qs] = ny;
+    }
+  }
+}
+
+// slot contents three places along the conveyor cycle (slot 1 stays)
+__device__ __forceinline__ void conveyor_rotate3(float2 (&X)[16]) {
+  float2 tmp[16];
+#pragma unroll
+  for (int s = 0; s < 16; ++s) tmp[s] = X[s];
+#pragma unroll
+  for (int k = 0; k < 15; ++k) X[cv_cyc((k + 3) % 15)] = tmp[cv_cyc(k)];
+}
+
+__device__ __forceinline__ void jacobi_sweep16(float2 (&S)[16], float2 (&U)[16], float& dg, int a) {
+#pragma unroll 1
+  for (int t0 = 0; t0 < 15; t0 += 3) {
+    conveyor_step16<0>(t0, S, U, dg, a);
+    conveyor_step16<1>(t0, S, U, dg, a);
+    conveyor_step16<2>(t0, S, U, dg, a);
+    conveyor_rotate3(S);
+    conveyor_rotate3(U);
+  }
+}
+
 // ------------------------------------------------------------------ phase 1
 // k_svd_precoder: one group of MG lanes per (BS k, subcarrier).  Forms the
 // serving link's compressed channel H~_kk (or reads it from workspace: large
@@ -412,8 +512,12 @@ __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, con
     if ((all && polish) || sweep == max_sweeps) break;
     polish = all;
     float dg = pick(S, a).x;
+    if constexpr (MG == 16) {
+      jacobi_sweep16(S, U, dg, a);
+    } else {
 #pragma unroll
-    for (int t = 0; t < MG - 1; ++t) jacobi_step<MG>(t, S, U, dg, a);
+      for (int t = 0; t < MG - 1; ++t) jacobi_step<MG>(t, S, U, dg, a);
+    }
   }
   // The rotations come from hardware reciprocal square roots and each is
   // applied in FP32, so U leaves the sweeps unitary only to ~1e-7 .. 1e-6:
@@ -995,13 +1099,14 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link(const SinrArgs A, const 
 // is needed (forward and adjoint).  With Q~ = R + E_ii E_ii* (eq. 25):
 //   a_r = e_r* Q~^{-1} e_r = |L_Q^{-1} e_r|^2   (as[r], every lane)
 //   x_r = [(I + Z*Z)^{-1}]_rr, Z = L_R^{-1} E_ii   (xs[r], every lane)
-// and SINR_r = a_r / x_r (eq. 5).  Returns Lq = chol(Q~) row a and
-// Zq = L_Q^{-1} E_ii row a; false if a factorisation failed.  R is destroyed
+// and SINR_r = a_r / x_r (eq. 5).  Returns Lq = chol(Q~) row a,
+// Zq = L_Q^{-1} E_ii row a and Z = L_R^{-1} E_ii row a; false if a
+// factorisation failed.  R is destroyed
 // (it holds chol(R) on return); Es is the group's MG x LT shared scratch.
 template <int MG, int LT>
 __device__ __forceinline__ bool sinr_core(float2 (&R)[MG], const float2 (&Eself)[LT], float2* Es,
                                           int a, float2 (&Lq)[MG], float2 (&Zq)[LT],
-                                          float (&as)[LT], float (&xs)[LT]) {
+                                          float (&as)[LT], float (&xs)[LT], float2 (&Z)[LT]) {
   // Q~ = R + E_ii E_ii*
 #pragma unroll
   for (int l = 0; l < LT; ++l) Es[a * LT + l] = Eself[l];
@@ -1016,7 +1121,6 @@ __device__ __forceinline__ bool sinr_core(float2 (&R)[MG], const float2 (&Eself)
 
   bool ok = chol_rows<MG, MG>(R, a);
   ok = chol_rows<MG, MG>(Lq, a) && ok;
-  float2 Z[LT];
 #pragma unroll
   for (int l = 0; l < LT; ++l) Z[l] = Zq[l] = Eself[l];
   trsv_rows<MG, MG, LT>(R, Z, a);
@@ -1347,9 +1451,9 @@ __global__ void __launch_bounds__(kThreads) k_sinr_finalize(const SinrArgs A, in
   float Ra2[MG];                                  // |R_ab|^2, for the listing below
 #pragma unroll
   for (int b = 0; b < MG; ++b) Ra2[b] = (a < m && b < m) ? cabs2(R[b]) : 0.f;
-  float2 Lq[MG], Zq[LT];
+  float2 Lq[MG], Zq[LT], Zr[LT];
   float as[LT], xs[LT];
-  const bool ok = sinr_core<MG, LT>(R, Eself, Es, a, Lq, Zq, as, xs);
+  const bool ok = sinr_core<MG, LT>(R, Eself, Es, a, Lq, Zq, as, xs, Zr);
   // Units whose SINRs are sensitive to the FP32 rounding of R are listed for
   // the refinement pass.  To first order SINR_r moves with y_r* dR y_r, where
   // y_r = R^{-1} e_r and e_r* y_r is its scale; the rounding of R perturbs
@@ -1362,9 +1466,8 @@ __global__ void __launch_bounds__(kThreads) k_sinr_finalize(const SinrArgs A, in
   if (A.rlist != nullptr) {
     float2 Y[LT];
 #pragma unroll
-    for (int l = 0; l < LT; ++l) Y[l] = Eself[l];
-    trsv_rows<MG, MG, LT>(R, Y, a);                 // R holds chol(R) here
-    trsv_rows_conjT<MG, MG, LT>(R, Y, a);           // Y = R^{-1} E_ii
+    for (int l = 0; l < LT; ++l) Y[l] = Zr[l];      // L_R^{-1} E_ii from sinr_core
+    trsv_rows_conjT<MG, MG, LT>(R, Y, a);           // Y = R^{-1} E_ii (R holds chol(R) here)
     float sens = 0.f;
 #pragma unroll
     for (int l = 0; l < LT; ++l) {
