@@ -186,6 +186,8 @@ KERNEL_SOURCES = {
     "k_sinr_link_wide": ("sinr_wide.cuh", "sinr_impl.cuh", "common.cuh", "kernels.h"),
     "k_sinr_link_tc_tf32": ("sinr_tc.cu", "common.cuh", "kernels.h"),
     "k_sinr_link_tc_bf16x2": ("sinr_tc.cu", "common.cuh", "kernels.h"),
+    "k_sinr_link_tc_tf32x3": ("sinr_tc.cu", "common.cuh", "kernels.h"),
+    "k_precoder_refine": ("precoder_refine.cu", "common.cuh", "kernels.h"),
 }
 
 
@@ -1548,8 +1550,8 @@ def main():
     ap.add_argument("--rank-sweep", action="store_true",
                     help="sweep the compressed sizes n, then p, on the workload (default mid_corr): "
                          "R_s, R_t and e_c per point")
-    ap.add_argument("--adjoint", action="store_true",
-                    help="also time the SVD-SINR adjoint (dSINR -> dG, dC) on the workload")
+    ap.add_argument("--no-adjoint", dest="adjoint", action="store_false",
+                    help="skip the timing of the SVD-SINR adjoint (dSINR -> dG, dC) on the workload")
     ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32", "bf16x2", "tf32x3"],
                     help="arithmetic of the interfering links' core contraction in the timed step "
                          "(fp32: FMA pipe; tf32, bf16x2, tf32x3: tensor cores; default tf32x3, "

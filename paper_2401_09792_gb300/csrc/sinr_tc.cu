@@ -160,60 +160,69 @@ __global__ void k_wait_selftest(long limit, int arrive, int* out) {
 // a = g RPT + a_in of H~, re/im), k over [Re w | Im w] per K segment:
 //   re row: [Re G ; -Im G],   im row: [Im G ; Re G]
 // segment 0 the rounded value (hi), segment 1 the rounded remainder (lo).
-// One thread writes one 16-byte chunk; padding is zero.
+// One CTA per (link, block): the block's core slab G[q][a][c0 .. c0+CB) is
+// staged in shared memory with coalesced loads (MG CB = 32 complex per q),
+// then every thread writes 16-byte chunks of the block; padding is zero.
 template <int PREC>
 __global__ void __launch_bounds__(256) k_core_prep(const float2* __restrict__ G, int m, int n, int p,
                                                    int MG, int kseg, int kbytes, int nblk, int nblocks,
                                                    unsigned char* __restrict__ out) {
   constexpr int ES = tc_es(PREC);
   constexpr int EPC = 16 / ES;                    // elements per 16-byte chunk
+  __shared__ float2 Gs[32 * 32];                  // [q][a][cl], p <= 32, MG CB = 32
   const int nkc = kbytes / 16;
   const int RPT = tc_rpt(MG), RG = tc_rg(MG), CB = tc_cb(MG);
   const int nchunk = kNtile * nkc;
-  for (int y = blockIdx.y; y < nblocks; y += gridDim.y)
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nchunk; idx += gridDim.x * blockDim.x) {
+  for (int y = blockIdx.x; y < nblocks; y += gridDim.x) {
     const int ch = y / nblk, b = y - ch * nblk;
+    __syncthreads();                               // the previous block's slab consumed
+    for (int idx = threadIdx.x; idx < p * MG * CB; idx += blockDim.x) {
+      const int cl = idx % CB, a = (idx / CB) % MG, q = idx / (CB * MG);
+      const int c = b * CB + cl;
+      Gs[idx] = (a < m && c < n) ? __ldg(G + (((size_t)ch * p + q) * m + a) * n + c) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
     unsigned char* blk = out + (size_t)y * kNtile * kbytes;
-    const int r = idx & 7, rest = idx >> 3;
-    const int rg = rest / nkc, kc = rest - rg * nkc;
-    const int j = rg * 8 + r;
-    const int ri = j & 1, a_in = (j >> 1) % RPT, cg = (j >> 1) / RPT;
-    const int c = b * CB + cg / RG, a = (cg % RG) * RPT + a_in;
-    const bool live = a < m && c < n;
-    const float2* gcol = G + ((size_t)ch * p * m + a) * n + c;     // + q m n
-    float x[EPC];
+    for (int idx = threadIdx.x; idx < nchunk; idx += blockDim.x) {
+      const int r = idx & 7, rest = idx >> 3;
+      const int rg = rest / nkc, kc = rest - rg * nkc;
+      const int j = rg * 8 + r;
+      const int ri = j & 1, a_in = (j >> 1) % RPT, cg = (j >> 1) / RPT;
+      const int cl = cg / RG, a = (cg % RG) * RPT + a_in;
+      float x[EPC];
 #pragma unroll
-    for (int e = 0; e < EPC; ++e) {
-      const int k = kc * EPC + e;                  // element within the row
-      const int seg = k / kseg, kk = k - seg * kseg;
-      float v = 0.f;
-      if (live && kk < 2 * p) {
-        const int q = kk < p ? kk : kk - p;
-        const float2 gv = __ldg(gcol + (size_t)q * m * n);
-        // re row: [Re G ; -Im G], im row: [Im G ; Re G]
-        v = ri == 0 ? (kk < p ? gv.x : -gv.y) : (kk < p ? gv.y : gv.x);
-        if (PREC == TS_PREC_BF16X2) {
-          const float hi = __bfloat162float(__float2bfloat16_rn(v));
-          v = seg == 0 ? hi : v - hi;
-        } else {
-          const float hi = to_tf32(v);
-          v = seg == 0 ? hi : to_tf32(v - hi);
+      for (int e = 0; e < EPC; ++e) {
+        const int k = kc * EPC + e;                // element within the row
+        const int seg = k / kseg, kk = k - seg * kseg;
+        float v = 0.f;
+        if (kk < 2 * p) {
+          const int q = kk < p ? kk : kk - p;
+          const float2 gv = Gs[(q * MG + a) * CB + cl];   // zero for padding rows and columns
+          // re row: [Re G ; -Im G], im row: [Im G ; Re G]
+          v = ri == 0 ? (kk < p ? gv.x : -gv.y) : (kk < p ? gv.y : gv.x);
+          if (PREC == TS_PREC_BF16X2) {
+            const float hi = __bfloat162float(__float2bfloat16_rn(v));
+            v = seg == 0 ? hi : v - hi;
+          } else {
+            const float hi = to_tf32(v);
+            v = seg == 0 ? hi : to_tf32(v - hi);
+          }
         }
+        x[e] = v;
       }
-      x[e] = v;
-    }
-    uint32_t words[4];
-    if (ES == 4) {
+      uint32_t words[4];
+      if (ES == 4) {
 #pragma unroll
-      for (int e = 0; e < 4; ++e) words[e] = __float_as_uint(x[e % EPC]);
-    } else {
+        for (int e = 0; e < 4; ++e) words[e] = __float_as_uint(x[e % EPC]);
+      } else {
 #pragma unroll
-      for (int w = 0; w < 4; ++w)
-        words[w] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[(2 * w) % EPC])) |
-                   ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[(2 * w + 1) % EPC])) << 16);
+        for (int w = 0; w < 4; ++w)
+          words[w] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[(2 * w) % EPC])) |
+                     ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x[(2 * w + 1) % EPC])) << 16);
+      }
+      *reinterpret_cast<uint4*>(blk + kmajor_off(j, kc * 16, kbytes)) =
+          make_uint4(words[0], words[1], words[2], words[3]);
     }
-    *reinterpret_cast<uint4*>(blk + kmajor_off(j, kc * 16, kbytes)) =
-        make_uint4(words[0], words[1], words[2], words[3]);
   }
 }
 
@@ -330,22 +339,25 @@ __global__ void __launch_bounds__(4 * kTile) k_tc_proj(const SinrArgs A, int kse
 // a block's rows for all 128 subcarriers.
 __global__ void k_v_tiles(const float2* __restrict__ V, int J, int K, int n, int L, int CB, int nblk,
                           int ntile, float2* __restrict__ Vt) {
-  const size_t per_tile = (size_t)nblk * kTile * CB * L;
-  const size_t total = (size_t)J * ntile * per_tile;
+  // 16-byte pieces: L is even, so a piece holds two streams of one column
+  const int half = CB * L / 2;                    // pieces per (tile, block, subcarrier)
+  const size_t total = (size_t)J * ntile * nblk * kTile * half;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x) {
-    const int l = (int)(idx % L);
-    size_t r = idx / L;
-    const int c = (int)(r % CB);
-    r /= CB;
+    const int piece = (int)(idx % half);
+    size_t r = idx / half;
     const int t = (int)(r % kTile);
     r /= kTile;
     const int b = (int)(r % nblk);
     r /= nblk;
     const int tile = (int)(r % ntile);
     const int k = (int)(r / ntile);
+    const int e = 2 * piece, c = e / L;
     const int kap = tile * kTile + t, col = b * CB + c;
-    Vt[idx] = (kap < K && col < n) ? V[(((size_t)k * K + kap) * n + col) * L + l] : cz();
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (kap < K && col < n)
+      v = __ldg(reinterpret_cast<const float4*>(V + (((size_t)k * K + kap) * n + b * CB) * L + e));
+    reinterpret_cast<float4*>(Vt)[idx] = v;
   }
 }
 
@@ -609,9 +621,8 @@ template <int PREC>
 cudaError_t launch_prep(const SinrArgs& A, int MG, int LT, unsigned char* prep, cudaStream_t s) {
   const TcPlan tp = tc_plan(MG, A.L, A.n, A.p, PREC);
   const size_t bbytes = tp.prep_bytes_per_link * (size_t)A.J * A.J;
-  const int nchunk = kNtile * (tp.kbytes / 16);
   const int nblocks = A.J * A.J * tp.nblk;
-  dim3 pgrid((nchunk + 255) / 256, nblocks < 65535 ? nblocks : 65535);
+  const int pgrid = nblocks < 152 * 64 ? nblocks : 152 * 64;
   k_core_prep<PREC><<<pgrid, 256, 0, s>>>(A.G, A.m, A.n, A.p, MG, tp.kseg, tp.kbytes, tp.nblk, nblocks,
                                           prep);
   cudaError_t e = cudaGetLastError();
@@ -628,7 +639,7 @@ cudaError_t launch_prep(const SinrArgs& A, int MG, int LT, unsigned char* prep, 
   if (e != cudaSuccess) return e;
   // the precoder rows, tiled per (tile, column block)
   const size_t abytes = tp.a_bytes_per_tile * ntile * (size_t)A.J * (A.J - 1);
-  const size_t vtotal = (size_t)A.J * ntile * tp.nblk * kTile * tp.VS;
+  const size_t vtotal = (size_t)A.J * ntile * tp.nblk * kTile * (tp.VS / 2);   // 16-byte pieces
   const int vblocks = (int)((vtotal + 255) / 256 < 152 * 16 ? (vtotal + 255) / 256 : 152 * 16);
   k_v_tiles<<<vblocks, 256, 0, s>>>(A.V, A.J, A.K, A.n, A.L, tc_cb(MG), tp.nblk, ntile,
                                     reinterpret_cast<float2*>(prep + bbytes + abytes));
