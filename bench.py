@@ -158,15 +158,25 @@ def precoder_flops(w) -> int:
     return int(8 * w.K * J * (P * p + m * n * p + m * m * n + m * n * L))
 
 
-def svd_launches(w, tensor_cores=False) -> int:
+def svd_launches(w, prec_id=None) -> int:
     """Kernels one SVD-precoded SINR call launches (path-form coefficients):
-    phase steps, [serving pass (+ its projections for wide cores)],
-    precoders, [core operand, projection operand, precoder tiles,] links,
-    finalize, refine."""
+    phase steps; the serving pass (FP32: one kernel, two for wide cores;
+    TF32X3: the serving projections and the tensor-core serving pass), unless
+    the precoder forms the serving channels itself; the precoder (two phases
+    when it reads the serving pass's channels of up to 512 columns and 16
+    rows) and, for up to 16 rows, the close-pair refinement; the
+    interfering-link pass (tensor-core modes: core operand, projection
+    operand, precoder tiles and the link kernel); finalize and refine."""
+    from paper_2401_09792_gb300 import tuckersinr as ts
+    tc = prec_id is not None and prec_id != ts.TS_PREC_FP32
+    tf32x3 = prec_id == ts.TS_PREC_TF32X3
     fused = w.m * w.n * w.p <= 8192
     wide = w.p > 32 or w.P * w.p > 8192
-    serve = 0 if fused else (2 if wide else 1)
-    return 1 + serve + 1 + (4 if tensor_cores else 1) + 2
+    serve = 0 if fused else (2 if (wide or tf32x3) else 1)
+    precoder = 2 if (not fused and w.m <= 16 and w.n <= 512) else 1
+    close = 1 if w.m <= 16 else 0
+    links = 4 if tc else 1
+    return 1 + serve + precoder + close + links + 2
 
 
 # ----------------------------------------------------------------- helpers
@@ -374,29 +384,25 @@ def run_ours(args):
     def step(e0=None, e1=None, e2=None, k0=None, k1=None):
         if e0 is not None:
             e0.record(stream)
+        # one call; the library records e1 between its precoder and link
+        # phases and k0, k1 around the link kernel
+        ts.ts_set_phase_event(e1)
+        ts.ts_set_timing_events(k0, k1)
         if world > 1:
-            # one range of the shared system (the precoder and link phases
-            # are one call here, so the phase split is not reported)
-            if e1 is not None:
-                e1.record(stream)
-            ts.ts_set_timing_events(k0, k1)
+            # one range of the shared system
             ts.ts_sinr_svd_range(d_all, kappa0, K, coef, dv["G"], dv["C"], dv["sigma2"], prec_id,
                                  sinr, flags, ws, stream)
-            ts.ts_set_timing_events(None, None)
         else:
-            ts.ts_svd_precoders(d, coef, dv["G"], dv["C"], ws, stream)
-            if e1 is not None:
-                e1.record(stream)
-            ts.ts_set_timing_events(k0, k1)
-            ts.ts_sinr_svd_from_precoders_prec(d, coef, dv["G"], dv["C"], dv["sigma2"], prec_id, sinr,
-                                               flags, ws, stream)
-            ts.ts_set_timing_events(None, None)
+            ts.ts_sinr_svd_prec(d, coef, dv["G"], dv["C"], dv["sigma2"], prec_id, sinr, flags, ws,
+                                stream)
+        ts.ts_set_timing_events(None, None)
+        ts.ts_set_phase_event(None)
         if e2 is not None:
             e2.record(stream)
 
     # path phase steps, precoders (with the serving links), links, finalize;
     # tensor-core modes add the core rewrite (a memset and a kernel)
-    launches_per_step = svd_launches(w, prec_id != ts.TS_PREC_FP32)
+    launches_per_step = svd_launches(w, prec_id)
     for _ in range(args.warmup):
         flush.zero_()
         step()
@@ -727,10 +733,8 @@ def _precision_variants(args, ts, torch, dev, w, dv, coef, d, sinr, flags, flush
         wsp = ts.workspace(d, op, dev)
 
         def step(k0=None, k1=None):
-            ts.ts_svd_precoders(d, coef, dv["G"], dv["C"], wsp, stream)
             ts.ts_set_timing_events(k0, k1)
-            ts.ts_sinr_svd_from_precoders_prec(d, coef, dv["G"], dv["C"], dv["sigma2"], prec, sinr,
-                                               flags, wsp, stream)
+            ts.ts_sinr_svd_prec(d, coef, dv["G"], dv["C"], dv["sigma2"], prec, sinr, flags, wsp, stream)
             ts.ts_set_timing_events(None, None)
 
         for _ in range(args.warmup):

@@ -169,6 +169,14 @@ int ts_abi_version(void);
  * covariance kernel).  NULL, NULL turns it off.  Not used otherwise. */
 void ts_set_timing_events(void* start, void* stop);
 
+/* Profiling hook: a caller-created CUDA event (cudaEvent_t as void*) that
+ * the following SVD-precoded SINR calls on this host thread record on their
+ * stream once the precoders are in the workspace (after the serving pass,
+ * the precoder kernels and the close-pair refinement, before the
+ * interfering-link pass): the boundary between the precoder phase and the
+ * link phase of one call.  NULL turns it off.  Not used otherwise. */
+void ts_set_phase_event(void* event);
+
 /* Mixed-precision re-evaluation of sensitive units (eq. 25-28).  The
  * interference-plus-noise covariance R = sum_{k != i} E_ik E_ik* +
  * sigma^2 I is formed and factored in FP32; a unit whose SINRs are
@@ -270,12 +278,17 @@ int ts_sinr_svd_from_precoders(const ts_dims* d, const ts_coef* coef,
 
 /* ts_sinr_svd with the interfering links' core contraction (eq. 15) in the
  * arithmetic `precision` (TS_PREC_*; TS_PREC_FP32 is ts_sinr_svd).  The
- * serving links and the precoders stay FP32.  Tensor-core modes need
+ * precoders stay FP32; the serving links' channels H~_kk that they are
+ * computed from are FP32 too, except that TS_PREC_TF32X3 forms them with
+ * the same three-product tensor-core contraction when the precoder does not
+ * contract the serving core itself (m n p > 8192).  Tensor-core modes need
  * even L <= 8, p <= 32 and m <= 16 (else TS_ERR_MODE); ws holds
- * ts_workspace_bytes(d, TS_OP_SINR_SVD_TF32 / _BF16X2 / _TF32X3) bytes (the core
- * rewritten as a tensor-core operand, then the ts_sinr_svd workspace).
- * ts_sinr_svd_from_precoders_prec is its second phase (after
- * ts_svd_precoders on the same ws). */
+ * ts_workspace_bytes(d, TS_OP_SINR_SVD_TF32 / _BF16X2 / _TF32X3) bytes (the
+ * ts_sinr_svd workspace, then the core rewritten as a tensor-core operand,
+ * the projections and the tiled precoder rows).
+ * ts_sinr_svd_from_precoders_prec is its second phase after ts_svd_precoders
+ * on the same ws (the serving channels of that sequence are FP32 in every
+ * mode). */
 int ts_sinr_svd_prec(const ts_dims* d, const ts_coef* coef, const ts_c64* G,
                      const ts_c64* C, const float* sigma2, int precision,
                      float* sinr, uint8_t* flags, void* ws, size_t ws_bytes,

@@ -18,6 +18,9 @@ thread_local int g_last_cuda = 0;
 // next SINR calls on this host thread (ts_set_timing_events)
 thread_local cudaEvent_t g_ev_start = nullptr;
 thread_local cudaEvent_t g_ev_stop = nullptr;
+// optional caller-owned event recorded once the precoders of an SVD call
+// are in the workspace (ts_set_phase_event)
+thread_local cudaEvent_t g_ev_phase = nullptr;
 // SINR sensitivity to R (see k_sinr_finalize) above which a unit is
 // re-evaluated from a double-float R with FP64 residuals
 // (ts_set_refinement); infinity turns refinement off
@@ -327,6 +330,8 @@ void ts_set_timing_events(void* start, void* stop) {
   g_ev_stop = static_cast<cudaEvent_t>(stop);
 }
 
+void ts_set_phase_event(void* event) { g_ev_phase = static_cast<cudaEvent_t>(event); }
+
 void ts_set_fit_iterations(int iterations) { g_fit_iters = iterations > 0 ? iterations : 40; }
 
 void ts_set_refinement(float threshold) {
@@ -585,8 +590,13 @@ int sinr_mmse_impl(const ts_dims* d, const ts_coef* coef, const ts_c64* G, const
   return cuda_status(e);
 }
 
+// The SVD precoders into the workspace.  With tc_prep (TF32X3, a core that
+// the precoder does not contract itself) the tensor-core operands are
+// prepared into tc_prep first, the serving links' projections included, and
+// the serving pass runs on the tensor cores.
 int svd_precoders_impl(const ts_dims* d, const ts_coef* coef, const ts_c64* G, const ts_c64* C,
-                       bool identity, void* ws, size_t ws_bytes, void* stream) {
+                       bool identity, void* ws, size_t ws_bytes, void* stream,
+                       void* tc_prep = nullptr) {
   static const float kOne = 1.f;
   static float dummy_out;
   int st = sinr_common_checks(d, coef, G, C, identity, &kOne, &dummy_out, ws, ws_bytes,
@@ -613,7 +623,12 @@ int svd_precoders_impl(const ts_dims* d, const ts_coef* coef, const ts_c64* G, c
     }
     a.serv_stride = 1;
     if (w.Wserv != 0 && !identity) a.Wserv = reinterpret_cast<float2*>(base + w.Wserv);
-    if (e == cudaSuccess) e = ts::launch_sinr_serving(a, s);
+    if (tc_prep != nullptr) {
+      if (e == cudaSuccess) e = ts::launch_tc_operands(a, TS_PREC_TF32X3, true, tc_prep, s);
+      if (e == cudaSuccess) e = ts::launch_serving_tc(a, tc_prep, s);
+    } else if (e == cudaSuccess) {
+      e = ts::launch_sinr_serving(a, s);
+    }
   }
   // units with a close pair of singular values are listed by the precoder
   // kernels and their precoders refined from H~ in double-float (off with
@@ -626,12 +641,16 @@ int svd_precoders_impl(const ts_dims* d, const ts_coef* coef, const ts_c64* G, c
   if (e == cudaSuccess && a.list_close) e = cudaMemsetAsync(a.rcount, 0, sizeof(int), s);
   if (e == cudaSuccess) e = ts::launch_svd_precoder(a, s);
   if (e == cudaSuccess && a.list_close) e = ts::launch_precoder_refine(a, s);
+  if (e == cudaSuccess && g_ev_phase != nullptr && !g_timing_suspended) e = cudaEventRecord(g_ev_phase, s);
   return cuda_status(e);
 }
 
+// operands_ready: svd_precoders_impl prepared the operands (all but the
+// precoder rows) into the same buffer
 int svd_from_precoders_prec_impl(const ts_dims* d, const ts_coef* coef, const ts_c64* G,
                                  const ts_c64* C, const float* sigma2, int prec, float* sinr,
-                                 uint8_t* flags, void* ws, size_t ws_bytes, void* stream) {
+                                 uint8_t* flags, void* ws, size_t ws_bytes, void* stream,
+                                 bool operands_ready = false) {
   int st = sinr_common_checks(d, coef, G, C, false, sigma2, sinr, ws, ws_bytes, TS_OP_SINR_SVD);
   if (st != TS_OK) return st;
   if (ws_bytes < prec_workspace_bytes(d, prec)) return TS_ERR_WORKSPACE;
@@ -643,7 +662,7 @@ int svd_from_precoders_prec_impl(const ts_dims* d, const ts_coef* coef, const ts
   a.pflag = reinterpret_cast<uint8_t*>(base + w.pflag);
   void* prep = base + w.total;
   const bool timed = g_ev_start != nullptr && g_ev_stop != nullptr && !g_timing_suspended;
-  cudaError_t e = ts::launch_core_prep(a, prec, prep, s);
+  cudaError_t e = operands_ready ? ts::launch_tc_vtiles(a, prec, prep, s) : ts::launch_core_prep(a, prec, prep, s);
   if (e == cudaSuccess && timed) e = cudaEventRecord(g_ev_start, s);
   if (e == cudaSuccess) e = ts::launch_sinr_links_tc(a, prec, prep, s);
   if (e == cudaSuccess && timed) e = cudaEventRecord(g_ev_stop, s);
@@ -817,10 +836,14 @@ int ts_sinr_svd_prec(const ts_dims* d, const ts_coef* coef, const ts_c64* G, con
   int st = check_prec(d, precision);
   if (st != TS_OK) return st;
   if (ws != nullptr && ws_bytes < prec_workspace_bytes(d, precision)) return TS_ERR_WORKSPACE;
-  st = svd_precoders_impl(d, coef, G, C, false, ws, ws_bytes, stream);
+  // TF32X3 also forms the serving channels on the tensor cores (where the
+  // precoder reads them from the serving pass)
+  const bool tc_serve = precision == TS_PREC_TF32X3 && ws != nullptr && !fuses_serve(d);
+  void* prep = tc_serve ? static_cast<char*>(ws) + carve(d, TS_OP_SINR_SVD).total : nullptr;
+  st = svd_precoders_impl(d, coef, G, C, false, ws, ws_bytes, stream, prep);
   if (st != TS_OK) return st;
   return svd_from_precoders_prec_impl(d, coef, G, C, sigma2, precision, sinr, flags, ws, ws_bytes,
-                                      stream);
+                                      stream, tc_serve);
 }
 
 int ts_sinr_svd_from_precoders_prec(const ts_dims* d, const ts_coef* coef, const ts_c64* G,

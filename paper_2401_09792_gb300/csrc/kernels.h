@@ -141,12 +141,19 @@ cudaError_t launch_sinr_rebuild(const SinrArgs& a, cudaStream_t s);
 cudaError_t launch_sinr_serving(const SinrArgs& a, cudaStream_t s);
 // Tensor-core interfering-link pass (reduced-precision modes, sinr_tc.cu):
 // shape support, bytes of the operands (the rewritten core of every link,
-// then the projections of the interfering links' subcarrier tiles), their
-// preparation into `prep` (once per call), and the link kernel.
+// the projections of the interfering links' subcarrier tiles, the tiled
+// precoder rows, and in TF32X3 the projections of the serving links'
+// tiles), their preparation into `prep` once per call (launch_core_prep:
+// operands then precoder rows; or launch_tc_operands before the precoders,
+// with `serving` for launch_serving_tc, and launch_tc_vtiles after them),
+// the link kernel, and the TF32X3 serving pass writing H~_kk to Hserv.
 bool tc_supported(int m, int L, int p);
 size_t tc_prep_bytes(int J, int m, int L, int n, int p, int K, int prec);
 cudaError_t launch_core_prep(const SinrArgs& a, int prec, void* prep, cudaStream_t s);
+cudaError_t launch_tc_operands(const SinrArgs& a, int prec, bool serving, void* prep, cudaStream_t s);
+cudaError_t launch_tc_vtiles(const SinrArgs& a, int prec, void* prep, cudaStream_t s);
 cudaError_t launch_sinr_links_tc(const SinrArgs& a, int prec, const void* prep, cudaStream_t s);
+cudaError_t launch_serving_tc(const SinrArgs& a, const void* prep, cudaStream_t s);
 // Widest serving channel (columns n) the register precoder stages whole.
 constexpr int kMaxNRegisterPrecoder = 512;
 // The SVD precoder forms H~_kk itself (re-reading the core G_kk once per

@@ -34,6 +34,11 @@
 // wait is bounded; on a timeout the tile's precoder flags get
 // TS_FLAG_TIMEOUT, outstanding copies and MMAs get another bounded wait,
 // and the TMEM is released.
+//
+// The same kernel with SERVE (TF32X3, before the precoders) forms the
+// serving links' H~_ii: one CTA per (tile, UE i), the serving link's
+// projections as the A operand, no precoder rows; the epilogue stores the
+// accumulator columns as rows of H~_ii for the precoder to read.
 #include <cuda_bf16.h>
 
 #include "sinr_impl.cuh"
@@ -61,7 +66,8 @@ struct TcPlan {
   int kseg;        // elements per K segment: 2p padded to 32 bytes
   int kbytes;      // bytes per operand row
   int nblk;        // column blocks = ceil(n / CB)
-  int VS;          // precoder rows of one subcarrier and block (float2): CB L
+  int VS;          // row stride of one subcarrier's precoder rows of a block
+                   // (float2): CB L, or CB L + 2 (see v_piece)
   int vstages;     // slots of the precoder-row ring (2 .. kVStages)
   int nthreads;    // 32 (2 + 4 RG): MMA warp, precoder-row warp, epilogue warps
   int off_A, off_B, off_V, off_bar, smem;   // byte offsets
@@ -80,6 +86,7 @@ inline TcPlan tc_plan(int MG, int L, int n, int p, int prec) {
   const int CB = tc_cb(MG);
   t.nblk = (n + CB - 1) / CB;
   t.VS = CB * L;
+  if ((t.VS / 2) % 8 != 0 && (t.VS / 2) % 2 == 0) t.VS += 2;
   t.nthreads = 32 * (2 + 4 * tc_rg(MG));
   int o = 0;
   t.off_A = o; o += kTile * t.kbytes;
@@ -96,6 +103,17 @@ inline TcPlan tc_plan(int MG, int L, int n, int p, int prec) {
   t.a_bytes_per_tile = (size_t)kTile * t.kbytes;
   t.v_bytes_per_tile = (size_t)t.nblk * kTile * t.VS * 8;
   return t;
+}
+
+// Position of 16-byte piece j of subcarrier t's precoder row (R pieces of
+// data) in the tile layout and in shared memory.  The epilogue threads of a
+// quarter warp (eight consecutive subcarriers) read the same j at once: rows
+// of a multiple of 8 pieces permute their pieces by t mod 8 (XOR), other
+// rows have an odd stride in pieces (VS padded), so the eight reads fall in
+// distinct shared-memory banks (a plain 128-byte stride made them an 8-way
+// conflict).
+__host__ __device__ __forceinline__ int v_piece(int j, int t, int R) {
+  return (R & 7) == 0 ? (j ^ (t & 7)) : j;
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -227,7 +245,8 @@ __global__ void __launch_bounds__(256) k_core_prep(const float2* __restrict__ G,
 }
 
 // ------------------------------------------------------ projection operand
-// A operand of (interfering link (i, k), subcarrier tile): row t =
+// A operand of (interfering link (i, k), subcarrier tile), or with serv of
+// the serving link (i, i) (grid z = 1, its own output region): row t =
 // subcarrier kap0 + t, k over [Re w | Im w] with w = C_ik^T conj(c_ik(kappa))
 // (eq. 15) in FP32, then per K segment rounded (hi) or the rounded
 // remainder (lo), in the canonical K-major layout.  The coefficients of a
@@ -238,7 +257,7 @@ constexpr int kProjPC = 32;
 constexpr int kProjQ = 8;      // projections w_q per thread
 
 template <int PREC>
-__global__ void __launch_bounds__(4 * kTile) k_tc_proj(const SinrArgs A, int kseg, int kbytes,
+__global__ void __launch_bounds__(4 * kTile) k_tc_proj(const SinrArgs A, int kseg, int kbytes, int serv,
                                                        unsigned char* __restrict__ out) {
   constexpr int ES = tc_es(PREC);
   constexpr int EPC = 16 / ES;
@@ -248,7 +267,7 @@ __global__ void __launch_bounds__(4 * kTile) k_tc_proj(const SinrArgs A, int kse
   const int i = blockIdx.y, z = blockIdx.z;
   const int kap0 = blockIdx.x * kTile;
   const int J = A.J, p = A.p, P = A.P, K = A.K;
-  const int k = z < i ? z : z + 1;
+  const int k = serv ? i : (z < i ? z : z + 1);
   const int ch = i * J + k;
   const int nkc = kbytes / 16;
   const int WS = 2 * p + 1;
@@ -293,7 +312,8 @@ __global__ void __launch_bounds__(4 * kTile) k_tc_proj(const SinrArgs A, int kse
     }
   }
   __syncthreads();
-  unsigned char* dst = out + (((size_t)i * (J - 1) + z) * gridDim.x + blockIdx.x) * (size_t)kTile * kbytes;
+  unsigned char* dst =
+      out + ((serv ? (size_t)i : (size_t)i * (J - 1) + z) * gridDim.x + blockIdx.x) * (size_t)kTile * kbytes;
   for (int idx = tid; idx < kTile * nkc; idx += nth) {
     const int r = idx & 7, rest = idx >> 3;
     const int rg = rest / nkc, kc = rest - rg * nkc;
@@ -334,19 +354,21 @@ __global__ void __launch_bounds__(4 * kTile) k_tc_proj(const SinrArgs A, int kse
 
 // ------------------------------------------------------- precoder tiles
 // The precoder rows V~_k(kappa)[c][l] of a (tile, column block) for the
-// link kernel, as one contiguous chunk: Vt[k][tile][b][t][CB][L] (t the
-// subcarrier of the tile), zero beyond K and n, so that one bulk copy moves
-// a block's rows for all 128 subcarriers.
-__global__ void k_v_tiles(const float2* __restrict__ V, int J, int K, int n, int L, int CB, int nblk,
-                          int ntile, float2* __restrict__ Vt) {
+// link kernel, as one contiguous chunk: Vt[k][tile][b][t][VS] (t the
+// subcarrier of the tile; a row holds [CB][L] as 16-byte pieces placed by
+// v_piece), zero beyond K and n and in the row padding, so that one bulk
+// copy moves a block's rows for all 128 subcarriers.
+__global__ void k_v_tiles(const float2* __restrict__ V, int J, int K, int n, int L, int CB, int VS,
+                          int nblk, int ntile, float2* __restrict__ Vt) {
   // 16-byte pieces: L is even, so a piece holds two streams of one column
-  const int half = CB * L / 2;                    // pieces per (tile, block, subcarrier)
+  const int half = VS / 2;                        // pieces per (tile, block, subcarrier) row
+  const int data = CB * L / 2;                    // of which hold precoder entries
   const size_t total = (size_t)J * ntile * nblk * kTile * half;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x) {
-    const int piece = (int)(idx % half);
     size_t r = idx / half;
     const int t = (int)(r % kTile);
+    const int piece = v_piece((int)(idx % half), t, data);    // an involution
     r /= kTile;
     const int b = (int)(r % nblk);
     r /= nblk;
@@ -355,7 +377,7 @@ __global__ void k_v_tiles(const float2* __restrict__ V, int J, int K, int n, int
     const int e = 2 * piece, c = e / L;
     const int kap = tile * kTile + t, col = b * CB + c;
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (kap < K && col < n)
+    if (piece < data && kap < K && col < n)
       v = __ldg(reinterpret_cast<const float4*>(V + (((size_t)k * K + kap) * n + b * CB) * L + e));
     reinterpret_cast<float4*>(Vt)[idx] = v;
   }
@@ -364,7 +386,31 @@ __global__ void k_v_tiles(const float2* __restrict__ V, int J, int K, int n, int
 // ----------------------------------------------------------- link kernel
 constexpr int kBars = 20;      // mbarriers of the link kernel (see below)
 
-template <int MG, int LT, int PREC>
+// One accumulator column group of a row group: the 2 RPT FP32 words (re, im
+// of RPT rows of H~) of this thread's TMEM lane, starting at column taddr.
+// Warp-collective; the caller waits (tcgen05.wait::ld) before reading h.
+template <int RPT>
+__device__ __forceinline__ void tmem_ld_rows(uint32_t taddr, uint32_t (&h)[2 * RPT]) {
+  if constexpr (RPT == 8) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(h[0]), "=r"(h[1]), "=r"(h[2]), "=r"(h[3]), "=r"(h[4]), "=r"(h[5]), "=r"(h[6]), "=r"(h[7]),
+          "=r"(h[8]), "=r"(h[9]), "=r"(h[10]), "=r"(h[11]), "=r"(h[12]), "=r"(h[13]), "=r"(h[14]), "=r"(h[15])
+        : "r"(taddr));
+  } else if constexpr (RPT == 4) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(h[0]), "=r"(h[1]), "=r"(h[2]), "=r"(h[3]), "=r"(h[4]), "=r"(h[5]), "=r"(h[6]),
+                   "=r"(h[7])
+                 : "r"(taddr));
+  } else {
+    static_assert(RPT == 2, "tcgen05.ld shape");
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(h[0]), "=r"(h[1]), "=r"(h[2]), "=r"(h[3])
+                 : "r"(taddr));
+  }
+}
+
+template <int MG, int LT, int PREC, bool SERVE>
 __global__ void __launch_bounds__(32 * (2 + 4 * tc_rg(MG)), 1)
     k_sinr_link_tc(const SinrArgs A, const unsigned char* __restrict__ prep,
                    const unsigned char* __restrict__ aop, const float2* __restrict__ vtiles, TcPlan tp) {
@@ -380,7 +426,7 @@ __global__ void __launch_bounds__(32 * (2 + 4 * tc_rg(MG)), 1)
   const int i = blockIdx.y, z = blockIdx.z;
   const int kap0 = blockIdx.x * kTile;
   const int J = A.J, m = A.m, n = A.n, L = A.L, K = A.K;
-  const int k = z < i ? z : z + 1;
+  const int k = SERVE ? i : (z < i ? z : z + 1);
   const int ch = i * J + k;
   const int kbytes = tp.kbytes, nblk = tp.nblk;
   unsigned char* sA = smem + tp.off_A;
@@ -399,7 +445,7 @@ __global__ void __launch_bounds__(32 * (2 + 4 * tc_rg(MG)), 1)
   if (tid == 0) {
     abort_flag = 0;
     // the refinement list of the finalize kernel that follows starts empty
-    if (A.rcount != nullptr && blockIdx.x == 0 && i == 0 && z == 0) *A.rcount = 0;
+    if (!SERVE && A.rcount != nullptr && blockIdx.x == 0 && i == 0 && z == 0) *A.rcount = 0;
     for (int s = 0; s < kBars; ++s)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar0 + 8u * s),
                    "r"((s == 8 || s == 9 || s >= 16) ? (uint32_t)NEPI : 1u));
@@ -438,7 +484,8 @@ __global__ void __launch_bounds__(32 * (2 + 4 * tc_rg(MG)), 1)
       asm volatile(
           "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
               smem_u32(sA)),
-          "l"(aop + (((size_t)i * (J - 1) + z) * gridDim.x + blockIdx.x) * (size_t)a_bytes), "r"(a_bytes),
+          "l"(aop + ((SERVE ? (size_t)i : (size_t)i * (J - 1) + z) * gridDim.x + blockIdx.x) * (size_t)a_bytes),
+          "r"(a_bytes),
           "r"(afull)
           : "memory");
       for (int b = 0; b < kBStages && b < nblk; ++b) issue_B(b);
@@ -498,8 +545,8 @@ __global__ void __launch_bounds__(32 * (2 + 4 * tc_rg(MG)), 1)
   } else if (warp == 1) {
     // ---------------- precoder rows: one bulk copy per block of the tile's
     // rows (k_v_tiles laid them out contiguously), into a ring shared by
-    // the row groups
-    if (lane == 0) {
+    // the row groups (idle for the serving links)
+    if (!SERVE && lane == 0) {
       const uint32_t chunk = (uint32_t)(kTile * tp.VS * 8);
       const float2* vt = vtiles + ((size_t)k * gridDim.x + blockIdx.x) * tp.v_bytes_per_tile / 8;
       bool ok = true;
@@ -525,6 +572,55 @@ __global__ void __launch_bounds__(32 * (2 + 4 * tc_rg(MG)), 1)
       for (int sl = 0; sl < kVStages; ++sl)
         if (last[sl] >= 0) mbar_wait(bar0 + 8u * (12 + sl), (uint32_t)((last[sl] / tp.vstages) & 1));
     }
+  } else if constexpr (SERVE) {
+    // ---------------- serving links: the rows of H~_ii (subcarrier t_in, rows
+    // of group g) from TMEM to Hserv, two adjacent columns per store
+    const int ew = warp - 2, quad = warp & 3, g = ew >> 2;
+    const int t_in = quad * 32 + lane;
+    const int kap = kap0 + t_in;
+    const bool vec = (n & 1) == 0;                // 16-byte aligned column pairs
+    bool good = true;
+    for (int b = 0; b < nblk; ++b) {
+      const int t = b & 1;
+      if (!mbar_wait(bar0 + 8u * (6 + t), (uint32_t)((b >> 1) & 1))) { good = false; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int ncb = min(CB, n - b * CB);
+#pragma unroll
+      for (int c2 = 0; c2 < CB; c2 += 2) {
+        if (c2 >= ncb) break;
+        const uint32_t tcol = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(t * kNtile);
+        uint32_t h0[2 * RPT], h1[2 * RPT];
+        tmem_ld_rows<RPT>(tcol + (uint32_t)((c2 * RG + g) * 2 * RPT), h0);
+        const bool two = c2 + 1 < ncb;
+        if (two) tmem_ld_rows<RPT>(tcol + (uint32_t)(((c2 + 1) * RG + g) * 2 * RPT), h1);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (kap < K) {
+#pragma unroll
+          for (int r = 0; r < RPT; ++r) {
+            const int a = g * RPT + r;
+            if (a >= m) continue;
+            float2* dst = A.Hserv + (((size_t)i * A.serv_stride * K + kap) * m + a) * n + b * CB + c2;
+            const float2 x0 = make_float2(__uint_as_float(h0[2 * r]), __uint_as_float(h0[2 * r + 1]));
+            if (two) {
+              const float2 x1 = make_float2(__uint_as_float(h1[2 * r]), __uint_as_float(h1[2 * r + 1]));
+              if (vec) {
+                *reinterpret_cast<float4*>(dst) = make_float4(x0.x, x0.y, x1.x, x1.y);
+              } else {
+                dst[0] = x0;
+                dst[1] = x1;
+              }
+            } else {
+              dst[0] = x0;
+            }
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar0 + 8u * (8 + t)) : "memory");
+    }
+    if (!good) *abort_v = 1;
   } else {
     // ---------------- epilogue: E += H~ V~ for (subcarrier t_in, rows of group g)
     const int ew = warp - 2, quad = warp & 3, g = ew >> 2;
@@ -547,31 +643,14 @@ __global__ void __launch_bounds__(32 * (2 + 4 * tc_rg(MG)), 1)
       for (int cc = 0; cc < CB; ++cc) {
         if (cc >= ncb) break;
         uint32_t h[2 * RPT];
-        const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) +
-                               (uint32_t)(t * kNtile + (cc * RG + g) * 2 * RPT);
-        if constexpr (RPT == 8) {
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-              : "=r"(h[0]), "=r"(h[1]), "=r"(h[2]), "=r"(h[3]), "=r"(h[4]), "=r"(h[5]), "=r"(h[6]),
-                "=r"(h[7]), "=r"(h[8]), "=r"(h[9]), "=r"(h[10]), "=r"(h[11]), "=r"(h[12]), "=r"(h[13]),
-                "=r"(h[14]), "=r"(h[15])
-              : "r"(taddr));
-        } else if constexpr (RPT == 4) {
-          asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                       : "=r"(h[0]), "=r"(h[1]), "=r"(h[2]), "=r"(h[3]), "=r"(h[4]), "=r"(h[5]),
-                         "=r"(h[6]), "=r"(h[7])
-                       : "r"(taddr));
-        } else {
-          static_assert(RPT == 2, "tcgen05.ld shape");
-          asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-                       : "=r"(h[0]), "=r"(h[1]), "=r"(h[2]), "=r"(h[3])
-                       : "r"(taddr));
-        }
+        tmem_ld_rows<RPT>(tmem + ((uint32_t)(quad * 32) << 16) +
+                              (uint32_t)(t * kNtile + (cc * RG + g) * 2 * RPT),
+                          h);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
         for (int l2 = 0; l2 < LT / 2; ++l2) {
           if (2 * l2 >= L) break;
-          const float4 v = reinterpret_cast<const float4*>(vb + cc * L)[l2];
+          const float4 v = reinterpret_cast<const float4*>(vb)[v_piece(cc * (L / 2) + l2, t_in, CB * L / 2)];
           const float2 v0 = make_float2(v.x, v.y), v1 = make_float2(v.z, v.w);
 #pragma unroll
           for (int r = 0; r < RPT; ++r) {
@@ -607,42 +686,81 @@ __global__ void __launch_bounds__(32 * (2 + 4 * tc_rg(MG)), 1)
   __syncthreads();
   if (*abort_v) {
     // an operand or an MMA never arrived: the tile's units are flagged (and
-    // get NaN from the finalisation)
-    for (int t = tid; t < kTile; t += blockDim.x)
-      if (kap0 + t < K) A.pflag[(size_t)i * K + kap0 + t] |= TS_FLAG_TIMEOUT;
+    // get NaN from the finalisation); for the serving links the tile's rows
+    // of H~_ii become NaN, which the precoder that reads them reports as
+    // unconverged (TS_FLAG_EIG_UNCONVERGED, NaN SINRs)
+    if constexpr (SERVE) {
+      const size_t rows = (size_t)min(kTile, K - kap0) * m * n;
+      float2* dst = A.Hserv + ((size_t)i * A.serv_stride * K + kap0) * m * n;
+      for (size_t e = tid; e < rows; e += blockDim.x) dst[e] = make_float2(__int_as_float(0x7fc00000), 0.f);
+    } else {
+      for (int t = tid; t < kTile; t += blockDim.x)
+        if (kap0 + t < K) A.pflag[(size_t)i * K + kap0 + t] |= TS_FLAG_TIMEOUT;
+    }
   }
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kNtile));
 }
 
-// both operands: the core of every link and the projections of the
-// interfering links' tiles (each written in full, padding included)
+// Layout of the operand buffer: the core operand of every link, the
+// projections of the interfering links' tiles, the precoder-row tiles, and
+// (TF32X3 only) the projections of the serving links' tiles.
+struct TcLayout {
+  size_t aop, vt, serv, total;
+};
+
+inline TcLayout tc_layout(const TcPlan& tp, int J, int K, int prec) {
+  const size_t ntile = (size_t)(K + kTile - 1) / kTile;
+  TcLayout l;
+  l.aop = tp.prep_bytes_per_link * (size_t)J * J;
+  l.vt = l.aop + tp.a_bytes_per_tile * ntile * J * (J - 1);
+  l.serv = l.vt + tp.v_bytes_per_tile * ntile * J;
+  l.total = l.serv + (prec == TS_PREC_TF32X3 ? tp.a_bytes_per_tile * ntile * J : 0);
+  return l;
+}
+
+// the operands that do not depend on the precoders: the core of every link
+// and the projections of the interfering links' tiles, with `serving` also
+// those of the serving links' tiles (each written in full, padding included)
 template <int PREC>
-cudaError_t launch_prep(const SinrArgs& A, int MG, int LT, unsigned char* prep, cudaStream_t s) {
+cudaError_t launch_operands(const SinrArgs& A, int MG, bool serving, unsigned char* prep, cudaStream_t s) {
   const TcPlan tp = tc_plan(MG, A.L, A.n, A.p, PREC);
-  const size_t bbytes = tp.prep_bytes_per_link * (size_t)A.J * A.J;
+  const TcLayout lay = tc_layout(tp, A.J, A.K, PREC);
   const int nblocks = A.J * A.J * tp.nblk;
   const int pgrid = nblocks < 152 * 64 ? nblocks : 152 * 64;
   k_core_prep<PREC><<<pgrid, 256, 0, s>>>(A.G, A.m, A.n, A.p, MG, tp.kseg, tp.kbytes, tp.nblk, nblocks,
                                           prep);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || A.J < 2) return e;
+  if (e != cudaSuccess || (A.J < 2 && !serving)) return e;
   const int smem = ((kTile * (2 * A.p + 1) * 4 + 15) & ~15) + kTile * (kProjPC + 1) * 8 +
                    kProjPC * A.p * 8;
   e = cudaFuncSetAttribute(k_tc_proj<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   const int ntile = (A.K + kTile - 1) / kTile;
-  dim3 grid(ntile, A.J, A.J - 1);
-  k_tc_proj<PREC><<<grid, kTile * ((A.p + kProjQ - 1) / kProjQ), smem, s>>>(A, tp.kseg, tp.kbytes,
-                                                                          prep + bbytes);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  // the precoder rows, tiled per (tile, column block)
-  const size_t abytes = tp.a_bytes_per_tile * ntile * (size_t)A.J * (A.J - 1);
+  const int nthr = kTile * ((A.p + kProjQ - 1) / kProjQ);
+  if (A.J >= 2) {
+    k_tc_proj<PREC><<<dim3(ntile, A.J, A.J - 1), nthr, smem, s>>>(A, tp.kseg, tp.kbytes, 0, prep + lay.aop);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (serving) {
+    k_tc_proj<PREC><<<dim3(ntile, A.J, 1), nthr, smem, s>>>(A, tp.kseg, tp.kbytes, 1, prep + lay.serv);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+// the precoder rows, tiled per (tile, column block)
+template <int PREC>
+cudaError_t launch_vtiles(const SinrArgs& A, int MG, unsigned char* prep, cudaStream_t s) {
+  if (A.J < 2) return cudaSuccess;
+  const TcPlan tp = tc_plan(MG, A.L, A.n, A.p, PREC);
+  const TcLayout lay = tc_layout(tp, A.J, A.K, PREC);
+  const int ntile = (A.K + kTile - 1) / kTile;
   const size_t vtotal = (size_t)A.J * ntile * tp.nblk * kTile * (tp.VS / 2);   // 16-byte pieces
   const int vblocks = (int)((vtotal + 255) / 256 < 152 * 16 ? (vtotal + 255) / 256 : 152 * 16);
-  k_v_tiles<<<vblocks, 256, 0, s>>>(A.V, A.J, A.K, A.n, A.L, tc_cb(MG), tp.nblk, ntile,
-                                    reinterpret_cast<float2*>(prep + bbytes + abytes));
+  k_v_tiles<<<vblocks, 256, 0, s>>>(A.V, A.J, A.K, A.n, A.L, tc_cb(MG), tp.VS, tp.nblk, ntile,
+                                    reinterpret_cast<float2*>(prep + lay.vt));
   return cudaGetLastError();
 }
 
@@ -650,14 +768,29 @@ template <int MG, int LT, int PREC>
 cudaError_t launch_tc(const SinrArgs& A, const unsigned char* prep, cudaStream_t s) {
   if (A.J < 2) return cudaSuccess;
   const TcPlan tp = tc_plan(MG, A.L, A.n, A.p, PREC);
-  auto kern = k_sinr_link_tc<MG, LT, PREC>;
+  const TcLayout lay = tc_layout(tp, A.J, A.K, PREC);
+  auto kern = k_sinr_link_tc<MG, LT, PREC, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, tp.smem);
   if (e != cudaSuccess) return e;
   dim3 grid((A.K + kTile - 1) / kTile, A.J, A.J - 1);
-  const unsigned char* aop = prep + tp.prep_bytes_per_link * (size_t)A.J * A.J;
-  const size_t abytes = tp.a_bytes_per_tile * grid.x * (size_t)A.J * (A.J - 1);
-  const float2* vt = reinterpret_cast<const float2*>(aop + abytes);
-  kern<<<grid, tp.nthreads, tp.smem, s>>>(A, prep, aop, vt, tp);
+  kern<<<grid, tp.nthreads, tp.smem, s>>>(A, prep, prep + lay.aop, reinterpret_cast<const float2*>(prep + lay.vt),
+                                          tp);
+  return cudaGetLastError();
+}
+
+// the serving links' H~_ii (TF32X3) into Hserv: the link kernel without the
+// precoder-row ring
+template <int MG>
+cudaError_t launch_serve_tc(const SinrArgs& A, const unsigned char* prep, cudaStream_t s) {
+  TcPlan tp = tc_plan(MG, A.L, A.n, A.p, TS_PREC_TF32X3);
+  const TcLayout lay = tc_layout(tp, A.J, A.K, TS_PREC_TF32X3);
+  tp.off_bar = (tp.off_V + 15) & ~15;
+  tp.smem = tp.off_bar + 24 * 8;
+  auto kern = k_sinr_link_tc<MG, 2, TS_PREC_TF32X3, true>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, tp.smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((A.K + kTile - 1) / kTile, A.J, 1);
+  kern<<<grid, tp.nthreads, tp.smem, s>>>(A, prep, prep + lay.serv, nullptr, tp);
   return cudaGetLastError();
 }
 
@@ -685,18 +818,41 @@ bool tc_supported(int m, int L, int p) {
 
 size_t tc_prep_bytes(int J, int m, int L, int n, int p, int K, int prec) {
   const detail::TcPlan tp = detail::tc_plan(detail::tc_mg(m), L, n, p, prec);
-  const size_t tiles = (size_t)(K + detail::kTile - 1) / detail::kTile;
-  return tp.prep_bytes_per_link * (size_t)J * J + tp.a_bytes_per_tile * tiles * J * (J - 1) +
-         tp.v_bytes_per_tile * tiles * J;
+  return detail::tc_layout(tp, J, K, prec).total;
+}
+
+cudaError_t launch_tc_operands(const SinrArgs& a, int prec, bool serving, void* prep, cudaStream_t s) {
+  using namespace detail;
+  unsigned char* pp = static_cast<unsigned char*>(prep);
+  const int MG = tc_mg(a.m);
+  if (prec == TS_PREC_TF32) return launch_operands<TS_PREC_TF32>(a, MG, false, pp, s);
+  if (prec == TS_PREC_TF32X3) return launch_operands<TS_PREC_TF32X3>(a, MG, serving, pp, s);
+  return launch_operands<TS_PREC_BF16X2>(a, MG, false, pp, s);
+}
+
+cudaError_t launch_tc_vtiles(const SinrArgs& a, int prec, void* prep, cudaStream_t s) {
+  using namespace detail;
+  unsigned char* pp = static_cast<unsigned char*>(prep);
+  const int MG = tc_mg(a.m);
+  if (prec == TS_PREC_TF32) return launch_vtiles<TS_PREC_TF32>(a, MG, pp, s);
+  if (prec == TS_PREC_TF32X3) return launch_vtiles<TS_PREC_TF32X3>(a, MG, pp, s);
+  return launch_vtiles<TS_PREC_BF16X2>(a, MG, pp, s);
 }
 
 cudaError_t launch_core_prep(const SinrArgs& a, int prec, void* prep, cudaStream_t s) {
+  cudaError_t e = launch_tc_operands(a, prec, false, prep, s);
+  return e == cudaSuccess ? launch_tc_vtiles(a, prec, prep, s) : e;
+}
+
+cudaError_t launch_serving_tc(const SinrArgs& a, const void* prep, cudaStream_t s) {
   using namespace detail;
-  unsigned char* pp = static_cast<unsigned char*>(prep);
-  const int MG = tc_mg(a.m), LT = tc_lt(a.m, a.L);
-  if (prec == TS_PREC_TF32) return launch_prep<TS_PREC_TF32>(a, MG, LT, pp, s);
-  if (prec == TS_PREC_TF32X3) return launch_prep<TS_PREC_TF32X3>(a, MG, LT, pp, s);
-  return launch_prep<TS_PREC_BF16X2>(a, MG, LT, pp, s);
+  const unsigned char* pp = static_cast<const unsigned char*>(prep);
+  switch (tc_mg(a.m)) {
+    case 2: return launch_serve_tc<2>(a, pp, s);
+    case 4: return launch_serve_tc<4>(a, pp, s);
+    case 8: return launch_serve_tc<8>(a, pp, s);
+    default: return launch_serve_tc<16>(a, pp, s);
+  }
 }
 
 cudaError_t launch_sinr_links_tc(const SinrArgs& a, int prec, const void* prep, cudaStream_t s) {

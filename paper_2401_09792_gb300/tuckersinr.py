@@ -74,6 +74,7 @@ _SIG = {
     "ts_last_cuda_error": (ctypes.c_int, []),
     "ts_abi_version": (ctypes.c_int, []),
     "ts_set_timing_events": (None, [_P, _P]),
+    "ts_set_phase_event": (None, [_P]),
     "ts_set_refinement": (None, [ctypes.c_float]),
     "ts_device_peaks": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double), _P]),
@@ -215,6 +216,12 @@ def ts_set_timing_events(start=None, stop=None):
     following SINR calls on this thread (None, None: off)."""
     h = lambda e: None if e is None else e.cuda_event  # noqa: E731
     load().ts_set_timing_events(h(start), h(stop))
+
+
+def ts_set_phase_event(event=None):
+    """Record a torch.cuda.Event between the precoder and link phases of the
+    following SVD-precoded SINR calls on this thread (None: off)."""
+    load().ts_set_phase_event(None if event is None else event.cuda_event)
 
 
 def ts_workspace_bytes(d: Dims, op: int) -> int:

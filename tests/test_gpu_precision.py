@@ -129,6 +129,10 @@ EDGE = {
     "m16_L8": dict(J=3, M=16, m=16, L=8, N=80, n=64, P=40, p=32, K=130),
     "m12_L2": dict(J=3, M=16, m=12, L=2, N=40, n=24, P=10, p=5, K=33),   # 16-lane groups, L <= 2
     "m2": dict(M=2, m=2, L=2, n=8, N=16, K=64),
+    # precoder-row layouts of the link pass: rows of 6 and 4 16-byte pieces
+    # (padded stride) beside the 8- and 16-piece rows (permuted) above
+    "m16_L6": dict(J=3, M=16, m=16, L=6, N=48, n=40, P=20, p=12, K=140),
+    "m14_L4": dict(J=3, M=16, m=14, L=4, N=40, n=30, P=16, p=9, K=129),
     "single_cell": dict(J=1, K=5),
 }
 
