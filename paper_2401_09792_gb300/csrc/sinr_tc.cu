@@ -453,7 +453,7 @@ __global__ void __launch_bounds__(32 * (2 + 4 * tc_rg(MG)), 1)
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(&tmem_slot)), "r"(2 * kNtile));
+                     smem_u32(&tmem_slot)), "r"(4 * kNtile));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -464,7 +464,8 @@ __global__ void __launch_bounds__(32 * (2 + 4 * tc_rg(MG)), 1)
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- loads and MMAs (one thread)
-      int loaded[kBStages] = {0, 0, 0}, consumed[kBStages] = {0, 0, 0};
+      // core blocks 0 .. nB - 1 copied (in order), 0 .. nC - 1 consumed
+      int nB = 0, nC = 0;
       auto issue_B = [&](int b) {
         const int s = b % kBStages;
         const uint32_t bar = bar0 + 8u * s;
@@ -475,7 +476,7 @@ __global__ void __launch_bounds__(32 * (2 + 4 * tc_rg(MG)), 1)
                 smem_u32(sB + s * blk_bytes)),
             "l"(prep_ch + (size_t)b * blk_bytes), "r"((uint32_t)blk_bytes), "r"(bar)
             : "memory");
-        ++loaded[s];
+        nB = b + 1;
       };
       const uint32_t a_bytes = (uint32_t)(kTile * kbytes);
       const uint32_t afull = bar0 + 8u * 10;
@@ -495,31 +496,40 @@ __global__ void __launch_bounds__(32 * (2 + 4 * tc_rg(MG)), 1)
       const uint32_t sbo = 128u * (uint32_t)(kbytes >> 4);
       const uint32_t segoff = (uint32_t)(tp.kseg * ES * 8);      // K segment start, bytes
       const int nk = tp.kseg / KMMA;                              // MMAs per chain
+      const uint32_t segcols = (uint32_t)(tp.kseg * ES / 4);      // K segment start, TMEM columns
+      // the projection operand once into TMEM columns 2 kNtile .. (one
+      // tcgen05.cp per 32 bytes of K: 8 columns of 128 lanes), so that the
+      // MMAs read only the core blocks from shared memory
+      const uint32_t at0 = tmem + 2u * kNtile;
       bool ok = mbar_wait(afull, 0);
+      if (ok)
+        for (int j = 0; j < kbytes / 32; ++j)
+          asm volatile("tcgen05.cp.cta_group::1.128x256b [%0], %1;" ::"r"(at0 + 8u * j),
+                       "l"(smem_desc(smem_u32(sA) + 256u * j, sbo))
+                       : "memory");
       for (int b = 0; ok && b < nblk; ++b) {
         const int s = b % kBStages, t = b & 1;
         if (!mbar_wait(bar0 + 8u * s, (uint32_t)((b / kBStages) & 1))) { ok = false; break; }
-        ++consumed[s];
+        nC = b + 1;
         if (b >= 2 && !mbar_wait(bar0 + 8u * (8 + t), (uint32_t)(((b - 2) >> 1) & 1))) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t d = tmem + (uint32_t)(t * kNtile);
-        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB + s * blk_bytes);
+        const uint32_t b0 = smem_u32(sB + s * blk_bytes);
 #pragma unroll
         for (int c = 0; c < NCHAIN; ++c) {
           // chains (hi, hi), (hi, lo), (lo, hi) of (A segment, B segment)
-          const uint32_t ao = a0 + (c == 2 ? segoff : 0u), bo = b0 + (c == 1 ? segoff : 0u);
+          const uint32_t at = at0 + (c == 2 ? segcols : 0u), bo = b0 + (c == 1 ? segoff : 0u);
           for (int ks = 0; ks < nk; ++ks) {
-            const uint64_t ad = smem_desc(ao + ks * 256, sbo);
             const uint64_t bd = smem_desc(bo + ks * 256, sbo);
             const uint32_t accum = (c > 0 || ks > 0) ? 1u : 0u;
             if (PREC == TS_PREC_BF16X2)
               asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                           "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-                           "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+                           "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+                           "r"(at + 8u * ks), "l"(bd), "r"(idesc), "r"(accum));
             else
               asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                           "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-                           "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+                           "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+                           "r"(at + 8u * ks), "l"(bd), "r"(idesc), "r"(accum));
           }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -539,7 +549,9 @@ __global__ void __launch_bounds__(32 * (2 + 4 * tc_rg(MG)), 1)
                        bar0 + 8u * 11) : "memory");
       if (!mbar_wait(bar0 + 8u * 11, 0)) *abort_v = 1;
       for (int s = 0; s < kBStages; ++s)
-        for (int u = consumed[s]; u < loaded[s]; ++u) mbar_wait(bar0 + 8u * s, (uint32_t)(u & 1));
+        // uses u of slot s (block s + u kBStages, phase u) copied but not consumed
+        for (int u = nC > s ? (nC - 1 - s) / kBStages + 1 : 0; u < (nB > s ? (nB - 1 - s) / kBStages + 1 : 0); ++u)
+          mbar_wait(bar0 + 8u * s, (uint32_t)(u & 1));
       if (!ok) mbar_wait(afull, 0);
     }
   } else if (warp == 1) {
@@ -550,7 +562,7 @@ __global__ void __launch_bounds__(32 * (2 + 4 * tc_rg(MG)), 1)
       const uint32_t chunk = (uint32_t)(kTile * tp.VS * 8);
       const float2* vt = vtiles + ((size_t)k * gridDim.x + blockIdx.x) * tp.v_bytes_per_tile / 8;
       bool ok = true;
-      int last[kVStages] = {-1, -1, -1, -1};
+      int nV = 0;                                 // blocks whose rows were copied
       for (int b = 0; b < nblk; ++b) {
         const int slot = b % tp.vstages;
         if (b >= tp.vstages && !mbar_wait(bar0 + 8u * (16 + slot), (uint32_t)(((b / tp.vstages) - 1) & 1))) {
@@ -565,12 +577,13 @@ __global__ void __launch_bounds__(32 * (2 + 4 * tc_rg(MG)), 1)
                 smem_u32(sV + (size_t)slot * kTile * tp.VS)),
             "l"(vt + (size_t)b * kTile * tp.VS), "r"(chunk), "r"(vfull)
             : "memory");
-        last[slot] = b;
+        nV = b + 1;
       }
       if (!ok) *abort_v = 1;
       // drain: the copies of the last block of each slot have landed
       for (int sl = 0; sl < kVStages; ++sl)
-        if (last[sl] >= 0) mbar_wait(bar0 + 8u * (12 + sl), (uint32_t)((last[sl] / tp.vstages) & 1));
+        if (sl < tp.vstages && sl < nV)
+          mbar_wait(bar0 + 8u * (12 + sl), (uint32_t)(((nV - 1 - sl) / tp.vstages) & 1));
     }
   } else if constexpr (SERVE) {
     // ---------------- serving links: the rows of H~_ii (subcarrier t_in, rows
@@ -699,7 +712,7 @@ __global__ void __launch_bounds__(32 * (2 + 4 * tc_rg(MG)), 1)
     }
   }
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kNtile));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(4 * kNtile));
 }
 
 // Layout of the operand buffer: the core operand of every link, the
