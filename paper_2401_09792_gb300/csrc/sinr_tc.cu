@@ -20,12 +20,14 @@
 //
 // k_sinr_link_tc: one CTA per (tile, UE i, interfering BS k), warp
 // specialised.  Warp 0, one thread: bulk copies (cp.async.bulk, mbarrier
-// transaction counts) of the projection operand and of the core operand in
-// blocks of CB columns of H~ (N = 64 accumulator columns) into a three-slot
-// ring, and the MMAs of each block into one of two TMEM buffers.  Warp 1,
-// one thread: the precoder rows of each block for the tile's subcarriers,
-// laid out contiguously once per call by k_v_tiles, one bulk copy per block
-// into a ring of up to four slots.  Warps 2 .. 1 + 4 RG (RG row groups of RPT rows): thread
+// transaction counts) of the projection operand (staged in the second core
+// slot, then copied once into TMEM with tcgen05.cp) and of the core operand
+// in blocks of CB columns of H~ (N = 128 accumulator columns) into a
+// two-slot ring, and the MMAs of each block (A from TMEM, B from shared
+// memory) into one of two TMEM buffers.  Warp 1, one thread: the precoder
+// rows of each block for the tile's subcarriers, laid out contiguously once
+// per call by k_v_tiles, one bulk copy per block into a ring of one to four
+// slots.  Warps 2 .. 1 + 4 RG (RG row groups of RPT rows): thread
 // (lane quadrant, group g) owns subcarrier t of the tile and rows
 // g RPT .. g RPT + RPT - 1; per block it reads its H~ rows from TMEM
 // (tcgen05.ld, one column at a time) and accumulates E += H~ V~, then frees
@@ -48,14 +50,21 @@ namespace detail {
 namespace {
 
 constexpr int kTile = 128;     // subcarriers per CTA = MMA M = TMEM lanes
-constexpr int kNtile = 64;     // accumulator columns per block (MMA N)
-constexpr int kBStages = 3;    // core-operand ring
-constexpr int kVStages = 4;    // precoder-row ring (at most; fewer when shared memory is short)
+constexpr int kNtile = 128;    // accumulator columns per block (MMA N)
+constexpr int kBStages = 2;    // core-operand ring
+// A tcgen05.mma of kind::tf32 with M = 128 and K = 8 takes about as long
+// for N = 64 as for N = 128 (a fixed issue cost of ~110 cycles on GB300,
+// measured), so N = 128 halves the MMA time per column; the core ring then
+// holds two 64 KB blocks, and the projection operand (the same size, as
+// kTile = kNtile) is staged in the second until it is copied into TMEM.
+static_assert(kTile == kNtile, "the projection operand is staged in a core slot");
+static_assert(kBStages == 2, "mbarrier layout and projection staging assume two core slots");
+constexpr int kVStages = 4;    // precoder-row ring (at most; down to one when shared memory is short)
 constexpr long kSpinLimit = 1L << 24;
 
 __host__ __device__ constexpr int tc_rpt(int MG) { return MG < 8 ? MG : 8; }
 __host__ __device__ constexpr int tc_rg(int MG) { return MG / tc_rpt(MG); }
-// H~ columns per block: N = 2 MG CB = 64
+// H~ columns per block: N = 2 MG CB = kNtile
 __host__ __device__ constexpr int tc_cb(int MG) { return kNtile / (2 * MG); }
 __host__ __device__ constexpr int tc_es(int prec) { return prec == TS_PREC_BF16X2 ? 2 : 4; }
 __host__ __device__ constexpr int tc_nseg(int prec) { return prec == TS_PREC_TF32 ? 1 : 2; }
@@ -68,7 +77,7 @@ struct TcPlan {
   int nblk;        // column blocks = ceil(n / CB)
   int VS;          // row stride of one subcarrier's precoder rows of a block
                    // (float2): CB L, or CB L + 2 (see v_piece)
-  int vstages;     // slots of the precoder-row ring (2 .. kVStages)
+  int vstages;     // slots of the precoder-row ring (1 .. kVStages)
   int nthreads;    // 32 (2 + 4 RG): MMA warp, precoder-row warp, epilogue warps
   int off_A, off_B, off_V, off_bar, smem;   // byte offsets
   size_t prep_bytes_per_link;               // k_core_prep output per link
@@ -89,12 +98,12 @@ inline TcPlan tc_plan(int MG, int L, int n, int p, int prec) {
   if ((t.VS / 2) % 8 != 0 && (t.VS / 2) % 2 == 0) t.VS += 2;
   t.nthreads = 32 * (2 + 4 * tc_rg(MG));
   int o = 0;
-  t.off_A = o; o += kTile * t.kbytes;
   t.off_B = o; o += kBStages * kNtile * t.kbytes;
+  t.off_A = t.off_B + (kBStages - 1) * kNtile * t.kbytes;     // staged in the last core slot
   // as many precoder-row slots as fit beside the operands (227 KB per CTA,
   // 1 KB of it static)
   t.vstages = kVStages;
-  while (t.vstages > 2 && o + t.vstages * kTile * t.VS * 8 + 24 * 8 + 16 > 226 * 1024) --t.vstages;
+  while (t.vstages > 1 && o + t.vstages * kTile * t.VS * 8 + 24 * 8 + 16 > 226 * 1024) --t.vstages;
   t.off_V = o; o += t.vstages * kTile * t.VS * 8;
   o = (o + 15) & ~15;
   t.off_bar = o; o += 24 * 8;
@@ -179,7 +188,7 @@ __global__ void k_wait_selftest(long limit, int arrive, int* out) {
 //   re row: [Re G ; -Im G],   im row: [Im G ; Re G]
 // segment 0 the rounded value (hi), segment 1 the rounded remainder (lo).
 // One CTA per (link, block): the block's core slab G[q][a][c0 .. c0+CB) is
-// staged in shared memory with coalesced loads (MG CB = 32 complex per q),
+// staged in shared memory with coalesced loads (MG CB = 64 complex per q),
 // then every thread writes 16-byte chunks of the block; padding is zero.
 template <int PREC>
 __global__ void __launch_bounds__(256) k_core_prep(const float2* __restrict__ G, int m, int n, int p,
@@ -187,7 +196,7 @@ __global__ void __launch_bounds__(256) k_core_prep(const float2* __restrict__ G,
                                                    unsigned char* __restrict__ out) {
   constexpr int ES = tc_es(PREC);
   constexpr int EPC = 16 / ES;                    // elements per 16-byte chunk
-  __shared__ float2 Gs[32 * 32];                  // [q][a][cl], p <= 32, MG CB = 32
+  __shared__ float2 Gs[32 * (kNtile / 2)];        // [q][a][cl], p <= 32, MG CB = kNtile / 2
   const int nkc = kbytes / 16;
   const int RPT = tc_rpt(MG), RG = tc_rg(MG), CB = tc_cb(MG);
   const int nchunk = kNtile * nkc;
@@ -384,7 +393,7 @@ __global__ void k_v_tiles(const float2* __restrict__ V, int J, int K, int n, int
 }
 
 // ----------------------------------------------------------- link kernel
-constexpr int kBars = 20;      // mbarriers of the link kernel (see below)
+constexpr int kBars = 21;      // mbarriers of the link kernel (see below)
 
 // One accumulator column group of a row group: the 2 RPT FP32 words (re, im
 // of RPT rows of H~) of this thread's TMEM lane, starting at column taddr.
@@ -432,11 +441,12 @@ __global__ void __launch_bounds__(32 * (2 + 4 * tc_rg(MG)), 1)
   unsigned char* sA = smem + tp.off_A;
   unsigned char* sB = smem + tp.off_B;
   float2* sV = reinterpret_cast<float2*>(smem + tp.off_V);
-  // mbarriers: 0..2 core block loaded, 3..5 its MMAs done (slot free),
+  // mbarriers: 0, 1 core block loaded, 3, 4 its MMAs done (slot free),
   // 6, 7 TMEM buffer written, 8, 9 TMEM buffer read (one arrival per
   // epilogue warp), 10 projection operand loaded, 11 final drain,
   // 12..15 precoder rows of a block loaded, 16..19 read (one arrival per
-  // epilogue warp)
+  // epilogue warp), 20 projection operand copied into TMEM (its staging
+  // slot free for core blocks)
   const uint32_t bar0 = smem_u32(smem + tp.off_bar);
   const size_t blk_bytes = (size_t)kNtile * kbytes;
   const unsigned char* prep_ch = prep + (size_t)ch * nblk * blk_bytes;
@@ -448,7 +458,7 @@ __global__ void __launch_bounds__(32 * (2 + 4 * tc_rg(MG)), 1)
     if (!SERVE && A.rcount != nullptr && blockIdx.x == 0 && i == 0 && z == 0) *A.rcount = 0;
     for (int s = 0; s < kBars; ++s)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar0 + 8u * s),
-                   "r"((s == 8 || s == 9 || s >= 16) ? (uint32_t)NEPI : 1u));
+                   "r"((s == 8 || s == 9 || (s >= 16 && s < 20)) ? (uint32_t)NEPI : 1u));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -489,7 +499,7 @@ __global__ void __launch_bounds__(32 * (2 + 4 * tc_rg(MG)), 1)
           "r"(a_bytes),
           "r"(afull)
           : "memory");
-      for (int b = 0; b < kBStages && b < nblk; ++b) issue_B(b);
+      for (int b = 0; b < kBStages - 1 && b < nblk; ++b) issue_B(b);
       const uint32_t idesc = (1u << 4) | ((PREC == TS_PREC_BF16X2 ? 1u : 2u) << 7) |
                              ((PREC == TS_PREC_BF16X2 ? 1u : 2u) << 10) | ((uint32_t)(kNtile >> 3) << 17) |
                              ((uint32_t)(kTile >> 4) << 24);
@@ -502,11 +512,19 @@ __global__ void __launch_bounds__(32 * (2 + 4 * tc_rg(MG)), 1)
       // MMAs read only the core blocks from shared memory
       const uint32_t at0 = tmem + 2u * kNtile;
       bool ok = mbar_wait(afull, 0);
-      if (ok)
+      if (ok) {
         for (int j = 0; j < kbytes / 32; ++j)
           asm volatile("tcgen05.cp.cta_group::1.128x256b [%0], %1;" ::"r"(at0 + 8u * j),
                        "l"(smem_desc(smem_u32(sA) + 256u * j, sbo))
                        : "memory");
+        // the staging slot is refilled with core blocks once the copies
+        // have read it
+        const uint32_t acopied = bar0 + 8u * 20;
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(acopied)
+                     : "memory");
+        ok = mbar_wait(acopied, 0);
+      }
+      if (ok && kBStages - 1 < nblk) issue_B(kBStages - 1);
       for (int b = 0; ok && b < nblk; ++b) {
         const int s = b % kBStages, t = b & 1;
         if (!mbar_wait(bar0 + 8u * s, (uint32_t)((b / kBStages) & 1))) { ok = false; break; }
@@ -518,9 +536,13 @@ __global__ void __launch_bounds__(32 * (2 + 4 * tc_rg(MG)), 1)
 #pragma unroll
         for (int c = 0; c < NCHAIN; ++c) {
           // chains (hi, hi), (hi, lo), (lo, hi) of (A segment, B segment)
-          const uint32_t at = at0 + (c == 2 ? segcols : 0u), bo = b0 + (c == 1 ? segoff : 0u);
+          const uint32_t at = at0 + (c == 2 ? segcols : 0u);
+          // descriptor of the chain's first K step; a K step (256 bytes)
+          // adds 16 to its 14-bit start-address field (no carry: shared
+          // addresses stay below 2^18)
+          const uint64_t bdc = smem_desc(b0 + (c == 1 ? segoff : 0u), sbo);
           for (int ks = 0; ks < nk; ++ks) {
-            const uint64_t bd = smem_desc(bo + ks * 256, sbo);
+            const uint64_t bd = bdc + 16ull * ks;
             const uint32_t accum = (c > 0 || ks > 0) ? 1u : 0u;
             if (PREC == TS_PREC_BF16X2)
               asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
