@@ -473,21 +473,7 @@ __global__ void __launch_bounds__(32 * (2 + 4 * tc_rg(MG)), 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      // ---------------- loads and MMAs (one thread)
-      // core blocks 0 .. nB - 1 copied (in order), 0 .. nC - 1 consumed
-      int nB = 0, nC = 0;
-      auto issue_B = [&](int b) {
-        const int s = b % kBStages;
-        const uint32_t bar = bar0 + 8u * s;
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                     "r"((uint32_t)blk_bytes) : "memory");
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                smem_u32(sB + s * blk_bytes)),
-            "l"(prep_ch + (size_t)b * blk_bytes), "r"((uint32_t)blk_bytes), "r"(bar)
-            : "memory");
-        nB = b + 1;
-      };
+      // ---------------- projection operand and MMAs (one thread)
       const uint32_t a_bytes = (uint32_t)(kTile * kbytes);
       const uint32_t afull = bar0 + 8u * 10;
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(afull), "r"(a_bytes)
@@ -499,7 +485,6 @@ __global__ void __launch_bounds__(32 * (2 + 4 * tc_rg(MG)), 1)
           "r"(a_bytes),
           "r"(afull)
           : "memory");
-      for (int b = 0; b < kBStages - 1 && b < nblk; ++b) issue_B(b);
       const uint32_t idesc = (1u << 4) | ((PREC == TS_PREC_BF16X2 ? 1u : 2u) << 7) |
                              ((PREC == TS_PREC_BF16X2 ? 1u : 2u) << 10) | ((uint32_t)(kNtile >> 3) << 17) |
                              ((uint32_t)(kTile >> 4) << 24);
@@ -509,7 +494,8 @@ __global__ void __launch_bounds__(32 * (2 + 4 * tc_rg(MG)), 1)
       const uint32_t segcols = (uint32_t)(tp.kseg * ES / 4);      // K segment start, TMEM columns
       // the projection operand once into TMEM columns 2 kNtile .. (one
       // tcgen05.cp per 32 bytes of K: 8 columns of 128 lanes), so that the
-      // MMAs read only the core blocks from shared memory
+      // MMAs read only the core blocks from shared memory; its staging slot
+      // takes core blocks once the copies have read it (barrier 20)
       const uint32_t at0 = tmem + 2u * kNtile;
       bool ok = mbar_wait(afull, 0);
       if (ok) {
@@ -517,18 +503,12 @@ __global__ void __launch_bounds__(32 * (2 + 4 * tc_rg(MG)), 1)
           asm volatile("tcgen05.cp.cta_group::1.128x256b [%0], %1;" ::"r"(at0 + 8u * j),
                        "l"(smem_desc(smem_u32(sA) + 256u * j, sbo))
                        : "memory");
-        // the staging slot is refilled with core blocks once the copies
-        // have read it
-        const uint32_t acopied = bar0 + 8u * 20;
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(acopied)
-                     : "memory");
-        ok = mbar_wait(acopied, 0);
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         bar0 + 8u * 20) : "memory");
       }
-      if (ok && kBStages - 1 < nblk) issue_B(kBStages - 1);
       for (int b = 0; ok && b < nblk; ++b) {
         const int s = b % kBStages, t = b & 1;
         if (!mbar_wait(bar0 + 8u * s, (uint32_t)((b / kBStages) & 1))) { ok = false; break; }
-        nC = b + 1;
         if (b >= 2 && !mbar_wait(bar0 + 8u * (8 + t), (uint32_t)(((b - 2) >> 1) & 1))) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t d = tmem + (uint32_t)(t * kNtile);
@@ -558,51 +538,63 @@ __global__ void __launch_bounds__(32 * (2 + 4 * tc_rg(MG)), 1)
                          bar0 + 8u * (6 + t)) : "memory");
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          bar0 + 8u * (3 + s)) : "memory");
-        // refill the slot of block b - 1 once its MMAs are done
-        if (b >= 1 && b - 1 + kBStages < nblk) {
-          const int s1 = (b - 1) % kBStages;
-          if (!mbar_wait(bar0 + 8u * (3 + s1), (uint32_t)(((b - 1) / kBStages) & 1))) { ok = false; break; }
-          issue_B(b - 1 + kBStages);
-        }
       }
       if (!ok) *abort_v = 1;
-      // drain: every MMA issued so far has completed, every copy has landed
+      // drain: every MMA and copy into TMEM issued so far has completed
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                        bar0 + 8u * 11) : "memory");
       if (!mbar_wait(bar0 + 8u * 11, 0)) *abort_v = 1;
-      for (int s = 0; s < kBStages; ++s)
-        // uses u of slot s (block s + u kBStages, phase u) copied but not consumed
-        for (int u = nC > s ? (nC - 1 - s) / kBStages + 1 : 0; u < (nB > s ? (nB - 1 - s) / kBStages + 1 : 0); ++u)
-          mbar_wait(bar0 + 8u * s, (uint32_t)(u & 1));
       if (!ok) mbar_wait(afull, 0);
     }
   } else if (warp == 1) {
-    // ---------------- precoder rows: one bulk copy per block of the tile's
-    // rows (k_v_tiles laid them out contiguously), into a ring shared by
-    // the row groups (idle for the serving links)
-    if (!SERVE && lane == 0) {
+    // ---------------- core blocks and precoder rows, in block order: core
+    // block b once the MMAs of block b - kBStages have read its slot (the
+    // last slot first once the projection operand is in TMEM), the
+    // precoder rows of block b (k_v_tiles laid them out contiguously) once
+    // the epilogue has read its slot of the ring
+    if (lane == 0) {
       const uint32_t chunk = (uint32_t)(kTile * tp.VS * 8);
-      const float2* vt = vtiles + ((size_t)k * gridDim.x + blockIdx.x) * tp.v_bytes_per_tile / 8;
+      const float2* vt = SERVE ? nullptr : vtiles + ((size_t)k * gridDim.x + blockIdx.x) * tp.v_bytes_per_tile / 8;
       bool ok = true;
-      int nV = 0;                                 // blocks whose rows were copied
+      int nB = 0, nV = 0;                          // blocks whose copies were issued
       for (int b = 0; b < nblk; ++b) {
-        const int slot = b % tp.vstages;
-        if (b >= tp.vstages && !mbar_wait(bar0 + 8u * (16 + slot), (uint32_t)(((b / tp.vstages) - 1) & 1))) {
+        const int s = b % kBStages;
+        if (b == kBStages - 1 && !mbar_wait(bar0 + 8u * 20, 0)) { ok = false; break; }
+        if (b >= kBStages && !mbar_wait(bar0 + 8u * (3 + s), (uint32_t)(((b / kBStages) - 1) & 1))) {
           ok = false;
           break;
         }
-        const uint32_t vfull = bar0 + 8u * (12 + slot);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(vfull), "r"(chunk)
-                     : "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar0 + 8u * s),
+                     "r"((uint32_t)blk_bytes) : "memory");
         asm volatile(
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                smem_u32(sV + (size_t)slot * kTile * tp.VS)),
-            "l"(vt + (size_t)b * kTile * tp.VS), "r"(chunk), "r"(vfull)
+                smem_u32(sB + s * blk_bytes)),
+            "l"(prep_ch + (size_t)b * blk_bytes), "r"((uint32_t)blk_bytes), "r"(bar0 + 8u * s)
             : "memory");
-        nV = b + 1;
+        nB = b + 1;
+        if constexpr (!SERVE) {
+          const int slot = b % tp.vstages;
+          if (b >= tp.vstages && !mbar_wait(bar0 + 8u * (16 + slot), (uint32_t)(((b / tp.vstages) - 1) & 1))) {
+            ok = false;
+            break;
+          }
+          const uint32_t vfull = bar0 + 8u * (12 + slot);
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(vfull), "r"(chunk)
+                       : "memory");
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                  smem_u32(sV + (size_t)slot * kTile * tp.VS)),
+              "l"(vt + (size_t)b * kTile * tp.VS), "r"(chunk), "r"(vfull)
+              : "memory");
+          nV = b + 1;
+        }
       }
       if (!ok) *abort_v = 1;
-      // drain: the copies of the last block of each slot have landed
+      // drain: the last copy of every slot has landed (each slot has at
+      // most one phase outstanding: a copy is issued only after the
+      // previous one into its slot was consumed)
+      for (int sl = 0; sl < kBStages; ++sl)
+        if (sl < nB) mbar_wait(bar0 + 8u * sl, (uint32_t)(((nB - 1 - sl) / kBStages) & 1));
       for (int sl = 0; sl < kVStages; ++sl)
         if (sl < tp.vstages && sl < nV)
           mbar_wait(bar0 + 8u * (12 + sl), (uint32_t)(((nV - 1 - sl) / tp.vstages) & 1));
@@ -674,13 +666,12 @@ __global__ void __launch_bounds__(32 * (2 + 4 * tc_rg(MG)), 1)
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const float2* vb = sV + ((size_t)slot * kTile + t_in) * tp.VS;
       const int ncb = min(CB, n - b * CB);       // columns of this block (uniform)
+      const uint32_t tcol = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(t * kNtile + g * 2 * RPT);
 #pragma unroll
       for (int cc = 0; cc < CB; ++cc) {
         if (cc >= ncb) break;
-        uint32_t h[2 * RPT];
-        tmem_ld_rows<RPT>(tmem + ((uint32_t)(quad * 32) << 16) +
-                              (uint32_t)(t * kNtile + (cc * RG + g) * 2 * RPT),
-                          h);
+        uint32_t hc[2 * RPT];
+        tmem_ld_rows<RPT>(tcol + (uint32_t)(cc * RG * 2 * RPT), hc);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
         for (int l2 = 0; l2 < LT / 2; ++l2) {
@@ -689,7 +680,7 @@ __global__ void __launch_bounds__(32 * (2 + 4 * tc_rg(MG)), 1)
           const float2 v0 = make_float2(v.x, v.y), v1 = make_float2(v.z, v.w);
 #pragma unroll
           for (int r = 0; r < RPT; ++r) {
-            const float2 hv = make_float2(__uint_as_float(h[2 * r]), __uint_as_float(h[2 * r + 1]));
+            const float2 hv = make_float2(__uint_as_float(hc[2 * r]), __uint_as_float(hc[2 * r + 1]));
             cmac(E[r][2 * l2], hv, v0);
             cmac(E[r][2 * l2 + 1], hv, v1);
           }
