@@ -287,6 +287,78 @@ __device__ __forceinline__ void jacobi_sweep16(float2 (&S)[16], float2 (&U)[16],
   }
 }
 
+// S scaled to unit trace (eigenvectors and eigenvalue ratios are unchanged;
+// the singular values are taken from W = U* H~)
+template <int MG>
+__device__ __forceinline__ void scale_unit_trace(float2 (&S)[MG], int a) {
+  const float tr = gsum<MG>(pick(S, a).x);
+  const float sc = tr > 0.f ? 1.f / tr : 1.f;
+#pragma unroll
+  for (int b = 0; b < MG; ++b) S[b] = cscale(S[b], sc);
+}
+
+// Cyclic Jacobi on S held in registers (see jacobi_step), accumulating the
+// rotations into U, until the relative off-diagonal norm is below ~5e-7,
+// then one more sweep: Jacobi converges quadratically, so that sweep takes
+// the off-diagonal from ~5e-7 to rounding level.  Without it a pair of
+// eigenvalues a relative gap g apart keeps its eigenvectors mixed by
+// ~5e-7 / g (up to 3e-4 in the per-stream SINR for g ~ 1e-3); with it the
+// mixing is the FP32 Gram's own ~u / g.  The stopping decision is taken
+// warp-wide (extra sweeps leave a converged S unchanged).  Returns whether
+// this group's S converged.
+template <int MG>
+__device__ __forceinline__ bool jacobi_eig(float2 (&S)[MG], float2 (&U)[MG], int a) {
+  const int max_sweeps = MG <= 8 ? 11 : 13;
+  bool polish = false, converged = false;
+  for (int sweep = 0;; ++sweep) {
+    float off = 0.f, dia = 0.f;
+#pragma unroll
+    for (int b = 0; b < MG; ++b) {
+      const float v = cabs2(S[b]);
+      if (b == a) dia += v; else off += v;
+    }
+    off = gsum<MG>(off);
+    dia = gsum<MG>(dia);
+    converged = off <= 2.3e-13f * dia;
+    const bool all = __all_sync(FULL, converged);
+    if ((all && polish) || sweep == max_sweeps) break;
+    polish = all;
+    float dg = pick(S, a).x;
+    if constexpr (MG == 16) {
+      jacobi_sweep16(S, U, dg, a);
+    } else {
+#pragma unroll
+      for (int t = 0; t < MG - 1; ++t) jacobi_step<MG>(t, S, U, dg, a);
+    }
+  }
+  return converged;
+}
+
+// The rotations come from hardware reciprocal square roots and each is
+// applied in FP32, so U leaves the sweeps unitary only to ~1e-7 .. 1e-6:
+// its columns drift from unit norm (the serving effective channel
+// E_kk = U_L Sigma_L scales with them) and from each other (which the
+// close-pair rotation would amplify by lambda / gap).  One pass of modified
+// Gram-Schmidt over the columns makes U unitary to rounding; it moves each
+// column by the size of its defect only.
+template <int MG>
+__device__ __forceinline__ void orthonormalize_columns(float2 (&U)[MG]) {
+#pragma unroll
+  for (int b = 0; b < MG; ++b) {
+    const float nb = gsum<MG>(cabs2(U[b]));
+    U[b] = cscale(U[b], nb > 0.f ? 1.f / sqrtf(nb) : 1.f);
+#pragma unroll
+    for (int b2 = b + 1; b2 < MG; ++b2) {
+      // U[:, b2] -= (U[:, b]* U[:, b2]) U[:, b]
+      float2 pr = cz();
+      cmacc(pr, U[b2], U[b]);                     // U_ab2 conj(U_ab)
+      pr.x = gsum<MG>(pr.x);
+      pr.y = gsum<MG>(pr.y);
+      cms(U[b2], pr, U[b]);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ phase 1
 // k_svd_precoder: one group of MG lanes per (BS k, subcarrier).  Forms the
 // serving link's compressed channel H~_kk (or reads it from workspace: large
@@ -398,13 +470,123 @@ __device__ __forceinline__ void serve_channels(const SinrArgs& A, const Precoder
   }
 }
 
-// PHASE 0: the whole precoder in one kernel.  PHASE 1 (serving channels
-// from the serving pass): Gram, Jacobi and Gram-Schmidt only, the Gram
-// accumulated over column chunks of H~ staged a chunk at a time, so that a
-// CTA holds little shared memory and many units hide the Jacobi's latency;
-// U and the eigenvalues go to workspace.  PHASE 2: the rest from the stored
-// U (W = U* H~, refinement, close pairs, V~, E_kk), with H~ staged whole.
-constexpr int kEigChunk = 16;   // columns of H~ per staged chunk in PHASE 1
+// PHASE 0: the whole precoder in one kernel.  Serving channels from the
+// serving pass take two kernels: k_svd_eig (Gram, Jacobi and Gram-Schmidt
+// only, the Gram accumulated over column chunks of H~ staged a chunk at a
+// time, so that a CTA holds little shared memory and many units hide the
+// Jacobi's latency; U and the eigenvalues go to workspace), then PHASE 2:
+// the rest from the stored U (W = U* H~, refinement, close pairs, V~, E_kk),
+// with H~ staged whole.
+constexpr int kEigChunk = 16;   // columns of H~ per staged chunk in k_svd_eig
+// Subcarriers per warm-started run of the eigensolve: runs start at
+// subcarriers (global index, kap_off included) that are multiples of it, so
+// that a subcarrier's result does not depend on the extent of the call.
+constexpr int kEigRun = 4;
+
+// The eigensolve of the two-kernel precoder, with warm starts: group g of MG lanes
+// walks the subcarriers of one run of kEigRun adjacent ones (BS k); the
+// first of the run is diagonalised from U = I, each later one from the
+// previous subcarrier's eigenvectors, S <- U* S U with U kept as the start
+// of the rotations.  Adjacent subcarriers have nearly the same Gram, so S
+// starts almost diagonal and the sweeps to the same stopping rule drop from
+// six or seven to about three; the transform costs less than half a sweep.
+// The Gram of every subcarrier is accumulated over column chunks of H~
+// (all groups together, as in k_svd_precoder), U and its product with S
+// pass through shared memory.  Writes U (row a in lane a), the eigenvalues
+// and the convergence of every unit, which k_svd_precoder<MG, LT, 2> reads.
+template <int MG>
+__global__ void __launch_bounds__(kThreads, 4) k_svd_eig(const SinrArgs A, int T, int SS, int off_U, int off_T) {
+  extern __shared__ __align__(16) float2 sm[];
+  const int tid = threadIdx.x, g = tid / MG, a = tid % MG;
+  const int nth = blockDim.x;
+  const int k = blockIdx.y;
+  const int m = A.m, n = A.n, K = A.K;
+  // global subcarrier of the CTA's first run start (runs aligned globally)
+  const int lead = A.kap_off % kEigRun;                  // local units before the first aligned start
+  const int kbase = blockIdx.x * T * kEigRun - lead;     // local subcarrier of run slot 0 of group 0
+  const int CS = kEigChunk + 1;
+  float2* chunk = sm;                                    // [t][row][CS], all groups
+  float2* Ub = sm + off_U + g * MG * SS;                 // the group's U
+  float2* Tb = sm + off_T + g * MG * SS;                 // S U
+  float2 S[MG], U[MG];
+  for (int r = 0; r < kEigRun; ++r) {
+    const int kap = kbase + g * kEigRun + r;
+    // Gram S = H~ H~* over column chunks (row a in lane a; zero rows for
+    // a >= m and outside the call's subcarriers)
+#pragma unroll
+    for (int b = 0; b < MG; ++b) S[b] = cz();
+    for (int c0 = 0; c0 < n; c0 += kEigChunk) {
+      __syncthreads();                                   // previous chunk consumed
+      for (int idx = tid; idx < T * MG * kEigChunk; idx += nth) {
+        const int c = idx % kEigChunk, aa = (idx / kEigChunk) % MG, t = idx / (kEigChunk * MG);
+        const int kk = kbase + t * kEigRun + r;
+        float2 v = cz();
+        if (aa < m && kk >= 0 && kk < K && c0 + c < n)
+          v = A.Hserv[(((size_t)k * A.serv_stride * K + kk) * m + aa) * n + c0 + c];
+        chunk[(t * MG + aa) * CS + c] = v;
+      }
+      __syncthreads();
+      const float2* cg = chunk + g * MG * CS;
+#pragma unroll 4
+      for (int c = 0; c < kEigChunk; ++c) {
+        const float2 x = cg[a * CS + c];
+#pragma unroll
+        for (int b = 0; b < MG; ++b) cmacc(S[b], x, cg[b * CS + c]);
+      }
+    }
+    scale_unit_trace<MG>(S, a);
+    // A subcarrier whose predecessor lies outside the call (the first of
+    // the call, in a run that starts before it) starts from U = I, which the
+    // transform below maps S to itself exactly.  The branch is on r only:
+    // the groups of a warp may sit at different run offsets, and the
+    // transform synchronises the whole warp.
+    if (r == 0 || kap - 1 < 0) {
+#pragma unroll
+      for (int b = 0; b < MG; ++b) U[b] = make_float2(b == a ? 1.f : 0.f, 0.f);
+    }
+    if (r > 0) {
+      // S <- U* S U with the previous subcarrier's eigenvectors (row a of U
+      // and of S in lane a; U and S U through shared memory)
+#pragma unroll
+      for (int b = 0; b < MG; ++b) Ub[a * SS + b] = U[b];
+      __syncwarp();
+      float2 Tr[MG];
+#pragma unroll
+      for (int b = 0; b < MG; ++b) Tr[b] = cz();
+#pragma unroll
+      for (int c = 0; c < MG; ++c) {
+        const float2 sac = S[c];
+#pragma unroll
+        for (int b = 0; b < MG; ++b) cmac(Tr[b], sac, Ub[c * SS + b]);
+      }
+#pragma unroll
+      for (int b = 0; b < MG; ++b) Tb[a * SS + b] = Tr[b];
+      __syncwarp();
+#pragma unroll
+      for (int b = 0; b < MG; ++b) S[b] = cz();
+#pragma unroll
+      for (int c = 0; c < MG; ++c) {
+        const float2 uca = cconj(Ub[c * SS + a]);
+#pragma unroll
+        for (int b = 0; b < MG; ++b) cmac(S[b], uca, Tb[c * SS + b]);
+      }
+      // U again from shared memory (it was only read there), so that it
+      // need not stay in registers through the products
+#pragma unroll
+      for (int b = 0; b < MG; ++b) U[b] = Ub[a * SS + b];
+      __syncwarp();                                      // Ub, Tb read before the next unit writes them
+    }
+    const bool converged = jacobi_eig<MG>(S, U, a);
+    orthonormalize_columns<MG>(U);
+    if (kap >= 0 && kap < K) {
+      const size_t ueig = ((size_t)k * K + kap) * MG;
+#pragma unroll
+      for (int b = 0; b < MG; ++b) A.Ueig[(ueig + a) * MG + b] = U[b];
+      A.lam_eig[ueig + a] = pick(S, a).x;
+      if (a == 0) A.conv_eig[(size_t)k * K + kap] = converged ? 1 : 0;
+    }
+  }
+}
 
 template <int MG, int LT, int PHASE>
 __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, const PrecoderPlan pl) {
@@ -423,36 +605,9 @@ __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, con
 
   float2 S[MG], U[MG];
   bool converged = false;
-  if (PHASE == 1) {
-    // Gram over column chunks: chunk [t][row][kEigChunk + 1] in the Hs region
-#pragma unroll
-    for (int b = 0; b < MG; ++b) S[b] = cz();
-    const int CS = kEigChunk + 1;
-    float2* ch = sm + pl.off_Hs;
-    for (int c0 = 0; c0 < n; c0 += kEigChunk) {
-      __syncthreads();                               // previous chunk consumed
-      for (int idx = tid; idx < T * MG * kEigChunk; idx += nth) {
-        const int c = idx % kEigChunk, aa = (idx / kEigChunk) % MG, t = idx / (kEigChunk * MG);
-        const int kk = kap0 + t;
-        float2 v = cz();
-        if (aa < m && kk < K && c0 + c < n)
-          v = A.Hserv[(((size_t)k * A.serv_stride * K + kk) * m + aa) * n + c0 + c];
-        ch[(t * MG + aa) * CS + c] = v;
-      }
-      __syncthreads();
-      const float2* cg = ch + g * MG * CS;
-#pragma unroll 4
-      for (int c = 0; c < kEigChunk; ++c) {
-        const float2 x = cg[a * CS + c];
-#pragma unroll
-        for (int b = 0; b < MG; ++b) cmacc(S[b], x, cg[b * CS + c]);
-      }
-    }
-  }
   // H~_kk rows of the T subcarriers (zero rows for a >= m and beyond K),
   // formed here or read from the all-link rebuild of the adjoint
-  if (PHASE == 1) {
-  } else if (A.fuse_serve) {
+  if (A.fuse_serve) {
     serve_channels<MG>(A, pl, k, kap0, sm);
   } else {
     for (int idx = tid; idx < T * MG * n; idx += nth) {
@@ -478,82 +633,12 @@ __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, con
       for (int b = 0; b < MG; ++b) cmacc(S[b], x, Hs[b * pl.SH + c]);
     }
   }
-  if (PHASE != 2) {
-
-  // scale S to unit trace (eigenvectors and eigenvalue ratios are unchanged;
-  // the singular values are taken from W below)
-  {
-    const float tr = gsum<MG>(pick(S, a).x);
-    const float sc = tr > 0.f ? 1.f / tr : 1.f;
-#pragma unroll
-    for (int b = 0; b < MG; ++b) S[b] = cscale(S[b], sc);
+  if (PHASE == 0) {
+    scale_unit_trace<MG>(S, a);
+    converged = jacobi_eig<MG>(S, U, a);
+    orthonormalize_columns<MG>(U);
   }
-  // Cyclic Jacobi on S held in registers (see jacobi_step), until the
-  // relative off-diagonal norm is below ~5e-7, then one more sweep: Jacobi
-  // converges quadratically, so that sweep takes the off-diagonal from
-  // ~5e-7 to rounding level.  Without it a pair of eigenvalues a relative
-  // gap g apart keeps its eigenvectors mixed by ~5e-7 / g (up to 3e-4 in
-  // the per-stream SINR for g ~ 1e-3); with it the mixing is the FP32
-  // Gram's own ~u / g.  The stopping decision is taken warp-wide (extra
-  // sweeps leave a converged S unchanged).
-  const int max_sweeps = MG <= 8 ? 11 : 13;
-  bool polish = false;
-  for (int sweep = 0;; ++sweep) {
-    float off = 0.f, dia = 0.f;
-#pragma unroll
-    for (int b = 0; b < MG; ++b) {
-      const float v = cabs2(S[b]);
-      if (b == a) dia += v; else off += v;
-    }
-    off = gsum<MG>(off);
-    dia = gsum<MG>(dia);
-    converged = off <= 2.3e-13f * dia;
-    const bool all = __all_sync(FULL, converged);
-    if ((all && polish) || sweep == max_sweeps) break;
-    polish = all;
-    float dg = pick(S, a).x;
-    if constexpr (MG == 16) {
-      jacobi_sweep16(S, U, dg, a);
-    } else {
-#pragma unroll
-      for (int t = 0; t < MG - 1; ++t) jacobi_step<MG>(t, S, U, dg, a);
-    }
-  }
-  // The rotations come from hardware reciprocal square roots and each is
-  // applied in FP32, so U leaves the sweeps unitary only to ~1e-7 .. 1e-6:
-  // its columns drift from unit norm (the serving effective channel
-  // E_kk = U_L Sigma_L below scales with them) and from each other (which
-  // the close-pair rotation below would amplify by lambda / gap).  One pass
-  // of modified Gram-Schmidt over the columns makes U unitary to rounding;
-  // it moves each column by the size of its defect only.
-  {
-#pragma unroll
-    for (int b = 0; b < MG; ++b) {
-      const float nb = gsum<MG>(cabs2(U[b]));
-      U[b] = cscale(U[b], nb > 0.f ? 1.f / sqrtf(nb) : 1.f);
-#pragma unroll
-      for (int b2 = b + 1; b2 < MG; ++b2) {
-        // U[:, b2] -= (U[:, b]* U[:, b2]) U[:, b]
-        float2 pr = cz();
-        cmacc(pr, U[b2], U[b]);                     // U_ab2 conj(U_ab)
-        pr.x = gsum<MG>(pr.x);
-        pr.y = gsum<MG>(pr.y);
-        cms(U[b2], pr, U[b]);
-      }
-    }
-  }
-  }  // PHASE != 2
   const size_t ueig = ((size_t)k * K + (kap < K ? kap : K - 1)) * MG;
-  if (PHASE == 1) {
-    // U (row a in lane a), the eigenvalues and the convergence to workspace
-    if (kap < K) {
-#pragma unroll
-      for (int b = 0; b < MG; ++b) A.Ueig[(ueig + a) * MG + b] = U[b];
-      A.lam_eig[ueig + a] = pick(S, a).x;
-      if (a == 0) A.conv_eig[(size_t)k * K + kap] = converged ? 1 : 0;
-    }
-    return;
-  }
   if (PHASE == 2) {
 #pragma unroll
     for (int b = 0; b < MG; ++b) {
@@ -1406,7 +1491,8 @@ __global__ void __launch_bounds__(kThreads) k_sinr_link_blk(const SinrArgs A, co
 // partial covariances, adds the noise (eq. 25) and evaluates the SINR.
 template <int MG, int LT, bool SVD>
 __global__ void __launch_bounds__(kThreads) k_sinr_finalize(const SinrArgs A, int T) {
-  __shared__ __align__(16) float2 sm_es[kThreads * LT + (kThreads / 2) * 2];
+  constexpr int kEsHalf = kThreads * LT + (kThreads / 2) * 2;
+  __shared__ __align__(16) float2 sm_es[2 * kEsHalf];
   const int tid = threadIdx.x, g = tid / MG, a = tid % MG;
   const int i = blockIdx.y;
   const int kap = blockIdx.x * T + g;
@@ -1414,29 +1500,54 @@ __global__ void __launch_bounds__(kThreads) k_sinr_finalize(const SinrArgs A, in
   const int kc = kap < K ? kap : K - 1;     // tail groups recompute the last subcarrier
   float2* Es = sm_es + g * (MG * LT + 2);
 
-  // R = sum_{k != i} E_ik E_ik* (eq. 25 without the serving term): row a of
-  // each interfering effective channel through the group's scratch
+  // R = sum_{k != i} E_ik E_ik* (eq. 25 without the serving term): the
+  // rows of each interfering effective channel through the group's scratch,
+  // two buffers, the next link's rows copied (cp.async) while the current
+  // one is accumulated; rows a >= m and streams l >= L stay zero
   float2 R[MG], Eself[LT];
 #pragma unroll
   for (int b = 0; b < MG; ++b) R[b] = cz();
+#pragma unroll
+  for (int l = 0; l < LT; ++l) {
+    Es[a * LT + l] = cz();
+    Es[kEsHalf + a * LT + l] = cz();
+  }
+  __syncwarp();
+  auto fetch = [&](int s) {
+    if (a < m) {
+      const float2* Ein = A.Eint + ((((size_t)i * (J - 1) + s) * K + kc) * m + a) * L;
+      float2* dst = Es + (s & 1) * kEsHalf + a * LT;
+      for (int l = 0; l < L; ++l) cp_async8(dst + l, Ein + l, true);
+    }
+    cp_async_commit();
+  };
+  if (J > 1) fetch(0);
   for (int s = 0; s < J - 1; ++s) {
-    float2 Er[LT];
-    const float2* Ein = A.Eint + ((((size_t)i * (J - 1) + s) * K + kc) * m + (a < m ? a : 0)) * L;
-#pragma unroll
-    for (int l = 0; l < LT; ++l) Er[l] = (a < m && l < L) ? Ein[l] : cz();
-#pragma unroll
-    for (int l = 0; l < LT; ++l) Es[a * LT + l] = Er[l];
+    if (s + 1 < J - 1) {
+      fetch(s + 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
     __syncwarp();
+    const float2* Eb = Es + (s & 1) * kEsHalf;
+    float2 Er[LT];
+#pragma unroll
+    for (int l2 = 0; l2 < LT / 2; ++l2) {
+      const float4 e = reinterpret_cast<const float4*>(Eb + a * LT)[l2];
+      Er[2 * l2] = make_float2(e.x, e.y);
+      Er[2 * l2 + 1] = make_float2(e.z, e.w);
+    }
 #pragma unroll
     for (int b = 0; b < MG; ++b) {
 #pragma unroll
       for (int l2 = 0; l2 < LT / 2; ++l2) {
-        const float4 e = reinterpret_cast<const float4*>(Es + b * LT)[l2];
+        const float4 e = reinterpret_cast<const float4*>(Eb + b * LT)[l2];
         cmacc(R[b], Er[2 * l2], make_float2(e.x, e.y));
         cmacc(R[b], Er[2 * l2 + 1], make_float2(e.z, e.w));
       }
     }
-    __syncwarp();
+    __syncwarp();                                 // buffer read before fetch(s + 2) refills it
   }
   // serving effective channel E_ii (eq. 24), from the precoder phase (svd)
   // or from the serving-link pass of k_sinr_link (wideband precoder)
@@ -1524,14 +1635,16 @@ cudaError_t run_precoder(const SinrArgs& A, cudaStream_t s) {
   if (!fused && A.Ueig != nullptr) {
     // two phases: the eigensolve with little shared memory per CTA (many
     // units resident), then the rest with H~ staged whole
-    const int T1 = kThreads / MG;
-    PrecoderPlan p1 = precoder_plan(MG, T1, kEigChunk, A.p, false);
-    p1.total = T1 * MG * (kEigChunk + 1);         // PHASE 1 uses the chunk region only
-    const size_t smem1 = (size_t)p1.total * sizeof(float2);
-    auto k1 = k_svd_precoder<MG, LT, 1>;
+    // (the eigensolve in warm-started runs of kEigRun adjacent subcarriers,
+    // aligned to the global subcarrier index)
+    const int T1 = kThreads / MG, SS = MG + 1;
+    const int off_U = T1 * MG * (kEigChunk + 1), off_T = off_U + T1 * MG * SS;
+    const size_t smem1 = (size_t)(off_T + T1 * MG * SS) * sizeof(float2);
+    const int runs = (A.K + A.kap_off % kEigRun + kEigRun - 1) / kEigRun;
+    auto k1 = k_svd_eig<MG>;
     cudaError_t e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
     if (e != cudaSuccess) return e;
-    k1<<<dim3((A.K + T1 - 1) / T1, A.J), T1 * MG, smem1, s>>>(A, p1);
+    k1<<<dim3((runs + T1 - 1) / T1, A.J), T1 * MG, smem1, s>>>(A, T1, SS, off_U, off_T);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     auto k2 = k_svd_precoder<MG, LT, 2>;
     if ((e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)

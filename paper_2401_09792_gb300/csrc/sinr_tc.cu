@@ -601,43 +601,44 @@ __global__ void __launch_bounds__(32 * (2 + 4 * tc_rg(MG)), 1)
     }
   } else if constexpr (SERVE) {
     // ---------------- serving links: the rows of H~_ii (subcarrier t_in, rows
-    // of group g) from TMEM to Hserv, two adjacent columns per store
+    // of group g) from TMEM to Hserv, four adjacent columns (one 32-byte
+    // sector) per store where rows are 32-byte aligned (n a multiple of 4)
+    static_assert(tc_cb(MG) % 4 == 0, "column blocks of whole sectors");
     const int ew = warp - 2, quad = warp & 3, g = ew >> 2;
     const int t_in = quad * 32 + lane;
     const int kap = kap0 + t_in;
-    const bool vec = (n & 1) == 0;                // 16-byte aligned column pairs
+    const bool vec = (n & 3) == 0;
     bool good = true;
     for (int b = 0; b < nblk; ++b) {
       const int t = b & 1;
       if (!mbar_wait(bar0 + 8u * (6 + t), (uint32_t)((b >> 1) & 1))) { good = false; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int ncb = min(CB, n - b * CB);
+      const uint32_t tcol = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(t * kNtile + g * 2 * RPT);
 #pragma unroll
-      for (int c2 = 0; c2 < CB; c2 += 2) {
-        if (c2 >= ncb) break;
-        const uint32_t tcol = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(t * kNtile);
-        uint32_t h0[2 * RPT], h1[2 * RPT];
-        tmem_ld_rows<RPT>(tcol + (uint32_t)((c2 * RG + g) * 2 * RPT), h0);
-        const bool two = c2 + 1 < ncb;
-        if (two) tmem_ld_rows<RPT>(tcol + (uint32_t)(((c2 + 1) * RG + g) * 2 * RPT), h1);
+      for (int c4 = 0; c4 < CB; c4 += 4) {
+        if (c4 >= ncb) break;
+        uint32_t h[4][2 * RPT];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (c4 + q < ncb) tmem_ld_rows<RPT>(tcol + (uint32_t)((c4 + q) * RG * 2 * RPT), h[q]);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (kap < K) {
 #pragma unroll
           for (int r = 0; r < RPT; ++r) {
             const int a = g * RPT + r;
             if (a >= m) continue;
-            float2* dst = A.Hserv + (((size_t)i * A.serv_stride * K + kap) * m + a) * n + b * CB + c2;
-            const float2 x0 = make_float2(__uint_as_float(h0[2 * r]), __uint_as_float(h0[2 * r + 1]));
-            if (two) {
-              const float2 x1 = make_float2(__uint_as_float(h1[2 * r]), __uint_as_float(h1[2 * r + 1]));
-              if (vec) {
-                *reinterpret_cast<float4*>(dst) = make_float4(x0.x, x0.y, x1.x, x1.y);
-              } else {
-                dst[0] = x0;
-                dst[1] = x1;
-              }
+            float2* dst = A.Hserv + (((size_t)i * A.serv_stride * K + kap) * m + a) * n + b * CB + c4;
+            if (vec && c4 + 4 <= ncb) {
+              asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(dst),
+                           "r"(h[0][2 * r]), "r"(h[0][2 * r + 1]), "r"(h[1][2 * r]), "r"(h[1][2 * r + 1]),
+                           "r"(h[2][2 * r]), "r"(h[2][2 * r + 1]), "r"(h[3][2 * r]), "r"(h[3][2 * r + 1])
+                           : "memory");
             } else {
-              dst[0] = x0;
+#pragma unroll
+              for (int q = 0; q < 4; ++q)
+                if (c4 + q < ncb)
+                  dst[q] = make_float2(__uint_as_float(h[q][2 * r]), __uint_as_float(h[q][2 * r + 1]));
             }
           }
         }

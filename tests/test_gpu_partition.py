@@ -80,6 +80,32 @@ def test_ranges_equal_the_whole_call_bit_for_bit(precoder, prec, mode):
         assert np.array_equal(fg, fw), bounds
 
 
+def test_warm_started_eigensolve_ranges():
+    """Serving channels from the serving pass (m n p > 8192): the eigensolve
+    runs in warm-started runs of 4 subcarriers aligned to the system's
+    subcarrier index.  Ranges that start at multiples of 4 reproduce the
+    whole call bit for bit; a range that starts inside a run restarts it
+    from scratch, so its first subcarriers agree to rounding (the flat
+    relative 1e-5 of the SINR) and the rest bit for bit."""
+    from tests.gpu_inputs import workload
+    w = workload(synth.SMALL, name="two-kernel precoder", J=3, M=16, m=16, N=80, n=64, P=40, p=32, L=8,
+                 K=300, sigma2=0.05)
+    assert w.m * w.n * w.p > 8192
+    case = Case(w)
+    for prec in (ts.TS_PREC_FP32, ts.TS_PREC_TF32X3):
+        whole, fw = _whole(case, "svd", prec, "paths")
+        got, fg = _ranges(case, "svd", prec, "paths", [(0, 100), (100, 300)])
+        assert np.array_equal(got, whole) and np.array_equal(fg, fw)
+        got, fg = _ranges(case, "svd", prec, "paths", [(0, 101), (101, 300)])
+        inside = np.zeros(w.K, bool)
+        inside[101:104] = True                      # the restarted part of the run [100, 104)
+        assert np.array_equal(got[:, ~inside], whole[:, ~inside])
+        assert np.array_equal(fg[:, ~inside], fw[:, ~inside])
+        assert np.all((fg[:, inside] & ts.TS_FLAG_ERRORS) == 0)
+        rel = np.abs(got[:, inside] - whole[:, inside]) / np.abs(whole[:, inside])
+        assert rel.max() <= 1e-5, rel.max()
+
+
 def test_range_arguments_are_checked():
     case = Case(synth.SMALL)
     cs, keep = case.coef_struct("paths")
