@@ -306,14 +306,7 @@ int ts_sinr_svd_from_precoders_prec(const ts_dims* d, const ts_coef* coef,
  * (dense coefficients: c[ch][d->K][P]).  Results and per-result flags of
  * the range only: sinr [J][count][L], flags [J][count]; they equal the same
  * subcarriers of a whole-system call bit for bit (the same arithmetic per
- * unit).  One exception: where the SVD precoders are computed from a
- * serving pass (m n p > 8192, m <= 16, n <= 512), their eigensolves run in
- * warm-started runs of 4 adjacent subcarriers aligned to multiples of 4 of
- * the system's subcarrier index, each started from its predecessor's
- * eigenvectors; a range whose kappa0 is not a multiple of 4 starts its
- * first run from scratch, and its first (up to 3) subcarriers then agree
- * with the whole-system call to rounding rather than bit for bit.
- * ws: ts_workspace_bytes of d with K = count, for the op of the
+ * unit).  ws: ts_workspace_bytes of d with K = count, for the op of the
  * call (TS_OP_SINR_SVD / _TF32 / _BF16X2 / _TF32X3 by precision, or
  * TS_OP_SINR_MMSE).  TS_ERR_DIMS unless 0 <= kappa0 and
  * kappa0 + count <= d->K. */

@@ -287,78 +287,6 @@ __device__ __forceinline__ void jacobi_sweep16(float2 (&S)[16], float2 (&U)[16],
   }
 }
 
-// S scaled to unit trace (eigenvectors and eigenvalue ratios are unchanged;
-// the singular values are taken from W = U* H~)
-template <int MG>
-__device__ __forceinline__ void scale_unit_trace(float2 (&S)[MG], int a) {
-  const float tr = gsum<MG>(pick(S, a).x);
-  const float sc = tr > 0.f ? 1.f / tr : 1.f;
-#pragma unroll
-  for (int b = 0; b < MG; ++b) S[b] = cscale(S[b], sc);
-}
-
-// Cyclic Jacobi on S held in registers (see jacobi_step), accumulating the
-// rotations into U, until the relative off-diagonal norm is below ~5e-7,
-// then one more sweep: Jacobi converges quadratically, so that sweep takes
-// the off-diagonal from ~5e-7 to rounding level.  Without it a pair of
-// eigenvalues a relative gap g apart keeps its eigenvectors mixed by
-// ~5e-7 / g (up to 3e-4 in the per-stream SINR for g ~ 1e-3); with it the
-// mixing is the FP32 Gram's own ~u / g.  The stopping decision is taken
-// warp-wide (extra sweeps leave a converged S unchanged).  Returns whether
-// this group's S converged.
-template <int MG>
-__device__ __forceinline__ bool jacobi_eig(float2 (&S)[MG], float2 (&U)[MG], int a) {
-  const int max_sweeps = MG <= 8 ? 11 : 13;
-  bool polish = false, converged = false;
-  for (int sweep = 0;; ++sweep) {
-    float off = 0.f, dia = 0.f;
-#pragma unroll
-    for (int b = 0; b < MG; ++b) {
-      const float v = cabs2(S[b]);
-      if (b == a) dia += v; else off += v;
-    }
-    off = gsum<MG>(off);
-    dia = gsum<MG>(dia);
-    converged = off <= 2.3e-13f * dia;
-    const bool all = __all_sync(FULL, converged);
-    if ((all && polish) || sweep == max_sweeps) break;
-    polish = all;
-    float dg = pick(S, a).x;
-    if constexpr (MG == 16) {
-      jacobi_sweep16(S, U, dg, a);
-    } else {
-#pragma unroll
-      for (int t = 0; t < MG - 1; ++t) jacobi_step<MG>(t, S, U, dg, a);
-    }
-  }
-  return converged;
-}
-
-// The rotations come from hardware reciprocal square roots and each is
-// applied in FP32, so U leaves the sweeps unitary only to ~1e-7 .. 1e-6:
-// its columns drift from unit norm (the serving effective channel
-// E_kk = U_L Sigma_L scales with them) and from each other (which the
-// close-pair rotation would amplify by lambda / gap).  One pass of modified
-// Gram-Schmidt over the columns makes U unitary to rounding; it moves each
-// column by the size of its defect only.
-template <int MG>
-__device__ __forceinline__ void orthonormalize_columns(float2 (&U)[MG]) {
-#pragma unroll
-  for (int b = 0; b < MG; ++b) {
-    const float nb = gsum<MG>(cabs2(U[b]));
-    U[b] = cscale(U[b], nb > 0.f ? 1.f / sqrtf(nb) : 1.f);
-#pragma unroll
-    for (int b2 = b + 1; b2 < MG; ++b2) {
-      // U[:, b2] -= (U[:, b]* U[:, b2]) U[:, b]
-      float2 pr = cz();
-      cmacc(pr, U[b2], U[b]);                     // U_ab2 conj(U_ab)
-      pr.x = gsum<MG>(pr.x);
-      pr.y = gsum<MG>(pr.y);
-      cms(U[b2], pr, U[b]);
-    }
-  }
-}
-
 // ------------------------------------------------------------------ phase 1
 // k_svd_precoder: one group of MG lanes per (BS k, subcarrier).  Forms the
 // serving link's compressed channel H~_kk (or reads it from workspace: large
@@ -470,123 +398,13 @@ __device__ __forceinline__ void serve_channels(const SinrArgs& A, const Precoder
   }
 }
 
-// PHASE 0: the whole precoder in one kernel.  Serving channels from the
-// serving pass take two kernels: k_svd_eig (Gram, Jacobi and Gram-Schmidt
-// only, the Gram accumulated over column chunks of H~ staged a chunk at a
-// time, so that a CTA holds little shared memory and many units hide the
-// Jacobi's latency; U and the eigenvalues go to workspace), then PHASE 2:
-// the rest from the stored U (W = U* H~, refinement, close pairs, V~, E_kk),
-// with H~ staged whole.
-constexpr int kEigChunk = 16;   // columns of H~ per staged chunk in k_svd_eig
-// Subcarriers per warm-started run of the eigensolve: runs start at
-// subcarriers (global index, kap_off included) that are multiples of it, so
-// that a subcarrier's result does not depend on the extent of the call.
-constexpr int kEigRun = 4;
-
-// The eigensolve of the two-kernel precoder, with warm starts: group g of MG lanes
-// walks the subcarriers of one run of kEigRun adjacent ones (BS k); the
-// first of the run is diagonalised from U = I, each later one from the
-// previous subcarrier's eigenvectors, S <- U* S U with U kept as the start
-// of the rotations.  Adjacent subcarriers have nearly the same Gram, so S
-// starts almost diagonal and the sweeps to the same stopping rule drop from
-// six or seven to about three; the transform costs less than half a sweep.
-// The Gram of every subcarrier is accumulated over column chunks of H~
-// (all groups together, as in k_svd_precoder), U and its product with S
-// pass through shared memory.  Writes U (row a in lane a), the eigenvalues
-// and the convergence of every unit, which k_svd_precoder<MG, LT, 2> reads.
-template <int MG>
-__global__ void __launch_bounds__(kThreads, 4) k_svd_eig(const SinrArgs A, int T, int SS, int off_U, int off_T) {
-  extern __shared__ __align__(16) float2 sm[];
-  const int tid = threadIdx.x, g = tid / MG, a = tid % MG;
-  const int nth = blockDim.x;
-  const int k = blockIdx.y;
-  const int m = A.m, n = A.n, K = A.K;
-  // global subcarrier of the CTA's first run start (runs aligned globally)
-  const int lead = A.kap_off % kEigRun;                  // local units before the first aligned start
-  const int kbase = blockIdx.x * T * kEigRun - lead;     // local subcarrier of run slot 0 of group 0
-  const int CS = kEigChunk + 1;
-  float2* chunk = sm;                                    // [t][row][CS], all groups
-  float2* Ub = sm + off_U + g * MG * SS;                 // the group's U
-  float2* Tb = sm + off_T + g * MG * SS;                 // S U
-  float2 S[MG], U[MG];
-  for (int r = 0; r < kEigRun; ++r) {
-    const int kap = kbase + g * kEigRun + r;
-    // Gram S = H~ H~* over column chunks (row a in lane a; zero rows for
-    // a >= m and outside the call's subcarriers)
-#pragma unroll
-    for (int b = 0; b < MG; ++b) S[b] = cz();
-    for (int c0 = 0; c0 < n; c0 += kEigChunk) {
-      __syncthreads();                                   // previous chunk consumed
-      for (int idx = tid; idx < T * MG * kEigChunk; idx += nth) {
-        const int c = idx % kEigChunk, aa = (idx / kEigChunk) % MG, t = idx / (kEigChunk * MG);
-        const int kk = kbase + t * kEigRun + r;
-        float2 v = cz();
-        if (aa < m && kk >= 0 && kk < K && c0 + c < n)
-          v = A.Hserv[(((size_t)k * A.serv_stride * K + kk) * m + aa) * n + c0 + c];
-        chunk[(t * MG + aa) * CS + c] = v;
-      }
-      __syncthreads();
-      const float2* cg = chunk + g * MG * CS;
-#pragma unroll 4
-      for (int c = 0; c < kEigChunk; ++c) {
-        const float2 x = cg[a * CS + c];
-#pragma unroll
-        for (int b = 0; b < MG; ++b) cmacc(S[b], x, cg[b * CS + c]);
-      }
-    }
-    scale_unit_trace<MG>(S, a);
-    // A subcarrier whose predecessor lies outside the call (the first of
-    // the call, in a run that starts before it) starts from U = I, which the
-    // transform below maps S to itself exactly.  The branch is on r only:
-    // the groups of a warp may sit at different run offsets, and the
-    // transform synchronises the whole warp.
-    if (r == 0 || kap - 1 < 0) {
-#pragma unroll
-      for (int b = 0; b < MG; ++b) U[b] = make_float2(b == a ? 1.f : 0.f, 0.f);
-    }
-    if (r > 0) {
-      // S <- U* S U with the previous subcarrier's eigenvectors (row a of U
-      // and of S in lane a; U and S U through shared memory)
-#pragma unroll
-      for (int b = 0; b < MG; ++b) Ub[a * SS + b] = U[b];
-      __syncwarp();
-      float2 Tr[MG];
-#pragma unroll
-      for (int b = 0; b < MG; ++b) Tr[b] = cz();
-#pragma unroll
-      for (int c = 0; c < MG; ++c) {
-        const float2 sac = S[c];
-#pragma unroll
-        for (int b = 0; b < MG; ++b) cmac(Tr[b], sac, Ub[c * SS + b]);
-      }
-#pragma unroll
-      for (int b = 0; b < MG; ++b) Tb[a * SS + b] = Tr[b];
-      __syncwarp();
-#pragma unroll
-      for (int b = 0; b < MG; ++b) S[b] = cz();
-#pragma unroll
-      for (int c = 0; c < MG; ++c) {
-        const float2 uca = cconj(Ub[c * SS + a]);
-#pragma unroll
-        for (int b = 0; b < MG; ++b) cmac(S[b], uca, Tb[c * SS + b]);
-      }
-      // U again from shared memory (it was only read there), so that it
-      // need not stay in registers through the products
-#pragma unroll
-      for (int b = 0; b < MG; ++b) U[b] = Ub[a * SS + b];
-      __syncwarp();                                      // Ub, Tb read before the next unit writes them
-    }
-    const bool converged = jacobi_eig<MG>(S, U, a);
-    orthonormalize_columns<MG>(U);
-    if (kap >= 0 && kap < K) {
-      const size_t ueig = ((size_t)k * K + kap) * MG;
-#pragma unroll
-      for (int b = 0; b < MG; ++b) A.Ueig[(ueig + a) * MG + b] = U[b];
-      A.lam_eig[ueig + a] = pick(S, a).x;
-      if (a == 0) A.conv_eig[(size_t)k * K + kap] = converged ? 1 : 0;
-    }
-  }
-}
+// PHASE 0: the whole precoder in one kernel.  PHASE 1 (serving channels
+// from the serving pass): Gram, Jacobi and Gram-Schmidt only, the Gram
+// accumulated over column chunks of H~ staged a chunk at a time, so that a
+// CTA holds little shared memory and many units hide the Jacobi's latency;
+// U and the eigenvalues go to workspace.  PHASE 2: the rest from the stored
+// U (W = U* H~, refinement, close pairs, V~, E_kk), with H~ staged whole.
+constexpr int kEigChunk = 16;   // columns of H~ per staged chunk in PHASE 1
 
 template <int MG, int LT, int PHASE>
 __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, const PrecoderPlan pl) {
@@ -605,9 +423,36 @@ __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, con
 
   float2 S[MG], U[MG];
   bool converged = false;
+  if (PHASE == 1) {
+    // Gram over column chunks: chunk [t][row][kEigChunk + 1] in the Hs region
+#pragma unroll
+    for (int b = 0; b < MG; ++b) S[b] = cz();
+    const int CS = kEigChunk + 1;
+    float2* ch = sm + pl.off_Hs;
+    for (int c0 = 0; c0 < n; c0 += kEigChunk) {
+      __syncthreads();                               // previous chunk consumed
+      for (int idx = tid; idx < T * MG * kEigChunk; idx += nth) {
+        const int c = idx % kEigChunk, aa = (idx / kEigChunk) % MG, t = idx / (kEigChunk * MG);
+        const int kk = kap0 + t;
+        float2 v = cz();
+        if (aa < m && kk < K && c0 + c < n)
+          v = A.Hserv[(((size_t)k * A.serv_stride * K + kk) * m + aa) * n + c0 + c];
+        ch[(t * MG + aa) * CS + c] = v;
+      }
+      __syncthreads();
+      const float2* cg = ch + g * MG * CS;
+#pragma unroll 4
+      for (int c = 0; c < kEigChunk; ++c) {
+        const float2 x = cg[a * CS + c];
+#pragma unroll
+        for (int b = 0; b < MG; ++b) cmacc(S[b], x, cg[b * CS + c]);
+      }
+    }
+  }
   // H~_kk rows of the T subcarriers (zero rows for a >= m and beyond K),
   // formed here or read from the all-link rebuild of the adjoint
-  if (A.fuse_serve) {
+  if (PHASE == 1) {
+  } else if (A.fuse_serve) {
     serve_channels<MG>(A, pl, k, kap0, sm);
   } else {
     for (int idx = tid; idx < T * MG * n; idx += nth) {
@@ -633,12 +478,82 @@ __global__ void __launch_bounds__(kThreads) k_svd_precoder(const SinrArgs A, con
       for (int b = 0; b < MG; ++b) cmacc(S[b], x, Hs[b * pl.SH + c]);
     }
   }
-  if (PHASE == 0) {
-    scale_unit_trace<MG>(S, a);
-    converged = jacobi_eig<MG>(S, U, a);
-    orthonormalize_columns<MG>(U);
+  if (PHASE != 2) {
+
+  // scale S to unit trace (eigenvectors and eigenvalue ratios are unchanged;
+  // the singular values are taken from W below)
+  {
+    const float tr = gsum<MG>(pick(S, a).x);
+    const float sc = tr > 0.f ? 1.f / tr : 1.f;
+#pragma unroll
+    for (int b = 0; b < MG; ++b) S[b] = cscale(S[b], sc);
   }
+  // Cyclic Jacobi on S held in registers (see jacobi_step), until the
+  // relative off-diagonal norm is below ~5e-7, then one more sweep: Jacobi
+  // converges quadratically, so that sweep takes the off-diagonal from
+  // ~5e-7 to rounding level.  Without it a pair of eigenvalues a relative
+  // gap g apart keeps its eigenvectors mixed by ~5e-7 / g (up to 3e-4 in
+  // the per-stream SINR for g ~ 1e-3); with it the mixing is the FP32
+  // Gram's own ~u / g.  The stopping decision is taken warp-wide (extra
+  // sweeps leave a converged S unchanged).
+  const int max_sweeps = MG <= 8 ? 11 : 13;
+  bool polish = false;
+  for (int sweep = 0;; ++sweep) {
+    float off = 0.f, dia = 0.f;
+#pragma unroll
+    for (int b = 0; b < MG; ++b) {
+      const float v = cabs2(S[b]);
+      if (b == a) dia += v; else off += v;
+    }
+    off = gsum<MG>(off);
+    dia = gsum<MG>(dia);
+    converged = off <= 2.3e-13f * dia;
+    const bool all = __all_sync(FULL, converged);
+    if ((all && polish) || sweep == max_sweeps) break;
+    polish = all;
+    float dg = pick(S, a).x;
+    if constexpr (MG == 16) {
+      jacobi_sweep16(S, U, dg, a);
+    } else {
+#pragma unroll
+      for (int t = 0; t < MG - 1; ++t) jacobi_step<MG>(t, S, U, dg, a);
+    }
+  }
+  // The rotations come from hardware reciprocal square roots and each is
+  // applied in FP32, so U leaves the sweeps unitary only to ~1e-7 .. 1e-6:
+  // its columns drift from unit norm (the serving effective channel
+  // E_kk = U_L Sigma_L below scales with them) and from each other (which
+  // the close-pair rotation below would amplify by lambda / gap).  One pass
+  // of modified Gram-Schmidt over the columns makes U unitary to rounding;
+  // it moves each column by the size of its defect only.
+  {
+#pragma unroll
+    for (int b = 0; b < MG; ++b) {
+      const float nb = gsum<MG>(cabs2(U[b]));
+      U[b] = cscale(U[b], nb > 0.f ? 1.f / sqrtf(nb) : 1.f);
+#pragma unroll
+      for (int b2 = b + 1; b2 < MG; ++b2) {
+        // U[:, b2] -= (U[:, b]* U[:, b2]) U[:, b]
+        float2 pr = cz();
+        cmacc(pr, U[b2], U[b]);                     // U_ab2 conj(U_ab)
+        pr.x = gsum<MG>(pr.x);
+        pr.y = gsum<MG>(pr.y);
+        cms(U[b2], pr, U[b]);
+      }
+    }
+  }
+  }  // PHASE != 2
   const size_t ueig = ((size_t)k * K + (kap < K ? kap : K - 1)) * MG;
+  if (PHASE == 1) {
+    // U (row a in lane a), the eigenvalues and the convergence to workspace
+    if (kap < K) {
+#pragma unroll
+      for (int b = 0; b < MG; ++b) A.Ueig[(ueig + a) * MG + b] = U[b];
+      A.lam_eig[ueig + a] = pick(S, a).x;
+      if (a == 0) A.conv_eig[(size_t)k * K + kap] = converged ? 1 : 0;
+    }
+    return;
+  }
   if (PHASE == 2) {
 #pragma unroll
     for (int b = 0; b < MG; ++b) {
@@ -1635,16 +1550,14 @@ cudaError_t run_precoder(const SinrArgs& A, cudaStream_t s) {
   if (!fused && A.Ueig != nullptr) {
     // two phases: the eigensolve with little shared memory per CTA (many
     // units resident), then the rest with H~ staged whole
-    // (the eigensolve in warm-started runs of kEigRun adjacent subcarriers,
-    // aligned to the global subcarrier index)
-    const int T1 = kThreads / MG, SS = MG + 1;
-    const int off_U = T1 * MG * (kEigChunk + 1), off_T = off_U + T1 * MG * SS;
-    const size_t smem1 = (size_t)(off_T + T1 * MG * SS) * sizeof(float2);
-    const int runs = (A.K + A.kap_off % kEigRun + kEigRun - 1) / kEigRun;
-    auto k1 = k_svd_eig<MG>;
+    const int T1 = kThreads / MG;
+    PrecoderPlan p1 = precoder_plan(MG, T1, kEigChunk, A.p, false);
+    p1.total = T1 * MG * (kEigChunk + 1);         // PHASE 1 uses the chunk region only
+    const size_t smem1 = (size_t)p1.total * sizeof(float2);
+    auto k1 = k_svd_precoder<MG, LT, 1>;
     cudaError_t e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
     if (e != cudaSuccess) return e;
-    k1<<<dim3((runs + T1 - 1) / T1, A.J), T1 * MG, smem1, s>>>(A, T1, SS, off_U, off_T);
+    k1<<<dim3((A.K + T1 - 1) / T1, A.J), T1 * MG, smem1, s>>>(A, p1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     auto k2 = k_svd_precoder<MG, LT, 2>;
     if ((e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)

@@ -80,13 +80,12 @@ def test_ranges_equal_the_whole_call_bit_for_bit(precoder, prec, mode):
         assert np.array_equal(fg, fw), bounds
 
 
-def test_warm_started_eigensolve_ranges():
-    """Serving channels from the serving pass (m n p > 8192): the eigensolve
-    runs in warm-started runs of 4 subcarriers aligned to the system's
-    subcarrier index.  Ranges that start at multiples of 4 reproduce the
-    whole call bit for bit; a range that starts inside a run restarts it
-    from scratch, so its first subcarriers agree to rounding (the flat
-    relative 1e-5 of the SINR) and the rest bit for bit."""
+def test_two_kernel_precoder_ranges():
+    """Serving channels from the serving pass (m n p > 8192: the serving
+    pass, then the eigensolve and the rest of the precoder as two kernels,
+    and in TF32X3 the serving channels on the tensor cores): ranges
+    reproduce the whole call bit for bit, split at a multiple of the
+    kernels' tiles or not."""
     from tests.gpu_inputs import workload
     w = workload(synth.SMALL, name="two-kernel precoder", J=3, M=16, m=16, N=80, n=64, P=40, p=32, L=8,
                  K=300, sigma2=0.05)
@@ -94,16 +93,10 @@ def test_warm_started_eigensolve_ranges():
     case = Case(w)
     for prec in (ts.TS_PREC_FP32, ts.TS_PREC_TF32X3):
         whole, fw = _whole(case, "svd", prec, "paths")
-        got, fg = _ranges(case, "svd", prec, "paths", [(0, 100), (100, 300)])
-        assert np.array_equal(got, whole) and np.array_equal(fg, fw)
-        got, fg = _ranges(case, "svd", prec, "paths", [(0, 101), (101, 300)])
-        inside = np.zeros(w.K, bool)
-        inside[101:104] = True                      # the restarted part of the run [100, 104)
-        assert np.array_equal(got[:, ~inside], whole[:, ~inside])
-        assert np.array_equal(fg[:, ~inside], fw[:, ~inside])
-        assert np.all((fg[:, inside] & ts.TS_FLAG_ERRORS) == 0)
-        rel = np.abs(got[:, inside] - whole[:, inside]) / np.abs(whole[:, inside])
-        assert rel.max() <= 1e-5, rel.max()
+        for bounds in ([(0, 100), (100, 300)], [(0, 101), (101, 300)], [(0, 1), (1, 257), (257, 300)]):
+            got, fg = _ranges(case, "svd", prec, "paths", bounds)
+            assert np.array_equal(got, whole), (prec, bounds)
+            assert np.array_equal(fg, fw), (prec, bounds)
 
 
 def test_range_arguments_are_checked():
