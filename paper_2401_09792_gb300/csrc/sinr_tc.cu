@@ -697,15 +697,28 @@ __global__ void __launch_bounds__(32 * (2 + 4 * tc_rg(MG)), 1)
     if (!good) *abort_v = 1;
     // rows of the interfering effective channel E_ik (eq. 24); the
     // finalisation forms the covariance of eq. (25)
+    // (four streams, one 32-byte sector, per store when L is a multiple of
+    // 4, so that every row starts on a sector)
     if (good && kap < K) {
 #pragma unroll
       for (int r = 0; r < RPT; ++r) {
         const int a = g * RPT + r;
         if (a >= m) continue;
         float2* Eout = A.Eint + ((((size_t)i * (J - 1) + z) * K + kap) * m + a) * L;
+        if ((L & 3) == 0) {
 #pragma unroll
-        for (int l = 0; l < LT; ++l)
-          if (l < L) Eout[l] = E[r][l];
+          for (int l4 = 0; l4 < LT / 4; ++l4)
+            if (4 * l4 < L)
+              asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(Eout + 4 * l4),
+                           "f"(E[r][4 * l4].x), "f"(E[r][4 * l4].y), "f"(E[r][4 * l4 + 1].x),
+                           "f"(E[r][4 * l4 + 1].y), "f"(E[r][4 * l4 + 2].x), "f"(E[r][4 * l4 + 2].y),
+                           "f"(E[r][4 * l4 + 3].x), "f"(E[r][4 * l4 + 3].y)
+                           : "memory");
+        } else {
+#pragma unroll
+          for (int l = 0; l < LT; ++l)
+            if (l < L) Eout[l] = E[r][l];
+        }
       }
     }
   }
