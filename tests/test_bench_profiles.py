@@ -44,3 +44,23 @@ def test_paper64_traffic_scales_the_eight_cell_capture(tmp_path, monkeypatch):
         assert synth.WORKLOADS["paper64_j8"].J == 8
     finally:
         bench.select_workload("mid")
+
+
+def test_launch_counts_follow_the_measured_kernel_sequences():
+    """gpu_launches in the bench line: the kernels of one SVD-precoded call,
+    as the ncu launch lists of the differentiation and mid steps show them
+    (phase steps, [core operand, projections, serving projections, serving
+    pass,] eigensolve, precoder rest, close pairs, [precoder tiles,] link
+    pass, finalize, refine)."""
+    from paper_2401_09792_gb300 import tuckersinr as ts
+    diff, mid = synth.WORKLOADS["diff"], synth.WORKLOADS["mid"]
+    # the two-kernel precoder, the tensor-core serving pass and link pass
+    assert bench.svd_launches(diff, ts.TS_PREC_TF32X3) == 12
+    # FP32: the serving pass of the link kernel, one link launch
+    assert bench.svd_launches(diff, ts.TS_PREC_FP32) == 8
+    # TF32 keeps the FP32 serving pass
+    assert bench.svd_launches(diff, ts.TS_PREC_TF32) == 11
+    # mid: the precoder forms the serving channels itself (one kernel)
+    assert mid.m * mid.n * mid.p <= 8192
+    assert bench.svd_launches(mid, ts.TS_PREC_TF32X3) == 9
+    assert bench.svd_launches(mid, ts.TS_PREC_FP32) == 6
