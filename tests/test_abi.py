@@ -85,6 +85,25 @@ def test_workspace_sizes(lib):
     assert bf16 >= svd + nch * (2 * m * n) * (6 * p) * 2
 
 
+def test_tensor_core_operand_layout(lib):
+    """The tensor-core workspace beyond the svd one, on the default system
+    (J = 2, m = 4 -> 4-row lane groups, n = 8, p = 4, L = 2, K = 64): 128
+    accumulator columns per block hold 128 / (2 * 4) = 16 columns of H~, so
+    one block per link and one 128-subcarrier tile; an operand row holds the
+    2p = 8 K-elements per segment (TF32: 4 bytes, one segment; TF32X3: hi and
+    lo).  Core: J^2 links x 1 block x 128 rows; projections: J (J - 1)
+    interfering links x 1 tile x 128 rows, and with TF32X3 also J serving
+    links; precoder rows: J BSs x 1 tile x 1 block x 128 subcarriers x
+    (16 columns x L = 32) complex, a whole number of 8-piece rows."""
+    d = _dims()
+    svd = lib.ts_workspace_bytes(ctypes.byref(d), 0)
+    J, rows, vtile = 2, 128, 128 * 16 * 2 * 8
+    for op, kbytes, serving in ((7, 8 * 4, 0), (14, 2 * 8 * 4, J)):
+        core = J * J * rows * kbytes
+        proj = (J * (J - 1) + serving) * rows * kbytes
+        assert lib.ts_workspace_bytes(ctypes.byref(d), op) - svd == core + proj + J * vtile, op
+
+
 def test_wide_cores_only_on_the_svd_path(lib):
     # p > 32 or P p > 8192: the SVD path streams the core (wide-core kernel);
     # the wideband-precoder path, the adjoints and the tensor-core modes stage
