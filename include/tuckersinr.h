@@ -510,8 +510,8 @@ int ts_project_precoder_adjoint(const ts_dims* d, const ts_c64* Pfull,
  *     each device also loads the library's module there, which commits the
  *     array: it may synchronise the device, and it fails with a CUDA error
  *     (TS_ERR_CUDA) if the device has no room left.  Make that first call at
- *     start-up -- before any stream capture and before a framework reserves
- *     the device's memory; later calls change no allocation.
+ *     start-up, before a framework reserves the device's memory; later calls
+ *     change no allocation.
  *   - Every call shares the one array per device, which keeps the previous
  *     call's contents (nothing needs clearing: each call writes every byte
  *     it reads).  Calls that overlap on the GPU -- on two streams, or from
